@@ -252,14 +252,17 @@ class Tomography:
         for _ in range(iters):
             q = self.apply_normal(p)
             pq = float(p @ q)
-            if not pq > 0.0:
+            if pq == 0.0 and rz == 0.0:
+                a = 0.0                      # r = 0: the iterate is exact, CG stops moving
+            elif not pq > 0.0:
                 raise FloatingPointError("p.Ap <= 0: operator not positive definite")
-            a = rz / pq
+            else:
+                a = rz / pq
             x = x + a * p
             r = r - a * q
             z = r / precond if precond is not None else r.copy()
             rz_new = float(r @ z)
-            beta = rz_new / rz
+            beta = rz_new / rz if rz != 0.0 else 0.0
             if history is not None:
                 history.append((x.copy(), r.copy(), z.copy(), p.copy(), a, beta))
             p = z + beta * p
