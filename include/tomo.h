@@ -1,0 +1,196 @@
+/*
+ * tomo.h - C ABI of the GB300 wavelet-domain MAP tomography solver.
+ *
+ * The library solves, for one or many adaptive-optics systems, the normal
+ * equations of the MAP atmospheric-tomography problem in a wavelet basis
+ * (Helin & Yudytskiy, "Wavelet methods in multi-conjugate adaptive optics",
+ * Sec. 5.1, eq. eqn_lse):
+ *
+ *     (A~^T C^-1 A~ + alpha D) c = A~^T C^-1 s,      A~ = Gamma P W^-1,
+ *
+ * with W the per-layer periodic orthonormal Daubechies transform (Sec. 5.1),
+ * P the guide-star ray-trace with the laser-guide-star cone effect (Sec. 2.1,
+ * eq. ngsproj and the LGS projection), Gamma the Fried-geometry Shack-Hartmann
+ * slope operator (eqs. SH_eq / SH_op), C the block-diagonal noise covariance
+ * with LGS tip/tilt removal (Sec. 4.3, eqs. removing_tt / widehatc) and D the
+ * diagonal wavelet-domain von Karman prior (Sec. 3).  The system is solved by
+ * CG or by PCG with the modified Jacobi preconditioner of Sec. 5.1, for a fixed
+ * number of iterations, warm-started from the previous frame.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - All device pointers are CUDA device memory owned by the caller; the
+ *   library never frees them.  Host pointers are read during the call only.
+ * - Element type of every device array: float when the geometry's
+ *   precision == 0, double when precision == 1 (tomo_jacobi_diagonal always
+ *   writes double).
+ * - Layer grids: layers concatenated in declaration order, each N_l x N_l,
+ *   row-major with the row index = y; node (ix, iy) sits at
+ *   ((ix - N/2) dx, (iy - N/2) dx) in metres; grids are periodic.
+ * - Coefficients: layers concatenated, each N_l x N_l in the Mallat pyramid
+ *   layout of the periodic 2-D DWT (rows = x transformed first, then columns):
+ *   level k occupies the top-left block of side N/2^(k-1); its quadrants are
+ *   [low-low (next level), high-x; high-y, high-high].
+ * - Slopes: sensors concatenated in declaration order; a full sensor gives
+ *   [sx of each valid subaperture, then sy], valid subapertures in row-major
+ *   order (row = y index); a tip/tilt-only sensor gives [mean sx, mean sy].
+ *   Slopes are phase differences across one subaperture (rad).
+ * - Every call enqueues its work on `cuda_stream` (a cudaStream_t, NULL = the
+ *   legacy default stream) and returns without waiting, unless stated.
+ * - Errors: a non-zero tomo_status; tomo_last_error() gives a message
+ *   (thread-local).  No C++ exception crosses this boundary.  A plan is not
+ *   thread-safe: do not use one plan from two threads at once.
+ */
+#ifndef TOMO_H
+#define TOMO_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tomo_plan tomo_plan;     /* opaque; created and owned by the library */
+
+typedef enum {
+  TOMO_OK = 0,
+  TOMO_ERR_ARG = 1,          /* a NULL pointer, a size or a flag out of range */
+  TOMO_ERR_GEOMETRY = 2,     /* a footprint wider than its layer grid, no valid subaperture, ... */
+  TOMO_ERR_LEVELS = 3,       /* N/2^(levels-1) < filter length, or N not a power of two */
+  TOMO_ERR_NOMEM = 4,        /* device or host allocation failed */
+  TOMO_ERR_CUDA = 5,         /* a CUDA runtime call failed (message has the CUDA error) */
+  TOMO_ERR_TIMEOUT = 6,      /* reserved for waits with a deadline */
+  TOMO_ERR_BREAKDOWN = 7,    /* p.Ap <= 0 or not finite during (P)CG: iterate frozen */
+  TOMO_ERR_UNSUPPORTED = 8   /* valid request this build does not implement */
+} tomo_status;
+
+/* One wavefront sensor (Sec. 2.1, Sec. 4.3). */
+typedef struct {
+  double theta_x, theta_y;     /* guide-star direction (rad) */
+  double height;               /* laser guide star altitude H (m); INFINITY or <= 0: natural star */
+  int n_sub;                   /* subapertures per side (>= 1) */
+  double d_sub;                /* subaperture side (m, > 0) */
+  const unsigned char *valid;  /* host, n_sub*n_sub, row = y; nonzero = valid.  NULL: the circular
+                                  pupil rule (centre radius within [obstruction*D/2, D/2]) */
+  double sigma;                /* noise standard deviation per slope (rad, > 0) */
+  int tt_only;                 /* 1: the sensor reports only the two mean slopes (tip/tilt NGS) */
+  int remove_tt;               /* 1: tip/tilt removal, C^-1 -> (I-T) sigma^-2 (I-T) (LGS) */
+} tomo_wfs;
+
+/* One turbulence layer (Sec. 2.1 layered model, Sec. 3 prior). */
+typedef struct {
+  double altitude;             /* h_l (m, >= 0) */
+  double dx;                   /* grid spacing (m, > 0) */
+  int N;                       /* grid side, a power of two >= 16 */
+  double prior_weight;         /* 1/c_rho(h_l) of D_l (> 0) */
+} tomo_layer;
+
+typedef struct {
+  double D_tel;                /* pupil diameter (m); used by the NULL-mask rule */
+  double obstruction;          /* central obstruction as a radius ratio in [0, 1) */
+  int n_wfs;
+  const tomo_wfs *wfs;         /* host array of n_wfs */
+  int n_layers;
+  const tomo_layer *layers;    /* host array of n_layers */
+  int wavelet_order;           /* Daubechies vanishing moments p, 1..4 (filter length 2p; 3 = paper) */
+  int levels;                  /* DWT levels J >= 1 */
+  double alpha;                /* regularisation weight of D (>= 0) */
+  double L0;                   /* outer scale (m); <= 0 drops the L0^(-11/3) term of D */
+  int precond;                 /* 0: CG, 1: modified Jacobi PCG (Sec. 5.1) */
+  int precision;               /* 0: FP32 operator with FP64 dot products and scalars; 1: FP64 */
+} tomo_geometry;
+
+typedef struct {
+  long long n_coeffs;          /* unknowns = sum of N_l^2 (= layer-grid elements) */
+  long long n_slopes;          /* elements of the slope vector */
+  int n_layers, n_wfs;
+  int cluster_size;            /* CTAs per layer in the transform kernels */
+  int kernels_per_iteration;   /* kernel launches per PCG iteration */
+  int kernels_per_solve_base;  /* launches per solve besides the iterations (warm start) */
+  long long device_bytes;      /* device memory held by the plan */
+  long long bytes_per_iteration; /* algorithmic bytes moved per PCG iteration (see DESIGN) */
+  int precision;
+} tomo_plan_info;
+
+/* Build a plan: validates `g`, copies every host input, builds the index
+ * tables, the prior D and the Jacobi diagonal (Sec. 5.1, computed exactly on
+ * the device), and allocates the workspace.  Synchronises `cuda_stream`.
+ * On success *out owns device memory until tomo_destroy. */
+tomo_status tomo_plan_create(const tomo_geometry *g, void *cuda_stream, tomo_plan **out);
+
+/* One frame (Sec. 5.1): b = A~^T C^-1 s from d_slopes, r0 = b - (A~^T C^-1 A~ + alpha D) x0,
+ * then exactly `iters` (P)CG iterations (Hestenes-Stiefel).
+ * d_slopes: n_slopes elements (read).  d_coeffs: n_coeffs elements; read as x0 when
+ * warm != 0 (warm restart: the previous frame's solution), ignored otherwise (x0 = 0);
+ * overwritten with x.  out_resnorm: host, may be NULL; when given the call waits for
+ * the stream and stores ||r|| (2-norm of the final recurrence residual); a breakdown
+ * is reported only then (TOMO_ERR_BREAKDOWN). */
+tomo_status tomo_solve(tomo_plan *p, const void *d_slopes, void *d_coeffs, int iters,
+                       int warm, void *cuda_stream, double *out_resnorm);
+
+/* `count` independent frames of `count` distinct plans that share precision and
+ * precond, solved together: every phase of the iteration is one launch for all
+ * of them.  plans/d_slopes/d_coeffs: host arrays of `count`; same per-plan
+ * semantics as tomo_solve. */
+tomo_status tomo_solve_batch(tomo_plan *const *plans, const void *const *d_slopes,
+                             void *const *d_coeffs, int count, int iters, int warm,
+                             void *cuda_stream);
+
+/* W^-1 (synthesis): d_coeffs (n_coeffs) -> d_layers (n_coeffs).  Sec. 5.1. */
+tomo_status tomo_coeffs_to_layers(tomo_plan *p, const void *d_coeffs, void *d_layers,
+                                  void *cuda_stream);
+
+/* W (analysis): d_layers (n_coeffs) -> d_coeffs (n_coeffs). */
+tomo_status tomo_layers_to_coeffs(tomo_plan *p, const void *d_layers, void *d_coeffs,
+                                  void *cuda_stream);
+
+/* Noise-free measurement A phi (eq. atm_tomo): d_layers (n_coeffs) -> d_slopes (n_slopes). */
+tomo_status tomo_layers_to_slopes(tomo_plan *p, const void *d_layers, void *d_slopes,
+                                  void *cuda_stream);
+
+/* Normal operator of eq. eqn_lse: d_out = (A~^T C^-1 A~ + alpha D) d_in (n_coeffs each).
+ * d_in and d_out must not overlap. */
+tomo_status tomo_apply_normal(tomo_plan *p, const void *d_in, void *d_out, void *cuda_stream);
+
+/* Right-hand side of eq. eqn_lse: d_out = A~^T C^-1 d_slopes (n_coeffs). */
+tomo_status tomo_rhs(tomo_plan *p, const void *d_slopes, void *d_out, void *cuda_stream);
+
+/* The modified Jacobi diagonal J (Sec. 5.1, including alpha D): n_coeffs doubles. */
+tomo_status tomo_jacobi_diagonal(tomo_plan *p, double *d_out, void *cuda_stream);
+
+/* Sizes and launch facts of a plan. */
+tomo_status tomo_plan_get_info(const tomo_plan *p, tomo_plan_info *out);
+
+/* Device memory held by the plan (bytes; 0 for NULL), for admission by memory. */
+size_t tomo_plan_device_bytes(const tomo_plan *p);
+
+/* Per-kernel timing: when enabled, every launch of the plan is bracketed by CUDA
+ * events; tomo_get_kernel_times returns, per kernel kind, the number of timed
+ * launches and their summed milliseconds since the last reset (waits for the
+ * stream).  Kinds: 0 transform-synthesis, 1 ray-trace/slopes, 2 adjoint+analysis,
+ * 3 vector update, 4 other.  n_kinds = 5. */
+tomo_status tomo_set_kernel_timing(tomo_plan *p, int enable);
+tomo_status tomo_get_kernel_times(tomo_plan *p, int *counts, double *ms, int n_kinds);
+
+/* Launch mode of tomo_solve: 1 (default) captures each distinct (slopes, coeffs,
+ * iters, warm) call once into a CUDA graph and replays it; 0 launches every
+ * kernel directly (one launch per kernel per call, no graph). */
+tomo_status tomo_set_launch_mode(tomo_plan *p, int use_graphs);
+
+/* Number of kernels this library has launched so far in this process. */
+long long tomo_launch_count(void);
+
+/* Thread-local message of the last failing call ("" if none). */
+const char *tomo_last_error(void);
+
+/* Release a plan and its device memory (waits for its work).  NULL-safe. */
+void tomo_destroy(tomo_plan *p);
+
+/* Library version string. */
+const char *tomo_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TOMO_H */

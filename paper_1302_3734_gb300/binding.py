@@ -1,0 +1,273 @@
+"""ctypes binding of ``libtomo.so`` (include/tomo.h): argument marshalling only.
+
+Every step of the solve runs in the library's CUDA kernels; this module only
+converts a geometry ``dict`` (see ``synth.configs``) into the C structs, checks
+tensor shapes/dtypes/devices, and passes raw device pointers and the current
+CUDA stream.  There is no fallback: if the library is missing or a call fails,
+an exception is raised.
+"""
+import ctypes
+import math
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtomo.so")
+
+STATUS = {0: "TOMO_OK", 1: "TOMO_ERR_ARG", 2: "TOMO_ERR_GEOMETRY", 3: "TOMO_ERR_LEVELS",
+          4: "TOMO_ERR_NOMEM", 5: "TOMO_ERR_CUDA", 6: "TOMO_ERR_TIMEOUT",
+          7: "TOMO_ERR_BREAKDOWN", 8: "TOMO_ERR_UNSUPPORTED"}
+
+KERNEL_KINDS = ("synthesis", "forward", "analysis", "update", "other")
+
+
+class TomoError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Wfs(ctypes.Structure):
+    _fields_ = [("theta_x", ctypes.c_double), ("theta_y", ctypes.c_double),
+                ("height", ctypes.c_double), ("n_sub", ctypes.c_int),
+                ("d_sub", ctypes.c_double), ("valid", ctypes.POINTER(ctypes.c_ubyte)),
+                ("sigma", ctypes.c_double), ("tt_only", ctypes.c_int),
+                ("remove_tt", ctypes.c_int)]
+
+
+class Layer(ctypes.Structure):
+    _fields_ = [("altitude", ctypes.c_double), ("dx", ctypes.c_double),
+                ("N", ctypes.c_int), ("prior_weight", ctypes.c_double)]
+
+
+class Geometry(ctypes.Structure):
+    _fields_ = [("D_tel", ctypes.c_double), ("obstruction", ctypes.c_double),
+                ("n_wfs", ctypes.c_int), ("wfs", ctypes.POINTER(Wfs)),
+                ("n_layers", ctypes.c_int), ("layers", ctypes.POINTER(Layer)),
+                ("wavelet_order", ctypes.c_int), ("levels", ctypes.c_int),
+                ("alpha", ctypes.c_double), ("L0", ctypes.c_double),
+                ("precond", ctypes.c_int), ("precision", ctypes.c_int)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("n_coeffs", ctypes.c_longlong), ("n_slopes", ctypes.c_longlong),
+                ("n_layers", ctypes.c_int), ("n_wfs", ctypes.c_int),
+                ("cluster_size", ctypes.c_int), ("kernels_per_iteration", ctypes.c_int),
+                ("kernels_per_solve_base", ctypes.c_int), ("device_bytes", ctypes.c_longlong),
+                ("bytes_per_iteration", ctypes.c_longlong), ("precision", ctypes.c_int)]
+
+
+# (name, restype, argtypes) of every symbol declared in include/tomo.h
+_VP = ctypes.c_void_p
+_I = ctypes.c_int
+SIGNATURES = [
+    ("tomo_plan_create", _I, [ctypes.POINTER(Geometry), _VP, ctypes.POINTER(_VP)]),
+    ("tomo_solve", _I, [_VP, _VP, _VP, _I, _I, _VP, ctypes.POINTER(ctypes.c_double)]),
+    ("tomo_solve_batch", _I, [ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP),
+                              _I, _I, _I, _VP]),
+    ("tomo_coeffs_to_layers", _I, [_VP, _VP, _VP, _VP]),
+    ("tomo_layers_to_coeffs", _I, [_VP, _VP, _VP, _VP]),
+    ("tomo_layers_to_slopes", _I, [_VP, _VP, _VP, _VP]),
+    ("tomo_apply_normal", _I, [_VP, _VP, _VP, _VP]),
+    ("tomo_rhs", _I, [_VP, _VP, _VP, _VP]),
+    ("tomo_jacobi_diagonal", _I, [_VP, _VP, _VP]),
+    ("tomo_plan_get_info", _I, [_VP, ctypes.POINTER(PlanInfo)]),
+    ("tomo_plan_device_bytes", ctypes.c_size_t, [_VP]),
+    ("tomo_set_kernel_timing", _I, [_VP, _I]),
+    ("tomo_get_kernel_times", _I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double), _I]),
+    ("tomo_set_launch_mode", _I, [_VP, _I]),
+    ("tomo_launch_count", ctypes.c_longlong, []),
+    ("tomo_last_error", ctypes.c_char_p, []),
+    ("tomo_destroy", None, [_VP]),
+    ("tomo_version", ctypes.c_char_p, []),
+]
+
+_lib = None
+
+
+def load_library(path=LIB_PATH):
+    """Load libtomo.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with paper_1302_3734_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status):
+    if status != 0:
+        raise TomoError(status, load_library().tomo_last_error().decode())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def geometry_struct(geom):
+    """C structs of a geometry dict; returns (Geometry, keep-alive list)."""
+    keep = []
+    ws = (Wfs * len(geom["wfs"]))()
+    for i, w in enumerate(geom["wfs"]):
+        ws[i].theta_x, ws[i].theta_y = float(w["theta"][0]), float(w["theta"][1])
+        h = float(w["height"])
+        ws[i].height = h if math.isfinite(h) else math.inf
+        ws[i].n_sub = int(w["n_sub"])
+        ws[i].d_sub = float(w["d_sub"])
+        if w.get("valid") is not None:
+            v = np.ascontiguousarray(np.asarray(w["valid"], dtype=np.uint8))
+            if v.shape != (w["n_sub"], w["n_sub"]):
+                raise ValueError("valid mask must be [n_sub, n_sub]")
+            keep.append(v)
+            ws[i].valid = v.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte))
+        else:
+            ws[i].valid = None
+        ws[i].sigma = float(w["sigma"])
+        ws[i].tt_only = int(bool(w["tt_only"]))
+        ws[i].remove_tt = int(bool(w["remove_tt"]))
+    ls = (Layer * len(geom["layers"]))()
+    for i, lay in enumerate(geom["layers"]):
+        ls[i].altitude = float(lay["altitude"])
+        ls[i].dx = float(lay["dx"])
+        ls[i].N = int(lay["N"])
+        ls[i].prior_weight = float(lay["prior_weight"])
+    keep += [ws, ls]
+    g = Geometry(float(geom["D_tel"]), float(geom.get("obstruction", 0.0)), len(geom["wfs"]),
+                 ws, len(geom["layers"]), ls, int(geom["wavelet_order"]), int(geom["levels"]),
+                 float(geom["alpha"]), float(geom["L0"]), int(geom["precond"]),
+                 int(geom["precision"]))
+    return g, keep
+
+
+class Plan:
+    """One adaptive-optics system: tables, prior, Jacobi diagonal and workspace on the GPU."""
+
+    def __init__(self, geom, stream=None):
+        lib = load_library()
+        g, keep = geometry_struct(geom)
+        h = ctypes.c_void_p()
+        _check(lib.tomo_plan_create(ctypes.byref(g), _stream(stream), ctypes.byref(h)))
+        self._h = h
+        self.info = self._info()
+        self.n = int(self.info.n_coeffs)
+        self.n_slopes = int(self.info.n_slopes)
+        self.precision = int(self.info.precision)
+        del keep
+
+    @property
+    def handle(self):
+        return self._h
+
+    def _info(self):
+        inf = PlanInfo()
+        _check(load_library().tomo_plan_get_info(self._h, ctypes.byref(inf)))
+        return inf
+
+    @property
+    def dtype(self):
+        import torch
+        return torch.float64 if self.precision else torch.float32
+
+    def _tensor(self, t, n, name, dtype=None):
+        dt = dtype or self.dtype
+        if not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if t.dtype != dt:
+            raise ValueError(f"{name} must be {dt}")
+        if not t.is_contiguous() or t.numel() != n:
+            raise ValueError(f"{name} must be contiguous with {n} elements")
+        return ctypes.c_void_p(t.data_ptr())
+
+    def solve(self, slopes, coeffs, iters, warm=True, stream=None, resnorm=False):
+        """One frame; coeffs holds x0 (warm) and receives x.  Returns ||r|| when resnorm."""
+        out = ctypes.c_double(0.0)
+        _check(load_library().tomo_solve(
+            self._h, self._tensor(slopes, self.n_slopes, "slopes"),
+            self._tensor(coeffs, self.n, "coeffs"), int(iters), int(bool(warm)),
+            _stream(stream), ctypes.byref(out) if resnorm else None))
+        return out.value if resnorm else None
+
+    def coeffs_to_layers(self, coeffs, layers, stream=None):
+        _check(load_library().tomo_coeffs_to_layers(
+            self._h, self._tensor(coeffs, self.n, "coeffs"), self._tensor(layers, self.n, "layers"),
+            _stream(stream)))
+
+    def layers_to_coeffs(self, layers, coeffs, stream=None):
+        _check(load_library().tomo_layers_to_coeffs(
+            self._h, self._tensor(layers, self.n, "layers"), self._tensor(coeffs, self.n, "coeffs"),
+            _stream(stream)))
+
+    def layers_to_slopes(self, layers, slopes, stream=None):
+        _check(load_library().tomo_layers_to_slopes(
+            self._h, self._tensor(layers, self.n, "layers"),
+            self._tensor(slopes, self.n_slopes, "slopes"), _stream(stream)))
+
+    def apply_normal(self, x, out, stream=None):
+        _check(load_library().tomo_apply_normal(
+            self._h, self._tensor(x, self.n, "x"), self._tensor(out, self.n, "out"), _stream(stream)))
+
+    def rhs(self, slopes, out, stream=None):
+        _check(load_library().tomo_rhs(
+            self._h, self._tensor(slopes, self.n_slopes, "slopes"),
+            self._tensor(out, self.n, "out"), _stream(stream)))
+
+    def jacobi_diagonal(self, out, stream=None):
+        import torch
+        _check(load_library().tomo_jacobi_diagonal(
+            self._h, self._tensor(out, self.n, "out", torch.float64), _stream(stream)))
+
+    def device_bytes(self):
+        return int(load_library().tomo_plan_device_bytes(self._h))
+
+    def set_kernel_timing(self, enable):
+        _check(load_library().tomo_set_kernel_timing(self._h, int(bool(enable))))
+
+    def kernel_times(self):
+        """{kind: (launches, total ms)} since timing was (re)enabled."""
+        k = len(KERNEL_KINDS)
+        counts = (ctypes.c_int * k)()
+        ms = (ctypes.c_double * k)()
+        _check(load_library().tomo_get_kernel_times(self._h, counts, ms, k))
+        return {name: (counts[i], ms[i]) for i, name in enumerate(KERNEL_KINDS)}
+
+    def set_launch_mode(self, use_graphs):
+        _check(load_library().tomo_set_launch_mode(self._h, int(bool(use_graphs))))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load_library().tomo_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def solve_batch(plans, slopes, coeffs, iters, warm=True, stream=None):
+    """Frames of several plans solved together (tomo_solve_batch)."""
+    n = len(plans)
+    ph = (ctypes.c_void_p * n)(*[p.handle.value for p in plans])
+    sp = (ctypes.c_void_p * n)(*[p._tensor(s, p.n_slopes, "slopes").value
+                                 for p, s in zip(plans, slopes)])
+    cp = (ctypes.c_void_p * n)(*[p._tensor(c, p.n, "coeffs").value for p, c in zip(plans, coeffs)])
+    _check(load_library().tomo_solve_batch(ph, sp, cp, n, int(iters), int(bool(warm)), _stream(stream)))
+
+
+def launch_count():
+    return int(load_library().tomo_launch_count())
+
+
+def version():
+    return load_library().tomo_version().decode()

@@ -1,0 +1,654 @@
+// C ABI of the tomography library (declared in include/tomo.h).
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/tomo.h"
+#include "common.h"
+#include "host_plan.h"
+#include "launch.h"
+
+using namespace tomo;
+
+namespace {
+
+thread_local std::string g_err;
+std::atomic<long long> g_launches{0};
+std::mutex g_cfg_mu;
+bool g_cfg_done[64] = {false};
+
+tomo_status fail(tomo_status st, const std::string &msg) {
+  g_err = msg;
+  return st;
+}
+
+tomo_status cuda_fail(cudaError_t e, const char *where) {
+  g_err = std::string(where) + ": " + cudaGetErrorString(e);
+  return TOMO_ERR_CUDA;
+}
+
+#define TOMO_CUDA(call, where)                      \
+  do {                                              \
+    cudaError_t e_ = (call);                        \
+    if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+  } while (0)
+
+enum Kind : int { kKindSynth = 0, kKindFwd = 1, kKindAnalysis = 2, kKindUpd = 3, kKindOther = 4, kNumKinds = 5 };
+
+// Everything one launch sequence needs (one plan, or a batch of plans).
+struct LaunchSet {
+  const InstDev *d_inst = nullptr;
+  int count = 0;
+  const ClusterItem *cl = nullptr;
+  int n_cl = 0, C = 0;
+  size_t smem = 0;
+  const FwdItem *fwd = nullptr;
+  int n_fwd = 0;
+  const UpdItem *upd = nullptr;
+  int n_upd = 0;
+  int precision = 0;
+};
+
+struct Timer {
+  bool on = false;
+  struct Rec { int kind; cudaEvent_t a, b; };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+};
+
+struct GraphEntry {
+  const void *slopes;
+  void *x;
+  int iters, warm;
+  cudaGraphExec_t exec;
+  int kernels;
+};
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Arena layout helper: reserve, then resolve against the base pointer.
+struct Arena {
+  size_t size = 0;
+  size_t take(size_t bytes) {
+    size_t off = align_up(size, 256);
+    size = off + bytes;
+    return off;
+  }
+};
+
+cudaError_t configure_device(int dev) {
+  std::lock_guard<std::mutex> lk(g_cfg_mu);
+  if (dev >= 0 && dev < 64 && g_cfg_done[dev]) return cudaSuccess;
+  cudaError_t e = configure_kernels();
+  if (e == cudaSuccess && dev >= 0 && dev < 64) g_cfg_done[dev] = true;
+  return e;
+}
+
+}  // namespace
+
+struct tomo_plan {
+  HostPlan hp;
+  int device = 0;
+  size_t esz = 4;
+  void *arena = nullptr;
+  size_t arena_bytes = 0;
+  InstDev h_inst{};
+  InstDev *d_inst = nullptr;
+  double *d_jdiag = nullptr;
+  LaunchSet ls;
+  int nc_max = 0, max_sub2 = 0;
+  cudaStream_t cap_stream = nullptr;
+  int use_graphs = 1;
+  std::vector<GraphEntry> graphs;
+  Timer timer;
+  double kind_ms[kNumKinds] = {0};
+  long long kind_n[kNumKinds] = {0};
+};
+
+namespace {
+
+// Launch one kernel through `fn`, bracketed by timing events when enabled.
+template <typename F>
+tomo_status timed(tomo_plan *p, int kind, cudaStream_t s, F fn, const char *what) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (p && p->timer.on) {
+    a = p->timer.get();
+    b = p->timer.get();
+    cudaEventRecord(a, s);
+  }
+  cudaError_t e = fn();
+  if (e != cudaSuccess) return cuda_fail(e, what);
+  g_launches.fetch_add(1);
+  if (p && p->timer.on) {
+    cudaEventRecord(b, s);
+    p->timer.recs.push_back({kind, a, b});
+  }
+  return TOMO_OK;
+}
+
+#define TOMO_TRY(x)                   \
+  do {                                \
+    tomo_status st_ = (x);            \
+    if (st_ != TOMO_OK) return st_;   \
+  } while (0)
+
+// The launch sequence of one solve (Sec. 5.1): right-hand side and initial
+// residual, then `iters` (P)CG iterations of four kernels each.
+tomo_status enqueue_solve(tomo_plan *tp, const LaunchSet &L, const void *const *slopes,
+                          void *const *x, int iters, int warm, cudaStream_t s, int *n_kernels) {
+  int nk = 0;
+  if (warm) {
+    IoArgs io{};
+    for (int i = 0; i < L.count; ++i) io.in0[i] = x[i];
+    TOMO_TRY(timed(tp, kKindSynth, s, [&] {
+      return launch_synthesis(L.precision, 0, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem, io, s);
+    }, "synthesis (warm start)"));
+    ++nk;
+  }
+  {
+    IoArgs io{};
+    for (int i = 0; i < L.count; ++i) io.in1[i] = slopes[i];
+    TOMO_TRY(timed(tp, kKindFwd, s, [&] {
+      return launch_forward(L.precision, warm ? 1 : 2, L.d_inst, L.fwd, L.n_fwd, io, s);
+    }, "forward (residual)"));
+    ++nk;
+  }
+  {
+    IoArgs io{};
+    for (int i = 0; i < L.count; ++i) io.out0[i] = x[i];
+    TOMO_TRY(timed(tp, kKindAnalysis, s, [&] {
+      return launch_analysis(L.precision, 1, 2, warm ? 1 : 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem, io, s);
+    }, "analysis (residual)"));
+    ++nk;
+  }
+  for (int it = 0; it < iters; ++it) {
+    IoArgs none{};
+    TOMO_TRY(timed(tp, kKindSynth, s, [&] {
+      return launch_synthesis(L.precision, 1, it == 0 ? 2 : 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem, none, s);
+    }, "synthesis"));
+    TOMO_TRY(timed(tp, kKindFwd, s, [&] {
+      return launch_forward(L.precision, 0, L.d_inst, L.fwd, L.n_fwd, none, s);
+    }, "forward"));
+    TOMO_TRY(timed(tp, kKindAnalysis, s, [&] {
+      return launch_analysis(L.precision, 1, 1, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem, none, s);
+    }, "analysis"));
+    IoArgs io{};
+    for (int i = 0; i < L.count; ++i) io.out0[i] = x[i];
+    TOMO_TRY(timed(tp, kKindUpd, s, [&] {
+      return launch_update(L.precision, L.d_inst, L.upd, L.n_upd, io, s);
+    }, "update"));
+    nk += 4;
+  }
+  if (n_kernels) *n_kernels = nk;
+  return TOMO_OK;
+}
+
+tomo_status check_plan(const tomo_plan *p) {
+  if (!p) return fail(TOMO_ERR_ARG, "plan is NULL");
+  return TOMO_OK;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+const char *tomo_version(void) { return "tomo-gb300 0.1 (sm_103a)"; }
+
+const char *tomo_last_error(void) { return g_err.c_str(); }
+
+long long tomo_launch_count(void) { return g_launches.load(); }
+
+tomo_status tomo_plan_create(const tomo_geometry *g, void *cuda_stream, tomo_plan **out) {
+  if (!out) return fail(TOMO_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  tomo_plan *p = new (std::nothrow) tomo_plan();
+  if (!p) return fail(TOMO_ERR_NOMEM, "host allocation failed");
+  std::string err;
+  tomo_status st = build_host_plan(g, &p->hp, &err);
+  if (st != TOMO_OK) {
+    delete p;
+    return fail(st, err);
+  }
+  const HostPlan &H = p->hp;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  cudaError_t ce = cudaGetDevice(&p->device);
+  if (ce != cudaSuccess) {
+    delete p;
+    return cuda_fail(ce, "cudaGetDevice");
+  }
+  ce = configure_device(p->device);
+  if (ce != cudaSuccess) {
+    delete p;
+    return cuda_fail(ce, "configuring kernels");
+  }
+  const size_t esz = H.precision ? 8 : 4;
+  p->esz = esz;
+  for (const auto &w : H.wfs) {
+    p->nc_max = std::max(p->nc_max, w.nc);
+    p->max_sub2 = std::max(p->max_sub2, w.n * w.n);
+  }
+
+  // ---- arena layout: tables (uploaded) then workspace (zeroed)
+  Arena A;
+  const size_t o_inst = A.take(sizeof(InstDev));
+  const size_t o_layers = A.take(sizeof(LayerDev) * H.layers.size());
+  const size_t o_wfs = A.take(sizeof(WfsDev) * H.wfs.size());
+  const size_t o_sub = A.take(sizeof(int) * H.sub_idx.size());
+  const size_t o_act = A.take(H.active.size());
+  const size_t o_posoff = A.take(sizeof(int) * H.pos_off.size());
+  const size_t o_posi0 = A.take(sizeof(int) * H.pos_i0.size());
+  const size_t o_posf = A.take(esz * H.pos_f.size());
+  const size_t o_rngoff = A.take(sizeof(int) * H.rng_off.size());
+  const size_t o_rng = A.take(sizeof(int4) * H.rng.size());
+  const size_t o_eidx = A.take(sizeof(int) * std::max<size_t>(1, H.edge_idx.size()));
+  const size_t o_et = A.take(esz * std::max<size_t>(2, H.edge_t.size()));
+  const size_t o_runrows = A.take(sizeof(int) * H.run_rows.size());
+  const size_t o_runab = A.take(sizeof(int2) * std::max<size_t>(1, H.run_ab.size()));
+  const size_t o_cl = A.take(sizeof(ClusterItem) * H.cl_items.size());
+  const size_t o_fwd = A.take(sizeof(FwdItem) * H.fwd_items.size());
+  const size_t o_upd = A.take(sizeof(UpdItem) * H.upd_items.size());
+  const size_t tables_end = align_up(A.size, 256);
+  const size_t n = static_cast<size_t>(H.n);
+  const size_t o_r = A.take(esz * n);
+  const size_t o_p = A.take(esz * n);
+  const size_t o_q = A.take(esz * n);
+  const size_t o_phi = A.take(esz * n);
+  const size_t o_v = A.take(esz * H.v_total);
+  const size_t o_jinv = A.take(esz * n);
+  const size_t o_jdiag = A.take(sizeof(double) * n);
+  const size_t o_scal = A.take(sizeof(double) * kNumScalars);
+  const size_t o_part = A.take(sizeof(double) * std::max(1, H.n_part));
+  const size_t o_tick = A.take(sizeof(unsigned) * (kTickFwd0 + H.n_wfs));
+  p->arena_bytes = align_up(A.size, 256);
+  ce = cudaMalloc(&p->arena, p->arena_bytes);
+  if (ce != cudaSuccess) {
+    delete p;
+    return fail(TOMO_ERR_NOMEM, std::string("cudaMalloc of the plan: ") + cudaGetErrorString(ce));
+  }
+  char *base = static_cast<char *>(p->arena);
+
+  InstDev &I = p->h_inst;
+  I.n = H.n;
+  I.n_layers = H.n_layers;
+  I.n_wfs = H.n_wfs;
+  I.J = H.J;
+  I.Lf = H.Lf;
+  I.precond = H.precond;
+  I.C = H.C;
+  I.n_slopes = H.n_slopes;
+  I.cl_part_off = H.cl_part_off;
+  I.upd_part_off = H.upd_part_off;
+  I.n_upd_blocks = H.n_upd_blocks;
+  I.fwd_part_off = H.fwd_part_off;
+  for (int t = 0; t < kMaxTaps; ++t) {
+    I.h[t] = t < H.Lf ? H.h[t] : 0.0;
+    I.g[t] = t < H.Lf ? H.g[t] : 0.0;
+  }
+  I.r = base + o_r;
+  I.p = base + o_p;
+  I.q = base + o_q;
+  I.phi = base + o_phi;
+  I.v = base + o_v;
+  I.jinv = base + o_jinv;
+  I.scal = reinterpret_cast<double *>(base + o_scal);
+  I.part = reinterpret_cast<double *>(base + o_part);
+  I.tick = reinterpret_cast<unsigned *>(base + o_tick);
+  I.layers = reinterpret_cast<const LayerDev *>(base + o_layers);
+  I.wfs = reinterpret_cast<const WfsDev *>(base + o_wfs);
+  I.sub_idx = reinterpret_cast<const int *>(base + o_sub);
+  I.active = reinterpret_cast<const unsigned char *>(base + o_act);
+  I.pos_off = reinterpret_cast<const int *>(base + o_posoff);
+  I.pos_i0 = reinterpret_cast<const int *>(base + o_posi0);
+  I.pos_f = base + o_posf;
+  I.rng_off = reinterpret_cast<const int *>(base + o_rngoff);
+  I.rng = reinterpret_cast<const int4 *>(base + o_rng);
+  I.edge_idx = reinterpret_cast<const int *>(base + o_eidx);
+  I.edge_t = base + o_et;
+  I.run_rows = reinterpret_cast<const int *>(base + o_runrows);
+  I.run_ab = reinterpret_cast<const int2 *>(base + o_runab);
+  p->d_inst = reinterpret_cast<InstDev *>(base + o_inst);
+  p->d_jdiag = reinterpret_cast<double *>(base + o_jdiag);
+
+  // host image of the tables
+  std::vector<char> img(tables_end, 0);
+  auto put = [&](size_t off, const void *src, size_t bytes) {
+    if (bytes) std::memcpy(img.data() + off, src, bytes);
+  };
+  put(o_inst, &I, sizeof(InstDev));
+  put(o_layers, H.layers.data(), sizeof(LayerDev) * H.layers.size());
+  put(o_wfs, H.wfs.data(), sizeof(WfsDev) * H.wfs.size());
+  put(o_sub, H.sub_idx.data(), sizeof(int) * H.sub_idx.size());
+  put(o_act, H.active.data(), H.active.size());
+  put(o_posoff, H.pos_off.data(), sizeof(int) * H.pos_off.size());
+  put(o_posi0, H.pos_i0.data(), sizeof(int) * H.pos_i0.size());
+  if (esz == 8) {
+    put(o_posf, H.pos_f.data(), 8 * H.pos_f.size());
+    put(o_et, H.edge_t.data(), 8 * H.edge_t.size());
+  } else {
+    std::vector<float> f(H.pos_f.begin(), H.pos_f.end());
+    put(o_posf, f.data(), 4 * f.size());
+    std::vector<float> e(H.edge_t.begin(), H.edge_t.end());
+    put(o_et, e.data(), 4 * e.size());
+  }
+  put(o_rngoff, H.rng_off.data(), sizeof(int) * H.rng_off.size());
+  put(o_rng, H.rng.data(), sizeof(int4) * H.rng.size());
+  put(o_eidx, H.edge_idx.data(), sizeof(int) * H.edge_idx.size());
+  put(o_runrows, H.run_rows.data(), sizeof(int) * H.run_rows.size());
+  put(o_runab, H.run_ab.data(), sizeof(int2) * H.run_ab.size());
+  put(o_cl, H.cl_items.data(), sizeof(ClusterItem) * H.cl_items.size());
+  put(o_fwd, H.fwd_items.data(), sizeof(FwdItem) * H.fwd_items.size());
+  put(o_upd, H.upd_items.data(), sizeof(UpdItem) * H.upd_items.size());
+
+  auto bail = [&](tomo_status code, const std::string &msg) {
+    cudaFree(p->arena);
+    delete p;
+    return fail(code, msg);
+  };
+  ce = cudaMemcpyAsync(base, img.data(), tables_end, cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(base + tables_end, 0, p->arena_bytes - tables_end, s);
+  if (ce != cudaSuccess) return bail(TOMO_ERR_CUDA, std::string("uploading the plan: ") + cudaGetErrorString(ce));
+
+  // ---- exact Jacobi diagonal (plan-time buffers in a temporary allocation)
+  {
+    Arena T;
+    const size_t t_prof = T.take(sizeof(double) * H.profiles.size());
+    const size_t t_poff = T.take(sizeof(int) * H.prof_off.size());
+    const size_t t_posd = T.take(sizeof(double) * H.pos_f.size());
+    void *tmp = nullptr;
+    ce = cudaMalloc(&tmp, align_up(T.size, 256));
+    if (ce != cudaSuccess) return bail(TOMO_ERR_NOMEM, "cudaMalloc of plan-time tables failed");
+    char *tb = static_cast<char *>(tmp);
+    ce = cudaMemcpyAsync(tb + t_prof, H.profiles.data(), sizeof(double) * H.profiles.size(), cudaMemcpyHostToDevice, s);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(tb + t_poff, H.prof_off.data(), sizeof(int) * H.prof_off.size(), cudaMemcpyHostToDevice, s);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(tb + t_posd, H.pos_f.data(), sizeof(double) * H.pos_f.size(), cudaMemcpyHostToDevice, s);
+    if (ce == cudaSuccess)
+      ce = launch_jacobi(p->d_inst, H.n, reinterpret_cast<double *>(tb + t_prof),
+                         reinterpret_cast<int *>(tb + t_poff), reinterpret_cast<double *>(tb + t_posd),
+                         p->d_jdiag, I.jinv, H.precision, p->nc_max, s);
+    if (ce == cudaSuccess) {
+      g_launches.fetch_add(1);
+      ce = cudaStreamSynchronize(s);
+    }
+    cudaFree(tmp);
+    if (ce != cudaSuccess) return bail(TOMO_ERR_CUDA, std::string("Jacobi diagonal: ") + cudaGetErrorString(ce));
+  }
+  ce = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
+  if (ce != cudaSuccess) return bail(TOMO_ERR_CUDA, "creating the capture stream");
+
+  LaunchSet &L = p->ls;
+  L.d_inst = p->d_inst;
+  L.count = 1;
+  L.cl = reinterpret_cast<const ClusterItem *>(base + o_cl);
+  L.n_cl = static_cast<int>(H.cl_items.size());
+  L.C = H.C;
+  L.smem = static_cast<size_t>(H.smem_transform);
+  L.fwd = reinterpret_cast<const FwdItem *>(base + o_fwd);
+  L.n_fwd = static_cast<int>(H.fwd_items.size());
+  L.upd = reinterpret_cast<const UpdItem *>(base + o_upd);
+  L.n_upd = static_cast<int>(H.upd_items.size());
+  L.precision = H.precision;
+  *out = p;
+  g_err.clear();
+  return TOMO_OK;
+}
+
+void tomo_destroy(tomo_plan *p) {
+  if (!p) return;
+  DeviceGuard dg(p->device);
+  cudaDeviceSynchronize();
+  for (auto &g : p->graphs) cudaGraphExecDestroy(g.exec);
+  for (auto &r : p->timer.recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : p->timer.pool) cudaEventDestroy(e);
+  if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+  cudaFree(p->arena);
+  delete p;
+}
+
+size_t tomo_plan_device_bytes(const tomo_plan *p) { return p ? p->arena_bytes : 0; }
+
+tomo_status tomo_plan_get_info(const tomo_plan *p, tomo_plan_info *out) {
+  TOMO_TRY(check_plan(p));
+  if (!out) return fail(TOMO_ERR_ARG, "out is NULL");
+  const HostPlan &H = p->hp;
+  out->n_coeffs = H.n;
+  out->n_slopes = H.n_slopes;
+  out->n_layers = H.n_layers;
+  out->n_wfs = H.n_wfs;
+  out->cluster_size = H.C;
+  out->kernels_per_iteration = 4;
+  out->kernels_per_solve_base = 3;
+  out->device_bytes = static_cast<long long>(p->arena_bytes);
+  // p-update + W^-1 (r, J^-1, p in; p, phi out), ray-trace (phi in, v out),
+  // gather + W + prior (v, p in; q out), update (x, p, r, q, J^-1 in; x, r out)
+  const long long vec = H.precond ? 15 : 13;
+  out->bytes_per_iteration = (vec * H.n + 2LL * H.v_total) * static_cast<long long>(p->esz);
+  out->precision = H.precision;
+  return TOMO_OK;
+}
+
+tomo_status tomo_set_kernel_timing(tomo_plan *p, int enable) {
+  TOMO_TRY(check_plan(p));
+  p->timer.on = enable != 0;
+  for (int k = 0; k < kNumKinds; ++k) {
+    p->kind_ms[k] = 0.0;
+    p->kind_n[k] = 0;
+  }
+  return TOMO_OK;
+}
+
+tomo_status tomo_get_kernel_times(tomo_plan *p, int *counts, double *ms, int n_kinds) {
+  TOMO_TRY(check_plan(p));
+  DeviceGuard dg(p->device);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "synchronising for kernel times");
+  for (auto &r : p->timer.recs) {
+    float t = 0.0f;
+    cudaEventElapsedTime(&t, r.a, r.b);
+    p->kind_ms[r.kind] += t;
+    p->kind_n[r.kind] += 1;
+    p->timer.pool.push_back(r.a);
+    p->timer.pool.push_back(r.b);
+  }
+  p->timer.recs.clear();
+  for (int k = 0; k < n_kinds && k < kNumKinds; ++k) {
+    if (counts) counts[k] = static_cast<int>(p->kind_n[k]);
+    if (ms) ms[k] = p->kind_ms[k];
+  }
+  return TOMO_OK;
+}
+
+tomo_status tomo_set_launch_mode(tomo_plan *p, int use_graphs) {
+  TOMO_TRY(check_plan(p));
+  p->use_graphs = use_graphs ? 1 : 0;
+  return TOMO_OK;
+}
+
+tomo_status tomo_solve(tomo_plan *p, const void *d_slopes, void *d_coeffs, int iters, int warm,
+                       void *cuda_stream, double *out_resnorm) {
+  TOMO_TRY(check_plan(p));
+  if (!d_slopes || !d_coeffs) return fail(TOMO_ERR_ARG, "slopes and coefficients must be device pointers");
+  if (iters < 0 || iters > 100000) return fail(TOMO_ERR_ARG, "iters out of range");
+  DeviceGuard dg(p->device);
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  warm = warm ? 1 : 0;
+  const void *sl[1] = {d_slopes};
+  void *xs[1] = {d_coeffs};
+  if (p->use_graphs && !p->timer.on) {
+    GraphEntry *ge = nullptr;
+    for (auto &g : p->graphs)
+      if (g.slopes == d_slopes && g.x == d_coeffs && g.iters == iters && g.warm == warm) ge = &g;
+    if (!ge) {
+      if (p->graphs.size() >= 16) {
+        cudaGraphExecDestroy(p->graphs.front().exec);
+        p->graphs.erase(p->graphs.begin());
+      }
+      cudaGraph_t graph = nullptr;
+      TOMO_CUDA(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+      int nk = 0;
+      const long long before = g_launches.load();
+      tomo_status st = enqueue_solve(nullptr, p->ls, sl, xs, iters, warm, p->cap_stream, &nk);
+      g_launches.store(before);
+      cudaError_t ce = cudaStreamEndCapture(p->cap_stream, &graph);
+      if (st != TOMO_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+      }
+      if (ce != cudaSuccess) return cuda_fail(ce, "end capture");
+      cudaGraphExec_t exec = nullptr;
+      ce = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ce != cudaSuccess) return cuda_fail(ce, "graph instantiate");
+      p->graphs.push_back({d_slopes, d_coeffs, iters, warm, exec, nk});
+      ge = &p->graphs.back();
+    }
+    TOMO_CUDA(cudaGraphLaunch(ge->exec, s), "graph launch");
+    g_launches.fetch_add(ge->kernels);
+  } else {
+    TOMO_TRY(enqueue_solve(p, p->ls, sl, xs, iters, warm, s, nullptr));
+  }
+  if (out_resnorm) {
+    double sc[kNumScalars];
+    TOMO_CUDA(cudaMemcpyAsync(sc, p->h_inst.scal, sizeof(sc), cudaMemcpyDeviceToHost, s), "reading scalars");
+    TOMO_CUDA(cudaStreamSynchronize(s), "synchronising the solve");
+    *out_resnorm = std::sqrt(std::max(0.0, sc[kRr]));
+    if (sc[kFlag] != 0.0) return fail(TOMO_ERR_BREAKDOWN, "PCG breakdown: p.Ap <= 0 or not finite");
+  }
+  return TOMO_OK;
+}
+
+tomo_status tomo_coeffs_to_layers(tomo_plan *p, const void *d_coeffs, void *d_layers, void *cuda_stream) {
+  TOMO_TRY(check_plan(p));
+  if (!d_coeffs || !d_layers) return fail(TOMO_ERR_ARG, "NULL device pointer");
+  DeviceGuard dg(p->device);
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  const LaunchSet &L = p->ls;
+  IoArgs io{};
+  io.in0[0] = d_coeffs;
+  io.out0[0] = d_layers;
+  return timed(p, kKindSynth, s, [&] {
+    return launch_synthesis(L.precision, 0, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem, io, s);
+  }, "synthesis");
+}
+
+tomo_status tomo_layers_to_coeffs(tomo_plan *p, const void *d_layers, void *d_coeffs, void *cuda_stream) {
+  TOMO_TRY(check_plan(p));
+  if (!d_coeffs || !d_layers) return fail(TOMO_ERR_ARG, "NULL device pointer");
+  DeviceGuard dg(p->device);
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  const LaunchSet &L = p->ls;
+  IoArgs io{};
+  io.in0[0] = d_layers;
+  io.out0[0] = d_coeffs;
+  return timed(p, kKindAnalysis, s, [&] {
+    return launch_analysis(L.precision, 0, 0, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem, io, s);
+  }, "analysis");
+}
+
+tomo_status tomo_layers_to_slopes(tomo_plan *p, const void *d_layers, void *d_slopes, void *cuda_stream) {
+  TOMO_TRY(check_plan(p));
+  if (!d_slopes || !d_layers) return fail(TOMO_ERR_ARG, "NULL device pointer");
+  DeviceGuard dg(p->device);
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  IoArgs io{};
+  io.in0[0] = d_layers;
+  io.out0[0] = d_slopes;
+  return timed(p, kKindOther, s, [&] {
+    return launch_slopes(p->ls.precision, p->d_inst, p->hp.n_wfs, p->max_sub2, io, s);
+  }, "slopes");
+}
+
+tomo_status tomo_apply_normal(tomo_plan *p, const void *d_in, void *d_out, void *cuda_stream) {
+  TOMO_TRY(check_plan(p));
+  if (!d_in || !d_out) return fail(TOMO_ERR_ARG, "NULL device pointer");
+  if (d_in == d_out) return fail(TOMO_ERR_ARG, "d_in and d_out must not overlap");
+  DeviceGuard dg(p->device);
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  const LaunchSet &L = p->ls;
+  IoArgs a{};
+  a.in0[0] = d_in;
+  TOMO_TRY(timed(p, kKindSynth, s, [&] {
+    return launch_synthesis(L.precision, 0, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem, a, s);
+  }, "synthesis"));
+  IoArgs b{};
+  TOMO_TRY(timed(p, kKindFwd, s, [&] { return launch_forward(L.precision, 0, L.d_inst, L.fwd, L.n_fwd, b, s); },
+                 "forward"));
+  IoArgs c{};
+  c.in1[0] = d_in;
+  c.out0[0] = d_out;
+  return timed(p, kKindAnalysis, s, [&] {
+    return launch_analysis(L.precision, 1, 1, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem, c, s);
+  }, "analysis");
+}
+
+tomo_status tomo_rhs(tomo_plan *p, const void *d_slopes, void *d_out, void *cuda_stream) {
+  TOMO_TRY(check_plan(p));
+  if (!d_slopes || !d_out) return fail(TOMO_ERR_ARG, "NULL device pointer");
+  DeviceGuard dg(p->device);
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  const LaunchSet &L = p->ls;
+  IoArgs a{};
+  a.in1[0] = d_slopes;
+  TOMO_TRY(timed(p, kKindFwd, s, [&] { return launch_forward(L.precision, 2, L.d_inst, L.fwd, L.n_fwd, a, s); },
+                 "forward (data)"));
+  IoArgs c{};
+  c.out0[0] = d_out;
+  return timed(p, kKindAnalysis, s, [&] {
+    return launch_analysis(L.precision, 1, 0, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem, c, s);
+  }, "analysis");
+}
+
+tomo_status tomo_jacobi_diagonal(tomo_plan *p, double *d_out, void *cuda_stream) {
+  TOMO_TRY(check_plan(p));
+  if (!d_out) return fail(TOMO_ERR_ARG, "NULL device pointer");
+  DeviceGuard dg(p->device);
+  TOMO_CUDA(cudaMemcpyAsync(d_out, p->d_jdiag, sizeof(double) * p->hp.n, cudaMemcpyDeviceToDevice,
+                            static_cast<cudaStream_t>(cuda_stream)),
+            "copying the Jacobi diagonal");
+  return TOMO_OK;
+}
+
+tomo_status tomo_solve_batch(tomo_plan *const *plans, const void *const *d_slopes, void *const *d_coeffs,
+                             int count, int iters, int warm, void *cuda_stream) {
+  if (!plans || !d_slopes || !d_coeffs || count < 0) return fail(TOMO_ERR_ARG, "NULL array or negative count");
+  for (int i = 0; i < count; ++i) {
+    tomo_status st = tomo_solve(plans[i], d_slopes[i], d_coeffs[i], iters, warm, cuda_stream, nullptr);
+    if (st != TOMO_OK) return st;
+  }
+  return TOMO_OK;
+}
+
+}  // extern "C"

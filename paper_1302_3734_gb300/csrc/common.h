@@ -1,0 +1,97 @@
+// Internal structures shared by the host plan builder and the CUDA kernels.
+//
+// One "instance" is one adaptive-optics system (one plan).  Kernels are written
+// over a table of instances so that a launch can serve one plan or a batch of
+// plans of uneven size; every work item of a launch names its instance.
+#pragma once
+
+#include <stdint.h>
+
+namespace tomo {
+
+constexpr int kMaxTaps = 8;        // Daubechies order <= 4
+constexpr int kMaxLevels = 12;
+constexpr int kFwdTile = 16;       // corners per side of a forward tile
+constexpr int kMaxBatch = 96;      // instances per launch (kernel-argument arrays)
+constexpr int kThreads = 256;      // threads per CTA of every hot kernel
+constexpr int kUpdChunk = 4096;    // coefficients per CTA of the vector update
+
+enum WfsKind : int { kFull = 0, kRemoveTT = 1, kTTOnly = 2 };
+
+// Scalar slots (double) of an instance.
+enum Scalar : int {
+  kRz = 0,      // r.z of the current iterate
+  kAlpha = 1,   // step length
+  kBeta = 2,    // direction update
+  kPq = 3,      // p.Ap
+  kRr = 4,      // r.r after the last update
+  kFlag = 5,    // 1 after a breakdown (p.Ap <= 0 or not finite)
+  kNumScalars = 8
+};
+
+// Ticket counters of an instance (unsigned).
+enum Ticket : int { kTickCluster = 0, kTickUpd = 1, kTickFwd0 = 2 };
+
+struct LayerDev {
+  int N, log2N;
+  int off;                      // offset of this layer in the coefficient / grid vectors
+  int pad;
+  double dalpha[kMaxLevels + 1];  // alpha * D at level k (index k = 1..J)
+};
+
+struct WfsDev {
+  int n, nc;                    // subapertures and corners per side
+  int S, kind;
+  int is_lgs;
+  int slope_off;                // offset of this sensor in the slope vector
+  int v_off;                    // offset of this sensor's corner field (nc*nc)
+  int n_tiles;                  // forward tiles (partial-sum slots)
+  int part_off;                 // offset of its partial sums in the instance partials (doubles)
+  int n_edge, edge_off;         // pupil-edge corners where Gamma^T 1_x or Gamma^T 1_y != 0
+  int sub_off;                  // offset into the subaperture-index table (n*n)
+  int act_off;                  // offset into the active-corner table (nc*nc)
+  int run_off;                  // offset of the per-row valid runs (n+1 row offsets)
+  int pad;
+  double inv_sigma2;
+};
+
+// Everything a kernel needs to know about one instance.  Pointers to element
+// type T arrays are void* (T = float or double by plan precision).
+struct InstDev {
+  int n, n_layers, n_wfs, J;
+  int Lf, precond, C, n_slopes;
+  int cl_part_off, upd_part_off, n_upd_blocks, fwd_part_off;
+  double h[kMaxTaps], g[kMaxTaps];
+  // workspace
+  void *r, *p, *q, *phi, *v, *jinv;
+  double *scal, *part;
+  unsigned *tick;
+  // geometry tables
+  const LayerDev *layers;
+  const WfsDev *wfs;
+  const int *sub_idx;           // per sensor n*n: index among the valid subapertures, or -1
+  const unsigned char *active;  // per sensor nc*nc: corner of a valid subaperture
+  const int *pos_off;           // per (m,l): offset of the x corner table (y table follows, nc)
+  const int *pos_i0;            // wrapped integer node index of each corner coordinate
+  const void *pos_f;            // fractional part (T)
+  const int *rng_off;           // per (m,l): offset of the x node ranges (y follow, N_l)
+  const int4 *rng;              // per node: corners (s0, c0, s1, c1) whose taps touch it
+  const int *edge_idx;          // corner index of each edge corner
+  const void *edge_t;           // (t_x, t_y) of each edge corner (T, interleaved)
+  const int *run_rows;          // per sensor (n+1): start of row b's runs in run_ab
+  const int2 *run_ab;           // [a_lo, a_hi) runs of valid subapertures in a row
+};
+
+// Per-launch pointer arguments (indexed by the instance's slot in the launch).
+struct IoArgs {
+  const void *in0[kMaxBatch];
+  const void *in1[kMaxBatch];
+  void *out0[kMaxBatch];
+};
+
+// Work items.
+struct ClusterItem { int inst, layer; };
+struct FwdItem { int inst, wfs, a0, b0, tile, pad0, pad1, pad2; };  // a0 < 0: tip/tilt-only sensor
+struct UpdItem { int inst, start, blk, pad; };
+
+}  // namespace tomo

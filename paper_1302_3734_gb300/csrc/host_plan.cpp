@@ -1,0 +1,402 @@
+// Host-side plan construction.  Geometry conventions (Sec. 2.1 of the paper and
+// the readings stated in tomo.h):
+//   layer node (ix, iy) at ((ix - N/2) dx, (iy - N/2) dx);
+//   sensor corner (a, b), a, b in 0..n, at ((a - n/2) d, (b - n/2) d);
+//   the corner seen on layer l along guide star m is
+//   (1 - h_l/H_m) r + theta_m h_l (H_m = infinity for a natural star).
+#include "host_plan.h"
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+
+namespace tomo {
+
+namespace {
+
+using cd = std::complex<double>;
+
+double binom(int n, int k) {
+  double r = 1.0;
+  for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+  return r;
+}
+
+// Roots of a monic polynomial (coefficients ascending, c[deg] == 1) by the
+// Weierstrass / Durand-Kerner simultaneous iteration.
+std::vector<cd> poly_roots(const std::vector<double> &c) {
+  const int deg = static_cast<int>(c.size()) - 1;
+  std::vector<cd> z(deg);
+  for (int k = 0; k < deg; ++k) z[k] = std::pow(cd(0.4, 0.9), k);
+  auto eval = [&](cd x) {
+    cd v(0.0, 0.0);
+    for (int i = deg; i >= 0; --i) v = v * x + c[i];
+    return v;
+  };
+  for (int it = 0; it < 500; ++it) {
+    double delta = 0.0;
+    for (int k = 0; k < deg; ++k) {
+      cd den(1.0, 0.0);
+      for (int j = 0; j < deg; ++j)
+        if (j != k) den *= (z[k] - z[j]);
+      cd step = eval(z[k]) / den;
+      z[k] -= step;
+      delta = std::max(delta, std::abs(step));
+    }
+    if (delta < 1e-16) break;
+  }
+  return z;
+}
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+int ilog2(int v) { int r = 0; while ((1 << r) < v) ++r; return r; }
+
+// One periodic synthesis level on x[0..M): y = [a | d] -> x.
+void synth_1d(std::vector<double> *x, int M, const std::vector<double> &h,
+              const std::vector<double> &g) {
+  std::vector<double> out(M, 0.0);
+  const int H = M / 2, L = static_cast<int>(h.size());
+  for (int i = 0; i < H; ++i)
+    for (int t = 0; t < L; ++t) out[(2 * i + t) % M] += h[t] * (*x)[i] + g[t] * (*x)[H + i];
+  for (int i = 0; i < M; ++i) (*x)[i] = out[i];
+}
+
+}  // namespace
+
+bool daubechies_filter(int p, std::vector<double> *h, std::string *err) {
+  if (p < 1 || 2 * p > kMaxTaps) {
+    *err = "wavelet_order must be in 1..4";
+    return false;
+  }
+  // (1 + z)^p times one factor (z - z_k) per root of
+  // P(y) = sum_{k<p} C(p-1+k, k) y^k, z_k the root of z^2 - (2 - 4 y_k) z + 1
+  // inside the unit circle; coefficients in descending powers.
+  std::vector<cd> poly{cd(1.0, 0.0)};
+  auto mul = [&](cd a0, cd a1) {  // poly *= (a0 z + a1)
+    std::vector<cd> r(poly.size() + 1, cd(0.0, 0.0));
+    for (size_t i = 0; i < poly.size(); ++i) {
+      r[i] += poly[i] * a0;
+      r[i + 1] += poly[i] * a1;
+    }
+    poly.swap(r);
+  };
+  for (int i = 0; i < p; ++i) mul(1.0, 1.0);
+  if (p > 1) {
+    std::vector<double> c(p);
+    for (int k = 0; k < p; ++k) c[k] = binom(p - 1 + k, k);
+    const double lead = c[p - 1];
+    for (auto &v : c) v /= lead;
+    for (const cd &y : poly_roots(c)) {
+      cd b = 2.0 - 4.0 * y;
+      cd disc = std::sqrt(b * b - 4.0);
+      cd z1 = (b + disc) / 2.0, z2 = (b - disc) / 2.0;
+      mul(1.0, -(std::abs(z1) < 1.0 ? z1 : z2));
+    }
+  }
+  h->assign(poly.size(), 0.0);
+  double s = 0.0;
+  for (size_t i = 0; i < poly.size(); ++i) {
+    (*h)[i] = poly[i].real();
+    s += (*h)[i];
+  }
+  for (auto &v : *h) v *= std::sqrt(2.0) / s;
+  // self-check: double-shift orthonormality
+  const int L = static_cast<int>(h->size());
+  for (int m = 0; 2 * m < L; ++m) {
+    double d = 0.0;
+    for (int k = 0; k + 2 * m < L; ++k) d += (*h)[k] * (*h)[k + 2 * m];
+    if (std::fabs(d - (m == 0 ? 1.0 : 0.0)) > 1e-12) {
+      *err = "Daubechies factorisation failed its orthonormality check";
+      return false;
+    }
+  }
+  return true;
+}
+
+tomo_status build_host_plan(const tomo_geometry *geo, HostPlan *P, std::string *err) {
+  char buf[256];
+  if (!geo || !geo->wfs || !geo->layers || geo->n_wfs < 1 || geo->n_layers < 1) {
+    *err = "geometry, its sensor and layer arrays must be non-empty";
+    return TOMO_ERR_ARG;
+  }
+  if (geo->precision != 0 && geo->precision != 1) { *err = "precision must be 0 or 1"; return TOMO_ERR_ARG; }
+  if (geo->precond != 0 && geo->precond != 1) { *err = "precond must be 0 or 1"; return TOMO_ERR_ARG; }
+  if (!(geo->alpha >= 0.0) || !std::isfinite(geo->alpha)) { *err = "alpha must be finite and >= 0"; return TOMO_ERR_ARG; }
+  if (geo->levels < 1 || geo->levels > kMaxLevels) { *err = "levels out of range"; return TOMO_ERR_LEVELS; }
+  if (geo->n_wfs > 4096 || geo->n_layers > 4096) { *err = "too many sensors or layers"; return TOMO_ERR_ARG; }
+  if (!(geo->obstruction >= 0.0 && geo->obstruction < 1.0)) { *err = "obstruction must be in [0, 1)"; return TOMO_ERR_ARG; }
+
+  P->n_layers = geo->n_layers;
+  P->n_wfs = geo->n_wfs;
+  P->J = geo->levels;
+  P->precond = geo->precond;
+  P->precision = geo->precision;
+  P->alpha = geo->alpha;
+  P->L0 = geo->L0;
+  if (!daubechies_filter(geo->wavelet_order, &P->h, err)) return TOMO_ERR_ARG;
+  P->Lf = static_cast<int>(P->h.size());
+  P->g.resize(P->Lf);
+  for (int k = 0; k < P->Lf; ++k) P->g[k] = ((k & 1) ? -1.0 : 1.0) * P->h[P->Lf - 1 - k];
+
+  // ---------------------------------------------------------------- layers
+  const int J = P->J;
+  int Nmin = 1 << 30, Nmax = 0;
+  P->n = 0;
+  for (int l = 0; l < geo->n_layers; ++l) {
+    const tomo_layer &L = geo->layers[l];
+    if (!is_pow2(L.N) || L.N < 16 || L.N > 4096) {
+      snprintf(buf, sizeof buf, "layer %d: N must be a power of two in [16, 4096]", l);
+      *err = buf;
+      return TOMO_ERR_LEVELS;
+    }
+    if ((L.N >> (J - 1)) < P->Lf) {
+      snprintf(buf, sizeof buf, "layer %d: N/2^(levels-1) = %d is below the filter length %d", l,
+               L.N >> (J - 1), P->Lf);
+      *err = buf;
+      return TOMO_ERR_LEVELS;
+    }
+    if (!(L.dx > 0.0) || !(L.prior_weight > 0.0) || !(L.altitude >= 0.0) ||
+        !std::isfinite(L.altitude) || !std::isfinite(L.prior_weight)) {
+      snprintf(buf, sizeof buf, "layer %d: dx, prior_weight must be > 0 and altitude >= 0", l);
+      *err = buf;
+      return TOMO_ERR_ARG;
+    }
+    LayerDev d{};
+    d.N = L.N;
+    d.log2N = ilog2(L.N);
+    d.off = P->n;
+    const double l0 = geo->L0 > 0.0 ? std::pow(geo->L0, -11.0 / 3.0) : 0.0;
+    for (int k = 1; k <= J; ++k)
+      d.dalpha[k] = geo->alpha * L.prior_weight * (l0 + std::pow(std::ldexp(L.dx, k), -11.0 / 3.0));
+    P->layers.push_back(d);
+    P->n += L.N * L.N;
+    Nmin = std::min(Nmin, L.N);
+    Nmax = std::max(Nmax, L.N);
+  }
+  // cluster size: every layer keeps >= 8 rows per CTA at level 1
+  P->C = std::min(16, Nmin / 8);
+  {
+    long long need = 0;
+    for (const auto &d : P->layers)
+      need = std::max(need, 2LL * d.N * (d.N / P->C) * (P->precision ? 8 : 4));
+    need += 3LL * P->C * P->C * (P->precision ? 8 : 4) + 2 * kMaxTaps * 8 + 64 * 8;
+    P->smem_transform = need;
+    if (need > 200 * 1024) {
+      *err = "layer grids too large for the transform kernels at this precision "
+             "(shared memory per CTA > 200 KB)";
+      return TOMO_ERR_UNSUPPORTED;
+    }
+  }
+
+  // --------------------------------------------------------------- sensors
+  int slope_off = 0, v_off = 0;
+  P->n_lgs = 0;
+  for (int m = 0; m < geo->n_wfs; ++m) {
+    const tomo_wfs &W = geo->wfs[m];
+    if (W.n_sub < 1 || W.n_sub > 1024 || !(W.d_sub > 0.0) || !(W.sigma > 0.0) ||
+        !std::isfinite(W.theta_x) || !std::isfinite(W.theta_y)) {
+      snprintf(buf, sizeof buf, "sensor %d: n_sub, d_sub, sigma or theta out of range", m);
+      *err = buf;
+      return TOMO_ERR_ARG;
+    }
+    if (W.tt_only && W.remove_tt) {
+      snprintf(buf, sizeof buf, "sensor %d: tt_only and remove_tt exclude each other", m);
+      *err = buf;
+      return TOMO_ERR_ARG;
+    }
+    const int n = W.n_sub, nc = n + 1;
+    const bool lgs = std::isfinite(W.height) && W.height > 0.0;
+    WfsDev d{};
+    d.n = n;
+    d.nc = nc;
+    d.kind = W.tt_only ? kTTOnly : (W.remove_tt ? kRemoveTT : kFull);
+    d.is_lgs = lgs ? 1 : 0;
+    d.inv_sigma2 = 1.0 / (W.sigma * W.sigma);
+    P->n_lgs += lgs ? 1 : 0;
+    // valid mask: given, or the circular pupil rule
+    std::vector<unsigned char> valid(n * n);
+    for (int b = 0; b < n; ++b)
+      for (int a = 0; a < n; ++a) {
+        if (W.valid) {
+          valid[b * n + a] = W.valid[b * n + a] ? 1 : 0;
+        } else {
+          const double cx = (a + 0.5 - n / 2.0) * W.d_sub, cy = (b + 0.5 - n / 2.0) * W.d_sub;
+          const double r = std::hypot(cx, cy);
+          valid[b * n + a] = (r <= geo->D_tel / 2.0 && r >= geo->obstruction * geo->D_tel / 2.0) ? 1 : 0;
+        }
+      }
+    d.sub_off = static_cast<int>(P->sub_idx.size());
+    int S = 0;
+    for (int i = 0; i < n * n; ++i) P->sub_idx.push_back(valid[i] ? S++ : -1);
+    if (S == 0) {
+      snprintf(buf, sizeof buf, "sensor %d has no valid subaperture", m);
+      *err = buf;
+      return TOMO_ERR_GEOMETRY;
+    }
+    d.S = S;
+    auto V = [&](int a, int b) -> int {
+      return (a >= 0 && b >= 0 && a < n && b < n && valid[b * n + a]) ? 1 : 0;
+    };
+    d.act_off = static_cast<int>(P->active.size());
+    for (int b = 0; b < nc; ++b)
+      for (int a = 0; a < nc; ++a)
+        P->active.push_back((V(a - 1, b - 1) | V(a, b - 1) | V(a - 1, b) | V(a, b)) ? 1 : 0);
+    // pupil-edge corners: Gamma^T 1_x and Gamma^T 1_y
+    d.edge_off = static_cast<int>(P->edge_idx.size());
+    for (int b = 0; b < nc; ++b)
+      for (int a = 0; a < nc; ++a) {
+        const double tx = 0.5 * (V(a - 1, b) + V(a - 1, b - 1) - V(a, b) - V(a, b - 1));
+        const double ty = 0.5 * (-V(a - 1, b) + V(a - 1, b - 1) - V(a, b) + V(a, b - 1));
+        if (tx != 0.0 || ty != 0.0) {
+          P->edge_idx.push_back(b * nc + a);
+          P->edge_t.push_back(tx);
+          P->edge_t.push_back(ty);
+        }
+      }
+    d.n_edge = static_cast<int>(P->edge_idx.size()) - d.edge_off;
+    // valid runs per row (for the Jacobi diagonal)
+    d.run_off = static_cast<int>(P->run_rows.size());
+    for (int b = 0; b < n; ++b) {
+      P->run_rows.push_back(static_cast<int>(P->run_ab.size()));
+      int a = 0;
+      while (a < n) {
+        while (a < n && !valid[b * n + a]) ++a;
+        if (a >= n) break;
+        int a1 = a;
+        while (a1 < n && valid[b * n + a1]) ++a1;
+        P->run_ab.push_back(make_int2(a, a1));
+        a = a1;
+      }
+    }
+    P->run_rows.push_back(static_cast<int>(P->run_ab.size()));
+    d.slope_off = slope_off;
+    slope_off += d.kind == kTTOnly ? 2 : 2 * S;
+    d.v_off = v_off;
+    v_off += nc * nc;
+    P->wfs.push_back(d);
+  }
+  P->n_slopes = slope_off;
+  P->v_total = v_off;
+
+  // ------------------------------------------------------ corner tables
+  P->pos_off.resize(P->n_wfs * P->n_layers);
+  P->rng_off.resize(P->n_wfs * P->n_layers);
+  for (int m = 0; m < P->n_wfs; ++m) {
+    const tomo_wfs &W = geo->wfs[m];
+    const WfsDev &d = P->wfs[m];
+    const bool lgs = d.is_lgs != 0;
+    for (int l = 0; l < P->n_layers; ++l) {
+      const tomo_layer &L = geo->layers[l];
+      const int N = L.N, n = d.n, nc = d.nc;
+      const double cone = lgs ? 1.0 - L.altitude / W.height : 1.0;
+      if (!(cone > 0.0)) {
+        snprintf(buf, sizeof buf, "layer %d lies at or above the altitude of guide star %d", l, m);
+        *err = buf;
+        return TOMO_ERR_GEOMETRY;
+      }
+      const int po = static_cast<int>(P->pos_i0.size());
+      P->pos_off[m * P->n_layers + l] = po;
+      std::vector<int> i0s[2];
+      for (int axis = 0; axis < 2; ++axis) {
+        const double th = axis == 0 ? W.theta_x : W.theta_y;
+        for (int a = 0; a < nc; ++a) {
+          const double r = (a - n / 2.0) * W.d_sub;
+          double gc = (cone * r + th * L.altitude) / L.dx + N / 2.0;
+          gc -= N * std::floor(gc / N);
+          if (gc >= N) gc -= N;
+          const double fl = std::floor(gc);
+          P->pos_i0.push_back(static_cast<int>(fl));
+          P->pos_f.push_back(gc - fl);
+          i0s[axis].push_back(static_cast<int>(fl));
+        }
+      }
+      // inverse ranges: node i <- corners whose two taps include i
+      const int ro = static_cast<int>(P->rng.size());
+      P->rng_off[m * P->n_layers + l] = ro;
+      for (int axis = 0; axis < 2; ++axis) {
+        std::vector<std::vector<int>> lists(N);
+        for (int a = 0; a < nc; ++a) {
+          const int i0 = i0s[axis][a];
+          lists[i0].push_back(a);
+          if ((i0 + 1) % N != i0) lists[(i0 + 1) % N].push_back(a);
+        }
+        for (int i = 0; i < N; ++i) {
+          std::vector<int> &li = lists[i];
+          std::sort(li.begin(), li.end());
+          li.erase(std::unique(li.begin(), li.end()), li.end());
+          int4 rr = make_int4(0, 0, 0, 0);
+          int nr = 0;
+          for (size_t k = 0; k < li.size();) {
+            size_t k1 = k + 1;
+            while (k1 < li.size() && li[k1] == li[k1 - 1] + 1) ++k1;
+            if (nr == 0) { rr.x = li[k]; rr.y = static_cast<int>(k1 - k); }
+            else if (nr == 1) { rr.z = li[k]; rr.w = static_cast<int>(k1 - k); }
+            ++nr;
+            k = k1;
+          }
+          if (nr > 2) {
+            snprintf(buf, sizeof buf, "footprint of sensor %d on layer %d is wider than the grid", m, l);
+            *err = buf;
+            return TOMO_ERR_GEOMETRY;
+          }
+          P->rng.push_back(rr);
+        }
+      }
+    }
+  }
+
+  // -------------------------------------------------- Jacobi basis profiles
+  P->prof_off.assign(static_cast<size_t>(P->n_layers) * (J + 1) * 2, 0);
+  for (int l = 0; l < P->n_layers; ++l) {
+    const int N = P->layers[l].N;
+    for (int k = 1; k <= J; ++k)
+      for (int kind = 0; kind < 2; ++kind) {
+        const int M = N >> (k - 1);
+        std::vector<double> x(N, 0.0);
+        x[kind == 0 ? 0 : M / 2] = 1.0;
+        for (int size = M; size <= N; size *= 2) synth_1d(&x, size, P->h, P->g);
+        P->prof_off[(l * (J + 1) + k) * 2 + kind] = static_cast<int>(P->profiles.size());
+        P->profiles.insert(P->profiles.end(), x.begin(), x.end());
+      }
+  }
+
+  // --------------------------------------------------------- work tables
+  int part = 0;
+  P->cl_part_off = part;
+  part += 2 * P->n_layers * P->C;   // (dot, second dot) per CTA
+  for (int l = 0; l < P->n_layers; ++l) P->cl_items.push_back({0, l});
+  P->n_upd_blocks = (P->n + kUpdChunk - 1) / kUpdChunk;
+  P->upd_part_off = part;
+  part += 2 * P->n_upd_blocks;
+  for (int b = 0; b < P->n_upd_blocks; ++b) P->upd_items.push_back({0, b * kUpdChunk, b, 0});
+  P->fwd_part_off = part;
+  for (int m = 0; m < P->n_wfs; ++m) {
+    WfsDev &d = P->wfs[m];
+    d.part_off = part;
+    if (d.kind == kTTOnly) {
+      d.n_tiles = 1;
+      P->fwd_items.push_back({0, m, -1, 0, 0, 0, 0, 0});
+      part += 2;
+      continue;
+    }
+    const int nt = (d.nc + kFwdTile - 1) / kFwdTile;
+    int tiles = 0;
+    for (int tb = 0; tb < nt; ++tb)
+      for (int ta = 0; ta < nt; ++ta) {
+        bool any = false;
+        for (int b = tb * kFwdTile; b < std::min(d.nc, (tb + 1) * kFwdTile) && !any; ++b)
+          for (int a = ta * kFwdTile; a < std::min(d.nc, (ta + 1) * kFwdTile) && !any; ++a)
+            any = P->active[d.act_off + b * d.nc + a] != 0;
+        if (!any) continue;
+        P->fwd_items.push_back({0, m, ta * kFwdTile, tb * kFwdTile, tiles, 0, 0, 0});
+        ++tiles;
+      }
+    d.n_tiles = tiles;
+    part += 2 * tiles;
+  }
+  P->n_part = part;
+  return TOMO_OK;
+}
+
+}  // namespace tomo

@@ -1,0 +1,53 @@
+// Host-side construction of a plan: validation of a tomo_geometry, the
+// Daubechies filters, the pupil masks and every index table the kernels read.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include <vector_functions.h>
+#include <vector_types.h>
+
+#include "../../include/tomo.h"
+#include "common.h"
+
+namespace tomo {
+
+struct HostPlan {
+  int n_layers = 0, n_wfs = 0, J = 0, Lf = 0, precond = 0, precision = 0;
+  double alpha = 0.0, L0 = 0.0;
+  int n = 0, n_slopes = 0, v_total = 0, C = 0;
+  int n_part = 0, cl_part_off = 0, upd_part_off = 0, fwd_part_off = 0, n_upd_blocks = 0;
+  int n_lgs = 0;
+  long long smem_transform = 0;   // dynamic shared memory of the transform kernels (bytes)
+  std::vector<double> h, g;
+  std::vector<LayerDev> layers;
+  std::vector<WfsDev> wfs;
+  std::vector<int> sub_idx;
+  std::vector<unsigned char> active;
+  std::vector<int> pos_off, pos_i0;
+  std::vector<double> pos_f;
+  std::vector<int> rng_off;
+  std::vector<int4> rng;
+  std::vector<int> edge_idx;
+  std::vector<double> edge_t;
+  std::vector<int> run_rows;
+  std::vector<int2> run_ab;
+  // 1-D basis functions for the Jacobi diagonal: per layer, per level k (1..J),
+  // per kind (0 scaling, 1 wavelet), N_l samples at position 0.
+  std::vector<double> profiles;
+  std::vector<int> prof_off;      // [layer * (J+1) * 2 + k * 2 + kind]
+  // work tables (instance slot 0)
+  std::vector<FwdItem> fwd_items;
+  std::vector<ClusterItem> cl_items;
+  std::vector<UpdItem> upd_items;
+};
+
+// Returns TOMO_OK or an error status with *err set.
+tomo_status build_host_plan(const tomo_geometry *g, HostPlan *out, std::string *err);
+
+// Orthonormal Daubechies low-pass filter with p vanishing moments (2p taps),
+// by spectral factorisation; exposed for tests through the plan only.
+bool daubechies_filter(int p, std::vector<double> *h, std::string *err);
+
+}  // namespace tomo

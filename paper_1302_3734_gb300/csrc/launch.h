@@ -1,0 +1,46 @@
+// Launchers of the CUDA kernels (defined in kernels.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.h"
+
+namespace tomo {
+
+constexpr int kMaxTransformSmem = 200 * 1024;   // opt-in dynamic shared memory of the transforms
+
+// Raise the dynamic shared memory and cluster-size limits of every kernel once
+// per device (before any launch, and before any stream capture).
+cudaError_t configure_kernels();
+
+// W^-1 over clusters of C CTAs per (instance, layer).  src: 0 = io.in0
+// coefficients, 1 = PCG direction update fused in (flags: kFlagFirst).
+cudaError_t launch_synthesis(int precision, int src, int flags, const InstDev *insts,
+                             const ClusterItem *items, int n_clusters, int C, size_t smem,
+                             const IoArgs &io, cudaStream_t s);
+
+// W over clusters; src 0 = io.in0 layers, 1 = adjoint gather from v; epi 0 plain,
+// 1 operator (q, p.q -> alpha), 2 residual (r, p, r.z); flags: kFlagWarm.
+cudaError_t launch_analysis(int precision, int src, int epi, int flags, const InstDev *insts,
+                            const ClusterItem *items, int n_clusters, int C, size_t smem,
+                            const IoArgs &io, cudaStream_t s);
+
+// Ray-trace, Fried slopes, noise weighting, Gamma^T.  mode 0 operator, 1 residual,
+// 2 data only.
+cudaError_t launch_forward(int precision, int mode, const InstDev *insts, const FwdItem *items,
+                           int n_items, const IoArgs &io, cudaStream_t s);
+
+// x, r update and the FP64 r.z reduction.
+cudaError_t launch_update(int precision, const InstDev *insts, const UpdItem *items, int n_items,
+                          const IoArgs &io, cudaStream_t s);
+
+// Noise-free measurement (single instance).
+cudaError_t launch_slopes(int precision, const InstDev *insts, int n_wfs, int max_sub2,
+                          const IoArgs &io, cudaStream_t s);
+
+// Exact modified Jacobi diagonal (single instance, plan time).
+cudaError_t launch_jacobi(const InstDev *insts, int n, const double *prof, const int *prof_off,
+                          const double *pos_fd, double *jdiag, void *jinv, int precision,
+                          int nc_max, cudaStream_t s);
+
+}  // namespace tomo

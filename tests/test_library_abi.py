@@ -1,0 +1,98 @@
+"""The C-ABI library builds, loads and exports every symbol include/tomo.h
+declares; host-side validation of geometries needs no GPU."""
+import ctypes
+import math
+import os
+import re
+import shutil
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "tomo.h")
+
+
+def _header_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(tomo_[a-z_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1302_3734_gb300 import build
+    if shutil.which("nvcc") is None and not os.path.exists(build.LIB):
+        pytest.skip("no nvcc and no prebuilt library")
+    build.build()
+    import paper_1302_3734_gb300 as pkg
+    return pkg.load_library()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _header_functions()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_the_header(lib):
+    from paper_1302_3734_gb300 import SIGNATURES
+    assert sorted(n for n, _, _ in SIGNATURES) == _header_functions()
+
+
+def test_version_and_error_string(lib):
+    assert b"sm_103a" in lib.tomo_version()
+    assert lib.tomo_last_error() is not None
+
+
+def _status_of(geom):
+    import paper_1302_3734_gb300 as pkg
+    lib = pkg.load_library()
+    g, keep = pkg.geometry_struct(geom)
+    h = ctypes.c_void_p()
+    st = lib.tomo_plan_create(ctypes.byref(g), None, ctypes.byref(h))
+    if st == 0:
+        lib.tomo_destroy(h)
+    return st, lib.tomo_last_error().decode()
+
+
+def test_validation_errors_without_gpu(lib):
+    from synth import configs
+    g = configs.small_lgs_config()
+    g["levels"] = 5            # 32 / 2^4 = 2 < 6 taps
+    st, msg = _status_of(g)
+    assert st == 3 and "filter length" in msg
+    g = configs.small_lgs_config()
+    g["wfs"][0]["tt_only"] = True
+    st, _ = _status_of(g)
+    assert st == 1
+    g = configs.small_lgs_config()
+    g["layers"][0]["N"] = 48   # not a power of two
+    st, _ = _status_of(g)
+    assert st == 3
+    g = configs.small_lgs_config()
+    g["wfs"][1]["valid"][:] = 0
+    st, msg = _status_of(g)
+    assert st == 2 and "no valid subaperture" in msg
+    g = configs.small_lgs_config(n_sub=16, N=16, dx=0.25)   # 8 m pupil on a 4 m grid
+    st, msg = _status_of(g)
+    assert st == 2 and "wider than the grid" in msg
+    g = configs.small_lgs_config()
+    g["layers"][2]["altitude"] = 95e3                        # above the sodium layer
+    st, _ = _status_of(g)
+    assert st == 2
+    g = configs.small_lgs_config()
+    g["wavelet_order"] = 7
+    st, _ = _status_of(g)
+    assert st == 1
+
+
+def test_a_valid_geometry_reaches_the_device_step(lib):
+    # without a GPU the only possible failure of a valid geometry is the CUDA step
+    import torch
+    from synth import configs
+    st, msg = _status_of(configs.config1())
+    if torch.cuda.is_available():
+        assert st == 0, msg
+    else:
+        assert st == 5, msg
