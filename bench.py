@@ -1,0 +1,333 @@
+"""Benchmark: wavelet-domain MAP tomography frames on GB300 (one JSON line).
+
+Workload (default): the E-ELT-sized MCAO system - 42 m pupil with 28 % of the
+area obstructed, six sodium LGS (84x84 Shack-Hartmann, 90 km, cone effect,
+tip/tilt removed) on a 1'-radius hexagon, three tip/tilt-only NGS at 1', nine
+layers of 128^2 at 0.5 m, db3 with 4 levels, modified-Jacobi PCG with 10
+iterations warm-started from the previous frame (Sec. 5.1 of the paper).
+Frames come from seeded von Karman screens advected by frozen flow at 500 Hz;
+slopes are the library's own noise-free measurement plus seeded noise.
+
+A step is one frame (right-hand side, initial residual, 10 PCG iterations).
+``value`` is frames solved per second with inputs resident in HBM; L2 is
+flushed (a 256 MiB write) before every timed step, outside the timed window.
+
+``--impl reference`` times the FP64 CPU oracle on the same frames instead.
+Under torchrun every rank solves its own independent telescope stream (weak
+scaling, no data-path collective).
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "tomography solves/s and p99 frame latency at 84x84 MCAO vs plain GPU PCG"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def workload():
+    from synth import configs
+    g = configs.config1()
+    return g, {"workload": "E-ELT MCAO 42m, 6 LGS 84x84 @90km + 3 TT NGS, 9 layers 128^2 @0.5m, "
+                           "db3 J=4, Jacobi PCG 10 it, warm start, 500 Hz frozen flow",
+               "n_coeffs": sum(l["N"] ** 2 for l in g["layers"]), "iters": g["iters"],
+               "precision": "FP32 operator, FP64 dots/scalars"}
+
+
+def frame_screens(geom, k, rank):
+    from synth import FrozenFlow
+    if not hasattr(frame_screens, "ff"):
+        frame_screens.ff = FrozenFlow(geom, 1, instance=rank)
+    return frame_screens.ff.layers(k * 0.002)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4)
+                          if len(s) > 5 + i and s[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+def cpu_baseline(geom, frames_s, x0, budget_s):
+    """The FP64 oracle solving the same frames on the host (single core)."""
+    from oracle import Tomography
+    t0 = time.perf_counter()
+    ora = Tomography(geom)
+    Jd = ora.jacobi_diagonal()
+    plan_s = time.perf_counter() - t0
+    x = np.asarray(x0, dtype=np.float64)
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        x = ora.pcg(ora.rhs(frames_s[n % len(frames_s)]), x, int(geom["iters"]), Jd)
+        n += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} consecutive frames of the same workload, 10 FP64 PCG iterations each, "
+                      f"numpy single core; plan (exact Jacobi diagonal) {plan_s:.2f}s excluded"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import Tomography
+    from synth import gaussian_noise
+    geom, cfg = workload()
+    ora = Tomography(geom)
+    Jd = ora.jacobi_diagonal()
+    frames = []
+    for k in range(args.warmup + args.steps):
+        s = ora.measure(frame_screens(geom, k, 0)) + gaussian_noise(
+            ora.meas_offsets[-1], 0.3, 1_000_000 + k)
+        frames.append(s)
+    x = np.zeros(ora.n)
+    for k in range(args.warmup):
+        x = ora.pcg(ora.rhs(frames[k]), x, int(geom["iters"]), Jd)
+    times = []
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        x = ora.pcg(ora.rhs(frames[args.warmup + k]), x, int(geom["iters"]), Jd)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    val = args.steps / tot
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "solves/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+            "latency_ms": {"p50": 1000 * float(np.percentile(times, 50)),
+                           "p99": 1000 * float(np.percentile(times, 99))},
+            "cpu_baseline": {"value": val, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} frames, FP64 numpy oracle, single core"},
+            "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import paper_1302_3734_gb300 as pkg
+    from paper_1302_3734_gb300 import build
+    from synth import gaussian_noise
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    build.build()
+    geom, cfg = workload()
+    dev = torch.device("cuda", local)
+    plan = pkg.Plan(geom)
+    info = plan.info
+    n, ns = plan.n, plan.n_slopes
+    F = args.warmup + args.steps
+    sig = np.concatenate([np.full(2 if w["tt_only"] else 2 * int(w["valid"].sum()), w["sigma"])
+                          for w in geom["wfs"]])
+
+    # frames: noise-free slopes from the library's measurement of the screens + noise
+    layers = torch.empty(n, dtype=torch.float32, device=dev)
+    slopes = torch.empty((F, ns), dtype=torch.float32, device=dev)
+    for k in range(F):
+        phis = frame_screens(geom, k, rank)
+        layers.copy_(torch.from_numpy(np.concatenate([p.ravel() for p in phis]).astype(np.float32)))
+        plan.layers_to_slopes(layers, slopes[k])
+        noise = gaussian_noise(ns, 1.0, 1_000_000 + 1000 * rank + k)
+        slopes[k] += torch.from_numpy((noise * sig).astype(np.float32)).to(dev)
+    torch.cuda.synchronize()
+    x = torch.zeros(n, dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    iters = int(geom["iters"])
+
+    def run(use_graphs, steps, first, record):
+        plan.set_launch_mode(use_graphs)
+        times = []
+        for k in range(steps):
+            flush.fill_(float(k))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            plan.solve(slopes[(first + k) % F], x, iters, warm=True)
+            e1.record()
+            if record:
+                times.append((e0, e1))
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in times]
+
+    # warm-up (also builds the CUDA graph), then the timed region
+    run(1, args.warmup, 0, False)
+    # plain one-launch-per-kernel PCG on the same frames, for comparison
+    plain = run(0, min(args.steps, 50), 0, True)
+    x.zero_()
+    run(1, args.warmup, 0, False)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = pkg.launch_count()
+    with Clocks(local) as clk:
+        times = run(1, args.steps, args.warmup, True)
+    launches = pkg.launch_count() - launches0
+    if dist:
+        dist.barrier()
+    tot_ms = sum(times)
+    if dist:
+        t = torch.tensor([tot_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    value = ws * args.steps / (tot_ms / 1000.0)
+    ms_step = tot_ms / args.steps
+
+    # end to end through the public API: pinned host slopes in, coefficients out
+    h_s = torch.empty(ns, dtype=torch.float32, pin_memory=True)
+    h_x = torch.empty(n, dtype=torch.float32, pin_memory=True)
+    d_s = torch.empty(ns, dtype=torch.float32, device=dev)
+    host_frames = slopes.cpu()
+    e2e = []
+    for k in range(args.steps):
+        h_s.copy_(host_frames[(args.warmup + k) % F])
+        flush.fill_(float(k))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        d_s.copy_(h_s, non_blocking=True)
+        plan.solve(d_s, x, iters, warm=True)
+        h_x.copy_(x, non_blocking=True)
+        e1.record()
+        e2e.append((e0, e1))
+    torch.cuda.synchronize()
+    e2e_ms = [a.elapsed_time(b) for a, b in e2e]
+
+    # per-kernel times (events around every launch, direct launches)
+    plan.set_kernel_timing(True)
+    run(0, min(args.steps, 50), args.warmup, False)
+    kt = plan.kernel_times()
+    plan.set_kernel_timing(False)
+    nlaunch = {k: v[0] for k, v in kt.items()}
+    dominant = max(kt, key=lambda k: kt[k][1])
+    sT = 4
+    V = (info.bytes_per_iteration // sT - 15 * n) // 2
+    per_launch_bytes = {"synthesis": 5 * n * sT, "forward": (n + V) * sT,
+                        "analysis": (2 * n + V) * sT, "update": 7 * n * sT}
+    cnt, ms = kt[dominant]
+    achieved = per_launch_bytes[dominant] * cnt / (ms / 1000.0) / 1e9
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        peak, peak_src = float(peaks["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        peak, peak_src = 6800.0, "fallback"
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": dict(cfg, l2="flushed (256 MiB write) before every timed step",
+                       parallelism=f"replicas x{ws}" if ws > 1 else "single GPU",
+                       launch="CUDA graph of the whole frame"),
+        "latency_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99))},
+        "plain_launch": {"value": 1000.0 / float(np.mean(plain)), "unit": "solves/s",
+                         "p50_ms": float(np.percentile(plain, 50)),
+                         "p99_ms": float(np.percentile(plain, 99)),
+                         "note": "same kernels, one launch per kernel, no graph"},
+        "e2e": {"value": ws * 1000.0 / float(np.mean(e2e_ms)), "unit": "solves/s",
+                "h2d_bytes_per_step": 4 * ns, "d2h_bytes_per_step": 4 * n,
+                "p99_ms": float(np.percentile(e2e_ms, 99))},
+        "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "peak_source": peak_src,
+                     "kernel_ms_per_launch": {k: (v[1] / v[0] if v[0] else None) for k, v in kt.items()},
+                     "bytes_per_iteration": info.bytes_per_iteration},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        from oracle import Tomography
+        ora = Tomography(geom)
+        frames = [ora.measure(frame_screens(geom, k, 0)) + gaussian_noise(ns, 1.0, 1_000_000 + k) * sig
+                  for k in range(min(F, 20))]
+        line["cpu_baseline"] = cpu_baseline(geom, frames, np.zeros(n), args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
