@@ -49,7 +49,7 @@ struct LaunchSet {
   int n_cl = 0, C = 0;
   size_t smem = 0;
   const FwdItem *fwd = nullptr;
-  int n_fwd = 0;
+  int n_fwd = 0, max_layers = 0, lf = 0;
   const UpdItem *upd = nullptr;
   int n_upd = 0;
   int precision = 0;
@@ -157,7 +157,7 @@ tomo_status enqueue_solve(tomo_plan *tp, const LaunchSet &L, const void *const *
     IoArgs io{};
     for (int i = 0; i < L.count; ++i) io.in0[i] = x[i];
     TOMO_TRY(timed(tp, kKindSynth, s, [&] {
-      return launch_synthesis(L.precision, 0, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem, io, s);
+      return launch_synthesis(L.precision, 0, L.lf, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem, io, s);
     }, "synthesis (warm start)"));
     ++nk;
   }
@@ -165,7 +165,7 @@ tomo_status enqueue_solve(tomo_plan *tp, const LaunchSet &L, const void *const *
     IoArgs io{};
     for (int i = 0; i < L.count; ++i) io.in1[i] = slopes[i];
     TOMO_TRY(timed(tp, kKindFwd, s, [&] {
-      return launch_forward(L.precision, warm ? 1 : 2, L.d_inst, L.fwd, L.n_fwd, io, s);
+      return launch_forward(L.precision, warm ? 1 : 2, L.max_layers, L.d_inst, L.fwd, L.n_fwd, io, s);
     }, "forward (residual)"));
     ++nk;
   }
@@ -173,20 +173,20 @@ tomo_status enqueue_solve(tomo_plan *tp, const LaunchSet &L, const void *const *
     IoArgs io{};
     for (int i = 0; i < L.count; ++i) io.out0[i] = x[i];
     TOMO_TRY(timed(tp, kKindAnalysis, s, [&] {
-      return launch_analysis(L.precision, 1, 2, warm ? 1 : 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem, io, s);
+      return launch_analysis(L.precision, 1, 2, L.lf, warm ? 1 : 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem, io, s);
     }, "analysis (residual)"));
     ++nk;
   }
   for (int it = 0; it < iters; ++it) {
     IoArgs none{};
     TOMO_TRY(timed(tp, kKindSynth, s, [&] {
-      return launch_synthesis(L.precision, 1, it == 0 ? 2 : 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem, none, s);
+      return launch_synthesis(L.precision, 1, L.lf, it == 0 ? 2 : 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem, none, s);
     }, "synthesis"));
     TOMO_TRY(timed(tp, kKindFwd, s, [&] {
-      return launch_forward(L.precision, 0, L.d_inst, L.fwd, L.n_fwd, none, s);
+      return launch_forward(L.precision, 0, L.max_layers, L.d_inst, L.fwd, L.n_fwd, none, s);
     }, "forward"));
     TOMO_TRY(timed(tp, kKindAnalysis, s, [&] {
-      return launch_analysis(L.precision, 1, 1, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem, none, s);
+      return launch_analysis(L.precision, 1, 1, L.lf, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem, none, s);
     }, "analysis"));
     IoArgs io{};
     for (int i = 0; i < L.count; ++i) io.out0[i] = x[i];
@@ -252,6 +252,10 @@ tomo_status tomo_plan_create(const tomo_geometry *g, void *cuda_stream, tomo_pla
   }
   const size_t esz = H.precision ? 8 : 4;
   p->esz = esz;
+  if (forward_smem(H.n_layers, H.precision) > static_cast<size_t>(kMaxForwardSmem)) {
+    delete p;
+    return fail(TOMO_ERR_UNSUPPORTED, "too many layers for the forward kernel's staged tables");
+  }
   for (const auto &w : H.wfs) {
     p->nc_max = std::max(p->nc_max, w.nc);
     p->max_sub2 = std::max(p->max_sub2, w.n * w.n);
@@ -267,8 +271,15 @@ tomo_status tomo_plan_create(const tomo_geometry *g, void *cuda_stream, tomo_pla
   const size_t o_posoff = A.take(sizeof(int) * H.pos_off.size());
   const size_t o_posi0 = A.take(sizeof(int) * H.pos_i0.size());
   const size_t o_posf = A.take(esz * H.pos_f.size());
-  const size_t o_rngoff = A.take(sizeof(int) * H.rng_off.size());
-  const size_t o_rng = A.take(sizeof(int4) * H.rng.size());
+  const size_t o_gtoff = A.take(sizeof(int) * H.gt_off.size());
+  const size_t o_gtidx = A.take(sizeof(int4) * std::max<size_t>(1, H.gt_idx.size()));
+  const size_t o_gtw = A.take(esz * std::max<size_t>(4, H.gt_w.size()));
+  const size_t o_gtcnt = A.take(std::max<size_t>(1, H.gt_cnt.size()));
+  const size_t o_ttseg = A.take(sizeof(int2) * H.tt_seg.size());
+  const size_t o_ttnode = A.take(sizeof(int) * std::max<size_t>(1, H.tt_node.size()));
+  const size_t o_ttbeg = A.take(sizeof(int) * H.tt_beg.size());
+  const size_t o_ttk = A.take(sizeof(int) * std::max<size_t>(1, H.tt_k.size()));
+  const size_t o_ttw = A.take(esz * std::max<size_t>(2, H.tt_w.size()));
   const size_t o_eidx = A.take(sizeof(int) * std::max<size_t>(1, H.edge_idx.size()));
   const size_t o_et = A.take(esz * std::max<size_t>(2, H.edge_t.size()));
   const size_t o_runrows = A.take(sizeof(int) * H.run_rows.size());
@@ -284,6 +295,7 @@ tomo_status tomo_plan_create(const tomo_geometry *g, void *cuda_stream, tomo_pla
   const size_t o_phi = A.take(esz * n);
   const size_t o_v = A.take(esz * H.v_total);
   const size_t o_jinv = A.take(esz * n);
+  const size_t o_ttc = A.take(esz * 2 * std::max(1, H.n_tt));
   const size_t o_jdiag = A.take(sizeof(double) * n);
   const size_t o_scal = A.take(sizeof(double) * kNumScalars);
   const size_t o_part = A.take(sizeof(double) * std::max(1, H.n_part));
@@ -329,8 +341,17 @@ tomo_status tomo_plan_create(const tomo_geometry *g, void *cuda_stream, tomo_pla
   I.pos_off = reinterpret_cast<const int *>(base + o_posoff);
   I.pos_i0 = reinterpret_cast<const int *>(base + o_posi0);
   I.pos_f = base + o_posf;
-  I.rng_off = reinterpret_cast<const int *>(base + o_rngoff);
-  I.rng = reinterpret_cast<const int4 *>(base + o_rng);
+  I.gt_off = reinterpret_cast<const int *>(base + o_gtoff);
+  I.gt_idx = reinterpret_cast<const int4 *>(base + o_gtidx);
+  I.gt_w = base + o_gtw;
+  I.gt_cnt = reinterpret_cast<const unsigned char *>(base + o_gtcnt);
+  I.tt_seg = reinterpret_cast<const int2 *>(base + o_ttseg);
+  I.tt_node = reinterpret_cast<const int *>(base + o_ttnode);
+  I.tt_beg = reinterpret_cast<const int *>(base + o_ttbeg);
+  I.tt_k = reinterpret_cast<const int *>(base + o_ttk);
+  I.tt_w = base + o_ttw;
+  I.ttc = base + o_ttc;
+  I.n_tt = H.n_tt;
   I.edge_idx = reinterpret_cast<const int *>(base + o_eidx);
   I.edge_t = base + o_et;
   I.run_rows = reinterpret_cast<const int *>(base + o_runrows);
@@ -350,17 +371,25 @@ tomo_status tomo_plan_create(const tomo_geometry *g, void *cuda_stream, tomo_pla
   put(o_act, H.active.data(), H.active.size());
   put(o_posoff, H.pos_off.data(), sizeof(int) * H.pos_off.size());
   put(o_posi0, H.pos_i0.data(), sizeof(int) * H.pos_i0.size());
-  if (esz == 8) {
-    put(o_posf, H.pos_f.data(), 8 * H.pos_f.size());
-    put(o_et, H.edge_t.data(), 8 * H.edge_t.size());
-  } else {
-    std::vector<float> f(H.pos_f.begin(), H.pos_f.end());
-    put(o_posf, f.data(), 4 * f.size());
-    std::vector<float> e(H.edge_t.begin(), H.edge_t.end());
-    put(o_et, e.data(), 4 * e.size());
-  }
-  put(o_rngoff, H.rng_off.data(), sizeof(int) * H.rng_off.size());
-  put(o_rng, H.rng.data(), sizeof(int4) * H.rng.size());
+  auto put_real = [&](size_t off, const std::vector<double> &v) {
+    if (esz == 8) {
+      put(off, v.data(), 8 * v.size());
+    } else {
+      std::vector<float> f(v.begin(), v.end());
+      put(off, f.data(), 4 * f.size());
+    }
+  };
+  put_real(o_posf, H.pos_f);
+  put_real(o_et, H.edge_t);
+  put_real(o_gtw, H.gt_w);
+  put_real(o_ttw, H.tt_w);
+  put(o_gtoff, H.gt_off.data(), sizeof(int) * H.gt_off.size());
+  put(o_gtidx, H.gt_idx.data(), sizeof(int4) * H.gt_idx.size());
+  put(o_gtcnt, H.gt_cnt.data(), H.gt_cnt.size());
+  put(o_ttseg, H.tt_seg.data(), sizeof(int2) * H.tt_seg.size());
+  put(o_ttnode, H.tt_node.data(), sizeof(int) * H.tt_node.size());
+  put(o_ttbeg, H.tt_beg.data(), sizeof(int) * H.tt_beg.size());
+  put(o_ttk, H.tt_k.data(), sizeof(int) * H.tt_k.size());
   put(o_eidx, H.edge_idx.data(), sizeof(int) * H.edge_idx.size());
   put(o_runrows, H.run_rows.data(), sizeof(int) * H.run_rows.size());
   put(o_runab, H.run_ab.data(), sizeof(int2) * H.run_ab.size());
@@ -415,6 +444,8 @@ tomo_status tomo_plan_create(const tomo_geometry *g, void *cuda_stream, tomo_pla
   L.smem = static_cast<size_t>(H.smem_transform);
   L.fwd = reinterpret_cast<const FwdItem *>(base + o_fwd);
   L.n_fwd = static_cast<int>(H.fwd_items.size());
+  L.max_layers = H.n_layers;
+  L.lf = H.Lf;
   L.upd = reinterpret_cast<const UpdItem *>(base + o_upd);
   L.n_upd = static_cast<int>(H.upd_items.size());
   L.precision = H.precision;
@@ -560,7 +591,7 @@ tomo_status tomo_coeffs_to_layers(tomo_plan *p, const void *d_coeffs, void *d_la
   io.in0[0] = d_coeffs;
   io.out0[0] = d_layers;
   return timed(p, kKindSynth, s, [&] {
-    return launch_synthesis(L.precision, 0, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem, io, s);
+    return launch_synthesis(L.precision, 0, L.lf, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem, io, s);
   }, "synthesis");
 }
 
@@ -574,7 +605,7 @@ tomo_status tomo_layers_to_coeffs(tomo_plan *p, const void *d_layers, void *d_co
   io.in0[0] = d_layers;
   io.out0[0] = d_coeffs;
   return timed(p, kKindAnalysis, s, [&] {
-    return launch_analysis(L.precision, 0, 0, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem, io, s);
+    return launch_analysis(L.precision, 0, 0, L.lf, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem, io, s);
   }, "analysis");
 }
 
@@ -601,16 +632,16 @@ tomo_status tomo_apply_normal(tomo_plan *p, const void *d_in, void *d_out, void 
   IoArgs a{};
   a.in0[0] = d_in;
   TOMO_TRY(timed(p, kKindSynth, s, [&] {
-    return launch_synthesis(L.precision, 0, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem, a, s);
+    return launch_synthesis(L.precision, 0, L.lf, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem, a, s);
   }, "synthesis"));
   IoArgs b{};
-  TOMO_TRY(timed(p, kKindFwd, s, [&] { return launch_forward(L.precision, 0, L.d_inst, L.fwd, L.n_fwd, b, s); },
+  TOMO_TRY(timed(p, kKindFwd, s, [&] { return launch_forward(L.precision, 0, L.max_layers, L.d_inst, L.fwd, L.n_fwd, b, s); },
                  "forward"));
   IoArgs c{};
   c.in1[0] = d_in;
   c.out0[0] = d_out;
   return timed(p, kKindAnalysis, s, [&] {
-    return launch_analysis(L.precision, 1, 1, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem, c, s);
+    return launch_analysis(L.precision, 1, 1, L.lf, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem, c, s);
   }, "analysis");
 }
 
@@ -622,12 +653,12 @@ tomo_status tomo_rhs(tomo_plan *p, const void *d_slopes, void *d_out, void *cuda
   const LaunchSet &L = p->ls;
   IoArgs a{};
   a.in1[0] = d_slopes;
-  TOMO_TRY(timed(p, kKindFwd, s, [&] { return launch_forward(L.precision, 2, L.d_inst, L.fwd, L.n_fwd, a, s); },
+  TOMO_TRY(timed(p, kKindFwd, s, [&] { return launch_forward(L.precision, 2, L.max_layers, L.d_inst, L.fwd, L.n_fwd, a, s); },
                  "forward (data)"));
   IoArgs c{};
   c.out0[0] = d_out;
   return timed(p, kKindAnalysis, s, [&] {
-    return launch_analysis(L.precision, 1, 0, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem, c, s);
+    return launch_analysis(L.precision, 1, 0, L.lf, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem, c, s);
   }, "analysis");
 }
 

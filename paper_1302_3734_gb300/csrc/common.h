@@ -14,7 +14,8 @@ constexpr int kMaxLevels = 12;
 constexpr int kFwdTile = 16;       // corners per side of a forward tile
 constexpr int kMaxBatch = 96;      // instances per launch (kernel-argument arrays)
 constexpr int kThreads = 256;      // threads per CTA of every hot kernel
-constexpr int kUpdChunk = 4096;    // coefficients per CTA of the vector update
+constexpr int kUpdChunk = 1024;    // coefficients per CTA of the vector update
+constexpr int kMaxTapsNode = 4;    // corners per axis whose bilinear taps reach one node
 
 enum WfsKind : int { kFull = 0, kRemoveTT = 1, kTTOnly = 2 };
 
@@ -51,7 +52,7 @@ struct WfsDev {
   int sub_off;                  // offset into the subaperture-index table (n*n)
   int act_off;                  // offset into the active-corner table (nc*nc)
   int run_off;                  // offset of the per-row valid runs (n+1 row offsets)
-  int pad;
+  int tt_idx;                   // index among the tip/tilt-only sensors, -1 otherwise
   double inv_sigma2;
 };
 
@@ -74,8 +75,17 @@ struct InstDev {
   const int *pos_off;           // per (m,l): offset of the x corner table (y table follows, nc)
   const int *pos_i0;            // wrapped integer node index of each corner coordinate
   const void *pos_f;            // fractional part (T)
-  const int *rng_off;           // per (m,l): offset of the x node ranges (y follow, N_l)
-  const int4 *rng;              // per node: corners (s0, c0, s1, c1) whose taps touch it
+  const int *gt_off;            // per (m,l): offset of the node tap tables (x: N_l, then y: N_l)
+  const int4 *gt_idx;           // per node: corner indices whose bilinear taps reach it
+  const void *gt_w;             // their weights (4 T per node; 0 beyond the count)
+  const unsigned char *gt_cnt;  // number of corners per node (<= kMaxTapsNode)
+  const int2 *tt_seg;           // per (layer, cluster rank): [first, end) tip/tilt-only nodes
+  const int *tt_node;           // local node index (row-in-CTA * N + column)
+  const int *tt_beg;            // entries [tt_beg[j], tt_beg[j+1]) of node j
+  const int *tt_k;              // tip/tilt-only sensor of the entry
+  const void *tt_w;             // (w t_x, w t_y) of the entry (T pairs)
+  void *ttc;                    // per tip/tilt-only sensor: the weighted mean slopes (T pairs)
+  int n_tt, pad_tt;
   const int *edge_idx;          // corner index of each edge corner
   const void *edge_t;           // (t_x, t_y) of each edge corner (T, interleaved)
   const int *run_rows;          // per sensor (n+1): start of row b's runs in run_ab

@@ -179,7 +179,7 @@ tomo_status build_host_plan(const tomo_geometry *geo, HostPlan *P, std::string *
   {
     long long need = 0;
     for (const auto &d : P->layers)
-      need = std::max(need, 2LL * d.N * (d.N / P->C) * (P->precision ? 8 : 4));
+      need = std::max(need, 2LL * d.N * (d.N / P->C + kMaxTaps) * (P->precision ? 8 : 4));
     need += 3LL * P->C * P->C * (P->precision ? 8 : 4) + 2 * kMaxTaps * 8 + 64 * 8;
     P->smem_transform = need;
     if (need > 200 * 1024) {
@@ -280,8 +280,15 @@ tomo_status build_host_plan(const tomo_geometry *geo, HostPlan *P, std::string *
   P->v_total = v_off;
 
   // ------------------------------------------------------ corner tables
+  // Per (sensor, layer): each corner's wrapped node index and fraction along x
+  // and y (forward bilinear taps), and per node the <= 4 corners whose taps
+  // reach it with their weights (the transposed ray-trace as a gather).
   P->pos_off.resize(P->n_wfs * P->n_layers);
-  P->rng_off.resize(P->n_wfs * P->n_layers);
+  P->gt_off.assign(P->n_wfs * P->n_layers, -1);
+  P->n_tt = 0;
+  for (auto &d : P->wfs) d.tt_idx = d.kind == kTTOnly ? P->n_tt++ : -1;
+  struct TTEntry { int layer, node, k; double wx, wy; };
+  std::vector<TTEntry> tt_entries;
   for (int m = 0; m < P->n_wfs; ++m) {
     const tomo_wfs &W = geo->wfs[m];
     const WfsDev &d = P->wfs[m];
@@ -298,6 +305,7 @@ tomo_status build_host_plan(const tomo_geometry *geo, HostPlan *P, std::string *
       const int po = static_cast<int>(P->pos_i0.size());
       P->pos_off[m * P->n_layers + l] = po;
       std::vector<int> i0s[2];
+      std::vector<double> fs[2];
       for (int axis = 0; axis < 2; ++axis) {
         const double th = axis == 0 ? W.theta_x : W.theta_y;
         for (int a = 0; a < nc; ++a) {
@@ -309,41 +317,89 @@ tomo_status build_host_plan(const tomo_geometry *geo, HostPlan *P, std::string *
           P->pos_i0.push_back(static_cast<int>(fl));
           P->pos_f.push_back(gc - fl);
           i0s[axis].push_back(static_cast<int>(fl));
+          fs[axis].push_back(gc - fl);
         }
       }
-      // inverse ranges: node i <- corners whose two taps include i
-      const int ro = static_cast<int>(P->rng.size());
-      P->rng_off[m * P->n_layers + l] = ro;
+      // a footprint wider than the grid would make a node receive corners from
+      // two periodic copies of the same side; reject it
+      if (cone * n * W.d_sub / L.dx + 2.0 > N) {
+        snprintf(buf, sizeof buf, "footprint of sensor %d on layer %d is wider than the grid", m, l);
+        *err = buf;
+        return TOMO_ERR_GEOMETRY;
+      }
+      if (d.kind == kTTOnly) {
+        // sparse adjoint of the tip/tilt-only sensor: its corner field is
+        // e_x t_x + e_y t_y on the pupil-edge corners only
+        for (int e = d.edge_off; e < d.edge_off + d.n_edge; ++e) {
+          const int c = P->edge_idx[e], a = c % nc, b = c / nc;
+          const double tx = P->edge_t[2 * e], ty = P->edge_t[2 * e + 1];
+          const int x0 = i0s[0][a], y0 = i0s[1][b], x1 = (x0 + 1) % N, y1 = (y0 + 1) % N;
+          const double fx = fs[0][a], fy = fs[1][b];
+          const int xs[4] = {x0, x1, x0, x1}, ys[4] = {y0, y0, y1, y1};
+          const double ws[4] = {(1 - fx) * (1 - fy), fx * (1 - fy), (1 - fx) * fy, fx * fy};
+          for (int t = 0; t < 4; ++t)
+            if (ws[t] != 0.0)
+              tt_entries.push_back({l, ys[t] * N + xs[t], d.tt_idx, ws[t] * tx, ws[t] * ty});
+        }
+        continue;
+      }
+      const int go = static_cast<int>(P->gt_cnt.size());
+      P->gt_off[m * P->n_layers + l] = go;
       for (int axis = 0; axis < 2; ++axis) {
-        std::vector<std::vector<int>> lists(N);
+        std::vector<std::vector<std::pair<int, double>>> lists(N);
         for (int a = 0; a < nc; ++a) {
           const int i0 = i0s[axis][a];
-          lists[i0].push_back(a);
-          if ((i0 + 1) % N != i0) lists[(i0 + 1) % N].push_back(a);
+          const double f = fs[axis][a];
+          lists[i0].push_back({a, 1.0 - f});
+          if (f != 0.0) lists[(i0 + 1) % N].push_back({a, f});
         }
         for (int i = 0; i < N; ++i) {
-          std::vector<int> &li = lists[i];
-          std::sort(li.begin(), li.end());
-          li.erase(std::unique(li.begin(), li.end()), li.end());
-          int4 rr = make_int4(0, 0, 0, 0);
-          int nr = 0;
-          for (size_t k = 0; k < li.size();) {
-            size_t k1 = k + 1;
-            while (k1 < li.size() && li[k1] == li[k1 - 1] + 1) ++k1;
-            if (nr == 0) { rr.x = li[k]; rr.y = static_cast<int>(k1 - k); }
-            else if (nr == 1) { rr.z = li[k]; rr.w = static_cast<int>(k1 - k); }
-            ++nr;
-            k = k1;
-          }
-          if (nr > 2) {
-            snprintf(buf, sizeof buf, "footprint of sensor %d on layer %d is wider than the grid", m, l);
+          if (lists[i].size() > static_cast<size_t>(kMaxTapsNode)) {
+            snprintf(buf, sizeof buf,
+                     "sensor %d on layer %d: more than %d corners per node (subaperture smaller "
+                     "than half a layer cell)", m, l, kMaxTapsNode);
             *err = buf;
-            return TOMO_ERR_GEOMETRY;
+            return TOMO_ERR_UNSUPPORTED;
           }
-          P->rng.push_back(rr);
+          int4 ix = make_int4(0, 0, 0, 0);
+          int *ip = &ix.x;
+          for (int t = 0; t < kMaxTapsNode; ++t) {
+            const bool on = t < static_cast<int>(lists[i].size());
+            ip[t] = on ? lists[i][t].first : 0;
+            P->gt_w.push_back(on ? lists[i][t].second : 0.0);
+          }
+          P->gt_idx.push_back(ix);
+          P->gt_cnt.push_back(static_cast<unsigned char>(lists[i].size()));
         }
       }
     }
+  }
+  // group the tip/tilt-only entries by (layer, cluster rank, node)
+  std::sort(tt_entries.begin(), tt_entries.end(), [](const TTEntry &x, const TTEntry &y) {
+    return x.layer != y.layer ? x.layer < y.layer : (x.node != y.node ? x.node < y.node : x.k < y.k);
+  });
+  P->tt_seg.assign(static_cast<size_t>(P->n_layers) * P->C, make_int2(0, 0));
+  {
+    size_t e = 0;
+    for (int l = 0; l < P->n_layers; ++l) {
+      const int N = P->layers[l].N, R0 = N / P->C;
+      for (int c = 0; c < P->C; ++c) {
+        const int first = static_cast<int>(P->tt_node.size());
+        while (e < tt_entries.size() && tt_entries[e].layer == l && tt_entries[e].node / N / R0 == c) {
+          const int node = tt_entries[e].node;
+          P->tt_node.push_back(node - c * R0 * N);
+          P->tt_beg.push_back(static_cast<int>(P->tt_k.size()));
+          while (e < tt_entries.size() && tt_entries[e].layer == l && tt_entries[e].node == node) {
+            P->tt_k.push_back(tt_entries[e].k);
+            P->tt_w.push_back(tt_entries[e].wx);
+            P->tt_w.push_back(tt_entries[e].wy);
+            ++e;
+          }
+        }
+        P->tt_seg[l * P->C + c] = make_int2(first, static_cast<int>(P->tt_node.size()));
+      }
+    }
+    P->tt_beg.push_back(static_cast<int>(P->tt_k.size()));
   }
 
   // -------------------------------------------------- Jacobi basis profiles

@@ -27,8 +27,14 @@ struct HostPlan {
   std::vector<unsigned char> active;
   std::vector<int> pos_off, pos_i0;
   std::vector<double> pos_f;
-  std::vector<int> rng_off;
-  std::vector<int4> rng;
+  std::vector<int> gt_off;
+  std::vector<int4> gt_idx;
+  std::vector<double> gt_w;        // 4 per node
+  std::vector<unsigned char> gt_cnt;
+  std::vector<int2> tt_seg;        // per (layer, rank)
+  std::vector<int> tt_node, tt_beg, tt_k;
+  std::vector<double> tt_w;        // 2 per entry
+  int n_tt = 0;
   std::vector<int> edge_idx;
   std::vector<double> edge_t;
   std::vector<int> run_rows;

@@ -11,13 +11,15 @@
 //   k_update     x += alpha p, r -= alpha q, r.J^-1 r -> beta     [chunk per CTA]
 //
 // The periodic 2-D DWT of one layer runs inside one thread-block cluster: CTA c
-// owns N/C consecutive rows; the row pass is local and the column pass reads
-// the Lf-2 halo rows of its neighbours through distributed shared memory.  The
-// coarse levels (block side <= C) are finished by CTA 0 alone.  Reductions are
-// FP64 (warp shuffle -> block -> per-CTA partial -> last CTA in a fixed order),
-// so results do not depend on scheduling.
+// owns N/C consecutive rows; the row pass is local, and before the column pass
+// each CTA copies the Lf-2 halo rows it needs from its neighbours' shared memory
+// (distributed shared memory) next to its own rows.  The coarse levels (block
+// side <= C) are finished by CTA 0 alone.  Reductions are FP64 (warp shuffle ->
+// block -> per-CTA partial -> the last CTA, in a fixed order), so results do not
+// depend on scheduling.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
+#include <stdint.h>
 
 #include "common.h"
 #include "launch.h"
@@ -58,6 +60,16 @@ __device__ double2 block_sum2(double a, double b) {
   return s_out;
 }
 
+// Fixed-order sum of `count` partial pairs (stride 2) by the whole block.
+__device__ double2 sum_partials(const double *part, int count) {
+  double a = 0.0, b = 0.0;
+  for (int q = threadIdx.x; q < count; q += blockDim.x) {
+    a += __ldcg(part + 2 * q);
+    b += __ldcg(part + 2 * q + 1);
+  }
+  return block_sum2(a, b);
+}
+
 // Copy one instance descriptor into shared memory.
 __device__ __forceinline__ void load_inst(InstDev *dst, const InstDev *src) {
   const int nw = sizeof(InstDev) / sizeof(int);
@@ -65,6 +77,21 @@ __device__ __forceinline__ void load_inst(InstDev *dst, const InstDev *src) {
   int *d = reinterpret_cast<int *>(dst);
   for (int i = threadIdx.x; i < nw; i += blockDim.x) d[i] = s[i];
   __syncthreads();
+}
+
+// Ticket of the "last CTA" pattern: every CTA publishes its partial, then the
+// CTA that draws the last ticket reduces them.  Returns true in that CTA.
+__device__ __forceinline__ bool last_ticket(unsigned *tick, unsigned total) {
+  __shared__ int s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned t = atomicAdd(tick, 1u);
+    s_last = (t == total - 1) ? 1 : 0;
+  }
+  __syncthreads();
+  if (s_last) __threadfence();
+  return s_last != 0;
 }
 
 // psi at corner (a, b) of sensor m: sum over layers of the bilinear
@@ -91,32 +118,38 @@ __device__ __forceinline__ T trace_corner(const InstDev &I, int m, int nc, const
 // ------------------------------------------------------------ k_forward
 // MODE 0: operator, z = Gamma P phi.  MODE 1: residual, z = s - Gamma P phi.
 // MODE 2: data only, z = s (phi = 0).  Writes the corner field
-// v_m = Gamma_m^T C_m^-1 z_m (C^-1 with tip/tilt removal or the tip/tilt-only
-// measurement), Sec. 4.3 and the operator expansion of Sec. 5.1.
+// v_m = Gamma_m^T C_m^-1 z_m (sigma^-2, with (I - T) when tip/tilt is removed),
+// or, for a tip/tilt-only sensor, its weighted mean slopes (e_x, e_y) whose
+// adjoint lives on the pupil edge (Sec. 4.3, operator expansion of Sec. 5.1).
 // io.in0: layer grids (NULL = the plan's phi); io.in1: slopes (MODE 1, 2).
+constexpr int kHalo = kFwdTile + 2;
+
+__host__ __device__ constexpr size_t fwd_table_bytes(int L, size_t esz) {
+  return ((sizeof(int) * (2 * L + 2 * L * kHalo) + 15) & ~size_t(15)) + 2 * L * kHalo * esz;
+}
+
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kThreads) k_forward(const InstDev *__restrict__ insts,
                                                      const FwdItem *__restrict__ items, IoArgs io) {
+  extern __shared__ __align__(16) unsigned char fsm[];
   __shared__ InstDev sI;
-  __shared__ T s_psi[kFwdTile + 2][kFwdTile + 3];
+  __shared__ T s_psi[kHalo][kHalo + 1];
   __shared__ T s_ex[kFwdTile + 1][kFwdTile + 2];
   __shared__ T s_ey[kFwdTile + 1][kFwdTile + 2];
   __shared__ double s_mean[2];
-  __shared__ int s_last;
   const FwdItem it = items[blockIdx.x];
   load_inst(&sI, insts + it.inst);
   const InstDev &I = sI;
   const WfsDev W = I.wfs[it.wfs];
   const T *phi = io.in0[it.inst] ? static_cast<const T *>(io.in0[it.inst]) : static_cast<const T *>(I.phi);
   const T *dat = static_cast<const T *>(io.in1[it.inst]);
-  T *v = static_cast<T *>(I.v) + W.v_off;
-  const int nc = W.nc, n = W.n, tid = threadIdx.x;
-  const T *et = static_cast<const T *>(I.edge_t) + 2 * W.edge_off;
-  const int *eidx = I.edge_idx + W.edge_off;
+  const int nc = W.nc, n = W.n, tid = threadIdx.x, L = I.n_layers;
 
   if (it.a0 < 0) {
-    // Tip/tilt-only sensor: sum over valid subapertures of the Fried slopes
-    // equals <Gamma^T 1, psi>, which lives on the pupil-edge corners only.
+    // Tip/tilt-only sensor: the sum of its Fried slopes over the valid
+    // subapertures is <Gamma^T 1, psi>, which lives on the pupil-edge corners.
+    const T *et = static_cast<const T *>(I.edge_t) + 2 * W.edge_off;
+    const int *eidx = I.edge_idx + W.edge_off;
     double ax = 0.0, ay = 0.0;
     if (MODE != 2) {
       for (int e = tid; e < W.n_edge; e += blockDim.x) {
@@ -127,30 +160,67 @@ __global__ void __launch_bounds__(kThreads) k_forward(const InstDev *__restrict_
       }
     }
     const double2 s = block_sum2(ax, ay);
-    double zx = s.x / W.S, zy = s.y / W.S;   // model mean slopes
-    if (MODE == 1) {
-      zx = double(dat[W.slope_off]) - zx;
-      zy = double(dat[W.slope_off + 1]) - zy;
-    } else if (MODE == 2) {
-      zx = double(dat[W.slope_off]);
-      zy = double(dat[W.slope_off + 1]);
+    if (tid == 0) {
+      double zx = s.x / W.S, zy = s.y / W.S;   // model mean slopes
+      if (MODE == 1) {
+        zx = double(dat[W.slope_off]) - zx;
+        zy = double(dat[W.slope_off + 1]) - zy;
+      } else if (MODE == 2) {
+        zx = double(dat[W.slope_off]);
+        zy = double(dat[W.slope_off + 1]);
+      }
+      // C^-1 = sigma^-2 I_2 on the two means; M^T spreads w/S to every slope
+      T *ttc = static_cast<T *>(I.ttc);
+      ttc[2 * W.tt_idx] = T(W.inv_sigma2 * zx / W.S);
+      ttc[2 * W.tt_idx + 1] = T(W.inv_sigma2 * zy / W.S);
     }
-    // C^-1 = sigma^-2 I_2 on the two means, M^T spreads w/S to every slope
-    const T cx = T(W.inv_sigma2 * zx / W.S), cy = T(W.inv_sigma2 * zy / W.S);
-    for (int e = tid; e < W.n_edge; e += blockDim.x) v[eidx[e]] = cx * et[2 * e] + cy * et[2 * e + 1];
     return;
   }
 
+  // stage this tile's corner->node tables for every layer
+  int *s_N = reinterpret_cast<int *>(fsm);
+  int *s_off = s_N + L;
+  int *s_x0 = s_off + L;
+  int *s_y0 = s_x0 + L * kHalo;
+  T *s_fx = reinterpret_cast<T *>(fsm + ((sizeof(int) * (2 * L + 2 * L * kHalo) + 15) & ~size_t(15)));
+  T *s_fy = s_fx + L * kHalo;
   const int a0 = it.a0, b0 = it.b0;
+  {
+    const T *pf = static_cast<const T *>(I.pos_f);
+    for (int idx = tid; idx < L * kHalo; idx += blockDim.x) {
+      const int l = idx / kHalo, u = idx - l * kHalo;
+      const int po = I.pos_off[it.wfs * L + l];
+      const int a = min(max(a0 - 1 + u, 0), nc - 1), b = min(max(b0 - 1 + u, 0), nc - 1);
+      s_x0[idx] = I.pos_i0[po + a];
+      s_fx[idx] = pf[po + a];
+      s_y0[idx] = I.pos_i0[po + nc + b];
+      s_fy[idx] = pf[po + nc + b];
+    }
+    for (int l = tid; l < L; l += blockDim.x) {
+      s_N[l] = I.layers[l].N;
+      s_off[l] = I.layers[l].off;
+    }
+  }
+  __syncthreads();
   const unsigned char *act = I.active + W.act_off;
   const int *sidx = I.sub_idx + W.sub_off;
   // 1. psi on the tile's corners plus a one-corner halo
-  for (int idx = tid; idx < (kFwdTile + 2) * (kFwdTile + 2); idx += blockDim.x) {
-    const int u = idx % (kFwdTile + 2), w = idx / (kFwdTile + 2);
+  for (int idx = tid; idx < kHalo * kHalo; idx += blockDim.x) {
+    const int u = idx % kHalo, w = idx / kHalo;
     const int a = a0 - 1 + u, b = b0 - 1 + w;
     T val = T(0);
-    if (MODE != 2 && a >= 0 && b >= 0 && a < nc && b < nc && act[b * nc + a])
-      val = trace_corner<T>(I, it.wfs, nc, phi, a, b);
+    if (MODE != 2 && a >= 0 && b >= 0 && a < nc && b < nc && act[b * nc + a]) {
+      for (int l = 0; l < L; ++l) {
+        const int N = s_N[l];
+        const int x0 = s_x0[l * kHalo + u], y0 = s_y0[l * kHalo + w];
+        const T fx = s_fx[l * kHalo + u], fy = s_fy[l * kHalo + w];
+        const int x1 = (x0 + 1) & (N - 1), y1 = (y0 + 1) & (N - 1);
+        const T *p = phi + s_off[l];
+        const T v00 = p[y0 * N + x0], v01 = p[y0 * N + x1];
+        const T v10 = p[y1 * N + x0], v11 = p[y1 * N + x1];
+        val += (T(1) - fy) * ((T(1) - fx) * v00 + fx * v01) + fy * ((T(1) - fx) * v10 + fx * v11);
+      }
+    }
     s_psi[w][u] = val;
   }
   __syncthreads();
@@ -188,6 +258,7 @@ __global__ void __launch_bounds__(kThreads) k_forward(const InstDev *__restrict_
   }
   __syncthreads();
   // 3. Gamma^T: each corner gathers its four neighbouring subapertures
+  T *v = static_cast<T *>(I.v) + W.v_off;
   {
     const int u = tid % kFwdTile, w = tid / kFwdTile;
     const int a = a0 + u, b = b0 + w;
@@ -202,30 +273,22 @@ __global__ void __launch_bounds__(kThreads) k_forward(const InstDev *__restrict_
   //    Gamma^T 1_y live on the pupil edge, the last tile of the sensor applies
   //    the rank-2 correction there once every tile's sums are in.
   const double2 s = block_sum2(sx_acc, sy_acc);
-  __threadfence();
-  __syncthreads();
   if (tid == 0) {
     I.part[W.part_off + 2 * it.tile] = s.x;
     I.part[W.part_off + 2 * it.tile + 1] = s.y;
-    __threadfence();
-    const unsigned t = atomicAdd(I.tick + kTickFwd0 + it.wfs, 1u);
-    s_last = (t == unsigned(W.n_tiles - 1));
   }
-  __syncthreads();
-  if (!s_last) return;
   __threadfence();
+  if (!last_ticket(I.tick + kTickFwd0 + it.wfs, unsigned(W.n_tiles))) return;
+  const double2 tot = sum_partials(I.part + W.part_off, W.n_tiles);
   if (tid == 0) {
-    double Sx = 0.0, Sy = 0.0;
-    for (int t = 0; t < W.n_tiles; ++t) {
-      Sx += __ldcg(I.part + W.part_off + 2 * t);
-      Sy += __ldcg(I.part + W.part_off + 2 * t + 1);
-    }
-    s_mean[0] = Sx / W.S;
-    s_mean[1] = Sy / W.S;
+    s_mean[0] = tot.x / W.S;
+    s_mean[1] = tot.y / W.S;
     I.tick[kTickFwd0 + it.wfs] = 0u;
   }
   __syncthreads();
   const T cx = T(W.inv_sigma2 * s_mean[0]), cy = T(W.inv_sigma2 * s_mean[1]);
+  const T *et = static_cast<const T *>(I.edge_t) + 2 * W.edge_off;
+  const int *eidx = I.edge_idx + W.edge_off;
   for (int e = tid; e < W.n_edge; e += blockDim.x) {
     const int c = eidx[e];
     v[c] = __ldcg(v + c) - (cx * et[2 * e] + cy * et[2 * e + 1]);
@@ -234,58 +297,103 @@ __global__ void __launch_bounds__(kThreads) k_forward(const InstDev *__restrict_
 
 // ------------------------------------------------------- transform helpers
 
-template <typename T>
+template <typename T, int LF>
 struct Filt {
-  T h[kMaxTaps], g[kMaxTaps];
-  int L;
+  T h[LF], g[LF];
+  __device__ __forceinline__ void load(const InstDev &I) {
+#pragma unroll
+    for (int t = 0; t < LF; ++t) {
+      h[t] = T(I.h[t]);
+      g[t] = T(I.g[t]);
+    }
+  }
 };
 
 template <typename T>
-__device__ __forceinline__ void load_filt(Filt<T> &f, const InstDev &I) {
-  f.L = I.Lf;
+struct W4 {
+  T w[4];
+  __device__ __forceinline__ void load(const void *base, int idx) {
+    const T *p = static_cast<const T *>(base) + 4 * idx;
 #pragma unroll
-  for (int t = 0; t < kMaxTaps; ++t) {
-    f.h[t] = T(t < I.Lf ? I.h[t] : 0.0);
-    f.g[t] = T(t < I.Lf ? I.g[t] : 0.0);
+    for (int t = 0; t < 4; ++t) w[t] = p[t];
   }
+};
+
+template <>
+__device__ __forceinline__ void W4<float>::load(const void *base, int idx) {
+  const float4 v = static_cast<const float4 *>(base)[idx];
+  w[0] = v.x;
+  w[1] = v.y;
+  w[2] = v.z;
+  w[3] = v.w;
 }
 
-// Adjoint ray-trace at layer node (row k, column i): g = sum_m P_m^T v_m, as a
-// gather over the corners whose bilinear taps include the node.
+// g on the CTA's rows [k0, k0+R0) of layer l: the transposed ray-trace
+// sum_m P_m^T v_m as a gather.  Each node has <= 4 contributing corners per
+// axis (precomputed with their bilinear weights); the tip/tilt-only sensors,
+// whose corner fields live on the pupil edge, add a short sparse list.
 template <typename T>
-__device__ __forceinline__ T gather_node(const InstDev &I, int l, int N, int k, int i) {
-  const T *pf = static_cast<const T *>(I.pos_f);
-  const T *vv = static_cast<const T *>(I.v);
-  T acc = T(0);
-  for (int m = 0; m < I.n_wfs; ++m) {
-    const WfsDev &W = I.wfs[m];
-    const int nc = W.nc;
-    const int po = I.pos_off[m * I.n_layers + l];
-    const int ro = I.rng_off[m * I.n_layers + l];
-    const int4 rx = I.rng[ro + i];
-    const int4 ry = I.rng[ro + N + k];
-    const T *vm = vv + W.v_off;
+__device__ void gather_rows(const InstDev &I, int l, int N, int R0, int crank, T *A) {
+  const int nt = blockDim.x, tid = threadIdx.x;
+  const int colsT = N < nt ? N : nt;
+  const int rowsT = nt / colsT;
+  const int ci = tid % colsT, rg = tid / colsT;
+  const int k0 = crank * R0;
+  for (int idx = tid; idx < R0 * N; idx += nt) A[idx] = T(0);
+  __syncthreads();
+  if (rg < rowsT) {
+    const T *vv = static_cast<const T *>(I.v);
+    for (int m = 0; m < I.n_wfs; ++m) {
+      const WfsDev &W = I.wfs[m];
+      if (W.kind == kTTOnly) continue;
+      const int nc = W.nc;
+      const int go = I.gt_off[m * I.n_layers + l];
+      const T *vm = vv + W.v_off;
+      for (int i = ci; i < N; i += colsT) {
+        const int cx = I.gt_cnt[go + i];
+        if (cx == 0) continue;
+        const int4 ax = I.gt_idx[go + i];
+        W4<T> wx;
+        wx.load(I.gt_w, go + i);
+        const int axs[4] = {ax.x, ax.y, ax.z, ax.w};
+        for (int kl = rg; kl < R0; kl += rowsT) {
+          const int k = k0 + kl;
+          const int cy = I.gt_cnt[go + N + k];
+          if (cy == 0) continue;
+          const int4 ay = I.gt_idx[go + N + k];
+          W4<T> wy;
+          wy.load(I.gt_w, go + N + k);
+          const int ays[4] = {ay.x, ay.y, ay.z, ay.w};
+          T acc = T(0);
 #pragma unroll
-    for (int yr = 0; yr < 2; ++yr) {
-      const int bs = yr ? ry.z : ry.x, bc = yr ? ry.w : ry.y;
-      for (int b = bs; b < bs + bc; ++b) {
-        const T fy = pf[po + nc + b];
-        const T wy = (I.pos_i0[po + nc + b] == k) ? T(1) - fy : fy;
-        T row = T(0);
+          for (int ty = 0; ty < 4; ++ty) {
+            if (ty < cy) {
+              const T *row = vm + ays[ty] * nc;
+              T s = T(0);
 #pragma unroll
-        for (int xr = 0; xr < 2; ++xr) {
-          const int as = xr ? rx.z : rx.x, ac = xr ? rx.w : rx.y;
-          for (int a = as; a < as + ac; ++a) {
-            const T fx = pf[po + a];
-            const T wx = (I.pos_i0[po + a] == i) ? T(1) - fx : fx;
-            row += wx * vm[b * nc + a];
+              for (int tx = 0; tx < 4; ++tx)
+                if (tx < cx) s += wx.w[tx] * row[axs[tx]];
+              acc += wy.w[ty] * s;
+            }
           }
+          A[kl * N + i] += acc;
         }
-        acc += wy * row;
       }
     }
   }
-  return acc;
+  if (I.n_tt == 0) return;
+  __syncthreads();
+  const int2 seg = I.tt_seg[l * I.C + crank];
+  const T *ttc = static_cast<const T *>(I.ttc);
+  const T *tw = static_cast<const T *>(I.tt_w);
+  for (int j = seg.x + tid; j < seg.y; j += nt) {
+    T acc = T(0);
+    for (int e = I.tt_beg[j]; e < I.tt_beg[j + 1]; ++e) {
+      const int k = I.tt_k[e];
+      acc += ttc[2 * k] * tw[2 * e] + ttc[2 * k + 1] * tw[2 * e + 1];
+    }
+    A[I.tt_node[j]] += acc;
+  }
 }
 
 // Epilogue of the analysis for one output coefficient.
@@ -330,13 +438,12 @@ struct Emit {
 // the plan's p), q = io.out0 (NULL: the plan's q); p.q -> alpha.
 // EPI resid: r = W g - alpha D x (x = io.out0, zeroed when cold), p = z = J^-1 r,
 // r.z -> rz.
-template <typename T, int SRC, int EPI>
+template <typename T, int SRC, int EPI, int LF>
 __global__ void __launch_bounds__(kThreads) k_analysis(const InstDev *__restrict__ insts,
                                                       const ClusterItem *__restrict__ items,
                                                       IoArgs io, int flags) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ InstDev sI;
-  __shared__ int s_last;
   cg::cluster_group cluster = cg::this_cluster();
   const int C = static_cast<int>(cluster.num_blocks());
   const int crank = static_cast<int>(cluster.block_rank());
@@ -347,10 +454,10 @@ __global__ void __launch_bounds__(kThreads) k_analysis(const InstDev *__restrict
   const int N = L.N, R0 = N / C, J = I.J, tid = threadIdx.x, nt = blockDim.x;
   T *A = reinterpret_cast<T *>(smem_raw);
   T *B = A + R0 * N;
-  T *cb = B + R0 * N;
+  T *cb = B + (R0 + kMaxTaps) * N;
   T *cb2 = cb + C * C;
-  Filt<T> f;
-  load_filt(f, I);
+  Filt<T, LF> f;
+  f.load(I);
 
   Emit<T, EPI> emit;
   emit.off = L.off;
@@ -372,10 +479,7 @@ __global__ void __launch_bounds__(kThreads) k_analysis(const InstDev *__restrict
     const T *src = static_cast<const T *>(io.in0[it.inst]) + L.off + crank * R0 * N;
     for (int idx = tid; idx < R0 * N; idx += nt) A[idx] = src[idx];
   } else {
-    for (int idx = tid; idx < R0 * N; idx += nt) {
-      const int k = crank * R0 + idx / N, i = idx % N;
-      A[idx] = gather_node<T>(I, it.layer, N, k, i);
-    }
+    gather_rows<T>(I, it.layer, N, R0, crank, A);
   }
   __syncthreads();
 
@@ -390,30 +494,33 @@ __global__ void __launch_bounds__(kThreads) k_analysis(const InstDev *__restrict
       const T *row = A + j * M;
       T lo = T(0), hi = T(0);
 #pragma unroll
-      for (int t = 0; t < kMaxTaps; ++t) {
-        if (t < f.L) {
-          const T x = row[(2 * i + t) & (M - 1)];
-          lo += f.h[t] * x;
-          hi += f.g[t] * x;
-        }
+      for (int t = 0; t < LF; ++t) {
+        const T x = row[(2 * i + t) & (M - 1)];
+        lo += f.h[t] * x;
+        hi += f.g[t] * x;
       }
       B[j * M + i] = lo;
       B[j * M + H + i] = hi;
     }
     cluster.sync();
-    // column pass (y): rows 2i..2i+Lf-1 may live in the next CTAs
+    // halo: the LF-2 rows after ours (mod M) from the next CTAs
+    for (int idx = tid; idx < (LF - 2) * M; idx += nt) {
+      const int j = idx / M, x = idx - j * M;
+      const int r = ((crank + 1) * R + j) & (M - 1);
+      B[(R + j) * M + x] = cluster.map_shared_rank(B, r >> lgR)[(r & (R - 1)) * M + x];
+    }
+    __syncthreads();
+    // column pass (y), local
     for (int idx = tid; idx < Rh * M; idx += nt) {
       const int il = idx / M, x = idx - il * M;
       const int i = crank * Rh + il;
+      const T *col = B + 2 * il * M + x;
       T lo = T(0), hi = T(0);
 #pragma unroll
-      for (int t = 0; t < kMaxTaps; ++t) {
-        if (t < f.L) {
-          const int r = (2 * i + t) & (M - 1);
-          const T val = cluster.map_shared_rank(B, r >> lgR)[(r & (R - 1)) * M + x];
-          lo += f.h[t] * val;
-          hi += f.g[t] * val;
-        }
+      for (int t = 0; t < LF; ++t) {
+        const T val = col[t * M];
+        lo += f.h[t] * val;
+        hi += f.g[t] * val;
       }
       if (x < H) {
         if (k == J) emit(i, x, J, lo);
@@ -442,12 +549,10 @@ __global__ void __launch_bounds__(kThreads) k_analysis(const InstDev *__restrict
           const int j = idx / H, i = idx - j * H;
           T lo = T(0), hi = T(0);
 #pragma unroll
-          for (int t = 0; t < kMaxTaps; ++t) {
-            if (t < f.L) {
-              const T x = cb[j * M + ((2 * i + t) & (M - 1))];
-              lo += f.h[t] * x;
-              hi += f.g[t] * x;
-            }
+          for (int t = 0; t < LF; ++t) {
+            const T x = cb[j * M + ((2 * i + t) & (M - 1))];
+            lo += f.h[t] * x;
+            hi += f.g[t] * x;
           }
           cb2[j * M + i] = lo;
           cb2[j * M + H + i] = hi;
@@ -457,12 +562,10 @@ __global__ void __launch_bounds__(kThreads) k_analysis(const InstDev *__restrict
           const int i = idx / M, x = idx - i * M;
           T lo = T(0), hi = T(0);
 #pragma unroll
-          for (int t = 0; t < kMaxTaps; ++t) {
-            if (t < f.L) {
-              const T val = cb2[((2 * i + t) & (M - 1)) * M + x];
-              lo += f.h[t] * val;
-              hi += f.g[t] * val;
-            }
+          for (int t = 0; t < LF; ++t) {
+            const T val = cb2[((2 * i + t) & (M - 1)) * M + x];
+            lo += f.h[t] * val;
+            hi += f.g[t] * val;
           }
           if (x < H && k < J) cb[i * H + x] = lo;
           else emit(i, x, (x < H) ? J : k, lo);
@@ -480,31 +583,23 @@ __global__ void __launch_bounds__(kThreads) k_analysis(const InstDev *__restrict
     const int slot = I.cl_part_off + 2 * (it.layer * C + crank);
     I.part[slot] = s.x;
     I.part[slot + 1] = s.y;
-    __threadfence();
-    const unsigned t = atomicAdd(I.tick + kTickCluster, 1u);
-    s_last = (t == unsigned(I.n_layers * C - 1));
   }
-  __syncthreads();
-  if (!s_last || tid != 0) return;
-  __threadfence();
-  double a0 = 0.0, a1 = 0.0;
-  for (int q = 0; q < I.n_layers * C; ++q) {
-    a0 += __ldcg(I.part + I.cl_part_off + 2 * q);
-    a1 += __ldcg(I.part + I.cl_part_off + 2 * q + 1);
-  }
+  if (!last_ticket(I.tick + kTickCluster, unsigned(I.n_layers * C))) return;
+  const double2 tot = sum_partials(I.part + I.cl_part_off, I.n_layers * C);
+  if (tid != 0) return;
   double *sc = I.scal;
   if (EPI == kEpiOp) {
     const double rz = sc[kRz];
-    sc[kPq] = a0;
+    sc[kPq] = tot.x;
     // r = 0 (so p = 0 and p.Ap = 0) means the iterate is already exact: step 0
-    const bool exact = (a0 == 0.0 && rz == 0.0);
-    const bool bad = !exact && (!(a0 > 0.0) || !isfinite(a0) || !isfinite(rz) || sc[kFlag] != 0.0);
+    const bool exact = (tot.x == 0.0 && rz == 0.0);
+    const bool bad = !exact && (!(tot.x > 0.0) || !isfinite(tot.x) || !isfinite(rz) || sc[kFlag] != 0.0);
     if (bad) sc[kFlag] = 1.0;
-    sc[kAlpha] = (bad || exact) ? 0.0 : rz / a0;
+    sc[kAlpha] = (bad || exact) ? 0.0 : rz / tot.x;
   } else {
-    sc[kRz] = a0;
-    sc[kRr] = a1;
-    sc[kFlag] = 0.0;
+    sc[kRz] = tot.x;
+    sc[kRr] = tot.y;
+    sc[kFlag] = isfinite(tot.x) ? 0.0 : 1.0;
     sc[kBeta] = 0.0;
   }
   I.tick[kTickCluster] = 0u;
@@ -514,12 +609,13 @@ __global__ void __launch_bounds__(kThreads) k_analysis(const InstDev *__restrict
 // SRC 0: coefficients from io.in0.  SRC 1: p <- J^-1 r + beta p (beta ignored
 // with kFlagFirst: p already holds z), written back to the plan's p.
 // Output: io.out0 (NULL: the plan's phi).
-template <typename T, int SRC>
+template <typename T, int SRC, int LF>
 __global__ void __launch_bounds__(kThreads) k_synthesis(const InstDev *__restrict__ insts,
                                                        const ClusterItem *__restrict__ items,
                                                        IoArgs io, int flags) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ InstDev sI;
+  constexpr int HL = LF / 2 - 1;   // halo rows of the column synthesis
   cg::cluster_group cluster = cg::this_cluster();
   const int C = static_cast<int>(cluster.num_blocks());
   const int crank = static_cast<int>(cluster.block_rank());
@@ -529,12 +625,12 @@ __global__ void __launch_bounds__(kThreads) k_synthesis(const InstDev *__restric
   const LayerDev &L = I.layers[it.layer];
   const int N = L.N, R0 = N / C, J = I.J, tid = threadIdx.x, nt = blockDim.x;
   T *buf0 = reinterpret_cast<T *>(smem_raw);
-  T *buf1 = buf0 + R0 * N;
-  T *cb = buf1 + R0 * N;   // low-low of the coarse stage
-  T *cb2 = cb + C * C;     // column-synthesised block
-  T *cb3 = cb2 + C * C;    // coarse pyramid (side C)
-  Filt<T> f;
-  load_filt(f, I);
+  T *buf1 = buf0 + (R0 + kMaxTaps) * N;
+  T *cb = buf1 + (R0 + kMaxTaps) * N;   // low-low of the coarse stage
+  T *cb2 = cb + C * C;                  // column-synthesised block
+  T *cb3 = cb2 + C * C;                 // coarse pyramid (side C)
+  Filt<T, LF> f;
+  f.load(I);
   T *out = io.out0[it.inst] ? static_cast<T *>(io.out0[it.inst]) : static_cast<T *>(I.phi);
   const T *src = static_cast<const T *>(io.in0[it.inst]);
   T *P = static_cast<T *>(I.p);
@@ -542,12 +638,13 @@ __global__ void __launch_bounds__(kThreads) k_synthesis(const InstDev *__restric
   const T *Jv = static_cast<const T *>(I.jinv);
   const T beta = T(I.scal[kBeta]);
   const bool first = (flags & kFlagFirst) != 0;
+  const bool pre = I.precond != 0;
   auto coef = [&](int row, int col) -> T {
     const int idx = L.off + row * N + col;
     if (SRC == 0) return src[idx];
     if (first) return P[idx];
     const T r = Rv[idx];
-    const T z = I.precond ? Jv[idx] * r : r;
+    const T z = pre ? Jv[idx] * r : r;
     const T pn = z + beta * P[idx];
     P[idx] = pn;
     return pn;
@@ -569,28 +666,28 @@ __global__ void __launch_bounds__(kThreads) k_synthesis(const InstDev *__restric
         const int M = N >> (k - 1), H = M >> 1;
         for (int idx = tid; idx < M * M; idx += nt) {
           const int y = idx / M, x = idx - y * M;
+          const int p = y & 1;
           T acc = T(0);
 #pragma unroll
-          for (int t = 0; t < kMaxTaps; ++t) {
-            if (t < f.L && !((y - t) & 1)) {
-              const int ii = ((y - t) & (M - 1)) >> 1;
-              const T lo = x < H ? cb[ii * H + x] : cb3[ii * C + x];
-              const T hi = cb3[(H + ii) * C + x];
-              acc += f.h[t] * lo + f.g[t] * hi;
-            }
+          for (int s = 0; s < LF / 2; ++s) {
+            const int t = p + 2 * s;
+            const int ii = ((y - t) & (M - 1)) >> 1;
+            const T lo = x < H ? cb[ii * H + x] : cb3[ii * C + x];
+            const T hi = cb3[(H + ii) * C + x];
+            acc += f.h[t] * lo + f.g[t] * hi;
           }
           cb2[y * M + x] = acc;
         }
         __syncthreads();
         for (int idx = tid; idx < M * M; idx += nt) {
           const int y = idx / M, j = idx - y * M;
+          const int q = j & 1;
           T acc = T(0);
 #pragma unroll
-          for (int t = 0; t < kMaxTaps; ++t) {
-            if (t < f.L && !((j - t) & 1)) {
-              const int jj = ((j - t) & (M - 1)) >> 1;
-              acc += f.h[t] * cb2[y * M + jj] + f.g[t] * cb2[y * M + H + jj];
-            }
+          for (int s = 0; s < LF / 2; ++s) {
+            const int t = q + 2 * s;
+            const int jj = ((j - t) & (M - 1)) >> 1;
+            acc += f.h[t] * cb2[y * M + jj] + f.g[t] * cb2[y * M + H + jj];
           }
           cb[y * M + j] = acc;
         }
@@ -614,27 +711,36 @@ __global__ void __launch_bounds__(kThreads) k_synthesis(const InstDev *__restric
     const int M = N >> (k - 1), H = M >> 1, R = M / C, Rh = R >> 1;
     int lgRh = 0;
     while ((1 << lgRh) < Rh) ++lgRh;
+    T *BL = B;                      // low-y rows:  HL halo rows, then Rh own rows
+    T *BH = B + (HL + Rh) * M;      // high-y rows: same layout
     // step 1: own low-y rows (LL | HL) and high-y rows (LH | HH)
     for (int idx = tid; idx < Rh * M; idx += nt) {
       const int jl = idx / M, x = idx - jl * M;
       const int i = crank * Rh + jl;
-      B[jl * M + x] = x < H ? A[jl * H + x] : coef(i, x);
-      B[(Rh + jl) * M + x] = coef(H + i, x);
+      BL[(HL + jl) * M + x] = x < H ? A[jl * H + x] : coef(i, x);
+      BH[(HL + jl) * M + x] = coef(H + i, x);
     }
     cluster.sync();
-    // step 2: column synthesis of own output rows; inputs may be remote
+    // halo: the HL rows before ours (mod H) from the previous CTAs
+    for (int idx = tid; idx < HL * M; idx += nt) {
+      const int j = idx / M, x = idx - j * M;
+      const int ii = (crank * Rh - HL + j) & (H - 1);
+      const int owner = ii >> lgRh, li = ii & (Rh - 1);
+      const T *oB = cluster.map_shared_rank(B, owner);
+      BL[j * M + x] = oB[(HL + li) * M + x];
+      BH[j * M + x] = oB[(HL + Rh + HL + li) * M + x];
+    }
+    __syncthreads();
+    // step 2: column synthesis of own output rows (local)
     for (int idx = tid; idx < R * M; idx += nt) {
       const int yl = idx / M, x = idx - yl * M;
-      const int y = crank * R + yl;
+      const int p = yl & 1;
+      const int base = ((yl - p) >> 1) + HL;
       T acc = T(0);
 #pragma unroll
-      for (int t = 0; t < kMaxTaps; ++t) {
-        if (t < f.L && !((y - t) & 1)) {
-          const int ii = ((y - t) & (M - 1)) >> 1;
-          const T *Bo = cluster.map_shared_rank(B, ii >> lgRh);
-          const int li = ii & (Rh - 1);
-          acc += f.h[t] * Bo[li * M + x] + f.g[t] * Bo[(Rh + li) * M + x];
-        }
+      for (int s = 0; s < LF / 2; ++s) {
+        const int t = p + 2 * s;
+        acc += f.h[t] * BL[(base - s) * M + x] + f.g[t] * BH[(base - s) * M + x];
       }
       A[yl * M + x] = acc;
     }
@@ -642,13 +748,14 @@ __global__ void __launch_bounds__(kThreads) k_synthesis(const InstDev *__restric
     // step 3: row synthesis (local)
     for (int idx = tid; idx < R * M; idx += nt) {
       const int yl = idx / M, j = idx - yl * M;
+      const int q = j & 1;
+      const T *row = A + yl * M;
       T acc = T(0);
 #pragma unroll
-      for (int t = 0; t < kMaxTaps; ++t) {
-        if (t < f.L && !((j - t) & 1)) {
-          const int jj = ((j - t) & (M - 1)) >> 1;
-          acc += f.h[t] * A[yl * M + jj] + f.g[t] * A[yl * M + H + jj];
-        }
+      for (int s = 0; s < LF / 2; ++s) {
+        const int t = q + 2 * s;
+        const int jj = ((j >> 1) - s) & (H - 1);
+        acc += f.h[t] * row[jj] + f.g[t] * row[H + jj];
       }
       if (k == 1) out[L.off + (crank * R + yl) * N + j] = acc;
       else B[yl * M + j] = acc;
@@ -662,54 +769,71 @@ __global__ void __launch_bounds__(kThreads) k_synthesis(const InstDev *__restric
 
 // -------------------------------------------------------------- k_update
 // x += alpha p, r -= alpha q, z = J^-1 r, r.z and r.r; the last CTA forms
-// beta = (r.z)_new / (r.z)_old.  io.out0: x.
+// beta = (r.z)_new / (r.z)_old.  io.out0: x.  Four consecutive elements per
+// thread (kUpdChunk = 4 * kThreads).
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_update(const InstDev *__restrict__ insts,
                                                     const UpdItem *__restrict__ items, IoArgs io) {
-  __shared__ int s_last;
   const UpdItem it = items[blockIdx.x];
   const InstDev *I = insts + it.inst;
-  const double alpha_d = I->scal[kAlpha];
-  const T alpha = T(alpha_d);
+  const T alpha = T(I->scal[kAlpha]);
   T *X = static_cast<T *>(io.out0[it.inst]);
   T *R = static_cast<T *>(I->r);
   const T *P = static_cast<const T *>(I->p);
   const T *Q = static_cast<const T *>(I->q);
   const T *Jv = static_cast<const T *>(I->jinv);
   const int precond = I->precond;
-  const int end = min(it.start + kUpdChunk, I->n);
+  const int n = I->n;
   double rz = 0.0, rr = 0.0;
-  for (int idx = it.start + threadIdx.x; idx < end; idx += blockDim.x) {
-    X[idx] = X[idx] + alpha * P[idx];
-    const T r = R[idx] - alpha * Q[idx];
-    R[idx] = r;
-    const T z = precond ? Jv[idx] * r : r;
-    rz += double(r) * double(z);
-    rr += double(r) * double(r);
+  const int i0 = it.start + 4 * threadIdx.x;
+  const bool vec = sizeof(T) == 4 && i0 + 3 < n &&
+                   ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(R) |
+                     reinterpret_cast<uintptr_t>(P) | reinterpret_cast<uintptr_t>(Q) |
+                     reinterpret_cast<uintptr_t>(Jv)) & 15) == 0;
+  if (vec) {
+    const float a = float(alpha);
+    float4 x = reinterpret_cast<const float4 *>(X)[i0 / 4];
+    float4 r = reinterpret_cast<const float4 *>(R)[i0 / 4];
+    const float4 p = reinterpret_cast<const float4 *>(P)[i0 / 4];
+    const float4 q = reinterpret_cast<const float4 *>(Q)[i0 / 4];
+    float4 z;
+    x.x += a * p.x; x.y += a * p.y; x.z += a * p.z; x.w += a * p.w;
+    r.x -= a * q.x; r.y -= a * q.y; r.z -= a * q.z; r.w -= a * q.w;
+    if (precond) {
+      const float4 j = reinterpret_cast<const float4 *>(Jv)[i0 / 4];
+      z = make_float4(j.x * r.x, j.y * r.y, j.z * r.z, j.w * r.w);
+    } else {
+      z = r;
+    }
+    reinterpret_cast<float4 *>(X)[i0 / 4] = x;
+    reinterpret_cast<float4 *>(R)[i0 / 4] = r;
+    rz = double(r.x) * z.x + double(r.y) * z.y + double(r.z) * z.z + double(r.w) * z.w;
+    rr = double(r.x) * r.x + double(r.y) * r.y + double(r.z) * r.z + double(r.w) * r.w;
+  } else {
+    for (int idx = i0; idx < i0 + 4 && idx < n; ++idx) {
+      X[idx] = X[idx] + alpha * P[idx];
+      const T r = R[idx] - alpha * Q[idx];
+      R[idx] = r;
+      const T z = precond ? Jv[idx] * r : r;
+      rz += double(r) * double(z);
+      rr += double(r) * double(r);
+    }
   }
   const double2 s = block_sum2(rz, rr);
   if (threadIdx.x == 0) {
     I->part[I->upd_part_off + 2 * it.blk] = s.x;
     I->part[I->upd_part_off + 2 * it.blk + 1] = s.y;
-    __threadfence();
-    const unsigned t = atomicAdd(I->tick + kTickUpd, 1u);
-    s_last = (t == unsigned(I->n_upd_blocks - 1));
   }
-  __syncthreads();
-  if (!s_last || threadIdx.x != 0) return;
-  __threadfence();
-  double a0 = 0.0, a1 = 0.0;
-  for (int b = 0; b < I->n_upd_blocks; ++b) {
-    a0 += __ldcg(I->part + I->upd_part_off + 2 * b);
-    a1 += __ldcg(I->part + I->upd_part_off + 2 * b + 1);
-  }
+  if (!last_ticket(I->tick + kTickUpd, unsigned(I->n_upd_blocks))) return;
+  const double2 tot = sum_partials(I->part + I->upd_part_off, I->n_upd_blocks);
+  if (threadIdx.x != 0) return;
   double *sc = I->scal;
   const double rz_old = sc[kRz];
-  if (!isfinite(a0)) sc[kFlag] = 1.0;
-  const bool stop = sc[kFlag] != 0.0 || !isfinite(a0) || !(rz_old != 0.0);
-  sc[kBeta] = stop ? 0.0 : a0 / rz_old;
-  sc[kRz] = a0;
-  sc[kRr] = a1;
+  if (!isfinite(tot.x)) sc[kFlag] = 1.0;
+  const bool stop = sc[kFlag] != 0.0 || !isfinite(tot.x) || !(rz_old != 0.0);
+  sc[kBeta] = stop ? 0.0 : tot.x / rz_old;
+  sc[kRz] = tot.x;
+  sc[kRr] = tot.y;
   I->tick[kTickUpd] = 0u;
 }
 
@@ -875,67 +999,117 @@ cudaError_t allow_cluster(K kernel) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
 }
 
+template <typename T, int LF>
+cudaError_t allow_lf() {
+  cudaError_t e = cudaSuccess;
+#define TOMO_CFG(K) if (e == cudaSuccess) e = allow_cluster(K)
+  TOMO_CFG((k_synthesis<T, 0, LF>));
+  TOMO_CFG((k_synthesis<T, 1, LF>));
+  TOMO_CFG((k_analysis<T, 0, kEpiPlain, LF>));
+  TOMO_CFG((k_analysis<T, 1, kEpiPlain, LF>));
+  TOMO_CFG((k_analysis<T, 1, kEpiOp, LF>));
+  TOMO_CFG((k_analysis<T, 1, kEpiResid, LF>));
+#undef TOMO_CFG
+  return e;
+}
+
+template <typename T>
+cudaError_t allow_type() {
+  cudaError_t e = allow_lf<T, 2>();
+  if (e == cudaSuccess) e = allow_lf<T, 4>();
+  if (e == cudaSuccess) e = allow_lf<T, 6>();
+  if (e == cudaSuccess) e = allow_lf<T, 8>();
+  for (int mode = 0; mode < 3 && e == cudaSuccess; ++mode) {
+    const void *k = mode == 0 ? reinterpret_cast<const void *>(k_forward<T, 0>)
+                  : mode == 1 ? reinterpret_cast<const void *>(k_forward<T, 1>)
+                              : reinterpret_cast<const void *>(k_forward<T, 2>);
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxForwardSmem);
+  }
+  return e;
+}
+
+template <typename T, int LF>
+cudaError_t synth_lf(int src, int flags, const InstDev *insts, const ClusterItem *items, int n_clusters,
+                     int C, size_t smem, const IoArgs &io, cudaStream_t s) {
+  return src ? launch_cluster(k_synthesis<T, 1, LF>, n_clusters, C, smem, s, insts, items, io, flags)
+             : launch_cluster(k_synthesis<T, 0, LF>, n_clusters, C, smem, s, insts, items, io, flags);
+}
+
+template <typename T>
+cudaError_t synth_t(int src, int lf, int flags, const InstDev *insts, const ClusterItem *items,
+                    int n_clusters, int C, size_t smem, const IoArgs &io, cudaStream_t s) {
+  switch (lf) {
+    case 2: return synth_lf<T, 2>(src, flags, insts, items, n_clusters, C, smem, io, s);
+    case 4: return synth_lf<T, 4>(src, flags, insts, items, n_clusters, C, smem, io, s);
+    case 6: return synth_lf<T, 6>(src, flags, insts, items, n_clusters, C, smem, io, s);
+    case 8: return synth_lf<T, 8>(src, flags, insts, items, n_clusters, C, smem, io, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename T, int LF>
+cudaError_t anal_lf(int src, int epi, int flags, const InstDev *insts, const ClusterItem *items,
+                    int n_clusters, int C, size_t smem, const IoArgs &io, cudaStream_t s) {
+#define TOMO_AN(S, E) launch_cluster(k_analysis<T, S, E, LF>, n_clusters, C, smem, s, insts, items, io, flags)
+  if (src == 0) return TOMO_AN(0, kEpiPlain);
+  if (epi == kEpiPlain) return TOMO_AN(1, kEpiPlain);
+  if (epi == kEpiOp) return TOMO_AN(1, kEpiOp);
+  return TOMO_AN(1, kEpiResid);
+#undef TOMO_AN
+}
+
+template <typename T>
+cudaError_t anal_t(int src, int epi, int lf, int flags, const InstDev *insts, const ClusterItem *items,
+                   int n_clusters, int C, size_t smem, const IoArgs &io, cudaStream_t s) {
+  switch (lf) {
+    case 2: return anal_lf<T, 2>(src, epi, flags, insts, items, n_clusters, C, smem, io, s);
+    case 4: return anal_lf<T, 4>(src, epi, flags, insts, items, n_clusters, C, smem, io, s);
+    case 6: return anal_lf<T, 6>(src, epi, flags, insts, items, n_clusters, C, smem, io, s);
+    case 8: return anal_lf<T, 8>(src, epi, flags, insts, items, n_clusters, C, smem, io, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 }  // namespace
 
 cudaError_t configure_kernels() {
-  cudaError_t e = cudaSuccess;
-#define TOMO_CFG(K) if (e == cudaSuccess) e = allow_cluster(K)
-  TOMO_CFG((k_synthesis<float, 0>));
-  TOMO_CFG((k_synthesis<float, 1>));
-  TOMO_CFG((k_synthesis<double, 0>));
-  TOMO_CFG((k_synthesis<double, 1>));
-  TOMO_CFG((k_analysis<float, 0, kEpiPlain>));
-  TOMO_CFG((k_analysis<float, 1, kEpiPlain>));
-  TOMO_CFG((k_analysis<float, 1, kEpiOp>));
-  TOMO_CFG((k_analysis<float, 1, kEpiResid>));
-  TOMO_CFG((k_analysis<double, 0, kEpiPlain>));
-  TOMO_CFG((k_analysis<double, 1, kEpiPlain>));
-  TOMO_CFG((k_analysis<double, 1, kEpiOp>));
-  TOMO_CFG((k_analysis<double, 1, kEpiResid>));
-#undef TOMO_CFG
+  cudaError_t e = allow_type<float>();
+  if (e == cudaSuccess) e = allow_type<double>();
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
   return e;
 }
 
-cudaError_t launch_synthesis(int precision, int src, int flags, const InstDev *insts,
+size_t forward_smem(int n_layers, int precision) {
+  return fwd_table_bytes(n_layers, precision ? 8 : 4);
+}
+
+cudaError_t launch_synthesis(int precision, int src, int lf, int flags, const InstDev *insts,
                              const ClusterItem *items, int n_clusters, int C, size_t smem,
                              const IoArgs &io, cudaStream_t s) {
-  if (precision == 0)
-    return src ? launch_cluster(k_synthesis<float, 1>, n_clusters, C, smem, s, insts, items, io, flags)
-               : launch_cluster(k_synthesis<float, 0>, n_clusters, C, smem, s, insts, items, io, flags);
-  return src ? launch_cluster(k_synthesis<double, 1>, n_clusters, C, smem, s, insts, items, io, flags)
-             : launch_cluster(k_synthesis<double, 0>, n_clusters, C, smem, s, insts, items, io, flags);
+  return precision == 0 ? synth_t<float>(src, lf, flags, insts, items, n_clusters, C, smem, io, s)
+                        : synth_t<double>(src, lf, flags, insts, items, n_clusters, C, smem, io, s);
 }
 
-cudaError_t launch_analysis(int precision, int src, int epi, int flags, const InstDev *insts,
+cudaError_t launch_analysis(int precision, int src, int epi, int lf, int flags, const InstDev *insts,
                             const ClusterItem *items, int n_clusters, int C, size_t smem,
                             const IoArgs &io, cudaStream_t s) {
-#define TOMO_AN(T, S, E) launch_cluster(k_analysis<T, S, E>, n_clusters, C, smem, s, insts, items, io, flags)
-  if (precision == 0) {
-    if (src == 0) return TOMO_AN(float, 0, kEpiPlain);
-    if (epi == kEpiPlain) return TOMO_AN(float, 1, kEpiPlain);
-    if (epi == kEpiOp) return TOMO_AN(float, 1, kEpiOp);
-    return TOMO_AN(float, 1, kEpiResid);
-  }
-  if (src == 0) return TOMO_AN(double, 0, kEpiPlain);
-  if (epi == kEpiPlain) return TOMO_AN(double, 1, kEpiPlain);
-  if (epi == kEpiOp) return TOMO_AN(double, 1, kEpiOp);
-  return TOMO_AN(double, 1, kEpiResid);
-#undef TOMO_AN
+  return precision == 0 ? anal_t<float>(src, epi, lf, flags, insts, items, n_clusters, C, smem, io, s)
+                        : anal_t<double>(src, epi, lf, flags, insts, items, n_clusters, C, smem, io, s);
 }
 
-cudaError_t launch_forward(int precision, int mode, const InstDev *insts, const FwdItem *items,
-                           int n_items, const IoArgs &io, cudaStream_t s) {
+cudaError_t launch_forward(int precision, int mode, int max_layers, const InstDev *insts,
+                           const FwdItem *items, int n_items, const IoArgs &io, cudaStream_t s) {
   const dim3 g(n_items), b(kThreads);
+  const size_t sm = forward_smem(max_layers, precision);
   if (precision == 0) {
-    if (mode == 0) k_forward<float, 0><<<g, b, 0, s>>>(insts, items, io);
-    else if (mode == 1) k_forward<float, 1><<<g, b, 0, s>>>(insts, items, io);
-    else k_forward<float, 2><<<g, b, 0, s>>>(insts, items, io);
+    if (mode == 0) k_forward<float, 0><<<g, b, sm, s>>>(insts, items, io);
+    else if (mode == 1) k_forward<float, 1><<<g, b, sm, s>>>(insts, items, io);
+    else k_forward<float, 2><<<g, b, sm, s>>>(insts, items, io);
   } else {
-    if (mode == 0) k_forward<double, 0><<<g, b, 0, s>>>(insts, items, io);
-    else if (mode == 1) k_forward<double, 1><<<g, b, 0, s>>>(insts, items, io);
-    else k_forward<double, 2><<<g, b, 0, s>>>(insts, items, io);
+    if (mode == 0) k_forward<double, 0><<<g, b, sm, s>>>(insts, items, io);
+    else if (mode == 1) k_forward<double, 1><<<g, b, sm, s>>>(insts, items, io);
+    else k_forward<double, 2><<<g, b, sm, s>>>(insts, items, io);
   }
   return cudaGetLastError();
 }

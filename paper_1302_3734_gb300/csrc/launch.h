@@ -8,6 +8,10 @@
 namespace tomo {
 
 constexpr int kMaxTransformSmem = 200 * 1024;   // opt-in dynamic shared memory of the transforms
+constexpr int kMaxForwardSmem = 150 * 1024;     // staged corner tables of the forward kernel
+
+// Dynamic shared memory of k_forward for `n_layers` layers.
+size_t forward_smem(int n_layers, int precision);
 
 // Raise the dynamic shared memory and cluster-size limits of every kernel once
 // per device (before any launch, and before any stream capture).
@@ -15,19 +19,19 @@ cudaError_t configure_kernels();
 
 // W^-1 over clusters of C CTAs per (instance, layer).  src: 0 = io.in0
 // coefficients, 1 = PCG direction update fused in (flags: kFlagFirst).
-cudaError_t launch_synthesis(int precision, int src, int flags, const InstDev *insts,
+cudaError_t launch_synthesis(int precision, int src, int lf, int flags, const InstDev *insts,
                              const ClusterItem *items, int n_clusters, int C, size_t smem,
                              const IoArgs &io, cudaStream_t s);
 
 // W over clusters; src 0 = io.in0 layers, 1 = adjoint gather from v; epi 0 plain,
 // 1 operator (q, p.q -> alpha), 2 residual (r, p, r.z); flags: kFlagWarm.
-cudaError_t launch_analysis(int precision, int src, int epi, int flags, const InstDev *insts,
+cudaError_t launch_analysis(int precision, int src, int epi, int lf, int flags, const InstDev *insts,
                             const ClusterItem *items, int n_clusters, int C, size_t smem,
                             const IoArgs &io, cudaStream_t s);
 
 // Ray-trace, Fried slopes, noise weighting, Gamma^T.  mode 0 operator, 1 residual,
 // 2 data only.
-cudaError_t launch_forward(int precision, int mode, const InstDev *insts, const FwdItem *items,
+cudaError_t launch_forward(int precision, int mode, int max_layers, const InstDev *insts, const FwdItem *items,
                            int n_items, const IoArgs &io, cudaStream_t s);
 
 // x, r update and the FP64 r.z reduction.
