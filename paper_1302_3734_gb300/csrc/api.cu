@@ -173,14 +173,16 @@ tomo_status enqueue_solve(tomo_plan *tp, const LaunchSet &L, const void *const *
     IoArgs io{};
     for (int i = 0; i < L.count; ++i) io.out0[i] = x[i];
     TOMO_TRY(timed(tp, kKindAnalysis, s, [&] {
-      return launch_analysis(L.precision, 1, 2, L.lf, warm ? 1 : 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem, io, s);
+      return launch_analysis(L.precision, 1, 2, L.lf, warm ? kFlagWarm : 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem,
+                             io, s);
     }, "analysis (residual)"));
     ++nk;
   }
   for (int it = 0; it < iters; ++it) {
     IoArgs none{};
     TOMO_TRY(timed(tp, kKindSynth, s, [&] {
-      return launch_synthesis(L.precision, 1, L.lf, it == 0 ? 2 : 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem, none, s);
+      return launch_synthesis(L.precision, 1, L.lf, (it == 0 ? kFlagFirst : 0) | (it << kIterShift), L.d_inst,
+                              L.cl, L.n_cl, L.C, L.smem, none, s);
     }, "synthesis"));
     TOMO_TRY(timed(tp, kKindFwd, s, [&] {
       return launch_forward(L.precision, 0, L.max_layers, L.d_inst, L.fwd, L.n_fwd, none, s);
@@ -191,7 +193,7 @@ tomo_status enqueue_solve(tomo_plan *tp, const LaunchSet &L, const void *const *
     IoArgs io{};
     for (int i = 0; i < L.count; ++i) io.out0[i] = x[i];
     TOMO_TRY(timed(tp, kKindUpd, s, [&] {
-      return launch_update(L.precision, L.d_inst, L.upd, L.n_upd, io, s);
+      return launch_update(L.precision, it << kIterShift, L.d_inst, L.upd, L.n_upd, io, s);
     }, "update"));
     nk += 4;
   }
@@ -216,6 +218,27 @@ struct DeviceGuard {
     if (prev >= 0 && cur != prev) cudaSetDevice(prev);
   }
 };
+
+// ||r|| after a solve: the FP64 partials of the last kernel that produced r
+// (the update, or the initial residual when iters == 0), summed on the host
+// in the same fixed order the device uses.
+tomo_status read_resnorm(tomo_plan *p, int iters, cudaStream_t s, double *out) {
+  const HostPlan &H = p->hp;
+  std::vector<double> part(std::max(1, H.n_part));
+  double sc[kNumScalars];
+  TOMO_CUDA(cudaMemcpyAsync(part.data(), p->h_inst.part, sizeof(double) * H.n_part,
+                            cudaMemcpyDeviceToHost, s), "reading partials");
+  TOMO_CUDA(cudaMemcpyAsync(sc, p->h_inst.scal, sizeof(sc), cudaMemcpyDeviceToHost, s), "reading scalars");
+  TOMO_CUDA(cudaStreamSynchronize(s), "synchronising the solve");
+  const int off = iters > 0 ? H.upd_part_off : H.cl_part_off;
+  const int cnt = iters > 0 ? H.n_upd_blocks : H.n_layers * H.C;
+  double rr = 0.0;
+  for (int q = 0; q < cnt; ++q) rr += part[off + 2 * q + 1];
+  *out = std::sqrt(std::max(0.0, rr));
+  if (sc[kFlag] != 0.0 || !std::isfinite(rr))
+    return fail(TOMO_ERR_BREAKDOWN, "PCG breakdown: p.Ap <= 0 or not finite");
+  return TOMO_OK;
+}
 
 }  // namespace
 
@@ -299,7 +322,6 @@ tomo_status tomo_plan_create(const tomo_geometry *g, void *cuda_stream, tomo_pla
   const size_t o_jdiag = A.take(sizeof(double) * n);
   const size_t o_scal = A.take(sizeof(double) * kNumScalars);
   const size_t o_part = A.take(sizeof(double) * std::max(1, H.n_part));
-  const size_t o_tick = A.take(sizeof(unsigned) * (kTickFwd0 + H.n_wfs));
   p->arena_bytes = align_up(A.size, 256);
   ce = cudaMalloc(&p->arena, p->arena_bytes);
   if (ce != cudaSuccess) {
@@ -333,7 +355,6 @@ tomo_status tomo_plan_create(const tomo_geometry *g, void *cuda_stream, tomo_pla
   I.jinv = base + o_jinv;
   I.scal = reinterpret_cast<double *>(base + o_scal);
   I.part = reinterpret_cast<double *>(base + o_part);
-  I.tick = reinterpret_cast<unsigned *>(base + o_tick);
   I.layers = reinterpret_cast<const LayerDev *>(base + o_layers);
   I.wfs = reinterpret_cast<const WfsDev *>(base + o_wfs);
   I.sub_idx = reinterpret_cast<const int *>(base + o_sub);
@@ -572,11 +593,7 @@ tomo_status tomo_solve(tomo_plan *p, const void *d_slopes, void *d_coeffs, int i
     TOMO_TRY(enqueue_solve(p, p->ls, sl, xs, iters, warm, s, nullptr));
   }
   if (out_resnorm) {
-    double sc[kNumScalars];
-    TOMO_CUDA(cudaMemcpyAsync(sc, p->h_inst.scal, sizeof(sc), cudaMemcpyDeviceToHost, s), "reading scalars");
-    TOMO_CUDA(cudaStreamSynchronize(s), "synchronising the solve");
-    *out_resnorm = std::sqrt(std::max(0.0, sc[kRr]));
-    if (sc[kFlag] != 0.0) return fail(TOMO_ERR_BREAKDOWN, "PCG breakdown: p.Ap <= 0 or not finite");
+    TOMO_TRY(read_resnorm(p, iters, s, out_resnorm));
   }
   return TOMO_OK;
 }

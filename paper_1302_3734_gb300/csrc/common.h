@@ -19,24 +19,23 @@ constexpr int kMaxTapsNode = 4;    // corners per axis whose bilinear taps reach
 
 enum WfsKind : int { kFull = 0, kRemoveTT = 1, kTTOnly = 2 };
 
-// Scalar slots (double) of an instance.
+// Scalar slots (double) of an instance.  r.z of iteration it lives in
+// kRz0 + (it & 1): the synthesis of iteration it writes it while reading the
+// other slot (r.z of iteration it-1) for beta.
 enum Scalar : int {
-  kRz = 0,      // r.z of the current iterate
-  kAlpha = 1,   // step length
-  kBeta = 2,    // direction update
-  kPq = 3,      // p.Ap
-  kRr = 4,      // r.r after the last update
+  kRz0 = 0,
+  kRz1 = 1,
   kFlag = 5,    // 1 after a breakdown (p.Ap <= 0 or not finite)
   kNumScalars = 8
 };
 
-// Ticket counters of an instance (unsigned).
-enum Ticket : int { kTickCluster = 0, kTickUpd = 1, kTickFwd0 = 2 };
+// Bits of the `flags` kernel argument; the iteration index sits above them.
+enum Flags : int { kFlagWarm = 1, kFlagFirst = 2, kIterShift = 8 };
 
 struct LayerDev {
   int N, log2N;
   int off;                      // offset of this layer in the coefficient / grid vectors
-  int pad;
+  int cache_kc;                 // transforms cache the coefficients of levels >= cache_kc
   double dalpha[kMaxLevels + 1];  // alpha * D at level k (index k = 1..J)
 };
 
@@ -52,7 +51,7 @@ struct WfsDev {
   int sub_off;                  // offset into the subaperture-index table (n*n)
   int act_off;                  // offset into the active-corner table (nc*nc)
   int run_off;                  // offset of the per-row valid runs (n+1 row offsets)
-  int tt_idx;                   // index among the tip/tilt-only sensors, -1 otherwise
+  int tt_idx;                   // slot among the sensors with a pupil-edge correction, -1 otherwise
   double inv_sigma2;
 };
 
@@ -66,7 +65,6 @@ struct InstDev {
   // workspace
   void *r, *p, *q, *phi, *v, *jinv;
   double *scal, *part;
-  unsigned *tick;
   // geometry tables
   const LayerDev *layers;
   const WfsDev *wfs;
@@ -79,13 +77,17 @@ struct InstDev {
   const int4 *gt_idx;           // per node: corner indices whose bilinear taps reach it
   const void *gt_w;             // their weights (4 T per node; 0 beyond the count)
   const unsigned char *gt_cnt;  // number of corners per node (<= kMaxTapsNode)
-  const int2 *tt_seg;           // per (layer, cluster rank): [first, end) tip/tilt-only nodes
+  // Pupil-edge corrections: a tip/tilt-only sensor's corner field is
+  // e_x t_x + e_y t_y and tip/tilt removal subtracts sigma^-2 (m_x t_x + m_y t_y),
+  // with t = Gamma^T 1 nonzero on the pupil edge only; both reach the layers
+  // through this sparse list.
+  const int2 *tt_seg;           // per (layer, cluster rank): [first, end) nodes with entries
   const int *tt_node;           // local node index (row-in-CTA * N + column)
   const int *tt_beg;            // entries [tt_beg[j], tt_beg[j+1]) of node j
-  const int *tt_k;              // tip/tilt-only sensor of the entry
+  const int *tt_k;              // edge slot of the entry
   const void *tt_w;             // (w t_x, w t_y) of the entry (T pairs)
-  void *ttc;                    // per tip/tilt-only sensor: the weighted mean slopes (T pairs)
-  int n_tt, pad_tt;
+  void *ttc;                    // per tip/tilt-only sensor: (e_x, e_y) (T pairs)
+  int n_tt, n_edge_wfs;         // tip/tilt-only sensors; sensors with an edge slot
   const int *edge_idx;          // corner index of each edge corner
   const void *edge_t;           // (t_x, t_y) of each edge corner (T, interleaved)
   const int *run_rows;          // per sensor (n+1): start of row b's runs in run_ab
@@ -98,6 +100,38 @@ struct IoArgs {
   const void *in1[kMaxBatch];
   void *out0[kMaxBatch];
 };
+
+#ifdef __CUDACC__
+#define TOMO_HD __host__ __device__
+#else
+#define TOMO_HD
+#endif
+
+// Shared-memory layout of the transform kernels (elements of T): two row
+// buffers of (N/C + kMaxTaps) x N, two coarse buffers of C x C, then the
+// coefficient cache.
+TOMO_HD inline int transform_cache_offset(int N, int C) {
+  return 2 * (N / C + kMaxTaps) * N + 2 * C * C;
+}
+
+// Elements of the coefficient cache of one CTA when levels >= kc are cached
+// (the largest over the cluster's ranks: rank 0 also holds the coarse block).
+TOMO_HD inline int transform_cache_size(int N, int C, int J, int kc) {
+  int kd = 0;
+  while (kd < J && (N >> kd) >= 2 * C) ++kd;
+  int total = 0;
+  for (int k = kc < 1 ? 1 : kc; k <= kd; ++k) {
+    const int M = N >> (k - 1), Rh = (M / C) >> 1;
+    total += Rh * (M >> 1) + Rh * M;
+  }
+  if (kd == J) {
+    const int M = N >> (J - 1), Rh = (M / C) >> 1;
+    total += Rh * (M >> 1);
+  } else {
+    total += C * C;
+  }
+  return total;
+}
 
 // Work items.
 struct ClusterItem { int inst, layer; };

@@ -177,16 +177,24 @@ tomo_status build_host_plan(const tomo_geometry *geo, HostPlan *P, std::string *
   // cluster size: every layer keeps >= 8 rows per CTA at level 1
   P->C = std::min(16, Nmin / 8);
   {
+    // shared memory of the transforms: row buffers, coarse buffers and the
+    // coefficient cache of as many (coarse-first) levels as fit
+    const long long esz = P->precision ? 8 : 4;
+    const long long budget = 220LL * 1024 - 4096;   // opt-in limit minus static shared memory
     long long need = 0;
-    for (const auto &d : P->layers)
-      need = std::max(need, 2LL * d.N * (d.N / P->C + kMaxTaps) * (P->precision ? 8 : 4));
-    need += 3LL * P->C * P->C * (P->precision ? 8 : 4) + 2 * kMaxTaps * 8 + 64 * 8;
-    P->smem_transform = need;
-    if (need > 200 * 1024) {
-      *err = "layer grids too large for the transform kernels at this precision "
-             "(shared memory per CTA > 200 KB)";
-      return TOMO_ERR_UNSUPPORTED;
+    for (auto &d : P->layers) {
+      const long long base = transform_cache_offset(d.N, P->C);
+      int kc = 1;
+      while (kc <= J && (base + transform_cache_size(d.N, P->C, J, kc)) * esz > budget) ++kc;
+      const long long bytes = (base + transform_cache_size(d.N, P->C, J, kc)) * esz;
+      if (bytes > budget) {
+        *err = "layer grids too large for the transform kernels at this precision";
+        return TOMO_ERR_UNSUPPORTED;
+      }
+      d.cache_kc = kc;
+      need = std::max(need, bytes);
     }
+    P->smem_transform = need;
   }
 
   // --------------------------------------------------------------- sensors
@@ -285,8 +293,13 @@ tomo_status build_host_plan(const tomo_geometry *geo, HostPlan *P, std::string *
   // reach it with their weights (the transposed ray-trace as a gather).
   P->pos_off.resize(P->n_wfs * P->n_layers);
   P->gt_off.assign(P->n_wfs * P->n_layers, -1);
+  // edge slots: tip/tilt-only sensors first (their (e_x, e_y) live in ttc),
+  // then the sensors with tip/tilt removal
   P->n_tt = 0;
   for (auto &d : P->wfs) d.tt_idx = d.kind == kTTOnly ? P->n_tt++ : -1;
+  P->n_edge_wfs = P->n_tt;
+  for (auto &d : P->wfs)
+    if (d.kind == kRemoveTT) d.tt_idx = P->n_edge_wfs++;
   struct TTEntry { int layer, node, k; double wx, wy; };
   std::vector<TTEntry> tt_entries;
   for (int m = 0; m < P->n_wfs; ++m) {
@@ -327,9 +340,8 @@ tomo_status build_host_plan(const tomo_geometry *geo, HostPlan *P, std::string *
         *err = buf;
         return TOMO_ERR_GEOMETRY;
       }
-      if (d.kind == kTTOnly) {
-        // sparse adjoint of the tip/tilt-only sensor: its corner field is
-        // e_x t_x + e_y t_y on the pupil-edge corners only
+      if (d.kind == kTTOnly || d.kind == kRemoveTT) {
+        // sparse adjoint of the rank-2 pupil-edge term of the sensor
         for (int e = d.edge_off; e < d.edge_off + d.n_edge; ++e) {
           const int c = P->edge_idx[e], a = c % nc, b = c / nc;
           const double tx = P->edge_t[2 * e], ty = P->edge_t[2 * e + 1];
@@ -341,7 +353,7 @@ tomo_status build_host_plan(const tomo_geometry *geo, HostPlan *P, std::string *
             if (ws[t] != 0.0)
               tt_entries.push_back({l, ys[t] * N + xs[t], d.tt_idx, ws[t] * tx, ws[t] * ty});
         }
-        continue;
+        if (d.kind == kTTOnly) continue;
       }
       const int go = static_cast<int>(P->gt_cnt.size());
       P->gt_off[m * P->n_layers + l] = go;
@@ -374,7 +386,11 @@ tomo_status build_host_plan(const tomo_geometry *geo, HostPlan *P, std::string *
       }
     }
   }
-  // group the tip/tilt-only entries by (layer, cluster rank, node)
+  if (P->n_edge_wfs > 64) {
+    *err = "more than 64 sensors with tip/tilt removal or tip/tilt-only measurement";
+    return TOMO_ERR_UNSUPPORTED;
+  }
+  // group the pupil-edge entries by (layer, cluster rank, node)
   std::sort(tt_entries.begin(), tt_entries.end(), [](const TTEntry &x, const TTEntry &y) {
     return x.layer != y.layer ? x.layer < y.layer : (x.node != y.node ? x.node < y.node : x.k < y.k);
   });

@@ -34,7 +34,7 @@ struct HostPlan {
   std::vector<int2> tt_seg;        // per (layer, rank)
   std::vector<int> tt_node, tt_beg, tt_k;
   std::vector<double> tt_w;        // 2 per entry
-  int n_tt = 0;
+  int n_tt = 0, n_edge_wfs = 0;
   std::vector<int> edge_idx;
   std::vector<double> edge_t;
   std::vector<int> run_rows;

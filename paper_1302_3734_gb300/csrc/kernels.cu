@@ -3,20 +3,28 @@
 // Per PCG iteration (Sec. 5.1 of the paper) four launches cover the operator
 // (W P^T Gamma^T C^-1 Gamma P W^-1 + alpha D) p and the (P)CG vector updates:
 //
-//   k_synthesis  p <- J^-1 r + beta p (fused), phi = W^-1 p      [cluster per layer]
+//   k_synthesis  beta from the r.z partials, p <- J^-1 r + beta p,
+//                phi = W^-1 p                                    [cluster per layer]
 //   k_forward    psi = P phi on sensor corners, Fried slopes,
-//                C^-1 weighting with tip/tilt removal, Gamma^T   [tile per sensor]
-//   k_analysis   g = sum_m P_m^T v_m (gather), q = W g + alpha D p,
-//                p.q -> alpha                                    [cluster per layer]
-//   k_update     x += alpha p, r -= alpha q, r.J^-1 r -> beta     [chunk per CTA]
+//                C^-1 weighting, Gamma^T; tip/tilt sums          [tile per sensor]
+//   k_analysis   g = sum_m P_m^T v_m (gather + pupil-edge list),
+//                q = W g + alpha D p, p.q partials               [cluster per layer]
+//   k_update     alpha from the p.q partials, x += alpha p,
+//                r -= alpha q, r.J^-1 r partials                 [chunk per CTA]
 //
 // The periodic 2-D DWT of one layer runs inside one thread-block cluster: CTA c
 // owns N/C consecutive rows; the row pass is local, and before the column pass
 // each CTA copies the Lf-2 halo rows it needs from its neighbours' shared memory
 // (distributed shared memory) next to its own rows.  The coarse levels (block
-// side <= C) are finished by CTA 0 alone.  Reductions are FP64 (warp shuffle ->
-// block -> per-CTA partial -> the last CTA, in a fixed order), so results do not
-// depend on scheduling.
+// side <= C) are finished by CTA 0 alone.  Each CTA loads every coefficient it
+// owns in one round trip at its start (with the PCG direction update fused in).
+//
+// Reductions are FP64: warp shuffle -> block -> one partial per CTA; the
+// consumer kernel (every CTA of it) sums the producer's partials in a fixed
+// order, so no kernel waits on a "last CTA" and results do not depend on
+// scheduling.  Kernels are launched with programmatic dependent launch: each
+// triggers its dependents at entry and waits (griddepcontrol.wait) only before
+// touching data the previous kernel wrote.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -29,6 +37,9 @@ namespace cg = cooperative_groups;
 namespace tomo {
 
 // ------------------------------------------------------------------ helpers
+
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -64,8 +75,8 @@ __device__ double2 block_sum2(double a, double b) {
 __device__ double2 sum_partials(const double *part, int count) {
   double a = 0.0, b = 0.0;
   for (int q = threadIdx.x; q < count; q += blockDim.x) {
-    a += __ldcg(part + 2 * q);
-    b += __ldcg(part + 2 * q + 1);
+    a += part[2 * q];
+    b += part[2 * q + 1];
   }
   return block_sum2(a, b);
 }
@@ -77,21 +88,6 @@ __device__ __forceinline__ void load_inst(InstDev *dst, const InstDev *src) {
   int *d = reinterpret_cast<int *>(dst);
   for (int i = threadIdx.x; i < nw; i += blockDim.x) d[i] = s[i];
   __syncthreads();
-}
-
-// Ticket of the "last CTA" pattern: every CTA publishes its partial, then the
-// CTA that draws the last ticket reduces them.  Returns true in that CTA.
-__device__ __forceinline__ bool last_ticket(unsigned *tick, unsigned total) {
-  __shared__ int s_last;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned t = atomicAdd(tick, 1u);
-    s_last = (t == total - 1) ? 1 : 0;
-  }
-  __syncthreads();
-  if (s_last) __threadfence();
-  return s_last != 0;
 }
 
 // psi at corner (a, b) of sensor m: sum over layers of the bilinear
@@ -118,9 +114,9 @@ __device__ __forceinline__ T trace_corner(const InstDev &I, int m, int nc, const
 // ------------------------------------------------------------ k_forward
 // MODE 0: operator, z = Gamma P phi.  MODE 1: residual, z = s - Gamma P phi.
 // MODE 2: data only, z = s (phi = 0).  Writes the corner field
-// v_m = Gamma_m^T C_m^-1 z_m (sigma^-2, with (I - T) when tip/tilt is removed),
-// or, for a tip/tilt-only sensor, its weighted mean slopes (e_x, e_y) whose
-// adjoint lives on the pupil edge (Sec. 4.3, operator expansion of Sec. 5.1).
+// v_m = Gamma_m^T sigma^-2 z_m and, with tip/tilt removal, each tile's sums of z
+// (the analysis subtracts the means on the pupil edge, Sec. 4.3 eq. widehatc).
+// A tip/tilt-only sensor writes its weighted mean slopes (e_x, e_y).
 // io.in0: layer grids (NULL = the plan's phi); io.in1: slopes (MODE 1, 2).
 constexpr int kHalo = kFwdTile + 2;
 
@@ -136,7 +132,7 @@ __global__ void __launch_bounds__(kThreads) k_forward(const InstDev *__restrict_
   __shared__ T s_psi[kHalo][kHalo + 1];
   __shared__ T s_ex[kFwdTile + 1][kFwdTile + 2];
   __shared__ T s_ey[kFwdTile + 1][kFwdTile + 2];
-  __shared__ double s_mean[2];
+  pdl_trigger();
   const FwdItem it = items[blockIdx.x];
   load_inst(&sI, insts + it.inst);
   const InstDev &I = sI;
@@ -150,6 +146,7 @@ __global__ void __launch_bounds__(kThreads) k_forward(const InstDev *__restrict_
     // subapertures is <Gamma^T 1, psi>, which lives on the pupil-edge corners.
     const T *et = static_cast<const T *>(I.edge_t) + 2 * W.edge_off;
     const int *eidx = I.edge_idx + W.edge_off;
+    pdl_wait();
     double ax = 0.0, ay = 0.0;
     if (MODE != 2) {
       for (int e = tid; e < W.n_edge; e += blockDim.x) {
@@ -177,7 +174,7 @@ __global__ void __launch_bounds__(kThreads) k_forward(const InstDev *__restrict_
     return;
   }
 
-  // stage this tile's corner->node tables for every layer
+  // stage this tile's corner->node tables for every layer (constant data)
   int *s_N = reinterpret_cast<int *>(fsm);
   int *s_off = s_N + L;
   int *s_x0 = s_off + L;
@@ -204,6 +201,7 @@ __global__ void __launch_bounds__(kThreads) k_forward(const InstDev *__restrict_
   __syncthreads();
   const unsigned char *act = I.active + W.act_off;
   const int *sidx = I.sub_idx + W.sub_off;
+  pdl_wait();
   // 1. psi on the tile's corners plus a one-corner halo
   for (int idx = tid; idx < kHalo * kHalo; idx += blockDim.x) {
     const int u = idx % kHalo, w = idx / kHalo;
@@ -269,29 +267,11 @@ __global__ void __launch_bounds__(kThreads) k_forward(const InstDev *__restrict_
     }
   }
   if (W.kind != kRemoveTT) return;
-  // 4. tip/tilt removal: (I - T) subtracts the mean slopes; as Gamma^T 1_x and
-  //    Gamma^T 1_y live on the pupil edge, the last tile of the sensor applies
-  //    the rank-2 correction there once every tile's sums are in.
+  // 4. tip/tilt removal: this tile's sums of z (the consumer forms the means)
   const double2 s = block_sum2(sx_acc, sy_acc);
   if (tid == 0) {
     I.part[W.part_off + 2 * it.tile] = s.x;
     I.part[W.part_off + 2 * it.tile + 1] = s.y;
-  }
-  __threadfence();
-  if (!last_ticket(I.tick + kTickFwd0 + it.wfs, unsigned(W.n_tiles))) return;
-  const double2 tot = sum_partials(I.part + W.part_off, W.n_tiles);
-  if (tid == 0) {
-    s_mean[0] = tot.x / W.S;
-    s_mean[1] = tot.y / W.S;
-    I.tick[kTickFwd0 + it.wfs] = 0u;
-  }
-  __syncthreads();
-  const T cx = T(W.inv_sigma2 * s_mean[0]), cy = T(W.inv_sigma2 * s_mean[1]);
-  const T *et = static_cast<const T *>(I.edge_t) + 2 * W.edge_off;
-  const int *eidx = I.edge_idx + W.edge_off;
-  for (int e = tid; e < W.n_edge; e += blockDim.x) {
-    const int c = eidx[e];
-    v[c] = __ldcg(v + c) - (cx * et[2 * e] + cy * et[2 * e + 1]);
   }
 }
 
@@ -305,6 +285,80 @@ struct Filt {
     for (int t = 0; t < LF; ++t) {
       h[t] = T(I.h[t]);
       g[t] = T(I.g[t]);
+    }
+  }
+};
+
+// Coefficients owned by cluster rank c of one layer, and their place in the
+// CTA's shared-memory cache.  Distributed levels k = 1..kd (block side
+// M = N/2^(k-1) >= 2C, R = M/C rows per CTA, Rh = R/2, H = M/2): the high-x
+// part of the low-y rows c*Rh + jl and the high-y rows H + c*Rh + jl; then the
+// CTA's low-low rows of level J (kd == J) or, on rank 0, the coarse pyramid
+// block of side C (kd < J).  Levels below cache_kc are read from global memory.
+struct CoefMap {
+  int N, C, J, kd, kc, crank;
+  int base[kMaxLevels + 3];
+  __device__ void init(int N_, int C_, int J_, int kc_, int crank_) {
+    N = N_;
+    C = C_;
+    J = J_;
+    crank = crank_;
+    kd = 0;
+    while (kd < J && (N >> kd) >= 2 * C) ++kd;
+    kc = kc_ < 1 ? 1 : kc_;
+    int off = 0;
+    for (int k = 1; k <= kd; ++k) {
+      base[k] = off;
+      if (k >= kc) {
+        const int M = N >> (k - 1), Rh = (M / C) >> 1;
+        off += Rh * (M >> 1) + Rh * M;
+      }
+    }
+    base[kd + 1] = off;
+    if (kd == J) {
+      const int M = N >> (J - 1), Rh = (M / C) >> 1;
+      off += Rh * (M >> 1);
+    } else if (crank == 0) {
+      off += C * C;
+    }
+    base[kd + 2] = off;
+  }
+  __device__ int total() const { return base[kd + 2]; }
+  __device__ int hl(int k, int jl, int x) const {
+    const int H = (N >> (k - 1)) >> 1;
+    return base[k] + jl * H + (x - H);
+  }
+  __device__ int lh(int k, int jl, int x) const {
+    const int M = N >> (k - 1), H = M >> 1, Rh = (M / C) >> 1;
+    return base[k] + Rh * H + jl * M + x;
+  }
+  __device__ int ll(int jl, int x) const { return base[kd + 1] + jl * ((N >> (J - 1)) >> 1) + x; }
+  __device__ int coarse(int r, int c) const { return base[kd + 1] + r * C + c; }
+  // pyramid position of cache slot q
+  __device__ void pos(int q, int &row, int &col) const {
+    if (q >= base[kd + 1]) {
+      const int q2 = q - base[kd + 1];
+      if (kd == J) {
+        const int M = N >> (J - 1), H = M >> 1, Rh = (M / C) >> 1;
+        row = crank * Rh + q2 / H;
+        col = q2 % H;
+      } else {
+        row = q2 / C;
+        col = q2 % C;
+      }
+      return;
+    }
+    int k = kd;
+    while (base[k] > q) --k;
+    const int M = N >> (k - 1), H = M >> 1, Rh = (M / C) >> 1;
+    int q2 = q - base[k];
+    if (q2 < Rh * H) {
+      row = crank * Rh + q2 / H;
+      col = H + q2 % H;
+    } else {
+      q2 -= Rh * H;
+      row = H + crank * Rh + q2 / M;
+      col = q2 % M;
     }
   }
 };
@@ -328,12 +382,42 @@ __device__ __forceinline__ void W4<float>::load(const void *base, int idx) {
   w[3] = v.w;
 }
 
+// Coefficients of the pupil-edge terms, per edge slot: (e_x, e_y) of the
+// tip/tilt-only sensors, and -sigma^-2 (mean z_x, mean z_y) of the sensors
+// with tip/tilt removal (summed here from the forward tiles' partials).
+template <typename T>
+__device__ void edge_coefficients(const InstDev &I, T *s_coef) {
+  const T *ttc = static_cast<const T *>(I.ttc);
+  for (int k = threadIdx.x; k < 2 * I.n_tt; k += blockDim.x) s_coef[k] = ttc[k];
+  // one warp per sensor with tip/tilt removal, lanes in a fixed order
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  int j = 0;
+  for (int m = 0; m < I.n_wfs; ++m) {
+    const WfsDev &W = I.wfs[m];
+    if (W.kind != kRemoveTT) continue;
+    if ((j++ % nw) != warp) continue;
+    double a = 0.0, b = 0.0;
+    for (int t = lane; t < W.n_tiles; t += 32) {
+      a += I.part[W.part_off + 2 * t];
+      b += I.part[W.part_off + 2 * t + 1];
+    }
+    a = warp_sum(a);
+    b = warp_sum(b);
+    if (lane == 0) {
+      s_coef[2 * W.tt_idx] = T(-W.inv_sigma2 * (a / W.S));
+      s_coef[2 * W.tt_idx + 1] = T(-W.inv_sigma2 * (b / W.S));
+    }
+  }
+  __syncthreads();
+}
+
 // g on the CTA's rows [k0, k0+R0) of layer l: the transposed ray-trace
 // sum_m P_m^T v_m as a gather.  Each node has <= 4 contributing corners per
-// axis (precomputed with their bilinear weights); the tip/tilt-only sensors,
-// whose corner fields live on the pupil edge, add a short sparse list.
+// axis (precomputed with their bilinear weights); the pupil-edge terms add a
+// short sparse list per CTA.
 template <typename T>
-__device__ void gather_rows(const InstDev &I, int l, int N, int R0, int crank, T *A) {
+__device__ void gather_rows(const InstDev &I, int l, int N, int R0, int crank, T *A,
+                            const T *s_coef) {
   const int nt = blockDim.x, tid = threadIdx.x;
   const int colsT = N < nt ? N : nt;
   const int rowsT = nt / colsT;
@@ -381,16 +465,15 @@ __device__ void gather_rows(const InstDev &I, int l, int N, int R0, int crank, T
       }
     }
   }
-  if (I.n_tt == 0) return;
+  if (I.n_edge_wfs == 0) return;
   __syncthreads();
   const int2 seg = I.tt_seg[l * I.C + crank];
-  const T *ttc = static_cast<const T *>(I.ttc);
   const T *tw = static_cast<const T *>(I.tt_w);
   for (int j = seg.x + tid; j < seg.y; j += nt) {
     T acc = T(0);
     for (int e = I.tt_beg[j]; e < I.tt_beg[j + 1]; ++e) {
       const int k = I.tt_k[e];
-      acc += ttc[2 * k] * tw[2 * e] + ttc[2 * k + 1] * tw[2 * e + 1];
+      acc += s_coef[2 * k] * tw[2 * e] + s_coef[2 * k + 1] * tw[2 * e + 1];
     }
     A[I.tt_node[j]] += acc;
   }
@@ -398,30 +481,30 @@ __device__ void gather_rows(const InstDev &I, int l, int N, int R0, int crank, T
 
 // Epilogue of the analysis for one output coefficient.
 enum Epi : int { kEpiPlain = 0, kEpiOp = 1, kEpiResid = 2 };
-enum Flags : int { kFlagWarm = 1, kFlagFirst = 2 };
 
 template <typename T, int EPI>
 struct Emit {
   T *out;          // plain: destination
-  const T *P;      // op: direction p
+  const T *P;      // op: direction p (global), cached copy in `cache`
   T *Q;            // op: q
   T *R, *Pn, *X;   // resid: r, p, x
   const T *jinv;
+  const T *cache;
   const double *dalpha;
   int off, N, precond, warm;
   double acc0, acc1;
-  __device__ __forceinline__ void operator()(int row, int col, int level, T w) {
+  __device__ __forceinline__ void operator()(int row, int col, int level, T w, int slot) {
     const int idx = off + row * N + col;
     if (EPI == kEpiPlain) {
       out[idx] = w;
     } else if (EPI == kEpiOp) {
-      const T pv = P[idx];
+      const T pv = slot >= 0 ? cache[slot] : P[idx];
       const T q = w + T(dalpha[level]) * pv;
       Q[idx] = q;
       acc0 += double(pv) * double(q);
     } else {
       T r = w;
-      if (warm) r -= T(dalpha[level]) * X[idx];
+      if (warm) r -= T(dalpha[level]) * (slot >= 0 ? cache[slot] : X[idx]);
       else X[idx] = T(0);
       const T z = precond ? jinv[idx] * r : r;
       R[idx] = r;
@@ -435,15 +518,18 @@ struct Emit {
 // ------------------------------------------------------------ k_analysis
 // SRC 0: layer grids from io.in0.  SRC 1: adjoint gather from the plan's v.
 // EPI plain: io.out0 = W g.  EPI op: q = W g + alpha D p with p = io.in1 (NULL:
-// the plan's p), q = io.out0 (NULL: the plan's q); p.q -> alpha.
-// EPI resid: r = W g - alpha D x (x = io.out0, zeroed when cold), p = z = J^-1 r,
-// r.z -> rz.
+// the plan's p), q = io.out0 (NULL: the plan's q); partial p.q per CTA.
+// EPI resid: r = W g - alpha D x (x = io.out0, zeroed when cold), p = z = J^-1 r;
+// partials r.z and r.r per CTA.
 template <typename T, int SRC, int EPI, int LF>
 __global__ void __launch_bounds__(kThreads) k_analysis(const InstDev *__restrict__ insts,
                                                       const ClusterItem *__restrict__ items,
                                                       IoArgs io, int flags) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ InstDev sI;
+  __shared__ CoefMap cm;
+  __shared__ T s_coef[2 * 64];
+  pdl_trigger();
   cg::cluster_group cluster = cg::this_cluster();
   const int C = static_cast<int>(cluster.num_blocks());
   const int crank = static_cast<int>(cluster.block_rank());
@@ -453,9 +539,11 @@ __global__ void __launch_bounds__(kThreads) k_analysis(const InstDev *__restrict
   const LayerDev &L = I.layers[it.layer];
   const int N = L.N, R0 = N / C, J = I.J, tid = threadIdx.x, nt = blockDim.x;
   T *A = reinterpret_cast<T *>(smem_raw);
-  T *B = A + R0 * N;
+  T *B = A + (R0 + kMaxTaps) * N;
   T *cb = B + (R0 + kMaxTaps) * N;
   T *cb2 = cb + C * C;
+  T *cache = reinterpret_cast<T *>(smem_raw) + transform_cache_offset(N, C);
+  if (tid == 0) cm.init(N, C, J, L.cache_kc, crank);
   Filt<T, LF> f;
   f.load(I);
 
@@ -467,21 +555,39 @@ __global__ void __launch_bounds__(kThreads) k_analysis(const InstDev *__restrict
   emit.warm = (flags & kFlagWarm) ? 1 : 0;
   emit.acc0 = emit.acc1 = 0.0;
   emit.jinv = static_cast<const T *>(I.jinv);
+  emit.cache = cache;
   emit.out = static_cast<T *>(io.out0[it.inst]);
   emit.P = io.in1[it.inst] ? static_cast<const T *>(io.in1[it.inst]) : static_cast<const T *>(I.p);
   emit.Q = io.out0[it.inst] ? static_cast<T *>(io.out0[it.inst]) : static_cast<T *>(I.q);
   emit.R = static_cast<T *>(I.r);
   emit.Pn = static_cast<T *>(I.p);
   emit.X = static_cast<T *>(io.out0[it.inst]);
+  __syncthreads();
+  pdl_wait();
+  // a new solve starts from the residual: clear the breakdown flag
+  if (EPI == kEpiResid && it.layer == 0 && crank == 0 && tid == 0) I.scal[kFlag] = 0.0;
 
+  // epilogue inputs (p, or x for a warm residual) for every owned coefficient
+  const bool use_cache = (EPI == kEpiOp) || (EPI == kEpiResid && emit.warm);
+  if (use_cache) {
+    const T *srcv = EPI == kEpiOp ? emit.P : emit.X;
+    for (int q = tid; q < cm.total(); q += nt) {
+      int row, col;
+      cm.pos(q, row, col);
+      cache[q] = srcv[L.off + row * N + col];
+    }
+  }
   // own rows [crank*R0, (crank+1)*R0) of the layer grid
   if (SRC == 0) {
     const T *src = static_cast<const T *>(io.in0[it.inst]) + L.off + crank * R0 * N;
     for (int idx = tid; idx < R0 * N; idx += nt) A[idx] = src[idx];
   } else {
-    gather_rows<T>(I, it.layer, N, R0, crank, A);
+    if (I.n_edge_wfs > 0) edge_coefficients<T>(I, s_coef);
+    gather_rows<T>(I, it.layer, N, R0, crank, A, s_coef);
   }
   __syncthreads();
+  auto slot_hl = [&](int k, int jl, int x) { return (use_cache && k >= cm.kc) ? cm.hl(k, jl, x) : -1; };
+  auto slot_lh = [&](int k, int jl, int x) { return (use_cache && k >= cm.kc) ? cm.lh(k, jl, x) : -1; };
 
   int M = N, k = 1;
   for (; k <= J && M >= 2 * C; ++k, M >>= 1) {
@@ -523,12 +629,12 @@ __global__ void __launch_bounds__(kThreads) k_analysis(const InstDev *__restrict
         hi += f.g[t] * val;
       }
       if (x < H) {
-        if (k == J) emit(i, x, J, lo);
+        if (k == J) emit(i, x, J, lo, use_cache ? cm.ll(il, x) : -1);
         else A[il * H + x] = lo;
       } else {
-        emit(i, x, k, lo);
+        emit(i, x, k, lo, slot_hl(k, il, x));
       }
-      emit(H + i, x, k, hi);
+      emit(H + i, x, k, hi, slot_lh(k, il, x));
     }
     cluster.sync();
   }
@@ -568,46 +674,28 @@ __global__ void __launch_bounds__(kThreads) k_analysis(const InstDev *__restrict
             hi += f.g[t] * val;
           }
           if (x < H && k < J) cb[i * H + x] = lo;
-          else emit(i, x, (x < H) ? J : k, lo);
-          emit(H + i, x, k, hi);
+          else emit(i, x, (x < H) ? J : k, lo, use_cache ? cm.coarse(i, x) : -1);
+          emit(H + i, x, k, hi, use_cache ? cm.coarse(H + i, x) : -1);
         }
         __syncthreads();
       }
     }
   }
   if (EPI == kEpiPlain) return;
-
-  // FP64 reduction of the epilogue dot products and the scalar step
+  // one FP64 partial per CTA; the next kernel sums them
   const double2 s = block_sum2(emit.acc0, emit.acc1);
   if (tid == 0) {
     const int slot = I.cl_part_off + 2 * (it.layer * C + crank);
     I.part[slot] = s.x;
     I.part[slot + 1] = s.y;
   }
-  if (!last_ticket(I.tick + kTickCluster, unsigned(I.n_layers * C))) return;
-  const double2 tot = sum_partials(I.part + I.cl_part_off, I.n_layers * C);
-  if (tid != 0) return;
-  double *sc = I.scal;
-  if (EPI == kEpiOp) {
-    const double rz = sc[kRz];
-    sc[kPq] = tot.x;
-    // r = 0 (so p = 0 and p.Ap = 0) means the iterate is already exact: step 0
-    const bool exact = (tot.x == 0.0 && rz == 0.0);
-    const bool bad = !exact && (!(tot.x > 0.0) || !isfinite(tot.x) || !isfinite(rz) || sc[kFlag] != 0.0);
-    if (bad) sc[kFlag] = 1.0;
-    sc[kAlpha] = (bad || exact) ? 0.0 : rz / tot.x;
-  } else {
-    sc[kRz] = tot.x;
-    sc[kRr] = tot.y;
-    sc[kFlag] = isfinite(tot.x) ? 0.0 : 1.0;
-    sc[kBeta] = 0.0;
-  }
-  I.tick[kTickCluster] = 0u;
 }
 
 // ----------------------------------------------------------- k_synthesis
-// SRC 0: coefficients from io.in0.  SRC 1: p <- J^-1 r + beta p (beta ignored
-// with kFlagFirst: p already holds z), written back to the plan's p.
+// SRC 0: coefficients from io.in0.  SRC 1 (PCG iteration it = flags >> 8):
+// r.z of this iteration from the previous kernel's partials (the initial
+// residual's for it = 0, else the update's), beta = (r.z)_it / (r.z)_(it-1),
+// p <- J^-1 r + beta p written back (it = 0: p already holds J^-1 r).
 // Output: io.out0 (NULL: the plan's phi).
 template <typename T, int SRC, int LF>
 __global__ void __launch_bounds__(kThreads) k_synthesis(const InstDev *__restrict__ insts,
@@ -615,7 +703,10 @@ __global__ void __launch_bounds__(kThreads) k_synthesis(const InstDev *__restric
                                                        IoArgs io, int flags) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ InstDev sI;
+  __shared__ CoefMap cm;
+  __shared__ T s_beta;
   constexpr int HL = LF / 2 - 1;   // halo rows of the column synthesis
+  pdl_trigger();
   cg::cluster_group cluster = cg::this_cluster();
   const int C = static_cast<int>(cluster.num_blocks());
   const int crank = static_cast<int>(cluster.block_rank());
@@ -628,7 +719,8 @@ __global__ void __launch_bounds__(kThreads) k_synthesis(const InstDev *__restric
   T *buf1 = buf0 + (R0 + kMaxTaps) * N;
   T *cb = buf1 + (R0 + kMaxTaps) * N;   // low-low of the coarse stage
   T *cb2 = cb + C * C;                  // column-synthesised block
-  T *cb3 = cb2 + C * C;                 // coarse pyramid (side C)
+  T *cache = reinterpret_cast<T *>(smem_raw) + transform_cache_offset(N, C);
+  if (tid == 0) cm.init(N, C, J, L.cache_kc, crank);
   Filt<T, LF> f;
   f.load(I);
   T *out = io.out0[it.inst] ? static_cast<T *>(io.out0[it.inst]) : static_cast<T *>(I.phi);
@@ -636,9 +728,28 @@ __global__ void __launch_bounds__(kThreads) k_synthesis(const InstDev *__restric
   T *P = static_cast<T *>(I.p);
   const T *Rv = static_cast<const T *>(I.r);
   const T *Jv = static_cast<const T *>(I.jinv);
-  const T beta = T(I.scal[kBeta]);
+  const int iter = flags >> kIterShift;
   const bool first = (flags & kFlagFirst) != 0;
   const bool pre = I.precond != 0;
+  pdl_wait();
+  if (SRC == 1) {
+    // r.z of this iteration; the first CTA of the instance records it
+    const double prev = I.scal[kRz0 + ((iter + 1) & 1)];
+    const double flag = I.scal[kFlag];
+    const double2 s = iter == 0 ? sum_partials(I.part + I.cl_part_off, I.n_layers * C)
+                                : sum_partials(I.part + I.upd_part_off, I.n_upd_blocks);
+    if (tid == 0) {
+      double beta = 0.0;
+      if (iter > 0) {
+        const bool stop = flag != 0.0 || !isfinite(s.x) || !(prev != 0.0);
+        beta = stop ? 0.0 : s.x / prev;
+      }
+      s_beta = T(beta);
+      if (it.layer == 0 && crank == 0) I.scal[kRz0 + (iter & 1)] = s.x;
+    }
+  }
+  __syncthreads();
+  const T beta = SRC == 1 ? s_beta : T(0);
   auto coef = [&](int row, int col) -> T {
     const int idx = L.off + row * N + col;
     if (SRC == 0) return src[idx];
@@ -649,19 +760,24 @@ __global__ void __launch_bounds__(kThreads) k_synthesis(const InstDev *__restric
     P[idx] = pn;
     return pn;
   };
-  int kd = 0;   // distributed levels 1..kd
-  while (kd < J && (N >> kd) >= 2 * C) ++kd;
+  // every owned coefficient of the cached levels in one round trip
+  for (int q = tid; q < cm.total(); q += nt) {
+    int row, col;
+    cm.pos(q, row, col);
+    cache[q] = coef(row, col);
+  }
+  __syncthreads();
+  const int kd = cm.kd;
 
   T *A = buf0, *B = buf1;
   if (kd < J) {
     if (crank == 0) {
-      for (int idx = tid; idx < C * C; idx += nt) cb3[idx] = coef(idx / C, idx % C);
-      __syncthreads();
       {
         const int HJ = (N >> (J - 1)) >> 1;
-        for (int idx = tid; idx < HJ * HJ; idx += nt) cb[idx] = cb3[(idx / HJ) * C + idx % HJ];
+        for (int idx = tid; idx < HJ * HJ; idx += nt) cb[idx] = cache[cm.coarse(idx / HJ, idx % HJ)];
       }
       __syncthreads();
+      const T *c3 = cache + cm.coarse(0, 0);
       for (int k = J; k > kd; --k) {
         const int M = N >> (k - 1), H = M >> 1;
         for (int idx = tid; idx < M * M; idx += nt) {
@@ -672,8 +788,8 @@ __global__ void __launch_bounds__(kThreads) k_synthesis(const InstDev *__restric
           for (int s = 0; s < LF / 2; ++s) {
             const int t = p + 2 * s;
             const int ii = ((y - t) & (M - 1)) >> 1;
-            const T lo = x < H ? cb[ii * H + x] : cb3[ii * C + x];
-            const T hi = cb3[(H + ii) * C + x];
+            const T lo = x < H ? cb[ii * H + x] : c3[ii * C + x];
+            const T hi = c3[(H + ii) * C + x];
             acc += f.h[t] * lo + f.g[t] * hi;
           }
           cb2[y * M + x] = acc;
@@ -700,10 +816,7 @@ __global__ void __launch_bounds__(kThreads) k_synthesis(const InstDev *__restric
     for (int j = tid; j < C; j += nt) A[j] = c0[crank * C + j];
   } else {
     const int M = N >> (J - 1), H = M >> 1, Rh = (M / C) >> 1;
-    for (int idx = tid; idx < Rh * H; idx += nt) {
-      const int il = idx / H, x = idx - il * H;
-      A[il * H + x] = coef(crank * Rh + il, x);
-    }
+    for (int idx = tid; idx < Rh * H; idx += nt) A[idx] = cache[cm.ll(idx / H, idx % H)];
   }
   __syncthreads();
 
@@ -711,14 +824,15 @@ __global__ void __launch_bounds__(kThreads) k_synthesis(const InstDev *__restric
     const int M = N >> (k - 1), H = M >> 1, R = M / C, Rh = R >> 1;
     int lgRh = 0;
     while ((1 << lgRh) < Rh) ++lgRh;
+    const bool cached = k >= cm.kc;
     T *BL = B;                      // low-y rows:  HL halo rows, then Rh own rows
     T *BH = B + (HL + Rh) * M;      // high-y rows: same layout
     // step 1: own low-y rows (LL | HL) and high-y rows (LH | HH)
     for (int idx = tid; idx < Rh * M; idx += nt) {
       const int jl = idx / M, x = idx - jl * M;
       const int i = crank * Rh + jl;
-      BL[(HL + jl) * M + x] = x < H ? A[jl * H + x] : coef(i, x);
-      BH[(HL + jl) * M + x] = coef(H + i, x);
+      BL[(HL + jl) * M + x] = x < H ? A[jl * H + x] : (cached ? cache[cm.hl(k, jl, x)] : coef(i, x));
+      BH[(HL + jl) * M + x] = cached ? cache[cm.lh(k, jl, x)] : coef(H + i, x);
     }
     cluster.sync();
     // halo: the HL rows before ours (mod H) from the previous CTAs
@@ -768,15 +882,17 @@ __global__ void __launch_bounds__(kThreads) k_synthesis(const InstDev *__restric
 }
 
 // -------------------------------------------------------------- k_update
-// x += alpha p, r -= alpha q, z = J^-1 r, r.z and r.r; the last CTA forms
-// beta = (r.z)_new / (r.z)_old.  io.out0: x.  Four consecutive elements per
-// thread (kUpdChunk = 4 * kThreads).
+// alpha = (r.z)_it / (p.Ap) from the analysis partials; x += alpha p,
+// r -= alpha q, z = J^-1 r; partials r.z and r.r per CTA.  io.out0: x.
+// Four consecutive elements per thread (kUpdChunk = 4 * kThreads).
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_update(const InstDev *__restrict__ insts,
-                                                    const UpdItem *__restrict__ items, IoArgs io) {
+                                                    const UpdItem *__restrict__ items, IoArgs io,
+                                                    int flags) {
+  __shared__ T s_alpha;
+  pdl_trigger();
   const UpdItem it = items[blockIdx.x];
   const InstDev *I = insts + it.inst;
-  const T alpha = T(I->scal[kAlpha]);
   T *X = static_cast<T *>(io.out0[it.inst]);
   T *R = static_cast<T *>(I->r);
   const T *P = static_cast<const T *>(I->p);
@@ -784,6 +900,22 @@ __global__ void __launch_bounds__(kThreads) k_update(const InstDev *__restrict__
   const T *Jv = static_cast<const T *>(I->jinv);
   const int precond = I->precond;
   const int n = I->n;
+  const int iter = flags >> kIterShift;
+  pdl_wait();
+  {
+    const double rz = I->scal[kRz0 + (iter & 1)];
+    const double flag = I->scal[kFlag];
+    const double2 pq = sum_partials(I->part + I->cl_part_off, I->n_layers * I->C);
+    if (threadIdx.x == 0) {
+      // r = 0 (so p = 0 and p.Ap = 0) means the iterate is already exact: step 0
+      const bool exact = (pq.x == 0.0 && rz == 0.0);
+      const bool bad = !exact && (!(pq.x > 0.0) || !isfinite(pq.x) || !isfinite(rz) || flag != 0.0);
+      if (bad && it.blk == 0) I->scal[kFlag] = 1.0;
+      s_alpha = T((bad || exact) ? 0.0 : rz / pq.x);
+    }
+    __syncthreads();
+  }
+  const T alpha = s_alpha;
   double rz = 0.0, rr = 0.0;
   const int i0 = it.start + 4 * threadIdx.x;
   const bool vec = sizeof(T) == 4 && i0 + 3 < n &&
@@ -824,17 +956,6 @@ __global__ void __launch_bounds__(kThreads) k_update(const InstDev *__restrict__
     I->part[I->upd_part_off + 2 * it.blk] = s.x;
     I->part[I->upd_part_off + 2 * it.blk + 1] = s.y;
   }
-  if (!last_ticket(I->tick + kTickUpd, unsigned(I->n_upd_blocks))) return;
-  const double2 tot = sum_partials(I->part + I->upd_part_off, I->n_upd_blocks);
-  if (threadIdx.x != 0) return;
-  double *sc = I->scal;
-  const double rz_old = sc[kRz];
-  if (!isfinite(tot.x)) sc[kFlag] = 1.0;
-  const bool stop = sc[kFlag] != 0.0 || !isfinite(tot.x) || !(rz_old != 0.0);
-  sc[kBeta] = stop ? 0.0 : tot.x / rz_old;
-  sc[kRz] = tot.x;
-  sc[kRr] = tot.y;
-  I->tick[kTickUpd] = 0u;
 }
 
 // ---------------------------------------------------------------- k_slopes
@@ -972,23 +1093,31 @@ __global__ void k_jacobi(const InstDev *__restrict__ insts, const double *__rest
 
 namespace {
 
-template <typename K>
-cudaError_t launch_cluster(K kernel, int n_clusters, int C, size_t smem, cudaStream_t s,
-                           const InstDev *insts, const ClusterItem *items, const IoArgs &io,
-                           int flags) {
+// Every hot-path launch allows programmatic dependent launch: the kernel's
+// prologue (descriptor and table loads) overlaps the previous kernel, and
+// griddepcontrol.wait orders its reads of the previous kernel's results.
+template <typename K, typename... Args>
+cudaError_t launch_ex(K kernel, dim3 grid, int cluster, size_t smem, cudaStream_t s, Args... args) {
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(n_clusters * C);
+  cfg.gridDim = grid;
   cfg.blockDim = dim3(kThreads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = C;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
+  cudaLaunchAttribute attr[2];
+  int na = 0;
+  attr[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[na].val.programmaticStreamSerializationAllowed = 1;
+  ++na;
+  if (cluster > 0) {
+    attr[na].id = cudaLaunchAttributeClusterDimension;
+    attr[na].val.clusterDim.x = cluster;
+    attr[na].val.clusterDim.y = 1;
+    attr[na].val.clusterDim.z = 1;
+    ++na;
+  }
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kernel, insts, items, io, flags);
+  cfg.numAttrs = na;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
 template <typename K>
@@ -1031,8 +1160,9 @@ cudaError_t allow_type() {
 template <typename T, int LF>
 cudaError_t synth_lf(int src, int flags, const InstDev *insts, const ClusterItem *items, int n_clusters,
                      int C, size_t smem, const IoArgs &io, cudaStream_t s) {
-  return src ? launch_cluster(k_synthesis<T, 1, LF>, n_clusters, C, smem, s, insts, items, io, flags)
-             : launch_cluster(k_synthesis<T, 0, LF>, n_clusters, C, smem, s, insts, items, io, flags);
+  const dim3 g(n_clusters * C);
+  return src ? launch_ex(k_synthesis<T, 1, LF>, g, C, smem, s, insts, items, io, flags)
+             : launch_ex(k_synthesis<T, 0, LF>, g, C, smem, s, insts, items, io, flags);
 }
 
 template <typename T>
@@ -1050,7 +1180,8 @@ cudaError_t synth_t(int src, int lf, int flags, const InstDev *insts, const Clus
 template <typename T, int LF>
 cudaError_t anal_lf(int src, int epi, int flags, const InstDev *insts, const ClusterItem *items,
                     int n_clusters, int C, size_t smem, const IoArgs &io, cudaStream_t s) {
-#define TOMO_AN(S, E) launch_cluster(k_analysis<T, S, E, LF>, n_clusters, C, smem, s, insts, items, io, flags)
+  const dim3 g(n_clusters * C);
+#define TOMO_AN(S, E) launch_ex(k_analysis<T, S, E, LF>, g, C, smem, s, insts, items, io, flags)
   if (src == 0) return TOMO_AN(0, kEpiPlain);
   if (epi == kEpiPlain) return TOMO_AN(1, kEpiPlain);
   if (epi == kEpiOp) return TOMO_AN(1, kEpiOp);
@@ -1100,25 +1231,23 @@ cudaError_t launch_analysis(int precision, int src, int epi, int lf, int flags, 
 
 cudaError_t launch_forward(int precision, int mode, int max_layers, const InstDev *insts,
                            const FwdItem *items, int n_items, const IoArgs &io, cudaStream_t s) {
-  const dim3 g(n_items), b(kThreads);
+  const dim3 g(n_items);
   const size_t sm = forward_smem(max_layers, precision);
   if (precision == 0) {
-    if (mode == 0) k_forward<float, 0><<<g, b, sm, s>>>(insts, items, io);
-    else if (mode == 1) k_forward<float, 1><<<g, b, sm, s>>>(insts, items, io);
-    else k_forward<float, 2><<<g, b, sm, s>>>(insts, items, io);
-  } else {
-    if (mode == 0) k_forward<double, 0><<<g, b, sm, s>>>(insts, items, io);
-    else if (mode == 1) k_forward<double, 1><<<g, b, sm, s>>>(insts, items, io);
-    else k_forward<double, 2><<<g, b, sm, s>>>(insts, items, io);
+    if (mode == 0) return launch_ex(k_forward<float, 0>, g, 0, sm, s, insts, items, io);
+    if (mode == 1) return launch_ex(k_forward<float, 1>, g, 0, sm, s, insts, items, io);
+    return launch_ex(k_forward<float, 2>, g, 0, sm, s, insts, items, io);
   }
-  return cudaGetLastError();
+  if (mode == 0) return launch_ex(k_forward<double, 0>, g, 0, sm, s, insts, items, io);
+  if (mode == 1) return launch_ex(k_forward<double, 1>, g, 0, sm, s, insts, items, io);
+  return launch_ex(k_forward<double, 2>, g, 0, sm, s, insts, items, io);
 }
 
-cudaError_t launch_update(int precision, const InstDev *insts, const UpdItem *items, int n_items,
-                          const IoArgs &io, cudaStream_t s) {
-  if (precision == 0) k_update<float><<<n_items, kThreads, 0, s>>>(insts, items, io);
-  else k_update<double><<<n_items, kThreads, 0, s>>>(insts, items, io);
-  return cudaGetLastError();
+cudaError_t launch_update(int precision, int flags, const InstDev *insts, const UpdItem *items,
+                          int n_items, const IoArgs &io, cudaStream_t s) {
+  const dim3 g(n_items);
+  return precision == 0 ? launch_ex(k_update<float>, g, 0, 0, s, insts, items, io, flags)
+                        : launch_ex(k_update<double>, g, 0, 0, s, insts, items, io, flags);
 }
 
 cudaError_t launch_slopes(int precision, const InstDev *insts, int n_wfs, int max_sub2,

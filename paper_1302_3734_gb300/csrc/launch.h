@@ -7,7 +7,7 @@
 
 namespace tomo {
 
-constexpr int kMaxTransformSmem = 200 * 1024;   // opt-in dynamic shared memory of the transforms
+constexpr int kMaxTransformSmem = 220 * 1024;   // opt-in dynamic shared memory of the transforms
 constexpr int kMaxForwardSmem = 150 * 1024;     // staged corner tables of the forward kernel
 
 // Dynamic shared memory of k_forward for `n_layers` layers.
@@ -34,9 +34,9 @@ cudaError_t launch_analysis(int precision, int src, int epi, int lf, int flags, 
 cudaError_t launch_forward(int precision, int mode, int max_layers, const InstDev *insts, const FwdItem *items,
                            int n_items, const IoArgs &io, cudaStream_t s);
 
-// x, r update and the FP64 r.z reduction.
-cudaError_t launch_update(int precision, const InstDev *insts, const UpdItem *items, int n_items,
-                          const IoArgs &io, cudaStream_t s);
+// x, r update and the FP64 r.z partials; flags carries the iteration index.
+cudaError_t launch_update(int precision, int flags, const InstDev *insts, const UpdItem *items,
+                          int n_items, const IoArgs &io, cudaStream_t s);
 
 // Noise-free measurement (single instance).
 cudaError_t launch_slopes(int precision, const InstDev *insts, int n_wfs, int max_sub2,
