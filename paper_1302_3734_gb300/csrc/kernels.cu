@@ -280,6 +280,9 @@ __global__ void __launch_bounds__(kThreads) k_forward(const InstDev *__restrict_
 template <typename T, int LF>
 struct Filt {
   T h[LF], g[LF];
+  // taps 2s + parity without a runtime array index
+  __device__ __forceinline__ T hs(int parity, int s) const { return parity ? h[2 * s + 1] : h[2 * s]; }
+  __device__ __forceinline__ T gs(int parity, int s) const { return parity ? g[2 * s + 1] : g[2 * s]; }
   __device__ __forceinline__ void load(const InstDev &I) {
 #pragma unroll
     for (int t = 0; t < LF; ++t) {
@@ -790,7 +793,7 @@ __global__ void __launch_bounds__(kThreads) k_synthesis(const InstDev *__restric
             const int ii = ((y - t) & (M - 1)) >> 1;
             const T lo = x < H ? cb[ii * H + x] : c3[ii * C + x];
             const T hi = c3[(H + ii) * C + x];
-            acc += f.h[t] * lo + f.g[t] * hi;
+            acc += f.hs(p, s) * lo + f.gs(p, s) * hi;
           }
           cb2[y * M + x] = acc;
         }
@@ -803,7 +806,7 @@ __global__ void __launch_bounds__(kThreads) k_synthesis(const InstDev *__restric
           for (int s = 0; s < LF / 2; ++s) {
             const int t = q + 2 * s;
             const int jj = ((j - t) & (M - 1)) >> 1;
-            acc += f.h[t] * cb2[y * M + jj] + f.g[t] * cb2[y * M + H + jj];
+            acc += f.hs(q, s) * cb2[y * M + jj] + f.gs(q, s) * cb2[y * M + H + jj];
           }
           cb[y * M + j] = acc;
         }
@@ -852,10 +855,8 @@ __global__ void __launch_bounds__(kThreads) k_synthesis(const InstDev *__restric
       const int base = ((yl - p) >> 1) + HL;
       T acc = T(0);
 #pragma unroll
-      for (int s = 0; s < LF / 2; ++s) {
-        const int t = p + 2 * s;
-        acc += f.h[t] * BL[(base - s) * M + x] + f.g[t] * BH[(base - s) * M + x];
-      }
+      for (int s = 0; s < LF / 2; ++s)
+        acc += f.hs(p, s) * BL[(base - s) * M + x] + f.gs(p, s) * BH[(base - s) * M + x];
       A[yl * M + x] = acc;
     }
     cluster.sync();
@@ -867,9 +868,8 @@ __global__ void __launch_bounds__(kThreads) k_synthesis(const InstDev *__restric
       T acc = T(0);
 #pragma unroll
       for (int s = 0; s < LF / 2; ++s) {
-        const int t = q + 2 * s;
         const int jj = ((j >> 1) - s) & (H - 1);
-        acc += f.h[t] * row[jj] + f.g[t] * row[H + jj];
+        acc += f.hs(q, s) * row[jj] + f.gs(q, s) * row[H + jj];
       }
       if (k == 1) out[L.off + (crank * R + yl) * N + j] = acc;
       else B[yl * M + j] = acc;
