@@ -373,6 +373,7 @@ tomo_status tomo_plan_create(const tomo_geometry *g, void *cuda_stream, tomo_pla
   I.tt_w = base + o_ttw;
   I.ttc = base + o_ttc;
   I.n_tt = H.n_tt;
+  I.n_edge_wfs = H.n_edge_wfs;
   I.edge_idx = reinterpret_cast<const int *>(base + o_eidx);
   I.edge_t = base + o_et;
   I.run_rows = reinterpret_cast<const int *>(base + o_runrows);
