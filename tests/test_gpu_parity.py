@@ -8,6 +8,9 @@ Tolerances (relative L2 over the whole output):
   Jacobi diagonal 1e-12 (computed in FP64 on the device);
 * FP64 operator (precision 1): 1e-11 everywhere.
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -26,10 +29,27 @@ def torch_cuda():
     return torch
 
 
-def rel(a, b):
+ERRORS = {}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def error_log():
+    """Measured errors, written to $TOMO_PARITY_LOG (JSON) when it is set."""
+    yield
+    path = os.environ.get("TOMO_PARITY_LOG")
+    if path:
+        old = json.load(open(path)) if os.path.exists(path) else {}
+        old.update(ERRORS)
+        json.dump(old, open(path, "w"), indent=1, sort_keys=True)
+
+
+def rel(a, b, key=None):
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+    e = float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+    if key is not None:
+        ERRORS[key] = e
+    return e
 
 
 def tol(geom, fp32):
@@ -83,41 +103,45 @@ def test_synthesis(case):
     c = np.random.default_rng(1).standard_normal(case.ora.n)
     out = case.empty(case.ora.n)
     case.plan.coeffs_to_layers(case.dev(c), out)
-    assert rel(case.host(out), case.ora.join(case.ora.synthesis(c))) < tol(case.geom, 2e-6)
+    assert rel(case.host(out), case.ora.join(case.ora.synthesis(c)),
+               f"synthesis/{case.geom['name']}") < tol(case.geom, 2e-6)
 
 
 def test_analysis(case):
     phi = np.random.default_rng(2).standard_normal(case.ora.n)
     out = case.empty(case.ora.n)
     case.plan.layers_to_coeffs(case.dev(phi), out)
-    assert rel(case.host(out), case.ora.analysis(case.ora.split(phi))) < tol(case.geom, 2e-6)
+    assert rel(case.host(out), case.ora.analysis(case.ora.split(phi)),
+               f"analysis/{case.geom['name']}") < tol(case.geom, 2e-6)
 
 
 def test_measurement(case):
     phis = FrozenFlow(case.geom, 3).layers(0.0)
     out = case.empty(case.plan.n_slopes)
     case.plan.layers_to_slopes(case.dev(case.ora.join(phis)), out)
-    assert rel(case.host(out), case.ora.measure(phis)) < tol(case.geom, 1e-5)
+    assert rel(case.host(out), case.ora.measure(phis),
+               f"measurement/{case.geom['name']}") < tol(case.geom, 1e-5)
 
 
 def test_normal_operator(case):
     c = np.random.default_rng(3).standard_normal(case.ora.n)
     out = case.empty(case.ora.n)
     case.plan.apply_normal(case.dev(c), out)
-    assert rel(case.host(out), case.ora.apply_normal(c)) < tol(case.geom, 1e-5)
+    assert rel(case.host(out), case.ora.apply_normal(c),
+               f"normal/{case.geom['name']}") < tol(case.geom, 1e-5)
 
 
 def test_rhs(case):
     s = np.random.default_rng(4).standard_normal(case.plan.n_slopes)
     out = case.empty(case.ora.n)
     case.plan.rhs(case.dev(s), out)
-    assert rel(case.host(out), case.ora.rhs(s)) < tol(case.geom, 1e-5)
+    assert rel(case.host(out), case.ora.rhs(s), f"rhs/{case.geom['name']}") < tol(case.geom, 1e-5)
 
 
 def test_jacobi_diagonal(case):
     out = case.torch.empty(case.ora.n, dtype=case.torch.float64, device="cuda")
     case.plan.jacobi_diagonal(out)
-    assert rel(case.host(out), case.ora.jacobi_diagonal()) < 1e-12
+    assert rel(case.host(out), case.ora.jacobi_diagonal(), f"jacobi/{case.geom['name']}") < 1e-12
 
 
 def _frame(case, seed=7):
@@ -138,7 +162,7 @@ def test_solve(case, warm):
     x = case.host(coeffs)
     phi = case.ora.join(case.ora.synthesis(x))
     phi_ref = case.ora.join(case.ora.synthesis(x_ref))
-    assert rel(phi, phi_ref) < tol(case.geom, 1e-5)
+    assert rel(phi, phi_ref, f"solve-{'warm' if warm else 'cold'}/{case.geom['name']}") < tol(case.geom, 1e-5)
     assert np.isfinite(resn) and resn > 0
 
 
