@@ -47,7 +47,7 @@ struct LaunchSet {
   int count = 0;
   const ClusterItem *cl = nullptr;
   int n_cl = 0, C = 0;
-  size_t smem = 0;
+  size_t smem = 0, smem_a = 0;   // synthesis / analysis dynamic shared memory
   const FwdItem *fwd = nullptr;
   int n_fwd = 0, max_layers = 0, lf = 0;
   const UpdItem *upd = nullptr;
@@ -173,7 +173,7 @@ tomo_status enqueue_solve(tomo_plan *tp, const LaunchSet &L, const void *const *
     IoArgs io{};
     for (int i = 0; i < L.count; ++i) io.out0[i] = x[i];
     TOMO_TRY(timed(tp, kKindAnalysis, s, [&] {
-      return launch_analysis(L.precision, 1, 2, L.lf, warm ? kFlagWarm : 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem,
+      return launch_analysis(L.precision, 1, 2, L.lf, warm ? kFlagWarm : 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem_a,
                              io, s);
     }, "analysis (residual)"));
     ++nk;
@@ -188,7 +188,7 @@ tomo_status enqueue_solve(tomo_plan *tp, const LaunchSet &L, const void *const *
       return launch_forward(L.precision, 0, L.max_layers, L.d_inst, L.fwd, L.n_fwd, none, s);
     }, "forward"));
     TOMO_TRY(timed(tp, kKindAnalysis, s, [&] {
-      return launch_analysis(L.precision, 1, 1, L.lf, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem, none, s);
+      return launch_analysis(L.precision, 1, 1, L.lf, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem_a, none, s);
     }, "analysis"));
     IoArgs io{};
     for (int i = 0; i < L.count; ++i) io.out0[i] = x[i];
@@ -374,6 +374,10 @@ tomo_status tomo_plan_create(const tomo_geometry *g, void *cuda_stream, tomo_pla
   I.ttc = base + o_ttc;
   I.n_tt = H.n_tt;
   I.n_edge_wfs = H.n_edge_wfs;
+  I.gather_staged = H.gather_staged;
+  I.n_dense = H.n_dense;
+  I.max_tt_nodes = H.max_tt_nodes;
+  I.max_tt_entries = H.max_tt_entries;
   I.edge_idx = reinterpret_cast<const int *>(base + o_eidx);
   I.edge_t = base + o_et;
   I.run_rows = reinterpret_cast<const int *>(base + o_runrows);
@@ -464,6 +468,7 @@ tomo_status tomo_plan_create(const tomo_geometry *g, void *cuda_stream, tomo_pla
   L.n_cl = static_cast<int>(H.cl_items.size());
   L.C = H.C;
   L.smem = static_cast<size_t>(H.smem_transform);
+  L.smem_a = static_cast<size_t>(H.smem_analysis);
   L.fwd = reinterpret_cast<const FwdItem *>(base + o_fwd);
   L.n_fwd = static_cast<int>(H.fwd_items.size());
   L.max_layers = H.n_layers;
@@ -623,7 +628,7 @@ tomo_status tomo_layers_to_coeffs(tomo_plan *p, const void *d_layers, void *d_co
   io.in0[0] = d_layers;
   io.out0[0] = d_coeffs;
   return timed(p, kKindAnalysis, s, [&] {
-    return launch_analysis(L.precision, 0, 0, L.lf, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem, io, s);
+    return launch_analysis(L.precision, 0, 0, L.lf, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem_a, io, s);
   }, "analysis");
 }
 
@@ -659,7 +664,7 @@ tomo_status tomo_apply_normal(tomo_plan *p, const void *d_in, void *d_out, void 
   c.in1[0] = d_in;
   c.out0[0] = d_out;
   return timed(p, kKindAnalysis, s, [&] {
-    return launch_analysis(L.precision, 1, 1, L.lf, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem, c, s);
+    return launch_analysis(L.precision, 1, 1, L.lf, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem_a, c, s);
   }, "analysis");
 }
 
@@ -676,7 +681,7 @@ tomo_status tomo_rhs(tomo_plan *p, const void *d_slopes, void *d_out, void *cuda
   IoArgs c{};
   c.out0[0] = d_out;
   return timed(p, kKindAnalysis, s, [&] {
-    return launch_analysis(L.precision, 1, 0, L.lf, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem, c, s);
+    return launch_analysis(L.precision, 1, 0, L.lf, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem_a, c, s);
   }, "analysis");
 }
 

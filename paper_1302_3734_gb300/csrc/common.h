@@ -13,7 +13,8 @@ constexpr int kMaxTaps = 8;        // Daubechies order <= 4
 constexpr int kMaxLevels = 12;
 constexpr int kFwdTile = 16;       // corners per side of a forward tile
 constexpr int kMaxBatch = 96;      // instances per launch (kernel-argument arrays)
-constexpr int kThreads = 256;      // threads per CTA of every hot kernel
+constexpr int kThreads = 256;      // threads per CTA of the hot kernels (transforms: below)
+constexpr int kAnalysisThreads = 512;  // threads per CTA of the gather + analysis kernel
 constexpr int kUpdChunk = 1024;    // coefficients per CTA of the vector update
 constexpr int kMaxTapsNode = 4;    // corners per axis whose bilinear taps reach one node
 
@@ -88,6 +89,10 @@ struct InstDev {
   const void *tt_w;             // (w t_x, w t_y) of the entry (T pairs)
   void *ttc;                    // per tip/tilt-only sensor: (e_x, e_y) (T pairs)
   int n_tt, n_edge_wfs;         // tip/tilt-only sensors; sensors with an edge slot
+  // Staging of the gather tables in the analysis kernel's shared memory
+  // (loaded before the dependency wait); 0 = read them from global memory.
+  int gather_staged, n_dense;   // flag; sensors with a dense corner field
+  int max_tt_nodes, max_tt_entries;  // largest per-CTA pupil-edge segment
   const int *edge_idx;          // corner index of each edge corner
   const void *edge_t;           // (t_x, t_y) of each edge corner (T, interleaved)
   const int *run_rows;          // per sensor (n+1): start of row b's runs in run_ab
@@ -131,6 +136,18 @@ TOMO_HD inline int transform_cache_size(int N, int C, int J, int kc) {
     total += C * C;
   }
   return total;
+}
+
+// Bytes of the staged gather tables of one analysis CTA (precision esz):
+// per dense sensor N column taps and R0 row taps (int4 corners, 4 weights, a
+// count), the sensors' (nc, v_off), and the CTA's pupil-edge segment.
+TOMO_HD inline long long gather_stage_bytes(int n_dense, int N, int R0, int max_nodes,
+                                            int max_entries, int esz) {
+  const long long taps = static_cast<long long>(n_dense) * (N + R0);
+  long long b = taps * 16 + taps * 4 * esz + taps * 4 + n_dense * 8;
+  b += static_cast<long long>(max_nodes) * 4 + (max_nodes + 1) * 4;
+  b += static_cast<long long>(max_entries) * 4 + max_entries * 2 * esz;
+  return (b + 64 + 15) / 16 * 16;
 }
 
 // Work items.

@@ -417,6 +417,29 @@ tomo_status build_host_plan(const tomo_geometry *geo, HostPlan *P, std::string *
     }
     P->tt_beg.push_back(static_cast<int>(P->tt_k.size()));
   }
+  // staging of the gather tables in the analysis kernel, when it fits
+  P->n_dense = 0;
+  for (const auto &d : P->wfs) P->n_dense += d.kind != kTTOnly ? 1 : 0;
+  for (const auto &sg : P->tt_seg) {
+    P->max_tt_nodes = std::max(P->max_tt_nodes, sg.y - sg.x);
+    P->max_tt_entries = std::max(P->max_tt_entries, P->tt_beg[sg.y] - P->tt_beg[sg.x]);
+  }
+  {
+    const long long esz = P->precision ? 8 : 4;
+    const long long budget = 220LL * 1024 - 4096;
+    bool fits = true;
+    long long need = 0;
+    for (const auto &d : P->layers) {
+      const long long tr = (transform_cache_offset(d.N, P->C) +
+                            transform_cache_size(d.N, P->C, J, d.cache_kc)) * esz;
+      const long long st = gather_stage_bytes(P->n_dense, d.N, d.N / P->C, P->max_tt_nodes,
+                                              P->max_tt_entries, static_cast<int>(esz));
+      fits = fits && tr + st <= budget;
+      need = std::max(need, tr + st);
+    }
+    P->gather_staged = fits ? 1 : 0;
+    P->smem_analysis = fits ? need : P->smem_transform;
+  }
 
   // -------------------------------------------------- Jacobi basis profiles
   P->prof_off.assign(static_cast<size_t>(P->n_layers) * (J + 1) * 2, 0);

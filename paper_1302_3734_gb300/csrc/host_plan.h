@@ -19,7 +19,9 @@ struct HostPlan {
   int n = 0, n_slopes = 0, v_total = 0, C = 0;
   int n_part = 0, cl_part_off = 0, upd_part_off = 0, fwd_part_off = 0, n_upd_blocks = 0;
   int n_lgs = 0;
-  long long smem_transform = 0;   // dynamic shared memory of the transform kernels (bytes)
+  long long smem_transform = 0;   // dynamic shared memory of the synthesis kernel (bytes)
+  long long smem_analysis = 0;    // dynamic shared memory of the gather + analysis kernel (bytes)
+  int gather_staged = 0, n_dense = 0, max_tt_nodes = 0, max_tt_entries = 0;
   std::vector<double> h, g;
   std::vector<LayerDev> layers;
   std::vector<WfsDev> wfs;

@@ -49,7 +49,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 // Sum of (a, b) over the block; the result is returned to every thread.
 __device__ double2 block_sum2(double a, double b) {
-  __shared__ double s_red[2][kThreads / 32];
+  __shared__ double s_red[2][32];
   __shared__ double2 s_out;
   a = warp_sum(a);
   b = warp_sum(b);
@@ -208,15 +208,28 @@ __global__ void __launch_bounds__(kThreads) k_forward(const InstDev *__restrict_
     const int a = a0 - 1 + u, b = b0 - 1 + w;
     T val = T(0);
     if (MODE != 2 && a >= 0 && b >= 0 && a < nc && b < nc && act[b * nc + a]) {
-      for (int l = 0; l < L; ++l) {
-        const int N = s_N[l];
-        const int x0 = s_x0[l * kHalo + u], y0 = s_y0[l * kHalo + w];
-        const T fx = s_fx[l * kHalo + u], fy = s_fy[l * kHalo + w];
-        const int x1 = (x0 + 1) & (N - 1), y1 = (y0 + 1) & (N - 1);
-        const T *p = phi + s_off[l];
-        const T v00 = p[y0 * N + x0], v01 = p[y0 * N + x1];
-        const T v10 = p[y1 * N + x0], v11 = p[y1 * N + x1];
-        val += (T(1) - fy) * ((T(1) - fx) * v00 + fx * v01) + fy * ((T(1) - fx) * v10 + fx * v11);
+      // four layers' loads in flight at a time; the sum keeps the layer order
+      for (int l0 = 0; l0 < L; l0 += 4) {
+        T v00[4], v01[4], v10[4], v11[4], fx[4], fy[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int l = l0 + j < L ? l0 + j : L - 1;
+          const int N = s_N[l];
+          const int x0 = s_x0[l * kHalo + u], y0 = s_y0[l * kHalo + w];
+          fx[j] = s_fx[l * kHalo + u];
+          fy[j] = s_fy[l * kHalo + w];
+          const int x1 = (x0 + 1) & (N - 1), y1 = (y0 + 1) & (N - 1);
+          const T *p = phi + s_off[l];
+          v00[j] = p[y0 * N + x0];
+          v01[j] = p[y0 * N + x1];
+          v10[j] = p[y1 * N + x0];
+          v11[j] = p[y1 * N + x1];
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (l0 + j < L)
+            val += (T(1) - fy[j]) * ((T(1) - fx[j]) * v00[j] + fx[j] * v01[j]) +
+                   fy[j] * ((T(1) - fx[j]) * v10[j] + fx[j] * v11[j]);
       }
     }
     s_psi[w][u] = val;
@@ -482,6 +495,117 @@ __device__ void gather_rows(const InstDev &I, int l, int N, int R0, int crank, T
   }
 }
 
+// Shared-memory copy of the gather tables of one analysis CTA (layer l, rows
+// [k0, k0+R0)): per dense sensor the corner taps of every column and of the
+// CTA's rows, and the CTA's pupil-edge segment.  Filled before the dependency
+// wait (the tables are constant), so the copy overlaps the previous kernel.
+template <typename T>
+struct GatherStage {
+  int4 *xi, *yi;
+  T *xw, *yw, *tw;
+  int *xc, *yc, *mnc, *mvo, *tn, *tb, *tk;
+  int nn;
+
+  __device__ void carve(unsigned char *base, int Md, int N, int R0, int max_nodes, int max_entries) {
+    xi = reinterpret_cast<int4 *>(base);
+    yi = xi + Md * N;
+    xw = reinterpret_cast<T *>(yi + Md * R0);
+    yw = xw + 4 * Md * N;
+    tw = yw + 4 * Md * R0;
+    xc = reinterpret_cast<int *>(tw + 2 * max_entries);
+    yc = xc + Md * N;
+    mnc = yc + Md * R0;
+    mvo = mnc + Md;
+    tn = mvo + Md;
+    tb = tn + max_nodes;
+    tk = tb + max_nodes + 1;
+  }
+
+  __device__ void fill(const InstDev &I, int l, int N, int R0, int crank) {
+    const int nt = blockDim.x, tid = threadIdx.x, k0 = crank * R0;
+    const T *gw = static_cast<const T *>(I.gt_w);
+    int md = 0;
+    for (int m = 0; m < I.n_wfs; ++m) {
+      const WfsDev &W = I.wfs[m];
+      if (W.kind == kTTOnly) continue;
+      const int go = I.gt_off[m * I.n_layers + l];
+      if (tid == 0) {
+        mnc[md] = W.nc;
+        mvo[md] = W.v_off;
+      }
+      for (int j = tid; j < N + R0; j += nt) {
+        const int src = j < N ? go + j : go + N + k0 + (j - N);
+        const int dst = j < N ? md * N + j : md * R0 + (j - N);
+        (j < N ? xi : yi)[dst] = I.gt_idx[src];
+        (j < N ? xc : yc)[dst] = I.gt_cnt[src];
+        T *w = (j < N ? xw : yw) + 4 * dst;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) w[t] = gw[4 * src + t];
+      }
+      ++md;
+    }
+    const int2 seg = I.tt_seg[l * I.C + crank];
+    nn = seg.y - seg.x;
+    const int e0 = I.tt_beg[seg.x], ne = I.tt_beg[seg.y] - e0;
+    const T *ttw = static_cast<const T *>(I.tt_w);
+    for (int j = tid; j < nn; j += nt) tn[j] = I.tt_node[seg.x + j];
+    for (int j = tid; j <= nn; j += nt) tb[j] = I.tt_beg[seg.x + j] - e0;
+    for (int e = tid; e < ne; e += nt) {
+      tk[e] = I.tt_k[e0 + e];
+      tw[2 * e] = ttw[2 * (e0 + e)];
+      tw[2 * e + 1] = ttw[2 * (e0 + e) + 1];
+    }
+  }
+};
+
+// The gather of gather_rows from the staged tables: one node per thread and
+// pass, the sensors unrolled so that their corner loads are in flight together.
+template <typename T>
+__device__ void gather_rows_staged(const InstDev &I, const GatherStage<T> &st, int N, int R0,
+                                   T *A, const T *s_coef) {
+  const int nt = blockDim.x, tid = threadIdx.x, Md = I.n_dense;
+  const T *vv = static_cast<const T *>(I.v);
+  for (int node = tid; node < R0 * N; node += nt) {
+    const int kl = node / N, i = node - kl * N;
+    T acc = T(0);
+#pragma unroll 3
+    for (int md = 0; md < Md; ++md) {
+      const int cx = st.xc[md * N + i], cy = st.yc[md * R0 + kl];
+      const int4 ax = st.xi[md * N + i], ay = st.yi[md * R0 + kl];
+      const T *wx = st.xw + 4 * (md * N + i);
+      const T *wy = st.yw + 4 * (md * R0 + kl);
+      const T *vm = vv + st.mvo[md];
+      const int nc = st.mnc[md];
+      const int axs[4] = {ax.x, ax.y, ax.z, ax.w};
+      const int ays[4] = {ay.x, ay.y, ay.z, ay.w};
+      T part = T(0);
+#pragma unroll
+      for (int ty = 0; ty < 4; ++ty) {
+        if (ty < cy) {
+          const T *row = vm + ays[ty] * nc;
+          T sx = T(0);
+#pragma unroll
+          for (int tx = 0; tx < 4; ++tx)
+            if (tx < cx) sx += wx[tx] * row[axs[tx]];
+          part += wy[ty] * sx;
+        }
+      }
+      acc += part;
+    }
+    A[node] = acc;
+  }
+  if (I.n_edge_wfs == 0) return;
+  __syncthreads();
+  for (int j = tid; j < st.nn; j += nt) {
+    T acc = T(0);
+    for (int e = st.tb[j]; e < st.tb[j + 1]; ++e) {
+      const int k = st.tk[e];
+      acc += s_coef[2 * k] * st.tw[2 * e] + s_coef[2 * k + 1] * st.tw[2 * e + 1];
+    }
+    A[st.tn[j]] += acc;
+  }
+}
+
 // Epilogue of the analysis for one output coefficient.
 enum Epi : int { kEpiPlain = 0, kEpiOp = 1, kEpiResid = 2 };
 
@@ -525,7 +649,7 @@ struct Emit {
 // EPI resid: r = W g - alpha D x (x = io.out0, zeroed when cold), p = z = J^-1 r;
 // partials r.z and r.r per CTA.
 template <typename T, int SRC, int EPI, int LF>
-__global__ void __launch_bounds__(kThreads) k_analysis(const InstDev *__restrict__ insts,
+__global__ void __launch_bounds__(kAnalysisThreads) k_analysis(const InstDev *__restrict__ insts,
                                                       const ClusterItem *__restrict__ items,
                                                       IoArgs io, int flags) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -565,19 +689,39 @@ __global__ void __launch_bounds__(kThreads) k_analysis(const InstDev *__restrict
   emit.R = static_cast<T *>(I.r);
   emit.Pn = static_cast<T *>(I.p);
   emit.X = static_cast<T *>(io.out0[it.inst]);
+  GatherStage<T> st;
+  const bool staged = SRC == 1 && I.gather_staged;
+  if (staged) {
+    const int off = transform_cache_offset(N, C) + transform_cache_size(N, C, J, L.cache_kc);
+    unsigned char *sb = smem_raw + ((static_cast<size_t>(off) * sizeof(T) + 15) & ~size_t(15));
+    st.carve(sb, I.n_dense, N, R0, I.max_tt_nodes, I.max_tt_entries);
+    st.fill(I, it.layer, N, R0, crank);
+  }
   __syncthreads();
   pdl_wait();
   // a new solve starts from the residual: clear the breakdown flag
   if (EPI == kEpiResid && it.layer == 0 && crank == 0 && tid == 0) I.scal[kFlag] = 0.0;
 
-  // epilogue inputs (p, or x for a warm residual) for every owned coefficient
+  // epilogue inputs (p, or x for a warm residual) for every owned coefficient,
+  // eight loads in flight per thread
   const bool use_cache = (EPI == kEpiOp) || (EPI == kEpiResid && emit.warm);
   if (use_cache) {
     const T *srcv = EPI == kEpiOp ? emit.P : emit.X;
-    for (int q = tid; q < cm.total(); q += nt) {
-      int row, col;
-      cm.pos(q, row, col);
-      cache[q] = srcv[L.off + row * N + col];
+    const int total = cm.total();
+    for (int q0 = tid; q0 < total; q0 += 8 * nt) {
+      T val[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int q = q0 + u * nt;
+        if (q < total) {
+          int row, col;
+          cm.pos(q, row, col);
+          val[u] = srcv[L.off + row * N + col];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (q0 + u * nt < total) cache[q0 + u * nt] = val[u];
     }
   }
   // own rows [crank*R0, (crank+1)*R0) of the layer grid
@@ -586,7 +730,8 @@ __global__ void __launch_bounds__(kThreads) k_analysis(const InstDev *__restrict
     for (int idx = tid; idx < R0 * N; idx += nt) A[idx] = src[idx];
   } else {
     if (I.n_edge_wfs > 0) edge_coefficients<T>(I, s_coef);
-    gather_rows<T>(I, it.layer, N, R0, crank, A, s_coef);
+    if (staged) gather_rows_staged<T>(I, st, N, R0, A, s_coef);
+    else gather_rows<T>(I, it.layer, N, R0, crank, A, s_coef);
   }
   __syncthreads();
   auto slot_hl = [&](int k, int jl, int x) { return (use_cache && k >= cm.kc) ? cm.hl(k, jl, x) : -1; };
@@ -763,11 +908,44 @@ __global__ void __launch_bounds__(kThreads) k_synthesis(const InstDev *__restric
     P[idx] = pn;
     return pn;
   };
-  // every owned coefficient of the cached levels in one round trip
-  for (int q = tid; q < cm.total(); q += nt) {
-    int row, col;
-    cm.pos(q, row, col);
-    cache[q] = coef(row, col);
+  // every owned coefficient of the cached levels, eight in flight per thread
+  {
+    const int total = cm.total();
+    for (int q0 = tid; q0 < total; q0 += 8 * nt) {
+      int idx[8];
+      T rv[8], jv[8], pv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int q = q0 + u * nt;
+        if (q < total) {
+          int row, col;
+          cm.pos(q, row, col);
+          idx[u] = L.off + row * N + col;
+          if (SRC == 0) {
+            pv[u] = src[idx[u]];
+          } else {
+            pv[u] = P[idx[u]];
+            if (!first) {
+              rv[u] = Rv[idx[u]];
+              jv[u] = pre ? Jv[idx[u]] : T(1);
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int q = q0 + u * nt;
+        if (q < total) {
+          T pn = pv[u];
+          if (SRC == 1 && !first) {
+            const T z = pre ? jv[u] * rv[u] : rv[u];
+            pn = z + beta * pv[u];
+            P[idx[u]] = pn;
+          }
+          cache[q] = pn;
+        }
+      }
+    }
   }
   __syncthreads();
   const int kd = cm.kd;
@@ -1097,10 +1275,11 @@ namespace {
 // prologue (descriptor and table loads) overlaps the previous kernel, and
 // griddepcontrol.wait orders its reads of the previous kernel's results.
 template <typename K, typename... Args>
-cudaError_t launch_ex(K kernel, dim3 grid, int cluster, size_t smem, cudaStream_t s, Args... args) {
+cudaError_t launch_ex(K kernel, dim3 grid, int threads, int cluster, size_t smem, cudaStream_t s,
+                      Args... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
-  cfg.blockDim = dim3(kThreads);
+  cfg.blockDim = dim3(threads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[2];
@@ -1161,8 +1340,8 @@ template <typename T, int LF>
 cudaError_t synth_lf(int src, int flags, const InstDev *insts, const ClusterItem *items, int n_clusters,
                      int C, size_t smem, const IoArgs &io, cudaStream_t s) {
   const dim3 g(n_clusters * C);
-  return src ? launch_ex(k_synthesis<T, 1, LF>, g, C, smem, s, insts, items, io, flags)
-             : launch_ex(k_synthesis<T, 0, LF>, g, C, smem, s, insts, items, io, flags);
+  return src ? launch_ex(k_synthesis<T, 1, LF>, g, kThreads, C, smem, s, insts, items, io, flags)
+             : launch_ex(k_synthesis<T, 0, LF>, g, kThreads, C, smem, s, insts, items, io, flags);
 }
 
 template <typename T>
@@ -1181,7 +1360,7 @@ template <typename T, int LF>
 cudaError_t anal_lf(int src, int epi, int flags, const InstDev *insts, const ClusterItem *items,
                     int n_clusters, int C, size_t smem, const IoArgs &io, cudaStream_t s) {
   const dim3 g(n_clusters * C);
-#define TOMO_AN(S, E) launch_ex(k_analysis<T, S, E, LF>, g, C, smem, s, insts, items, io, flags)
+#define TOMO_AN(S, E) launch_ex(k_analysis<T, S, E, LF>, g, kAnalysisThreads, C, smem, s, insts, items, io, flags)
   if (src == 0) return TOMO_AN(0, kEpiPlain);
   if (epi == kEpiPlain) return TOMO_AN(1, kEpiPlain);
   if (epi == kEpiOp) return TOMO_AN(1, kEpiOp);
@@ -1234,20 +1413,20 @@ cudaError_t launch_forward(int precision, int mode, int max_layers, const InstDe
   const dim3 g(n_items);
   const size_t sm = forward_smem(max_layers, precision);
   if (precision == 0) {
-    if (mode == 0) return launch_ex(k_forward<float, 0>, g, 0, sm, s, insts, items, io);
-    if (mode == 1) return launch_ex(k_forward<float, 1>, g, 0, sm, s, insts, items, io);
-    return launch_ex(k_forward<float, 2>, g, 0, sm, s, insts, items, io);
+    if (mode == 0) return launch_ex(k_forward<float, 0>, g, kThreads, 0, sm, s, insts, items, io);
+    if (mode == 1) return launch_ex(k_forward<float, 1>, g, kThreads, 0, sm, s, insts, items, io);
+    return launch_ex(k_forward<float, 2>, g, kThreads, 0, sm, s, insts, items, io);
   }
-  if (mode == 0) return launch_ex(k_forward<double, 0>, g, 0, sm, s, insts, items, io);
-  if (mode == 1) return launch_ex(k_forward<double, 1>, g, 0, sm, s, insts, items, io);
-  return launch_ex(k_forward<double, 2>, g, 0, sm, s, insts, items, io);
+  if (mode == 0) return launch_ex(k_forward<double, 0>, g, kThreads, 0, sm, s, insts, items, io);
+  if (mode == 1) return launch_ex(k_forward<double, 1>, g, kThreads, 0, sm, s, insts, items, io);
+  return launch_ex(k_forward<double, 2>, g, kThreads, 0, sm, s, insts, items, io);
 }
 
 cudaError_t launch_update(int precision, int flags, const InstDev *insts, const UpdItem *items,
                           int n_items, const IoArgs &io, cudaStream_t s) {
   const dim3 g(n_items);
-  return precision == 0 ? launch_ex(k_update<float>, g, 0, 0, s, insts, items, io, flags)
-                        : launch_ex(k_update<double>, g, 0, 0, s, insts, items, io, flags);
+  return precision == 0 ? launch_ex(k_update<float>, g, kThreads, 0, 0, s, insts, items, io, flags)
+                        : launch_ex(k_update<double>, g, kThreads, 0, 0, s, insts, items, io, flags);
 }
 
 cudaError_t launch_slopes(int precision, const InstDev *insts, int n_wfs, int max_sub2,
