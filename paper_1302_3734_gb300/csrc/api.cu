@@ -171,7 +171,10 @@ tomo_status enqueue_solve(tomo_plan *tp, const LaunchSet &L, const void *const *
   }
   {
     IoArgs io{};
-    for (int i = 0; i < L.count; ++i) io.out0[i] = x[i];
+    for (int i = 0; i < L.count; ++i) {
+      io.out0[i] = x[i];
+      io.in1[i] = slopes[i];   // tip/tilt-only sensors' data term
+    }
     TOMO_TRY(timed(tp, kKindAnalysis, s, [&] {
       return launch_analysis(L.precision, 1, 2, L.lf, warm ? kFlagWarm : 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem_a,
                              io, s);
@@ -318,7 +321,6 @@ tomo_status tomo_plan_create(const tomo_geometry *g, void *cuda_stream, tomo_pla
   const size_t o_phi = A.take(esz * n);
   const size_t o_v = A.take(esz * H.v_total);
   const size_t o_jinv = A.take(esz * n);
-  const size_t o_ttc = A.take(esz * 2 * std::max(1, H.n_tt));
   const size_t o_jdiag = A.take(sizeof(double) * n);
   const size_t o_scal = A.take(sizeof(double) * kNumScalars);
   const size_t o_part = A.take(sizeof(double) * std::max(1, H.n_part));
@@ -371,7 +373,6 @@ tomo_status tomo_plan_create(const tomo_geometry *g, void *cuda_stream, tomo_pla
   I.tt_beg = reinterpret_cast<const int *>(base + o_ttbeg);
   I.tt_k = reinterpret_cast<const int *>(base + o_ttk);
   I.tt_w = base + o_ttw;
-  I.ttc = base + o_ttc;
   I.n_tt = H.n_tt;
   I.n_edge_wfs = H.n_edge_wfs;
   I.gather_staged = H.gather_staged;
@@ -680,6 +681,7 @@ tomo_status tomo_rhs(tomo_plan *p, const void *d_slopes, void *d_out, void *cuda
                  "forward (data)"));
   IoArgs c{};
   c.out0[0] = d_out;
+  c.in1[0] = d_slopes;
   return timed(p, kKindAnalysis, s, [&] {
     return launch_analysis(L.precision, 1, 0, L.lf, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem_a, c, s);
   }, "analysis");

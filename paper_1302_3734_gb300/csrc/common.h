@@ -87,7 +87,6 @@ struct InstDev {
   const int *tt_beg;            // entries [tt_beg[j], tt_beg[j+1]) of node j
   const int *tt_k;              // edge slot of the entry
   const void *tt_w;             // (w t_x, w t_y) of the entry (T pairs)
-  void *ttc;                    // per tip/tilt-only sensor: (e_x, e_y) (T pairs)
   int n_tt, n_edge_wfs;         // tip/tilt-only sensors; sensors with an edge slot
   // Staging of the gather tables in the analysis kernel's shared memory
   // (loaded before the dependency wait); 0 = read them from global memory.

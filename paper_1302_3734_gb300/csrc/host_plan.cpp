@@ -470,9 +470,12 @@ tomo_status build_host_plan(const tomo_geometry *geo, HostPlan *P, std::string *
     WfsDev &d = P->wfs[m];
     d.part_off = part;
     if (d.kind == kTTOnly) {
-      d.n_tiles = 1;
-      P->fwd_items.push_back({0, m, -1, 0, 0, 0, 0, 0});
-      part += 2;
+      // (edge corner, layer) pairs, one per thread of a chunk
+      const int pairs = d.n_edge * P->n_layers;
+      const int chunks = (pairs + kThreads - 1) / kThreads;
+      d.n_tiles = chunks;
+      for (int c = 0; c < chunks; ++c) P->fwd_items.push_back({0, m, -1, 0, c, 0, 0, 0});
+      part += 2 * chunks;
       continue;
     }
     const int nt = (d.nc + kFwdTile - 1) / kFwdTile;

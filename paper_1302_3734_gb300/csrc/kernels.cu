@@ -143,33 +143,45 @@ __global__ void __launch_bounds__(kThreads) k_forward(const InstDev *__restrict_
 
   if (it.a0 < 0) {
     // Tip/tilt-only sensor: the sum of its Fried slopes over the valid
-    // subapertures is <Gamma^T 1, psi>, which lives on the pupil-edge corners.
-    const T *et = static_cast<const T *>(I.edge_t) + 2 * W.edge_off;
-    const int *eidx = I.edge_idx + W.edge_off;
+    // subapertures is <Gamma^T 1, psi>, which lives on the pupil-edge corners;
+    // one (edge corner, layer) term per thread, one FP64 partial per chunk.
+    if (MODE == 2) return;   // data only: the model term is zero
+    const int pair = it.tile * blockDim.x + tid;
+    const bool on = pair < W.n_edge * L;
+    int x0 = 0, y0 = 0, x1 = 0, y1 = 0, N = 1, off = 0;
+    T fx = T(0), fy = T(0), tx = T(0), ty = T(0);
+    if (on) {
+      const int e = pair / L, l = pair - e * L;
+      const int c = I.edge_idx[W.edge_off + e];
+      const int a = c % nc, b = c / nc;
+      const T *et = static_cast<const T *>(I.edge_t) + 2 * (W.edge_off + e);
+      const T *pf = static_cast<const T *>(I.pos_f);
+      const int po = I.pos_off[it.wfs * L + l];
+      N = I.layers[l].N;
+      off = I.layers[l].off;
+      x0 = I.pos_i0[po + a];
+      y0 = I.pos_i0[po + nc + b];
+      fx = pf[po + a];
+      fy = pf[po + nc + b];
+      x1 = (x0 + 1) & (N - 1);
+      y1 = (y0 + 1) & (N - 1);
+      tx = et[0];
+      ty = et[1];
+    }
     pdl_wait();
     double ax = 0.0, ay = 0.0;
-    if (MODE != 2) {
-      for (int e = tid; e < W.n_edge; e += blockDim.x) {
-        const int c = eidx[e];
-        const T ps = trace_corner<T>(I, it.wfs, nc, phi, c % nc, c / nc);
-        ax += double(et[2 * e]) * double(ps);
-        ay += double(et[2 * e + 1]) * double(ps);
-      }
+    if (on) {
+      const T *p = phi + off;
+      const T v00 = p[y0 * N + x0], v01 = p[y0 * N + x1];
+      const T v10 = p[y1 * N + x0], v11 = p[y1 * N + x1];
+      const T ps = (T(1) - fy) * ((T(1) - fx) * v00 + fx * v01) + fy * ((T(1) - fx) * v10 + fx * v11);
+      ax = double(tx) * double(ps);
+      ay = double(ty) * double(ps);
     }
     const double2 s = block_sum2(ax, ay);
     if (tid == 0) {
-      double zx = s.x / W.S, zy = s.y / W.S;   // model mean slopes
-      if (MODE == 1) {
-        zx = double(dat[W.slope_off]) - zx;
-        zy = double(dat[W.slope_off + 1]) - zy;
-      } else if (MODE == 2) {
-        zx = double(dat[W.slope_off]);
-        zy = double(dat[W.slope_off + 1]);
-      }
-      // C^-1 = sigma^-2 I_2 on the two means; M^T spreads w/S to every slope
-      T *ttc = static_cast<T *>(I.ttc);
-      ttc[2 * W.tt_idx] = T(W.inv_sigma2 * zx / W.S);
-      ttc[2 * W.tt_idx + 1] = T(W.inv_sigma2 * zy / W.S);
+      I.part[W.part_off + 2 * it.tile] = s.x;
+      I.part[W.part_off + 2 * it.tile + 1] = s.y;
     }
     return;
   }
@@ -312,13 +324,15 @@ struct Filt {
 // CTA's low-low rows of level J (kd == J) or, on rank 0, the coarse pyramid
 // block of side C (kd < J).  Levels below cache_kc are read from global memory.
 struct CoefMap {
-  int N, C, J, kd, kc, crank;
+  int N, C, J, kd, kc, crank, lgN, lgC;
   int base[kMaxLevels + 3];
   __device__ void init(int N_, int C_, int J_, int kc_, int crank_) {
     N = N_;
     C = C_;
     J = J_;
     crank = crank_;
+    lgN = __ffs(N) - 1;
+    lgC = __ffs(C) - 1;
     kd = 0;
     while (kd < J && (N >> kd) >= 2 * C) ++kd;
     kc = kc_ < 1 ? 1 : kc_;
@@ -340,41 +354,43 @@ struct CoefMap {
     base[kd + 2] = off;
   }
   __device__ int total() const { return base[kd + 2]; }
+  // sizes of level k as log2: block side M, half H, CTA rows R, half Rh
+  __device__ int lgM(int k) const { return lgN - (k - 1); }
   __device__ int hl(int k, int jl, int x) const {
-    const int H = (N >> (k - 1)) >> 1;
-    return base[k] + jl * H + (x - H);
+    const int lh = lgM(k) - 1;
+    return base[k] + (jl << lh) + (x - (1 << lh));
   }
   __device__ int lh(int k, int jl, int x) const {
-    const int M = N >> (k - 1), H = M >> 1, Rh = (M / C) >> 1;
-    return base[k] + Rh * H + jl * M + x;
+    const int lm = lgM(k), lrh = lm - lgC - 1;
+    return base[k] + (1 << (lrh + lm - 1)) + (jl << lm) + x;
   }
-  __device__ int ll(int jl, int x) const { return base[kd + 1] + jl * ((N >> (J - 1)) >> 1) + x; }
-  __device__ int coarse(int r, int c) const { return base[kd + 1] + r * C + c; }
+  __device__ int ll(int jl, int x) const { return base[kd + 1] + (jl << (lgM(J) - 1)) + x; }
+  __device__ int coarse(int r, int c) const { return base[kd + 1] + (r << lgC) + c; }
   // pyramid position of cache slot q
   __device__ void pos(int q, int &row, int &col) const {
     if (q >= base[kd + 1]) {
       const int q2 = q - base[kd + 1];
       if (kd == J) {
-        const int M = N >> (J - 1), H = M >> 1, Rh = (M / C) >> 1;
-        row = crank * Rh + q2 / H;
-        col = q2 % H;
+        const int lh = lgM(J) - 1, lrh = lgM(J) - lgC - 1;
+        row = (crank << lrh) + (q2 >> lh);
+        col = q2 & ((1 << lh) - 1);
       } else {
-        row = q2 / C;
-        col = q2 % C;
+        row = q2 >> lgC;
+        col = q2 & (C - 1);
       }
       return;
     }
     int k = kd;
     while (base[k] > q) --k;
-    const int M = N >> (k - 1), H = M >> 1, Rh = (M / C) >> 1;
+    const int lm = lgM(k), lh = lm - 1, lrh = lm - lgC - 1;
     int q2 = q - base[k];
-    if (q2 < Rh * H) {
-      row = crank * Rh + q2 / H;
-      col = H + q2 % H;
+    if (q2 < (1 << (lrh + lh))) {
+      row = (crank << lrh) + (q2 >> lh);
+      col = (1 << lh) + (q2 & ((1 << lh) - 1));
     } else {
-      q2 -= Rh * H;
-      row = H + crank * Rh + q2 / M;
-      col = q2 % M;
+      q2 -= 1 << (lrh + lh);
+      row = (1 << lh) + (crank << lrh) + (q2 >> lm);
+      col = q2 & ((1 << lm) - 1);
     }
   }
 };
@@ -398,30 +414,44 @@ __device__ __forceinline__ void W4<float>::load(const void *base, int idx) {
   w[3] = v.w;
 }
 
-// Coefficients of the pupil-edge terms, per edge slot: (e_x, e_y) of the
-// tip/tilt-only sensors, and -sigma^-2 (mean z_x, mean z_y) of the sensors
-// with tip/tilt removal (summed here from the forward tiles' partials).
+// Coefficients of the pupil-edge terms, per edge slot, from the forward
+// kernel's FP64 partials (one warp per sensor, lanes in a fixed order):
+// * tip/tilt removal: -sigma^-2 (mean z_x, mean z_y);
+// * tip/tilt-only sensor: sigma^-2 z / S with z its two mean slopes: the
+//   model's (tt_mode 0), data minus model (1), or the data alone (2), the data
+//   read from `slopes`.
 template <typename T>
-__device__ void edge_coefficients(const InstDev &I, T *s_coef) {
-  const T *ttc = static_cast<const T *>(I.ttc);
-  for (int k = threadIdx.x; k < 2 * I.n_tt; k += blockDim.x) s_coef[k] = ttc[k];
-  // one warp per sensor with tip/tilt removal, lanes in a fixed order
+__device__ void edge_coefficients(const InstDev &I, T *s_coef, int tt_mode, const T *slopes) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   int j = 0;
   for (int m = 0; m < I.n_wfs; ++m) {
     const WfsDev &W = I.wfs[m];
-    if (W.kind != kRemoveTT) continue;
+    if (W.kind == kFull) continue;
     if ((j++ % nw) != warp) continue;
     double a = 0.0, b = 0.0;
-    for (int t = lane; t < W.n_tiles; t += 32) {
-      a += I.part[W.part_off + 2 * t];
-      b += I.part[W.part_off + 2 * t + 1];
+    if (!(W.kind == kTTOnly && tt_mode == 2)) {
+      for (int t = lane; t < W.n_tiles; t += 32) {
+        a += I.part[W.part_off + 2 * t];
+        b += I.part[W.part_off + 2 * t + 1];
+      }
     }
     a = warp_sum(a);
     b = warp_sum(b);
-    if (lane == 0) {
+    if (lane != 0) continue;
+    if (W.kind == kRemoveTT) {
       s_coef[2 * W.tt_idx] = T(-W.inv_sigma2 * (a / W.S));
       s_coef[2 * W.tt_idx + 1] = T(-W.inv_sigma2 * (b / W.S));
+    } else {
+      double zx = a / W.S, zy = b / W.S;
+      if (tt_mode == 1) {
+        zx = double(slopes[W.slope_off]) - zx;
+        zy = double(slopes[W.slope_off + 1]) - zy;
+      } else if (tt_mode == 2) {
+        zx = double(slopes[W.slope_off]);
+        zy = double(slopes[W.slope_off + 1]);
+      }
+      s_coef[2 * W.tt_idx] = T(W.inv_sigma2 * zx / W.S);
+      s_coef[2 * W.tt_idx + 1] = T(W.inv_sigma2 * zy / W.S);
     }
   }
   __syncthreads();
@@ -563,10 +593,10 @@ struct GatherStage {
 template <typename T>
 __device__ void gather_rows_staged(const InstDev &I, const GatherStage<T> &st, int N, int R0,
                                    T *A, const T *s_coef) {
-  const int nt = blockDim.x, tid = threadIdx.x, Md = I.n_dense;
+  const int nt = blockDim.x, tid = threadIdx.x, Md = I.n_dense, lgN = __ffs(N) - 1;
   const T *vv = static_cast<const T *>(I.v);
   for (int node = tid; node < R0 * N; node += nt) {
-    const int kl = node / N, i = node - kl * N;
+    const int kl = node >> lgN, i = node & (N - 1);
     T acc = T(0);
 #pragma unroll 3
     for (int md = 0; md < Md; ++md) {
@@ -656,6 +686,7 @@ __global__ void __launch_bounds__(kAnalysisThreads) k_analysis(const InstDev *__
   __shared__ InstDev sI;
   __shared__ CoefMap cm;
   __shared__ T s_coef[2 * 64];
+  __shared__ double s_dal[kMaxLevels + 1];
   pdl_trigger();
   cg::cluster_group cluster = cg::this_cluster();
   const int C = static_cast<int>(cluster.num_blocks());
@@ -671,13 +702,14 @@ __global__ void __launch_bounds__(kAnalysisThreads) k_analysis(const InstDev *__
   T *cb2 = cb + C * C;
   T *cache = reinterpret_cast<T *>(smem_raw) + transform_cache_offset(N, C);
   if (tid == 0) cm.init(N, C, J, L.cache_kc, crank);
+  if (tid <= J) s_dal[tid] = L.dalpha[tid];
   Filt<T, LF> f;
   f.load(I);
 
   Emit<T, EPI> emit;
   emit.off = L.off;
   emit.N = N;
-  emit.dalpha = L.dalpha;
+  emit.dalpha = s_dal;
   emit.precond = I.precond;
   emit.warm = (flags & kFlagWarm) ? 1 : 0;
   emit.acc0 = emit.acc1 = 0.0;
@@ -729,7 +761,11 @@ __global__ void __launch_bounds__(kAnalysisThreads) k_analysis(const InstDev *__
     const T *src = static_cast<const T *>(io.in0[it.inst]) + L.off + crank * R0 * N;
     for (int idx = tid; idx < R0 * N; idx += nt) A[idx] = src[idx];
   } else {
-    if (I.n_edge_wfs > 0) edge_coefficients<T>(I, s_coef);
+    // the tip/tilt-only sensors' measurement term: model (operator), data
+    // minus model (warm residual) or data alone (cold residual, right-hand side)
+    const int tt_mode = EPI == kEpiOp ? 0 : (EPI == kEpiResid && emit.warm ? 1 : 2);
+    if (I.n_edge_wfs > 0)
+      edge_coefficients<T>(I, s_coef, tt_mode, static_cast<const T *>(io.in1[it.inst]));
     if (staged) gather_rows_staged<T>(I, st, N, R0, A, s_coef);
     else gather_rows<T>(I, it.layer, N, R0, crank, A, s_coef);
   }
@@ -737,14 +773,14 @@ __global__ void __launch_bounds__(kAnalysisThreads) k_analysis(const InstDev *__
   auto slot_hl = [&](int k, int jl, int x) { return (use_cache && k >= cm.kc) ? cm.hl(k, jl, x) : -1; };
   auto slot_lh = [&](int k, int jl, int x) { return (use_cache && k >= cm.kc) ? cm.lh(k, jl, x) : -1; };
 
+  const int lgN = L.log2N, lgC = __ffs(C) - 1;
   int M = N, k = 1;
   for (; k <= J && M >= 2 * C; ++k, M >>= 1) {
-    const int R = M / C, H = M >> 1, Rh = R >> 1;
-    int lgR = 0;
-    while ((1 << lgR) < R) ++lgR;
+    const int lgM = lgN - (k - 1), lgH = lgM - 1, lgR = lgM - lgC;
+    const int R = M >> lgC, H = M >> 1, Rh = R >> 1;
     // row pass (x): local
     for (int idx = tid; idx < R * H; idx += nt) {
-      const int j = idx / H, i = idx - j * H;
+      const int j = idx >> lgH, i = idx & (H - 1);
       const T *row = A + j * M;
       T lo = T(0), hi = T(0);
 #pragma unroll
@@ -759,14 +795,14 @@ __global__ void __launch_bounds__(kAnalysisThreads) k_analysis(const InstDev *__
     cluster.sync();
     // halo: the LF-2 rows after ours (mod M) from the next CTAs
     for (int idx = tid; idx < (LF - 2) * M; idx += nt) {
-      const int j = idx / M, x = idx - j * M;
+      const int j = idx >> lgM, x = idx & (M - 1);
       const int r = ((crank + 1) * R + j) & (M - 1);
       B[(R + j) * M + x] = cluster.map_shared_rank(B, r >> lgR)[(r & (R - 1)) * M + x];
     }
     __syncthreads();
     // column pass (y), local
     for (int idx = tid; idx < Rh * M; idx += nt) {
-      const int il = idx / M, x = idx - il * M;
+      const int il = idx >> lgM, x = idx & (M - 1);
       const int i = crank * Rh + il;
       const T *col = B + 2 * il * M + x;
       T lo = T(0), hi = T(0);
@@ -790,7 +826,7 @@ __global__ void __launch_bounds__(kAnalysisThreads) k_analysis(const InstDev *__
     // coarse levels: the remaining low-low block (side M = C) in CTA 0
     if (crank == 0) {
       for (int idx = tid; idx < M * M; idx += nt) {
-        const int r = idx / M, c = idx - r * M;
+        const int r = idx >> lgC, c = idx & (M - 1);   // M == C here
         cb[idx] = cluster.map_shared_rank(A, r)[c];   // each CTA holds one row of side M
       }
     }
@@ -798,9 +834,9 @@ __global__ void __launch_bounds__(kAnalysisThreads) k_analysis(const InstDev *__
     if (crank == 0) {
       __syncthreads();
       for (; k <= J; ++k, M >>= 1) {
-        const int H = M >> 1;
+        const int H = M >> 1, lgMc = __ffs(M) - 1;
         for (int idx = tid; idx < M * H; idx += nt) {
-          const int j = idx / H, i = idx - j * H;
+          const int j = idx >> (lgMc - 1), i = idx & (H - 1);
           T lo = T(0), hi = T(0);
 #pragma unroll
           for (int t = 0; t < LF; ++t) {
@@ -813,7 +849,7 @@ __global__ void __launch_bounds__(kAnalysisThreads) k_analysis(const InstDev *__
         }
         __syncthreads();
         for (int idx = tid; idx < H * M; idx += nt) {
-          const int i = idx / M, x = idx - i * M;
+          const int i = idx >> lgMc, x = idx & (M - 1);
           T lo = T(0), hi = T(0);
 #pragma unroll
           for (int t = 0; t < LF; ++t) {
@@ -955,14 +991,15 @@ __global__ void __launch_bounds__(kThreads) k_synthesis(const InstDev *__restric
     if (crank == 0) {
       {
         const int HJ = (N >> (J - 1)) >> 1;
-        for (int idx = tid; idx < HJ * HJ; idx += nt) cb[idx] = cache[cm.coarse(idx / HJ, idx % HJ)];
+        const int lgHJ = __ffs(HJ) - 1;
+        for (int idx = tid; idx < HJ * HJ; idx += nt) cb[idx] = cache[cm.coarse(idx >> lgHJ, idx & (HJ - 1))];
       }
       __syncthreads();
       const T *c3 = cache + cm.coarse(0, 0);
       for (int k = J; k > kd; --k) {
-        const int M = N >> (k - 1), H = M >> 1;
+        const int M = N >> (k - 1), H = M >> 1, lgMc = __ffs(M) - 1;
         for (int idx = tid; idx < M * M; idx += nt) {
-          const int y = idx / M, x = idx - y * M;
+          const int y = idx >> lgMc, x = idx & (M - 1);
           const int p = y & 1;
           T acc = T(0);
 #pragma unroll
@@ -977,7 +1014,7 @@ __global__ void __launch_bounds__(kThreads) k_synthesis(const InstDev *__restric
         }
         __syncthreads();
         for (int idx = tid; idx < M * M; idx += nt) {
-          const int y = idx / M, j = idx - y * M;
+          const int y = idx >> lgMc, j = idx & (M - 1);
           const int q = j & 1;
           T acc = T(0);
 #pragma unroll
@@ -996,21 +1033,21 @@ __global__ void __launch_bounds__(kThreads) k_synthesis(const InstDev *__restric
     const T *c0 = cluster.map_shared_rank(cb, 0);
     for (int j = tid; j < C; j += nt) A[j] = c0[crank * C + j];
   } else {
-    const int M = N >> (J - 1), H = M >> 1, Rh = (M / C) >> 1;
-    for (int idx = tid; idx < Rh * H; idx += nt) A[idx] = cache[cm.ll(idx / H, idx % H)];
+    const int M = N >> (J - 1), H = M >> 1, Rh = (M / C) >> 1, lgH = __ffs(H) - 1;
+    for (int idx = tid; idx < Rh * H; idx += nt) A[idx] = cache[cm.ll(idx >> lgH, idx & (H - 1))];
   }
   __syncthreads();
 
+  const int lgN = L.log2N, lgC = __ffs(C) - 1;
   for (int k = kd; k >= 1; --k) {
-    const int M = N >> (k - 1), H = M >> 1, R = M / C, Rh = R >> 1;
-    int lgRh = 0;
-    while ((1 << lgRh) < Rh) ++lgRh;
+    const int lgM = lgN - (k - 1), lgRh = lgM - lgC - 1;
+    const int M = N >> (k - 1), H = M >> 1, R = M >> lgC, Rh = R >> 1;
     const bool cached = k >= cm.kc;
     T *BL = B;                      // low-y rows:  HL halo rows, then Rh own rows
     T *BH = B + (HL + Rh) * M;      // high-y rows: same layout
     // step 1: own low-y rows (LL | HL) and high-y rows (LH | HH)
     for (int idx = tid; idx < Rh * M; idx += nt) {
-      const int jl = idx / M, x = idx - jl * M;
+      const int jl = idx >> lgM, x = idx & (M - 1);
       const int i = crank * Rh + jl;
       BL[(HL + jl) * M + x] = x < H ? A[jl * H + x] : (cached ? cache[cm.hl(k, jl, x)] : coef(i, x));
       BH[(HL + jl) * M + x] = cached ? cache[cm.lh(k, jl, x)] : coef(H + i, x);
@@ -1018,7 +1055,7 @@ __global__ void __launch_bounds__(kThreads) k_synthesis(const InstDev *__restric
     cluster.sync();
     // halo: the HL rows before ours (mod H) from the previous CTAs
     for (int idx = tid; idx < HL * M; idx += nt) {
-      const int j = idx / M, x = idx - j * M;
+      const int j = idx >> lgM, x = idx & (M - 1);
       const int ii = (crank * Rh - HL + j) & (H - 1);
       const int owner = ii >> lgRh, li = ii & (Rh - 1);
       const T *oB = cluster.map_shared_rank(B, owner);
@@ -1028,7 +1065,7 @@ __global__ void __launch_bounds__(kThreads) k_synthesis(const InstDev *__restric
     __syncthreads();
     // step 2: column synthesis of own output rows (local)
     for (int idx = tid; idx < R * M; idx += nt) {
-      const int yl = idx / M, x = idx - yl * M;
+      const int yl = idx >> lgM, x = idx & (M - 1);
       const int p = yl & 1;
       const int base = ((yl - p) >> 1) + HL;
       T acc = T(0);
@@ -1040,7 +1077,7 @@ __global__ void __launch_bounds__(kThreads) k_synthesis(const InstDev *__restric
     cluster.sync();
     // step 3: row synthesis (local)
     for (int idx = tid; idx < R * M; idx += nt) {
-      const int yl = idx / M, j = idx - yl * M;
+      const int yl = idx >> lgM, j = idx & (M - 1);
       const int q = j & 1;
       const T *row = A + yl * M;
       T acc = T(0);
@@ -1080,6 +1117,35 @@ __global__ void __launch_bounds__(kThreads) k_update(const InstDev *__restrict__
   const int n = I->n;
   const int iter = flags >> kIterShift;
   pdl_wait();
+  // the vectors do not depend on alpha: their loads go out first
+  const int i0 = it.start + 4 * threadIdx.x;
+  const bool vec = sizeof(T) == 4 && i0 + 3 < n &&
+                   ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(R) |
+                     reinterpret_cast<uintptr_t>(P) | reinterpret_cast<uintptr_t>(Q) |
+                     reinterpret_cast<uintptr_t>(Jv)) & 15) == 0;
+  T xv[4], rv[4], pv[4], qv[4], jv[4];
+  if (vec) {
+    const float4 x4 = reinterpret_cast<const float4 *>(X)[i0 >> 2];
+    const float4 r4 = reinterpret_cast<const float4 *>(R)[i0 >> 2];
+    const float4 p4 = reinterpret_cast<const float4 *>(P)[i0 >> 2];
+    const float4 q4 = reinterpret_cast<const float4 *>(Q)[i0 >> 2];
+    const float4 j4 = precond ? reinterpret_cast<const float4 *>(Jv)[i0 >> 2] : make_float4(1.f, 1.f, 1.f, 1.f);
+    xv[0] = x4.x; xv[1] = x4.y; xv[2] = x4.z; xv[3] = x4.w;
+    rv[0] = r4.x; rv[1] = r4.y; rv[2] = r4.z; rv[3] = r4.w;
+    pv[0] = p4.x; pv[1] = p4.y; pv[2] = p4.z; pv[3] = p4.w;
+    qv[0] = q4.x; qv[1] = q4.y; qv[2] = q4.z; qv[3] = q4.w;
+    jv[0] = j4.x; jv[1] = j4.y; jv[2] = j4.z; jv[3] = j4.w;
+  } else {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int idx = i0 + u < n ? i0 + u : n - 1;
+      xv[u] = X[idx];
+      rv[u] = R[idx];
+      pv[u] = P[idx];
+      qv[u] = Q[idx];
+      jv[u] = precond ? Jv[idx] : T(1);
+    }
+  }
   {
     const double rz = I->scal[kRz0 + (iter & 1)];
     const double flag = I->scal[kFlag];
@@ -1095,39 +1161,26 @@ __global__ void __launch_bounds__(kThreads) k_update(const InstDev *__restrict__
   }
   const T alpha = s_alpha;
   double rz = 0.0, rr = 0.0;
-  const int i0 = it.start + 4 * threadIdx.x;
-  const bool vec = sizeof(T) == 4 && i0 + 3 < n &&
-                   ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(R) |
-                     reinterpret_cast<uintptr_t>(P) | reinterpret_cast<uintptr_t>(Q) |
-                     reinterpret_cast<uintptr_t>(Jv)) & 15) == 0;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    xv[u] += alpha * pv[u];
+    rv[u] -= alpha * qv[u];
+    const T z = precond ? jv[u] * rv[u] : rv[u];
+    if (i0 + u < n) {
+      rz += double(rv[u]) * double(z);
+      rr += double(rv[u]) * double(rv[u]);
+    }
+  }
   if (vec) {
-    const float a = float(alpha);
-    float4 x = reinterpret_cast<const float4 *>(X)[i0 / 4];
-    float4 r = reinterpret_cast<const float4 *>(R)[i0 / 4];
-    const float4 p = reinterpret_cast<const float4 *>(P)[i0 / 4];
-    const float4 q = reinterpret_cast<const float4 *>(Q)[i0 / 4];
-    float4 z;
-    x.x += a * p.x; x.y += a * p.y; x.z += a * p.z; x.w += a * p.w;
-    r.x -= a * q.x; r.y -= a * q.y; r.z -= a * q.z; r.w -= a * q.w;
-    if (precond) {
-      const float4 j = reinterpret_cast<const float4 *>(Jv)[i0 / 4];
-      z = make_float4(j.x * r.x, j.y * r.y, j.z * r.z, j.w * r.w);
-    } else {
-      z = r;
-    }
-    reinterpret_cast<float4 *>(X)[i0 / 4] = x;
-    reinterpret_cast<float4 *>(R)[i0 / 4] = r;
-    rz = double(r.x) * z.x + double(r.y) * z.y + double(r.z) * z.z + double(r.w) * z.w;
-    rr = double(r.x) * r.x + double(r.y) * r.y + double(r.z) * r.z + double(r.w) * r.w;
+    reinterpret_cast<float4 *>(X)[i0 >> 2] = make_float4(xv[0], xv[1], xv[2], xv[3]);
+    reinterpret_cast<float4 *>(R)[i0 >> 2] = make_float4(rv[0], rv[1], rv[2], rv[3]);
   } else {
-    for (int idx = i0; idx < i0 + 4 && idx < n; ++idx) {
-      X[idx] = X[idx] + alpha * P[idx];
-      const T r = R[idx] - alpha * Q[idx];
-      R[idx] = r;
-      const T z = precond ? Jv[idx] * r : r;
-      rz += double(r) * double(z);
-      rr += double(r) * double(r);
-    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (i0 + u < n) {
+        X[i0 + u] = xv[u];
+        R[i0 + u] = rv[u];
+      }
   }
   const double2 s = block_sum2(rz, rr);
   if (threadIdx.x == 0) {
