@@ -379,6 +379,7 @@ tomo_status tomo_plan_create(const tomo_geometry *g, void *cuda_stream, tomo_pla
   I.n_dense = H.n_dense;
   I.max_tt_nodes = H.max_tt_nodes;
   I.max_tt_entries = H.max_tt_entries;
+  I.max_taps = H.max_taps;
   I.edge_idx = reinterpret_cast<const int *>(base + o_eidx);
   I.edge_t = base + o_et;
   I.run_rows = reinterpret_cast<const int *>(base + o_runrows);

@@ -91,6 +91,7 @@ struct InstDev {
   // Staging of the gather tables in the analysis kernel's shared memory
   // (loaded before the dependency wait); 0 = read them from global memory.
   int gather_staged, n_dense;   // flag; sensors with a dense corner field
+  int max_taps, pad_taps;       // largest number of corners per node and axis (<= 4)
   int max_tt_nodes, max_tt_entries;  // largest per-CTA pupil-edge segment
   const int *edge_idx;          // corner index of each edge corner
   const void *edge_t;           // (t_x, t_y) of each edge corner (T, interleaved)

@@ -420,6 +420,8 @@ tomo_status build_host_plan(const tomo_geometry *geo, HostPlan *P, std::string *
   // staging of the gather tables in the analysis kernel, when it fits
   P->n_dense = 0;
   for (const auto &d : P->wfs) P->n_dense += d.kind != kTTOnly ? 1 : 0;
+  P->max_taps = 1;
+  for (unsigned char c : P->gt_cnt) P->max_taps = std::max(P->max_taps, static_cast<int>(c));
   for (const auto &sg : P->tt_seg) {
     P->max_tt_nodes = std::max(P->max_tt_nodes, sg.y - sg.x);
     P->max_tt_entries = std::max(P->max_tt_entries, P->tt_beg[sg.y] - P->tt_beg[sg.x]);

@@ -590,7 +590,7 @@ struct GatherStage {
 
 // The gather of gather_rows from the staged tables: one node per thread and
 // pass, the sensors unrolled so that their corner loads are in flight together.
-template <typename T>
+template <typename T, int KT>
 __device__ void gather_rows_staged(const InstDev &I, const GatherStage<T> &st, int N, int R0,
                                    T *A, const T *s_coef) {
   const int nt = blockDim.x, tid = threadIdx.x, Md = I.n_dense, lgN = __ffs(N) - 1;
@@ -610,12 +610,12 @@ __device__ void gather_rows_staged(const InstDev &I, const GatherStage<T> &st, i
       const int ays[4] = {ay.x, ay.y, ay.z, ay.w};
       T part = T(0);
 #pragma unroll
-      for (int ty = 0; ty < 4; ++ty) {
+      for (int ty = 0; ty < KT; ++ty) {
         if (ty < cy) {
           const T *row = vm + ays[ty] * nc;
           T sx = T(0);
 #pragma unroll
-          for (int tx = 0; tx < 4; ++tx)
+          for (int tx = 0; tx < KT; ++tx)
             if (tx < cx) sx += wx[tx] * row[axs[tx]];
           part += wy[ty] * sx;
         }
@@ -679,7 +679,7 @@ struct Emit {
 // EPI resid: r = W g - alpha D x (x = io.out0, zeroed when cold), p = z = J^-1 r;
 // partials r.z and r.r per CTA.
 template <typename T, int SRC, int EPI, int LF>
-__global__ void __launch_bounds__(kAnalysisThreads) k_analysis(const InstDev *__restrict__ insts,
+__global__ void __launch_bounds__(kAnalysisThreads, 2) k_analysis(const InstDev *__restrict__ insts,
                                                       const ClusterItem *__restrict__ items,
                                                       IoArgs io, int flags) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -766,7 +766,8 @@ __global__ void __launch_bounds__(kAnalysisThreads) k_analysis(const InstDev *__
     const int tt_mode = EPI == kEpiOp ? 0 : (EPI == kEpiResid && emit.warm ? 1 : 2);
     if (I.n_edge_wfs > 0)
       edge_coefficients<T>(I, s_coef, tt_mode, static_cast<const T *>(io.in1[it.inst]));
-    if (staged) gather_rows_staged<T>(I, st, N, R0, A, s_coef);
+    if (staged && I.max_taps <= 3) gather_rows_staged<T, 3>(I, st, N, R0, A, s_coef);
+    else if (staged) gather_rows_staged<T, 4>(I, st, N, R0, A, s_coef);
     else gather_rows<T>(I, it.layer, N, R0, crank, A, s_coef);
   }
   __syncthreads();
