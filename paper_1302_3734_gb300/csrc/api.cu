@@ -2,6 +2,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -259,7 +260,9 @@ tomo_status tomo_plan_create(const tomo_geometry *g, void *cuda_stream, tomo_pla
   tomo_plan *p = new (std::nothrow) tomo_plan();
   if (!p) return fail(TOMO_ERR_NOMEM, "host allocation failed");
   std::string err;
-  tomo_status st = build_host_plan(g, &p->hp, &err);
+  int creq = 0;
+  if (const char *env = std::getenv("TOMO_CLUSTER_SIZE")) creq = std::atoi(env);
+  tomo_status st = build_host_plan(g, &p->hp, &err, creq);
   if (st != TOMO_OK) {
     delete p;
     return fail(st, err);

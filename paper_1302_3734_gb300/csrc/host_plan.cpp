@@ -114,7 +114,8 @@ bool daubechies_filter(int p, std::vector<double> *h, std::string *err) {
   return true;
 }
 
-tomo_status build_host_plan(const tomo_geometry *geo, HostPlan *P, std::string *err) {
+tomo_status build_host_plan(const tomo_geometry *geo, HostPlan *P, std::string *err,
+                            int cluster_request) {
   char buf[256];
   if (!geo || !geo->wfs || !geo->layers || geo->n_wfs < 1 || geo->n_layers < 1) {
     *err = "geometry, its sensor and layer arrays must be non-empty";
@@ -174,8 +175,16 @@ tomo_status build_host_plan(const tomo_geometry *geo, HostPlan *P, std::string *
     Nmin = std::min(Nmin, L.N);
     Nmax = std::max(Nmax, L.N);
   }
-  // cluster size: every layer keeps >= 8 rows per CTA at level 1
+  // cluster size: every layer keeps >= 8 rows per CTA at level 1, unless the
+  // caller asks for another power of two (1..16, at most N/2)
   P->C = std::min(16, Nmin / 8);
+  if (cluster_request > 0) {
+    if (cluster_request > 16 || (cluster_request & (cluster_request - 1)) || cluster_request > Nmin / 2) {
+      *err = "cluster size must be a power of two in [1, min(16, N/2)]";
+      return TOMO_ERR_ARG;
+    }
+    P->C = cluster_request;
+  }
   {
     // shared memory of the transforms: row buffers, coarse buffers and the
     // coefficient cache of as many (coarse-first) levels as fit

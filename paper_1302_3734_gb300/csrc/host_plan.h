@@ -51,8 +51,10 @@ struct HostPlan {
   std::vector<UpdItem> upd_items;
 };
 
-// Returns TOMO_OK or an error status with *err set.
-tomo_status build_host_plan(const tomo_geometry *g, HostPlan *out, std::string *err);
+// Returns TOMO_OK or an error status with *err set.  cluster_request > 0 asks
+// for that many CTAs per layer in the transform kernels (0: the default).
+tomo_status build_host_plan(const tomo_geometry *g, HostPlan *out, std::string *err,
+                            int cluster_request = 0);
 
 // Orthonormal Daubechies low-pass filter with p vanishing moments (2p taps),
 // by spectral factorisation; exposed for tests through the plan only.
