@@ -158,6 +158,26 @@ tomo_status tomo_rhs(tomo_plan *p, const void *d_slopes, void *d_out, void *cuda
 /* The modified Jacobi diagonal J (Sec. 5.1, including alpha D): n_coeffs doubles. */
 tomo_status tomo_jacobi_diagonal(tomo_plan *p, double *d_out, void *cuda_stream);
 
+/* The modified Jacobi diagonal for regularisation weight `alpha`
+ * (diag(sum over LGS of A~^T C~^-1 A~) + alpha D, n_coeffs doubles into d_out),
+ * recomputed without allocating any device memory.  The paper has no
+ * counterpart: this is a service for callers that cannot allocate when they
+ * need the diagonal again, e.g. a real-time control thread retuning alpha,
+ * which must not take the latency of cudaMalloc, or code living inside
+ * another framework's memory pool.  The computation's scratch (basis
+ * profiles and corner fractions of the plan) lives in a fixed 4 MiB device
+ * array owned by the library; every GPU that loads the library holds it until
+ * the process exits.  A plan needing more scratch than that is rejected with
+ * TOMO_ERR_UNSUPPORTED and a message giving both sizes.  The first call on a
+ * device looks up the array's device address; make that first call before
+ * any stream capture.  Every call overwrites the whole scratch it reads (none
+ * of it must start at zero), and all calls share it: calls that overlap on the
+ * GPU (different streams, or different host threads) race and must be
+ * serialised by the caller.  The plan itself is not modified.  Enqueued on
+ * `cuda_stream`; the host tables are copied before the call returns. */
+tomo_status tomo_jacobi_diagonal_noalloc(const tomo_plan *p, double alpha, double *d_out,
+                                         void *cuda_stream);
+
 /* Sizes and launch facts of a plan. */
 tomo_status tomo_plan_get_info(const tomo_plan *p, tomo_plan_info *out);
 

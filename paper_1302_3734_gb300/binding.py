@@ -72,6 +72,7 @@ SIGNATURES = [
     ("tomo_apply_normal", _I, [_VP, _VP, _VP, _VP]),
     ("tomo_rhs", _I, [_VP, _VP, _VP, _VP]),
     ("tomo_jacobi_diagonal", _I, [_VP, _VP, _VP]),
+    ("tomo_jacobi_diagonal_noalloc", _I, [_VP, ctypes.c_double, _VP, _VP]),
     ("tomo_plan_get_info", _I, [_VP, ctypes.POINTER(PlanInfo)]),
     ("tomo_plan_device_bytes", ctypes.c_size_t, [_VP]),
     ("tomo_set_kernel_timing", _I, [_VP, _I]),
@@ -225,6 +226,12 @@ class Plan:
         import torch
         _check(load_library().tomo_jacobi_diagonal(
             self._h, self._tensor(out, self.n, "out", torch.float64), _stream(stream)))
+
+    def jacobi_diagonal_noalloc(self, out, alpha, stream=None):
+        """The Jacobi diagonal for `alpha`, computed without device allocation."""
+        import torch
+        _check(load_library().tomo_jacobi_diagonal_noalloc(
+            self._h, float(alpha), self._tensor(out, self.n, "out", torch.float64), _stream(stream)))
 
     def device_bytes(self):
         return int(load_library().tomo_plan_device_bytes(self._h))

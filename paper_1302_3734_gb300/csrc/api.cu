@@ -14,6 +14,7 @@
 #include "common.h"
 #include "host_plan.h"
 #include "launch.h"
+#include "plan_internal.h"
 
 using namespace tomo;
 
@@ -29,6 +30,14 @@ tomo_status fail(tomo_status st, const std::string &msg) {
   return st;
 }
 
+}  // namespace
+
+namespace tomo {
+tomo_status set_error(tomo_status st, const std::string &msg) { return fail(st, msg); }
+}  // namespace tomo
+
+namespace {
+
 tomo_status cuda_fail(cudaError_t e, const char *where) {
   g_err = std::string(where) + ": " + cudaGetErrorString(e);
   return TOMO_ERR_CUDA;
@@ -39,47 +48,6 @@ tomo_status cuda_fail(cudaError_t e, const char *where) {
     cudaError_t e_ = (call);                        \
     if (e_ != cudaSuccess) return cuda_fail(e_, where); \
   } while (0)
-
-enum Kind : int { kKindSynth = 0, kKindFwd = 1, kKindAnalysis = 2, kKindUpd = 3, kKindOther = 4, kNumKinds = 5 };
-
-// Everything one launch sequence needs (one plan, or a batch of plans).
-struct LaunchSet {
-  const InstDev *d_inst = nullptr;
-  int count = 0;
-  const ClusterItem *cl = nullptr;
-  int n_cl = 0, C = 0;
-  size_t smem = 0, smem_a = 0;   // synthesis / analysis dynamic shared memory
-  const FwdItem *fwd = nullptr;
-  int n_fwd = 0, max_layers = 0, lf = 0;
-  const UpdItem *upd = nullptr;
-  int n_upd = 0;
-  int precision = 0;
-};
-
-struct Timer {
-  bool on = false;
-  struct Rec { int kind; cudaEvent_t a, b; };
-  std::vector<Rec> recs;
-  std::vector<cudaEvent_t> pool;
-  cudaEvent_t get() {
-    if (!pool.empty()) {
-      cudaEvent_t e = pool.back();
-      pool.pop_back();
-      return e;
-    }
-    cudaEvent_t e = nullptr;
-    cudaEventCreate(&e);
-    return e;
-  }
-};
-
-struct GraphEntry {
-  const void *slopes;
-  void *x;
-  int iters, warm;
-  cudaGraphExec_t exec;
-  int kernels;
-};
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -102,25 +70,6 @@ cudaError_t configure_device(int dev) {
 }
 
 }  // namespace
-
-struct tomo_plan {
-  HostPlan hp;
-  int device = 0;
-  size_t esz = 4;
-  void *arena = nullptr;
-  size_t arena_bytes = 0;
-  InstDev h_inst{};
-  InstDev *d_inst = nullptr;
-  double *d_jdiag = nullptr;
-  LaunchSet ls;
-  int nc_max = 0, max_sub2 = 0;
-  cudaStream_t cap_stream = nullptr;
-  int use_graphs = 1;
-  std::vector<GraphEntry> graphs;
-  Timer timer;
-  double kind_ms[kNumKinds] = {0};
-  long long kind_n[kNumKinds] = {0};
-};
 
 namespace {
 
@@ -455,7 +404,7 @@ tomo_status tomo_plan_create(const tomo_geometry *g, void *cuda_stream, tomo_pla
     if (ce == cudaSuccess)
       ce = launch_jacobi(p->d_inst, H.n, reinterpret_cast<double *>(tb + t_prof),
                          reinterpret_cast<int *>(tb + t_poff), reinterpret_cast<double *>(tb + t_posd),
-                         p->d_jdiag, I.jinv, H.precision, p->nc_max, s);
+                         p->d_jdiag, I.jinv, H.precision, p->nc_max, -1.0, s);
     if (ce == cudaSuccess) {
       g_launches.fetch_add(1);
       ce = cudaStreamSynchronize(s);

@@ -38,6 +38,7 @@ struct LayerDev {
   int off;                      // offset of this layer in the coefficient / grid vectors
   int cache_kc;                 // transforms cache the coefficients of levels >= cache_kc
   double dalpha[kMaxLevels + 1];  // alpha * D at level k (index k = 1..J)
+  double dprior[kMaxLevels + 1];  // D at level k, without alpha
 };
 
 struct WfsDev {

@@ -168,8 +168,10 @@ tomo_status build_host_plan(const tomo_geometry *geo, HostPlan *P, std::string *
     d.log2N = ilog2(L.N);
     d.off = P->n;
     const double l0 = geo->L0 > 0.0 ? std::pow(geo->L0, -11.0 / 3.0) : 0.0;
-    for (int k = 1; k <= J; ++k)
-      d.dalpha[k] = geo->alpha * L.prior_weight * (l0 + std::pow(std::ldexp(L.dx, k), -11.0 / 3.0));
+    for (int k = 1; k <= J; ++k) {
+      d.dprior[k] = L.prior_weight * (l0 + std::pow(std::ldexp(L.dx, k), -11.0 / 3.0));
+      d.dalpha[k] = geo->alpha * d.dprior[k];
+    }
     P->layers.push_back(d);
     P->n += L.N * L.N;
     Nmin = std::min(Nmin, L.N);

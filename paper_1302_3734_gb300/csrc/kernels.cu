@@ -1246,7 +1246,8 @@ __global__ void __launch_bounds__(kThreads) k_slopes(const InstDev *__restrict__
 // One warp per coefficient; FP64 throughout.
 __global__ void k_jacobi(const InstDev *__restrict__ insts, const double *__restrict__ prof,
                          const int *__restrict__ prof_off, const double *__restrict__ pos_fd,
-                         double *__restrict__ jdiag, void *jinv, int precision, int nc_max) {
+                         double *__restrict__ jdiag, void *jinv, int precision, int nc_max,
+                         double alpha) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const InstDev &I = insts[0];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1314,10 +1315,13 @@ __global__ void k_jacobi(const InstDev *__restrict__ insts, const double *__rest
   }
   acc = warp_sum(acc);
   if (lane == 0) {
-    const double Jv = acc + L.dalpha[k];
+    // alpha < 0: the plan's own alpha D; otherwise alpha D for the given alpha
+    const double Jv = acc + (alpha < 0.0 ? L.dalpha[k] : alpha * L.dprior[k]);
     jdiag[lam] = Jv;
-    if (precision) static_cast<double *>(jinv)[lam] = 1.0 / Jv;
-    else static_cast<float *>(jinv)[lam] = float(1.0 / Jv);
+    if (jinv) {
+      if (precision) static_cast<double *>(jinv)[lam] = 1.0 / Jv;
+      else static_cast<float *>(jinv)[lam] = float(1.0 / Jv);
+    }
   }
 }
 
@@ -1493,14 +1497,14 @@ cudaError_t launch_slopes(int precision, const InstDev *insts, int n_wfs, int ma
 
 cudaError_t launch_jacobi(const InstDev *insts, int n, const double *prof, const int *prof_off,
                           const double *pos_fd, double *jdiag, void *jinv, int precision,
-                          int nc_max, cudaStream_t s) {
+                          int nc_max, double alpha, cudaStream_t s) {
   const size_t per_warp = 4 * static_cast<size_t>(nc_max + 1) * sizeof(double);
   int warps = static_cast<int>((96 * 1024) / per_warp);
   warps = warps < 1 ? 1 : (warps > 8 ? 8 : warps);
   const size_t smem = per_warp * warps;
   const int blocks = (n + warps - 1) / warps;
   k_jacobi<<<blocks, warps * 32, smem, s>>>(insts, prof, prof_off, pos_fd, jdiag, jinv, precision,
-                                           nc_max);
+                                           nc_max, alpha);
   return cudaGetLastError();
 }
 

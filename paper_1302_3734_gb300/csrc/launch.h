@@ -42,9 +42,12 @@ cudaError_t launch_update(int precision, int flags, const InstDev *insts, const 
 cudaError_t launch_slopes(int precision, const InstDev *insts, int n_wfs, int max_sub2,
                           const IoArgs &io, cudaStream_t s);
 
-// Exact modified Jacobi diagonal (single instance, plan time).
+// Exact modified Jacobi diagonal (single instance): diag(sum_LGS A~^T C~^-1 A~)
+// + alpha D into jdiag (alpha < 0: the plan's alpha), and its inverse into jinv
+// unless jinv is NULL.  prof,
+// prof_off, pos_fd: the plan's basis profiles and FP64 corner fractions.
 cudaError_t launch_jacobi(const InstDev *insts, int n, const double *prof, const int *prof_off,
                           const double *pos_fd, double *jdiag, void *jinv, int precision,
-                          int nc_max, cudaStream_t s);
+                          int nc_max, double alpha, cudaStream_t s);
 
 }  // namespace tomo

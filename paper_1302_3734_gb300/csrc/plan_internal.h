@@ -1,0 +1,78 @@
+// Internal definition of the plan object shared by the C-ABI translation units.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/tomo.h"
+#include "common.h"
+#include "host_plan.h"
+
+namespace tomo {
+
+enum Kind : int { kKindSynth = 0, kKindFwd = 1, kKindAnalysis = 2, kKindUpd = 3, kKindOther = 4, kNumKinds = 5 };
+
+// Everything one launch sequence needs (one plan, or a batch of plans).
+struct LaunchSet {
+  const InstDev *d_inst = nullptr;
+  int count = 0;
+  const ClusterItem *cl = nullptr;
+  int n_cl = 0, C = 0;
+  size_t smem = 0, smem_a = 0;   // synthesis / analysis dynamic shared memory
+  const FwdItem *fwd = nullptr;
+  int n_fwd = 0, max_layers = 0, lf = 0;
+  const UpdItem *upd = nullptr;
+  int n_upd = 0;
+  int precision = 0;
+};
+
+struct Timer {
+  bool on = false;
+  struct Rec { int kind; cudaEvent_t a, b; };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+};
+
+struct GraphEntry {
+  const void *slopes;
+  void *x;
+  int iters, warm;
+  cudaGraphExec_t exec;
+  int kernels;
+};
+
+// Record the thread-local message returned by tomo_last_error().
+tomo_status set_error(tomo_status st, const std::string &msg);
+
+}  // namespace tomo
+
+struct tomo_plan {
+  tomo::HostPlan hp;
+  int device = 0;
+  size_t esz = 4;
+  void *arena = nullptr;
+  size_t arena_bytes = 0;
+  tomo::InstDev h_inst{};
+  tomo::InstDev *d_inst = nullptr;
+  double *d_jdiag = nullptr;
+  tomo::LaunchSet ls;
+  int nc_max = 0, max_sub2 = 0;
+  cudaStream_t cap_stream = nullptr;
+  int use_graphs = 1;
+  std::vector<tomo::GraphEntry> graphs;
+  tomo::Timer timer;
+  double kind_ms[tomo::kNumKinds] = {0};
+  long long kind_n[tomo::kNumKinds] = {0};
+};
