@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--batch", type=int, default=16, help="E-ELT instances per batched solve")
+    ap.add_argument("--no-batch", action="store_true")
     return ap.parse_args()
 
 
@@ -173,6 +175,66 @@ def run_reference(args):
             "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def _time_batch(pkg, torch, plans, slopes, xs, iters, flush, steps, warmup):
+    for _ in range(warmup):
+        pkg.solve_batch(plans, slopes, xs, iters, warm=True)
+    torch.cuda.synchronize()
+    times = []
+    for k in range(steps):
+        flush.fill_(float(k))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        pkg.solve_batch(plans, slopes, xs, iters, warm=True)
+        e1.record()
+        times.append((e0, e1))
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in times]
+
+
+def bench_batched(pkg, torch, geom, slopes, flush, iters, args, peak, dev):
+    """Many instances per launch: B E-ELT systems, and the 64 uneven instances."""
+    from synth import configs, gaussian_noise
+    out = {}
+    steps = max(5, min(args.steps, 100))
+    # B E-ELT instances, each on its own frame of the stream
+    B = args.batch
+    plans = [pkg.Plan(geom) for _ in range(B)]
+    F = slopes.shape[0]
+    sl = [slopes[(3 * i) % F].clone() for i in range(B)]
+    xs = [torch.zeros(plans[0].n, dtype=torch.float32, device=dev) for _ in range(B)]
+    t = _time_batch(pkg, torch, plans, sl, xs, iters, flush, steps, 3)
+    ms = float(np.mean(t))
+    bytes_it = sum(p.info.bytes_per_iteration for p in plans)
+    out["eelt"] = {"instances": B, "solves_per_s": B * 1000.0 / ms, "ms_per_batch": ms,
+                   "p99_ms": float(np.percentile(t, 99)),
+                   "achieved_GBps_per_iteration_bytes": bytes_it * iters / (ms / 1000.0) / 1e9,
+                   "frac_of_hbm_peak": bytes_it * iters / (ms / 1000.0) / 1e9 / peak}
+    for p in plans:
+        p.close()
+    # the 64-instance uneven workload
+    geoms = configs.config2()
+    plans = [pkg.Plan(g) for g in geoms]
+    sl = []
+    for i, (g, p) in enumerate(zip(geoms, plans)):
+        sig = np.concatenate([np.full(2 if w["tt_only"] else 2 * int(w["valid"].sum()), w["sigma"])
+                              for w in g["wfs"]])
+        sl.append(torch.tensor(gaussian_noise(p.n_slopes, 1.0, 3_000_000 + i) * sig,
+                               dtype=torch.float32, device=dev))
+    xs = [torch.zeros(p.n, dtype=torch.float32, device=dev) for p in plans]
+    t = _time_batch(pkg, torch, plans, sl, xs, 10, flush, steps, 3)
+    ms = float(np.mean(t))
+    bytes_it = sum(p.info.bytes_per_iteration for p in plans)
+    out["uneven64"] = {"instances": len(plans), "solves_per_s": len(plans) * 1000.0 / ms,
+                       "ms_per_batch": ms, "p99_ms": float(np.percentile(t, 99)),
+                       "coefficients": int(sum(p.n for p in plans)),
+                       "achieved_GBps_per_iteration_bytes": bytes_it * 10 / (ms / 1000.0) / 1e9,
+                       "frac_of_hbm_peak": bytes_it * 10 / (ms / 1000.0) / 1e9 / peak}
+    for p in plans:
+        p.close()
+    return out
 
 
 def main():
@@ -316,6 +378,8 @@ def main():
         "gpu_launches": launches,
         "clocks": clk.summary(),
     }
+    if not args.no_batch:
+        line["batched"] = bench_batched(pkg, torch, geom, slopes, flush, iters, args, peak, dev)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         from oracle import Tomography
         ora = Tomography(geom)

@@ -1,4 +1,5 @@
 // C ABI of the tomography library (declared in include/tomo.h).
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -101,10 +102,12 @@ tomo_status timed(tomo_plan *p, int kind, cudaStream_t s, F fn, const char *what
 // The launch sequence of one solve (Sec. 5.1): right-hand side and initial
 // residual, then `iters` (P)CG iterations of four kernels each.
 tomo_status enqueue_solve(tomo_plan *tp, const LaunchSet &L, const void *const *slopes,
-                          void *const *x, int iters, int warm, cudaStream_t s, int *n_kernels) {
+                          void *const *x, int iters, int warm, cudaStream_t s, int *n_kernels,
+                          const int *active = nullptr) {
   int nk = 0;
   if (warm) {
     IoArgs io{};
+    io.active = active;
     for (int i = 0; i < L.count; ++i) io.in0[i] = x[i];
     TOMO_TRY(timed(tp, kKindSynth, s, [&] {
       return launch_synthesis(L.precision, 0, L.lf, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem, io, s);
@@ -113,6 +116,7 @@ tomo_status enqueue_solve(tomo_plan *tp, const LaunchSet &L, const void *const *
   }
   {
     IoArgs io{};
+    io.active = active;
     for (int i = 0; i < L.count; ++i) io.in1[i] = slopes[i];
     TOMO_TRY(timed(tp, kKindFwd, s, [&] {
       return launch_forward(L.precision, warm ? 1 : 2, L.max_layers, L.d_inst, L.fwd, L.n_fwd, io, s);
@@ -121,6 +125,7 @@ tomo_status enqueue_solve(tomo_plan *tp, const LaunchSet &L, const void *const *
   }
   {
     IoArgs io{};
+    io.active = active;
     for (int i = 0; i < L.count; ++i) {
       io.out0[i] = x[i];
       io.in1[i] = slopes[i];   // tip/tilt-only sensors' data term
@@ -133,6 +138,7 @@ tomo_status enqueue_solve(tomo_plan *tp, const LaunchSet &L, const void *const *
   }
   for (int it = 0; it < iters; ++it) {
     IoArgs none{};
+    none.active = active;
     TOMO_TRY(timed(tp, kKindSynth, s, [&] {
       return launch_synthesis(L.precision, 1, L.lf, (it == 0 ? kFlagFirst : 0) | (it << kIterShift), L.d_inst,
                               L.cl, L.n_cl, L.C, L.smem, none, s);
@@ -144,6 +150,7 @@ tomo_status enqueue_solve(tomo_plan *tp, const LaunchSet &L, const void *const *
       return launch_analysis(L.precision, 1, 1, L.lf, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem_a, none, s);
     }, "analysis"));
     IoArgs io{};
+    io.active = active;
     for (int i = 0; i < L.count; ++i) io.out0[i] = x[i];
     TOMO_TRY(timed(tp, kKindUpd, s, [&] {
       return launch_update(L.precision, it << kIterShift, L.d_inst, L.upd, L.n_upd, io, s);
@@ -190,6 +197,224 @@ tomo_status read_resnorm(tomo_plan *p, int iters, cudaStream_t s, double *out) {
   *out = std::sqrt(std::max(0.0, rr));
   if (sc[kFlag] != 0.0 || !std::isfinite(rr))
     return fail(TOMO_ERR_BREAKDOWN, "PCG breakdown: p.Ap <= 0 or not finite");
+  return TOMO_OK;
+}
+
+// ------------------------------------------------------------------ batches
+// Plans solved together: grouped by (cluster size, filter length, precision),
+// one launch per group and phase.  Built once per distinct list of plans and
+// cached; a plan's destruction drops every batch that contains it.
+struct BatchGroup {
+  LaunchSet ls;
+  std::vector<int> members;   // position in the batch of each instance slot
+  void *arena = nullptr;
+};
+
+struct BatchGraph {
+  std::vector<const void *> slopes;
+  std::vector<void *> x;
+  const int *active;
+  int iters, warm;
+  cudaGraphExec_t exec;
+  int kernels;
+};
+
+struct Batch {
+  std::vector<tomo_plan *> plans;
+  std::vector<BatchGroup> groups;
+  std::vector<BatchGraph> graphs;
+  cudaStream_t cap = nullptr;
+  int device = 0;
+};
+
+std::mutex g_batch_mu;
+std::vector<Batch *> g_batches;
+
+void free_batch(Batch *b) {
+  for (auto &g : b->graphs) cudaGraphExecDestroy(g.exec);
+  for (auto &g : b->groups) cudaFree(g.arena);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  delete b;
+}
+
+tomo_status build_batch(tomo_plan *const *plans, int count, Batch **out) {
+  Batch *b = new Batch();
+  b->plans.assign(plans, plans + count);
+  b->device = plans[0]->device;
+  for (int i = 0; i < count; ++i)
+    if (plans[i]->device != b->device) {
+      delete b;
+      return fail(TOMO_ERR_ARG, "all plans of a batch must live on the same device");
+    }
+  // group members by launch shape
+  for (int i = 0; i < count; ++i) {
+    const HostPlan &H = plans[i]->hp;
+    BatchGroup *g = nullptr;
+    for (auto &cand : b->groups) {
+      const HostPlan &H0 = plans[cand.members[0]]->hp;
+      if (H0.C == H.C && H0.Lf == H.Lf && H0.precision == H.precision &&
+          static_cast<int>(cand.members.size()) < kMaxBatch)
+        g = &cand;
+    }
+    if (!g) {
+      b->groups.emplace_back();
+      g = &b->groups.back();
+    }
+    g->members.push_back(i);
+  }
+  for (auto &g : b->groups) {
+    const int k = static_cast<int>(g.members.size());
+    std::vector<InstDev> insts;
+    std::vector<ClusterItem> cl;
+    std::vector<FwdItem> fwd;
+    std::vector<UpdItem> upd;
+    LaunchSet &L = g.ls;
+    for (int slot = 0; slot < k; ++slot) {
+      const tomo_plan *p = plans[g.members[slot]];
+      const HostPlan &H = p->hp;
+      insts.push_back(p->h_inst);
+      for (auto c : H.cl_items) cl.push_back({slot, c.layer});
+      for (auto f : H.fwd_items) {
+        f.inst = slot;
+        fwd.push_back(f);
+      }
+      for (auto u : H.upd_items) {
+        u.inst = slot;
+        upd.push_back(u);
+      }
+      L.smem = std::max(L.smem, static_cast<size_t>(H.smem_transform));
+      L.smem_a = std::max(L.smem_a, static_cast<size_t>(H.smem_analysis));
+      L.max_layers = std::max(L.max_layers, H.n_layers);
+      L.C = H.C;
+      L.lf = H.Lf;
+      L.precision = H.precision;
+    }
+    Arena A;
+    const size_t o_i = A.take(sizeof(InstDev) * insts.size());
+    const size_t o_c = A.take(sizeof(ClusterItem) * cl.size());
+    const size_t o_f = A.take(sizeof(FwdItem) * fwd.size());
+    const size_t o_u = A.take(sizeof(UpdItem) * upd.size());
+    const size_t bytes = align_up(A.size, 256);
+    std::vector<char> img(bytes, 0);
+    std::memcpy(img.data() + o_i, insts.data(), sizeof(InstDev) * insts.size());
+    std::memcpy(img.data() + o_c, cl.data(), sizeof(ClusterItem) * cl.size());
+    std::memcpy(img.data() + o_f, fwd.data(), sizeof(FwdItem) * fwd.size());
+    std::memcpy(img.data() + o_u, upd.data(), sizeof(UpdItem) * upd.size());
+    cudaError_t e = cudaMalloc(&g.arena, bytes);
+    if (e == cudaSuccess) e = cudaMemcpy(g.arena, img.data(), bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      free_batch(b);
+      return cuda_fail(e, "uploading batch tables");
+    }
+    char *base = static_cast<char *>(g.arena);
+    L.d_inst = reinterpret_cast<const InstDev *>(base + o_i);
+    L.count = k;
+    L.cl = reinterpret_cast<const ClusterItem *>(base + o_c);
+    L.n_cl = static_cast<int>(cl.size());
+    L.fwd = reinterpret_cast<const FwdItem *>(base + o_f);
+    L.n_fwd = static_cast<int>(fwd.size());
+    L.upd = reinterpret_cast<const UpdItem *>(base + o_u);
+    L.n_upd = static_cast<int>(upd.size());
+  }
+  cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    free_batch(b);
+    return cuda_fail(e, "creating the batch capture stream");
+  }
+  *out = b;
+  return TOMO_OK;
+}
+
+tomo_status get_batch(tomo_plan *const *plans, int count, Batch **out) {
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  for (Batch *b : g_batches)
+    if (static_cast<int>(b->plans.size()) == count && std::equal(plans, plans + count, b->plans.begin())) {
+      *out = b;
+      return TOMO_OK;
+    }
+  if (g_batches.size() >= 32) {
+    free_batch(g_batches.front());
+    g_batches.erase(g_batches.begin());
+  }
+  DeviceGuard dg(plans[0]->device);
+  Batch *b = nullptr;
+  TOMO_TRY(build_batch(plans, count, &b));
+  g_batches.push_back(b);
+  *out = b;
+  return TOMO_OK;
+}
+
+void drop_batches_of(const tomo_plan *p) {
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  for (size_t i = 0; i < g_batches.size();) {
+    Batch *b = g_batches[i];
+    if (std::find(b->plans.begin(), b->plans.end(), p) != b->plans.end()) {
+      free_batch(b);
+      g_batches.erase(g_batches.begin() + i);
+    } else {
+      ++i;
+    }
+  }
+}
+
+// One solve of every instance of the batch (each group in turn); `active`
+// (device, one int per batch position) lets instances sit out.
+tomo_status batch_enqueue(Batch *b, const void *const *slopes, void *const *x, const int *const *active_g,
+                          int iters, int warm, cudaStream_t s, int *n_kernels) {
+  int total = 0;
+  for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+    const BatchGroup &g = b->groups[gi];
+    std::vector<const void *> sl(g.members.size());
+    std::vector<void *> xs(g.members.size());
+    for (size_t slot = 0; slot < g.members.size(); ++slot) {
+      sl[slot] = slopes[g.members[slot]];
+      xs[slot] = x[g.members[slot]];
+    }
+    int nk = 0;
+    TOMO_TRY(enqueue_solve(nullptr, g.ls, sl.data(), xs.data(), iters, warm, s, &nk,
+                           active_g ? active_g[gi] : nullptr));
+    total += nk;
+  }
+  if (n_kernels) *n_kernels = total;
+  return TOMO_OK;
+}
+
+tomo_status batch_solve(Batch *b, const void *const *slopes, void *const *x, const int *const *active_g,
+                        int iters, int warm, cudaStream_t s) {
+  const int count = static_cast<int>(b->plans.size());
+  const int *key_active = active_g ? active_g[0] : nullptr;
+  BatchGraph *ge = nullptr;
+  for (auto &g : b->graphs)
+    if (g.iters == iters && g.warm == warm && g.active == key_active &&
+        std::equal(slopes, slopes + count, g.slopes.begin()) && std::equal(x, x + count, g.x.begin()))
+      ge = &g;
+  if (!ge) {
+    if (b->graphs.size() >= 16) {
+      cudaGraphExecDestroy(b->graphs.front().exec);
+      b->graphs.erase(b->graphs.begin());
+    }
+    cudaGraph_t graph = nullptr;
+    TOMO_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal), "begin batch capture");
+    int nk = 0;
+    const long long before = g_launches.load();
+    tomo_status st = batch_enqueue(b, slopes, x, active_g, iters, warm, b->cap, &nk);
+    g_launches.store(before);
+    cudaError_t ce = cudaStreamEndCapture(b->cap, &graph);
+    if (st != TOMO_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    if (ce != cudaSuccess) return cuda_fail(ce, "end batch capture");
+    cudaGraphExec_t exec = nullptr;
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) return cuda_fail(ce, "batch graph instantiate");
+    b->graphs.push_back({std::vector<const void *>(slopes, slopes + count),
+                         std::vector<void *>(x, x + count), key_active, iters, warm, exec, nk});
+    ge = &b->graphs.back();
+  }
+  TOMO_CUDA(cudaGraphLaunch(ge->exec, s), "batch graph launch");
+  g_launches.fetch_add(ge->kernels);
   return TOMO_OK;
 }
 
@@ -439,6 +664,7 @@ void tomo_destroy(tomo_plan *p) {
   if (!p) return;
   DeviceGuard dg(p->device);
   cudaDeviceSynchronize();
+  drop_batches_of(p);
   for (auto &g : p->graphs) cudaGraphExecDestroy(g.exec);
   for (auto &r : p->timer.recs) {
     cudaEventDestroy(r.a);
@@ -653,11 +879,18 @@ tomo_status tomo_jacobi_diagonal(tomo_plan *p, double *d_out, void *cuda_stream)
 tomo_status tomo_solve_batch(tomo_plan *const *plans, const void *const *d_slopes, void *const *d_coeffs,
                              int count, int iters, int warm, void *cuda_stream) {
   if (!plans || !d_slopes || !d_coeffs || count < 0) return fail(TOMO_ERR_ARG, "NULL array or negative count");
+  if (count == 0) return TOMO_OK;
+  if (iters < 0 || iters > 100000) return fail(TOMO_ERR_ARG, "iters out of range");
   for (int i = 0; i < count; ++i) {
-    tomo_status st = tomo_solve(plans[i], d_slopes[i], d_coeffs[i], iters, warm, cuda_stream, nullptr);
-    if (st != TOMO_OK) return st;
+    if (!plans[i] || !d_slopes[i] || !d_coeffs[i]) return fail(TOMO_ERR_ARG, "NULL plan or buffer in the batch");
+    for (int j = 0; j < i; ++j)
+      if (plans[j] == plans[i]) return fail(TOMO_ERR_ARG, "a plan appears twice in one batch");
   }
-  return TOMO_OK;
+  Batch *b = nullptr;
+  TOMO_TRY(get_batch(plans, count, &b));
+  DeviceGuard dg(b->device);
+  return batch_solve(b, d_slopes, d_coeffs, nullptr, iters, warm ? 1 : 0,
+                     static_cast<cudaStream_t>(cuda_stream));
 }
 
 }  // extern "C"

@@ -105,6 +105,7 @@ struct IoArgs {
   const void *in0[kMaxBatch];
   const void *in1[kMaxBatch];
   void *out0[kMaxBatch];
+  const int *active;            // device flags per instance slot; NULL = all active
 };
 
 #ifdef __CUDACC__

@@ -134,6 +134,7 @@ __global__ void __launch_bounds__(kThreads) k_forward(const InstDev *__restrict_
   __shared__ T s_ey[kFwdTile + 1][kFwdTile + 2];
   pdl_trigger();
   const FwdItem it = items[blockIdx.x];
+  if (io.active && !io.active[it.inst]) return;
   load_inst(&sI, insts + it.inst);
   const InstDev &I = sI;
   const WfsDev W = I.wfs[it.wfs];
@@ -692,6 +693,7 @@ __global__ void __launch_bounds__(kAnalysisThreads, 2) k_analysis(const InstDev 
   const int C = static_cast<int>(cluster.num_blocks());
   const int crank = static_cast<int>(cluster.block_rank());
   const ClusterItem it = items[blockIdx.x / C];
+  if (io.active && !io.active[it.inst]) return;   // the whole cluster leaves together
   load_inst(&sI, insts + it.inst);
   const InstDev &I = sI;
   const LayerDev &L = I.layers[it.layer];
@@ -896,6 +898,7 @@ __global__ void __launch_bounds__(kThreads) k_synthesis(const InstDev *__restric
   const int C = static_cast<int>(cluster.num_blocks());
   const int crank = static_cast<int>(cluster.block_rank());
   const ClusterItem it = items[blockIdx.x / C];
+  if (io.active && !io.active[it.inst]) return;   // the whole cluster leaves together
   load_inst(&sI, insts + it.inst);
   const InstDev &I = sI;
   const LayerDev &L = I.layers[it.layer];
@@ -1108,6 +1111,7 @@ __global__ void __launch_bounds__(kThreads) k_update(const InstDev *__restrict__
   __shared__ T s_alpha;
   pdl_trigger();
   const UpdItem it = items[blockIdx.x];
+  if (io.active && !io.active[it.inst]) return;
   const InstDev *I = insts + it.inst;
   T *X = static_cast<T *>(io.out0[it.inst]);
   T *R = static_cast<T *>(I->r);
