@@ -475,9 +475,10 @@ tomo_status tomo_plan_create(const tomo_geometry *g, void *cuda_stream, tomo_pla
   const size_t o_posi0 = A.take(sizeof(int) * H.pos_i0.size());
   const size_t o_posf = A.take(esz * H.pos_f.size());
   const size_t o_gtoff = A.take(sizeof(int) * H.gt_off.size());
-  const size_t o_gtidx = A.take(sizeof(int4) * std::max<size_t>(1, H.gt_idx.size()));
-  const size_t o_gtw = A.take(esz * std::max<size_t>(4, H.gt_w.size()));
-  const size_t o_gtcnt = A.take(std::max<size_t>(1, H.gt_cnt.size()));
+  const size_t n_rec = std::max<size_t>(1, H.gt_ro.size());
+  const size_t o_gtrec = A.take(esz * H.rec_stride * n_rec);
+  const size_t o_gtys = A.take(sizeof(int) * n_rec);
+  const size_t o_vsrun = A.take(sizeof(int4) * std::max<size_t>(1, H.vs_run.size()));
   const size_t o_ttseg = A.take(sizeof(int2) * H.tt_seg.size());
   const size_t o_ttnode = A.take(sizeof(int) * std::max<size_t>(1, H.tt_node.size()));
   const size_t o_ttbeg = A.take(sizeof(int) * H.tt_beg.size());
@@ -496,7 +497,9 @@ tomo_status tomo_plan_create(const tomo_geometry *g, void *cuda_stream, tomo_pla
   const size_t o_p = A.take(esz * n);
   const size_t o_q = A.take(esz * n);
   const size_t o_phi = A.take(esz * n);
-  const size_t o_v = A.take(esz * H.v_total);
+  // a tap window of a sensor with fewer corners than taps reads (at zero
+  // weight) up to max_taps rows and columns past its field: zero padding
+  const size_t o_v = A.take(esz * (H.v_total + 32));
   const size_t o_jinv = A.take(esz * n);
   const size_t o_jdiag = A.take(sizeof(double) * n);
   const size_t o_scal = A.take(sizeof(double) * kNumScalars);
@@ -542,9 +545,10 @@ tomo_status tomo_plan_create(const tomo_geometry *g, void *cuda_stream, tomo_pla
   I.pos_i0 = reinterpret_cast<const int *>(base + o_posi0);
   I.pos_f = base + o_posf;
   I.gt_off = reinterpret_cast<const int *>(base + o_gtoff);
-  I.gt_idx = reinterpret_cast<const int4 *>(base + o_gtidx);
-  I.gt_w = base + o_gtw;
-  I.gt_cnt = reinterpret_cast<const unsigned char *>(base + o_gtcnt);
+  I.gt_rec = base + o_gtrec;
+  I.gt_ys = reinterpret_cast<const int *>(base + o_gtys);
+  I.vs_run = reinterpret_cast<const int4 *>(base + o_vsrun);
+  I.vstage = H.vstage;
   I.tt_seg = reinterpret_cast<const int2 *>(base + o_ttseg);
   I.tt_node = reinterpret_cast<const int *>(base + o_ttnode);
   I.tt_beg = reinterpret_cast<const int *>(base + o_ttbeg);
@@ -557,6 +561,7 @@ tomo_status tomo_plan_create(const tomo_geometry *g, void *cuda_stream, tomo_pla
   I.max_tt_nodes = H.max_tt_nodes;
   I.max_tt_entries = H.max_tt_entries;
   I.max_taps = H.max_taps;
+  I.rec_stride = H.rec_stride;
   I.edge_idx = reinterpret_cast<const int *>(base + o_eidx);
   I.edge_t = base + o_et;
   I.run_rows = reinterpret_cast<const int *>(base + o_runrows);
@@ -586,11 +591,28 @@ tomo_status tomo_plan_create(const tomo_geometry *g, void *cuda_stream, tomo_pla
   };
   put_real(o_posf, H.pos_f);
   put_real(o_et, H.edge_t);
-  put_real(o_gtw, H.gt_w);
+  {
+    // tap records in the plan's precision, the window offset's int bits in slot 0
+    std::vector<char> rec(esz * H.rec_stride * n_rec, 0);
+    for (size_t r = 0; r < H.gt_ro.size(); ++r) {
+      char *dst = rec.data() + esz * H.rec_stride * r;
+      std::memcpy(dst, &H.gt_ro[r], sizeof(int));
+      for (int t = 0; t < H.max_taps; ++t) {
+        const double w = H.gt_rw[4 * r + t];
+        if (esz == 8) {
+          std::memcpy(dst + 8 * (1 + t), &w, 8);
+        } else {
+          const float wf = static_cast<float>(w);
+          std::memcpy(dst + 4 * (1 + t), &wf, 4);
+        }
+      }
+    }
+    put(o_gtrec, rec.data(), rec.size());
+  }
+  put(o_gtys, H.gt_ys.data(), sizeof(int) * H.gt_ys.size());
+  put(o_vsrun, H.vs_run.data(), sizeof(int4) * H.vs_run.size());
   put_real(o_ttw, H.tt_w);
   put(o_gtoff, H.gt_off.data(), sizeof(int) * H.gt_off.size());
-  put(o_gtidx, H.gt_idx.data(), sizeof(int4) * H.gt_idx.size());
-  put(o_gtcnt, H.gt_cnt.data(), H.gt_cnt.size());
   put(o_ttseg, H.tt_seg.data(), sizeof(int2) * H.tt_seg.size());
   put(o_ttnode, H.tt_node.data(), sizeof(int) * H.tt_node.size());
   put(o_ttbeg, H.tt_beg.data(), sizeof(int) * H.tt_beg.size());

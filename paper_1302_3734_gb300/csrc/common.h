@@ -55,6 +55,8 @@ struct WfsDev {
   int run_off;                  // offset of the per-row valid runs (n+1 row offsets)
   int tt_idx;                   // slot among the sensors with a pupil-edge correction, -1 otherwise
   double inv_sigma2;
+  double inv_S;                 // 1 / S (means of the slopes)
+  double tt_scale;              // sigma^-2 / S
 };
 
 // Everything a kernel needs to know about one instance.  Pointers to element
@@ -75,10 +77,14 @@ struct InstDev {
   const int *pos_off;           // per (m,l): offset of the x corner table (y table follows, nc)
   const int *pos_i0;            // wrapped integer node index of each corner coordinate
   const void *pos_f;            // fractional part (T)
-  const int *gt_off;            // per (m,l): offset of the node tap tables (x: N_l, then y: N_l)
-  const int4 *gt_idx;           // per node: corner indices whose bilinear taps reach it
-  const void *gt_w;             // their weights (4 T per node; 0 beyond the count)
-  const unsigned char *gt_cnt;  // number of corners per node (<= kMaxTapsNode)
+  const int *gt_off;            // per (m,l): first tap record (x: N_l records, then y: N_l)
+  // Tap records, rec_stride T each, 16-byte aligned: slot 0 holds the int
+  // offset of the window's first tap (x: corner column; y: v_off + nc * corner
+  // row; -1 when no corner reaches the node), slots 1..max_taps its weights.
+  const void *gt_rec;
+  const int *gt_ys;             // per row record: its window start in the staged v rows
+  const int4 *vs_run;           // per (layer, rank, dense sensor): v run {g0, 16-byte words, smem offset}
+  int vstage, pad_vs;           // staged v elements per analysis CTA
   // Pupil-edge corrections: a tip/tilt-only sensor's corner field is
   // e_x t_x + e_y t_y and tip/tilt removal subtracts sigma^-2 (m_x t_x + m_y t_y),
   // with t = Gamma^T 1 nonzero on the pupil edge only; both reach the layers
@@ -92,7 +98,7 @@ struct InstDev {
   // Staging of the gather tables in the analysis kernel's shared memory
   // (loaded before the dependency wait); 0 = read them from global memory.
   int gather_staged, n_dense;   // flag; sensors with a dense corner field
-  int max_taps, pad_taps;       // largest number of corners per node and axis (<= 4)
+  int max_taps, rec_stride;     // taps per window (2..4); T words per tap record (4 or 8)
   int max_tt_nodes, max_tt_entries;  // largest per-CTA pupil-edge segment
   const int *edge_idx;          // corner index of each edge corner
   const void *edge_t;           // (t_x, t_y) of each edge corner (T, interleaved)
@@ -141,12 +147,13 @@ TOMO_HD inline int transform_cache_size(int N, int C, int J, int kc) {
 }
 
 // Bytes of the staged gather tables of one analysis CTA (precision esz):
-// per dense sensor N column taps and R0 row taps (int4 corners, 4 weights, a
-// count), the sensors' (nc, v_off), and the CTA's pupil-edge segment.
+// per dense sensor N column and R0 row tap records, the corner rows of v the
+// CTA reads (vstage T elements), the sensors' nc, and the CTA's pupil-edge
+// segment.
 TOMO_HD inline long long gather_stage_bytes(int n_dense, int N, int R0, int max_nodes,
-                                            int max_entries, int esz) {
-  const long long taps = static_cast<long long>(n_dense) * (N + R0);
-  long long b = taps * 16 + taps * 4 * esz + taps * 4 + n_dense * 8;
+                                            int max_entries, int esz, int rec_stride, int vstage) {
+  const long long recs = static_cast<long long>(n_dense) * (N + R0);
+  long long b = (recs * rec_stride + vstage) * esz + n_dense * 12 + 4;
   b += static_cast<long long>(max_nodes) * 4 + (max_nodes + 1) * 4;
   b += static_cast<long long>(max_entries) * 4 + max_entries * 2 * esz;
   return (b + 64 + 15) / 16 * 16;

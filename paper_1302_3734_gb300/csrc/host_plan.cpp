@@ -7,6 +7,8 @@
 #include "host_plan.h"
 
 #include <algorithm>
+#include <array>
+#include <climits>
 #include <cmath>
 #include <complex>
 #include <cstdio>
@@ -254,6 +256,8 @@ tomo_status build_host_plan(const tomo_geometry *geo, HostPlan *P, std::string *
       return TOMO_ERR_GEOMETRY;
     }
     d.S = S;
+    d.inv_S = 1.0 / S;
+    d.tt_scale = d.inv_sigma2 / S;
     auto V = [&](int a, int b) -> int {
       return (a >= 0 && b >= 0 && a < n && b < n && valid[b * n + a]) ? 1 : 0;
     };
@@ -300,8 +304,9 @@ tomo_status build_host_plan(const tomo_geometry *geo, HostPlan *P, std::string *
 
   // ------------------------------------------------------ corner tables
   // Per (sensor, layer): each corner's wrapped node index and fraction along x
-  // and y (forward bilinear taps), and per node the <= 4 corners whose taps
-  // reach it with their weights (the transposed ray-trace as a gather).
+  // and y (forward bilinear taps), and per node and axis the window of
+  // consecutive corners whose taps reach it with their weights (the transposed
+  // ray-trace as a gather).
   P->pos_off.resize(P->n_wfs * P->n_layers);
   P->gt_off.assign(P->n_wfs * P->n_layers, -1);
   // edge slots: tip/tilt-only sensors first (their (e_x, e_y) live in ttc),
@@ -313,6 +318,8 @@ tomo_status build_host_plan(const tomo_geometry *geo, HostPlan *P, std::string *
     if (d.kind == kRemoveTT) d.tt_idx = P->n_edge_wfs++;
   struct TTEntry { int layer, node, k; double wx, wy; };
   std::vector<TTEntry> tt_entries;
+  std::vector<int> win_a0, win_n;   // per node and axis: first corner and count
+  std::vector<std::array<double, kMaxTapsNode>> win_w;
   for (int m = 0; m < P->n_wfs; ++m) {
     const tomo_wfs &W = geo->wfs[m];
     const WfsDev &d = P->wfs[m];
@@ -366,36 +373,64 @@ tomo_status build_host_plan(const tomo_geometry *geo, HostPlan *P, std::string *
         }
         if (d.kind == kTTOnly) continue;
       }
-      const int go = static_cast<int>(P->gt_cnt.size());
+      // per node the consecutive run of corners whose bilinear taps reach it
+      // (consecutive because the footprint is narrower than the grid)
+      const int go = static_cast<int>(win_a0.size());
       P->gt_off[m * P->n_layers + l] = go;
       for (int axis = 0; axis < 2; ++axis) {
-        std::vector<std::vector<std::pair<int, double>>> lists(N);
+        std::vector<int> a0(N, -1), cnt(N, 0);
+        std::vector<std::array<double, kMaxTapsNode>> w(N);
+        for (auto &x : w) x.fill(0.0);
+        auto add = [&](int i, int a, double wt) -> bool {
+          if (cnt[i] == 0) a0[i] = a;
+          else if (a != a0[i] + cnt[i]) return false;
+          if (cnt[i] == kMaxTapsNode) return false;
+          w[i][cnt[i]++] = wt;
+          return true;
+        };
         for (int a = 0; a < nc; ++a) {
           const int i0 = i0s[axis][a];
           const double f = fs[axis][a];
-          lists[i0].push_back({a, 1.0 - f});
-          if (f != 0.0) lists[(i0 + 1) % N].push_back({a, f});
-        }
-        for (int i = 0; i < N; ++i) {
-          if (lists[i].size() > static_cast<size_t>(kMaxTapsNode)) {
+          bool ok = add(i0, a, 1.0 - f);
+          if (f != 0.0) ok = ok && add((i0 + 1) % N, a, f);
+          if (!ok) {
             snprintf(buf, sizeof buf,
                      "sensor %d on layer %d: more than %d corners per node (subaperture smaller "
                      "than half a layer cell)", m, l, kMaxTapsNode);
             *err = buf;
             return TOMO_ERR_UNSUPPORTED;
           }
-          int4 ix = make_int4(0, 0, 0, 0);
-          int *ip = &ix.x;
-          for (int t = 0; t < kMaxTapsNode; ++t) {
-            const bool on = t < static_cast<int>(lists[i].size());
-            ip[t] = on ? lists[i][t].first : 0;
-            P->gt_w.push_back(on ? lists[i][t].second : 0.0);
-          }
-          P->gt_idx.push_back(ix);
-          P->gt_cnt.push_back(static_cast<unsigned char>(lists[i].size()));
+        }
+        for (int i = 0; i < N; ++i) {
+          win_a0.push_back(a0[i]);
+          win_n.push_back(cnt[i]);
+          win_w.push_back(w[i]);
+          P->max_taps = std::max(P->max_taps, cnt[i]);
         }
       }
     }
+  }
+  // records of KT taps (the widest run, at least 2), the window clamped to the
+  // sensor's corners so that its zero-weight taps read inside the sensor's field
+  {
+    const int KT = std::max(2, P->max_taps);
+    P->max_taps = KT;
+    P->rec_stride = KT <= 3 ? 4 : 8;
+    P->gt_ro.assign(win_a0.size(), -1);
+    P->gt_rw.assign(4 * win_a0.size(), 0.0);
+    for (int m = 0; m < P->n_wfs; ++m)
+      for (int l = 0; l < P->n_layers; ++l) {
+        const int go = P->gt_off[m * P->n_layers + l];
+        if (go < 0) continue;
+        const WfsDev &d = P->wfs[m];
+        const int N = P->layers[l].N, nc = d.nc;
+        for (int r = go; r < go + 2 * N; ++r) {
+          if (win_n[r] == 0) continue;
+          const int w0 = std::min(win_a0[r], std::max(0, nc - KT));
+          for (int t = 0; t < win_n[r]; ++t) P->gt_rw[4 * r + win_a0[r] - w0 + t] = win_w[r][t];
+          P->gt_ro[r] = r < go + N ? w0 : d.v_off + w0 * nc;
+        }
+      }
   }
   if (P->n_edge_wfs > 64) {
     *err = "more than 64 sensors with tip/tilt removal or tip/tilt-only measurement";
@@ -431,11 +466,54 @@ tomo_status build_host_plan(const tomo_geometry *geo, HostPlan *P, std::string *
   // staging of the gather tables in the analysis kernel, when it fits
   P->n_dense = 0;
   for (const auto &d : P->wfs) P->n_dense += d.kind != kTTOnly ? 1 : 0;
-  P->max_taps = 1;
-  for (unsigned char c : P->gt_cnt) P->max_taps = std::max(P->max_taps, static_cast<int>(c));
   for (const auto &sg : P->tt_seg) {
     P->max_tt_nodes = std::max(P->max_tt_nodes, sg.y - sg.x);
     P->max_tt_entries = std::max(P->max_tt_entries, P->tt_beg[sg.y] - P->tt_beg[sg.x]);
+  }
+  // Corner rows of v that each analysis CTA's gather reads: per (layer, rank,
+  // dense sensor) one run [g0, g0 + 16 nvec bytes) of v, 16-byte aligned,
+  // covering every tap window of the CTA's node rows (KT rows of nc corners
+  // plus KT columns of over-read when nc < KT); runs are packed in that order
+  // in shared memory, and gt_ys gives each node row's window start there.
+  {
+    const int KT = P->max_taps, vq = P->precision ? 2 : 4;   // T elements per 16 bytes
+    P->gt_ys.assign(P->gt_ro.size(), -1);
+    P->vs_run.assign(static_cast<size_t>(P->n_layers) * P->C * std::max(1, P->n_dense),
+                     make_int4(0, 0, 0, 0));
+    P->vstage = 0;
+    for (int l = 0; l < P->n_layers; ++l) {
+      const int N = P->layers[l].N, R0 = N / P->C;
+      for (int c = 0; c < P->C; ++c) {
+        int sb = 0, md = 0;
+        for (int m = 0; m < P->n_wfs; ++m) {
+          const int go = P->gt_off[m * P->n_layers + l];
+          if (go < 0) continue;
+          const WfsDev &d = P->wfs[m];
+          int lo = INT_MAX, hi = -1;
+          for (int k = c * R0; k < (c + 1) * R0; ++k) {
+            const int ro = P->gt_ro[go + N + k];
+            if (ro < 0) continue;
+            const int y0 = (ro - d.v_off) / d.nc;
+            lo = std::min(lo, y0);
+            hi = std::max(hi, y0 + KT - 1);
+          }
+          int4 run = make_int4(0, 0, sb, 0);
+          if (hi >= 0) {
+            const int g0 = (d.v_off + lo * d.nc) / vq * vq;
+            const int g1 = (d.v_off + hi * d.nc + d.nc + KT + vq - 1) / vq * vq;
+            run = make_int4(g0, (g1 - g0) / vq, sb, 0);
+            for (int k = c * R0; k < (c + 1) * R0; ++k) {
+              const int ro = P->gt_ro[go + N + k];
+              if (ro >= 0) P->gt_ys[go + N + k] = sb + ro - g0;
+            }
+            sb += g1 - g0;
+          }
+          P->vs_run[(static_cast<size_t>(l) * P->C + c) * P->n_dense + md] = run;
+          ++md;
+        }
+        P->vstage = std::max(P->vstage, sb);
+      }
+    }
   }
   {
     const long long esz = P->precision ? 8 : 4;
@@ -446,7 +524,8 @@ tomo_status build_host_plan(const tomo_geometry *geo, HostPlan *P, std::string *
       const long long tr = (transform_cache_offset(d.N, P->C) +
                             transform_cache_size(d.N, P->C, J, d.cache_kc)) * esz;
       const long long st = gather_stage_bytes(P->n_dense, d.N, d.N / P->C, P->max_tt_nodes,
-                                              P->max_tt_entries, static_cast<int>(esz));
+                                              P->max_tt_entries, static_cast<int>(esz),
+                                              P->rec_stride, P->vstage);
       fits = fits && tr + st <= budget;
       need = std::max(need, tr + st);
     }

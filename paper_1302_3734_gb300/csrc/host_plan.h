@@ -21,7 +21,8 @@ struct HostPlan {
   int n_lgs = 0;
   long long smem_transform = 0;   // dynamic shared memory of the synthesis kernel (bytes)
   long long smem_analysis = 0;    // dynamic shared memory of the gather + analysis kernel (bytes)
-  int gather_staged = 0, n_dense = 0, max_tt_nodes = 0, max_tt_entries = 0, max_taps = 0;
+  int gather_staged = 0, n_dense = 0, max_tt_nodes = 0, max_tt_entries = 0, max_taps = 0,
+      rec_stride = 0;
   std::vector<double> h, g;
   std::vector<LayerDev> layers;
   std::vector<WfsDev> wfs;
@@ -29,10 +30,16 @@ struct HostPlan {
   std::vector<unsigned char> active;
   std::vector<int> pos_off, pos_i0;
   std::vector<double> pos_f;
+  // Adjoint tap windows: per (sensor, layer) N_l column records then N_l row
+  // records; record r covers corners [gt_ro[r], gt_ro[r] + max_taps) of one
+  // axis with weights gt_rw[4r ..] (row records add the sensor's v offset and
+  // scale the corner row by nc); gt_ro = -1: no corner reaches the node.
   std::vector<int> gt_off;
-  std::vector<int4> gt_idx;
-  std::vector<double> gt_w;        // 4 per node
-  std::vector<unsigned char> gt_cnt;
+  std::vector<int> gt_ro;
+  std::vector<double> gt_rw;       // 4 per record, 0 beyond the window's taps
+  std::vector<int> gt_ys;          // row records: window start in the CTA's staged v rows
+  std::vector<int4> vs_run;        // per (layer, rank, dense sensor): {g0, nvec, smem offset, 0}
+  int vstage = 0;                  // largest staged v (T elements) of one analysis CTA
   std::vector<int2> tt_seg;        // per (layer, rank)
   std::vector<int> tt_node, tt_beg, tt_k;
   std::vector<double> tt_w;        // 2 per entry

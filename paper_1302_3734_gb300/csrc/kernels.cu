@@ -47,12 +47,57 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// Inner-product accumulator of one thread.  FP64 plans: a double.  FP32
+// plans: an unevaluated double-float sum hi + lo (about 48 significant bits)
+// on the FP32 pipes: the product of two floats enters exactly (the FMA gives
+// the rounding error of a*b) and additions use Knuth's two-sum, so the error
+// stays close to an FP64 accumulation while the FP64 pipe, a small fraction
+// of the FP32 rate on this GPU, is left to the cross-block sums.  The _rn
+// intrinsics keep the compiler from contracting the error-free steps.
+template <typename T>
+struct Acc;
+
+template <>
+struct Acc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double x) { s += x; }
+  __device__ __forceinline__ void add_prod(double a, double b) { s += a * b; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+
+template <>
+struct Acc<float> {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float t = __fadd_rn(hi, x);
+    const float bp = __fsub_rn(t, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(x, bp));
+    hi = t;
+    lo = __fadd_rn(lo, e);
+  }
+  __device__ __forceinline__ void add_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float e = __fmaf_rn(a, b, -p);
+    add(p);
+    lo = __fadd_rn(lo, e);
+  }
+  // this += o, renormalised so that |lo| <= ulp(hi) / 2
+  __device__ __forceinline__ void merge(float ohi, float olo) {
+    add(ohi);
+    lo = __fadd_rn(lo, olo);
+    const float t = __fadd_rn(hi, lo);
+    lo = __fsub_rn(lo, __fsub_rn(t, hi));
+    hi = t;
+  }
+  __device__ __forceinline__ double value() const { return double(hi) + double(lo); }
+};
+
 // Sum of (a, b) over the block; the result is returned to every thread.
-__device__ double2 block_sum2(double a, double b) {
+// Fixed order: lane trees in each warp, then the warps' sums in warp 0.
+__device__ double2 block_sum2(Acc<double> aa, Acc<double> bb) {
   __shared__ double s_red[2][32];
   __shared__ double2 s_out;
-  a = warp_sum(a);
-  b = warp_sum(b);
+  const double a = warp_sum(aa.s), b = warp_sum(bb.s);
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (lane == 0) {
     s_red[0][w] = a;
@@ -71,14 +116,59 @@ __device__ double2 block_sum2(double a, double b) {
   return s_out;
 }
 
-// Fixed-order sum of `count` partial pairs (stride 2) by the whole block.
-__device__ double2 sum_partials(const double *part, int count) {
-  double a = 0.0, b = 0.0;
-  for (int q = threadIdx.x; q < count; q += blockDim.x) {
-    a += part[2 * q];
-    b += part[2 * q + 1];
+__device__ __forceinline__ void warp_merge_down(Acc<float> &a) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h = __shfl_down_sync(0xffffffffu, a.hi, o);
+    const float l = __shfl_down_sync(0xffffffffu, a.lo, o);
+    a.merge(h, l);
   }
-  return block_sum2(a, b);
+}
+
+__device__ double2 block_sum2(Acc<float> a, Acc<float> b) {
+  __shared__ float s_red[4][32];
+  __shared__ double2 s_out;
+  warp_merge_down(a);   // lane 0 holds the warp's sum
+  warp_merge_down(b);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    s_red[0][w] = a.hi;
+    s_red[1][w] = a.lo;
+    s_red[2][w] = b.hi;
+    s_red[3][w] = b.lo;
+  }
+  __syncthreads();
+  if (w == 0) {
+    const int nw = blockDim.x >> 5;
+    Acc<float> x, y;
+    if (lane < nw) {
+      x.hi = s_red[0][lane];
+      x.lo = s_red[1][lane];
+      y.hi = s_red[2][lane];
+      y.lo = s_red[3][lane];
+    }
+    warp_merge_down(x);
+    warp_merge_down(y);
+    if (lane == 0) s_out = make_double2(x.value(), y.value());
+  }
+  __syncthreads();
+  return s_out;
+}
+
+// Fixed-order sum of `count` FP64 partial pairs (stride 2): warp 0 sums the
+// first of each pair and warp 1 the second (one of them does both in a
+// one-warp block); the result is returned to every thread.
+__device__ double2 sum_partials(const double *part, int count) {
+  __shared__ double s_sp[2];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int k = w; k < 2; k += nw) {
+    double a = 0.0;
+    for (int q = lane; q < count; q += 32) a += part[2 * q + k];
+    a = warp_sum(a);
+    if (lane == 0) s_sp[k] = a;
+  }
+  __syncthreads();
+  return make_double2(s_sp[0], s_sp[1]);
 }
 
 // Copy one instance descriptor into shared memory.
@@ -89,6 +179,16 @@ __device__ __forceinline__ void load_inst(InstDev *dst, const InstDev *src) {
   for (int i = threadIdx.x; i < nw; i += blockDim.x) d[i] = s[i];
   __syncthreads();
 }
+
+// 16-byte asynchronous global -> shared copy (cp.async, L2 only) and its
+// completion for the calling thread.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(__cvta_generic_to_global(gmem))
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // psi at corner (a, b) of sensor m: sum over layers of the bilinear
 // interpolation of phi_l at the corner's traced position (Sec. 2.1, P_m).
@@ -170,14 +270,14 @@ __global__ void __launch_bounds__(kThreads) k_forward(const InstDev *__restrict_
       ty = et[1];
     }
     pdl_wait();
-    double ax = 0.0, ay = 0.0;
+    Acc<T> ax, ay;
     if (on) {
       const T *p = phi + off;
       const T v00 = p[y0 * N + x0], v01 = p[y0 * N + x1];
       const T v10 = p[y1 * N + x0], v11 = p[y1 * N + x1];
       const T ps = (T(1) - fy) * ((T(1) - fx) * v00 + fx * v01) + fy * ((T(1) - fx) * v10 + fx * v11);
-      ax = double(tx) * double(ps);
-      ay = double(ty) * double(ps);
+      ax.add_prod(tx, ps);
+      ay.add_prod(ty, ps);
     }
     const double2 s = block_sum2(ax, ay);
     if (tid == 0) {
@@ -249,7 +349,7 @@ __global__ void __launch_bounds__(kThreads) k_forward(const InstDev *__restrict_
   }
   __syncthreads();
   // 2. weighted slopes of the subapertures the tile's corners touch
-  double sx_acc = 0.0, sy_acc = 0.0;
+  Acc<T> sx_acc, sy_acc;
   const T isg = T(W.inv_sigma2);
   for (int idx = tid; idx < (kFwdTile + 1) * (kFwdTile + 1); idx += blockDim.x) {
     const int u = idx % (kFwdTile + 1), w = idx / (kFwdTile + 1);
@@ -270,8 +370,8 @@ __global__ void __launch_bounds__(kThreads) k_forward(const InstDev *__restrict_
           sy = dat[W.slope_off + W.S + j];
         }
         if (u >= 1 && w >= 1) {   // subapertures owned by this tile
-          sx_acc += double(sx);
-          sy_acc += double(sy);
+          sx_acc.add(sx);
+          sy_acc.add(sy);
         }
         ex = isg * sx;
         ey = isg * sy;
@@ -396,25 +496,6 @@ struct CoefMap {
   }
 };
 
-template <typename T>
-struct W4 {
-  T w[4];
-  __device__ __forceinline__ void load(const void *base, int idx) {
-    const T *p = static_cast<const T *>(base) + 4 * idx;
-#pragma unroll
-    for (int t = 0; t < 4; ++t) w[t] = p[t];
-  }
-};
-
-template <>
-__device__ __forceinline__ void W4<float>::load(const void *base, int idx) {
-  const float4 v = static_cast<const float4 *>(base)[idx];
-  w[0] = v.x;
-  w[1] = v.y;
-  w[2] = v.z;
-  w[3] = v.w;
-}
-
 // Coefficients of the pupil-edge terms, per edge slot, from the forward
 // kernel's FP64 partials (one warp per sensor, lanes in a fixed order):
 // * tip/tilt removal: -sigma^-2 (mean z_x, mean z_y);
@@ -440,10 +521,10 @@ __device__ void edge_coefficients(const InstDev &I, T *s_coef, int tt_mode, cons
     b = warp_sum(b);
     if (lane != 0) continue;
     if (W.kind == kRemoveTT) {
-      s_coef[2 * W.tt_idx] = T(-W.inv_sigma2 * (a / W.S));
-      s_coef[2 * W.tt_idx + 1] = T(-W.inv_sigma2 * (b / W.S));
+      s_coef[2 * W.tt_idx] = T(-(a * W.tt_scale));
+      s_coef[2 * W.tt_idx + 1] = T(-(b * W.tt_scale));
     } else {
-      double zx = a / W.S, zy = b / W.S;
+      double zx = a * W.inv_S, zy = b * W.inv_S;
       if (tt_mode == 1) {
         zx = double(slopes[W.slope_off]) - zx;
         zy = double(slopes[W.slope_off + 1]) - zy;
@@ -451,127 +532,167 @@ __device__ void edge_coefficients(const InstDev &I, T *s_coef, int tt_mode, cons
         zx = double(slopes[W.slope_off]);
         zy = double(slopes[W.slope_off + 1]);
       }
-      s_coef[2 * W.tt_idx] = T(W.inv_sigma2 * zx / W.S);
-      s_coef[2 * W.tt_idx + 1] = T(W.inv_sigma2 * zy / W.S);
+      s_coef[2 * W.tt_idx] = T(zx * W.tt_scale);
+      s_coef[2 * W.tt_idx + 1] = T(zy * W.tt_scale);
     }
   }
   __syncthreads();
 }
 
-// g on the CTA's rows [k0, k0+R0) of layer l: the transposed ray-trace
-// sum_m P_m^T v_m as a gather.  Each node has <= 4 contributing corners per
-// axis (precomputed with their bilinear weights); the pupil-edge terms add a
-// short sparse list per CTA.
+// One adjoint tap record: the window's first tap (an int in slot 0) and its
+// KT weights, read with 16-byte vector loads.
+template <typename T, int KT>
+struct TapRec {
+  static constexpr int RS = KT <= 3 ? 4 : 8;   // T words per record
+  int off;
+  T w[KT];
+  __device__ __forceinline__ void load(const T *rec) {
+    if constexpr (sizeof(T) == 4) {
+      const float4 a = reinterpret_cast<const float4 *>(rec)[0];
+      off = __float_as_int(a.x);
+      w[0] = a.y;
+      w[1] = a.z;
+      if constexpr (KT >= 3) w[2] = a.w;
+      if constexpr (KT >= 4) w[3] = reinterpret_cast<const float4 *>(rec)[1].x;
+    } else {
+      const double2 a = reinterpret_cast<const double2 *>(rec)[0];
+      const double2 b = reinterpret_cast<const double2 *>(rec)[1];
+      off = __double2loint(a.x);
+      w[0] = a.y;
+      w[1] = b.x;
+      if constexpr (KT >= 3) w[2] = b.y;
+      if constexpr (KT >= 4) w[3] = reinterpret_cast<const double2 *>(rec)[2].x;
+    }
+  }
+};
+
+// (P^T v)(node) for one sensor: the KT x KT window of its corner field at p
+// (row stride nc) weighted by the column weights x.w and the row weights y.w.
+template <typename T, int KT, bool SHARED>
+__device__ __forceinline__ T window_sum(const T *__restrict__ p, int nc, const TapRec<T, KT> &x,
+                                        const TapRec<T, KT> &y) {
+  T v[KT][KT];
+#pragma unroll
+  for (int ty = 0; ty < KT; ++ty)
+#pragma unroll
+    for (int tx = 0; tx < KT; ++tx) v[ty][tx] = SHARED ? p[ty * nc + tx] : __ldg(p + ty * nc + tx);
+  T acc = T(0);
+#pragma unroll
+  for (int ty = 0; ty < KT; ++ty) {
+    T sx = x.w[0] * v[ty][0];
+#pragma unroll
+    for (int tx = 1; tx < KT; ++tx) sx += x.w[tx] * v[ty][tx];
+    acc += y.w[ty] * sx;
+  }
+  return acc;
+}
+
+// Pupil-edge terms of the CTA's nodes: A[node] += sum over its entries of
+// (e_x t_x + e_y t_y) w (one short list per node, edge slots in s_coef).
 template <typename T>
+__device__ __forceinline__ void gather_edges(int nn, const int *tn, const int *tb, const int *tk,
+                                             const T *tw, T *A, const T *s_coef) {
+  for (int j = threadIdx.x; j < nn; j += blockDim.x) {
+    T acc = T(0);
+    for (int e = tb[j]; e < tb[j + 1]; ++e) {
+      const int k = tk[e];
+      acc += s_coef[2 * k] * tw[2 * e] + s_coef[2 * k + 1] * tw[2 * e + 1];
+    }
+    A[tn[j]] += acc;
+  }
+}
+
+// g on the CTA's rows [k0, k0+R0) of layer l: the transposed ray-trace
+// sum_m P_m^T v_m as a gather, from the tap records in global memory (plans
+// whose records do not fit next to the transform buffers).  One node per
+// thread and pass, sensors outer so that each sensor's record bases are
+// uniform; the pupil-edge terms add a short sparse list per CTA.
+template <typename T, int KT>
 __device__ void gather_rows(const InstDev &I, int l, int N, int R0, int crank, T *A,
                             const T *s_coef) {
-  const int nt = blockDim.x, tid = threadIdx.x;
-  const int colsT = N < nt ? N : nt;
-  const int rowsT = nt / colsT;
-  const int ci = tid % colsT, rg = tid / colsT;
-  const int k0 = crank * R0;
-  for (int idx = tid; idx < R0 * N; idx += nt) A[idx] = T(0);
-  __syncthreads();
-  if (rg < rowsT) {
-    const T *vv = static_cast<const T *>(I.v);
-    for (int m = 0; m < I.n_wfs; ++m) {
-      const WfsDev &W = I.wfs[m];
-      if (W.kind == kTTOnly) continue;
-      const int nc = W.nc;
-      const int go = I.gt_off[m * I.n_layers + l];
-      const T *vm = vv + W.v_off;
-      for (int i = ci; i < N; i += colsT) {
-        const int cx = I.gt_cnt[go + i];
-        if (cx == 0) continue;
-        const int4 ax = I.gt_idx[go + i];
-        W4<T> wx;
-        wx.load(I.gt_w, go + i);
-        const int axs[4] = {ax.x, ax.y, ax.z, ax.w};
-        for (int kl = rg; kl < R0; kl += rowsT) {
-          const int k = k0 + kl;
-          const int cy = I.gt_cnt[go + N + k];
-          if (cy == 0) continue;
-          const int4 ay = I.gt_idx[go + N + k];
-          W4<T> wy;
-          wy.load(I.gt_w, go + N + k);
-          const int ays[4] = {ay.x, ay.y, ay.z, ay.w};
-          T acc = T(0);
-#pragma unroll
-          for (int ty = 0; ty < 4; ++ty) {
-            if (ty < cy) {
-              const T *row = vm + ays[ty] * nc;
-              T s = T(0);
-#pragma unroll
-              for (int tx = 0; tx < 4; ++tx)
-                if (tx < cx) s += wx.w[tx] * row[axs[tx]];
-              acc += wy.w[ty] * s;
-            }
-          }
-          A[kl * N + i] += acc;
-        }
-      }
+  constexpr int RS = TapRec<T, KT>::RS;
+  const int nt = blockDim.x, tid = threadIdx.x, lgN = __ffs(N) - 1, k0 = crank * R0;
+  const T *vv = static_cast<const T *>(I.v);
+  const T *rec = static_cast<const T *>(I.gt_rec);
+  for (int node = tid; node < R0 * N; node += nt) A[node] = T(0);
+  for (int m = 0; m < I.n_wfs; ++m) {
+    const WfsDev &W = I.wfs[m];
+    if (W.kind == kTTOnly) continue;
+    const int go = I.gt_off[m * I.n_layers + l], nc = W.nc;
+    const T *xr = rec + static_cast<size_t>(go) * RS;
+    const T *yr = rec + static_cast<size_t>(go + N + k0) * RS;
+    for (int node = tid; node < R0 * N; node += nt) {
+      TapRec<T, KT> x, y;
+      x.load(xr + (node & (N - 1)) * RS);
+      y.load(yr + (node >> lgN) * RS);
+      if (x.off >= 0 && y.off >= 0) A[node] += window_sum<T, KT, false>(vv + y.off + x.off, nc, x, y);
     }
   }
   if (I.n_edge_wfs == 0) return;
   __syncthreads();
   const int2 seg = I.tt_seg[l * I.C + crank];
-  const T *tw = static_cast<const T *>(I.tt_w);
-  for (int j = seg.x + tid; j < seg.y; j += nt) {
-    T acc = T(0);
-    for (int e = I.tt_beg[j]; e < I.tt_beg[j + 1]; ++e) {
-      const int k = I.tt_k[e];
-      acc += s_coef[2 * k] * tw[2 * e] + s_coef[2 * k + 1] * tw[2 * e + 1];
-    }
-    A[I.tt_node[j]] += acc;
-  }
+  gather_edges<T>(seg.y - seg.x, I.tt_node + seg.x, I.tt_beg + seg.x, I.tt_k,
+                  static_cast<const T *>(I.tt_w), A, s_coef);
 }
 
 // Shared-memory copy of the gather tables of one analysis CTA (layer l, rows
-// [k0, k0+R0)): per dense sensor the corner taps of every column and of the
-// CTA's rows, and the CTA's pupil-edge segment.  Filled before the dependency
-// wait (the tables are constant), so the copy overlaps the previous kernel.
+// [k0, k0+R0)): per dense sensor the tap records of every column and of the
+// CTA's rows (a row record's offset rewritten to its window start in the
+// staged v rows), the sensors' nc, and the CTA's pupil-edge segment, filled
+// before the dependency wait (the tables are constant) so that the copy
+// overlaps the previous kernel; after the wait, the corner rows of v that the
+// CTA reads (one aligned run per sensor, packed).
 template <typename T>
 struct GatherStage {
-  int4 *xi, *yi;
-  T *xw, *yw, *tw;
-  int *xc, *yc, *mnc, *mvo, *tn, *tb, *tk;
+  T *xr, *yr, *vs, *tw;
+  int *mnc, *vpre, *vsrc, *tn, *tb, *tk;
   int nn;
 
-  __device__ void carve(unsigned char *base, int Md, int N, int R0, int max_nodes, int max_entries) {
-    xi = reinterpret_cast<int4 *>(base);
-    yi = xi + Md * N;
-    xw = reinterpret_cast<T *>(yi + Md * R0);
-    yw = xw + 4 * Md * N;
-    tw = yw + 4 * Md * R0;
-    xc = reinterpret_cast<int *>(tw + 2 * max_entries);
-    yc = xc + Md * N;
-    mnc = yc + Md * R0;
-    mvo = mnc + Md;
-    tn = mvo + Md;
+  __device__ void carve(unsigned char *base, int Md, int N, int R0, int RS, int vstage,
+                        int max_nodes, int max_entries) {
+    xr = reinterpret_cast<T *>(base);
+    yr = xr + Md * N * RS;
+    vs = yr + Md * R0 * RS;
+    tw = vs + vstage;
+    mnc = reinterpret_cast<int *>(tw + 2 * max_entries);
+    vpre = mnc + Md;
+    vsrc = vpre + Md + 1;
+    tn = vsrc + Md;
     tb = tn + max_nodes;
     tk = tb + max_nodes + 1;
   }
 
   __device__ void fill(const InstDev &I, int l, int N, int R0, int crank) {
-    const int nt = blockDim.x, tid = threadIdx.x, k0 = crank * R0;
-    const T *gw = static_cast<const T *>(I.gt_w);
+    const int nt = blockDim.x, tid = threadIdx.x, k0 = crank * R0, RS = I.rec_stride;
+    const int cpr = RS * static_cast<int>(sizeof(T)) / 16;       // 16-byte words per record
+    const int vx = N * cpr, vy = R0 * cpr;
+    const T *rec = static_cast<const T *>(I.gt_rec);
+    const int4 *runs = I.vs_run + (l * I.C + crank) * I.n_dense;
     int md = 0;
     for (int m = 0; m < I.n_wfs; ++m) {
       const WfsDev &W = I.wfs[m];
       if (W.kind == kTTOnly) continue;
       const int go = I.gt_off[m * I.n_layers + l];
       if (tid == 0) {
+        const int4 r = runs[md];
         mnc[md] = W.nc;
-        mvo[md] = W.v_off;
+        vpre[md] = r.z * static_cast<int>(sizeof(T)) / 16;
+        vsrc[md] = r.x * static_cast<int>(sizeof(T)) / 16;
+        vpre[md + 1] = vpre[md] + r.y;
       }
-      for (int j = tid; j < N + R0; j += nt) {
-        const int src = j < N ? go + j : go + N + k0 + (j - N);
-        const int dst = j < N ? md * N + j : md * R0 + (j - N);
-        (j < N ? xi : yi)[dst] = I.gt_idx[src];
-        (j < N ? xc : yc)[dst] = I.gt_cnt[src];
-        T *w = (j < N ? xw : yw) + 4 * dst;
-#pragma unroll
-        for (int t = 0; t < 4; ++t) w[t] = gw[4 * src + t];
+      const uint4 *sx = reinterpret_cast<const uint4 *>(rec + static_cast<size_t>(go) * RS);
+      const uint4 *sy = reinterpret_cast<const uint4 *>(rec + static_cast<size_t>(go + N + k0) * RS);
+      uint4 *dx = reinterpret_cast<uint4 *>(xr + md * N * RS);
+      uint4 *dy = reinterpret_cast<uint4 *>(yr + md * R0 * RS);
+      for (int j = tid; j < vx + vy; j += nt) {
+        if (j < vx) {
+          dx[j] = sx[j];
+        } else {
+          const int q = j - vx;
+          uint4 w = sy[q];
+          if (q % cpr == 0) w.x = static_cast<unsigned>(I.gt_ys[go + N + k0 + q / cpr]);
+          dy[q] = w;
+        }
       }
       ++md;
     }
@@ -587,54 +708,45 @@ struct GatherStage {
       tw[2 * e + 1] = ttw[2 * (e0 + e) + 1];
     }
   }
+
+  // Starts the asynchronous copy of the CTA's corner rows of v (written by
+  // the previous kernel) into shared memory; cp_async_wait_all() and a
+  // barrier complete it.  Needs fill() and a barrier first.
+  __device__ void load_v_async(const InstDev &I) const {
+    const int nt = blockDim.x, Md = I.n_dense, total = vpre[Md];
+    const uint4 *src = static_cast<const uint4 *>(I.v);
+    uint4 *dst = reinterpret_cast<uint4 *>(vs);
+    int md = 0;
+    for (int j = threadIdx.x; j < total; j += nt) {
+      while (md + 1 < Md && vpre[md + 1] <= j) ++md;
+      cp_async16(dst + j, src + vsrc[md] + j - vpre[md]);
+    }
+    cp_async_commit();
+  }
 };
 
-// The gather of gather_rows from the staged tables: one node per thread and
-// pass, the sensors unrolled so that their corner loads are in flight together.
+// The gather of gather_rows from the staged records and v rows: one node per
+// thread and pass, sensors inner with the sum in a register.
 template <typename T, int KT>
 __device__ void gather_rows_staged(const InstDev &I, const GatherStage<T> &st, int N, int R0,
                                    T *A, const T *s_coef) {
+  constexpr int RS = TapRec<T, KT>::RS;
   const int nt = blockDim.x, tid = threadIdx.x, Md = I.n_dense, lgN = __ffs(N) - 1;
-  const T *vv = static_cast<const T *>(I.v);
   for (int node = tid; node < R0 * N; node += nt) {
-    const int kl = node >> lgN, i = node & (N - 1);
+    const T *xr = st.xr + (node & (N - 1)) * RS;
+    const T *yr = st.yr + (node >> lgN) * RS;
     T acc = T(0);
-#pragma unroll 3
     for (int md = 0; md < Md; ++md) {
-      const int cx = st.xc[md * N + i], cy = st.yc[md * R0 + kl];
-      const int4 ax = st.xi[md * N + i], ay = st.yi[md * R0 + kl];
-      const T *wx = st.xw + 4 * (md * N + i);
-      const T *wy = st.yw + 4 * (md * R0 + kl);
-      const T *vm = vv + st.mvo[md];
-      const int nc = st.mnc[md];
-      const int axs[4] = {ax.x, ax.y, ax.z, ax.w};
-      const int ays[4] = {ay.x, ay.y, ay.z, ay.w};
-      T part = T(0);
-#pragma unroll
-      for (int ty = 0; ty < KT; ++ty) {
-        if (ty < cy) {
-          const T *row = vm + ays[ty] * nc;
-          T sx = T(0);
-#pragma unroll
-          for (int tx = 0; tx < KT; ++tx)
-            if (tx < cx) sx += wx[tx] * row[axs[tx]];
-          part += wy[ty] * sx;
-        }
-      }
-      acc += part;
+      TapRec<T, KT> x, y;
+      x.load(xr + md * N * RS);
+      y.load(yr + md * R0 * RS);
+      if (x.off >= 0 && y.off >= 0) acc += window_sum<T, KT, true>(st.vs + y.off + x.off, st.mnc[md], x, y);
     }
     A[node] = acc;
   }
   if (I.n_edge_wfs == 0) return;
   __syncthreads();
-  for (int j = tid; j < st.nn; j += nt) {
-    T acc = T(0);
-    for (int e = st.tb[j]; e < st.tb[j + 1]; ++e) {
-      const int k = st.tk[e];
-      acc += s_coef[2 * k] * st.tw[2 * e] + s_coef[2 * k + 1] * st.tw[2 * e + 1];
-    }
-    A[st.tn[j]] += acc;
-  }
+  gather_edges<T>(st.nn, st.tn, st.tb, st.tk, st.tw, A, s_coef);
 }
 
 // Epilogue of the analysis for one output coefficient.
@@ -650,7 +762,7 @@ struct Emit {
   const T *cache;
   const double *dalpha;
   int off, N, precond, warm;
-  double acc0, acc1;
+  Acc<T> acc0, acc1;
   __device__ __forceinline__ void operator()(int row, int col, int level, T w, int slot) {
     const int idx = off + row * N + col;
     if (EPI == kEpiPlain) {
@@ -659,7 +771,7 @@ struct Emit {
       const T pv = slot >= 0 ? cache[slot] : P[idx];
       const T q = w + T(dalpha[level]) * pv;
       Q[idx] = q;
-      acc0 += double(pv) * double(q);
+      acc0.add_prod(pv, q);
     } else {
       T r = w;
       if (warm) r -= T(dalpha[level]) * (slot >= 0 ? cache[slot] : X[idx]);
@@ -667,8 +779,8 @@ struct Emit {
       const T z = precond ? jinv[idx] * r : r;
       R[idx] = r;
       Pn[idx] = z;
-      acc0 += double(r) * double(z);
-      acc1 += double(r) * double(r);
+      acc0.add_prod(r, z);
+      acc1.add_prod(r, r);
     }
   }
 };
@@ -714,7 +826,6 @@ __global__ void __launch_bounds__(kAnalysisThreads, 2) k_analysis(const InstDev 
   emit.dalpha = s_dal;
   emit.precond = I.precond;
   emit.warm = (flags & kFlagWarm) ? 1 : 0;
-  emit.acc0 = emit.acc1 = 0.0;
   emit.jinv = static_cast<const T *>(I.jinv);
   emit.cache = cache;
   emit.out = static_cast<T *>(io.out0[it.inst]);
@@ -728,7 +839,7 @@ __global__ void __launch_bounds__(kAnalysisThreads, 2) k_analysis(const InstDev 
   if (staged) {
     const int off = transform_cache_offset(N, C) + transform_cache_size(N, C, J, L.cache_kc);
     unsigned char *sb = smem_raw + ((static_cast<size_t>(off) * sizeof(T) + 15) & ~size_t(15));
-    st.carve(sb, I.n_dense, N, R0, I.max_tt_nodes, I.max_tt_entries);
+    st.carve(sb, I.n_dense, N, R0, I.rec_stride, I.vstage, I.max_tt_nodes, I.max_tt_entries);
     st.fill(I, it.layer, N, R0, crank);
   }
   __syncthreads();
@@ -736,8 +847,10 @@ __global__ void __launch_bounds__(kAnalysisThreads, 2) k_analysis(const InstDev 
   // a new solve starts from the residual: clear the breakdown flag
   if (EPI == kEpiResid && it.layer == 0 && crank == 0 && tid == 0) I.scal[kFlag] = 0.0;
 
-  // epilogue inputs (p, or x for a warm residual) for every owned coefficient,
-  // eight loads in flight per thread
+  // the gather's corner rows of v go out first, then the epilogue inputs (p,
+  // or x for a warm residual) of every owned coefficient, eight loads in
+  // flight per thread
+  if (staged) st.load_v_async(I);
   const bool use_cache = (EPI == kEpiOp) || (EPI == kEpiResid && emit.warm);
   if (use_cache) {
     const T *srcv = EPI == kEpiOp ? emit.P : emit.X;
@@ -768,9 +881,17 @@ __global__ void __launch_bounds__(kAnalysisThreads, 2) k_analysis(const InstDev 
     const int tt_mode = EPI == kEpiOp ? 0 : (EPI == kEpiResid && emit.warm ? 1 : 2);
     if (I.n_edge_wfs > 0)
       edge_coefficients<T>(I, s_coef, tt_mode, static_cast<const T *>(io.in1[it.inst]));
-    if (staged && I.max_taps <= 3) gather_rows_staged<T, 3>(I, st, N, R0, A, s_coef);
-    else if (staged) gather_rows_staged<T, 4>(I, st, N, R0, A, s_coef);
-    else gather_rows<T>(I, it.layer, N, R0, crank, A, s_coef);
+    if (staged) {
+      cp_async_wait_all();
+      __syncthreads();
+      if (I.max_taps <= 2) gather_rows_staged<T, 2>(I, st, N, R0, A, s_coef);
+      else if (I.max_taps == 3) gather_rows_staged<T, 3>(I, st, N, R0, A, s_coef);
+      else gather_rows_staged<T, 4>(I, st, N, R0, A, s_coef);
+    } else {
+      if (I.max_taps <= 2) gather_rows<T, 2>(I, it.layer, N, R0, crank, A, s_coef);
+      else if (I.max_taps == 3) gather_rows<T, 3>(I, it.layer, N, R0, crank, A, s_coef);
+      else gather_rows<T, 4>(I, it.layer, N, R0, crank, A, s_coef);
+    }
   }
   __syncthreads();
   auto slot_hl = [&](int k, int jl, int x) { return (use_cache && k >= cm.kc) ? cm.hl(k, jl, x) : -1; };
@@ -1165,15 +1286,15 @@ __global__ void __launch_bounds__(kThreads) k_update(const InstDev *__restrict__
     __syncthreads();
   }
   const T alpha = s_alpha;
-  double rz = 0.0, rr = 0.0;
+  Acc<T> rz, rr;
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
     xv[u] += alpha * pv[u];
     rv[u] -= alpha * qv[u];
     const T z = precond ? jv[u] * rv[u] : rv[u];
     if (i0 + u < n) {
-      rz += double(rv[u]) * double(z);
-      rr += double(rv[u]) * double(rv[u]);
+      rz.add_prod(rv[u], z);
+      rr.add_prod(rv[u], rv[u]);
     }
   }
   if (vec) {
@@ -1212,12 +1333,12 @@ __global__ void __launch_bounds__(kThreads) k_slopes(const InstDev *__restrict__
     if (blockIdx.x != 0) return;
     const T *et = static_cast<const T *>(I.edge_t) + 2 * W.edge_off;
     const int *eidx = I.edge_idx + W.edge_off;
-    double ax = 0.0, ay = 0.0;
+    Acc<double> ax, ay;
     for (int e = threadIdx.x; e < W.n_edge; e += blockDim.x) {
       const int c = eidx[e];
       const T ps = trace_corner<T>(I, m, nc, phi, c % nc, c / nc);
-      ax += double(et[2 * e]) * double(ps);
-      ay += double(et[2 * e + 1]) * double(ps);
+      ax.add_prod(double(et[2 * e]), double(ps));
+      ay.add_prod(double(et[2 * e + 1]), double(ps));
     }
     const double2 s = block_sum2(ax, ay);
     if (threadIdx.x == 0) {
