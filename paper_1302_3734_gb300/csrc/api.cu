@@ -479,6 +479,8 @@ tomo_status tomo_plan_create(const tomo_geometry *g, void *cuda_stream, tomo_pla
   const size_t o_gtrec = A.take(esz * H.rec_stride * n_rec);
   const size_t o_gtys = A.take(sizeof(int) * n_rec);
   const size_t o_vsrun = A.take(sizeof(int4) * std::max<size_t>(1, H.vs_run.size()));
+  const size_t o_stage = A.take(std::max<size_t>(16, H.stage_img.size()));
+  const size_t o_eslot = A.take(sizeof(EdgeSlot) * H.edge_slots.size());
   const size_t o_ttseg = A.take(sizeof(int2) * H.tt_seg.size());
   const size_t o_ttnode = A.take(sizeof(int) * std::max<size_t>(1, H.tt_node.size()));
   const size_t o_ttbeg = A.take(sizeof(int) * H.tt_beg.size());
@@ -549,6 +551,9 @@ tomo_status tomo_plan_create(const tomo_geometry *g, void *cuda_stream, tomo_pla
   I.gt_ys = reinterpret_cast<const int *>(base + o_gtys);
   I.vs_run = reinterpret_cast<const int4 *>(base + o_vsrun);
   I.vstage = H.vstage;
+  I.stage_img = base + o_stage;
+  I.edge_slots = reinterpret_cast<const EdgeSlot *>(base + o_eslot);
+  I.img_stride = H.img_stride;
   I.tt_seg = reinterpret_cast<const int2 *>(base + o_ttseg);
   I.tt_node = reinterpret_cast<const int *>(base + o_ttnode);
   I.tt_beg = reinterpret_cast<const int *>(base + o_ttbeg);
@@ -611,6 +616,8 @@ tomo_status tomo_plan_create(const tomo_geometry *g, void *cuda_stream, tomo_pla
   }
   put(o_gtys, H.gt_ys.data(), sizeof(int) * H.gt_ys.size());
   put(o_vsrun, H.vs_run.data(), sizeof(int4) * H.vs_run.size());
+  put(o_stage, H.stage_img.data(), H.stage_img.size());
+  put(o_eslot, H.edge_slots.data(), sizeof(EdgeSlot) * H.edge_slots.size());
   put_real(o_ttw, H.tt_w);
   put(o_gtoff, H.gt_off.data(), sizeof(int) * H.gt_off.size());
   put(o_ttseg, H.tt_seg.data(), sizeof(int2) * H.tt_seg.size());

@@ -59,6 +59,13 @@ struct WfsDev {
   double tt_scale;              // sigma^-2 / S
 };
 
+// One sensor with a pupil-edge term (edge slot k = its tt_idx): where its
+// forward partials are and how they scale into the edge coefficients.
+struct EdgeSlot {
+  int part_off, n_tiles, kind, slope_off;
+  double inv_S, tt_scale;
+};
+
 // Everything a kernel needs to know about one instance.  Pointers to element
 // type T arrays are void* (T = float or double by plan precision).
 struct InstDev {
@@ -85,6 +92,8 @@ struct InstDev {
   const int *gt_ys;             // per row record: its window start in the staged v rows
   const int4 *vs_run;           // per (layer, rank, dense sensor): v run {g0, 16-byte words, smem offset}
   int vstage, pad_vs;           // staged v elements per analysis CTA
+  const void *stage_img;        // per (layer, rank): the CTA's stage image (img_stride bytes apart)
+  long long img_stride;
   // Pupil-edge corrections: a tip/tilt-only sensor's corner field is
   // e_x t_x + e_y t_y and tip/tilt removal subtracts sigma^-2 (m_x t_x + m_y t_y),
   // with t = Gamma^T 1 nonzero on the pupil edge only; both reach the layers
@@ -95,6 +104,7 @@ struct InstDev {
   const int *tt_k;              // edge slot of the entry
   const void *tt_w;             // (w t_x, w t_y) of the entry (T pairs)
   int n_tt, n_edge_wfs;         // tip/tilt-only sensors; sensors with an edge slot
+  const EdgeSlot *edge_slots;   // per edge slot (n_edge_wfs)
   // Staging of the gather tables in the analysis kernel's shared memory
   // (loaded before the dependency wait); 0 = read them from global memory.
   int gather_staged, n_dense;   // flag; sensors with a dense corner field
@@ -146,17 +156,32 @@ TOMO_HD inline int transform_cache_size(int N, int C, int J, int kc) {
   return total;
 }
 
-// Bytes of the staged gather tables of one analysis CTA (precision esz):
-// per dense sensor N column and R0 row tap records, the corner rows of v the
-// CTA reads (vstage T elements), the sensors' nc, and the CTA's pupil-edge
-// segment.
-TOMO_HD inline long long gather_stage_bytes(int n_dense, int N, int R0, int max_nodes,
-                                            int max_entries, int esz, int rec_stride, int vstage) {
-  const long long recs = static_cast<long long>(n_dense) * (N + R0);
-  long long b = (recs * rec_stride + vstage) * esz + n_dense * 12 + 4;
-  b += static_cast<long long>(max_nodes) * 4 + (max_nodes + 1) * 4;
-  b += static_cast<long long>(max_entries) * 4 + max_entries * 2 * esz;
-  return (b + 64 + 15) / 16 * 16;
+// Shared-memory layout of the staged gather tables of one analysis CTA
+// (bytes from the stage base, 16-byte aligned): an image copied verbatim from
+// the plan (per dense sensor N column and R0 row tap records, the latter with
+// their window start in the staged v rows; the CTA's pupil-edge weights; the
+// sensors' nc; the v run prefix and sources; the pupil-edge nodes, entry
+// starts and slots; the node count), then the corner rows of v the CTA reads.
+struct StageLayout {
+  int xr, yr, tw, mnc, vpre, vsrc, tn, tb, tk, nn, image, vs, total;
+};
+TOMO_HD inline StageLayout stage_layout(int n_dense, int N, int R0, int rec_stride, int esz,
+                                        int max_nodes, int max_entries, int vstage) {
+  StageLayout L;
+  L.xr = 0;
+  L.yr = L.xr + n_dense * N * rec_stride * esz;
+  L.tw = L.yr + n_dense * R0 * rec_stride * esz;
+  L.mnc = (L.tw + 2 * max_entries * esz + 3) / 4 * 4;
+  L.vpre = L.mnc + 4 * n_dense;
+  L.vsrc = L.vpre + 4 * (n_dense + 1);
+  L.tn = L.vsrc + 4 * n_dense;
+  L.tb = L.tn + 4 * max_nodes;
+  L.tk = L.tb + 4 * (max_nodes + 1);
+  L.nn = L.tk + 4 * max_entries;
+  L.image = (L.nn + 4 + 15) / 16 * 16;
+  L.vs = L.image;
+  L.total = L.vs + vstage * esz;
+  return L;
 }
 
 // Work items.

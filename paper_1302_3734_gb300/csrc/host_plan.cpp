@@ -12,6 +12,7 @@
 #include <cmath>
 #include <complex>
 #include <cstdio>
+#include <cstring>
 
 namespace tomo {
 
@@ -516,21 +517,81 @@ tomo_status build_host_plan(const tomo_geometry *geo, HostPlan *P, std::string *
     }
   }
   {
-    const long long esz = P->precision ? 8 : 4;
+    const int esz = P->precision ? 8 : 4;
     const long long budget = 220LL * 1024 - 4096;
     bool fits = true;
     long long need = 0;
     for (const auto &d : P->layers) {
       const long long tr = (transform_cache_offset(d.N, P->C) +
-                            transform_cache_size(d.N, P->C, J, d.cache_kc)) * esz;
-      const long long st = gather_stage_bytes(P->n_dense, d.N, d.N / P->C, P->max_tt_nodes,
-                                              P->max_tt_entries, static_cast<int>(esz),
-                                              P->rec_stride, P->vstage);
-      fits = fits && tr + st <= budget;
-      need = std::max(need, tr + st);
+                            transform_cache_size(d.N, P->C, J, d.cache_kc)) * static_cast<long long>(esz);
+      const StageLayout sl = stage_layout(P->n_dense, d.N, d.N / P->C, P->rec_stride, esz,
+                                          P->max_tt_nodes, P->max_tt_entries, P->vstage);
+      const long long st = (tr + 15) / 16 * 16 + sl.total;
+      fits = fits && st <= budget;
+      need = std::max(need, st);
     }
     P->gather_staged = fits ? 1 : 0;
     P->smem_analysis = fits ? need : P->smem_transform;
+  }
+  // the stage images, one per analysis CTA
+  if (P->gather_staged) {
+    const int esz = P->precision ? 8 : 4, RS = P->rec_stride;
+    long long stride = 16;
+    for (const auto &d : P->layers)
+      stride = std::max<long long>(stride, stage_layout(P->n_dense, d.N, d.N / P->C, RS, esz,
+                                                        P->max_tt_nodes, P->max_tt_entries, P->vstage).image);
+    P->img_stride = stride;
+    P->stage_img.assign(static_cast<size_t>(stride) * P->n_layers * P->C, 0);
+    auto put_real = [&](unsigned char *dst, double v) {
+      if (esz == 8) {
+        std::memcpy(dst, &v, 8);
+      } else {
+        const float f = static_cast<float>(v);
+        std::memcpy(dst, &f, 4);
+      }
+    };
+    auto put_int = [&](unsigned char *dst, int v) { std::memcpy(dst, &v, 4); };
+    for (int l = 0; l < P->n_layers; ++l) {
+      const int N = P->layers[l].N, R0 = N / P->C;
+      const StageLayout sl = stage_layout(P->n_dense, N, R0, RS, esz, P->max_tt_nodes,
+                                          P->max_tt_entries, P->vstage);
+      for (int c = 0; c < P->C; ++c) {
+        unsigned char *img = P->stage_img.data() + static_cast<size_t>(stride) * (l * P->C + c);
+        int md = 0, vpre = 0;
+        for (int m = 0; m < P->n_wfs; ++m) {
+          const int go = P->gt_off[m * P->n_layers + l];
+          if (go < 0) continue;
+          auto put_rec = [&](unsigned char *dst, int r, int off) {
+            put_int(dst, off);
+            for (int t = 0; t < P->max_taps; ++t) put_real(dst + esz * (1 + t), P->gt_rw[4 * r + t]);
+          };
+          for (int i = 0; i < N; ++i)
+            put_rec(img + sl.xr + static_cast<size_t>(esz) * RS * (md * N + i), go + i, P->gt_ro[go + i]);
+          for (int k = 0; k < R0; ++k) {
+            const int r = go + N + c * R0 + k;
+            put_rec(img + sl.yr + static_cast<size_t>(esz) * RS * (md * R0 + k), r, P->gt_ys[r]);
+          }
+          const int4 run = P->vs_run[(static_cast<size_t>(l) * P->C + c) * P->n_dense + md];
+          const int vq = 16 / esz;
+          put_int(img + sl.mnc + 4 * md, P->wfs[m].nc);
+          put_int(img + sl.vpre + 4 * md, vpre);
+          put_int(img + sl.vsrc + 4 * md, run.x / vq);
+          vpre += run.y;
+          ++md;
+        }
+        put_int(img + sl.vpre + 4 * md, vpre);
+        const int2 seg = P->tt_seg[l * P->C + c];
+        const int nn = seg.y - seg.x, e0 = P->tt_beg[seg.x], ne = P->tt_beg[seg.y] - e0;
+        for (int j = 0; j < nn; ++j) put_int(img + sl.tn + 4 * j, P->tt_node[seg.x + j]);
+        for (int j = 0; j <= nn; ++j) put_int(img + sl.tb + 4 * j, P->tt_beg[seg.x + j] - e0);
+        for (int e = 0; e < ne; ++e) {
+          put_int(img + sl.tk + 4 * e, P->tt_k[e0 + e]);
+          put_real(img + sl.tw + esz * (2 * e), P->tt_w[2 * (e0 + e)]);
+          put_real(img + sl.tw + esz * (2 * e + 1), P->tt_w[2 * (e0 + e) + 1]);
+        }
+        put_int(img + sl.nn, nn);
+      }
+    }
   }
 
   // -------------------------------------------------- Jacobi basis profiles
@@ -586,6 +647,10 @@ tomo_status build_host_plan(const tomo_geometry *geo, HostPlan *P, std::string *
     part += 2 * tiles;
   }
   P->n_part = part;
+  P->edge_slots.assign(std::max(1, P->n_edge_wfs), EdgeSlot{0, 0, 0, 0, 0.0, 0.0});
+  for (const auto &d : P->wfs)
+    if (d.tt_idx >= 0)
+      P->edge_slots[d.tt_idx] = EdgeSlot{d.part_off, d.n_tiles, d.kind, d.slope_off, d.inv_S, d.tt_scale};
   return TOMO_OK;
 }
 

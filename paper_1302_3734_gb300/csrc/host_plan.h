@@ -40,10 +40,13 @@ struct HostPlan {
   std::vector<int> gt_ys;          // row records: window start in the CTA's staged v rows
   std::vector<int4> vs_run;        // per (layer, rank, dense sensor): {g0, nvec, smem offset, 0}
   int vstage = 0;                  // largest staged v (T elements) of one analysis CTA
+  std::vector<unsigned char> stage_img;   // per (layer, rank) stage image, img_stride bytes apart
+  long long img_stride = 0;
   std::vector<int2> tt_seg;        // per (layer, rank)
   std::vector<int> tt_node, tt_beg, tt_k;
   std::vector<double> tt_w;        // 2 per entry
   int n_tt = 0, n_edge_wfs = 0;
+  std::vector<EdgeSlot> edge_slots;
   std::vector<int> edge_idx;
   std::vector<double> edge_t;
   std::vector<int> run_rows;

@@ -41,6 +41,17 @@ namespace tomo {
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+// The two halves of a cluster barrier (cluster.sync() is both): every thread
+// of every CTA in the cluster alternates arrive and wait.  arrive releases the
+// thread's earlier shared-memory accesses (including reads of other CTAs'
+// shared memory); wait returns once all threads of the cluster have arrived.
+__device__ __forceinline__ void cluster_arrive() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+  asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -155,6 +166,46 @@ __device__ double2 block_sum2(Acc<float> a, Acc<float> b) {
   return s_out;
 }
 
+// The block's double-float sums of (a, b) as (a.hi, a.lo, b.hi, b.lo), valid
+// in thread 0.
+__device__ float4 block_sum2_df(Acc<float> a, Acc<float> b) {
+  __shared__ float s_red[4][32];
+  warp_merge_down(a);
+  warp_merge_down(b);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    s_red[0][w] = a.hi;
+    s_red[1][w] = a.lo;
+    s_red[2][w] = b.hi;
+    s_red[3][w] = b.lo;
+  }
+  __syncthreads();
+  Acc<float> x, y;
+  if (w == 0) {
+    const int nw = blockDim.x >> 5;
+    if (lane < nw) {
+      x.hi = s_red[0][lane];
+      x.lo = s_red[1][lane];
+      y.hi = s_red[2][lane];
+      y.lo = s_red[3][lane];
+    }
+    warp_merge_down(x);
+    warp_merge_down(y);
+  }
+  return make_float4(x.hi, x.lo, y.hi, y.lo);
+}
+
+// A forward tile's two partial sums in its 16-byte partial slot: doubles for
+// FP64 plans, double-float pairs (hi, lo, hi, lo) for FP32 plans.
+__device__ __forceinline__ void store_tile_partial(double *slot, Acc<double> a, Acc<double> b) {
+  const double2 s = block_sum2(a, b);
+  if (threadIdx.x == 0) *reinterpret_cast<double2 *>(slot) = s;
+}
+__device__ __forceinline__ void store_tile_partial(double *slot, Acc<float> a, Acc<float> b) {
+  const float4 s = block_sum2_df(a, b);
+  if (threadIdx.x == 0) *reinterpret_cast<float4 *>(slot) = s;
+}
+
 // Fixed-order sum of `count` FP64 partial pairs (stride 2): warp 0 sums the
 // first of each pair and warp 1 the second (one of them does both in a
 // one-warp block); the result is returned to every thread.
@@ -180,12 +231,22 @@ __device__ __forceinline__ void load_inst(InstDev *dst, const InstDev *src) {
   __syncthreads();
 }
 
-// 16-byte asynchronous global -> shared copy (cp.async, L2 only) and its
-// completion for the calling thread.
+// Asynchronous global -> shared copies (cp.async: 16 bytes through L2 only,
+// or one element) and their completion for the calling thread.
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
   const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(__cvta_generic_to_global(gmem))
                : "memory");
+}
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T *smem, const T *gmem) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  if constexpr (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(__cvta_generic_to_global(gmem))
+                 : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(__cvta_generic_to_global(gmem))
+                 : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
@@ -279,11 +340,7 @@ __global__ void __launch_bounds__(kThreads) k_forward(const InstDev *__restrict_
       ax.add_prod(tx, ps);
       ay.add_prod(ty, ps);
     }
-    const double2 s = block_sum2(ax, ay);
-    if (tid == 0) {
-      I.part[W.part_off + 2 * it.tile] = s.x;
-      I.part[W.part_off + 2 * it.tile + 1] = s.y;
-    }
+    store_tile_partial(I.part + W.part_off + 2 * it.tile, ax, ay);
     return;
   }
 
@@ -394,11 +451,7 @@ __global__ void __launch_bounds__(kThreads) k_forward(const InstDev *__restrict_
   }
   if (W.kind != kRemoveTT) return;
   // 4. tip/tilt removal: this tile's sums of z (the consumer forms the means)
-  const double2 s = block_sum2(sx_acc, sy_acc);
-  if (tid == 0) {
-    I.part[W.part_off + 2 * it.tile] = s.x;
-    I.part[W.part_off + 2 * it.tile + 1] = s.y;
-  }
+  store_tile_partial(I.part + W.part_off + 2 * it.tile, sx_acc, sy_acc);
 }
 
 // ------------------------------------------------------- transform helpers
@@ -497,43 +550,93 @@ struct CoefMap {
 };
 
 // Coefficients of the pupil-edge terms, per edge slot, from the forward
-// kernel's FP64 partials (one warp per sensor, lanes in a fixed order):
+// kernel's tile partials (one warp per slot, lanes in a fixed order):
 // * tip/tilt removal: -sigma^-2 (mean z_x, mean z_y);
 // * tip/tilt-only sensor: sigma^-2 z / S with z its two mean slopes: the
 //   model's (tt_mode 0), data minus model (1), or the data alone (2), the data
 //   read from `slopes`.
+// FP32 plans sum the double-float partials and form the coefficients in
+// double-float arithmetic; FP64 plans use doubles.
+__device__ __forceinline__ void edge_pair(const EdgeSlot &es, int tt_mode, double a, double b,
+                                          const double *slopes, double *out) {
+  if (es.kind == kRemoveTT) {
+    out[0] = -(a * es.tt_scale);
+    out[1] = -(b * es.tt_scale);
+    return;
+  }
+  double zx = a * es.inv_S, zy = b * es.inv_S;
+  if (tt_mode == 1) {
+    zx = slopes[es.slope_off] - zx;
+    zy = slopes[es.slope_off + 1] - zy;
+  } else if (tt_mode == 2) {
+    zx = slopes[es.slope_off];
+    zy = slopes[es.slope_off + 1];
+  }
+  out[0] = zx * es.tt_scale;
+  out[1] = zy * es.tt_scale;
+}
+
+// (hi + lo) * s as a double-float (s rounded to float first)
+__device__ __forceinline__ float2 df_scale(float hi, float lo, float s) {
+  const float p = __fmul_rn(hi, s);
+  return make_float2(p, __fadd_rn(__fmaf_rn(hi, s, -p), __fmul_rn(lo, s)));
+}
+
+__device__ __forceinline__ float edge_one(const EdgeSlot &es, int tt_mode, float hi, float lo, float data) {
+  const float scale = static_cast<float>(es.tt_scale);
+  if (es.kind == kRemoveTT) {
+    const float2 m = df_scale(hi, lo, scale);
+    return -__fadd_rn(m.x, m.y);
+  }
+  if (tt_mode == 2) return __fmul_rn(data, scale);
+  float2 z = df_scale(hi, lo, static_cast<float>(es.inv_S));
+  if (tt_mode == 1) {
+    // data - z by two-sum, then the low part
+    const float t = __fsub_rn(data, z.x);
+    const float bp = __fsub_rn(t, data);
+    const float e = __fadd_rn(__fsub_rn(data, __fsub_rn(t, bp)), __fsub_rn(-z.x, bp));
+    z = make_float2(t, __fsub_rn(e, z.y));
+  }
+  const float2 c = df_scale(z.x, z.y, scale);
+  return __fadd_rn(c.x, c.y);
+}
+
 template <typename T>
 __device__ void edge_coefficients(const InstDev &I, T *s_coef, int tt_mode, const T *slopes) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  int j = 0;
-  for (int m = 0; m < I.n_wfs; ++m) {
-    const WfsDev &W = I.wfs[m];
-    if (W.kind == kFull) continue;
-    if ((j++ % nw) != warp) continue;
-    double a = 0.0, b = 0.0;
-    if (!(W.kind == kTTOnly && tt_mode == 2)) {
-      for (int t = lane; t < W.n_tiles; t += 32) {
-        a += I.part[W.part_off + 2 * t];
-        b += I.part[W.part_off + 2 * t + 1];
+  for (int k = warp; k < I.n_edge_wfs; k += nw) {
+    const EdgeSlot es = I.edge_slots[k];
+    const bool sum = !(es.kind == kTTOnly && tt_mode == 2);
+    if constexpr (sizeof(T) == 4) {
+      Acc<float> a, b;
+      if (sum)
+        for (int t = lane; t < es.n_tiles; t += 32) {
+          const float4 v = reinterpret_cast<const float4 *>(I.part + es.part_off)[t];
+          a.merge(v.x, v.y);
+          b.merge(v.z, v.w);
+        }
+      warp_merge_down(a);
+      warp_merge_down(b);
+      if (lane == 0) {
+        const bool tt = es.kind == kTTOnly && tt_mode != 0;
+        s_coef[2 * k] = edge_one(es, tt_mode, a.hi, a.lo, tt ? float(slopes[es.slope_off]) : 0.f);
+        s_coef[2 * k + 1] = edge_one(es, tt_mode, b.hi, b.lo, tt ? float(slopes[es.slope_off + 1]) : 0.f);
       }
-    }
-    a = warp_sum(a);
-    b = warp_sum(b);
-    if (lane != 0) continue;
-    if (W.kind == kRemoveTT) {
-      s_coef[2 * W.tt_idx] = T(-(a * W.tt_scale));
-      s_coef[2 * W.tt_idx + 1] = T(-(b * W.tt_scale));
     } else {
-      double zx = a * W.inv_S, zy = b * W.inv_S;
-      if (tt_mode == 1) {
-        zx = double(slopes[W.slope_off]) - zx;
-        zy = double(slopes[W.slope_off + 1]) - zy;
-      } else if (tt_mode == 2) {
-        zx = double(slopes[W.slope_off]);
-        zy = double(slopes[W.slope_off + 1]);
+      double a = 0.0, b = 0.0;
+      if (sum)
+        for (int t = lane; t < es.n_tiles; t += 32) {
+          a += I.part[es.part_off + 2 * t];
+          b += I.part[es.part_off + 2 * t + 1];
+        }
+      a = warp_sum(a);
+      b = warp_sum(b);
+      if (lane == 0) {
+        double out[2];
+        edge_pair(es, tt_mode, a, b, reinterpret_cast<const double *>(slopes), out);
+        s_coef[2 * k] = T(out[0]);
+        s_coef[2 * k + 1] = T(out[1]);
       }
-      s_coef[2 * W.tt_idx] = T(zx * W.tt_scale);
-      s_coef[2 * W.tt_idx + 1] = T(zy * W.tt_scale);
     }
   }
   __syncthreads();
@@ -636,78 +739,46 @@ __device__ void gather_rows(const InstDev &I, int l, int N, int R0, int crank, T
 }
 
 // Shared-memory copy of the gather tables of one analysis CTA (layer l, rows
-// [k0, k0+R0)): per dense sensor the tap records of every column and of the
-// CTA's rows (a row record's offset rewritten to its window start in the
-// staged v rows), the sensors' nc, and the CTA's pupil-edge segment, filled
-// before the dependency wait (the tables are constant) so that the copy
-// overlaps the previous kernel; after the wait, the corner rows of v that the
-// CTA reads (one aligned run per sensor, packed).
+// [k0, k0+R0)), laid out by stage_layout: the plan's stage image for the CTA
+// (tap records, pupil-edge segment, run tables), copied with cp.async before
+// the dependency wait since the tables are constant, so the copy overlaps the
+// previous kernel; after the wait, the corner rows of v that the CTA reads.
 template <typename T>
 struct GatherStage {
+  unsigned char *base;
   T *xr, *yr, *vs, *tw;
-  int *mnc, *vpre, *vsrc, *tn, *tb, *tk;
-  int nn;
+  int *mnc, *vpre, *vsrc, *tn, *tb, *tk, *pnn;
+  int image_bytes;
 
-  __device__ void carve(unsigned char *base, int Md, int N, int R0, int RS, int vstage,
-                        int max_nodes, int max_entries) {
-    xr = reinterpret_cast<T *>(base);
-    yr = xr + Md * N * RS;
-    vs = yr + Md * R0 * RS;
-    tw = vs + vstage;
-    mnc = reinterpret_cast<int *>(tw + 2 * max_entries);
-    vpre = mnc + Md;
-    vsrc = vpre + Md + 1;
-    tn = vsrc + Md;
-    tb = tn + max_nodes;
-    tk = tb + max_nodes + 1;
+  __device__ void carve(unsigned char *b, int Md, int N, int R0, const InstDev &I) {
+    const StageLayout sl = stage_layout(Md, N, R0, I.rec_stride, static_cast<int>(sizeof(T)),
+                                        I.max_tt_nodes, I.max_tt_entries, I.vstage);
+    base = b;
+    xr = reinterpret_cast<T *>(b + sl.xr);
+    yr = reinterpret_cast<T *>(b + sl.yr);
+    tw = reinterpret_cast<T *>(b + sl.tw);
+    vs = reinterpret_cast<T *>(b + sl.vs);
+    mnc = reinterpret_cast<int *>(b + sl.mnc);
+    vpre = reinterpret_cast<int *>(b + sl.vpre);
+    vsrc = reinterpret_cast<int *>(b + sl.vsrc);
+    tn = reinterpret_cast<int *>(b + sl.tn);
+    tb = reinterpret_cast<int *>(b + sl.tb);
+    tk = reinterpret_cast<int *>(b + sl.tk);
+    pnn = reinterpret_cast<int *>(b + sl.nn);
+    image_bytes = sl.image;
   }
 
-  __device__ void fill(const InstDev &I, int l, int N, int R0, int crank) {
-    const int nt = blockDim.x, tid = threadIdx.x, k0 = crank * R0, RS = I.rec_stride;
-    const int cpr = RS * static_cast<int>(sizeof(T)) / 16;       // 16-byte words per record
-    const int vx = N * cpr, vy = R0 * cpr;
-    const T *rec = static_cast<const T *>(I.gt_rec);
-    const int4 *runs = I.vs_run + (l * I.C + crank) * I.n_dense;
-    int md = 0;
-    for (int m = 0; m < I.n_wfs; ++m) {
-      const WfsDev &W = I.wfs[m];
-      if (W.kind == kTTOnly) continue;
-      const int go = I.gt_off[m * I.n_layers + l];
-      if (tid == 0) {
-        const int4 r = runs[md];
-        mnc[md] = W.nc;
-        vpre[md] = r.z * static_cast<int>(sizeof(T)) / 16;
-        vsrc[md] = r.x * static_cast<int>(sizeof(T)) / 16;
-        vpre[md + 1] = vpre[md] + r.y;
-      }
-      const uint4 *sx = reinterpret_cast<const uint4 *>(rec + static_cast<size_t>(go) * RS);
-      const uint4 *sy = reinterpret_cast<const uint4 *>(rec + static_cast<size_t>(go + N + k0) * RS);
-      uint4 *dx = reinterpret_cast<uint4 *>(xr + md * N * RS);
-      uint4 *dy = reinterpret_cast<uint4 *>(yr + md * R0 * RS);
-      for (int j = tid; j < vx + vy; j += nt) {
-        if (j < vx) {
-          dx[j] = sx[j];
-        } else {
-          const int q = j - vx;
-          uint4 w = sy[q];
-          if (q % cpr == 0) w.x = static_cast<unsigned>(I.gt_ys[go + N + k0 + q / cpr]);
-          dy[q] = w;
-        }
-      }
-      ++md;
-    }
-    const int2 seg = I.tt_seg[l * I.C + crank];
-    nn = seg.y - seg.x;
-    const int e0 = I.tt_beg[seg.x], ne = I.tt_beg[seg.y] - e0;
-    const T *ttw = static_cast<const T *>(I.tt_w);
-    for (int j = tid; j < nn; j += nt) tn[j] = I.tt_node[seg.x + j];
-    for (int j = tid; j <= nn; j += nt) tb[j] = I.tt_beg[seg.x + j] - e0;
-    for (int e = tid; e < ne; e += nt) {
-      tk[e] = I.tt_k[e0 + e];
-      tw[2 * e] = ttw[2 * (e0 + e)];
-      tw[2 * e + 1] = ttw[2 * (e0 + e) + 1];
-    }
+  // Starts the copy of the CTA's stage image; cp_async_wait_all() and a
+  // barrier complete it.
+  __device__ void issue_image(const InstDev &I, int l, int crank) const {
+    const uint4 *src = reinterpret_cast<const uint4 *>(static_cast<const unsigned char *>(I.stage_img) +
+                                                       I.img_stride * (l * I.C + crank));
+    uint4 *dst = reinterpret_cast<uint4 *>(base);
+    for (int j = threadIdx.x; j < image_bytes / 16; j += blockDim.x) cp_async16(dst + j, src + j);
+    cp_async_commit();
   }
+
+  __device__ int nn() const { return *pnn; }
 
   // Starts the asynchronous copy of the CTA's corner rows of v (written by
   // the previous kernel) into shared memory; cp_async_wait_all() and a
@@ -746,7 +817,7 @@ __device__ void gather_rows_staged(const InstDev &I, const GatherStage<T> &st, i
   }
   if (I.n_edge_wfs == 0) return;
   __syncthreads();
-  gather_edges<T>(st.nn, st.tn, st.tb, st.tk, st.tw, A, s_coef);
+  gather_edges<T>(st.nn(), st.tn, st.tb, st.tk, st.tw, A, s_coef);
 }
 
 // Epilogue of the analysis for one output coefficient.
@@ -839,37 +910,29 @@ __global__ void __launch_bounds__(kAnalysisThreads, 2) k_analysis(const InstDev 
   if (staged) {
     const int off = transform_cache_offset(N, C) + transform_cache_size(N, C, J, L.cache_kc);
     unsigned char *sb = smem_raw + ((static_cast<size_t>(off) * sizeof(T) + 15) & ~size_t(15));
-    st.carve(sb, I.n_dense, N, R0, I.rec_stride, I.vstage, I.max_tt_nodes, I.max_tt_entries);
-    st.fill(I, it.layer, N, R0, crank);
+    st.carve(sb, I.n_dense, N, R0, I);
+    st.issue_image(I, it.layer, crank);
+    cp_async_wait_all();
   }
   __syncthreads();
   pdl_wait();
   // a new solve starts from the residual: clear the breakdown flag
   if (EPI == kEpiResid && it.layer == 0 && crank == 0 && tid == 0) I.scal[kFlag] = 0.0;
 
-  // the gather's corner rows of v go out first, then the epilogue inputs (p,
-  // or x for a warm residual) of every owned coefficient, eight loads in
-  // flight per thread
+  // asynchronous copies: the gather's corner rows of v, then the epilogue
+  // inputs (p, or x for a warm residual) of every owned coefficient into the
+  // coefficient cache; both complete before the transform
   if (staged) st.load_v_async(I);
   const bool use_cache = (EPI == kEpiOp) || (EPI == kEpiResid && emit.warm);
   if (use_cache) {
     const T *srcv = EPI == kEpiOp ? emit.P : emit.X;
     const int total = cm.total();
-    for (int q0 = tid; q0 < total; q0 += 8 * nt) {
-      T val[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int q = q0 + u * nt;
-        if (q < total) {
-          int row, col;
-          cm.pos(q, row, col);
-          val[u] = srcv[L.off + row * N + col];
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < 8; ++u)
-        if (q0 + u * nt < total) cache[q0 + u * nt] = val[u];
+    for (int q = tid; q < total; q += nt) {
+      int row, col;
+      cm.pos(q, row, col);
+      cp_async_elem(cache + q, srcv + L.off + row * N + col);
     }
+    cp_async_commit();
   }
   // own rows [crank*R0, (crank+1)*R0) of the layer grid
   if (SRC == 0) {
@@ -893,15 +956,21 @@ __global__ void __launch_bounds__(kAnalysisThreads, 2) k_analysis(const InstDev 
       else gather_rows<T, 4>(I, it.layer, N, R0, crank, A, s_coef);
     }
   }
+  cp_async_wait_all();
   __syncthreads();
   auto slot_hl = [&](int k, int jl, int x) { return (use_cache && k >= cm.kc) ? cm.hl(k, jl, x) : -1; };
   auto slot_lh = [&](int k, int jl, int x) { return (use_cache && k >= cm.kc) ? cm.lh(k, jl, x) : -1; };
 
+  // Distributed levels: one cluster barrier per level (row pass done) before
+  // the halo rows are read from the next CTAs; the reads are released with
+  // an arrive, and the matching wait comes just before this CTA next
+  // overwrites B (the next level's row pass, or the end of the kernel).
   const int lgN = L.log2N, lgC = __ffs(C) - 1;
   int M = N, k = 1;
   for (; k <= J && M >= 2 * C; ++k, M >>= 1) {
     const int lgM = lgN - (k - 1), lgH = lgM - 1, lgR = lgM - lgC;
     const int R = M >> lgC, H = M >> 1, Rh = R >> 1;
+    if (k > 1) cluster_wait();
     // row pass (x): local
     for (int idx = tid; idx < R * H; idx += nt) {
       const int j = idx >> lgH, i = idx & (H - 1);
@@ -923,6 +992,7 @@ __global__ void __launch_bounds__(kAnalysisThreads, 2) k_analysis(const InstDev 
       const int r = ((crank + 1) * R + j) & (M - 1);
       B[(R + j) * M + x] = cluster.map_shared_rank(B, r >> lgR)[(r & (R - 1)) * M + x];
     }
+    cluster_arrive();
     __syncthreads();
     // column pass (y), local
     for (int idx = tid; idx < Rh * M; idx += nt) {
@@ -944,10 +1014,12 @@ __global__ void __launch_bounds__(kAnalysisThreads, 2) k_analysis(const InstDev 
       }
       emit(H + i, x, k, hi, slot_lh(k, il, x));
     }
-    cluster.sync();
+    __syncthreads();
   }
+  if (k > 1) cluster_wait();   // the next CTAs have read this CTA's halo rows
   if (k <= J) {
     // coarse levels: the remaining low-low block (side M = C) in CTA 0
+    cluster.sync();   // every CTA's low-low row is written
     if (crank == 0) {
       for (int idx = tid; idx < M * M; idx += nt) {
         const int r = idx >> lgC, c = idx & (M - 1);   // M == C here
@@ -1163,19 +1235,41 @@ __global__ void __launch_bounds__(kThreads) k_synthesis(const InstDev *__restric
   }
   __syncthreads();
 
+  // Distributed levels, per level: own coefficient rows (V), their row
+  // synthesis (x) into U after HL halo rows, one cluster barrier, the halo
+  // rows of the previous CTAs, then the column synthesis (y) into V, which is
+  // the next level's low-low block.  The halo reads are released with an
+  // arrive; the matching wait comes before this CTA next overwrites U (the
+  // next level's first step, or the end of the kernel).
   const int lgN = L.log2N, lgC = __ffs(C) - 1;
+  T *U = A, *V = B;   // U holds the low-low block of level kd
   for (int k = kd; k >= 1; --k) {
     const int lgM = lgN - (k - 1), lgRh = lgM - lgC - 1;
     const int M = N >> (k - 1), H = M >> 1, R = M >> lgC, Rh = R >> 1;
     const bool cached = k >= cm.kc;
-    T *BL = B;                      // low-y rows:  HL halo rows, then Rh own rows
-    T *BH = B + (HL + Rh) * M;      // high-y rows: same layout
-    // step 1: own low-y rows (LL | HL) and high-y rows (LH | HH)
+    if (k < kd) cluster_wait();
+    // step 1: own rows, low-y (LL | HL) then high-y (LH | HH), into V
     for (int idx = tid; idx < Rh * M; idx += nt) {
       const int jl = idx >> lgM, x = idx & (M - 1);
       const int i = crank * Rh + jl;
-      BL[(HL + jl) * M + x] = x < H ? A[jl * H + x] : (cached ? cache[cm.hl(k, jl, x)] : coef(i, x));
-      BH[(HL + jl) * M + x] = cached ? cache[cm.lh(k, jl, x)] : coef(H + i, x);
+      V[jl * M + x] = x < H ? U[jl * H + x] : (cached ? cache[cm.hl(k, jl, x)] : coef(i, x));
+      V[(Rh + jl) * M + x] = cached ? cache[cm.lh(k, jl, x)] : coef(H + i, x);
+    }
+    __syncthreads();
+    // step 2: row synthesis (x) into U: low-y rows at XL, high-y rows at XH
+    T *XL = U;                      // HL halo rows, then Rh own rows
+    T *XH = U + (HL + Rh) * M;      // same layout
+    for (int idx = tid; idx < 2 * Rh * M; idx += nt) {
+      const int r = idx >> lgM, j = idx & (M - 1);
+      const int q = j & 1;
+      const T *row = V + r * M;
+      T acc = T(0);
+#pragma unroll
+      for (int s = 0; s < LF / 2; ++s) {
+        const int jj = ((j >> 1) - s) & (H - 1);
+        acc += f.hs(q, s) * row[jj] + f.gs(q, s) * row[H + jj];
+      }
+      (r < Rh ? XL + (HL + r) * M : XH + (HL + r - Rh) * M)[j] = acc;
     }
     cluster.sync();
     // halo: the HL rows before ours (mod H) from the previous CTAs
@@ -1183,12 +1277,13 @@ __global__ void __launch_bounds__(kThreads) k_synthesis(const InstDev *__restric
       const int j = idx >> lgM, x = idx & (M - 1);
       const int ii = (crank * Rh - HL + j) & (H - 1);
       const int owner = ii >> lgRh, li = ii & (Rh - 1);
-      const T *oB = cluster.map_shared_rank(B, owner);
-      BL[j * M + x] = oB[(HL + li) * M + x];
-      BH[j * M + x] = oB[(HL + Rh + HL + li) * M + x];
+      const T *oU = cluster.map_shared_rank(U, owner);
+      XL[j * M + x] = oU[(HL + li) * M + x];
+      XH[j * M + x] = oU[(HL + Rh + HL + li) * M + x];
     }
+    cluster_arrive();
     __syncthreads();
-    // step 2: column synthesis of own output rows (local)
+    // step 3: column synthesis (y) of own output rows
     for (int idx = tid; idx < R * M; idx += nt) {
       const int yl = idx >> lgM, x = idx & (M - 1);
       const int p = yl & 1;
@@ -1196,29 +1291,16 @@ __global__ void __launch_bounds__(kThreads) k_synthesis(const InstDev *__restric
       T acc = T(0);
 #pragma unroll
       for (int s = 0; s < LF / 2; ++s)
-        acc += f.hs(p, s) * BL[(base - s) * M + x] + f.gs(p, s) * BH[(base - s) * M + x];
-      A[yl * M + x] = acc;
-    }
-    cluster.sync();
-    // step 3: row synthesis (local)
-    for (int idx = tid; idx < R * M; idx += nt) {
-      const int yl = idx >> lgM, j = idx & (M - 1);
-      const int q = j & 1;
-      const T *row = A + yl * M;
-      T acc = T(0);
-#pragma unroll
-      for (int s = 0; s < LF / 2; ++s) {
-        const int jj = ((j >> 1) - s) & (H - 1);
-        acc += f.hs(q, s) * row[jj] + f.gs(q, s) * row[H + jj];
-      }
-      if (k == 1) out[L.off + (crank * R + yl) * N + j] = acc;
-      else B[yl * M + j] = acc;
+        acc += f.hs(p, s) * XL[(base - s) * M + x] + f.gs(p, s) * XH[(base - s) * M + x];
+      if (k == 1) out[L.off + (crank * R + yl) * N + x] = acc;
+      else V[yl * M + x] = acc;
     }
     __syncthreads();
-    T *tmp = A;
-    A = B;
-    B = tmp;
+    T *tmp = U;
+    U = V;
+    V = tmp;
   }
+  if (kd >= 1) cluster_wait();   // the next CTAs have read this CTA's halo rows
 }
 
 // -------------------------------------------------------------- k_update
