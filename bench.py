@@ -34,6 +34,44 @@ sys.path.insert(0, ROOT)
 METRIC = "tomography solves/s and p99 frame latency at 84x84 MCAO vs plain GPU PCG"
 
 
+# DRAM bytes (read + write) per launch of each PCG kernel on this workload, from one ncu capture
+# with flushed caches, valid only for the kernel source file they were taken from.
+NCU_TRAFFIC = {
+    "kernels_cu_sha256": "2772239d08ea4d0be8796178826e0bb2c9396ed493531b9f2fba940e200ea6c6",
+    "bytes": {"analysis": 7466240, "synthesis": 659968, "forward": 752256, "update": 2982144},
+}
+
+
+def ncu_traffic(kind):
+    import hashlib
+    path = os.path.join(ROOT, "paper_1302_3734_gb300", "csrc", "kernels.cu")
+    try:
+        digest = hashlib.sha256(open(path, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    return NCU_TRAFFIC["bytes"].get(kind) if digest == NCU_TRAFFIC["kernels_cu_sha256"] else None
+
+
+def l2_probe(torch, dev):
+    """Copy bandwidth of a 32 MiB -> 32 MiB copy that stays in the 129 MB L2 (read + write bytes
+    over CUDA-event time, best of 20 after warm-up)."""
+    a = torch.empty(8 << 20, dtype=torch.float32, device=dev).fill_(1.0)
+    b = torch.empty_like(a)
+    for _ in range(5):
+        b.copy_(a)
+    best = float("inf")
+    for _ in range(20):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(10):
+            b.copy_(a)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1) / 10)
+    return 2 * a.numel() * 4 / (best / 1000.0) / 1e9
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -353,6 +391,7 @@ def main():
         peak, peak_src = float(peaks["hbm_gbs"]), "measured"
     except (OSError, KeyError, ValueError):
         peak, peak_src = 6800.0, "fallback"
+    l2_gbs = l2_probe(torch, dev)
 
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws,
@@ -371,8 +410,9 @@ def main():
                 "h2d_bytes_per_step": 4 * ns, "d2h_bytes_per_step": 4 * n,
                 "p99_ms": float(np.percentile(e2e_ms, 99))},
         "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": ncu_traffic(dominant),
                      "peak_source": peak_src,
+                     "l2_peak_gbs": l2_gbs, "frac_of_l2_peak": achieved / l2_gbs,
                      "kernel_ms_per_launch": {k: (v[1] / v[0] if v[0] else None) for k, v in kt.items()},
                      "bytes_per_iteration": info.bytes_per_iteration},
         "gpu_launches": launches,
