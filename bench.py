@@ -82,6 +82,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--batch", type=int, default=16, help="E-ELT instances per batched solve")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
+                    help="length of the served 16-telescope stream (0: skip it)")
     return ap.parse_args()
 
 
@@ -275,6 +277,103 @@ def bench_batched(pkg, torch, geom, slopes, flush, iters, args, peak, dev):
     return out
 
 
+def served_geometries():
+    """16 telescopes cycling the three geometry families: the 8 m system (FP32 operator, Jacobi
+    PCG), the E-ELT system, and instances of the uneven 64-instance set."""
+    from synth import configs
+    uneven = configs.config2()
+    out = []
+    for i in range(16):
+        if i % 3 == 0:
+            g = configs.config0()
+            g = dict(g, precision=0, precond=1, iters=10, name=g["name"].replace("fp64", "fp32-pcg"))
+        elif i % 3 == 1:
+            g = configs.config1()
+        else:
+            g = uneven[i]
+        out.append(g)
+    return out
+
+
+def bench_served(pkg, torch, args, dev, frames_per_tel=16, rate_hz=500.0):
+    """Served stream: every telescope emits frames at rate_hz with a seeded phase for
+    args.serve_seconds; the server solves each warm-started (10 PCG iterations), batching the
+    frames that wait.  Latency is from tomo_server_submit to the coefficients in host memory."""
+    from synth import FrozenFlow, gaussian_noise
+    geoms = served_geometries()
+    # frames: frozen-flow screens measured by a temporary plan, plus noise (host float32)
+    frames = []
+    for i, g in enumerate(geoms):
+        p = pkg.Plan(g)
+        flow = FrozenFlow(g, 3, instance=i)
+        sig = np.concatenate([np.full(2 if w["tt_only"] else 2 * int(w["valid"].sum()), w["sigma"])
+                              for w in g["wfs"]])
+        lay = torch.empty(p.n, dtype=torch.float32, device=dev)
+        sl = torch.empty(p.n_slopes, dtype=torch.float32, device=dev)
+        fr = []
+        for k in range(frames_per_tel):
+            lay.copy_(torch.from_numpy(np.concatenate([x.ravel() for x in flow.layers(k / rate_hz)])
+                                       .astype(np.float32)))
+            p.layers_to_slopes(lay, sl)
+            noise = gaussian_noise(p.n_slopes, 1.0, 5_000_000 + 1000 * i + k) * sig
+            fr.append(np.ascontiguousarray(sl.cpu().numpy() + noise.astype(np.float32)))
+        frames.append(fr)
+        p.close()
+    srv = pkg.Server(budget_bytes=16 << 30, iters=10, max_in_flight=3, queue_depth=64, result_slots=2)
+    ids = [srv.admit(g) for g in geoms]
+    stats0 = srv.stats()
+    # warm-up: every telescope's first frame, so the batch graphs exist
+    for i, t in enumerate(ids):
+        srv.submit(t, frames[i][0], tag=-1)
+    srv.drain(120.0)
+    srv.poll()
+    period = 1.0 / rate_hz
+    n_frames = int(args.serve_seconds * rate_hz)
+    rng = np.random.default_rng(3)
+    phase = rng.uniform(0.0, period, len(ids))
+    t0 = srv.clock() + 0.05
+    sched = sorted((t0 + phase[i] + k * period, i, k) for i in range(len(ids)) for k in range(n_frames))
+    results, lag, full = [], [], 0
+    j = 0
+    while j < len(sched):
+        now = srv.clock()
+        if sched[j][0] > now:
+            if sched[j][0] - now > 0.0005:
+                results += srv.poll()
+                time.sleep(0.0002)
+            continue
+        while j < len(sched) and sched[j][0] <= now:
+            ts, i, k = sched[j]
+            if not srv.submit(ids[i], frames[i][k % frames_per_tel], tag=k):
+                full += 1
+            lag.append(now - ts)
+            j += 1
+    srv.drain(300.0)
+    results += srv.poll()
+    stats = srv.stats()
+    srv.close()
+    ok = [r for r in results if r["status"] == 0]
+    lat = np.array([r["t_done"] - r["t_submit"] for r in ok]) * 1000.0
+    span = max(r["t_done"] for r in ok) - t0
+    kinds = {}
+    for r in ok:
+        name = geoms[ids.index(r["telescope"])]["name"].split("-")[0]
+        kinds.setdefault(name, []).append((r["t_done"] - r["t_submit"]) * 1000.0)
+    return {
+        "telescopes": len(ids), "rate_hz_per_telescope": rate_hz, "seconds": args.serve_seconds,
+        "frames_offered": len(sched), "frames_done": len(ok), "frames_refused_queue_full": full,
+        "solves_per_s": len(ok) / span,
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "max": float(lat.max())},
+        "latency_ms_p99_by_family": {k: float(np.percentile(v, 99)) for k, v in kinds.items()},
+        "launches": stats["launches"], "mean_frames_per_launch": len(ok) / max(1, stats["launches"]),
+        "client_pacing_lag_ms_p99": float(np.percentile(np.array(lag) * 1000.0, 99)),
+        "device_bytes_admitted": stats0["bytes_in_use"], "budget_bytes": stats0["budget_bytes"],
+        "workload": "16 telescopes cycling the 8 m (FP32 PCG), E-ELT and uneven-instance "
+                    "geometries; 500 Hz frozen-flow frames each; 10 PCG iterations, warm start",
+    }
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -420,6 +519,8 @@ def main():
     }
     if not args.no_batch:
         line["batched"] = bench_batched(pkg, torch, geom, slopes, flush, iters, args, peak, dev)
+    if args.serve_seconds > 0 and rank == 0:
+        line["served"] = bench_served(pkg, torch, args, dev)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         from oracle import Tomography
         ora = Tomography(geom)

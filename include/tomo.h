@@ -61,7 +61,8 @@ typedef enum {
   TOMO_ERR_CUDA = 5,         /* a CUDA runtime call failed (message has the CUDA error) */
   TOMO_ERR_TIMEOUT = 6,      /* reserved for waits with a deadline */
   TOMO_ERR_BREAKDOWN = 7,    /* p.Ap <= 0 or not finite during (P)CG: iterate frozen */
-  TOMO_ERR_UNSUPPORTED = 8   /* valid request this build does not implement */
+  TOMO_ERR_UNSUPPORTED = 8,  /* valid request this build does not implement */
+  TOMO_ERR_FULL = 9          /* a bounded queue is full (served frames of one telescope) */
 } tomo_status;
 
 /* One wavefront sensor (Sec. 2.1, Sec. 4.3). */
@@ -196,6 +197,92 @@ tomo_status tomo_get_kernel_times(tomo_plan *p, int *counts, double *ms, int n_k
  * iters, warm) call once into a CUDA graph and replays it; 0 launches every
  * kernel directly (one launch per kernel per call, no graph). */
 tomo_status tomo_set_launch_mode(tomo_plan *p, int use_graphs);
+
+/* ------------------------------------------------------------------ serving
+ * A request loop for a stream of slope frames from several telescopes, the
+ * real-time setting of Sec. 5: every frame is one tomo_solve of its
+ * telescope's plan, warm-started from that telescope's previous solution
+ * (Sec. 5.1), and each telescope's frames are solved strictly in arrival
+ * order.  The server owns the plans (admitted by device memory), one device
+ * slot per telescope for the frame's slopes and the warm-start coefficients,
+ * and two threads: a worker that launches, whenever a telescope with a
+ * waiting frame is idle, one batched solve (tomo_solve_batch's kernels, from
+ * a CUDA graph over all admitted plans with a per-launch mask of the
+ * telescopes that have a frame) after the frames' host-to-device copies and
+ * followed by the coefficients' device-to-host copies; and a completion
+ * thread that timestamps finished frames.  Frames that arrive while others
+ * are on the GPU go into the next launch, on the next of `max_in_flight`
+ * streams, so launches overlap on the device.
+ * Timestamps are seconds on the steady clock returned by tomo_server_clock(). */
+typedef struct tomo_server tomo_server;
+
+typedef struct {
+  int telescope;               /* id from tomo_server_admit */
+  int status;                  /* TOMO_OK, or the error of the launch that held the frame */
+  long long tag;               /* the caller's tag from tomo_server_submit */
+  double t_submit;             /* tomo_server_submit copied the frame in */
+  double t_launch;             /* the launch holding the frame was enqueued */
+  double t_done;               /* its coefficients were in host memory */
+  int batch_size;              /* frames in that launch */
+  int result_slot;             /* where tomo_server_result finds the coefficients */
+} tomo_frame_result;
+
+typedef struct {
+  long long frames_submitted, frames_done, launches;
+  long long bytes_in_use;      /* plans + telescope slots + batch tables (device) */
+  long long budget_bytes;
+  int telescopes;              /* admitted */
+  int in_flight;               /* launches on the device now */
+} tomo_server_stats;
+
+/* Create a server on the current device.  budget_bytes: device memory the
+ * server may hold (0: no limit).  iters: PCG iterations per frame (>= 0).
+ * max_in_flight: launches on the device at once (1..4).  queue_depth: frames
+ * a telescope may have waiting before tomo_server_submit returns
+ * TOMO_ERR_FULL (1..256).  result_slots: results kept per telescope for
+ * tomo_server_result (1..256). */
+tomo_status tomo_server_create(size_t budget_bytes, int iters, int max_in_flight, int queue_depth,
+                               int result_slots, tomo_server **out);
+
+/* Admit a telescope: builds its plan (as tomo_plan_create) and its slots if
+ * they fit the budget, else TOMO_ERR_NOMEM and nothing is kept.  Waits until
+ * no launch is in flight, then rebuilds the batch; frames of other telescopes
+ * wait meanwhile.  *telescope: the new id (ids are never reused).  The first
+ * frame starts from x0 = 0. */
+tomo_status tomo_server_admit(tomo_server *s, const tomo_geometry *g, int *telescope);
+
+/* Release a telescope and its memory (waits for its frame in flight; frames
+ * still waiting are dropped and not reported). */
+tomo_status tomo_server_release(tomo_server *s, int telescope);
+
+/* Submit one frame: copies n_slopes elements (float, or double for precision 1
+ * plans) from host memory and returns; `tag` comes back in the result.
+ * TOMO_ERR_FULL: queue_depth frames of this telescope are already waiting. */
+tomo_status tomo_server_submit(tomo_server *s, int telescope, const void *host_slopes, long long tag);
+
+/* Up to `max` finished frames (oldest first) into out; returns how many. */
+int tomo_server_poll(tomo_server *s, tomo_frame_result *out, int max);
+
+/* Copy the coefficients (n_coeffs elements) of a finished frame into
+ * host_out.  TOMO_ERR_ARG if that slot already holds a later frame. */
+tomo_status tomo_server_result(tomo_server *s, int telescope, int result_slot, long long tag,
+                               void *host_out);
+
+/* Wait until every submitted frame is finished (TOMO_ERR_TIMEOUT after
+ * timeout_s seconds). */
+tomo_status tomo_server_drain(tomo_server *s, double timeout_s);
+
+tomo_status tomo_server_get_stats(tomo_server *s, tomo_server_stats *out);
+
+/* The plan of an admitted telescope (owned by the server; for
+ * tomo_plan_get_info and the operator calls, not for solves). */
+tomo_status tomo_server_get_plan(tomo_server *s, int telescope, const tomo_plan **out);
+
+/* The steady clock of the frame timestamps (seconds). */
+double tomo_server_clock(void);
+
+/* Stop the threads, finish the frames in flight, release every plan.  NULL-safe. */
+void tomo_server_destroy(tomo_server *s);
 
 /* Number of kernels this library has launched so far in this process. */
 long long tomo_launch_count(void);

@@ -5,8 +5,8 @@ eq. eqn_lse) runs in hand-written sm_103a CUDA kernels behind the C ABI of
 ``include/tomo.h``; ``binding`` is a thin ctypes layer over it and ``build``
 compiles the library in-tree.
 """
-from .binding import (Plan, TomoError, solve_batch, launch_count, load_library, version,
+from .binding import (Plan, Server, TomoError, solve_batch, launch_count, load_library, version,
                       geometry_struct, SIGNATURES, LIB_PATH)
 
-__all__ = ["Plan", "TomoError", "solve_batch", "launch_count", "load_library", "version",
+__all__ = ["Plan", "Server", "TomoError", "solve_batch", "launch_count", "load_library", "version",
            "geometry_struct", "SIGNATURES", "LIB_PATH"]

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libtomo.so")
 
 STATUS = {0: "TOMO_OK", 1: "TOMO_ERR_ARG", 2: "TOMO_ERR_GEOMETRY", 3: "TOMO_ERR_LEVELS",
           4: "TOMO_ERR_NOMEM", 5: "TOMO_ERR_CUDA", 6: "TOMO_ERR_TIMEOUT",
-          7: "TOMO_ERR_BREAKDOWN", 8: "TOMO_ERR_UNSUPPORTED"}
+          7: "TOMO_ERR_BREAKDOWN", 8: "TOMO_ERR_UNSUPPORTED", 9: "TOMO_ERR_FULL"}
 
 KERNEL_KINDS = ("synthesis", "forward", "analysis", "update", "other")
 
@@ -48,6 +48,20 @@ class Geometry(ctypes.Structure):
                 ("wavelet_order", ctypes.c_int), ("levels", ctypes.c_int),
                 ("alpha", ctypes.c_double), ("L0", ctypes.c_double),
                 ("precond", ctypes.c_int), ("precision", ctypes.c_int)]
+
+
+class FrameResult(ctypes.Structure):
+    _fields_ = [("telescope", ctypes.c_int), ("status", ctypes.c_int), ("tag", ctypes.c_longlong),
+                ("t_submit", ctypes.c_double), ("t_launch", ctypes.c_double),
+                ("t_done", ctypes.c_double), ("batch_size", ctypes.c_int),
+                ("result_slot", ctypes.c_int)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("frames_submitted", ctypes.c_longlong), ("frames_done", ctypes.c_longlong),
+                ("launches", ctypes.c_longlong), ("bytes_in_use", ctypes.c_longlong),
+                ("budget_bytes", ctypes.c_longlong), ("telescopes", ctypes.c_int),
+                ("in_flight", ctypes.c_int)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -82,6 +96,17 @@ SIGNATURES = [
     ("tomo_last_error", ctypes.c_char_p, []),
     ("tomo_destroy", None, [_VP]),
     ("tomo_version", ctypes.c_char_p, []),
+    ("tomo_server_create", _I, [ctypes.c_size_t, _I, _I, _I, _I, ctypes.POINTER(_VP)]),
+    ("tomo_server_admit", _I, [_VP, ctypes.POINTER(Geometry), ctypes.POINTER(_I)]),
+    ("tomo_server_release", _I, [_VP, _I]),
+    ("tomo_server_submit", _I, [_VP, _I, _VP, ctypes.c_longlong]),
+    ("tomo_server_poll", _I, [_VP, ctypes.POINTER(FrameResult), _I]),
+    ("tomo_server_result", _I, [_VP, _I, _I, ctypes.c_longlong, _VP]),
+    ("tomo_server_drain", _I, [_VP, ctypes.c_double]),
+    ("tomo_server_get_stats", _I, [_VP, ctypes.POINTER(ServerStats)]),
+    ("tomo_server_get_plan", _I, [_VP, _I, ctypes.POINTER(_VP)]),
+    ("tomo_server_clock", ctypes.c_double, []),
+    ("tomo_server_destroy", None, [_VP]),
 ]
 
 _lib = None
@@ -270,6 +295,100 @@ def solve_batch(plans, slopes, coeffs, iters, warm=True, stream=None):
                                  for p, s in zip(plans, slopes)])
     cp = (ctypes.c_void_p * n)(*[p._tensor(c, p.n, "coeffs").value for p, c in zip(plans, coeffs)])
     _check(load_library().tomo_solve_batch(ph, sp, cp, n, int(iters), int(bool(warm)), _stream(stream)))
+
+
+class Server:
+    """The served stream of tomo_server_*: telescopes admitted by device memory, frames
+    submitted from host memory and solved warm-started, batched on arrival."""
+
+    def __init__(self, budget_bytes=0, iters=10, max_in_flight=2, queue_depth=16, result_slots=8):
+        lib = load_library()
+        h = ctypes.c_void_p()
+        _check(lib.tomo_server_create(int(budget_bytes), int(iters), int(max_in_flight),
+                                      int(queue_depth), int(result_slots), ctypes.byref(h)))
+        self._h = h
+        self._info = {}
+        self._buf = (FrameResult * 4096)()
+
+    def admit(self, geom):
+        """Admit a telescope; returns its id (TomoError with status TOMO_ERR_NOMEM when the
+        budget does not allow it)."""
+        lib = load_library()
+        g, keep = geometry_struct(geom)
+        tid = ctypes.c_int(-1)
+        _check(lib.tomo_server_admit(self._h, ctypes.byref(g), ctypes.byref(tid)))
+        del keep
+        plan = ctypes.c_void_p()
+        _check(lib.tomo_server_get_plan(self._h, tid.value, ctypes.byref(plan)))
+        inf = PlanInfo()
+        _check(lib.tomo_plan_get_info(plan, ctypes.byref(inf)))
+        self._info[tid.value] = inf
+        return tid.value
+
+    def info(self, telescope):
+        return self._info[telescope]
+
+    def release(self, telescope):
+        _check(load_library().tomo_server_release(self._h, int(telescope)))
+        self._info.pop(telescope, None)
+
+    def submit(self, telescope, slopes, tag):
+        """slopes: C-contiguous host array (float32, or float64 for precision-1 plans) of
+        n_slopes elements.  Returns False when the telescope's queue is full."""
+        inf = self._info[telescope]
+        dt = np.float64 if inf.precision else np.float32
+        if slopes.dtype != dt or not slopes.flags.c_contiguous or slopes.size != inf.n_slopes:
+            raise ValueError(f"slopes must be a contiguous {np.dtype(dt).name} array of {inf.n_slopes}")
+        st = load_library().tomo_server_submit(self._h, int(telescope),
+                                                ctypes.c_void_p(slopes.ctypes.data), int(tag))
+        if st == 9:
+            return False
+        _check(st)
+        return True
+
+    def poll(self):
+        """Finished frames: a list of dicts (telescope, status, tag, t_submit, t_launch,
+        t_done, batch_size, result_slot)."""
+        out = []
+        lib = load_library()
+        while True:
+            k = lib.tomo_server_poll(self._h, self._buf, len(self._buf))
+            for i in range(k):
+                r = self._buf[i]
+                out.append({f: getattr(r, f) for f, _ in FrameResult._fields_})
+            if k < len(self._buf):
+                return out
+
+    def result(self, telescope, result_slot, tag):
+        """Coefficients of a finished frame (numpy array), or None if the slot moved on."""
+        inf = self._info[telescope]
+        out = np.empty(int(inf.n_coeffs), dtype=np.float64 if inf.precision else np.float32)
+        st = load_library().tomo_server_result(self._h, int(telescope), int(result_slot), int(tag),
+                                                ctypes.c_void_p(out.ctypes.data))
+        return out if st == 0 else None
+
+    def drain(self, timeout_s=60.0):
+        _check(load_library().tomo_server_drain(self._h, float(timeout_s)))
+
+    def stats(self):
+        st = ServerStats()
+        _check(load_library().tomo_server_get_stats(self._h, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    @staticmethod
+    def clock():
+        return float(load_library().tomo_server_clock())
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load_library().tomo_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def launch_count():

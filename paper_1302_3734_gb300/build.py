@@ -1,6 +1,6 @@
 """In-tree build of the CUDA library ``libtomo.so`` for sm_103a.
 
-The three translation units are compiled in parallel (nvcc for the CUDA files,
+The translation units are compiled in parallel (nvcc for the CUDA files,
 g++ for the host plan builder) and linked with nvcc.  The result lives next to
 this file so that the Python binding loads it from the source tree.
 """
@@ -26,7 +26,7 @@ def _cuda_home():
 
 
 def _sources():
-    return [os.path.join(CSRC, f) for f in ("kernels.cu", "api.cu", "noalloc.cu", "host_plan.cpp")]
+    return [os.path.join(CSRC, f) for f in ("kernels.cu", "api.cu", "noalloc.cu", "server.cu", "host_plan.cpp")]
 
 
 def _deps():

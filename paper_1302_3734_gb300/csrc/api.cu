@@ -200,35 +200,44 @@ tomo_status read_resnorm(tomo_plan *p, int iters, cudaStream_t s, double *out) {
   return TOMO_OK;
 }
 
-// ------------------------------------------------------------------ batches
-// Plans solved together: grouped by (cluster size, filter length, precision),
-// one launch per group and phase.  Built once per distinct list of plans and
-// cached; a plan's destruction drops every batch that contains it.
-struct BatchGroup {
-  LaunchSet ls;
-  std::vector<int> members;   // position in the batch of each instance slot
-  void *arena = nullptr;
-};
-
-struct BatchGraph {
-  std::vector<const void *> slopes;
-  std::vector<void *> x;
-  const int *active;
-  int iters, warm;
-  cudaGraphExec_t exec;
-  int kernels;
-};
-
-struct Batch {
-  std::vector<tomo_plan *> plans;
-  std::vector<BatchGroup> groups;
-  std::vector<BatchGraph> graphs;
-  cudaStream_t cap = nullptr;
-  int device = 0;
-};
-
 std::mutex g_batch_mu;
 std::vector<Batch *> g_batches;
+
+tomo_status get_batch(tomo_plan *const *plans, int count, Batch **out) {
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  for (Batch *b : g_batches)
+    if (static_cast<int>(b->plans.size()) == count && std::equal(plans, plans + count, b->plans.begin())) {
+      *out = b;
+      return TOMO_OK;
+    }
+  if (g_batches.size() >= 32) {
+    free_batch(g_batches.front());
+    g_batches.erase(g_batches.begin());
+  }
+  DeviceGuard dg(plans[0]->device);
+  Batch *b = nullptr;
+  TOMO_TRY(build_batch(plans, count, &b));
+  g_batches.push_back(b);
+  *out = b;
+  return TOMO_OK;
+}
+
+void drop_batches_of(const tomo_plan *p) {
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  for (size_t i = 0; i < g_batches.size();) {
+    Batch *b = g_batches[i];
+    if (std::find(b->plans.begin(), b->plans.end(), p) != b->plans.end()) {
+      free_batch(b);
+      g_batches.erase(g_batches.begin() + i);
+    } else {
+      ++i;
+    }
+  }
+}
+
+}  // namespace
+
+namespace tomo {
 
 void free_batch(Batch *b) {
   for (auto &g : b->graphs) cudaGraphExecDestroy(g.exec);
@@ -301,6 +310,7 @@ tomo_status build_batch(tomo_plan *const *plans, int count, Batch **out) {
     std::memcpy(img.data() + o_f, fwd.data(), sizeof(FwdItem) * fwd.size());
     std::memcpy(img.data() + o_u, upd.data(), sizeof(UpdItem) * upd.size());
     cudaError_t e = cudaMalloc(&g.arena, bytes);
+    g.bytes = bytes;
     if (e == cudaSuccess) e = cudaMemcpy(g.arena, img.data(), bytes, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
       free_batch(b);
@@ -323,38 +333,6 @@ tomo_status build_batch(tomo_plan *const *plans, int count, Batch **out) {
   }
   *out = b;
   return TOMO_OK;
-}
-
-tomo_status get_batch(tomo_plan *const *plans, int count, Batch **out) {
-  std::lock_guard<std::mutex> lk(g_batch_mu);
-  for (Batch *b : g_batches)
-    if (static_cast<int>(b->plans.size()) == count && std::equal(plans, plans + count, b->plans.begin())) {
-      *out = b;
-      return TOMO_OK;
-    }
-  if (g_batches.size() >= 32) {
-    free_batch(g_batches.front());
-    g_batches.erase(g_batches.begin());
-  }
-  DeviceGuard dg(plans[0]->device);
-  Batch *b = nullptr;
-  TOMO_TRY(build_batch(plans, count, &b));
-  g_batches.push_back(b);
-  *out = b;
-  return TOMO_OK;
-}
-
-void drop_batches_of(const tomo_plan *p) {
-  std::lock_guard<std::mutex> lk(g_batch_mu);
-  for (size_t i = 0; i < g_batches.size();) {
-    Batch *b = g_batches[i];
-    if (std::find(b->plans.begin(), b->plans.end(), p) != b->plans.end()) {
-      free_batch(b);
-      g_batches.erase(g_batches.begin() + i);
-    } else {
-      ++i;
-    }
-  }
 }
 
 // One solve of every instance of the batch (each group in turn); `active`
@@ -418,7 +396,7 @@ tomo_status batch_solve(Batch *b, const void *const *slopes, void *const *x, con
   return TOMO_OK;
 }
 
-}  // namespace
+}  // namespace tomo
 
 extern "C" {
 

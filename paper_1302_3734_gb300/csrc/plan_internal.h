@@ -76,3 +76,44 @@ struct tomo_plan {
   double kind_ms[tomo::kNumKinds] = {0};
   long long kind_n[tomo::kNumKinds] = {0};
 };
+
+namespace tomo {
+
+// Plans solved together: grouped by (cluster size, filter length, precision),
+// one launch per group and phase.  Built once per distinct list of plans and
+// cached; a plan's destruction drops every batch that contains it.
+struct BatchGroup {
+  LaunchSet ls;
+  std::vector<int> members;   // position in the batch of each instance slot
+  void *arena = nullptr;
+  size_t bytes = 0;           // device bytes of the group's tables
+};
+
+struct BatchGraph {
+  std::vector<const void *> slopes;
+  std::vector<void *> x;
+  const int *active;
+  int iters, warm;
+  cudaGraphExec_t exec;
+  int kernels;
+};
+
+struct Batch {
+  std::vector<tomo_plan *> plans;
+  std::vector<BatchGroup> groups;
+  std::vector<BatchGraph> graphs;
+  cudaStream_t cap = nullptr;
+  int device = 0;
+};
+
+// Build a batch of plans (all on one device); free it with free_batch.
+tomo_status build_batch(tomo_plan *const *plans, int count, Batch **out);
+void free_batch(Batch *b);
+// One solve of every active instance of the batch on stream s, replayed from
+// a graph cached per (iters, warm, active masks, slope and coefficient
+// pointers).  active_g: per launch group a device array of one int per group
+// slot (nonzero = solve), or NULL for all.
+tomo_status batch_solve(Batch *b, const void *const *slopes, void *const *x, const int *const *active_g,
+                        int iters, int warm, cudaStream_t s);
+
+}  // namespace tomo

@@ -1,0 +1,158 @@
+"""The served stream (tomo_server_*): frames of several telescopes of different
+sizes, admitted by memory, solved warm-started and batched on arrival.
+
+* every frame served in the mix is bitwise the frame solved alone (the same
+  telescope's frames through tomo_solve, one after the other, warm-started);
+* sampled frames match the FP64 oracle (PCG from the server's own previous
+  frame, as a warm start is defined);
+* admission by a device-memory budget, release, the bounded frame queue and
+  drain.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import Tomography
+from synth import configs, FrozenFlow, gaussian_noise
+
+from test_gpu_parity import ERRORS, error_log, rel  # noqa: F401  (shared error log)
+
+pytestmark = pytest.mark.gpu
+
+ITERS = 6
+
+
+def _geoms():
+    small = configs.small_lgs_config(16, 32, 3, 2)
+    ragged = configs.small_lgs_config(24, 64, 2, 3, order=2)
+    cfg0 = configs.config0()
+    cfg0 = dict(cfg0, precision=0, precond=1, name=cfg0["name"] + "-fp32")
+    return [small, ragged, cfg0]
+
+
+def _frames(geom, k_frames, seed):
+    ora = Tomography(geom)
+    ns = int(ora.meas_offsets[-1])
+    sig = np.concatenate([np.full(2 if w["tt_only"] else 2 * int(w["valid"].sum()), w["sigma"])
+                          for w in geom["wfs"]])
+    flow = FrozenFlow(geom, 3, instance=seed)
+    out = []
+    for k in range(k_frames):
+        s = ora.measure(flow.layers(0.002 * k)) + gaussian_noise(ns, 1.0, 50_000 + 100 * seed + k) * sig
+        out.append(np.ascontiguousarray(s, dtype=np.float32))
+    return ora, out
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1302_3734_gb300 import build
+    build.build()
+    import paper_1302_3734_gb300 as pkg
+    return torch, pkg
+
+
+def _serve(pkg, geoms, frames, **kw):
+    srv = pkg.Server(iters=ITERS, result_slots=len(frames[0]) + 1, queue_depth=len(frames[0]) + 1, **kw)
+    ids = [srv.admit(g) for g in geoms]
+    # interleaved arrivals, as several telescopes emit frames at the same rate
+    for k in range(len(frames[0])):
+        for i, tid in enumerate(ids):
+            assert srv.submit(tid, frames[i][k], tag=k)
+    srv.drain(120.0)
+    res = srv.poll()
+    got = {}
+    for r in res:
+        assert r["status"] == 0
+        assert r["t_submit"] <= r["t_launch"] <= r["t_done"]
+        x = srv.result(r["telescope"], r["result_slot"], r["tag"])
+        assert x is not None
+        got[(ids.index(r["telescope"]), r["tag"])] = x
+    stats = srv.stats()
+    srv.close()
+    return got, res, stats
+
+
+def test_served_frames_are_bitwise_the_frames_solved_alone(lib):
+    torch, pkg = lib
+    geoms = _geoms()
+    K = 5
+    data = [_frames(g, K, i) for i, g in enumerate(geoms)]
+    frames = [d[1] for d in data]
+    got, res, stats = _serve(pkg, geoms, frames, max_in_flight=2)
+    assert stats["frames_done"] == K * len(geoms)
+    assert max(r["batch_size"] for r in res) > 1, "frames of different telescopes never shared a launch"
+    for i, g in enumerate(geoms):
+        plan = pkg.Plan(g)
+        x = torch.zeros(plan.n, dtype=torch.float32, device="cuda")
+        for k in range(K):
+            s = torch.tensor(frames[i][k], device="cuda")
+            plan.solve(s, x, ITERS, warm=True)
+            alone = x.cpu().numpy()
+            assert np.array_equal(alone, got[(i, k)]), (g["name"], k)
+        plan.close()
+
+
+def test_served_frames_match_the_oracle(lib):
+    torch, pkg = lib
+    geoms = _geoms()
+    K = 4
+    data = [_frames(g, K, 10 + i) for i, g in enumerate(geoms)]
+    got, _, _ = _serve(pkg, geoms, [d[1] for d in data], max_in_flight=3)
+    for i, g in enumerate(geoms):
+        ora = data[i][0]
+        for k in (0, K - 1):
+            x0 = np.zeros(ora.n) if k == 0 else got[(i, k - 1)].astype(np.float64)
+            s = data[i][1][k].astype(np.float64)
+            x_ref = ora.pcg(ora.rhs(s), x0, ITERS, ora.jacobi_diagonal() if g["precond"] else None)
+            e = rel(ora.join(ora.synthesis(got[(i, k)].astype(np.float64))),
+                    ora.join(ora.synthesis(x_ref)), f"served/{g['name']}/frame{k}")
+            assert e < 1e-5, (g["name"], k, e)
+
+
+def test_admission_by_memory_budget(lib):
+    torch, pkg = lib
+    g = configs.small_lgs_config(16, 32, 3, 2)
+    probe = pkg.Server(iters=2)
+    a = probe.admit(g)
+    one = probe.stats()["bytes_in_use"]
+    probe.close()
+    srv = pkg.Server(budget_bytes=int(2.5 * one), iters=2)
+    ids = [srv.admit(g), srv.admit(g)]
+    with pytest.raises(pkg.TomoError) as ei:
+        srv.admit(g)
+    assert ei.value.status == 4
+    assert srv.stats()["telescopes"] == 2
+    srv.release(ids[0])
+    ids.append(srv.admit(g))
+    assert srv.stats()["telescopes"] == 2 and srv.stats()["bytes_in_use"] <= int(2.5 * one)
+    s = np.zeros(srv.info(ids[-1]).n_slopes, dtype=np.float32)
+    assert srv.submit(ids[-1], s, tag=7)
+    srv.drain(60.0)
+    (r,) = srv.poll()
+    assert r["tag"] == 7 and r["status"] == 0
+    assert np.all(srv.result(ids[-1], r["result_slot"], 7) == 0.0)   # zero data, zero start: x = 0
+    srv.close()
+    del a
+
+
+def test_bounded_queue_release_and_drain(lib):
+    torch, pkg = lib
+    g = configs.small_lgs_config(16, 32, 3, 2)
+    srv = pkg.Server(iters=400, queue_depth=2, result_slots=2)
+    tid = srv.admit(g)
+    s = np.ones(srv.info(tid).n_slopes, dtype=np.float32)
+    ok = [srv.submit(tid, s, tag=k) for k in range(6)]
+    assert ok[:2] == [True, True] and not all(ok), ok   # the first frame holds a slot while it runs
+    srv.drain(60.0)
+    assert all(r["status"] == 0 for r in srv.poll())
+    # frames still waiting when their telescope leaves are dropped; drain still returns
+    t2 = srv.admit(g)
+    for k in range(2):
+        srv.submit(t2, s, tag=100 + k)
+    srv.release(t2)
+    srv.drain(60.0)
+    srv.poll()
+    assert srv.stats()["telescopes"] == 1
+    srv.close()

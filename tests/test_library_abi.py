@@ -96,3 +96,20 @@ def test_a_valid_geometry_reaches_the_device_step(lib):
         assert st == 0, msg
     else:
         assert st == 5, msg
+
+
+def test_server_argument_validation_without_gpu(lib):
+    import ctypes
+    h = ctypes.c_void_p()
+    for args in ((0, -1, 2, 8, 4), (0, 10, 0, 8, 4), (0, 10, 5, 8, 4), (0, 10, 2, 0, 4),
+                 (0, 10, 2, 8, 0), (0, 10, 2, 300, 4)):
+        assert lib.tomo_server_create(*args, ctypes.byref(h)) == 1, args
+        assert not h.value
+    assert lib.tomo_server_create(0, 10, 2, 8, 4, None) == 1
+    # NULL servers are refused, not dereferenced
+    assert lib.tomo_server_submit(None, 0, None, 0) == 1
+    assert lib.tomo_server_release(None, 0) == 1
+    assert lib.tomo_server_drain(None, 1.0) == 1
+    assert lib.tomo_server_poll(None, None, 4) == 0
+    lib.tomo_server_destroy(None)
+    assert lib.tomo_server_clock() > 0.0
