@@ -239,9 +239,11 @@ def bench_batched(pkg, torch, geom, slopes, flush, iters, args, peak, dev):
     from synth import configs, gaussian_noise
     out = {}
     steps = max(5, min(args.steps, 100))
-    # B E-ELT instances, each on its own frame of the stream
+    from paper_1302_3734_gb300.autotune import tune_cluster_size, _plans
+    # B E-ELT instances, each on its own frame of the stream, at the tuned cluster size
     B = args.batch
-    plans = [pkg.Plan(geom) for _ in range(B)]
+    c_e, tab_e = tune_cluster_size([geom] * B, iters)
+    plans = _plans([geom] * B, c_e)
     F = slopes.shape[0]
     sl = [slopes[(3 * i) % F].clone() for i in range(B)]
     xs = [torch.zeros(plans[0].n, dtype=torch.float32, device=dev) for _ in range(B)]
@@ -249,6 +251,7 @@ def bench_batched(pkg, torch, geom, slopes, flush, iters, args, peak, dev):
     ms = float(np.mean(t))
     bytes_it = sum(p.info.bytes_per_iteration for p in plans)
     out["eelt"] = {"instances": B, "solves_per_s": B * 1000.0 / ms, "ms_per_batch": ms,
+                   "cluster_size": c_e, "autotune_solves_per_s": tab_e,
                    "p99_ms": float(np.percentile(t, 99)),
                    "achieved_GBps_per_iteration_bytes": bytes_it * iters / (ms / 1000.0) / 1e9,
                    "frac_of_hbm_peak": bytes_it * iters / (ms / 1000.0) / 1e9 / peak}
@@ -256,7 +259,8 @@ def bench_batched(pkg, torch, geom, slopes, flush, iters, args, peak, dev):
         p.close()
     # the 64-instance uneven workload
     geoms = configs.config2()
-    plans = [pkg.Plan(g) for g in geoms]
+    c_u, tab_u = tune_cluster_size(geoms, 10)
+    plans = _plans(geoms, c_u)
     sl = []
     for i, (g, p) in enumerate(zip(geoms, plans)):
         sig = np.concatenate([np.full(2 if w["tt_only"] else 2 * int(w["valid"].sum()), w["sigma"])
@@ -268,6 +272,7 @@ def bench_batched(pkg, torch, geom, slopes, flush, iters, args, peak, dev):
     ms = float(np.mean(t))
     bytes_it = sum(p.info.bytes_per_iteration for p in plans)
     out["uneven64"] = {"instances": len(plans), "solves_per_s": len(plans) * 1000.0 / ms,
+                       "cluster_size": c_u, "autotune_solves_per_s": tab_u,
                        "ms_per_batch": ms, "p99_ms": float(np.percentile(t, 99)),
                        "coefficients": int(sum(p.n for p in plans)),
                        "achieved_GBps_per_iteration_bytes": bytes_it * 10 / (ms / 1000.0) / 1e9,
@@ -319,8 +324,21 @@ def bench_served(pkg, torch, args, dev, frames_per_tel=16, rate_hz=500.0):
             fr.append(np.ascontiguousarray(sl.cpu().numpy() + noise.astype(np.float32)))
         frames.append(fr)
         p.close()
+    from paper_1302_3734_gb300.autotune import tune_cluster_size
+    c_s, tab_s = tune_cluster_size(geoms, 10)
     srv = pkg.Server(budget_bytes=16 << 30, iters=10, max_in_flight=3, queue_depth=64, result_slots=2)
-    ids = [srv.admit(g) for g in geoms]
+    srv.set_policy(latest_only=True)
+    ids = []
+    for g in geoms:
+        cc = c_s
+        while True:
+            try:
+                ids.append(srv.admit(g, cluster_size=cc))
+                break
+            except pkg.TomoError as e:
+                if e.status not in (1, 8) or cc >= 16:
+                    raise
+                cc *= 2
     stats0 = srv.stats()
     # warm-up: every telescope's first frame, so the batch graphs exist
     for i, t in enumerate(ids):
@@ -353,6 +371,7 @@ def bench_served(pkg, torch, args, dev, frames_per_tel=16, rate_hz=500.0):
     stats = srv.stats()
     srv.close()
     ok = [r for r in results if r["status"] == 0]
+    superseded = sum(1 for r in results if r["status"] == 10)
     lat = np.array([r["t_done"] - r["t_submit"] for r in ok]) * 1000.0
     span = max(r["t_done"] for r in ok) - t0
     kinds = {}
@@ -362,6 +381,8 @@ def bench_served(pkg, torch, args, dev, frames_per_tel=16, rate_hz=500.0):
     return {
         "telescopes": len(ids), "rate_hz_per_telescope": rate_hz, "seconds": args.serve_seconds,
         "frames_offered": len(sched), "frames_done": len(ok), "frames_refused_queue_full": full,
+        "frames_superseded": superseded, "policy": "latest frame (older waiting frames superseded)",
+        "cluster_size": c_s, "autotune_solves_per_s": tab_s,
         "solves_per_s": len(ok) / span,
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                        "max": float(lat.max())},

@@ -62,7 +62,9 @@ typedef enum {
   TOMO_ERR_TIMEOUT = 6,      /* reserved for waits with a deadline */
   TOMO_ERR_BREAKDOWN = 7,    /* p.Ap <= 0 or not finite during (P)CG: iterate frozen */
   TOMO_ERR_UNSUPPORTED = 8,  /* valid request this build does not implement */
-  TOMO_ERR_FULL = 9          /* a bounded queue is full (served frames of one telescope) */
+  TOMO_ERR_FULL = 9,         /* a bounded queue is full (served frames of one telescope) */
+  TOMO_ERR_SUPERSEDED = 10   /* a served frame skipped because a newer one of its telescope
+                                was waiting (latest-frame policy) */
 } tomo_status;
 
 /* One wavefront sensor (Sec. 2.1, Sec. 4.3). */
@@ -113,11 +115,26 @@ typedef struct {
   int precision;
 } tomo_plan_info;
 
+/* Launch shape of a plan (zero-initialise; every field 0 means the default). */
+typedef struct {
+  int cluster_size;            /* CTAs per layer in the transform kernels (one thread-block cluster
+                                  per layer): 0 = min(16, N_min/8); else a power of two in
+                                  [1, min(16, N_min/2)].  Large clusters give the lowest latency of
+                                  one solve, small ones the most solves per second in big batches */
+  int reserved[7];             /* must be 0 */
+} tomo_plan_options;
+
 /* Build a plan: validates `g`, copies every host input, builds the index
  * tables, the prior D and the Jacobi diagonal (Sec. 5.1, computed exactly on
  * the device), and allocates the workspace.  Synchronises `cuda_stream`.
  * On success *out owns device memory until tomo_destroy. */
 tomo_status tomo_plan_create(const tomo_geometry *g, void *cuda_stream, tomo_plan **out);
+
+/* tomo_plan_create with launch options (NULL: the defaults).  TOMO_ERR_ARG for a
+ * cluster size that is not allowed; TOMO_ERR_UNSUPPORTED when the layer grids do
+ * not fit one CTA's shared memory at that cluster size. */
+tomo_status tomo_plan_create_ex(const tomo_geometry *g, const tomo_plan_options *opt,
+                                void *cuda_stream, tomo_plan **out);
 
 /* One frame (Sec. 5.1): b = A~^T C^-1 s from d_slopes, r0 = b - (A~^T C^-1 A~ + alpha D) x0,
  * then exactly `iters` (P)CG iterations (Hestenes-Stiefel).
@@ -228,7 +245,7 @@ typedef struct {
 } tomo_frame_result;
 
 typedef struct {
-  long long frames_submitted, frames_done, launches;
+  long long frames_submitted, frames_done, frames_superseded, launches;
   long long bytes_in_use;      /* plans + telescope slots + batch tables (device) */
   long long budget_bytes;
   int telescopes;              /* admitted */
@@ -250,6 +267,16 @@ tomo_status tomo_server_create(size_t budget_bytes, int iters, int max_in_flight
  * wait meanwhile.  *telescope: the new id (ids are never reused).  The first
  * frame starts from x0 = 0. */
 tomo_status tomo_server_admit(tomo_server *s, const tomo_geometry *g, int *telescope);
+
+/* tomo_server_admit with plan launch options (NULL: the defaults). */
+tomo_status tomo_server_admit_ex(tomo_server *s, const tomo_geometry *g, const tomo_plan_options *opt,
+                                 int *telescope);
+
+/* Frame policy: 0 (default) solves every frame of a telescope in order; 1 solves
+ * only the newest waiting frame when a launch is formed and reports the older
+ * waiting ones as TOMO_ERR_SUPERSEDED (the real-time choice when the stream
+ * outruns the solver: a stale frame's reconstruction is never applied). */
+tomo_status tomo_server_set_policy(tomo_server *s, int latest_only);
 
 /* Release a telescope and its memory (waits for its frame in flight; frames
  * still waiting are dropped and not reported). */

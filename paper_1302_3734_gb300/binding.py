@@ -17,7 +17,8 @@ LIB_PATH = os.path.join(_HERE, "libtomo.so")
 
 STATUS = {0: "TOMO_OK", 1: "TOMO_ERR_ARG", 2: "TOMO_ERR_GEOMETRY", 3: "TOMO_ERR_LEVELS",
           4: "TOMO_ERR_NOMEM", 5: "TOMO_ERR_CUDA", 6: "TOMO_ERR_TIMEOUT",
-          7: "TOMO_ERR_BREAKDOWN", 8: "TOMO_ERR_UNSUPPORTED", 9: "TOMO_ERR_FULL"}
+          7: "TOMO_ERR_BREAKDOWN", 8: "TOMO_ERR_UNSUPPORTED", 9: "TOMO_ERR_FULL",
+          10: "TOMO_ERR_SUPERSEDED"}
 
 KERNEL_KINDS = ("synthesis", "forward", "analysis", "update", "other")
 
@@ -59,9 +60,13 @@ class FrameResult(ctypes.Structure):
 
 class ServerStats(ctypes.Structure):
     _fields_ = [("frames_submitted", ctypes.c_longlong), ("frames_done", ctypes.c_longlong),
-                ("launches", ctypes.c_longlong), ("bytes_in_use", ctypes.c_longlong),
+                ("frames_superseded", ctypes.c_longlong), ("launches", ctypes.c_longlong), ("bytes_in_use", ctypes.c_longlong),
                 ("budget_bytes", ctypes.c_longlong), ("telescopes", ctypes.c_int),
                 ("in_flight", ctypes.c_int)]
+
+
+class PlanOptions(ctypes.Structure):
+    _fields_ = [("cluster_size", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -77,6 +82,8 @@ _VP = ctypes.c_void_p
 _I = ctypes.c_int
 SIGNATURES = [
     ("tomo_plan_create", _I, [ctypes.POINTER(Geometry), _VP, ctypes.POINTER(_VP)]),
+    ("tomo_plan_create_ex", _I, [ctypes.POINTER(Geometry), ctypes.POINTER(PlanOptions), _VP,
+                                 ctypes.POINTER(_VP)]),
     ("tomo_solve", _I, [_VP, _VP, _VP, _I, _I, _VP, ctypes.POINTER(ctypes.c_double)]),
     ("tomo_solve_batch", _I, [ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP),
                               _I, _I, _I, _VP]),
@@ -98,6 +105,9 @@ SIGNATURES = [
     ("tomo_version", ctypes.c_char_p, []),
     ("tomo_server_create", _I, [ctypes.c_size_t, _I, _I, _I, _I, ctypes.POINTER(_VP)]),
     ("tomo_server_admit", _I, [_VP, ctypes.POINTER(Geometry), ctypes.POINTER(_I)]),
+    ("tomo_server_admit_ex", _I, [_VP, ctypes.POINTER(Geometry), ctypes.POINTER(PlanOptions),
+                                  ctypes.POINTER(_I)]),
+    ("tomo_server_set_policy", _I, [_VP, _I]),
     ("tomo_server_release", _I, [_VP, _I]),
     ("tomo_server_submit", _I, [_VP, _I, _VP, ctypes.c_longlong]),
     ("tomo_server_poll", _I, [_VP, ctypes.POINTER(FrameResult), _I]),
@@ -178,11 +188,14 @@ def geometry_struct(geom):
 class Plan:
     """One adaptive-optics system: tables, prior, Jacobi diagonal and workspace on the GPU."""
 
-    def __init__(self, geom, stream=None):
+    def __init__(self, geom, stream=None, cluster_size=0):
         lib = load_library()
         g, keep = geometry_struct(geom)
         h = ctypes.c_void_p()
-        _check(lib.tomo_plan_create(ctypes.byref(g), _stream(stream), ctypes.byref(h)))
+        opt = PlanOptions()
+        opt.cluster_size = int(cluster_size)
+        _check(lib.tomo_plan_create_ex(ctypes.byref(g), ctypes.byref(opt), _stream(stream),
+                                       ctypes.byref(h)))
         self._h = h
         self.info = self._info()
         self.n = int(self.info.n_coeffs)
@@ -310,13 +323,15 @@ class Server:
         self._info = {}
         self._buf = (FrameResult * 4096)()
 
-    def admit(self, geom):
+    def admit(self, geom, cluster_size=0):
         """Admit a telescope; returns its id (TomoError with status TOMO_ERR_NOMEM when the
         budget does not allow it)."""
         lib = load_library()
         g, keep = geometry_struct(geom)
         tid = ctypes.c_int(-1)
-        _check(lib.tomo_server_admit(self._h, ctypes.byref(g), ctypes.byref(tid)))
+        opt = PlanOptions()
+        opt.cluster_size = int(cluster_size)
+        _check(lib.tomo_server_admit_ex(self._h, ctypes.byref(g), ctypes.byref(opt), ctypes.byref(tid)))
         del keep
         plan = ctypes.c_void_p()
         _check(lib.tomo_server_get_plan(self._h, tid.value, ctypes.byref(plan)))
@@ -327,6 +342,11 @@ class Server:
 
     def info(self, telescope):
         return self._info[telescope]
+
+    def set_policy(self, latest_only):
+        """True: solve only the newest waiting frame of a telescope; older ones come back with
+        status TOMO_ERR_SUPERSEDED."""
+        _check(load_library().tomo_server_set_policy(self._h, int(bool(latest_only))))
 
     def release(self, telescope):
         _check(load_library().tomo_server_release(self._h, int(telescope)))

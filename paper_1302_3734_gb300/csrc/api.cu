@@ -407,13 +407,23 @@ const char *tomo_last_error(void) { return g_err.c_str(); }
 long long tomo_launch_count(void) { return g_launches.load(); }
 
 tomo_status tomo_plan_create(const tomo_geometry *g, void *cuda_stream, tomo_plan **out) {
+  return tomo_plan_create_ex(g, nullptr, cuda_stream, out);
+}
+
+tomo_status tomo_plan_create_ex(const tomo_geometry *g, const tomo_plan_options *opt, void *cuda_stream,
+                                tomo_plan **out) {
   if (!out) return fail(TOMO_ERR_ARG, "out is NULL");
   *out = nullptr;
+  int creq = 0;
+  if (opt) {
+    for (int r : opt->reserved)
+      if (r != 0) return fail(TOMO_ERR_ARG, "tomo_plan_options.reserved must be zero");
+    if (opt->cluster_size < 0) return fail(TOMO_ERR_ARG, "cluster size must be >= 0");
+    creq = opt->cluster_size;
+  }
   tomo_plan *p = new (std::nothrow) tomo_plan();
   if (!p) return fail(TOMO_ERR_NOMEM, "host allocation failed");
   std::string err;
-  int creq = 0;
-  if (const char *env = std::getenv("TOMO_CLUSTER_SIZE")) creq = std::atoi(env);
   tomo_status st = build_host_plan(g, &p->hp, &err, creq);
   if (st != TOMO_OK) {
     delete p;

@@ -102,7 +102,8 @@ struct tomo_server {
   std::list<tomo_frame_result> results;
   int paused = 0;
   bool stop = false;
-  long long submitted = 0, done = 0, dropped = 0, launches = 0;
+  int latest_only = 0;
+  long long submitted = 0, done = 0, dropped = 0, superseded = 0, launches = 0;
 
   std::thread worker, completer;
 };
@@ -174,6 +175,16 @@ void worker_main(tomo_server *S) {
     for (auto &kv : S->tels) {
       Telescope *t = kv.second;
       if (t->busy || t->queue.empty()) continue;
+      if (S->latest_only) {
+        const double tnow = now_s();
+        while (t->queue.size() > 1) {
+          const Waiting old = t->queue.front();
+          t->queue.pop_front();
+          t->free_in.push_back(old.in_slot);
+          S->results.push_back({t->id, TOMO_ERR_SUPERSEDED, old.tag, old.t_submit, tnow, tnow, 0, -1});
+          ++S->superseded;
+        }
+      }
       const Waiting w = t->queue.front();
       t->queue.pop_front();
       t->busy = true;
@@ -373,11 +384,23 @@ tomo_status tomo_server_create(size_t budget_bytes, int iters, int max_in_flight
 }
 
 tomo_status tomo_server_admit(tomo_server *S, const tomo_geometry *g, int *telescope) {
+  return tomo_server_admit_ex(S, g, nullptr, telescope);
+}
+
+tomo_status tomo_server_set_policy(tomo_server *S, int latest_only) {
+  if (!S) return set_error(TOMO_ERR_ARG, "server is NULL");
+  std::lock_guard<std::mutex> lk(S->mu);
+  S->latest_only = latest_only ? 1 : 0;
+  return TOMO_OK;
+}
+
+tomo_status tomo_server_admit_ex(tomo_server *S, const tomo_geometry *g, const tomo_plan_options *opt,
+                                 int *telescope) {
   if (!S || !g || !telescope) return set_error(TOMO_ERR_ARG, "server, geometry and telescope must not be NULL");
   std::lock_guard<std::mutex> admin(S->admin_mu);
   cudaSetDevice(S->device);
   Telescope *t = new Telescope();
-  tomo_status st = tomo_plan_create(g, S->admin_stream, &t->plan);
+  tomo_status st = tomo_plan_create_ex(g, opt, S->admin_stream, &t->plan);
   if (st != TOMO_OK) {
     delete t;
     return st;
@@ -507,7 +530,7 @@ tomo_status tomo_server_drain(tomo_server *S, double timeout_s) {
   if (!S) return set_error(TOMO_ERR_ARG, "server is NULL");
   std::unique_lock<std::mutex> lk(S->mu);
   const bool ok = S->cv_idle.wait_for(lk, std::chrono::duration<double>(timeout_s), [&] {
-    return S->inflight.empty() && !ready(S) && S->done + S->dropped == S->submitted;
+    return S->inflight.empty() && !ready(S) && S->done + S->dropped + S->superseded == S->submitted;
   });
   return ok ? TOMO_OK : set_error(TOMO_ERR_TIMEOUT, "drain: frames still waiting or in flight");
 }
@@ -517,6 +540,7 @@ tomo_status tomo_server_get_stats(tomo_server *S, tomo_server_stats *out) {
   std::lock_guard<std::mutex> lk(S->mu);
   out->frames_submitted = S->submitted;
   out->frames_done = S->done;
+  out->frames_superseded = S->superseded;
   out->launches = S->launches;
   out->bytes_in_use = static_cast<long long>(used_bytes(S));
   out->budget_bytes = static_cast<long long>(S->budget);

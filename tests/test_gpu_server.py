@@ -9,6 +9,8 @@ sizes, admitted by memory, solved warm-started and batched on arrival.
   drain.
 """
 
+import time
+
 import numpy as np
 import pytest
 
@@ -26,7 +28,7 @@ def _geoms():
     small = configs.small_lgs_config(16, 32, 3, 2)
     ragged = configs.small_lgs_config(24, 64, 2, 3, order=2)
     cfg0 = configs.config0()
-    cfg0 = dict(cfg0, precision=0, precond=1, name=cfg0["name"] + "-fp32")
+    cfg0 = dict(cfg0, precision=0, precond=1, name=cfg0["name"].replace("fp64", "fp32-pcg"))
     return [small, ragged, cfg0]
 
 
@@ -155,4 +157,26 @@ def test_bounded_queue_release_and_drain(lib):
     srv.drain(60.0)
     srv.poll()
     assert srv.stats()["telescopes"] == 1
+    srv.close()
+
+
+def test_latest_frame_policy_supersedes_stale_frames(lib):
+    torch, pkg = lib
+    g = configs.small_lgs_config(16, 32, 3, 2)
+    srv = pkg.Server(iters=3000, queue_depth=8, result_slots=4)
+    srv.set_policy(latest_only=True)
+    tid = srv.admit(g)
+    s = np.ones(srv.info(tid).n_slopes, dtype=np.float32)
+    assert srv.submit(tid, s, tag=0)
+    t0 = time.monotonic()
+    while srv.stats()["in_flight"] == 0 and time.monotonic() - t0 < 5.0:
+        time.sleep(0.0005)
+    assert srv.stats()["in_flight"] == 1   # frame 0 runs (3000 iterations); 1..4 wait behind it
+    for k in range(1, 5):
+        assert srv.submit(tid, s, tag=k)
+    srv.drain(60.0)
+    res = {r["tag"]: r for r in srv.poll()}
+    assert res[0]["status"] == 0 and res[4]["status"] == 0      # the running frame and the newest
+    assert [res[k]["status"] for k in (1, 2, 3)] == [10, 10, 10]  # superseded
+    assert srv.stats()["frames_superseded"] == 3
     srv.close()

@@ -113,3 +113,20 @@ def test_server_argument_validation_without_gpu(lib):
     assert lib.tomo_server_poll(None, None, 4) == 0
     lib.tomo_server_destroy(None)
     assert lib.tomo_server_clock() > 0.0
+
+
+def test_plan_options_validation_without_gpu(lib):
+    import ctypes
+    from synth import configs
+    from paper_1302_3734_gb300.binding import geometry_struct, PlanOptions
+    g, keep = geometry_struct(configs.small_lgs_config())
+    h = ctypes.c_void_p()
+    opt = PlanOptions()
+    opt.reserved[3] = 1
+    assert lib.tomo_plan_create_ex(ctypes.byref(g), ctypes.byref(opt), None, ctypes.byref(h)) == 1
+    opt = PlanOptions()
+    for bad in (3, 32, 17):            # not a power of two, too large
+        opt.cluster_size = bad
+        assert lib.tomo_plan_create_ex(ctypes.byref(g), ctypes.byref(opt), None, ctypes.byref(h)) == 1
+        assert "cluster size" in lib.tomo_last_error().decode()
+    assert not h.value
