@@ -82,6 +82,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--batch", type=int, default=16, help="E-ELT instances per batched solve")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-large", action="store_true", help="skip the 100 m configuration")
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="length of the served 16-telescope stream (0: skip it)")
     return ap.parse_args()
@@ -277,6 +278,47 @@ def bench_batched(pkg, torch, geom, slopes, flush, iters, args, peak, dev):
                        "coefficients": int(sum(p.n for p in plans)),
                        "achieved_GBps_per_iteration_bytes": bytes_it * 10 / (ms / 1000.0) / 1e9,
                        "frac_of_hbm_peak": bytes_it * 10 / (ms / 1000.0) / 1e9 / peak}
+    for p in plans:
+        p.close()
+    return out
+
+
+def bench_large(pkg, torch, dev, flush, peak, steps=5, warmup=2):
+    """The 100 m stress configuration (35 layers of 512^2, db4 J=5, 20 PCG iterations):
+    one instance, and a batch of four."""
+    from synth import configs, gaussian_noise
+    g = configs.config4()
+    iters = int(g["iters"])
+    out = {"workload": "100 m, 9 LGS 200x200 + 3 TT NGS, 35 layers 512^2, db4 J=5, Jacobi PCG "
+                       f"{iters} it, cold start", "n_coeffs": sum(l["N"] ** 2 for l in g["layers"])}
+    plans = [pkg.Plan(g) for _ in range(4)]
+    sl = [torch.tensor(gaussian_noise(plans[0].n_slopes, 0.3, 6_000_000 + i), dtype=torch.float32,
+                       device=dev) for i in range(4)]
+    xs = [torch.zeros(plans[0].n, dtype=torch.float32, device=dev) for _ in range(4)]
+    bytes_it = plans[0].info.bytes_per_iteration
+    for label, k in (("single", 1), ("batch4", 4)):
+        def once():
+            if k == 1:
+                plans[0].solve(sl[0], xs[0], iters, warm=False)
+            else:
+                pkg.solve_batch(plans, sl, xs, iters, warm=False)
+        for _ in range(warmup):
+            once()
+        torch.cuda.synchronize()
+        t = []
+        for j in range(steps):
+            flush.fill_(float(j))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            once()
+            e1.record()
+            t.append((e0, e1))
+        torch.cuda.synchronize()
+        ms = float(np.mean([a.elapsed_time(b) for a, b in t]))
+        gbs = k * bytes_it * iters / (ms / 1000.0) / 1e9
+        out[label] = {"solves_per_s": k * 1000.0 / ms, "ms": ms, "achieved_GBps_per_iteration_bytes": gbs,
+                      "frac_of_hbm_peak": gbs / peak}
     for p in plans:
         p.close()
     return out
@@ -540,6 +582,8 @@ def main():
     }
     if not args.no_batch:
         line["batched"] = bench_batched(pkg, torch, geom, slopes, flush, iters, args, peak, dev)
+    if not args.no_large and rank == 0:
+        line["large"] = bench_large(pkg, torch, dev, flush, peak)
     if args.serve_seconds > 0 and rank == 0:
         line["served"] = bench_served(pkg, torch, args, dev)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

@@ -76,7 +76,7 @@ namespace {
 
 // Launch one kernel through `fn`, bracketed by timing events when enabled.
 template <typename F>
-tomo_status timed(tomo_plan *p, int kind, cudaStream_t s, F fn, const char *what) {
+tomo_status timed(tomo_plan *p, int kind, cudaStream_t s, F fn, const char *what, int kernels = 1) {
   cudaEvent_t a = nullptr, b = nullptr;
   if (p && p->timer.on) {
     a = p->timer.get();
@@ -85,7 +85,7 @@ tomo_status timed(tomo_plan *p, int kind, cudaStream_t s, F fn, const char *what
   }
   cudaError_t e = fn();
   if (e != cudaSuccess) return cuda_fail(e, what);
-  g_launches.fetch_add(1);
+  g_launches.fetch_add(kernels);
   if (p && p->timer.on) {
     cudaEventRecord(b, s);
     p->timer.recs.push_back({kind, a, b});
@@ -132,9 +132,9 @@ tomo_status enqueue_solve(tomo_plan *tp, const LaunchSet &L, const void *const *
     }
     TOMO_TRY(timed(tp, kKindAnalysis, s, [&] {
       return launch_analysis(L.precision, 1, 2, L.lf, warm ? kFlagWarm : 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem_a,
-                             io, s);
-    }, "analysis (residual)"));
-    ++nk;
+                             io, s, L.split, L.smem_g);
+    }, "analysis (residual)", analysis_launches(1, L.split)));
+    nk += analysis_launches(1, L.split);
   }
   for (int it = 0; it < iters; ++it) {
     IoArgs none{};
@@ -147,15 +147,15 @@ tomo_status enqueue_solve(tomo_plan *tp, const LaunchSet &L, const void *const *
       return launch_forward(L.precision, 0, L.max_layers, L.d_inst, L.fwd, L.n_fwd, none, s);
     }, "forward"));
     TOMO_TRY(timed(tp, kKindAnalysis, s, [&] {
-      return launch_analysis(L.precision, 1, 1, L.lf, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem_a, none, s);
-    }, "analysis"));
+      return launch_analysis(L.precision, 1, 1, L.lf, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem_a, none, s, L.split, L.smem_g);
+    }, "analysis", analysis_launches(1, L.split)));
     IoArgs io{};
     io.active = active;
     for (int i = 0; i < L.count; ++i) io.out0[i] = x[i];
     TOMO_TRY(timed(tp, kKindUpd, s, [&] {
       return launch_update(L.precision, it << kIterShift, L.d_inst, L.upd, L.n_upd, io, s);
     }, "update"));
-    nk += 4;
+    nk += 3 + analysis_launches(1, L.split);
   }
   if (n_kernels) *n_kernels = nk;
   return TOMO_OK;
@@ -262,6 +262,7 @@ tomo_status build_batch(tomo_plan *const *plans, int count, Batch **out) {
     for (auto &cand : b->groups) {
       const HostPlan &H0 = plans[cand.members[0]]->hp;
       if (H0.C == H.C && H0.Lf == H.Lf && H0.precision == H.precision &&
+          H0.gather_staged == H.gather_staged &&
           static_cast<int>(cand.members.size()) < kMaxBatch)
         g = &cand;
     }
@@ -297,6 +298,8 @@ tomo_status build_batch(tomo_plan *const *plans, int count, Batch **out) {
       L.C = H.C;
       L.lf = H.Lf;
       L.precision = H.precision;
+      L.split = H.gather_staged ? 0 : 1;
+      L.smem_g = std::max(L.smem_g, static_cast<size_t>(H.smem_gather));
     }
     Arena A;
     const size_t o_i = A.take(sizeof(InstDev) * insts.size());
@@ -469,6 +472,7 @@ tomo_status tomo_plan_create_ex(const tomo_geometry *g, const tomo_plan_options 
   const size_t o_vsrun = A.take(sizeof(int4) * std::max<size_t>(1, H.vs_run.size()));
   const size_t o_stage = A.take(std::max<size_t>(16, H.stage_img.size()));
   const size_t o_eslot = A.take(sizeof(EdgeSlot) * H.edge_slots.size());
+  const size_t o_gtcols = A.take(sizeof(int2) * std::max<size_t>(1, H.gt_cols.size()));
   const size_t o_ttseg = A.take(sizeof(int2) * H.tt_seg.size());
   const size_t o_ttnode = A.take(sizeof(int) * std::max<size_t>(1, H.tt_node.size()));
   const size_t o_ttbeg = A.take(sizeof(int) * H.tt_beg.size());
@@ -541,6 +545,7 @@ tomo_status tomo_plan_create_ex(const tomo_geometry *g, const tomo_plan_options 
   I.vstage = H.vstage;
   I.stage_img = base + o_stage;
   I.edge_slots = reinterpret_cast<const EdgeSlot *>(base + o_eslot);
+  I.gt_cols = reinterpret_cast<const int2 *>(base + o_gtcols);
   I.img_stride = H.img_stride;
   I.tt_seg = reinterpret_cast<const int2 *>(base + o_ttseg);
   I.tt_node = reinterpret_cast<const int *>(base + o_ttnode);
@@ -606,6 +611,7 @@ tomo_status tomo_plan_create_ex(const tomo_geometry *g, const tomo_plan_options 
   put(o_vsrun, H.vs_run.data(), sizeof(int4) * H.vs_run.size());
   put(o_stage, H.stage_img.data(), H.stage_img.size());
   put(o_eslot, H.edge_slots.data(), sizeof(EdgeSlot) * H.edge_slots.size());
+  put(o_gtcols, H.gt_cols.data(), sizeof(int2) * H.gt_cols.size());
   put_real(o_ttw, H.tt_w);
   put(o_gtoff, H.gt_off.data(), sizeof(int) * H.gt_off.size());
   put(o_ttseg, H.tt_seg.data(), sizeof(int2) * H.tt_seg.size());
@@ -672,6 +678,8 @@ tomo_status tomo_plan_create_ex(const tomo_geometry *g, const tomo_plan_options 
   L.upd = reinterpret_cast<const UpdItem *>(base + o_upd);
   L.n_upd = static_cast<int>(H.upd_items.size());
   L.precision = H.precision;
+  L.split = H.gather_staged ? 0 : 1;
+  L.smem_g = static_cast<size_t>(H.smem_gather);
   *out = p;
   g_err.clear();
   return TOMO_OK;
@@ -704,8 +712,8 @@ tomo_status tomo_plan_get_info(const tomo_plan *p, tomo_plan_info *out) {
   out->n_layers = H.n_layers;
   out->n_wfs = H.n_wfs;
   out->cluster_size = H.C;
-  out->kernels_per_iteration = 4;
-  out->kernels_per_solve_base = 3;
+  out->kernels_per_iteration = 3 + analysis_launches(1, p->ls.split);
+  out->kernels_per_solve_base = 2 + analysis_launches(1, p->ls.split);
   out->device_bytes = static_cast<long long>(p->arena_bytes);
   // p-update + W^-1 (r, J^-1, p in; p, phi out), ray-trace (phi in, v out),
   // gather + W + prior (v, p in; q out), update (x, p, r, q, J^-1 in; x, r out)
@@ -825,7 +833,7 @@ tomo_status tomo_layers_to_coeffs(tomo_plan *p, const void *d_layers, void *d_co
   io.in0[0] = d_layers;
   io.out0[0] = d_coeffs;
   return timed(p, kKindAnalysis, s, [&] {
-    return launch_analysis(L.precision, 0, 0, L.lf, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem_a, io, s);
+    return launch_analysis(L.precision, 0, 0, L.lf, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem_a, io, s, L.split, L.smem_g);
   }, "analysis");
 }
 
@@ -861,8 +869,8 @@ tomo_status tomo_apply_normal(tomo_plan *p, const void *d_in, void *d_out, void 
   c.in1[0] = d_in;
   c.out0[0] = d_out;
   return timed(p, kKindAnalysis, s, [&] {
-    return launch_analysis(L.precision, 1, 1, L.lf, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem_a, c, s);
-  }, "analysis");
+    return launch_analysis(L.precision, 1, 1, L.lf, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem_a, c, s, L.split, L.smem_g);
+  }, "analysis", analysis_launches(1, L.split));
 }
 
 tomo_status tomo_rhs(tomo_plan *p, const void *d_slopes, void *d_out, void *cuda_stream) {
@@ -879,8 +887,8 @@ tomo_status tomo_rhs(tomo_plan *p, const void *d_slopes, void *d_out, void *cuda
   c.out0[0] = d_out;
   c.in1[0] = d_slopes;
   return timed(p, kKindAnalysis, s, [&] {
-    return launch_analysis(L.precision, 1, 0, L.lf, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem_a, c, s);
-  }, "analysis");
+    return launch_analysis(L.precision, 1, 0, L.lf, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem_a, c, s, L.split, L.smem_g);
+  }, "analysis", analysis_launches(1, L.split));
 }
 
 tomo_status tomo_jacobi_diagonal(tomo_plan *p, double *d_out, void *cuda_stream) {

@@ -14,7 +14,11 @@ constexpr int kMaxLevels = 12;
 constexpr int kFwdTile = 16;       // corners per side of a forward tile
 constexpr int kMaxBatch = 96;      // instances per launch (kernel-argument arrays)
 constexpr int kThreads = 256;      // threads per CTA of the hot kernels (transforms: below)
-constexpr int kAnalysisThreads = 512;  // threads per CTA of the gather + analysis kernel
+constexpr int kAnalysisThreads = 512;  // threads per CTA of the gather + analysis kernel when two fit an SM
+constexpr int kAnalysisThreadsMax = 1024;  // ... when its shared memory leaves room for one
+constexpr int kSynthThreads = 512;     // threads per CTA of the synthesis kernel (at most)
+constexpr int kGatherThreads = 512;    // threads per CTA of the separate gather kernel
+constexpr int kMaxGatherSensors = 64;  // dense sensors the separate gather kernel stages
 constexpr int kUpdChunk = 1024;    // coefficients per CTA of the vector update
 constexpr int kMaxTapsNode = 4;    // corners per axis whose bilinear taps reach one node
 
@@ -92,6 +96,7 @@ struct InstDev {
   const int *gt_ys;             // per row record: its window start in the staged v rows
   const int4 *vs_run;           // per (layer, rank, dense sensor): v run {g0, 16-byte words, smem offset}
   int vstage, pad_vs;           // staged v elements per analysis CTA
+  const int2 *gt_cols;          // per (m,l): columns [x, x+y) mod N_l that the sensor's taps reach
   const void *stage_img;        // per (layer, rank): the CTA's stage image (img_stride bytes apart)
   long long img_stride;
   // Pupil-edge corrections: a tip/tilt-only sensor's corner field is

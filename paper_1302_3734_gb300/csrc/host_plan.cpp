@@ -433,6 +433,28 @@ tomo_status build_host_plan(const tomo_geometry *geo, HostPlan *P, std::string *
         }
       }
   }
+  // per (sensor, layer): the columns its taps reach, one run mod N (all
+  // columns when the valid records do not form one run)
+  P->gt_cols.assign(static_cast<size_t>(P->n_wfs) * P->n_layers, make_int2(0, 0));
+  for (int m = 0; m < P->n_wfs; ++m)
+    for (int l = 0; l < P->n_layers; ++l) {
+      const int go = P->gt_off[m * P->n_layers + l];
+      if (go < 0) continue;
+      const int N = P->layers[l].N;
+      int nv = 0, c0 = -1;
+      for (int i = 0; i < N; ++i) {
+        const bool v = P->gt_ro[go + i] >= 0;
+        nv += v ? 1 : 0;
+        if (v && P->gt_ro[go + (i + N - 1) % N] < 0 && c0 < 0) c0 = i;
+      }
+      int2 cols = make_int2(0, nv == 0 ? 0 : N);
+      if (nv > 0 && nv < N && c0 >= 0) {
+        int run = 0;
+        while (run < N && P->gt_ro[go + (c0 + run) % N] >= 0) ++run;
+        if (run == nv) cols = make_int2(c0, nv);
+      }
+      P->gt_cols[m * P->n_layers + l] = cols;
+    }
   if (P->n_edge_wfs > 64) {
     *err = "more than 64 sensors with tip/tilt removal or tip/tilt-only measurement";
     return TOMO_ERR_UNSUPPORTED;
@@ -532,6 +554,16 @@ tomo_status build_host_plan(const tomo_geometry *geo, HostPlan *P, std::string *
     }
     P->gather_staged = fits ? 1 : 0;
     P->smem_analysis = fits ? need : P->smem_transform;
+    for (const auto &d : P->layers)
+      P->smem_gather = std::max<long long>(P->smem_gather, static_cast<long long>(d.N / P->C) * d.N * esz);
+    if (!fits && P->smem_gather > 220LL * 1024) {
+      *err = "layer grids too large for the separate gather kernel's band buffer";
+      return TOMO_ERR_UNSUPPORTED;
+    }
+    if (!fits && P->n_dense > kMaxGatherSensors) {
+      *err = "more than 64 sensors with a dense corner field on layer grids too large for the staged gather";
+      return TOMO_ERR_UNSUPPORTED;
+    }
   }
   // the stage images, one per analysis CTA
   if (P->gather_staged) {

@@ -38,6 +38,8 @@ struct HostPlan {
   std::vector<int> gt_ro;
   std::vector<double> gt_rw;       // 4 per record, 0 beyond the window's taps
   std::vector<int> gt_ys;          // row records: window start in the CTA's staged v rows
+  std::vector<int2> gt_cols;       // per (m,l): columns [x, x+y) mod N that the sensor's taps reach
+  long long smem_gather = 0;       // dynamic shared memory of the separate gather kernel (bytes)
   std::vector<int4> vs_run;        // per (layer, rank, dense sensor): {g0, nvec, smem offset, 0}
   int vstage = 0;                  // largest staged v (T elements) of one analysis CTA
   std::vector<unsigned char> stage_img;   // per (layer, rank) stage image, img_stride bytes apart

@@ -820,6 +820,100 @@ __device__ void gather_rows_staged(const InstDev &I, const GatherStage<T> &st, i
   gather_edges<T>(st.nn(), st.tn, st.tb, st.tk, st.tw, A, s_coef);
 }
 
+// The gather of one CTA band (layer l, rows [k0, k0+R0)) from the tap records
+// and corner fields in global memory, into the band buffer A (shared memory):
+// sensor by sensor, over the band rows and only the columns the sensor's taps
+// reach (gt_cols), then the pupil-edge list.  Each node receives the sensors'
+// terms in sensor order, as the fused gathers do.  For plans whose tables do
+// not fit the analysis CTAs' shared memory; k_gather runs it.
+template <typename T, int KT>
+__device__ void gather_band_global(const InstDev &I, int l, int N, int R0, int crank, T *A,
+                                   const T *s_coef, const int *s_go, const int *s_nc, const int2 *s_cols,
+                                   int Md) {
+  constexpr int RS = TapRec<T, KT>::RS;
+  const int nt = blockDim.x, tid = threadIdx.x, k0 = crank * R0;
+  const T *vv = static_cast<const T *>(I.v);
+  const T *rec = static_cast<const T *>(I.gt_rec);
+  for (int node = tid; node < R0 * N; node += nt) A[node] = T(0);
+  __syncthreads();
+  for (int md = 0; md < Md; ++md) {
+    const int2 cols = s_cols[md];
+    if (cols.y == 0) continue;
+    // threads per row: the power of two >= the column count (at most nt)
+    int tpr = 1;
+    while (tpr < cols.y && tpr < nt) tpr <<= 1;
+    const int rows_per_pass = nt / tpr, ci = tid % tpr;
+    const T *xr = rec + static_cast<size_t>(s_go[md]) * RS;
+    const T *yr = rec + static_cast<size_t>(s_go[md] + N + k0) * RS;
+    for (int kl = tid / tpr; kl < R0; kl += rows_per_pass) {
+      TapRec<T, KT> y;
+      y.load(yr + kl * RS);
+      if (y.off < 0) continue;
+      for (int c = ci; c < cols.y; c += tpr) {
+        const int i = (cols.x + c) & (N - 1);
+        TapRec<T, KT> x;
+        x.load(xr + i * RS);
+        if (x.off >= 0) A[kl * N + i] += window_sum<T, KT, false>(vv + y.off + x.off, s_nc[md], x, y);
+      }
+    }
+    __syncthreads();
+  }
+  if (I.n_edge_wfs == 0) return;
+  const int2 seg = I.tt_seg[l * I.C + crank];
+  gather_edges<T>(seg.y - seg.x, I.tt_node + seg.x, I.tt_beg + seg.x, I.tt_k,
+                  static_cast<const T *>(I.tt_w), A, s_coef);
+  __syncthreads();
+}
+
+// ------------------------------------------------------------- k_gather
+// g = sum_m P_m^T v_m (Sec. 5.1, the transposed ray-trace) into the plan's phi
+// buffer, one CTA per (instance, layer, band of N/C rows), for plans whose
+// gather tables are not staged in the analysis kernel; k_analysis with SRC 2
+// then transforms it.  phi is free here: the forward kernel that read it has
+// finished (dependency wait) and the next synthesis rewrites it.
+// tt_mode as in edge_coefficients; io.in1: the slopes (tip/tilt-only data).
+template <typename T>
+__global__ void __launch_bounds__(kGatherThreads) k_gather(const InstDev *__restrict__ insts,
+                                                           const ClusterItem *__restrict__ items,
+                                                           IoArgs io, int C, int tt_mode) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ InstDev sI;
+  __shared__ T s_coef[2 * 64];
+  __shared__ int s_go[kMaxGatherSensors], s_nc[kMaxGatherSensors];
+  __shared__ int2 s_cols[kMaxGatherSensors];
+  __shared__ int s_md;
+  pdl_trigger();
+  const ClusterItem it = items[blockIdx.x / C];
+  const int crank = blockIdx.x % C;
+  if (io.active && !io.active[it.inst]) return;
+  load_inst(&sI, insts + it.inst);
+  const InstDev &I = sI;
+  if (threadIdx.x == 0) {
+    int md = 0;
+    for (int m = 0; m < I.n_wfs && md < kMaxGatherSensors; ++m) {
+      const WfsDev &W = I.wfs[m];
+      if (W.kind == kTTOnly) continue;
+      s_go[md] = I.gt_off[m * I.n_layers + it.layer];
+      s_nc[md] = W.nc;
+      s_cols[md] = I.gt_cols[m * I.n_layers + it.layer];
+      ++md;
+    }
+    s_md = md;
+  }
+  const LayerDev &L = I.layers[it.layer];
+  const int N = L.N, R0 = N / C;
+  T *A = reinterpret_cast<T *>(smem_raw);
+  __syncthreads();
+  pdl_wait();
+  if (I.n_edge_wfs > 0)
+    edge_coefficients<T>(I, s_coef, tt_mode, static_cast<const T *>(io.in1[it.inst]));
+  if (I.max_taps <= 2) gather_band_global<T, 2>(I, it.layer, N, R0, crank, A, s_coef, s_go, s_nc, s_cols, s_md);
+  else if (I.max_taps == 3) gather_band_global<T, 3>(I, it.layer, N, R0, crank, A, s_coef, s_go, s_nc, s_cols, s_md);
+  else gather_band_global<T, 4>(I, it.layer, N, R0, crank, A, s_coef, s_go, s_nc, s_cols, s_md);
+  T *g = static_cast<T *>(I.phi) + L.off + crank * R0 * N;
+  for (int node = threadIdx.x; node < R0 * N; node += blockDim.x) g[node] = A[node];
+}
+
 // Epilogue of the analysis for one output coefficient.
 enum Epi : int { kEpiPlain = 0, kEpiOp = 1, kEpiResid = 2 };
 
@@ -831,46 +925,66 @@ struct Emit {
   T *R, *Pn, *X;   // resid: r, p, x
   const T *jinv;
   const T *cache;
-  const double *dalpha;
+  const T *dalpha; // alpha D per level
   int off, N, precond, warm;
   Acc<T> acc0, acc1;
-  __device__ __forceinline__ void operator()(int row, int col, int level, T w, int slot) {
+  // What the epilogue of (row, col) reads besides w: p (op) or x (warm
+  // residual), from the cache when slot >= 0, and J^-1 (residual).  Fetched
+  // ahead so that several outputs' loads are in flight together.
+  struct Pre {
+    T a, j;
+  };
+  __device__ __forceinline__ Pre fetch(int row, int col, int slot) const {
+    Pre f{T(0), T(1)};
+    const int idx = off + row * N + col;
+    if (EPI == kEpiOp) {
+      f.a = slot >= 0 ? cache[slot] : P[idx];
+    } else if (EPI == kEpiResid) {
+      if (warm) f.a = slot >= 0 ? cache[slot] : X[idx];
+      if (precond) f.j = jinv[idx];
+    }
+    return f;
+  }
+  __device__ __forceinline__ void put(int row, int col, int level, T w, const Pre &f) {
     const int idx = off + row * N + col;
     if (EPI == kEpiPlain) {
       out[idx] = w;
     } else if (EPI == kEpiOp) {
-      const T pv = slot >= 0 ? cache[slot] : P[idx];
-      const T q = w + T(dalpha[level]) * pv;
+      const T q = w + dalpha[level] * f.a;
       Q[idx] = q;
-      acc0.add_prod(pv, q);
+      acc0.add_prod(f.a, q);
     } else {
       T r = w;
-      if (warm) r -= T(dalpha[level]) * (slot >= 0 ? cache[slot] : X[idx]);
+      if (warm) r -= dalpha[level] * f.a;
       else X[idx] = T(0);
-      const T z = precond ? jinv[idx] * r : r;
+      const T z = precond ? f.j * r : r;
       R[idx] = r;
       Pn[idx] = z;
       acc0.add_prod(r, z);
       acc1.add_prod(r, r);
     }
   }
+  __device__ __forceinline__ void operator()(int row, int col, int level, T w, int slot) {
+    put(row, col, level, w, fetch(row, col, slot));
+  }
 };
 
 // ------------------------------------------------------------ k_analysis
 // SRC 0: layer grids from io.in0.  SRC 1: adjoint gather from the plan's v.
+// SRC 2: the gather k_gather left in the plan's phi.
 // EPI plain: io.out0 = W g.  EPI op: q = W g + alpha D p with p = io.in1 (NULL:
 // the plan's p), q = io.out0 (NULL: the plan's q); partial p.q per CTA.
 // EPI resid: r = W g - alpha D x (x = io.out0, zeroed when cold), p = z = J^-1 r;
 // partials r.z and r.r per CTA.
 template <typename T, int SRC, int EPI, int LF>
-__global__ void __launch_bounds__(kAnalysisThreads, 2) k_analysis(const InstDev *__restrict__ insts,
+__global__ void __launch_bounds__(kAnalysisThreadsMax, 1) k_analysis(const InstDev *__restrict__ insts,
                                                       const ClusterItem *__restrict__ items,
                                                       IoArgs io, int flags) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ InstDev sI;
   __shared__ CoefMap cm;
   __shared__ T s_coef[2 * 64];
-  __shared__ double s_dal[kMaxLevels + 1];
+  __shared__ T s_dal[kMaxLevels + 1];
   pdl_trigger();
   cg::cluster_group cluster = cg::this_cluster();
   const int C = static_cast<int>(cluster.num_blocks());
@@ -887,7 +1001,7 @@ __global__ void __launch_bounds__(kAnalysisThreads, 2) k_analysis(const InstDev 
   T *cb2 = cb + C * C;
   T *cache = reinterpret_cast<T *>(smem_raw) + transform_cache_offset(N, C);
   if (tid == 0) cm.init(N, C, J, L.cache_kc, crank);
-  if (tid <= J) s_dal[tid] = L.dalpha[tid];
+  if (tid <= J) s_dal[tid] = T(L.dalpha[tid]);
   Filt<T, LF> f;
   f.load(I);
 
@@ -935,8 +1049,9 @@ __global__ void __launch_bounds__(kAnalysisThreads, 2) k_analysis(const InstDev 
     cp_async_commit();
   }
   // own rows [crank*R0, (crank+1)*R0) of the layer grid
-  if (SRC == 0) {
-    const T *src = static_cast<const T *>(io.in0[it.inst]) + L.off + crank * R0 * N;
+  if (SRC == 0 || SRC == 2) {
+    const T *src = (SRC == 0 ? static_cast<const T *>(io.in0[it.inst]) : static_cast<const T *>(I.phi)) +
+                   L.off + crank * R0 * N;
     for (int idx = tid; idx < R0 * N; idx += nt) A[idx] = src[idx];
   } else {
     // the tip/tilt-only sensors' measurement term: model (operator), data
@@ -994,25 +1109,48 @@ __global__ void __launch_bounds__(kAnalysisThreads, 2) k_analysis(const InstDev 
     }
     cluster_arrive();
     __syncthreads();
-    // column pass (y), local
-    for (int idx = tid; idx < Rh * M; idx += nt) {
-      const int il = idx >> lgM, x = idx & (M - 1);
-      const int i = crank * Rh + il;
-      const T *col = B + 2 * il * M + x;
-      T lo = T(0), hi = T(0);
+    // column pass (y), local; the epilogue inputs of kColU outputs per thread
+    // are fetched before any of them is written
+    constexpr int kColU = SRC == 2 ? 4 : (SRC == 1 ? 1 : 2);
+    for (int idx0 = tid; idx0 < Rh * M; idx0 += kColU * nt) {
+      T lo[kColU], hi[kColU];
+      typename Emit<T, EPI>::Pre fa[kColU], fb[kColU];
 #pragma unroll
-      for (int t = 0; t < LF; ++t) {
-        const T val = col[t * M];
-        lo += f.h[t] * val;
-        hi += f.g[t] * val;
+      for (int u = 0; u < kColU; ++u) {
+        const int idx = idx0 + u * nt;
+        if (idx < Rh * M) {
+          const int il = idx >> lgM, x = idx & (M - 1);
+          const int i = crank * Rh + il;
+          const T *col = B + 2 * il * M + x;
+          T l = T(0), h = T(0);
+#pragma unroll
+          for (int t = 0; t < LF; ++t) {
+            const T val = col[t * M];
+            l += f.h[t] * val;
+            h += f.g[t] * val;
+          }
+          lo[u] = l;
+          hi[u] = h;
+          if (x >= H) fa[u] = emit.fetch(i, x, slot_hl(k, il, x));
+          else if (k == J) fa[u] = emit.fetch(i, x, use_cache ? cm.ll(il, x) : -1);
+          fb[u] = emit.fetch(H + i, x, slot_lh(k, il, x));
+        }
       }
-      if (x < H) {
-        if (k == J) emit(i, x, J, lo, use_cache ? cm.ll(il, x) : -1);
-        else A[il * H + x] = lo;
-      } else {
-        emit(i, x, k, lo, slot_hl(k, il, x));
+#pragma unroll
+      for (int u = 0; u < kColU; ++u) {
+        const int idx = idx0 + u * nt;
+        if (idx < Rh * M) {
+          const int il = idx >> lgM, x = idx & (M - 1);
+          const int i = crank * Rh + il;
+          if (x < H) {
+            if (k == J) emit.put(i, x, J, lo[u], fa[u]);
+            else A[il * H + x] = lo[u];
+          } else {
+            emit.put(i, x, k, lo[u], fa[u]);
+          }
+          emit.put(H + i, x, k, hi[u], fb[u]);
+        }
       }
-      emit(H + i, x, k, hi, slot_lh(k, il, x));
     }
     __syncthreads();
   }
@@ -1078,7 +1216,7 @@ __global__ void __launch_bounds__(kAnalysisThreads, 2) k_analysis(const InstDev 
 // p <- J^-1 r + beta p written back (it = 0: p already holds J^-1 r).
 // Output: io.out0 (NULL: the plan's phi).
 template <typename T, int SRC, int LF>
-__global__ void __launch_bounds__(kThreads) k_synthesis(const InstDev *__restrict__ insts,
+__global__ void __launch_bounds__(kSynthThreads, 1) k_synthesis(const InstDev *__restrict__ insts,
                                                        const ClusterItem *__restrict__ items,
                                                        IoArgs io, int flags) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1131,14 +1269,30 @@ __global__ void __launch_bounds__(kThreads) k_synthesis(const InstDev *__restric
   }
   __syncthreads();
   const T beta = SRC == 1 ? s_beta : T(0);
-  auto coef = [&](int row, int col) -> T {
+  // a coefficient of an uncached level: its loads (raw), then the direction
+  // update and its store (finish)
+  struct Raw {
+    T p, r, j;
+  };
+  auto raw = [&](int row, int col) -> Raw {
     const int idx = L.off + row * N + col;
-    if (SRC == 0) return src[idx];
-    if (first) return P[idx];
-    const T r = Rv[idx];
-    const T z = pre ? Jv[idx] * r : r;
-    const T pn = z + beta * P[idx];
-    P[idx] = pn;
+    Raw v{T(0), T(0), T(1)};
+    if (SRC == 0) {
+      v.p = src[idx];
+    } else {
+      v.p = P[idx];
+      if (!first) {
+        v.r = Rv[idx];
+        if (pre) v.j = Jv[idx];
+      }
+    }
+    return v;
+  };
+  auto finish = [&](const Raw &v, int row, int col) -> T {
+    if (SRC == 0 || first) return v.p;
+    const T z = pre ? v.j * v.r : v.r;
+    const T pn = z + beta * v.p;
+    P[L.off + row * N + col] = pn;
     return pn;
   };
   // every owned coefficient of the cached levels, eight in flight per thread
@@ -1248,12 +1402,40 @@ __global__ void __launch_bounds__(kThreads) k_synthesis(const InstDev *__restric
     const int M = N >> (k - 1), H = M >> 1, R = M >> lgC, Rh = R >> 1;
     const bool cached = k >= cm.kc;
     if (k < kd) cluster_wait();
-    // step 1: own rows, low-y (LL | HL) then high-y (LH | HH), into V
-    for (int idx = tid; idx < Rh * M; idx += nt) {
-      const int jl = idx >> lgM, x = idx & (M - 1);
-      const int i = crank * Rh + jl;
-      V[jl * M + x] = x < H ? U[jl * H + x] : (cached ? cache[cm.hl(k, jl, x)] : coef(i, x));
-      V[(Rh + jl) * M + x] = cached ? cache[cm.lh(k, jl, x)] : coef(H + i, x);
+    // step 1: own rows, low-y (LL | HL) then high-y (LH | HH), into V; the
+    // coefficients of uncached levels (with the fused direction update) are
+    // loaded kRowU per thread before any is updated
+    if (cached) {
+      for (int idx = tid; idx < Rh * M; idx += nt) {
+        const int jl = idx >> lgM, x = idx & (M - 1);
+        V[jl * M + x] = x < H ? U[jl * H + x] : cache[cm.hl(k, jl, x)];
+        V[(Rh + jl) * M + x] = cache[cm.lh(k, jl, x)];
+      }
+    } else {
+      constexpr int kRowU = 4;
+      for (int idx0 = tid; idx0 < Rh * M; idx0 += kRowU * nt) {
+        Raw ra[kRowU], rb[kRowU];
+#pragma unroll
+        for (int u = 0; u < kRowU; ++u) {
+          const int idx = idx0 + u * nt;
+          if (idx < Rh * M) {
+            const int jl = idx >> lgM, x = idx & (M - 1);
+            const int i = crank * Rh + jl;
+            if (x >= H) ra[u] = raw(i, x);
+            rb[u] = raw(H + i, x);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kRowU; ++u) {
+          const int idx = idx0 + u * nt;
+          if (idx < Rh * M) {
+            const int jl = idx >> lgM, x = idx & (M - 1);
+            const int i = crank * Rh + jl;
+            V[jl * M + x] = x < H ? U[jl * H + x] : finish(ra[u], i, x);
+            V[(Rh + jl) * M + x] = finish(rb[u], H + i, x);
+          }
+        }
+      }
     }
     __syncthreads();
     // step 2: row synthesis (x) into U: low-y rows at XL, high-y rows at XH
@@ -1582,6 +1764,9 @@ cudaError_t allow_lf() {
   TOMO_CFG((k_analysis<T, 1, kEpiPlain, LF>));
   TOMO_CFG((k_analysis<T, 1, kEpiOp, LF>));
   TOMO_CFG((k_analysis<T, 1, kEpiResid, LF>));
+  TOMO_CFG((k_analysis<T, 2, kEpiPlain, LF>));
+  TOMO_CFG((k_analysis<T, 2, kEpiOp, LF>));
+  TOMO_CFG((k_analysis<T, 2, kEpiResid, LF>));
 #undef TOMO_CFG
   return e;
 }
@@ -1598,6 +1783,8 @@ cudaError_t allow_type() {
                               : reinterpret_cast<const void *>(k_forward<T, 2>);
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxForwardSmem);
   }
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_gather<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxTransformSmem);
   return e;
 }
 
@@ -1605,8 +1792,11 @@ template <typename T, int LF>
 cudaError_t synth_lf(int src, int flags, const InstDev *insts, const ClusterItem *items, int n_clusters,
                      int C, size_t smem, const IoArgs &io, cudaStream_t s) {
   const dim3 g(n_clusters * C);
-  return src ? launch_ex(k_synthesis<T, 1, LF>, g, kThreads, C, smem, s, insts, items, io, flags)
-             : launch_ex(k_synthesis<T, 0, LF>, g, kThreads, C, smem, s, insts, items, io, flags);
+  // two CTAs of 256 threads per SM when their shared memory allows (two clusters per GPC),
+  // else one CTA of 512
+  const int nt = smem <= kTwoPerSmSmem ? kSynthThreads / 2 : kSynthThreads;
+  return src ? launch_ex(k_synthesis<T, 1, LF>, g, nt, C, smem, s, insts, items, io, flags)
+             : launch_ex(k_synthesis<T, 0, LF>, g, nt, C, smem, s, insts, items, io, flags);
 }
 
 template <typename T>
@@ -1625,8 +1815,15 @@ template <typename T, int LF>
 cudaError_t anal_lf(int src, int epi, int flags, const InstDev *insts, const ClusterItem *items,
                     int n_clusters, int C, size_t smem, const IoArgs &io, cudaStream_t s) {
   const dim3 g(n_clusters * C);
-#define TOMO_AN(S, E) launch_ex(k_analysis<T, S, E, LF>, g, kAnalysisThreads, C, smem, s, insts, items, io, flags)
+  // two CTAs of 512 threads per SM when their shared memory allows, else one of 1024
+  const int nt = smem <= kTwoPerSmSmem ? kAnalysisThreads : kAnalysisThreadsMax;
+#define TOMO_AN(S, E) launch_ex(k_analysis<T, S, E, LF>, g, nt, C, smem, s, insts, items, io, flags)
   if (src == 0) return TOMO_AN(0, kEpiPlain);
+  if (src == 2) {
+    if (epi == kEpiPlain) return TOMO_AN(2, kEpiPlain);
+    if (epi == kEpiOp) return TOMO_AN(2, kEpiOp);
+    return TOMO_AN(2, kEpiResid);
+  }
   if (epi == kEpiPlain) return TOMO_AN(1, kEpiPlain);
   if (epi == kEpiOp) return TOMO_AN(1, kEpiOp);
   return TOMO_AN(1, kEpiResid);
@@ -1667,8 +1864,18 @@ cudaError_t launch_synthesis(int precision, int src, int lf, int flags, const In
 }
 
 cudaError_t launch_analysis(int precision, int src, int epi, int lf, int flags, const InstDev *insts,
-                            const ClusterItem *items, int n_clusters, int C, size_t smem,
-                            const IoArgs &io, cudaStream_t s) {
+                             const ClusterItem *items, int n_clusters, int C, size_t smem, const IoArgs &io,
+                             cudaStream_t s, int split, size_t smem_gather) {
+  if (src == 1 && split) {
+    // gather in its own kernel, then the transform of its output
+    const int tt_mode = epi == kEpiOp ? 0 : (epi == kEpiResid && (flags & kFlagWarm) ? 1 : 2);
+    const dim3 g(n_clusters * C);
+    cudaError_t e = precision == 0
+                        ? launch_ex(k_gather<float>, g, kGatherThreads, 0, smem_gather, s, insts, items, io, C, tt_mode)
+                        : launch_ex(k_gather<double>, g, kGatherThreads, 0, smem_gather, s, insts, items, io, C, tt_mode);
+    if (e != cudaSuccess) return e;
+    src = 2;
+  }
   return precision == 0 ? anal_t<float>(src, epi, lf, flags, insts, items, n_clusters, C, smem, io, s)
                         : anal_t<double>(src, epi, lf, flags, insts, items, n_clusters, C, smem, io, s);
 }

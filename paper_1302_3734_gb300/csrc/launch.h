@@ -9,6 +9,7 @@ namespace tomo {
 
 constexpr int kMaxTransformSmem = 220 * 1024;   // opt-in dynamic shared memory of the transforms
 constexpr int kMaxForwardSmem = 150 * 1024;     // staged corner tables of the forward kernel
+constexpr size_t kTwoPerSmSmem = 108 * 1024;   // dynamic shared memory that lets two CTAs share an SM
 
 // Dynamic shared memory of k_forward for `n_layers` layers.
 size_t forward_smem(int n_layers, int precision);
@@ -27,7 +28,9 @@ cudaError_t launch_synthesis(int precision, int src, int lf, int flags, const In
 // 1 operator (q, p.q -> alpha), 2 residual (r, p, r.z); flags: kFlagWarm.
 cudaError_t launch_analysis(int precision, int src, int epi, int lf, int flags, const InstDev *insts,
                             const ClusterItem *items, int n_clusters, int C, size_t smem,
-                            const IoArgs &io, cudaStream_t s);
+                            const IoArgs &io, cudaStream_t s, int split, size_t smem_gather);
+// Kernels one launch_analysis call launches.
+inline int analysis_launches(int src, int split) { return (src == 1 && split) ? 2 : 1; }
 
 // Ray-trace, Fried slopes, noise weighting, Gamma^T.  mode 0 operator, 1 residual,
 // 2 data only.

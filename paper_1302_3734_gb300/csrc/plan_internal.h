@@ -26,6 +26,8 @@ struct LaunchSet {
   const UpdItem *upd = nullptr;
   int n_upd = 0;
   int precision = 0;
+  int split = 0;                 // gather in its own kernel (tables not staged in shared memory)
+  size_t smem_g = 0;             // its dynamic shared memory
 };
 
 struct Timer {
