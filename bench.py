@@ -104,6 +104,21 @@ def frame_screens(geom, k, rank):
     return frame_screens.ff.layers(k * 0.002)
 
 
+def max_over_ranks(value_ms, dist, device):
+    """The slowest rank's time: the job ends when its last rank does."""
+    if not dist:
+        return value_ms
+    import torch
+    t = torch.tensor([value_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(ws, steps, tot_ms):
+    """Whole-job solves per second: every rank solves `steps` frames in the slowest rank's time."""
+    return ws * steps / (tot_ms / 1000.0)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -506,12 +521,8 @@ def main():
     launches = pkg.launch_count() - launches0
     if dist:
         dist.barrier()
-    tot_ms = sum(times)
-    if dist:
-        t = torch.tensor([tot_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    value = ws * args.steps / (tot_ms / 1000.0)
+    tot_ms = max_over_ranks(sum(times), dist, dev)
+    value = job_rate(ws, args.steps, tot_ms)
     ms_step = tot_ms / args.steps
 
     # end to end through the public API: pinned host slopes in, coefficients out

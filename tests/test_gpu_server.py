@@ -180,3 +180,29 @@ def test_latest_frame_policy_supersedes_stale_frames(lib):
     assert [res[k]["status"] for k in (1, 2, 3)] == [10, 10, 10]  # superseded
     assert srv.stats()["frames_superseded"] == 3
     srv.close()
+
+
+def test_every_100th_frame_of_a_served_stream_matches_the_oracle(lib):
+    torch, pkg = lib
+    geoms = _geoms()[:2]
+    K = 201
+    data = [_frames(g, K, 20 + i) for i, g in enumerate(geoms)]
+    srv = pkg.Server(iters=ITERS, queue_depth=256, result_slots=256)
+    ids = [srv.admit(g) for g in geoms]
+    for k in range(K):
+        for i, tid in enumerate(ids):
+            assert srv.submit(tid, data[i][1][k], tag=k)
+    srv.drain(300.0)
+    res = srv.poll()
+    assert len(res) == K * len(ids) and all(r["status"] == 0 for r in res)
+    got = {(ids.index(r["telescope"]), r["tag"]): srv.result(r["telescope"], r["result_slot"], r["tag"])
+           for r in res if r["tag"] % 100 in (0, 99)}
+    srv.close()
+    for i, g in enumerate(geoms):
+        ora = data[i][0]
+        for k in (100, 200):
+            x0 = got[(i, k - 1)].astype(np.float64)
+            s = data[i][1][k].astype(np.float64)
+            x_ref = ora.pcg(ora.rhs(s), x0, ITERS, ora.jacobi_diagonal())
+            e = rel(got[(i, k)].astype(np.float64), x_ref, f"served-stream/{g['name']}/frame{k}")
+            assert e < 1e-5, (g["name"], k, e)
