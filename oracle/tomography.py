@@ -24,6 +24,12 @@ Readings where the paper is silent (each is listed in the design notes):
   approximation block taking k = J; L0 <= 0 drops the L0 term;
 * a tip/tilt-only natural guide star measures the two means of the
   full-resolution Fried slopes of its sensor, with noise sigma^2 I_2;
+* spot elongation (Sec. 4.3, eq. elongation_matrix): an LGS subaperture's
+  noise block is sigma^2 (I + tau g g^T) with g = beta / f the elongation
+  vector in units of the spot's FWHM, read as growing linearly with the
+  subaperture centre's distance from the laser launch point:
+  g = elong_scale * (r - llt); natural guide stars have none; the modified
+  Jacobi diagonal keeps sigma^-2 I blocks (a preconditioner only);
 * CG is Hestenes-Stiefel for exactly ``iters`` iterations.
 
 Pins: tests/test_oracle_solver.py (SPD-ness, a dense Cholesky solve that CG must
@@ -113,6 +119,38 @@ class Tomography:
         """(I - T) y: subtract the mean x- and mean y-slope."""
         return np.concatenate([y[:S] - y[:S].mean(), y[S:] - y[S:].mean()])
 
+    def elongation(self, m):
+        """(g_x, g_y) per valid subaperture of sensor m (row-major), or None when its
+        noise is sigma^2 I: LGS sensors with elong_tau > 0 only."""
+        w = self.wfs[m]
+        tau = float(w.get("elong_tau", 0.0))
+        if tau <= 0.0 or not (math.isfinite(float(w["height"])) and float(w["height"]) > 0) or w["tt_only"]:
+            return None
+        n, d = int(w["n_sub"]), float(w["d_sub"])
+        b, a = np.nonzero(np.asarray(w["valid"], bool))          # row-major: b = row (y), a = column (x)
+        cx, cy = (a + 0.5 - n / 2.0) * d, (b + 0.5 - n / 2.0) * d
+        lx, ly = w.get("llt", (0.0, 0.0))
+        eps = float(w.get("elong_scale", 0.0))
+        return eps * (cx - lx), eps * (cy - ly)
+
+    def noise_inverse_apply(self, m, y):
+        """C_tilde_m^-1 y: per subaperture the 2x2 block sigma^2 (I + tau g g^T)
+        (eq. elongation_matrix), solved as written; sigma^-2 y without elongation."""
+        w, S = self.wfs[m], self.S[m]
+        y = np.asarray(y, dtype=np.float64)
+        el = self.elongation(m)
+        if el is None:
+            return y / w["sigma"] ** 2
+        tau = float(w["elong_tau"])
+        gx, gy = el
+        C = np.empty((S, 2, 2))
+        C[:, 0, 0] = 1.0 + tau * gx * gx
+        C[:, 0, 1] = C[:, 1, 0] = tau * gx * gy
+        C[:, 1, 1] = 1.0 + tau * gy * gy
+        C *= w["sigma"] ** 2
+        z = np.linalg.solve(C, np.stack([y[:S], y[S:]], axis=1)[..., None])[..., 0]
+        return np.concatenate([z[:, 0], z[:, 1]])
+
     def weight_model(self, m, y):
         """Sensor m's block of C^-1 acting on model slopes y = Gamma_m P_m phi,
         returned in full-resolution slope space (so Gamma_m^T applies next)."""
@@ -122,8 +160,9 @@ class Tomography:
             t = inv * np.array([y[:S].mean(), y[S:].mean()])     # sigma^-2 M y
             return np.concatenate([np.full(S, t[0] / S), np.full(S, t[1] / S)])  # M^T
         if w["remove_tt"]:
-            return inv * self._remove_tt(y, S)                     # (I-T) s^-2 (I-T) y
-        return inv * y
+            # (I - T) C_tilde^-1 (I - T) y
+            return self._remove_tt(self.noise_inverse_apply(m, self._remove_tt(y, S)), S)
+        return self.noise_inverse_apply(m, y)
 
     def weight_data(self, m, s_m):
         """Sensor m's block of C^-1 applied to measured data s_m."""
@@ -131,9 +170,10 @@ class Tomography:
         inv = 1.0 / (w["sigma"] ** 2)
         if w["tt_only"]:
             return np.concatenate([np.full(S, inv * s_m[0] / S), np.full(S, inv * s_m[1] / S)])
+        s_m = np.asarray(s_m, dtype=np.float64)
         if w["remove_tt"]:
-            return inv * self._remove_tt(np.asarray(s_m, dtype=np.float64), S)
-        return inv * np.asarray(s_m, dtype=np.float64)
+            return self._remove_tt(self.noise_inverse_apply(m, self._remove_tt(s_m, S)), S)
+        return self.noise_inverse_apply(m, s_m)
 
     def apply_normal(self, c):
         """A_op c = W sum_m P_m^T Gamma_m^T C_m^-1 Gamma_m P_m W^-1 c + alpha D c."""

@@ -197,3 +197,27 @@ def small_lgs_config(n_sub=16, N=32, n_layers=3, levels=2, order=3, precision=0,
             "wavelet_order": order, "levels": levels, "alpha": 1.0,
             "L0": OUTER_SCALE, "precond": precond, "precision": precision,
             "iters": 8, "warm": True, "cn2": cn2, "r0": R0_500NM, "seed_base": 9000}
+
+
+def with_elongation(geom, tau=0.8, spot_fwhm_arcsec=1.0, sodium_depth_m=10e3, launch_radius=None):
+    """A copy of geom with spot elongation (Sec. 4.3, eq. elongation_matrix) on every
+    laser guide star sensor: tau as in the paper's tests (0.8); a subaperture's
+    elongation is the sodium layer's depth seen from the distance to the launch
+    point, depth * r / H^2 rad, in units of the spot FWHM, so
+    elong_scale = depth / H^2 / FWHM per metre; the lasers are launched from the pupil
+    edge (launch_radius, default D/2) at their guide star's azimuth."""
+    import copy
+    g = copy.deepcopy(geom)
+    R = g["D_tel"] / 2.0 if launch_radius is None else float(launch_radius)
+    fwhm = spot_fwhm_arcsec * math.pi / 180.0 / 3600.0
+    for w in g["wfs"]:
+        H = float(w["height"])
+        if w["tt_only"] or not (math.isfinite(H) and H > 0):
+            continue
+        az = math.atan2(float(w["theta"][1]), float(w["theta"][0]))
+        w["elong_tau"] = float(tau)
+        w["elong_scale"] = sodium_depth_m / H ** 2 / fwhm
+        w["llt"] = (R * math.cos(az), R * math.sin(az))
+    g["name"] = g["name"] + "-elong"
+    return g
+
