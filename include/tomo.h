@@ -77,7 +77,15 @@ typedef struct {
                                   pupil rule (centre radius within [obstruction*D/2, D/2]) */
   double sigma;                /* noise standard deviation per slope (rad, > 0) */
   int tt_only;                 /* 1: the sensor reports only the two mean slopes (tip/tilt NGS) */
-  int remove_tt;               /* 1: tip/tilt removal, C^-1 -> (I-T) sigma^-2 (I-T) (LGS) */
+  int remove_tt;               /* 1: tip/tilt removal, C^-1 -> (I-T) C_tilde^-1 (I-T) (LGS) */
+  /* Spot elongation of a laser guide star (Sec. 4.3, eq. elongation_matrix): each
+   * subaperture's noise block is sigma^2 (I + tau g g^T) with g = elong_scale * (r - llt),
+   * r the subaperture centre and llt the laser launch point (pupil coordinates, m), g in
+   * units of the spot FWHM.  elong_tau <= 0 (or a natural star): sigma^2 I.  The modified
+   * Jacobi diagonal keeps sigma^-2 I blocks (it is only the preconditioner). */
+  double elong_tau;            /* tau, 0..1 */
+  double elong_scale;          /* |g| per metre of distance from the launch point (1/m) */
+  double llt_x, llt_y;         /* launch point (m) */
 } tomo_wfs;
 
 /* One turbulence layer (Sec. 2.1 layered model, Sec. 3 prior). */

@@ -34,7 +34,9 @@ class Wfs(ctypes.Structure):
                 ("height", ctypes.c_double), ("n_sub", ctypes.c_int),
                 ("d_sub", ctypes.c_double), ("valid", ctypes.POINTER(ctypes.c_ubyte)),
                 ("sigma", ctypes.c_double), ("tt_only", ctypes.c_int),
-                ("remove_tt", ctypes.c_int)]
+                ("remove_tt", ctypes.c_int), ("elong_tau", ctypes.c_double),
+                ("elong_scale", ctypes.c_double), ("llt_x", ctypes.c_double),
+                ("llt_y", ctypes.c_double)]
 
 
 class Layer(ctypes.Structure):
@@ -171,6 +173,10 @@ def geometry_struct(geom):
         ws[i].sigma = float(w["sigma"])
         ws[i].tt_only = int(bool(w["tt_only"]))
         ws[i].remove_tt = int(bool(w["remove_tt"]))
+        ws[i].elong_tau = float(w.get("elong_tau", 0.0))
+        ws[i].elong_scale = float(w.get("elong_scale", 0.0))
+        llt = w.get("llt", (0.0, 0.0))
+        ws[i].llt_x, ws[i].llt_y = float(llt[0]), float(llt[1])
     ls = (Layer * len(geom["layers"]))()
     for i, lay in enumerate(geom["layers"]):
         ls[i].altitude = float(lay["altitude"])

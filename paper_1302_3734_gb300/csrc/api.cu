@@ -472,6 +472,7 @@ tomo_status tomo_plan_create_ex(const tomo_geometry *g, const tomo_plan_options 
   const size_t o_vsrun = A.take(sizeof(int4) * std::max<size_t>(1, H.vs_run.size()));
   const size_t o_stage = A.take(std::max<size_t>(16, H.stage_img.size()));
   const size_t o_eslot = A.take(sizeof(EdgeSlot) * H.edge_slots.size());
+  const size_t o_gel = A.take(esz * std::max<size_t>(2, H.gel.size()));
   const size_t o_gtcols = A.take(sizeof(int2) * std::max<size_t>(1, H.gt_cols.size()));
   const size_t o_ttseg = A.take(sizeof(int2) * H.tt_seg.size());
   const size_t o_ttnode = A.take(sizeof(int) * std::max<size_t>(1, H.tt_node.size()));
@@ -543,8 +544,10 @@ tomo_status tomo_plan_create_ex(const tomo_geometry *g, const tomo_plan_options 
   I.gt_ys = reinterpret_cast<const int *>(base + o_gtys);
   I.vs_run = reinterpret_cast<const int4 *>(base + o_vsrun);
   I.vstage = H.vstage;
+  I.v_total = H.v_total;
   I.stage_img = base + o_stage;
   I.edge_slots = reinterpret_cast<const EdgeSlot *>(base + o_eslot);
+  I.gel = H.gel.empty() ? nullptr : base + o_gel;
   I.gt_cols = reinterpret_cast<const int2 *>(base + o_gtcols);
   I.img_stride = H.img_stride;
   I.tt_seg = reinterpret_cast<const int2 *>(base + o_ttseg);
@@ -611,6 +614,7 @@ tomo_status tomo_plan_create_ex(const tomo_geometry *g, const tomo_plan_options 
   put(o_vsrun, H.vs_run.data(), sizeof(int4) * H.vs_run.size());
   put(o_stage, H.stage_img.data(), H.stage_img.size());
   put(o_eslot, H.edge_slots.data(), sizeof(EdgeSlot) * H.edge_slots.size());
+  if (!H.gel.empty()) put_real(o_gel, H.gel);
   put(o_gtcols, H.gt_cols.data(), sizeof(int2) * H.gt_cols.size());
   put_real(o_ttw, H.tt_w);
   put(o_gtoff, H.gt_off.data(), sizeof(int) * H.gt_off.size());

@@ -24,6 +24,8 @@ constexpr int kMaxTapsNode = 4;    // corners per axis whose bilinear taps reach
 
 enum WfsKind : int { kFull = 0, kRemoveTT = 1, kTTOnly = 2 };
 
+constexpr int kMaxEdgeSlots = 64;   // sensors with a pupil-edge term
+
 // Scalar slots (double) of an instance.  r.z of iteration it lives in
 // kRz0 + (it & 1): the synthesis of iteration it writes it while reading the
 // other slot (r.z of iteration it-1) for beta.
@@ -61,6 +63,10 @@ struct WfsDev {
   double inv_sigma2;
   double inv_S;                 // 1 / S (means of the slopes)
   double tt_scale;              // sigma^-2 / S
+  // spot elongation (LGS): the subaperture's noise block sigma^2 (I + tau g g^T),
+  // g = el_eps * (centre - (el_lx, el_ly)); centre = ((a + 1/2 - n/2) d, (b + 1/2 - n/2) d)
+  int elong, pad_el;
+  double el_tau, el_eps, el_lx, el_ly, d_sub;
 };
 
 // One sensor with a pupil-edge term (edge slot k = its tt_idx): where its
@@ -68,6 +74,10 @@ struct WfsDev {
 struct EdgeSlot {
   int part_off, n_tiles, kind, slope_off;
   double inv_S, tt_scale;
+  // tip/tilt removal under spot elongation: sigma^-2, and M = mean over the
+  // subapertures of C_tilde_j^-1 (symmetric 2x2)
+  int elong, pad;
+  double inv_sigma2, mb_xx, mb_xy, mb_yy;
 };
 
 // Everything a kernel needs to know about one instance.  Pointers to element
@@ -95,7 +105,7 @@ struct InstDev {
   const void *gt_rec;
   const int *gt_ys;             // per row record: its window start in the staged v rows
   const int4 *vs_run;           // per (layer, rank, dense sensor): v run {g0, 16-byte words, smem offset}
-  int vstage, pad_vs;           // staged v elements per analysis CTA
+  int vstage, v_total;          // staged v elements per analysis CTA; corner values of all sensors
   const int2 *gt_cols;          // per (m,l): columns [x, x+y) mod N_l that the sensor's taps reach
   const void *stage_img;        // per (layer, rank): the CTA's stage image (img_stride bytes apart)
   long long img_stride;
@@ -110,6 +120,11 @@ struct InstDev {
   const void *tt_w;             // (w t_x, w t_y) of the entry (T pairs)
   int n_tt, n_edge_wfs;         // tip/tilt-only sensors; sensors with an edge slot
   const EdgeSlot *edge_slots;   // per edge slot (n_edge_wfs)
+  // Tip/tilt removal under spot elongation: the corner fields
+  // Gamma^T (sigma^-2 c_j g_x,j g_j) and Gamma^T (sigma^-2 c_j g_y,j g_j)
+  // (c_j = tau / (1 + tau |g_j|^2)), laid out like v (Gx: v_total, then Gy),
+  // whose sum weighted by the sensor's mean slopes completes its corner field.
+  const void *gel;
   // Staging of the gather tables in the analysis kernel's shared memory
   // (loaded before the dependency wait); 0 = read them from global memory.
   int gather_staged, n_dense;   // flag; sensors with a dense corner field
@@ -134,6 +149,11 @@ struct IoArgs {
 #else
 #define TOMO_HD
 #endif
+
+// Partial sums per forward tile of a sensor's slope vector: 2 (the sums of z),
+// or 4 with tip/tilt removal under elongation (also the sums of C_tilde^-1 z).
+TOMO_HD inline int tile_partials(const WfsDev &d) { return (d.elong && d.kind == 1) ? 4 : 2; }
+
 
 // Shared-memory layout of the transform kernels (elements of T): two row
 // buffers of (N/C + kMaxTaps) x N, two coarse buffers of C x C, then the
@@ -165,10 +185,12 @@ TOMO_HD inline int transform_cache_size(int N, int C, int J, int kc) {
 // (bytes from the stage base, 16-byte aligned): an image copied verbatim from
 // the plan (per dense sensor N column and R0 row tap records, the latter with
 // their window start in the staged v rows; the CTA's pupil-edge weights; the
-// sensors' nc; the v run prefix and sources; the pupil-edge nodes, entry
-// starts and slots; the node count), then the corner rows of v the CTA reads.
+// sensors' nc; the v run prefix and sources; each sensor's edge slot when its
+// corner field takes the elongation correction, else -1; the pupil-edge nodes,
+// entry starts and slots; the node count), then the corner rows of v the CTA
+// reads.
 struct StageLayout {
-  int xr, yr, tw, mnc, vpre, vsrc, tn, tb, tk, nn, image, vs, total;
+  int xr, yr, tw, mnc, vpre, vsrc, mslot, tn, tb, tk, nn, image, vs, total;
 };
 TOMO_HD inline StageLayout stage_layout(int n_dense, int N, int R0, int rec_stride, int esz,
                                         int max_nodes, int max_entries, int vstage) {
@@ -179,7 +201,8 @@ TOMO_HD inline StageLayout stage_layout(int n_dense, int N, int R0, int rec_stri
   L.mnc = (L.tw + 2 * max_entries * esz + 3) / 4 * 4;
   L.vpre = L.mnc + 4 * n_dense;
   L.vsrc = L.vpre + 4 * (n_dense + 1);
-  L.tn = L.vsrc + 4 * n_dense;
+  L.mslot = L.vsrc + 4 * n_dense;
+  L.tn = L.mslot + 4 * n_dense;
   L.tb = L.tn + 4 * max_nodes;
   L.tk = L.tb + 4 * (max_nodes + 1);
   L.nn = L.tk + 4 * max_entries;

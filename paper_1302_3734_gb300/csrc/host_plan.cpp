@@ -235,6 +235,18 @@ tomo_status build_host_plan(const tomo_geometry *geo, HostPlan *P, std::string *
     d.kind = W.tt_only ? kTTOnly : (W.remove_tt ? kRemoveTT : kFull);
     d.is_lgs = lgs ? 1 : 0;
     d.inv_sigma2 = 1.0 / (W.sigma * W.sigma);
+    if (!(W.elong_tau >= 0.0 && W.elong_tau <= 1.0) || !std::isfinite(W.elong_scale) ||
+        !std::isfinite(W.llt_x) || !std::isfinite(W.llt_y)) {
+      snprintf(buf, sizeof buf, "sensor %d: elong_tau must be in [0, 1] and the elongation finite", m);
+      *err = buf;
+      return TOMO_ERR_ARG;
+    }
+    d.elong = (lgs && !W.tt_only && W.elong_tau > 0.0 && W.elong_scale != 0.0) ? 1 : 0;
+    d.el_tau = W.elong_tau;
+    d.el_eps = W.elong_scale;
+    d.el_lx = W.llt_x;
+    d.el_ly = W.llt_y;
+    d.d_sub = W.d_sub;
     P->n_lgs += lgs ? 1 : 0;
     // valid mask: given, or the circular pupil rule
     std::vector<unsigned char> valid(n * n);
@@ -608,6 +620,8 @@ tomo_status build_host_plan(const tomo_geometry *geo, HostPlan *P, std::string *
           put_int(img + sl.mnc + 4 * md, P->wfs[m].nc);
           put_int(img + sl.vpre + 4 * md, vpre);
           put_int(img + sl.vsrc + 4 * md, run.x / vq);
+          const WfsDev &dm = P->wfs[m];
+          put_int(img + sl.mslot + 4 * md, (dm.elong && dm.kind == kRemoveTT) ? dm.tt_idx : -1);
           vpre += run.y;
           ++md;
         }
@@ -676,13 +690,75 @@ tomo_status build_host_plan(const tomo_geometry *geo, HostPlan *P, std::string *
         ++tiles;
       }
     d.n_tiles = tiles;
-    part += 2 * tiles;
+    part += tile_partials(d) * tiles;
   }
   P->n_part = part;
-  P->edge_slots.assign(std::max(1, P->n_edge_wfs), EdgeSlot{0, 0, 0, 0, 0.0, 0.0});
-  for (const auto &d : P->wfs)
-    if (d.tt_idx >= 0)
-      P->edge_slots[d.tt_idx] = EdgeSlot{d.part_off, d.n_tiles, d.kind, d.slope_off, d.inv_S, d.tt_scale};
+  P->edge_slots.assign(std::max(1, P->n_edge_wfs), EdgeSlot{});
+  for (int m = 0; m < P->n_wfs; ++m) {
+    const WfsDev &d = P->wfs[m];
+    if (d.tt_idx < 0) continue;
+    EdgeSlot e{};
+    e.part_off = d.part_off;
+    e.n_tiles = d.n_tiles;
+    e.kind = d.kind;
+    e.slope_off = d.slope_off;
+    e.inv_S = d.inv_S;
+    e.tt_scale = d.tt_scale;
+    e.inv_sigma2 = d.inv_sigma2;
+    e.elong = (d.elong && d.kind == kRemoveTT) ? 1 : 0;
+    if (e.elong) {
+      // M = mean over the valid subapertures of C_tilde_j^-1 = sigma^-2 (I - c_j g_j g_j^T)
+      double xx = 0.0, xy = 0.0, yy = 0.0;
+      for (int b = 0; b < d.n; ++b)
+        for (int a = 0; a < d.n; ++a) {
+          if (P->sub_idx[d.sub_off + b * d.n + a] < 0) continue;
+          const double gx = d.el_eps * ((a + 0.5 - d.n / 2.0) * d.d_sub - d.el_lx);
+          const double gy = d.el_eps * ((b + 0.5 - d.n / 2.0) * d.d_sub - d.el_ly);
+          const double c = d.el_tau / (1.0 + d.el_tau * (gx * gx + gy * gy));
+          xx += 1.0 - c * gx * gx;
+          xy += -c * gx * gy;
+          yy += 1.0 - c * gy * gy;
+        }
+      e.mb_xx = d.inv_sigma2 * xx / d.S;
+      e.mb_xy = d.inv_sigma2 * xy / d.S;
+      e.mb_yy = d.inv_sigma2 * yy / d.S;
+    }
+    P->edge_slots[d.tt_idx] = e;
+  }
+  // the elongation corner fields: Fried transpose of sigma^-2 c_j g_k,j g_j,
+  // corner (a, b) receiving +-1/2 from the valid subapertures around it
+  bool any_el = false;
+  for (const auto &e : P->edge_slots) any_el = any_el || e.elong;
+  P->gel.clear();
+  if (any_el) {
+    P->gel.assign(2 * static_cast<size_t>(P->v_total), 0.0);
+    for (int m = 0; m < P->n_wfs; ++m) {
+      const WfsDev &d = P->wfs[m];
+      if (!(d.elong && d.kind == kRemoveTT)) continue;
+      const int n = d.n, nc = d.nc;
+      auto field = [&](int k, int a, int b, double *ex, double *ey) {
+        *ex = *ey = 0.0;
+        if (a < 0 || b < 0 || a >= n || b >= n || P->sub_idx[d.sub_off + b * n + a] < 0) return;
+        const double gx = d.el_eps * ((a + 0.5 - n / 2.0) * d.d_sub - d.el_lx);
+        const double gy = d.el_eps * ((b + 0.5 - n / 2.0) * d.d_sub - d.el_ly);
+        const double c = d.el_tau / (1.0 + d.el_tau * (gx * gx + gy * gy));
+        const double gk = k == 0 ? gx : gy;
+        *ex = d.inv_sigma2 * c * gk * gx;
+        *ey = d.inv_sigma2 * c * gk * gy;
+      };
+      for (int k = 0; k < 2; ++k)
+        for (int b = 0; b < nc; ++b)
+          for (int a = 0; a < nc; ++a) {
+            double x00, y00, x01, y01, x10, y10, x11, y11;   // (a-1,b-1) (a-1,b) (a,b-1) (a,b)
+            field(k, a - 1, b - 1, &x00, &y00);
+            field(k, a - 1, b, &x01, &y01);
+            field(k, a, b - 1, &x10, &y10);
+            field(k, a, b, &x11, &y11);
+            P->gel[k * static_cast<size_t>(P->v_total) + d.v_off + b * nc + a] =
+                0.5 * (x01 + x00 - x11 - x10) + 0.5 * (-y01 + y00 - y11 + y10);
+          }
+    }
+  }
   return TOMO_OK;
 }
 

@@ -49,6 +49,7 @@ struct HostPlan {
   std::vector<double> tt_w;        // 2 per entry
   int n_tt = 0, n_edge_wfs = 0;
   std::vector<EdgeSlot> edge_slots;
+  std::vector<double> gel;         // elongation corner fields (2 * v_total), empty if none
   std::vector<int> edge_idx;
   std::vector<double> edge_t;
   std::vector<int> run_rows;

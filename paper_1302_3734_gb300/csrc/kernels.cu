@@ -406,8 +406,14 @@ __global__ void __launch_bounds__(kThreads) k_forward(const InstDev *__restrict_
   }
   __syncthreads();
   // 2. weighted slopes of the subapertures the tile's corners touch
-  Acc<T> sx_acc, sy_acc;
+  Acc<T> sx_acc, sy_acc, qx_acc, qy_acc;
   const T isg = T(W.inv_sigma2);
+  // spot elongation: the block sigma^2 (I + tau g g^T) is inverted in closed
+  // form, sigma^-2 (I - c g g^T) with c = tau / (1 + tau |g|^2)
+  const bool elong = W.elong != 0;
+  const T el_tau = T(W.el_tau), el_eps = T(W.el_eps), el_d = T(W.d_sub);
+  const T el_cx = T(0.5 - 0.5 * n) * el_d - T(W.el_lx), el_cy = T(0.5 - 0.5 * n) * el_d - T(W.el_ly);
+  const bool four = tile_partials(W) == 4;
   for (int idx = tid; idx < (kFwdTile + 1) * (kFwdTile + 1); idx += blockDim.x) {
     const int u = idx % (kFwdTile + 1), w = idx / (kFwdTile + 1);
     const int a = a0 - 1 + u, b = b0 - 1 + w;
@@ -426,12 +432,24 @@ __global__ void __launch_bounds__(kThreads) k_forward(const InstDev *__restrict_
           sx = dat[W.slope_off + j];
           sy = dat[W.slope_off + W.S + j];
         }
+        if (elong) {
+          const T gx = el_eps * (T(a) * el_d + el_cx), gy = el_eps * (T(b) * el_d + el_cy);
+          const T c = el_tau / (T(1) + el_tau * (gx * gx + gy * gy));
+          const T dot = c * (gx * sx + gy * sy);
+          ex = isg * (sx - gx * dot);
+          ey = isg * (sy - gy * dot);
+        } else {
+          ex = isg * sx;
+          ey = isg * sy;
+        }
         if (u >= 1 && w >= 1) {   // subapertures owned by this tile
           sx_acc.add(sx);
           sy_acc.add(sy);
+          if (four) {
+            qx_acc.add(ex);
+            qy_acc.add(ey);
+          }
         }
-        ex = isg * sx;
-        ey = isg * sy;
       }
     }
     s_ex[w][u] = ex;
@@ -451,7 +469,12 @@ __global__ void __launch_bounds__(kThreads) k_forward(const InstDev *__restrict_
   }
   if (W.kind != kRemoveTT) return;
   // 4. tip/tilt removal: this tile's sums of z (the consumer forms the means)
-  store_tile_partial(I.part + W.part_off + 2 * it.tile, sx_acc, sy_acc);
+  if (four) {
+    store_tile_partial(I.part + W.part_off + 4 * it.tile, sx_acc, sy_acc);
+    store_tile_partial(I.part + W.part_off + 4 * it.tile + 2, qx_acc, qy_acc);
+  } else {
+    store_tile_partial(I.part + W.part_off + 2 * it.tile, sx_acc, sy_acc);
+  }
 }
 
 // ------------------------------------------------------- transform helpers
@@ -601,41 +624,92 @@ __device__ __forceinline__ float edge_one(const EdgeSlot &es, int tt_mode, float
   return __fadd_rn(c.x, c.y);
 }
 
+// Tip/tilt removal under spot elongation: with m and q the means of z and of
+// C_tilde^-1 z over the subapertures, (I - T) C_tilde^-1 (I - T) z =
+// C_tilde^-1 z - C_tilde^-1 m - (q - M m), M = mean C_tilde_j^-1.  The forward
+// kernel applied the first term; -sigma^-2 m - q + M m is constant over the
+// subapertures (its Gamma^T lives on the pupil edge: this coefficient pair);
+// the rest, sigma^-2 c_j g_j (g_j . m), reaches the corner field as
+// m_x Gx + m_y Gy (returned in mo).
+__device__ __forceinline__ void edge_elong(const EdgeSlot &es, double a, double b, double qa, double qb,
+                                           double *out, double *mo) {
+  const double mx = a * es.inv_S, my = b * es.inv_S, qx = qa * es.inv_S, qy = qb * es.inv_S;
+  out[0] = -es.inv_sigma2 * mx - qx + (es.mb_xx * mx + es.mb_xy * my);
+  out[1] = -es.inv_sigma2 * my - qy + (es.mb_xy * mx + es.mb_yy * my);
+  mo[0] = mx;
+  mo[1] = my;
+}
+
+// s_coef: 2 * kMaxEdgeSlots pupil-edge coefficient pairs, then per slot the
+// mean slopes (m_x, m_y) that weight the elongation fields (0 without).
 template <typename T>
 __device__ void edge_coefficients(const InstDev &I, T *s_coef, int tt_mode, const T *slopes) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int k = warp; k < I.n_edge_wfs; k += nw) {
     const EdgeSlot es = I.edge_slots[k];
     const bool sum = !(es.kind == kTTOnly && tt_mode == 2);
+    const int stride = es.elong ? 4 : 2;   // doubles per tile
     if constexpr (sizeof(T) == 4) {
-      Acc<float> a, b;
+      Acc<float> a, b, qa, qb;
       if (sum)
         for (int t = lane; t < es.n_tiles; t += 32) {
-          const float4 v = reinterpret_cast<const float4 *>(I.part + es.part_off)[t];
+          const float4 *pt = reinterpret_cast<const float4 *>(I.part + es.part_off + stride * t);
+          const float4 v = pt[0];
           a.merge(v.x, v.y);
           b.merge(v.z, v.w);
+          if (es.elong) {
+            const float4 w = pt[1];
+            qa.merge(w.x, w.y);
+            qb.merge(w.z, w.w);
+          }
         }
       warp_merge_down(a);
       warp_merge_down(b);
+      if (es.elong) {
+        warp_merge_down(qa);
+        warp_merge_down(qb);
+      }
       if (lane == 0) {
-        const bool tt = es.kind == kTTOnly && tt_mode != 0;
-        s_coef[2 * k] = edge_one(es, tt_mode, a.hi, a.lo, tt ? float(slopes[es.slope_off]) : 0.f);
-        s_coef[2 * k + 1] = edge_one(es, tt_mode, b.hi, b.lo, tt ? float(slopes[es.slope_off + 1]) : 0.f);
+        if (es.elong) {
+          double out[2], mo[2];
+          edge_elong(es, a.value(), b.value(), qa.value(), qb.value(), out, mo);
+          s_coef[2 * k] = T(out[0]);
+          s_coef[2 * k + 1] = T(out[1]);
+          s_coef[2 * kMaxEdgeSlots + 2 * k] = T(mo[0]);
+          s_coef[2 * kMaxEdgeSlots + 2 * k + 1] = T(mo[1]);
+        } else {
+          const bool tt = es.kind == kTTOnly && tt_mode != 0;
+          s_coef[2 * k] = edge_one(es, tt_mode, a.hi, a.lo, tt ? float(slopes[es.slope_off]) : 0.f);
+          s_coef[2 * k + 1] = edge_one(es, tt_mode, b.hi, b.lo, tt ? float(slopes[es.slope_off + 1]) : 0.f);
+          s_coef[2 * kMaxEdgeSlots + 2 * k] = T(0);
+          s_coef[2 * kMaxEdgeSlots + 2 * k + 1] = T(0);
+        }
       }
     } else {
-      double a = 0.0, b = 0.0;
+      double a = 0.0, b = 0.0, qa = 0.0, qb = 0.0;
       if (sum)
         for (int t = lane; t < es.n_tiles; t += 32) {
-          a += I.part[es.part_off + 2 * t];
-          b += I.part[es.part_off + 2 * t + 1];
+          a += I.part[es.part_off + stride * t];
+          b += I.part[es.part_off + stride * t + 1];
+          if (es.elong) {
+            qa += I.part[es.part_off + stride * t + 2];
+            qb += I.part[es.part_off + stride * t + 3];
+          }
         }
       a = warp_sum(a);
       b = warp_sum(b);
+      if (es.elong) {
+        qa = warp_sum(qa);
+        qb = warp_sum(qb);
+      }
       if (lane == 0) {
-        double out[2];
-        edge_pair(es, tt_mode, a, b, reinterpret_cast<const double *>(slopes), out);
+        double out[2], mo[2] = {0.0, 0.0};
+        if (es.elong) edge_elong(es, a, b, qa, qb, out, mo);
+        else edge_pair(es, tt_mode, a, b, reinterpret_cast<const double *>(slopes), out);
         s_coef[2 * k] = T(out[0]);
         s_coef[2 * k + 1] = T(out[1]);
+        s_coef[2 * kMaxEdgeSlots + 2 * k] = T(mo[0]);
+        s_coef[2 * kMaxEdgeSlots + 2 * k + 1] = T(mo[1]);
       }
     }
   }
@@ -705,39 +779,6 @@ __device__ __forceinline__ void gather_edges(int nn, const int *tn, const int *t
   }
 }
 
-// g on the CTA's rows [k0, k0+R0) of layer l: the transposed ray-trace
-// sum_m P_m^T v_m as a gather, from the tap records in global memory (plans
-// whose records do not fit next to the transform buffers).  One node per
-// thread and pass, sensors outer so that each sensor's record bases are
-// uniform; the pupil-edge terms add a short sparse list per CTA.
-template <typename T, int KT>
-__device__ void gather_rows(const InstDev &I, int l, int N, int R0, int crank, T *A,
-                            const T *s_coef) {
-  constexpr int RS = TapRec<T, KT>::RS;
-  const int nt = blockDim.x, tid = threadIdx.x, lgN = __ffs(N) - 1, k0 = crank * R0;
-  const T *vv = static_cast<const T *>(I.v);
-  const T *rec = static_cast<const T *>(I.gt_rec);
-  for (int node = tid; node < R0 * N; node += nt) A[node] = T(0);
-  for (int m = 0; m < I.n_wfs; ++m) {
-    const WfsDev &W = I.wfs[m];
-    if (W.kind == kTTOnly) continue;
-    const int go = I.gt_off[m * I.n_layers + l], nc = W.nc;
-    const T *xr = rec + static_cast<size_t>(go) * RS;
-    const T *yr = rec + static_cast<size_t>(go + N + k0) * RS;
-    for (int node = tid; node < R0 * N; node += nt) {
-      TapRec<T, KT> x, y;
-      x.load(xr + (node & (N - 1)) * RS);
-      y.load(yr + (node >> lgN) * RS);
-      if (x.off >= 0 && y.off >= 0) A[node] += window_sum<T, KT, false>(vv + y.off + x.off, nc, x, y);
-    }
-  }
-  if (I.n_edge_wfs == 0) return;
-  __syncthreads();
-  const int2 seg = I.tt_seg[l * I.C + crank];
-  gather_edges<T>(seg.y - seg.x, I.tt_node + seg.x, I.tt_beg + seg.x, I.tt_k,
-                  static_cast<const T *>(I.tt_w), A, s_coef);
-}
-
 // Shared-memory copy of the gather tables of one analysis CTA (layer l, rows
 // [k0, k0+R0)), laid out by stage_layout: the plan's stage image for the CTA
 // (tap records, pupil-edge segment, run tables), copied with cp.async before
@@ -747,7 +788,7 @@ template <typename T>
 struct GatherStage {
   unsigned char *base;
   T *xr, *yr, *vs, *tw;
-  int *mnc, *vpre, *vsrc, *tn, *tb, *tk, *pnn;
+  int *mnc, *vpre, *vsrc, *mslot, *tn, *tb, *tk, *pnn;
   int image_bytes;
 
   __device__ void carve(unsigned char *b, int Md, int N, int R0, const InstDev &I) {
@@ -761,6 +802,7 @@ struct GatherStage {
     mnc = reinterpret_cast<int *>(b + sl.mnc);
     vpre = reinterpret_cast<int *>(b + sl.vpre);
     vsrc = reinterpret_cast<int *>(b + sl.vsrc);
+    mslot = reinterpret_cast<int *>(b + sl.mslot);
     tn = reinterpret_cast<int *>(b + sl.tn);
     tb = reinterpret_cast<int *>(b + sl.tb);
     tk = reinterpret_cast<int *>(b + sl.tk);
@@ -779,6 +821,20 @@ struct GatherStage {
   }
 
   __device__ int nn() const { return *pnn; }
+
+  // Spot elongation with tip/tilt removal: v += m_x Gx + m_y Gy over the staged
+  // corner rows of those sensors (the mean slopes from edge_coefficients).
+  __device__ void add_elongation(const InstDev &I, const T *s_coef) const {
+    constexpr int vq = 16 / static_cast<int>(sizeof(T));
+    const T *gx = static_cast<const T *>(I.gel), *gy = gx + I.v_total;
+    for (int md = 0; md < I.n_dense; ++md) {
+      const int k = mslot[md];
+      if (k < 0) continue;
+      const T mx = s_coef[2 * kMaxEdgeSlots + 2 * k], my = s_coef[2 * kMaxEdgeSlots + 2 * k + 1];
+      const int e0 = vpre[md] * vq, cnt = (vpre[md + 1] - vpre[md]) * vq, g0 = vsrc[md] * vq;
+      for (int i = threadIdx.x; i < cnt; i += blockDim.x) vs[e0 + i] += mx * gx[g0 + i] + my * gy[g0 + i];
+    }
+  }
 
   // Starts the asynchronous copy of the CTA's corner rows of v (written by
   // the previous kernel) into shared memory; cp_async_wait_all() and a
@@ -828,8 +884,8 @@ __device__ void gather_rows_staged(const InstDev &I, const GatherStage<T> &st, i
 // not fit the analysis CTAs' shared memory; k_gather runs it.
 template <typename T, int KT>
 __device__ void gather_band_global(const InstDev &I, int l, int N, int R0, int crank, T *A,
-                                   const T *s_coef, const int *s_go, const int *s_nc, const int2 *s_cols,
-                                   int Md) {
+                                   const T *s_coef, const int *s_go, const int *s_nc, const int *s_el,
+                                   const int2 *s_cols, int Md) {
   constexpr int RS = TapRec<T, KT>::RS;
   const int nt = blockDim.x, tid = threadIdx.x, k0 = crank * R0;
   const T *vv = static_cast<const T *>(I.v);
@@ -853,7 +909,16 @@ __device__ void gather_band_global(const InstDev &I, int l, int N, int R0, int c
         const int i = (cols.x + c) & (N - 1);
         TapRec<T, KT> x;
         x.load(xr + i * RS);
-        if (x.off >= 0) A[kl * N + i] += window_sum<T, KT, false>(vv + y.off + x.off, s_nc[md], x, y);
+        if (x.off < 0) continue;
+        T acc = window_sum<T, KT, false>(vv + y.off + x.off, s_nc[md], x, y);
+        if (s_el[md] >= 0) {
+          // spot elongation with tip/tilt removal: the windows of m_x Gx + m_y Gy
+          const T *gx = static_cast<const T *>(I.gel), *gy = gx + I.v_total;
+          const int k = s_el[md];
+          acc += s_coef[2 * kMaxEdgeSlots + 2 * k] * window_sum<T, KT, false>(gx + y.off + x.off, s_nc[md], x, y) +
+                 s_coef[2 * kMaxEdgeSlots + 2 * k + 1] * window_sum<T, KT, false>(gy + y.off + x.off, s_nc[md], x, y);
+        }
+        A[kl * N + i] += acc;
       }
     }
     __syncthreads();
@@ -878,8 +943,8 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(const InstDev *__rest
                                                            IoArgs io, int C, int tt_mode) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ InstDev sI;
-  __shared__ T s_coef[2 * 64];
-  __shared__ int s_go[kMaxGatherSensors], s_nc[kMaxGatherSensors];
+  __shared__ T s_coef[4 * kMaxEdgeSlots];
+  __shared__ int s_go[kMaxGatherSensors], s_nc[kMaxGatherSensors], s_el[kMaxGatherSensors];
   __shared__ int2 s_cols[kMaxGatherSensors];
   __shared__ int s_md;
   pdl_trigger();
@@ -895,6 +960,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(const InstDev *__rest
       if (W.kind == kTTOnly) continue;
       s_go[md] = I.gt_off[m * I.n_layers + it.layer];
       s_nc[md] = W.nc;
+      s_el[md] = (W.elong && W.kind == kRemoveTT) ? W.tt_idx : -1;
       s_cols[md] = I.gt_cols[m * I.n_layers + it.layer];
       ++md;
     }
@@ -907,9 +973,9 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(const InstDev *__rest
   pdl_wait();
   if (I.n_edge_wfs > 0)
     edge_coefficients<T>(I, s_coef, tt_mode, static_cast<const T *>(io.in1[it.inst]));
-  if (I.max_taps <= 2) gather_band_global<T, 2>(I, it.layer, N, R0, crank, A, s_coef, s_go, s_nc, s_cols, s_md);
-  else if (I.max_taps == 3) gather_band_global<T, 3>(I, it.layer, N, R0, crank, A, s_coef, s_go, s_nc, s_cols, s_md);
-  else gather_band_global<T, 4>(I, it.layer, N, R0, crank, A, s_coef, s_go, s_nc, s_cols, s_md);
+  if (I.max_taps <= 2) gather_band_global<T, 2>(I, it.layer, N, R0, crank, A, s_coef, s_go, s_nc, s_el, s_cols, s_md);
+  else if (I.max_taps == 3) gather_band_global<T, 3>(I, it.layer, N, R0, crank, A, s_coef, s_go, s_nc, s_el, s_cols, s_md);
+  else gather_band_global<T, 4>(I, it.layer, N, R0, crank, A, s_coef, s_go, s_nc, s_el, s_cols, s_md);
   T *g = static_cast<T *>(I.phi) + L.off + crank * R0 * N;
   for (int node = threadIdx.x; node < R0 * N; node += blockDim.x) g[node] = A[node];
 }
@@ -983,7 +1049,7 @@ __global__ void __launch_bounds__(kAnalysisThreadsMax, 1) k_analysis(const InstD
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ InstDev sI;
   __shared__ CoefMap cm;
-  __shared__ T s_coef[2 * 64];
+  __shared__ T s_coef[4 * kMaxEdgeSlots];
   __shared__ T s_dal[kMaxLevels + 1];
   pdl_trigger();
   cg::cluster_group cluster = cg::this_cluster();
@@ -1020,7 +1086,8 @@ __global__ void __launch_bounds__(kAnalysisThreadsMax, 1) k_analysis(const InstD
   emit.Pn = static_cast<T *>(I.p);
   emit.X = static_cast<T *>(io.out0[it.inst]);
   GatherStage<T> st;
-  const bool staged = SRC == 1 && I.gather_staged;
+  // SRC 1 plans stage their tables (those that cannot run k_gather, SRC 2)
+  const bool staged = SRC == 1;
   if (staged) {
     const int off = transform_cache_offset(N, C) + transform_cache_size(N, C, J, L.cache_kc);
     unsigned char *sb = smem_raw + ((static_cast<size_t>(off) * sizeof(T) + 15) & ~size_t(15));
@@ -1062,13 +1129,13 @@ __global__ void __launch_bounds__(kAnalysisThreadsMax, 1) k_analysis(const InstD
     if (staged) {
       cp_async_wait_all();
       __syncthreads();
+      if (I.gel) {
+        st.add_elongation(I, s_coef);
+        __syncthreads();
+      }
       if (I.max_taps <= 2) gather_rows_staged<T, 2>(I, st, N, R0, A, s_coef);
       else if (I.max_taps == 3) gather_rows_staged<T, 3>(I, st, N, R0, A, s_coef);
       else gather_rows_staged<T, 4>(I, st, N, R0, A, s_coef);
-    } else {
-      if (I.max_taps <= 2) gather_rows<T, 2>(I, it.layer, N, R0, crank, A, s_coef);
-      else if (I.max_taps == 3) gather_rows<T, 3>(I, it.layer, N, R0, crank, A, s_coef);
-      else gather_rows<T, 4>(I, it.layer, N, R0, crank, A, s_coef);
     }
   }
   cp_async_wait_all();
