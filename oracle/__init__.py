@@ -16,13 +16,17 @@ in numpy float64, in the paper's order and notation:
                      its transpose;
 * ``tomography``  - noise weighting with tip/tilt removal, diagonal wavelet prior
                      D, the normal operator of eq. eqn_lse, its right-hand side,
-                     the modified Jacobi diagonal, and Hestenes-Stiefel (P)CG.
+                     the modified Jacobi diagonal, and Hestenes-Stiefel (P)CG;
+* ``fitting``     - the fitting step: piecewise-bilinear mirrors H, the NGS
+                     projections P over the evaluation directions, and CG on
+                     H^T H a = H^T P phi.
 
 Each function is pinned by tests/test_oracle_*.py against closed forms,
 invariants, textbook special cases and brute force on tiny inputs; nothing in
 those pins comes from the CUDA path.
 """
 from .tomography import Tomography
-from . import wavelets, atmosphere, tomography
+from .fitting import Fitting
+from . import wavelets, atmosphere, tomography, fitting
 
-__all__ = ["Tomography", "wavelets", "atmosphere", "tomography"]
+__all__ = ["Tomography", "Fitting", "wavelets", "atmosphere", "tomography", "fitting"]

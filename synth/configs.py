@@ -221,3 +221,31 @@ def with_elongation(geom, tau=0.8, spot_fwhm_arcsec=1.0, sodium_depth_m=10e3, la
     g["name"] = g["name"] + "-elong"
     return g
 
+
+
+def with_fitting(geom, altitudes=(0.0, 4000.0, 12700.0), pitches=(0.5, 0.72, 1.0), field_arcmin=2.0,
+                 n_dir=5, iters=4):
+    """A copy of geom with the fitting step's geometry (Sec. 4.1, eq. fit_step_min;
+    Sec. 5.1 setup): mirrors at ``altitudes`` with actuator ``pitches``, each a
+    square grid covering the aperture seen from every direction; ``n_dir`` x
+    ``n_dir`` directions on a square field of side ``field_arcmin``; the aperture
+    sampled at the corners of the valid subapertures of the first full-resolution
+    sensor.  The paper gives the altitudes and the total, 9296 degrees of freedom,
+    not the pitches: on the E-ELT geometry the default pitches (0.5, 0.72, 1.0 m)
+    give 4240 + 2856 + 2200 = 9296 actuators whose support reaches a sampling
+    point."""
+    import copy
+    g = copy.deepcopy(geom)
+    full = [w for w in g["wfs"] if not w["tt_only"]][0]
+    n_sub, d = int(full["n_sub"]), float(full["d_sub"])
+    half = 0.5 * field_arcmin * ARCMIN
+    ts = np.linspace(-half, half, n_dir) if n_dir > 1 else np.zeros(1)
+    dms = []
+    for h, p in zip(altitudes, pitches):
+        R = n_sub * d / 2.0 + float(h) * half
+        dms.append({"altitude": float(h), "pitch": float(p), "n": 2 * int(math.ceil(R / p)) + 3})
+    g["fitting"] = {"dms": dms, "directions": [(float(tx), float(ty)) for ty in ts for tx in ts],
+                    "n_sub": n_sub, "d_sub": d,
+                    "valid": pupil_mask(n_sub, d, g["D_tel"], g["obstruction"]), "iters": int(iters)}
+    g["name"] = g["name"] + "-fit"
+    return g
