@@ -119,7 +119,9 @@ typedef struct {
   int kernels_per_iteration;   /* kernel launches per PCG iteration */
   int kernels_per_solve_base;  /* launches per solve besides the iterations (warm start) */
   long long device_bytes;      /* device memory held by the plan */
-  long long bytes_per_iteration; /* algorithmic bytes moved per PCG iteration (see DESIGN) */
+  long long bytes_per_iteration; /* algorithmic bytes of one PCG iteration: (15 n + 2 V) elements,
+                                    13 n + 2 V without the preconditioner (n coefficients,
+                                    V sensor corners) */
   int precision;
 } tomo_plan_info;
 
@@ -222,6 +224,94 @@ tomo_status tomo_get_kernel_times(tomo_plan *p, int *counts, double *ms, int n_k
  * iters, warm) call once into a CUDA graph and replays it; 0 launches every
  * kernel directly (one launch per kernel per call, no graph). */
 tomo_status tomo_set_launch_mode(tomo_plan *p, int use_graphs);
+
+/* ------------------------------------------------------------------ fitting
+ * The fitting step (Sec. 4.1, eqs. fit_step_ideal / fit_step_min): mirror
+ * commands a minimising sum_j || H_j a - P_j phi ||^2 over directions theta_j,
+ * solved by CG (Hestenes-Stiefel, no preconditioner) on the normal equations
+ * H^T H a = H^T P phi for a fixed number of iterations, optionally from the
+ * previous commands.
+ *
+ * - Mirror k is a square grid of n x n actuators with spacing `pitch`,
+ *   conjugated to `altitude`.  Actuator (i, j) (column i = x, row j = y) sits
+ *   at ((i - (n-1)/2) pitch, (j - (n-1)/2) pitch) and the mirror's shape is
+ *   the piecewise-bilinear interpolation of its commands, zero beyond the
+ *   outermost actuators.  H_j a (x) = sum_k a_k(x + altitude_k theta_j).
+ * - The aperture is sampled at the corners of the valid subapertures of an
+ *   n_sub x n_sub grid of spacing d_sub: corner (a, b) at
+ *   ((a - n_sub/2) d_sub, (b - n_sub/2) d_sub), each with weight 1.
+ * - P_j is the natural-guide-star ray-trace (eq. ngsproj) through the plan's
+ *   layers: sum_l phi_l(x + h_l theta_j), bilinear on the periodic grids.
+ * - Command vectors: the mirrors concatenated, each n x n row-major (row = y),
+ *   of the plan's element type.
+ * A fit refers to its plan, which must outlive it; like a plan, a fit is not
+ * thread-safe.  Every call enqueues on `cuda_stream` and returns. */
+typedef struct tomo_fit tomo_fit;
+
+typedef struct {
+  double altitude;             /* m, >= 0 */
+  double pitch;                /* actuator spacing (m), 0 < pitch <= 4 d_sub */
+  int n;                       /* actuators per side, 2..4096 */
+} tomo_dm;
+
+typedef struct {
+  int n_dm;                    /* 1..4 */
+  const tomo_dm *dms;          /* host array of n_dm */
+  int n_dir;                   /* evaluation directions, 1..256 */
+  const double *theta;         /* host [n_dir][2]: (theta_x, theta_y) in rad */
+  int n_sub;                   /* aperture sampling grid, 1..1024 subapertures per side */
+  double d_sub;                /* m, > 0 */
+  const unsigned char *valid;  /* host, n_sub*n_sub, row = y; nonzero = valid (not NULL) */
+} tomo_fit_geometry;
+
+typedef struct {
+  long long n_act;             /* elements of a command vector (sum of n^2) */
+  long long n_active;          /* actuators whose support reaches a sampling point in some
+                                  direction (nonzero diagonal of H^T H) */
+  int n_points;                /* sampling points (corners of valid subapertures) */
+  int n_dir, n_dm;
+  int kernels_per_iteration;   /* launches per CG iteration */
+  int kernels_per_solve_base;  /* launches per tomo_fit_solve besides the iterations */
+  long long device_bytes;      /* device memory held by the fit */
+} tomo_fit_info;
+
+/* Build a fit for plan p: validates g, builds the tap tables of H, H^T and P
+ * (FP64 on the host, stored in the plan's element type) and allocates the
+ * workspace.  Synchronises the device.  On success *out owns device memory
+ * until tomo_fit_destroy.  TOMO_ERR_ARG: an argument out of the ranges above. */
+tomo_status tomo_fit_create(tomo_plan *p, const tomo_fit_geometry *g, tomo_fit **out);
+
+tomo_status tomo_fit_get_info(const tomo_fit *f, tomo_fit_info *out);
+
+/* d_out = H^T H d_a (both n_act elements, device). */
+tomo_status tomo_fit_apply_normal(tomo_fit *f, const void *d_a, void *d_out, void *cuda_stream);
+
+/* d_out = H^T P phi, phi the plan's layer grids in d_layers (device). */
+tomo_status tomo_fit_rhs(tomo_fit *f, const void *d_layers, void *d_out, void *cuda_stream);
+
+/* Quality of a correction (Sec. 5.1): d_rms[j] (device, n_dir doubles) = the
+ * root mean square over the sampling points of P_j phi - H_j a after removing
+ * its mean, for the layers d_layers (e.g. the true atmosphere) and commands d_a
+ * (NULL: no correction).  The Marechal approximation of the Strehl ratio at
+ * wavelength lambda is exp(-(2 pi r / lambda)^2), r in the layers' units. */
+tomo_status tomo_fit_residual_rms(tomo_fit *f, const void *d_layers, const void *d_a, double *d_rms,
+                                  void *cuda_stream);
+
+/* `iters` CG iterations on H^T H a = H^T P phi; d_a holds the starting
+ * commands when warm != 0 (ignored otherwise: the start is 0) and receives the
+ * result.  A p.Hp <= 0 with a nonzero residual freezes the iterate. */
+tomo_status tomo_fit_solve(tomo_fit *f, const void *d_layers, void *d_a, int iters, int warm,
+                           void *cuda_stream);
+
+/* The reconstruction of one frame, slopes to mirror commands: tomo_solve of
+ * the fit's plan (d_coeffs in/out, `iters` iterations), phi = W^-1 c into the
+ * fit's own layer buffer, then tomo_fit_solve (d_a in/out, `fit_iters`
+ * iterations); `warm` applies to both.  Replayed from one CUDA graph per
+ * argument set. */
+tomo_status tomo_reconstruct(tomo_fit *f, const void *d_slopes, void *d_coeffs, void *d_a, int iters,
+                             int fit_iters, int warm, void *cuda_stream);
+
+void tomo_fit_destroy(tomo_fit *f);
 
 /* ------------------------------------------------------------------ serving
  * A request loop for a stream of slope frames from several telescopes, the

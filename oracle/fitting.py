@@ -29,6 +29,14 @@ Readings (the paper gives no discretisation of the aperture or the mirrors):
 * the normal equations H^T H a = H^T P phi are solved by Hestenes-Stiefel CG,
   without preconditioner, for exactly ``iters`` iterations from a0.
 
+Quality of a correction (Sec. 5.1, the Marechal approximation of the Strehl
+ratio): in direction theta_j the residual wavefront is P_j phi - H_j a on the
+sampling points; r(theta_j) is its root mean square after removing its mean
+(piston does not affect the image), and s(theta_j) = exp(-(2 pi r / lambda)^2).
+Readings: phases are radians at the 500 nm wavelength the screens are drawn at,
+so at lambda the phase error is r * 500 nm / lambda; the paper evaluates at
+2200 nm (K band).
+
 A coefficient vector holds the mirrors concatenated, each n_k x n_k row-major.
 
 Pins: tests/test_oracle_fitting.py (brute-force hat sums, exact reproduction of
@@ -143,6 +151,22 @@ class Fitting:
     def objective(self, phis, a):
         """|| H a - P phi ||_2^2 summed over the directions (eq. fit_step_min)."""
         return float(sum(np.sum(self.residual(phis, a, j) ** 2) for j in range(len(self.theta))))
+
+    def residual_rms(self, phis, a):
+        """r(theta_j) for every direction: the RMS over the sampling points of
+        P_j phi - H_j a after its mean is removed (rad at 500 nm)."""
+        out = np.empty(len(self.theta))
+        for j in range(len(self.theta)):
+            e = self.residual(phis, a, j)[self.act]
+            out[j] = math.sqrt(max(0.0, float(np.mean((e - e.mean()) ** 2))))
+        return out
+
+    @staticmethod
+    def strehl(rms_rad500, wavelength=2200e-9):
+        """Marechal approximation exp(-(2 pi r / lambda)^2) of the Strehl ratio for a
+        wavefront error of rms_rad500 radians at 500 nm, observed at `wavelength`."""
+        phase = np.asarray(rms_rad500, dtype=np.float64) * (500e-9 / wavelength)
+        return np.exp(-phase ** 2)
 
     def cg(self, b, a0, iters):
         """Hestenes-Stiefel CG on H^T H a = b for exactly ``iters`` iterations."""

@@ -79,6 +79,23 @@ class PlanInfo(ctypes.Structure):
                 ("bytes_per_iteration", ctypes.c_longlong), ("precision", ctypes.c_int)]
 
 
+class Dm(ctypes.Structure):
+    _fields_ = [("altitude", ctypes.c_double), ("pitch", ctypes.c_double), ("n", ctypes.c_int)]
+
+
+class FitGeometry(ctypes.Structure):
+    _fields_ = [("n_dm", ctypes.c_int), ("dms", ctypes.POINTER(Dm)), ("n_dir", ctypes.c_int),
+                ("theta", ctypes.POINTER(ctypes.c_double)), ("n_sub", ctypes.c_int),
+                ("d_sub", ctypes.c_double), ("valid", ctypes.POINTER(ctypes.c_ubyte))]
+
+
+class FitInfo(ctypes.Structure):
+    _fields_ = [("n_act", ctypes.c_longlong), ("n_active", ctypes.c_longlong),
+                ("n_points", ctypes.c_int), ("n_dir", ctypes.c_int), ("n_dm", ctypes.c_int),
+                ("kernels_per_iteration", ctypes.c_int), ("kernels_per_solve_base", ctypes.c_int),
+                ("device_bytes", ctypes.c_longlong)]
+
+
 # (name, restype, argtypes) of every symbol declared in include/tomo.h
 _VP = ctypes.c_void_p
 _I = ctypes.c_int
@@ -119,6 +136,14 @@ SIGNATURES = [
     ("tomo_server_get_plan", _I, [_VP, _I, ctypes.POINTER(_VP)]),
     ("tomo_server_clock", ctypes.c_double, []),
     ("tomo_server_destroy", None, [_VP]),
+    ("tomo_fit_create", _I, [_VP, ctypes.POINTER(FitGeometry), ctypes.POINTER(_VP)]),
+    ("tomo_fit_get_info", _I, [_VP, ctypes.POINTER(FitInfo)]),
+    ("tomo_fit_apply_normal", _I, [_VP, _VP, _VP, _VP]),
+    ("tomo_fit_rhs", _I, [_VP, _VP, _VP, _VP]),
+    ("tomo_fit_residual_rms", _I, [_VP, _VP, _VP, _VP, _VP]),
+    ("tomo_fit_solve", _I, [_VP, _VP, _VP, _I, _I, _VP]),
+    ("tomo_reconstruct", _I, [_VP, _VP, _VP, _VP, _I, _I, _I, _VP]),
+    ("tomo_fit_destroy", None, [_VP]),
 ]
 
 _lib = None
@@ -314,6 +339,82 @@ def solve_batch(plans, slopes, coeffs, iters, warm=True, stream=None):
                                  for p, s in zip(plans, slopes)])
     cp = (ctypes.c_void_p * n)(*[p._tensor(c, p.n, "coeffs").value for p, c in zip(plans, coeffs)])
     _check(load_library().tomo_solve_batch(ph, sp, cp, n, int(iters), int(bool(warm)), _stream(stream)))
+
+
+def fit_geometry_struct(fit):
+    """C structs of a fitting geometry dict (``geom["fitting"]``, see
+    ``synth.configs.with_fitting``); returns (FitGeometry, keep-alive list)."""
+    dms = (Dm * len(fit["dms"]))()
+    for i, m in enumerate(fit["dms"]):
+        dms[i].altitude, dms[i].pitch, dms[i].n = float(m["altitude"]), float(m["pitch"]), int(m["n"])
+    th = np.ascontiguousarray(np.asarray(fit["directions"], dtype=np.float64).reshape(-1, 2))
+    v = np.ascontiguousarray(np.asarray(fit["valid"], dtype=np.uint8))
+    if v.shape != (fit["n_sub"], fit["n_sub"]):
+        raise ValueError("valid mask must be [n_sub, n_sub]")
+    g = FitGeometry(len(fit["dms"]), dms, th.shape[0], th.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                    int(fit["n_sub"]), float(fit["d_sub"]), v.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)))
+    return g, [dms, th, v]
+
+
+class Fit:
+    """The fitting step of a plan (tomo_fit_*): mirror commands from the layers."""
+
+    def __init__(self, plan, fit):
+        lib = load_library()
+        g, keep = fit_geometry_struct(fit)
+        h = ctypes.c_void_p()
+        _check(lib.tomo_fit_create(plan.handle, ctypes.byref(g), ctypes.byref(h)))
+        del keep
+        self._h = h
+        self.plan = plan
+        inf = FitInfo()
+        _check(lib.tomo_fit_get_info(h, ctypes.byref(inf)))
+        self.info = inf
+        self.n = int(inf.n_act)
+
+    def apply_normal(self, a, out, stream=None):
+        p = self.plan
+        _check(load_library().tomo_fit_apply_normal(
+            self._h, p._tensor(a, self.n, "a"), p._tensor(out, self.n, "out"), _stream(stream)))
+
+    def rhs(self, layers, out, stream=None):
+        p = self.plan
+        _check(load_library().tomo_fit_rhs(
+            self._h, p._tensor(layers, p.n, "layers"), p._tensor(out, self.n, "out"), _stream(stream)))
+
+    def residual_rms(self, layers, a, out, stream=None):
+        """out (float64 CUDA tensor of n_dir): the piston-removed RMS of P_j phi - H_j a per
+        direction (a = None: no correction)."""
+        import torch
+        p = self.plan
+        _check(load_library().tomo_fit_residual_rms(
+            self._h, p._tensor(layers, p.n, "layers"), None if a is None else p._tensor(a, self.n, "a"),
+            p._tensor(out, int(self.info.n_dir), "out", torch.float64), _stream(stream)))
+
+    def solve(self, layers, a, iters, warm=True, stream=None):
+        """CG on H^T H a = H^T P phi; a holds the start (warm) and receives the commands."""
+        p = self.plan
+        _check(load_library().tomo_fit_solve(
+            self._h, p._tensor(layers, p.n, "layers"), p._tensor(a, self.n, "a"), int(iters),
+            int(bool(warm)), _stream(stream)))
+
+    def reconstruct(self, slopes, coeffs, a, iters, fit_iters, warm=True, stream=None):
+        """Slopes to mirror commands: the plan's solve, W^-1, then the fitting solve."""
+        p = self.plan
+        _check(load_library().tomo_reconstruct(
+            self._h, p._tensor(slopes, p.n_slopes, "slopes"), p._tensor(coeffs, p.n, "coeffs"),
+            p._tensor(a, self.n, "a"), int(iters), int(fit_iters), int(bool(warm)), _stream(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load_library().tomo_fit_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:

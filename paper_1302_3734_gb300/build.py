@@ -26,11 +26,11 @@ def _cuda_home():
 
 
 def _sources():
-    return [os.path.join(CSRC, f) for f in ("kernels.cu", "api.cu", "noalloc.cu", "server.cu", "host_plan.cpp")]
+    return [os.path.join(CSRC, f) for f in ("kernels.cu", "api.cu", "noalloc.cu", "server.cu", "fit.cu", "host_plan.cpp")]
 
 
 def _deps():
-    files = _sources() + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    files = _sources() + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     files.append(os.path.join(INCLUDE, "tomo.h"))
     return files
 

@@ -35,6 +35,7 @@ tomo_status fail(tomo_status st, const std::string &msg) {
 
 namespace tomo {
 tomo_status set_error(tomo_status st, const std::string &msg) { return fail(st, msg); }
+void count_launches(long long k) { g_launches.fetch_add(k); }
 }  // namespace tomo
 
 namespace {
@@ -119,7 +120,7 @@ tomo_status enqueue_solve(tomo_plan *tp, const LaunchSet &L, const void *const *
     io.active = active;
     for (int i = 0; i < L.count; ++i) io.in1[i] = slopes[i];
     TOMO_TRY(timed(tp, kKindFwd, s, [&] {
-      return launch_forward(L.precision, warm ? 1 : 2, L.max_layers, L.d_inst, L.fwd, L.n_fwd, io, s);
+      return launch_forward(L.precision, warm ? 1 : 2, L.max_layers, L.elong, L.d_inst, L.fwd, L.n_fwd, io, s);
     }, "forward (residual)"));
     ++nk;
   }
@@ -144,7 +145,7 @@ tomo_status enqueue_solve(tomo_plan *tp, const LaunchSet &L, const void *const *
                               L.cl, L.n_cl, L.C, L.smem, none, s);
     }, "synthesis"));
     TOMO_TRY(timed(tp, kKindFwd, s, [&] {
-      return launch_forward(L.precision, 0, L.max_layers, L.d_inst, L.fwd, L.n_fwd, none, s);
+      return launch_forward(L.precision, 0, L.max_layers, L.elong, L.d_inst, L.fwd, L.n_fwd, none, s);
     }, "forward"));
     TOMO_TRY(timed(tp, kKindAnalysis, s, [&] {
       return launch_analysis(L.precision, 1, 1, L.lf, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem_a, none, s, L.split, L.smem_g);
@@ -165,19 +166,6 @@ tomo_status check_plan(const tomo_plan *p) {
   if (!p) return fail(TOMO_ERR_ARG, "plan is NULL");
   return TOMO_OK;
 }
-
-struct DeviceGuard {
-  int prev = -1;
-  explicit DeviceGuard(int dev) {
-    cudaGetDevice(&prev);
-    if (prev != dev) cudaSetDevice(dev);
-  }
-  ~DeviceGuard() {
-    int cur = -1;
-    cudaGetDevice(&cur);
-    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
-  }
-};
 
 // ||r|| after a solve: the FP64 partials of the last kernel that produced r
 // (the update, or the initial residual when iters == 0), summed on the host
@@ -238,6 +226,13 @@ void drop_batches_of(const tomo_plan *p) {
 }  // namespace
 
 namespace tomo {
+
+tomo_status enqueue_plan_solve(tomo_plan *p, const void *slopes, void *x, int iters, int warm, cudaStream_t s,
+                               int *n_kernels) {
+  const void *sl[1] = {slopes};
+  void *xs[1] = {x};
+  return enqueue_solve(nullptr, p->ls, sl, xs, iters, warm ? 1 : 0, s, n_kernels);
+}
 
 void free_batch(Batch *b) {
   for (auto &g : b->graphs) cudaGraphExecDestroy(g.exec);
@@ -300,6 +295,7 @@ tomo_status build_batch(tomo_plan *const *plans, int count, Batch **out) {
       L.precision = H.precision;
       L.split = H.gather_staged ? 0 : 1;
       L.smem_g = std::max(L.smem_g, static_cast<size_t>(H.smem_gather));
+      for (const auto &w : H.wfs) L.elong |= w.elong;
     }
     Arena A;
     const size_t o_i = A.take(sizeof(InstDev) * insts.size());
@@ -684,6 +680,8 @@ tomo_status tomo_plan_create_ex(const tomo_geometry *g, const tomo_plan_options 
   L.precision = H.precision;
   L.split = H.gather_staged ? 0 : 1;
   L.smem_g = static_cast<size_t>(H.smem_gather);
+  L.elong = 0;
+  for (const auto &w : H.wfs) L.elong |= w.elong;
   *out = p;
   g_err.clear();
   return TOMO_OK;
@@ -867,7 +865,7 @@ tomo_status tomo_apply_normal(tomo_plan *p, const void *d_in, void *d_out, void 
     return launch_synthesis(L.precision, 0, L.lf, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem, a, s);
   }, "synthesis"));
   IoArgs b{};
-  TOMO_TRY(timed(p, kKindFwd, s, [&] { return launch_forward(L.precision, 0, L.max_layers, L.d_inst, L.fwd, L.n_fwd, b, s); },
+  TOMO_TRY(timed(p, kKindFwd, s, [&] { return launch_forward(L.precision, 0, L.max_layers, L.elong, L.d_inst, L.fwd, L.n_fwd, b, s); },
                  "forward"));
   IoArgs c{};
   c.in1[0] = d_in;
@@ -885,7 +883,7 @@ tomo_status tomo_rhs(tomo_plan *p, const void *d_slopes, void *d_out, void *cuda
   const LaunchSet &L = p->ls;
   IoArgs a{};
   a.in1[0] = d_slopes;
-  TOMO_TRY(timed(p, kKindFwd, s, [&] { return launch_forward(L.precision, 2, L.max_layers, L.d_inst, L.fwd, L.n_fwd, a, s); },
+  TOMO_TRY(timed(p, kKindFwd, s, [&] { return launch_forward(L.precision, 2, L.max_layers, L.elong, L.d_inst, L.fwd, L.n_fwd, a, s); },
                  "forward (data)"));
   IoArgs c{};
   c.out0[0] = d_out;

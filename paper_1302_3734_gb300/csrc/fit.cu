@@ -1,0 +1,854 @@
+// The fitting step (Sec. 4.1, eqs. fit_step_ideal / fit_step_min): mirror
+// commands a from the reconstructed layers phi by CG on H^T H a = H^T P phi,
+// and tomo_reconstruct, slopes to commands in one graph.
+//
+// H_j a (x) = sum_k a_k(x + h_k theta_j), each mirror a piecewise-bilinear
+// function of its actuator grid; P_j phi (x) = sum_l phi_l(x + h_l theta_j)
+// (eq. ngsproj), bilinear on the periodic layer grids; x runs over the corners
+// of the valid subapertures of the aperture sampling grid.  Three kernels per
+// CG iteration:
+//
+//   k_fit_mirror   u_j = H_j p on every (direction, corner), with the CG
+//                  direction p = r + beta p formed on the fly      [corner per thread]
+//   k_fit_adjoint  q = sum_j H_j^T u_j as a gather over per-actuator tap
+//                  windows; writes p; p.q partials                  [4 threads per actuator]
+//   k_fit_update   alpha, a += alpha p, r -= alpha q, r.r partials  [actuator per thread]
+//
+// The tap tables (corner -> actuator and corner -> layer node, and for H^T
+// each actuator's window of corners with its weights) are built in FP64 on
+// the host from the same corner -> actuator taps, so the gather is the exact
+// transpose of the mirror kernel.  Inner products are accumulated as in the
+// tomography kernels (double-float per thread for FP32, one FP64 partial per
+// block, partials summed by every consumer block in a fixed order), so results
+// are bitwise reproducible.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/tomo.h"
+#include "common.h"
+#include "device_util.cuh"
+#include "launch.h"
+#include "plan_internal.h"
+
+namespace tomo {
+
+constexpr int kFitThreads = 256;
+constexpr int kMaxDm = 4;
+constexpr int kMaxFitDirs = 256;
+constexpr int kRrSlots = 4;   // r.r partial slots (ring over iterations), then 2 p.q slots
+
+// Everything the fitting kernels read (passed by value).
+struct FitDev {
+  int n_dir, n_dm, nc, n_layers;
+  int n_act, kw, nblk_adj, nblk_upd, part_stride, n_points;
+  int dm_n[kMaxDm], dm_off[kMaxDm], w_off[kMaxDm];
+  const unsigned char *act;   // nc*nc corner mask
+  const int2 *lay;            // per layer (N, offset in the layer vector)
+  const int *hx0, *hy0;       // [dm][dir][nc]: left / lower actuator of each corner column / row
+  const void *hfx, *hfy;      //   and its fraction (T)
+  const int *px0, *py0;       // [layer][dir][nc]: left / lower layer node (mod N)
+  const void *pfx, *pfy;      //   and its fraction (T)
+  const int *wx0, *wy0;       // per (dm, dir, actuator column / row): first corner of its window
+  const void *wxw, *wyw;      //   kw weights (T), zero beyond the window
+  void *u;                    // [dir][nc*nc]
+  void *r, *p, *q;            // [n_act]
+  double *part;               // (kRrSlots + 2) * part_stride
+  double *flag;               // nonzero after a breakdown
+};
+
+// Fixed-order sum of n FP64 partials, returned to every thread of the block.
+__device__ double fit_sum(const double *part, int n) {
+  __shared__ double s_v;
+  if (threadIdx.x < 32) {
+    double a = 0.0;
+    for (int i = threadIdx.x; i < n; i += 32) a += part[i];
+    a = warp_sum(a);
+    if (threadIdx.x == 0) s_v = a;
+  }
+  __syncthreads();
+  const double v = s_v;
+  __syncthreads();
+  return v;
+}
+
+// r.r of CG iteration `it` (it = 0: the initial residual, from the adjoint
+// kernel; later ones from the updates).
+__device__ __forceinline__ double fit_rr(const FitDev &F, int it) {
+  return fit_sum(F.part + (it % kRrSlots) * F.part_stride, it == 0 ? F.nblk_adj : F.nblk_upd);
+}
+
+__device__ __forceinline__ double fit_beta(const FitDev &F, int it) {
+  const double num = fit_rr(F, it), den = fit_rr(F, it - 1);
+  return den != 0.0 ? num / den : 0.0;
+}
+
+__device__ __forceinline__ float fit_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fit_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// CG direction of actuator i: p = r (first iteration) or r + beta p.
+template <typename T>
+__device__ __forceinline__ T fit_dir(const T *r, const T *p, int i, bool first, T beta) {
+  return first ? r[i] : fit_fma(beta, p[i], r[i]);
+}
+
+// MODE 0: u_j = H_j p, p the CG direction of iteration `it` (from r and the
+//         previous p).
+// MODE 1: u_j = P_j phi - H_j x (x = NULL: P_j phi).
+// MODE 2: u_j = H_j x.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kFitThreads) k_fit_mirror(FitDev F, const T *__restrict__ x,
+                                                           const T *__restrict__ phi, int it) {
+  pdl_trigger();
+  const int j = blockIdx.y, nc = F.nc, nn = nc * nc;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool on = c < nn && F.act[c];
+  const int a = c % nc, b = c / nc;
+  pdl_wait();
+  T beta = T(0);
+  const bool first = it == 0;
+  if (MODE == 0 && !first) beta = T(fit_beta(F, it));
+  if (c >= nn) return;
+  T val = T(0);
+  if (on) {
+    if (MODE == 1 && phi) {
+      const T *fx = static_cast<const T *>(F.pfx), *fy = static_cast<const T *>(F.pfy);
+      for (int l = 0; l < F.n_layers; ++l) {
+        const int2 L = F.lay[l];
+        const int tx = (l * F.n_dir + j) * nc + a, ty = (l * F.n_dir + j) * nc + b;
+        const int x0 = F.px0[tx], y0 = F.py0[ty];
+        const int x1 = (x0 + 1) & (L.x - 1), y1 = (y0 + 1) & (L.x - 1);
+        const T wx = fx[tx], wy = fy[ty];
+        const T *g = phi + L.y;
+        val += (T(1) - wy) * ((T(1) - wx) * g[y0 * L.x + x0] + wx * g[y0 * L.x + x1]) +
+               wy * ((T(1) - wx) * g[y1 * L.x + x0] + wx * g[y1 * L.x + x1]);
+      }
+    }
+    if (MODE != 1 || x) {
+      const T *fx = static_cast<const T *>(F.hfx), *fy = static_cast<const T *>(F.hfy);
+      const T *r = static_cast<const T *>(F.r), *p = static_cast<const T *>(F.p);
+      T h = T(0);
+      for (int k = 0; k < F.n_dm; ++k) {
+        const int n = F.dm_n[k], o = F.dm_off[k];
+        const int tx = (k * F.n_dir + j) * nc + a, ty = (k * F.n_dir + j) * nc + b;
+        const int x0 = F.hx0[tx], y0 = F.hy0[ty];
+        const T wx1 = fx[tx], wy1 = fy[ty];
+        const T wx[2] = {T(1) - wx1, wx1}, wy[2] = {T(1) - wy1, wy1};
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy) {
+          const int iy = y0 + dy;
+          if (iy < 0 || iy >= n) continue;
+          T row = T(0);
+#pragma unroll
+          for (int dx = 0; dx < 2; ++dx) {
+            const int ix = x0 + dx;
+            if (ix < 0 || ix >= n) continue;
+            const int i = o + iy * n + ix;
+            const T v = MODE == 0 ? fit_dir(r, p, i, first, beta) : x[i];
+            row += wx[dx] * v;
+          }
+          h += wy[dy] * row;
+        }
+      }
+      val = MODE == 1 ? val - h : h;
+    }
+  }
+  static_cast<T *>(F.u)[j * nn + c] = val;
+}
+
+// sum_j H_j^T u_j for actuator `act` of mirror k (column i, row jj), over the
+// directions j = g, g+4, ...; the four direction groups are then combined
+// across lanes in a fixed order.
+template <typename T, int KW>
+__device__ __forceinline__ T fit_gather(const FitDev &F, int k, int i, int jj, int g) {
+  const int n = F.dm_n[k], nc = F.nc, nn = nc * nc;
+  const T *u = static_cast<const T *>(F.u);
+  const T *wxw = static_cast<const T *>(F.wxw), *wyw = static_cast<const T *>(F.wyw);
+  T s = T(0);
+  for (int j = g; j < F.n_dir; j += 4) {
+    const int ex = F.w_off[k] + j * n + i, ey = F.w_off[k] + j * n + jj;
+    const T *ux = u + j * nn + F.wy0[ey] * nc + F.wx0[ex];
+    T wx[KW];
+#pragma unroll
+    for (int t = 0; t < KW; ++t) wx[t] = wxw[ex * KW + t];
+    T acc = T(0);
+#pragma unroll
+    for (int t2 = 0; t2 < KW; ++t2) {
+      T row = T(0);
+#pragma unroll
+      for (int t1 = 0; t1 < KW; ++t1) row += wx[t1] * ux[t2 * nc + t1];
+      acc += wyw[ey * KW + t2] * row;
+    }
+    s += acc;
+  }
+  s += __shfl_xor_sync(0xffffffffu, s, 1);
+  s += __shfl_xor_sync(0xffffffffu, s, 2);
+  return s;
+}
+
+// MODE 0 (CG iteration `it`): q = H^T u, p written, p.q partials.
+// MODE 1 (initial residual): r = H^T u, r.r partials.
+// MODE 2: out = H^T u.
+template <typename T, int MODE, int KW>
+__global__ void __launch_bounds__(kFitThreads) k_fit_adjoint(FitDev F, T *__restrict__ out, int it) {
+  pdl_trigger();
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int g = gid & 3, act = gid >> 2;
+  const bool on = act < F.n_act;
+  int k = 0;
+  while (k + 1 < F.n_dm && act >= F.dm_off[k + 1]) ++k;
+  const int loc = act - F.dm_off[k], n = F.dm_n[k];
+  const int i = loc % n, jj = loc / n;
+  pdl_wait();
+  T beta = T(0);
+  const bool first = it == 0;
+  if (MODE == 0 && !first) beta = T(fit_beta(F, it));
+  // idle lanes take part in the shuffles with an empty direction loop
+  const T s = on ? fit_gather<T, KW>(F, k, i, jj, g) : fit_gather<T, KW>(F, 0, 0, 0, F.n_dir);
+  Acc<T> d, z;
+  if (on && g == 0) {
+    T *r = static_cast<T *>(F.r), *p = static_cast<T *>(F.p), *q = static_cast<T *>(F.q);
+    if (MODE == 2) {
+      out[act] = s;
+    } else if (MODE == 1) {
+      r[act] = s;
+      d.add_prod(s, s);
+    } else {
+      const T pn = fit_dir(r, p, act, first, beta);
+      p[act] = pn;
+      q[act] = s;
+      d.add_prod(pn, s);
+    }
+  }
+  if (MODE != 2) {
+    const double2 v = block_sum2(d, z);
+    const int slot = MODE == 1 ? 0 : kRrSlots + (it & 1);
+    if (threadIdx.x == 0) F.part[slot * F.part_stride + blockIdx.x] = v.x;
+  }
+}
+
+// alpha = r.r / p.q of iteration `it`; a += alpha p (a = alpha p when the
+// solve started from zero), r -= alpha q, r.r partials of iteration it + 1.
+template <typename T>
+__global__ void __launch_bounds__(kFitThreads) k_fit_update(FitDev F, T *__restrict__ a, int it, int cold) {
+  pdl_trigger();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  pdl_wait();
+  const double rr = fit_rr(F, it);
+  const double pq = fit_sum(F.part + (kRrSlots + (it & 1)) * F.part_stride, F.nblk_adj);
+  double alpha = 0.0;
+  if (pq == 0.0 && rr == 0.0) {
+    alpha = 0.0;   // exact iterate: CG stops moving
+  } else if (!(pq > 0.0) || !isfinite(rr / pq)) {
+    if (i == 0) F.flag[0] = 1.0;
+  } else {
+    alpha = rr / pq;
+  }
+  Acc<T> d, z;
+  if (i < F.n_act) {
+    const T al = T(alpha);
+    const T *p = static_cast<const T *>(F.p), *q = static_cast<const T *>(F.q);
+    T *r = static_cast<T *>(F.r);
+    a[i] = (cold && it == 0) ? al * p[i] : fit_fma(al, p[i], a[i]);
+    const T rn = fit_fma(-al, q[i], r[i]);
+    r[i] = rn;
+    d.add_prod(rn, rn);
+  }
+  const double2 v = block_sum2(d, z);
+  if (threadIdx.x == 0) F.part[((it + 1) % kRrSlots) * F.part_stride + blockIdx.x] = v.x;
+}
+
+// r(theta_j) of the residual u_j on the sampling points: the root mean square
+// after removing the mean, sqrt(mean(u^2) - mean(u)^2), one block per
+// direction (the quality measure of Sec. 5.1; the Strehl ratio follows on the
+// host).
+template <typename T>
+__global__ void __launch_bounds__(kFitThreads) k_fit_rms(FitDev F, double *__restrict__ rms) {
+  pdl_trigger();
+  const int j = blockIdx.x, nn = F.nc * F.nc;
+  const T *u = static_cast<const T *>(F.u) + static_cast<size_t>(j) * nn;
+  pdl_wait();
+  Acc<T> s1, s2;
+  for (int c = threadIdx.x; c < nn; c += blockDim.x)
+    if (F.act[c]) {
+      s1.add(u[c]);
+      s2.add_prod(u[c], u[c]);
+    }
+  const double2 v = block_sum2(s1, s2);
+  if (threadIdx.x == 0) {
+    const double m = v.x / F.n_points, q = v.y / F.n_points;
+    rms[j] = sqrt(fmax(0.0, q - m * m));
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+
+template <typename T>
+cudaError_t fit_mirror(int mode, const FitDev &F, const T *x, const T *phi, int it, cudaStream_t s) {
+  const dim3 g((F.nc * F.nc + kFitThreads - 1) / kFitThreads, F.n_dir);
+  if (mode == 0) return launch_ex(k_fit_mirror<T, 0>, g, kFitThreads, 0, 0, s, F, x, phi, it);
+  if (mode == 1) return launch_ex(k_fit_mirror<T, 1>, g, kFitThreads, 0, 0, s, F, x, phi, it);
+  return launch_ex(k_fit_mirror<T, 2>, g, kFitThreads, 0, 0, s, F, x, phi, it);
+}
+
+template <typename T, int KW>
+cudaError_t fit_adjoint_kw(int mode, const FitDev &F, T *out, int it, cudaStream_t s) {
+  const dim3 g(F.nblk_adj);
+  if (mode == 0) return launch_ex(k_fit_adjoint<T, 0, KW>, g, kFitThreads, 0, 0, s, F, out, it);
+  if (mode == 1) return launch_ex(k_fit_adjoint<T, 1, KW>, g, kFitThreads, 0, 0, s, F, out, it);
+  return launch_ex(k_fit_adjoint<T, 2, KW>, g, kFitThreads, 0, 0, s, F, out, it);
+}
+
+template <typename T>
+cudaError_t fit_adjoint(int mode, const FitDev &F, T *out, int it, cudaStream_t s) {
+  if (F.kw <= 2) return fit_adjoint_kw<T, 2>(mode, F, out, it, s);
+  if (F.kw <= 4) return fit_adjoint_kw<T, 4>(mode, F, out, it, s);
+  return fit_adjoint_kw<T, 8>(mode, F, out, it, s);
+}
+
+template <typename T>
+cudaError_t fit_rms(const FitDev &F, double *rms, cudaStream_t s) {
+  return launch_ex(k_fit_rms<T>, dim3(F.n_dir), kFitThreads, 0, 0, s, F, rms);
+}
+
+template <typename T>
+cudaError_t fit_update(const FitDev &F, T *a, int it, int cold, cudaStream_t s) {
+  return launch_ex(k_fit_update<T>, dim3(F.nblk_upd), kFitThreads, 0, 0, s, F, a, it, cold);
+}
+
+}  // namespace tomo
+
+// ---------------------------------------------------------------- the object
+
+struct tomo_fit {
+  tomo_plan *plan = nullptr;
+  int device = 0, precision = 0;
+  size_t esz = 4;
+  tomo::FitDev F{};
+  void *arena = nullptr;
+  size_t arena_bytes = 0;
+  void *phi = nullptr;   // layer grids of tomo_reconstruct
+  long long n_active = 0;
+  int n_points = 0;
+  cudaStream_t cap = nullptr;
+  struct Graph {
+    int kind;
+    const void *in;
+    void *x, *a;
+    int iters, fit_iters, warm;
+    cudaGraphExec_t exec;
+    int kernels;
+  };
+  std::vector<Graph> graphs;
+};
+
+namespace {
+
+using tomo::FitDev;
+
+tomo_status fit_fail(tomo_status st, const std::string &m) { return tomo::set_error(st, m); }
+
+tomo_status fit_cuda(cudaError_t e, const char *where) {
+  return tomo::set_error(TOMO_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define FIT_CUDA(call, where)                          \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return fit_cuda(e_, where); \
+  } while (0)
+
+#define FIT_TRY(x)                  \
+  do {                              \
+    tomo_status st_ = (x);          \
+    if (st_ != TOMO_OK) return st_; \
+  } while (0)
+
+// Host tables of one fit (FP64; converted to the plan's element type on upload).
+struct FitTables {
+  std::vector<unsigned char> act;
+  std::vector<int> hx0, hy0, px0, py0, wx0, wy0;
+  std::vector<double> hfx, hfy, pfx, pfy, wxw, wyw;
+  std::vector<int2> lay;
+  int kw = 0, n_points = 0;
+  long long n_active = 0;
+};
+
+// Left tap and fraction of coordinate g: g = i0 + f, 0 <= f < 1.
+inline void tap(double g, int *i0, double *f) {
+  const double fl = std::floor(g);
+  *i0 = static_cast<int>(fl);
+  *f = g - fl;
+}
+
+// Corner -> actuator taps of mirror k along one axis for direction offset
+// `shift` (h_k theta), and each actuator's window of corners.  Returns false
+// if a window is not contiguous or longer than 8.
+bool mirror_axis(int nc, int n_sub, double d, const tomo_dm &m, double shift, int *i0, double *f,
+                 std::vector<std::vector<std::pair<int, double>>> *win) {
+  win->assign(m.n, {});
+  for (int a = 0; a < nc; ++a) {
+    const double g = ((a - 0.5 * n_sub) * d + shift) / m.pitch + 0.5 * (m.n - 1);
+    tap(g, &i0[a], &f[a]);
+    const double w[2] = {1.0 - f[a], f[a]};
+    for (int t = 0; t < 2; ++t) {
+      const int i = i0[a] + t;
+      if (i >= 0 && i < m.n && w[t] != 0.0) (*win)[i].push_back({a, w[t]});
+    }
+  }
+  for (const auto &v : *win) {
+    if (v.size() > 8) return false;
+    for (size_t t = 1; t < v.size(); ++t)
+      if (v[t].first != v[t - 1].first + 1) return false;
+  }
+  return true;
+}
+
+tomo_status build_tables(const tomo::HostPlan &H, const tomo_fit_geometry *g, FitTables *T, std::string *err) {
+  const int nc = g->n_sub + 1, ns = g->n_sub, nd = g->n_dir;
+  const double d = g->d_sub;
+  T->act.assign(static_cast<size_t>(nc) * nc, 0);
+  for (int b = 0; b < ns; ++b)
+    for (int a = 0; a < ns; ++a)
+      if (g->valid[b * ns + a])
+        for (int db = 0; db < 2; ++db)
+          for (int da = 0; da < 2; ++da) T->act[(b + db) * nc + a + da] = 1;
+  T->n_points = 0;
+  for (auto v : T->act) T->n_points += v;
+  if (T->n_points == 0) {
+    *err = "the aperture sampling has no valid subaperture";
+    return TOMO_ERR_GEOMETRY;
+  }
+  // mirror taps and windows
+  std::vector<std::vector<std::pair<int, double>>> wins_x, wins_y;
+  std::vector<std::vector<std::vector<std::pair<int, double>>>> allx, ally;   // [k*nd + j][i]
+  T->hx0.resize(static_cast<size_t>(g->n_dm) * nd * nc);
+  T->hy0.resize(T->hx0.size());
+  T->hfx.resize(T->hx0.size());
+  T->hfy.resize(T->hx0.size());
+  int kw = 1;
+  for (int k = 0; k < g->n_dm; ++k)
+    for (int j = 0; j < nd; ++j) {
+      const tomo_dm &m = g->dms[k];
+      const size_t o = (static_cast<size_t>(k) * nd + j) * nc;
+      if (!mirror_axis(nc, ns, d, m, m.altitude * g->theta[2 * j], &T->hx0[o], &T->hfx[o], &wins_x) ||
+          !mirror_axis(nc, ns, d, m, m.altitude * g->theta[2 * j + 1], &T->hy0[o], &T->hfy[o], &wins_y)) {
+        *err = "mirror " + std::to_string(k) + ": an actuator's window of sampling corners is longer than 8";
+        return TOMO_ERR_UNSUPPORTED;
+      }
+      for (const auto &v : wins_x) kw = std::max(kw, static_cast<int>(v.size()));
+      for (const auto &v : wins_y) kw = std::max(kw, static_cast<int>(v.size()));
+      allx.push_back(wins_x);
+      ally.push_back(wins_y);
+    }
+  T->kw = kw <= 2 ? 2 : (kw <= 4 ? 4 : 8);
+  if (T->kw > nc) {
+    *err = "the aperture sampling grid is narrower than an actuator's window";
+    return TOMO_ERR_UNSUPPORTED;
+  }
+  // windows: start corner (shifted so the window stays inside 0..nc-1) and kw weights
+  for (int k = 0; k < g->n_dm; ++k)
+    for (int j = 0; j < nd; ++j)
+      for (int axis = 0; axis < 2; ++axis) {
+        const auto &wins = (axis == 0 ? allx : ally)[k * nd + j];
+        auto &w0 = axis == 0 ? T->wx0 : T->wy0;
+        auto &ww = axis == 0 ? T->wxw : T->wyw;
+        for (const auto &v : wins) {
+          int s = v.empty() ? 0 : v.front().first;
+          const int s_eff = std::min(s, nc - T->kw);
+          w0.push_back(s_eff);
+          std::vector<double> w(T->kw, 0.0);
+          for (size_t t = 0; t < v.size(); ++t) w[s - s_eff + t] = v[t].second;
+          ww.insert(ww.end(), w.begin(), w.end());
+        }
+      }
+  // actuators reached by a sampling point: nonzero diagonal of H^T H
+  T->n_active = 0;
+  for (int k = 0; k < g->n_dm; ++k) {
+    const int n = g->dms[k].n;
+    std::vector<unsigned char> hit(static_cast<size_t>(n) * n, 0);
+    for (int j = 0; j < nd; ++j) {
+      const size_t o = (static_cast<size_t>(k) * nd + j) * nc;
+      for (int b = 0; b < nc; ++b)
+        for (int a = 0; a < nc; ++a) {
+          if (!T->act[b * nc + a]) continue;
+          const double wx[2] = {1.0 - T->hfx[o + a], T->hfx[o + a]};
+          const double wy[2] = {1.0 - T->hfy[o + b], T->hfy[o + b]};
+          for (int dy = 0; dy < 2; ++dy)
+            for (int dx = 0; dx < 2; ++dx) {
+              const int ix = T->hx0[o + a] + dx, iy = T->hy0[o + b] + dy;
+              if (ix >= 0 && ix < n && iy >= 0 && iy < n && wx[dx] * wy[dy] > 0.0) hit[iy * n + ix] = 1;
+            }
+        }
+    }
+    for (auto v : hit) T->n_active += v;
+  }
+  // layer taps (natural guide star: no cone)
+  const int L = H.n_layers;
+  T->px0.resize(static_cast<size_t>(L) * nd * nc);
+  T->py0.resize(T->px0.size());
+  T->pfx.resize(T->px0.size());
+  T->pfy.resize(T->px0.size());
+  for (int l = 0; l < L; ++l) {
+    const int N = H.layers[l].N;
+    T->lay.push_back({N, H.layers[l].off});
+    for (int j = 0; j < nd; ++j)
+      for (int a = 0; a < nc; ++a) {
+        const size_t o = (static_cast<size_t>(l) * nd + j) * nc + a;
+        const double r = (a - 0.5 * ns) * d;
+        for (int axis = 0; axis < 2; ++axis) {
+          const double gc = (r + g->theta[2 * j + axis] * H.layer_alt[l]) / H.layer_dx[l] + 0.5 * N;
+          int i0;
+          double f;
+          tap(gc, &i0, &f);
+          i0 = ((i0 % N) + N) % N;
+          (axis == 0 ? T->px0 : T->py0)[o] = i0;
+          (axis == 0 ? T->pfx : T->pfy)[o] = f;
+        }
+      }
+  }
+  return TOMO_OK;
+}
+
+size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+// The launches of one fitting solve on stream s; they are added to the launch
+// count.
+template <typename T>
+tomo_status enqueue_fit(tomo_fit *f, const void *layers, void *a, int iters, int warm, cudaStream_t s,
+                        int *nk) {
+  const FitDev &F = f->F;
+  T *av = static_cast<T *>(a);
+  int k = 0;
+  if (!warm && iters == 0) FIT_CUDA(cudaMemsetAsync(a, 0, F.n_act * sizeof(T), s), "zero start");
+  FIT_CUDA(tomo::fit_mirror<T>(1, F, warm ? av : nullptr, static_cast<const T *>(layers), 0, s), "fit residual");
+  FIT_CUDA(tomo::fit_adjoint<T>(1, F, nullptr, 0, s), "fit residual gather");
+  k += 2;
+  for (int it = 0; it < iters; ++it) {
+    FIT_CUDA(tomo::fit_mirror<T>(0, F, nullptr, nullptr, it, s), "fit mirror");
+    FIT_CUDA(tomo::fit_adjoint<T>(0, F, nullptr, it, s), "fit gather");
+    FIT_CUDA(tomo::fit_update<T>(F, av, it, warm ? 0 : 1, s), "fit update");
+    k += 3;
+  }
+  tomo::count_launches(k);
+  *nk = k;
+  return TOMO_OK;
+}
+
+tomo_status enqueue_fit_any(tomo_fit *f, const void *layers, void *a, int iters, int warm, cudaStream_t s,
+                            int *nk) {
+  return f->precision == 0 ? enqueue_fit<float>(f, layers, a, iters, warm, s, nk)
+                           : enqueue_fit<double>(f, layers, a, iters, warm, s, nk);
+}
+
+// kind 0: tomo_fit_solve, 1: tomo_reconstruct.
+tomo_status enqueue_kind(tomo_fit *f, int kind, const void *in, void *x, void *a, int iters, int fit_iters,
+                         int warm, cudaStream_t s, int *nk) {
+  if (kind == 0) return enqueue_fit_any(f, in, a, fit_iters, warm, s, nk);
+  int k1 = 0, k2 = 0;
+  FIT_TRY(tomo::enqueue_plan_solve(f->plan, in, x, iters, warm, s, &k1));
+  // phi = W^-1 c into the fit's layer buffer
+  tomo_plan *p = f->plan;
+  tomo::IoArgs io{};
+  io.in0[0] = x;
+  io.out0[0] = f->phi;
+  const tomo::LaunchSet &L = p->ls;
+  FIT_CUDA(tomo::launch_synthesis(L.precision, 0, L.lf, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem, io, s),
+           "synthesis of the reconstructed layers");
+  tomo::count_launches(1);
+  FIT_TRY(enqueue_fit_any(f, f->phi, a, fit_iters, warm, s, &k2));
+  *nk = k1 + 1 + k2;
+  return TOMO_OK;
+}
+
+tomo_status run_graph(tomo_fit *f, int kind, const void *in, void *x, void *a, int iters, int fit_iters,
+                      int warm, cudaStream_t s) {
+  tomo_fit::Graph *ge = nullptr;
+  for (auto &g : f->graphs)
+    if (g.kind == kind && g.in == in && g.x == x && g.a == a && g.iters == iters && g.fit_iters == fit_iters &&
+        g.warm == warm)
+      ge = &g;
+  if (!ge) {
+    if (f->graphs.size() >= 16) {
+      cudaGraphExecDestroy(f->graphs.front().exec);
+      f->graphs.erase(f->graphs.begin());
+    }
+    cudaGraph_t graph = nullptr;
+    FIT_CUDA(cudaStreamBeginCapture(f->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+    int nk = 0;
+    const long long before = tomo_launch_count();
+    tomo_status st = enqueue_kind(f, kind, in, x, a, iters, fit_iters, warm, f->cap, &nk);
+    tomo::count_launches(before - tomo_launch_count());   // a capture launches nothing
+    cudaError_t ce = cudaStreamEndCapture(f->cap, &graph);
+    if (st != TOMO_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    if (ce != cudaSuccess) return fit_cuda(ce, "end capture");
+    cudaGraphExec_t exec = nullptr;
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) return fit_cuda(ce, "graph instantiate");
+    f->graphs.push_back({kind, in, x, a, iters, fit_iters, warm, exec, nk});
+    ge = &f->graphs.back();
+  }
+  FIT_CUDA(cudaGraphLaunch(ge->exec, s), "graph launch");
+  tomo::count_launches(ge->kernels);
+  return TOMO_OK;
+}
+
+template <typename T>
+void put(std::vector<unsigned char> &img, size_t off, const std::vector<double> &v) {
+  T *d = reinterpret_cast<T *>(img.data() + off);
+  for (size_t i = 0; i < v.size(); ++i) d[i] = static_cast<T>(v[i]);
+}
+
+}  // namespace
+
+extern "C" {
+
+tomo_status tomo_fit_create(tomo_plan *p, const tomo_fit_geometry *g, tomo_fit **out) {
+  if (!p || !g || !out) return fit_fail(TOMO_ERR_ARG, "NULL argument");
+  *out = nullptr;
+  if (g->n_dm < 1 || g->n_dm > tomo::kMaxDm || !g->dms)
+    return fit_fail(TOMO_ERR_ARG, "n_dm must be in 1..4 with a mirror array");
+  if (g->n_dir < 1 || g->n_dir > tomo::kMaxFitDirs || !g->theta)
+    return fit_fail(TOMO_ERR_ARG, "n_dir must be in 1..256 with a direction array");
+  if (g->n_sub < 1 || g->n_sub > 1024 || !(g->d_sub > 0.0) || !std::isfinite(g->d_sub) || !g->valid)
+    return fit_fail(TOMO_ERR_ARG, "n_sub must be in 1..1024, d_sub > 0 and valid not NULL");
+  long long n_act = 0;
+  for (int k = 0; k < g->n_dm; ++k) {
+    const tomo_dm &m = g->dms[k];
+    if (m.n < 2 || m.n > 4096 || !(m.pitch > 0.0) || !(m.pitch <= 4.0 * g->d_sub) || !(m.altitude >= 0.0) ||
+        !std::isfinite(m.altitude))
+      return fit_fail(TOMO_ERR_ARG, "mirror " + std::to_string(k) +
+                                        ": n must be in 2..4096, 0 < pitch <= 4 d_sub and altitude >= 0");
+    n_act += static_cast<long long>(m.n) * m.n;
+  }
+  for (int j = 0; j < 2 * g->n_dir; ++j)
+    if (!std::isfinite(g->theta[j])) return fit_fail(TOMO_ERR_ARG, "directions must be finite");
+  if (n_act > (1LL << 28)) return fit_fail(TOMO_ERR_ARG, "too many actuators");
+  const tomo::HostPlan &H = p->hp;
+  FitTables T;
+  std::string err;
+  FIT_TRY(([&] {
+    tomo_status st = build_tables(H, g, &T, &err);
+    return st == TOMO_OK ? st : fit_fail(st, err);
+  }()));
+  tomo_fit *f = new tomo_fit();
+  f->plan = p;
+  f->device = p->device;
+  f->precision = H.precision;
+  f->esz = H.precision ? 8 : 4;
+  f->n_active = T.n_active;
+  f->n_points = T.n_points;
+  FitDev &F = f->F;
+  const int nc = g->n_sub + 1, nd = g->n_dir;
+  F.n_dir = nd;
+  F.n_dm = g->n_dm;
+  F.nc = nc;
+  F.n_layers = H.n_layers;
+  F.n_act = static_cast<int>(n_act);
+  F.kw = T.kw;
+  F.n_points = T.n_points;
+  F.nblk_adj = static_cast<int>((4 * n_act + tomo::kFitThreads - 1) / tomo::kFitThreads);
+  F.nblk_upd = static_cast<int>((n_act + tomo::kFitThreads - 1) / tomo::kFitThreads);
+  F.part_stride = std::max(F.nblk_adj, F.nblk_upd);
+  int off = 0, woff = 0;
+  for (int k = 0; k < g->n_dm; ++k) {
+    F.dm_n[k] = g->dms[k].n;
+    F.dm_off[k] = off;
+    F.w_off[k] = woff;
+    off += g->dms[k].n * g->dms[k].n;
+    woff += nd * g->dms[k].n;
+  }
+  for (int k = g->n_dm; k < tomo::kMaxDm; ++k) F.dm_off[k] = off;
+  // one arena: tables, then the workspace
+  const size_t es = f->esz;
+  struct Item { size_t *off; size_t bytes; };
+  size_t o_act, o_lay, o_hx0, o_hy0, o_hfx, o_hfy, o_px0, o_py0, o_pfx, o_pfy, o_wx0, o_wy0, o_wxw, o_wyw,
+      o_u, o_r, o_p, o_q, o_phi, o_part, o_flag;
+  const Item items[] = {
+      {&o_act, T.act.size()},
+      {&o_lay, T.lay.size() * sizeof(int2)},
+      {&o_hx0, T.hx0.size() * sizeof(int)},
+      {&o_hy0, T.hy0.size() * sizeof(int)},
+      {&o_hfx, T.hfx.size() * es},
+      {&o_hfy, T.hfy.size() * es},
+      {&o_px0, T.px0.size() * sizeof(int)},
+      {&o_py0, T.py0.size() * sizeof(int)},
+      {&o_pfx, T.pfx.size() * es},
+      {&o_pfy, T.pfy.size() * es},
+      {&o_wx0, T.wx0.size() * sizeof(int)},
+      {&o_wy0, T.wy0.size() * sizeof(int)},
+      {&o_wxw, T.wxw.size() * es},
+      {&o_wyw, T.wyw.size() * es},
+      {&o_u, static_cast<size_t>(nd) * nc * nc * es},
+      {&o_r, n_act * es},
+      {&o_p, n_act * es},
+      {&o_q, n_act * es},
+      {&o_phi, static_cast<size_t>(H.n) * es},
+      {&o_part, static_cast<size_t>(tomo::kRrSlots + 2) * F.part_stride * sizeof(double)},
+      {&o_flag, sizeof(double)},
+  };
+  size_t total = 0;
+  for (const auto &it : items) {
+    *it.off = total;
+    total = align256(total + it.bytes);
+  }
+  const size_t tables_end = o_u;
+  std::vector<unsigned char> img(tables_end, 0);
+  std::memcpy(img.data() + o_act, T.act.data(), T.act.size());
+  std::memcpy(img.data() + o_lay, T.lay.data(), T.lay.size() * sizeof(int2));
+  std::memcpy(img.data() + o_hx0, T.hx0.data(), T.hx0.size() * sizeof(int));
+  std::memcpy(img.data() + o_hy0, T.hy0.data(), T.hy0.size() * sizeof(int));
+  std::memcpy(img.data() + o_px0, T.px0.data(), T.px0.size() * sizeof(int));
+  std::memcpy(img.data() + o_py0, T.py0.data(), T.py0.size() * sizeof(int));
+  std::memcpy(img.data() + o_wx0, T.wx0.data(), T.wx0.size() * sizeof(int));
+  std::memcpy(img.data() + o_wy0, T.wy0.data(), T.wy0.size() * sizeof(int));
+  const std::pair<size_t, const std::vector<double> *> reals[] = {
+      {o_hfx, &T.hfx}, {o_hfy, &T.hfy}, {o_pfx, &T.pfx}, {o_pfy, &T.pfy}, {o_wxw, &T.wxw}, {o_wyw, &T.wyw}};
+  for (const auto &rv : reals) {
+    if (f->precision) put<double>(img, rv.first, *rv.second);
+    else put<float>(img, rv.first, *rv.second);
+  }
+  tomo::DeviceGuard dg(f->device);
+  cudaError_t e = cudaMalloc(&f->arena, total);
+  if (e != cudaSuccess) {
+    delete f;
+    return fit_fail(TOMO_ERR_NOMEM, std::string("device allocation of the fit: ") + cudaGetErrorString(e));
+  }
+  f->arena_bytes = total;
+  unsigned char *base = static_cast<unsigned char *>(f->arena);
+  e = cudaMemcpy(base, img.data(), tables_end, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(base + tables_end, 0, total - tables_end);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&f->cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    tomo_fit_destroy(f);
+    return fit_cuda(e, "uploading the fit tables");
+  }
+  F.act = base + o_act;
+  F.lay = reinterpret_cast<const int2 *>(base + o_lay);
+  F.hx0 = reinterpret_cast<const int *>(base + o_hx0);
+  F.hy0 = reinterpret_cast<const int *>(base + o_hy0);
+  F.hfx = base + o_hfx;
+  F.hfy = base + o_hfy;
+  F.px0 = reinterpret_cast<const int *>(base + o_px0);
+  F.py0 = reinterpret_cast<const int *>(base + o_py0);
+  F.pfx = base + o_pfx;
+  F.pfy = base + o_pfy;
+  F.wx0 = reinterpret_cast<const int *>(base + o_wx0);
+  F.wy0 = reinterpret_cast<const int *>(base + o_wy0);
+  F.wxw = base + o_wxw;
+  F.wyw = base + o_wyw;
+  F.u = base + o_u;
+  F.r = base + o_r;
+  F.p = base + o_p;
+  F.q = base + o_q;
+  f->phi = base + o_phi;
+  F.part = reinterpret_cast<double *>(base + o_part);
+  F.flag = reinterpret_cast<double *>(base + o_flag);
+  *out = f;
+  return TOMO_OK;
+}
+
+tomo_status tomo_fit_get_info(const tomo_fit *f, tomo_fit_info *out) {
+  if (!f || !out) return fit_fail(TOMO_ERR_ARG, "NULL argument");
+  out->n_act = f->F.n_act;
+  out->n_active = f->n_active;
+  out->n_points = f->n_points;
+  out->n_dir = f->F.n_dir;
+  out->n_dm = f->F.n_dm;
+  out->kernels_per_iteration = 3;
+  out->kernels_per_solve_base = 2;
+  out->device_bytes = static_cast<long long>(f->arena_bytes);
+  return TOMO_OK;
+}
+
+tomo_status tomo_fit_apply_normal(tomo_fit *f, const void *d_a, void *d_out, void *cuda_stream) {
+  if (!f || !d_a || !d_out) return fit_fail(TOMO_ERR_ARG, "NULL argument");
+  tomo::DeviceGuard dg(f->device);
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  if (f->precision == 0) {
+    FIT_CUDA(tomo::fit_mirror<float>(2, f->F, static_cast<const float *>(d_a), nullptr, 0, s), "fit mirror");
+    FIT_CUDA(tomo::fit_adjoint<float>(2, f->F, static_cast<float *>(d_out), 0, s), "fit gather");
+  } else {
+    FIT_CUDA(tomo::fit_mirror<double>(2, f->F, static_cast<const double *>(d_a), nullptr, 0, s), "fit mirror");
+    FIT_CUDA(tomo::fit_adjoint<double>(2, f->F, static_cast<double *>(d_out), 0, s), "fit gather");
+  }
+  tomo::count_launches(2);
+  return TOMO_OK;
+}
+
+tomo_status tomo_fit_rhs(tomo_fit *f, const void *d_layers, void *d_out, void *cuda_stream) {
+  if (!f || !d_layers || !d_out) return fit_fail(TOMO_ERR_ARG, "NULL argument");
+  tomo::DeviceGuard dg(f->device);
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  if (f->precision == 0) {
+    FIT_CUDA(tomo::fit_mirror<float>(1, f->F, nullptr, static_cast<const float *>(d_layers), 0, s), "fit project");
+    FIT_CUDA(tomo::fit_adjoint<float>(2, f->F, static_cast<float *>(d_out), 0, s), "fit gather");
+  } else {
+    FIT_CUDA(tomo::fit_mirror<double>(1, f->F, nullptr, static_cast<const double *>(d_layers), 0, s),
+             "fit project");
+    FIT_CUDA(tomo::fit_adjoint<double>(2, f->F, static_cast<double *>(d_out), 0, s), "fit gather");
+  }
+  tomo::count_launches(2);
+  return TOMO_OK;
+}
+
+tomo_status tomo_fit_residual_rms(tomo_fit *f, const void *d_layers, const void *d_a, double *d_rms,
+                                  void *cuda_stream) {
+  if (!f || !d_layers || !d_rms) return fit_fail(TOMO_ERR_ARG, "NULL argument");
+  tomo::DeviceGuard dg(f->device);
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  if (f->precision == 0) {
+    FIT_CUDA(tomo::fit_mirror<float>(1, f->F, static_cast<const float *>(d_a), static_cast<const float *>(d_layers),
+                                     0, s), "fit residual");
+    FIT_CUDA(tomo::fit_rms<float>(f->F, d_rms, s), "fit residual rms");
+  } else {
+    FIT_CUDA(tomo::fit_mirror<double>(1, f->F, static_cast<const double *>(d_a),
+                                      static_cast<const double *>(d_layers), 0, s), "fit residual");
+    FIT_CUDA(tomo::fit_rms<double>(f->F, d_rms, s), "fit residual rms");
+  }
+  tomo::count_launches(2);
+  return TOMO_OK;
+}
+
+tomo_status tomo_fit_solve(tomo_fit *f, const void *d_layers, void *d_a, int iters, int warm, void *cuda_stream) {
+  if (!f || !d_layers || !d_a) return fit_fail(TOMO_ERR_ARG, "NULL argument");
+  if (iters < 0 || iters > 100000) return fit_fail(TOMO_ERR_ARG, "iters out of range");
+  tomo::DeviceGuard dg(f->device);
+  const tomo_plan *p = f->plan;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  if (p->use_graphs) return run_graph(f, 0, d_layers, nullptr, d_a, 0, iters, warm ? 1 : 0, s);
+  int nk = 0;
+  return enqueue_fit_any(f, d_layers, d_a, iters, warm ? 1 : 0, s, &nk);
+}
+
+tomo_status tomo_reconstruct(tomo_fit *f, const void *d_slopes, void *d_coeffs, void *d_a, int iters,
+                             int fit_iters, int warm, void *cuda_stream) {
+  if (!f || !d_slopes || !d_coeffs || !d_a) return fit_fail(TOMO_ERR_ARG, "NULL argument");
+  if (iters < 0 || iters > 100000 || fit_iters < 0 || fit_iters > 100000)
+    return fit_fail(TOMO_ERR_ARG, "iters out of range");
+  tomo::DeviceGuard dg(f->device);
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  if (f->plan->use_graphs) return run_graph(f, 1, d_slopes, d_coeffs, d_a, iters, fit_iters, warm ? 1 : 0, s);
+  int nk = 0;
+  return enqueue_kind(f, 1, d_slopes, d_coeffs, d_a, iters, fit_iters, warm ? 1 : 0, s, &nk);
+}
+
+void tomo_fit_destroy(tomo_fit *f) {
+  if (!f) return;
+  tomo::DeviceGuard dg(f->device);
+  for (auto &g : f->graphs) cudaGraphExecDestroy(g.exec);
+  if (f->cap) cudaStreamDestroy(f->cap);
+  if (f->arena) cudaFree(f->arena);
+  delete f;
+}
+
+}  // extern "C"

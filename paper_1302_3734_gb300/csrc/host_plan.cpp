@@ -176,6 +176,8 @@ tomo_status build_host_plan(const tomo_geometry *geo, HostPlan *P, std::string *
       d.dalpha[k] = geo->alpha * d.dprior[k];
     }
     P->layers.push_back(d);
+    P->layer_alt.push_back(L.altitude);
+    P->layer_dx.push_back(L.dx);
     P->n += L.N * L.N;
     Nmin = std::min(Nmin, L.N);
     Nmax = std::max(Nmax, L.N);

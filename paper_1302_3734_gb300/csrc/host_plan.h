@@ -25,6 +25,7 @@ struct HostPlan {
       rec_stride = 0;
   std::vector<double> h, g;
   std::vector<LayerDev> layers;
+  std::vector<double> layer_alt, layer_dx;   // altitude and grid spacing (m) of each layer
   std::vector<WfsDev> wfs;
   std::vector<int> sub_idx;
   std::vector<unsigned char> active;

@@ -30,6 +30,7 @@
 #include <stdint.h>
 
 #include "common.h"
+#include "device_util.cuh"
 #include "launch.h"
 
 namespace cg = cooperative_groups;
@@ -37,9 +38,6 @@ namespace cg = cooperative_groups;
 namespace tomo {
 
 // ------------------------------------------------------------------ helpers
-
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 // The two halves of a cluster barrier (cluster.sync() is both): every thread
 // of every CTA in the cluster alternates arrive and wait.  arrive releases the
@@ -52,149 +50,6 @@ __device__ __forceinline__ void cluster_wait() {
   asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Inner-product accumulator of one thread.  FP64 plans: a double.  FP32
-// plans: an unevaluated double-float sum hi + lo (about 48 significant bits)
-// on the FP32 pipes: the product of two floats enters exactly (the FMA gives
-// the rounding error of a*b) and additions use Knuth's two-sum, so the error
-// stays close to an FP64 accumulation while the FP64 pipe, a small fraction
-// of the FP32 rate on this GPU, is left to the cross-block sums.  The _rn
-// intrinsics keep the compiler from contracting the error-free steps.
-template <typename T>
-struct Acc;
-
-template <>
-struct Acc<double> {
-  double s = 0.0;
-  __device__ __forceinline__ void add(double x) { s += x; }
-  __device__ __forceinline__ void add_prod(double a, double b) { s += a * b; }
-  __device__ __forceinline__ double value() const { return s; }
-};
-
-template <>
-struct Acc<float> {
-  float hi = 0.f, lo = 0.f;
-  __device__ __forceinline__ void add(float x) {
-    const float t = __fadd_rn(hi, x);
-    const float bp = __fsub_rn(t, hi);
-    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(x, bp));
-    hi = t;
-    lo = __fadd_rn(lo, e);
-  }
-  __device__ __forceinline__ void add_prod(float a, float b) {
-    const float p = __fmul_rn(a, b);
-    const float e = __fmaf_rn(a, b, -p);
-    add(p);
-    lo = __fadd_rn(lo, e);
-  }
-  // this += o, renormalised so that |lo| <= ulp(hi) / 2
-  __device__ __forceinline__ void merge(float ohi, float olo) {
-    add(ohi);
-    lo = __fadd_rn(lo, olo);
-    const float t = __fadd_rn(hi, lo);
-    lo = __fsub_rn(lo, __fsub_rn(t, hi));
-    hi = t;
-  }
-  __device__ __forceinline__ double value() const { return double(hi) + double(lo); }
-};
-
-// Sum of (a, b) over the block; the result is returned to every thread.
-// Fixed order: lane trees in each warp, then the warps' sums in warp 0.
-__device__ double2 block_sum2(Acc<double> aa, Acc<double> bb) {
-  __shared__ double s_red[2][32];
-  __shared__ double2 s_out;
-  const double a = warp_sum(aa.s), b = warp_sum(bb.s);
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) {
-    s_red[0][w] = a;
-    s_red[1][w] = b;
-  }
-  __syncthreads();
-  if (w == 0) {
-    const int nw = blockDim.x >> 5;
-    double x = lane < nw ? s_red[0][lane] : 0.0;
-    double y = lane < nw ? s_red[1][lane] : 0.0;
-    x = warp_sum(x);
-    y = warp_sum(y);
-    if (lane == 0) s_out = make_double2(x, y);
-  }
-  __syncthreads();
-  return s_out;
-}
-
-__device__ __forceinline__ void warp_merge_down(Acc<float> &a) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const float h = __shfl_down_sync(0xffffffffu, a.hi, o);
-    const float l = __shfl_down_sync(0xffffffffu, a.lo, o);
-    a.merge(h, l);
-  }
-}
-
-__device__ double2 block_sum2(Acc<float> a, Acc<float> b) {
-  __shared__ float s_red[4][32];
-  __shared__ double2 s_out;
-  warp_merge_down(a);   // lane 0 holds the warp's sum
-  warp_merge_down(b);
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) {
-    s_red[0][w] = a.hi;
-    s_red[1][w] = a.lo;
-    s_red[2][w] = b.hi;
-    s_red[3][w] = b.lo;
-  }
-  __syncthreads();
-  if (w == 0) {
-    const int nw = blockDim.x >> 5;
-    Acc<float> x, y;
-    if (lane < nw) {
-      x.hi = s_red[0][lane];
-      x.lo = s_red[1][lane];
-      y.hi = s_red[2][lane];
-      y.lo = s_red[3][lane];
-    }
-    warp_merge_down(x);
-    warp_merge_down(y);
-    if (lane == 0) s_out = make_double2(x.value(), y.value());
-  }
-  __syncthreads();
-  return s_out;
-}
-
-// The block's double-float sums of (a, b) as (a.hi, a.lo, b.hi, b.lo), valid
-// in thread 0.
-__device__ float4 block_sum2_df(Acc<float> a, Acc<float> b) {
-  __shared__ float s_red[4][32];
-  warp_merge_down(a);
-  warp_merge_down(b);
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) {
-    s_red[0][w] = a.hi;
-    s_red[1][w] = a.lo;
-    s_red[2][w] = b.hi;
-    s_red[3][w] = b.lo;
-  }
-  __syncthreads();
-  Acc<float> x, y;
-  if (w == 0) {
-    const int nw = blockDim.x >> 5;
-    if (lane < nw) {
-      x.hi = s_red[0][lane];
-      x.lo = s_red[1][lane];
-      y.hi = s_red[2][lane];
-      y.lo = s_red[3][lane];
-    }
-    warp_merge_down(x);
-    warp_merge_down(y);
-  }
-  return make_float4(x.hi, x.lo, y.hi, y.lo);
-}
-
 // A forward tile's two partial sums in its 16-byte partial slot: doubles for
 // FP64 plans, double-float pairs (hi, lo, hi, lo) for FP32 plans.
 __device__ __forceinline__ void store_tile_partial(double *slot, Acc<double> a, Acc<double> b) {
@@ -204,22 +59,6 @@ __device__ __forceinline__ void store_tile_partial(double *slot, Acc<double> a, 
 __device__ __forceinline__ void store_tile_partial(double *slot, Acc<float> a, Acc<float> b) {
   const float4 s = block_sum2_df(a, b);
   if (threadIdx.x == 0) *reinterpret_cast<float4 *>(slot) = s;
-}
-
-// Fixed-order sum of `count` FP64 partial pairs (stride 2): warp 0 sums the
-// first of each pair and warp 1 the second (one of them does both in a
-// one-warp block); the result is returned to every thread.
-__device__ double2 sum_partials(const double *part, int count) {
-  __shared__ double s_sp[2];
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int k = w; k < 2; k += nw) {
-    double a = 0.0;
-    for (int q = lane; q < count; q += 32) a += part[2 * q + k];
-    a = warp_sum(a);
-    if (lane == 0) s_sp[k] = a;
-  }
-  __syncthreads();
-  return make_double2(s_sp[0], s_sp[1]);
 }
 
 // Copy one instance descriptor into shared memory.
@@ -279,13 +118,15 @@ __device__ __forceinline__ T trace_corner(const InstDev &I, int m, int nc, const
 // (the analysis subtracts the means on the pupil edge, Sec. 4.3 eq. widehatc).
 // A tip/tilt-only sensor writes its weighted mean slopes (e_x, e_y).
 // io.in0: layer grids (NULL = the plan's phi); io.in1: slopes (MODE 1, 2).
+// EL: some sensor of the launch has elongated spots (Sec. 4.3); without it the
+// elongation code is compiled out.
 constexpr int kHalo = kFwdTile + 2;
 
 __host__ __device__ constexpr size_t fwd_table_bytes(int L, size_t esz) {
   return ((sizeof(int) * (2 * L + 2 * L * kHalo) + 15) & ~size_t(15)) + 2 * L * kHalo * esz;
 }
 
-template <typename T, int MODE>
+template <typename T, int MODE, bool EL>
 __global__ void __launch_bounds__(kThreads) k_forward(const InstDev *__restrict__ insts,
                                                      const FwdItem *__restrict__ items, IoArgs io) {
   extern __shared__ __align__(16) unsigned char fsm[];
@@ -410,10 +251,11 @@ __global__ void __launch_bounds__(kThreads) k_forward(const InstDev *__restrict_
   const T isg = T(W.inv_sigma2);
   // spot elongation: the block sigma^2 (I + tau g g^T) is inverted in closed
   // form, sigma^-2 (I - c g g^T) with c = tau / (1 + tau |g|^2)
-  const bool elong = W.elong != 0;
-  const T el_tau = T(W.el_tau), el_eps = T(W.el_eps), el_d = T(W.d_sub);
-  const T el_cx = T(0.5 - 0.5 * n) * el_d - T(W.el_lx), el_cy = T(0.5 - 0.5 * n) * el_d - T(W.el_ly);
-  const bool four = tile_partials(W) == 4;
+  const bool elong = EL && W.elong != 0;
+  const T el_tau = EL ? T(W.el_tau) : T(0), el_eps = EL ? T(W.el_eps) : T(0), el_d = EL ? T(W.d_sub) : T(0);
+  const T el_cx = EL ? T(0.5 - 0.5 * n) * el_d - T(W.el_lx) : T(0);
+  const T el_cy = EL ? T(0.5 - 0.5 * n) * el_d - T(W.el_ly) : T(0);
+  const bool four = EL && tile_partials(W) == 4;
   for (int idx = tid; idx < (kFwdTile + 1) * (kFwdTile + 1); idx += blockDim.x) {
     const int u = idx % (kFwdTile + 1), w = idx / (kFwdTile + 1);
     const int a = a0 - 1 + u, b = b0 - 1 + w;
@@ -1785,34 +1627,6 @@ __global__ void k_jacobi(const InstDev *__restrict__ insts, const double *__rest
 
 namespace {
 
-// Every hot-path launch allows programmatic dependent launch: the kernel's
-// prologue (descriptor and table loads) overlaps the previous kernel, and
-// griddepcontrol.wait orders its reads of the previous kernel's results.
-template <typename K, typename... Args>
-cudaError_t launch_ex(K kernel, dim3 grid, int threads, int cluster, size_t smem, cudaStream_t s,
-                      Args... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = dim3(threads);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[2];
-  int na = 0;
-  attr[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[na].val.programmaticStreamSerializationAllowed = 1;
-  ++na;
-  if (cluster > 0) {
-    attr[na].id = cudaLaunchAttributeClusterDimension;
-    attr[na].val.clusterDim.x = cluster;
-    attr[na].val.clusterDim.y = 1;
-    attr[na].val.clusterDim.z = 1;
-    ++na;
-  }
-  cfg.attrs = attr;
-  cfg.numAttrs = na;
-  return cudaLaunchKernelEx(&cfg, kernel, args...);
-}
-
 template <typename K>
 cudaError_t allow_cluster(K kernel) {
   cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1844,12 +1658,14 @@ cudaError_t allow_type() {
   if (e == cudaSuccess) e = allow_lf<T, 4>();
   if (e == cudaSuccess) e = allow_lf<T, 6>();
   if (e == cudaSuccess) e = allow_lf<T, 8>();
-  for (int mode = 0; mode < 3 && e == cudaSuccess; ++mode) {
-    const void *k = mode == 0 ? reinterpret_cast<const void *>(k_forward<T, 0>)
-                  : mode == 1 ? reinterpret_cast<const void *>(k_forward<T, 1>)
-                              : reinterpret_cast<const void *>(k_forward<T, 2>);
-    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxForwardSmem);
-  }
+  const void *fwd[6] = {reinterpret_cast<const void *>(k_forward<T, 0, false>),
+                        reinterpret_cast<const void *>(k_forward<T, 1, false>),
+                        reinterpret_cast<const void *>(k_forward<T, 2, false>),
+                        reinterpret_cast<const void *>(k_forward<T, 0, true>),
+                        reinterpret_cast<const void *>(k_forward<T, 1, true>),
+                        reinterpret_cast<const void *>(k_forward<T, 2, true>)};
+  for (int i = 0; i < 6 && e == cudaSuccess; ++i)
+    e = cudaFuncSetAttribute(fwd[i], cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxForwardSmem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_gather<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxTransformSmem);
   return e;
@@ -1947,18 +1763,23 @@ cudaError_t launch_analysis(int precision, int src, int epi, int lf, int flags, 
                         : anal_t<double>(src, epi, lf, flags, insts, items, n_clusters, C, smem, io, s);
 }
 
-cudaError_t launch_forward(int precision, int mode, int max_layers, const InstDev *insts,
+template <typename T, bool EL>
+cudaError_t fwd_t(int mode, dim3 g, size_t sm, cudaStream_t s, const InstDev *insts, const FwdItem *items,
+                  const IoArgs &io) {
+  if (mode == 0) return launch_ex(k_forward<T, 0, EL>, g, kThreads, 0, sm, s, insts, items, io);
+  if (mode == 1) return launch_ex(k_forward<T, 1, EL>, g, kThreads, 0, sm, s, insts, items, io);
+  return launch_ex(k_forward<T, 2, EL>, g, kThreads, 0, sm, s, insts, items, io);
+}
+
+cudaError_t launch_forward(int precision, int mode, int max_layers, int elong, const InstDev *insts,
                            const FwdItem *items, int n_items, const IoArgs &io, cudaStream_t s) {
   const dim3 g(n_items);
   const size_t sm = forward_smem(max_layers, precision);
-  if (precision == 0) {
-    if (mode == 0) return launch_ex(k_forward<float, 0>, g, kThreads, 0, sm, s, insts, items, io);
-    if (mode == 1) return launch_ex(k_forward<float, 1>, g, kThreads, 0, sm, s, insts, items, io);
-    return launch_ex(k_forward<float, 2>, g, kThreads, 0, sm, s, insts, items, io);
-  }
-  if (mode == 0) return launch_ex(k_forward<double, 0>, g, kThreads, 0, sm, s, insts, items, io);
-  if (mode == 1) return launch_ex(k_forward<double, 1>, g, kThreads, 0, sm, s, insts, items, io);
-  return launch_ex(k_forward<double, 2>, g, kThreads, 0, sm, s, insts, items, io);
+  if (precision == 0)
+    return elong ? fwd_t<float, true>(mode, g, sm, s, insts, items, io)
+                 : fwd_t<float, false>(mode, g, sm, s, insts, items, io);
+  return elong ? fwd_t<double, true>(mode, g, sm, s, insts, items, io)
+               : fwd_t<double, false>(mode, g, sm, s, insts, items, io);
 }
 
 cudaError_t launch_update(int precision, int flags, const InstDev *insts, const UpdItem *items,

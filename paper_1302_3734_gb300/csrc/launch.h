@@ -33,9 +33,9 @@ cudaError_t launch_analysis(int precision, int src, int epi, int lf, int flags, 
 inline int analysis_launches(int src, int split) { return (src == 1 && split) ? 2 : 1; }
 
 // Ray-trace, Fried slopes, noise weighting, Gamma^T.  mode 0 operator, 1 residual,
-// 2 data only.
-cudaError_t launch_forward(int precision, int mode, int max_layers, const InstDev *insts, const FwdItem *items,
-                           int n_items, const IoArgs &io, cudaStream_t s);
+// 2 data only.  elong: some sensor of the launch has elongated spots.
+cudaError_t launch_forward(int precision, int mode, int max_layers, int elong, const InstDev *insts,
+                           const FwdItem *items, int n_items, const IoArgs &io, cudaStream_t s);
 
 // x, r update and the FP64 r.z partials; flags carries the iteration index.
 cudaError_t launch_update(int precision, int flags, const InstDev *insts, const UpdItem *items,

@@ -28,6 +28,7 @@ struct LaunchSet {
   int precision = 0;
   int split = 0;                 // gather in its own kernel (tables not staged in shared memory)
   size_t smem_g = 0;             // its dynamic shared memory
+  int elong = 0;                 // some sensor has elongated spots (k_forward variant)
 };
 
 struct Timer {
@@ -57,6 +58,23 @@ struct GraphEntry {
 
 // Record the thread-local message returned by tomo_last_error().
 tomo_status set_error(tomo_status st, const std::string &msg);
+
+// Add k kernel launches to the count tomo_launch_count() reports.
+void count_launches(long long k);
+
+// Makes `dev` the current device for the guard's lifetime.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
 
 }  // namespace tomo
 
@@ -117,5 +135,10 @@ void free_batch(Batch *b);
 // slot (nonzero = solve), or NULL for all.
 tomo_status batch_solve(Batch *b, const void *const *slopes, void *const *x, const int *const *active_g,
                         int iters, int warm, cudaStream_t s);
+
+// Enqueue one solve of plan p on stream s, kernel by kernel (for capture into
+// a caller's graph); *n_kernels receives the number of launches.
+tomo_status enqueue_plan_solve(tomo_plan *p, const void *slopes, void *x, int iters, int warm, cudaStream_t s,
+                               int *n_kernels);
 
 }  // namespace tomo

@@ -129,3 +129,36 @@ def test_eelt_fitting_geometry_has_the_papers_degrees_of_freedom():
     assert [m["altitude"] for m in f.dms] == [0.0, 4000.0, 12700.0]
     assert len(f.theta) == 25 and f.iters == 4
     assert f.active_actuators() == 9296
+
+
+def test_residual_rms_ignores_piston_and_vanishes_for_a_fitted_atmosphere():
+    g = tiny(n_sub=6, N=32, dm_pitches=(0.5, 0.5), dm_alts=(0.0, 3000.0))
+    f = Fitting(g)
+    rng = np.random.default_rng(6)
+    phis = [rng.standard_normal((32, 32)) for _ in g["layers"]]
+    a = rng.standard_normal(f.n)
+    r = f.residual_rms(phis, a)
+    assert r.shape == (3,) and np.all(r > 0)
+    shifted = [phis[0] + 2.5, phis[1] - 0.7]           # piston on every layer
+    assert np.allclose(f.residual_rms(shifted, a), r, rtol=1e-12, atol=0)
+    for j in range(3):                                 # the RMS is numpy's standard deviation
+        e = f.residual(phis, a, j)[f.act]
+        assert math.isclose(r[j], float(np.std(e)), rel_tol=1e-12)
+    # layers holding mirror shapes node for node: zero residual in every direction
+    a_star = rng.standard_normal(f.n)
+    grids = []
+    for k, (m, lay) in enumerate(zip(f.dms, g["layers"])):
+        o = lay["N"] // 2 - (m["n"] - 1) // 2
+        grid = np.zeros((lay["N"], lay["N"]))
+        grid[o:o + m["n"], o:o + m["n"]] = a_star[f.offsets[k]:f.offsets[k + 1]].reshape(m["n"], m["n"])
+        grids.append(grid)
+    assert np.all(f.residual_rms(grids, a_star) < 1e-12)
+
+
+def test_marechal_strehl_closed_forms():
+    assert Fitting.strehl(0.0) == 1.0
+    # 2200/500 rad at 500 nm is 1 rad at 2200 nm: exp(-1)
+    assert math.isclose(float(Fitting.strehl(2200.0 / 500.0)), math.exp(-1.0), rel_tol=1e-15)
+    assert math.isclose(float(Fitting.strehl(1.0, wavelength=500e-9)), math.exp(-1.0), rel_tol=1e-15)
+    s = Fitting.strehl(np.linspace(0.0, 5.0, 11))
+    assert np.all(np.diff(s) < 0) and s[0] == 1.0
