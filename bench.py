@@ -12,6 +12,12 @@ A step is one frame (right-hand side, initial residual, 10 PCG iterations).
 ``value`` is frames solved per second with inputs resident in HBM; L2 is
 flushed (a 256 MiB write) before every timed step, outside the timed window.
 
+Further legs of the same line: ``batched`` (16 E-ELT systems, and 64 systems of
+uneven size, per launch), ``large`` (the 100 m system), ``closed_loop`` (the
+E-ELT system with its three mirrors: fitting and pseudo-open-loop control per
+frame, with the Strehl ratio of the correction) and ``served`` (16 telescopes
+streaming frames through the server).
+
 ``--impl reference`` times the FP64 CPU oracle on the same frames instead.
 Under torchrun every rank solves its own independent telescope stream (weak
 scaling, no data-path collective).
@@ -83,6 +89,8 @@ def parse():
     ap.add_argument("--batch", type=int, default=16, help="E-ELT instances per batched solve")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the 100 m configuration")
+    ap.add_argument("--no-loop", action="store_true", help="skip the E-ELT closed loop with fitting")
+    ap.add_argument("--loop-frames", type=int, default=120)
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="length of the served 16-telescope stream (0: skip it)")
     return ap.parse_args()
@@ -396,6 +404,86 @@ def bench_large(pkg, torch, dev, flush, peak, steps=5, warmup=2):
     return out
 
 
+def bench_closed_loop(pkg, torch, dev, flush, frames, gain=0.4, fit_iters=4):
+    """The reconstruction and pseudo-open-loop control of Secs. 4.1-4.2 on the E-ELT system with
+    its three mirrors (0, 4 and 12.7 km, 9296 actuators reached) and the 5 x 5 directions of a 2'
+    field: each frame the sensors measure the frozen-flow atmosphere minus the mirror shapes
+    applied two frames earlier, and one tomo_polc_step (mirror slopes, 10 warm PCG iterations,
+    W^-1, 4 warm fitting CG iterations, control update; one CUDA graph) computes the next
+    commands.  Timed: the control step (CUDA events, L2 flushed before each).  Quality: the
+    Marechal Strehl at 2200 nm of the residual wavefront in the 25 directions, from
+    tomo_fit_residual_rms, averaged over the second half of the frames (long exposure), with
+    and without the correction."""
+    from synth import configs, FrozenFlow, gaussian_noise
+    g = configs.with_fitting(configs.config1())
+    plan = pkg.Plan(g)
+    fit = pkg.Fit(plan, g["fitting"])
+    n, ns, na = plan.n, plan.n_slopes, fit.n
+    nd = int(fit.info.n_dir)
+    sig = np.concatenate([np.full(2 if w["tt_only"] else 2 * int(w["valid"].sum()), w["sigma"])
+                          for w in g["wfs"]])
+    flow = FrozenFlow(g, 1, instance=7)
+    truth = torch.empty((frames, n), dtype=torch.float32, device=dev)
+    meas = torch.empty((frames, ns), dtype=torch.float32, device=dev)
+    for t in range(frames):
+        truth[t].copy_(torch.from_numpy(np.concatenate([p.ravel() for p in flow.layers(0.002 * t)])
+                                        .astype(np.float32)))
+        plan.layers_to_slopes(truth[t], meas[t])
+        meas[t] += torch.from_numpy((gaussian_noise(ns, 1.0, 5_000_000 + t) * sig).astype(np.float32)).to(dev)
+    buf = [torch.zeros(na, dtype=torch.float32, device=dev) for _ in range(2)]
+    x = torch.zeros(n, dtype=torch.float32, device=dev)
+    rec = torch.zeros(na, dtype=torch.float32, device=dev)
+    s = torch.empty(ns, dtype=torch.float32, device=dev)
+    rms = torch.empty((frames, nd), dtype=torch.float64, device=dev)
+    rms_open = torch.empty((frames, nd), dtype=torch.float64, device=dev)
+    times = []
+    for t in range(frames):
+        a_tm2, a_tm1 = buf[t % 2], buf[(t + 1) % 2]
+        fit.mirror_slopes(a_tm2, s, slopes_in=meas[t], scale=-1.0)
+        fit.residual_rms(truth[t], a_tm2, rms[t])
+        fit.residual_rms(truth[t], None, rms_open[t])
+        flush.fill_(float(t))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fit.polc_step(s, x, rec, a_tm2, a_tm1, a_tm2, gain, 10, fit_iters, warm=t > 0)
+        e1.record()
+        times.append((e0, e1))
+    torch.cuda.synchronize()
+    ms = np.array([a.elapsed_time(b) for a, b in times])
+    le = slice(frames // 2, frames)
+    strehl = np.exp(-(rms.cpu().numpy()[le] * (500.0 / 2200.0)) ** 2).mean(axis=0)
+    strehl_open = np.exp(-(rms_open.cpu().numpy()[le] * (500.0 / 2200.0)) ** 2).mean(axis=0)
+    # the fitting step alone, on the last reconstructed layers
+    lay = torch.empty(n, dtype=torch.float32, device=dev)
+    plan.coeffs_to_layers(x, lay)
+    a = torch.zeros(na, dtype=torch.float32, device=dev)
+    ft = []
+    for k in range(60):
+        flush.fill_(float(k))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fit.solve(lay, a, fit_iters, warm=True)
+        e1.record()
+        ft.append((e0, e1))
+    torch.cuda.synchronize()
+    fit_ms = np.array([a0.elapsed_time(b0) for a0, b0 in ft[10:]])
+    out = {"frames": frames, "gain": gain, "fit_iters": fit_iters, "tomo_iters": 10,
+           "actuators": na, "actuators_reached": int(fit.info.n_active), "directions": nd,
+           "control_steps_per_s": 1000.0 / float(ms[5:].mean()),
+           "control_step_ms": {"p50": float(np.percentile(ms[5:], 50)), "p99": float(np.percentile(ms[5:], 99))},
+           "fitting_ms": {"mean": float(fit_ms.mean()), "p99": float(np.percentile(fit_ms, 99))},
+           "strehl_2200nm_long_exposure": {"field_average": float(strehl.mean()),
+                                           "on_axis": float(strehl[nd // 2]),
+                                           "uncorrected_field_average": float(strehl_open.mean())},
+           "note": "synthetic frozen-flow atmosphere (von Karman, r0 0.15 m, L0 25 m), not OCTOPUS: "
+                   "the Strehl values are not comparable with the paper's figures"}
+    fit.close()
+    plan.close()
+    return out
+
+
 def served_geometries():
     """16 telescopes cycling the three geometry families: the 8 m system (FP32 operator, Jacobi
     PCG), the E-ELT system, and instances of the uneven 64-instance set."""
@@ -652,6 +740,8 @@ def main():
         line["batched"] = bench_batched(pkg, torch, geom, slopes, flush, iters, args, peak, dev)
     if not args.no_large and rank == 0:
         line["large"] = bench_large(pkg, torch, dev, flush, peak)
+    if not args.no_loop and rank == 0:
+        line["closed_loop"] = bench_closed_loop(pkg, torch, dev, flush, args.loop_frames)
     if args.serve_seconds > 0 and rank == 0:
         line["served"] = bench_served(pkg, torch, args, dev)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

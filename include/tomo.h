@@ -311,6 +311,32 @@ tomo_status tomo_fit_solve(tomo_fit *f, const void *d_layers, void *d_a, int ite
 tomo_status tomo_reconstruct(tomo_fit *f, const void *d_slopes, void *d_coeffs, void *d_a, int iters,
                              int fit_iters, int warm, void *cuda_stream);
 
+/* ------------------------------------------------------------------ closed loop
+ * Pseudo-open-loop control (Sec. 4.2, Algorithm 4.1) with a delay of two
+ * frames: the data s measured while the commands a_{t-2} were applied give
+ *   step 1: s_ol = s + A_hat a_{t-2},
+ *   step 2: Delta a = R s_ol - a_{t-2},
+ *   step 3: a_t = a_{t-1} + gain Delta a,
+ * with R the reconstruction of tomo_reconstruct.  A_hat maps commands to the
+ * plan's slope layout: each mirror acts on the guide-star light like a layer
+ * at its altitude (sensor m sees sum_k a_k((1 - h_k/H_m) r + theta_m h_k) on
+ * its corners; cone factor 1 for a natural star), measured like layers are
+ * (Fried slopes; the two means for a tip/tilt-only sensor). */
+
+/* d_out = d_in + scale * A_hat d_a (d_in NULL: 0; d_in may equal d_out). */
+tomo_status tomo_mirror_slopes(tomo_fit *f, const void *d_a, const void *d_in, void *d_out, double scale,
+                               void *cuda_stream);
+
+/* One control step from the residual slopes d_slopes: steps 1 to 3 above.
+ * d_coeffs (tomography coefficients) and d_a_rec (R s_ol, the reconstructed
+ * commands) hold the previous frame's values when warm != 0 and receive this
+ * frame's; d_a_t receives a_t and may be the storage of d_a_tm2 (so two
+ * command buffers can alternate); no other two of the command buffers may
+ * share storage.  Replayed from one CUDA graph per argument set. */
+tomo_status tomo_polc_step(tomo_fit *f, const void *d_slopes, void *d_coeffs, void *d_a_rec, const void *d_a_tm2,
+                           const void *d_a_tm1, void *d_a_t, double gain, int iters, int fit_iters, int warm,
+                           void *cuda_stream);
+
 void tomo_fit_destroy(tomo_fit *f);
 
 /* ------------------------------------------------------------------ serving

@@ -18,8 +18,10 @@ in numpy float64, in the paper's order and notation:
                      D, the normal operator of eq. eqn_lse, its right-hand side,
                      the modified Jacobi diagonal, and Hestenes-Stiefel (P)CG;
 * ``fitting``     - the fitting step: piecewise-bilinear mirrors H, the NGS
-                     projections P over the evaluation directions, and CG on
-                     H^T H a = H^T P phi.
+                     projections P over the evaluation directions, CG on
+                     H^T H a = H^T P phi, and the Marechal Strehl of a correction;
+* ``control``     - pseudo-open-loop control: the mirrors measured by the
+                     sensors (A_hat) and one step of the two-frame-delay loop.
 
 Each function is pinned by tests/test_oracle_*.py against closed forms,
 invariants, textbook special cases and brute force on tiny inputs; nothing in
@@ -27,6 +29,7 @@ those pins comes from the CUDA path.
 """
 from .tomography import Tomography
 from .fitting import Fitting
-from . import wavelets, atmosphere, tomography, fitting
+from .control import Control
+from . import wavelets, atmosphere, tomography, fitting, control
 
-__all__ = ["Tomography", "Fitting", "wavelets", "atmosphere", "tomography", "fitting"]
+__all__ = ["Tomography", "Fitting", "Control", "wavelets", "atmosphere", "tomography", "fitting", "control"]

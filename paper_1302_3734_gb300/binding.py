@@ -143,6 +143,8 @@ SIGNATURES = [
     ("tomo_fit_residual_rms", _I, [_VP, _VP, _VP, _VP, _VP]),
     ("tomo_fit_solve", _I, [_VP, _VP, _VP, _I, _I, _VP]),
     ("tomo_reconstruct", _I, [_VP, _VP, _VP, _VP, _I, _I, _I, _VP]),
+    ("tomo_mirror_slopes", _I, [_VP, _VP, _VP, _VP, ctypes.c_double, _VP]),
+    ("tomo_polc_step", _I, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_double, _I, _I, _I, _VP]),
     ("tomo_fit_destroy", None, [_VP]),
 ]
 
@@ -404,6 +406,24 @@ class Fit:
         _check(load_library().tomo_reconstruct(
             self._h, p._tensor(slopes, p.n_slopes, "slopes"), p._tensor(coeffs, p.n, "coeffs"),
             p._tensor(a, self.n, "a"), int(iters), int(fit_iters), int(bool(warm)), _stream(stream)))
+
+    def mirror_slopes(self, a, out, slopes_in=None, scale=1.0, stream=None):
+        """out = slopes_in + scale * A_hat a (slopes_in None: 0)."""
+        p = self.plan
+        _check(load_library().tomo_mirror_slopes(
+            self._h, p._tensor(a, self.n, "a"),
+            None if slopes_in is None else p._tensor(slopes_in, p.n_slopes, "slopes_in"),
+            p._tensor(out, p.n_slopes, "out"), float(scale), _stream(stream)))
+
+    def polc_step(self, slopes, coeffs, a_rec, a_tm2, a_tm1, a_t, gain, iters, fit_iters, warm=True,
+                  stream=None):
+        """One step of pseudo-open-loop control (Algorithm 4.1) from the residual slopes."""
+        p = self.plan
+        _check(load_library().tomo_polc_step(
+            self._h, p._tensor(slopes, p.n_slopes, "slopes"), p._tensor(coeffs, p.n, "coeffs"),
+            p._tensor(a_rec, self.n, "a_rec"), p._tensor(a_tm2, self.n, "a_tm2"),
+            p._tensor(a_tm1, self.n, "a_tm1"), p._tensor(a_t, self.n, "a_t"), float(gain), int(iters),
+            int(fit_iters), int(bool(warm)), _stream(stream)))
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

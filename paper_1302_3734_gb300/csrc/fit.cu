@@ -1,6 +1,8 @@
 // The fitting step (Sec. 4.1, eqs. fit_step_ideal / fit_step_min): mirror
 // commands a from the reconstructed layers phi by CG on H^T H a = H^T P phi,
-// and tomo_reconstruct, slopes to commands in one graph.
+// tomo_reconstruct, slopes to commands in one graph, and the closed loop of
+// Sec. 4.2 (Algorithm 4.1): the mirrors as the sensors see them (A_hat) and one
+// pseudo-open-loop control step.
 //
 // H_j a (x) = sum_k a_k(x + h_k theta_j), each mirror a piecewise-bilinear
 // function of its actuator grid; P_j phi (x) = sum_l phi_l(x + h_l theta_j)
@@ -60,6 +62,14 @@ struct FitDev {
   void *r, *p, *q;            // [n_act]
   double *part;               // (kRrSlots + 2) * part_stride
   double *flag;               // nonzero after a breakdown
+  // the mirrors seen by the plan's sensors (A_hat)
+  int n_wfs, max_S;
+  const int4 *sens;           // per sensor: slope offset, valid subapertures S, corners per side, tip/tilt only
+  const int2 *sens_off;       // per sensor: first (sensor, mirror) tap entry, first subaperture
+  const int *sx0, *sy0;       // per (sensor, mirror): left / lower actuator of each corner column / row
+  const void *sfx, *sfy;      //   and its fraction (T)
+  const int2 *sub_ab;         // valid subapertures (a, b) of every sensor, row-major
+  void *s_ol;                 // pseudo-open-loop slopes (the plan's slope layout)
 };
 
 // Fixed-order sum of n FP64 partials, returned to every thread of the block.
@@ -87,6 +97,11 @@ __device__ __forceinline__ double fit_beta(const FitDev &F, int it) {
   const double num = fit_rr(F, it), den = fit_rr(F, it - 1);
   return den != 0.0 ? num / den : 0.0;
 }
+
+template <typename T>
+struct T2 {
+  T x, y;
+};
 
 __device__ __forceinline__ float fit_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fit_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
@@ -286,6 +301,90 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_rms(FitDev F, double *__res
   }
 }
 
+// sum_k a_k at corner (a, b) of a sensor whose (sensor, mirror) taps start at
+// `tab`: every mirror seen like a layer at its altitude, with the cone effect
+// of a laser guide star (Sec. 4.2, A_hat).
+template <typename T>
+__device__ __forceinline__ T sensor_mirror(const FitDev &F, const T *__restrict__ cmd, int tab, int nc, int a,
+                                           int b) {
+  const T *fx = static_cast<const T *>(F.sfx), *fy = static_cast<const T *>(F.sfy);
+  T psi = T(0);
+  for (int k = 0; k < F.n_dm; ++k) {
+    const int n = F.dm_n[k], o = tab + k * nc;
+    const int x0 = F.sx0[o + a], y0 = F.sy0[o + b];
+    const T wx1 = fx[o + a], wy1 = fy[o + b];
+    const T wx[2] = {T(1) - wx1, wx1}, wy[2] = {T(1) - wy1, wy1};
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy) {
+      const int iy = y0 + dy;
+      if (iy < 0 || iy >= n) continue;
+      T row = T(0);
+#pragma unroll
+      for (int dx = 0; dx < 2; ++dx) {
+        const int ix = x0 + dx;
+        if (ix >= 0 && ix < n) row += wx[dx] * cmd[F.dm_off[k] + iy * n + ix];
+      }
+      psi += wy[dy] * row;
+    }
+  }
+  return psi;
+}
+
+// Fried slopes of the mirror field on valid subaperture (a, b).
+template <typename T>
+__device__ __forceinline__ T2<T> mirror_slopes_at(const FitDev &F, const T *cmd, int tab, int nc, int a, int b) {
+  const T p00 = sensor_mirror(F, cmd, tab, nc, a, b), p10 = sensor_mirror(F, cmd, tab, nc, a + 1, b);
+  const T p01 = sensor_mirror(F, cmd, tab, nc, a, b + 1), p11 = sensor_mirror(F, cmd, tab, nc, a + 1, b + 1);
+  return {T(0.5) * (p10 + p11 - p00 - p01), T(0.5) * (p01 + p11 - p00 - p10)};
+}
+
+// out = in + scale * A_hat cmd (in = NULL: 0) in the plan's slope layout:
+// Fried slopes of the mirrors on every valid subaperture, or their two means
+// for a tip/tilt-only sensor.  grid.y = sensor.
+template <typename T>
+__global__ void __launch_bounds__(kFitThreads) k_mirror_slopes(FitDev F, const T *__restrict__ cmd,
+                                                              const T *__restrict__ in, T *__restrict__ out,
+                                                              T scale) {
+  pdl_trigger();
+  const int m = blockIdx.y;
+  const int4 sd = F.sens[m];
+  const int2 so = F.sens_off[m];
+  pdl_wait();
+  if (sd.w) {
+    if (blockIdx.x != 0) return;
+    Acc<T> ax, ay;
+    for (int j = threadIdx.x; j < sd.y; j += blockDim.x) {
+      const int2 ab = F.sub_ab[so.y + j];
+      const T2<T> g = mirror_slopes_at(F, cmd, so.x, sd.z, ab.x, ab.y);
+      ax.add(g.x);
+      ay.add(g.y);
+    }
+    const double2 v = block_sum2(ax, ay);
+    if (threadIdx.x == 0) {
+      out[sd.x] = (in ? in[sd.x] : T(0)) + scale * T(v.x / sd.y);
+      out[sd.x + 1] = (in ? in[sd.x + 1] : T(0)) + scale * T(v.y / sd.y);
+    }
+    return;
+  }
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= sd.y) return;
+  const int2 ab = F.sub_ab[so.y + j];
+  const T2<T> g = mirror_slopes_at(F, cmd, so.x, sd.z, ab.x, ab.y);
+  out[sd.x + j] = (in ? in[sd.x + j] : T(0)) + scale * g.x;
+  out[sd.x + sd.y + j] = (in ? in[sd.x + sd.y + j] : T(0)) + scale * g.y;
+}
+
+// Algorithm 4.1, step 3 with step 2 folded in: a_t = a_{t-1} + g (R s_ol - a_{t-2}).
+template <typename T>
+__global__ void __launch_bounds__(kFitThreads) k_polc_update(FitDev F, const T *__restrict__ a_tm1,
+                                                            const T *__restrict__ a_rec, const T *a_tm2, T *a_t,
+                                                            T gain) {
+  pdl_trigger();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  pdl_wait();
+  if (i < F.n_act) a_t[i] = fit_fma(gain, a_rec[i] - a_tm2[i], a_tm1[i]);
+}
+
 // ------------------------------------------------------------------ launchers
 
 template <typename T>
@@ -317,6 +416,18 @@ cudaError_t fit_rms(const FitDev &F, double *rms, cudaStream_t s) {
 }
 
 template <typename T>
+cudaError_t mirror_slopes(const FitDev &F, const T *cmd, const T *in, T *out, T scale, cudaStream_t s) {
+  const dim3 g((F.max_S + kFitThreads - 1) / kFitThreads, F.n_wfs);
+  return launch_ex(k_mirror_slopes<T>, g, kFitThreads, 0, 0, s, F, cmd, in, out, scale);
+}
+
+template <typename T>
+cudaError_t polc_update(const FitDev &F, const T *a_tm1, const T *a_rec, const T *a_tm2, T *a_t, T gain,
+                        cudaStream_t s) {
+  return launch_ex(k_polc_update<T>, dim3(F.nblk_upd), kFitThreads, 0, 0, s, F, a_tm1, a_rec, a_tm2, a_t, gain);
+}
+
+template <typename T>
 cudaError_t fit_update(const FitDev &F, T *a, int it, int cold, cudaStream_t s) {
   return launch_ex(k_fit_update<T>, dim3(F.nblk_upd), kFitThreads, 0, 0, s, F, a, it, cold);
 }
@@ -336,11 +447,23 @@ struct tomo_fit {
   long long n_active = 0;
   int n_points = 0;
   cudaStream_t cap = nullptr;
-  struct Graph {
+  // The arguments of one graph-launched call.  kind 0: tomo_fit_solve (in =
+  // layers); 1: tomo_reconstruct (in = slopes); 2: tomo_polc_step (in = slopes).
+  struct Call {
     int kind;
     const void *in;
     void *x, *a;
+    const void *a_tm2, *a_tm1;
+    void *a_t;
+    double gain;
     int iters, fit_iters, warm;
+    bool operator==(const Call &o) const {
+      return kind == o.kind && in == o.in && x == o.x && a == o.a && a_tm2 == o.a_tm2 && a_tm1 == o.a_tm1 &&
+             a_t == o.a_t && gain == o.gain && iters == o.iters && fit_iters == o.fit_iters && warm == o.warm;
+    }
+  };
+  struct Graph {
+    Call call;
     cudaGraphExec_t exec;
     int kernels;
   };
@@ -377,6 +500,12 @@ struct FitTables {
   std::vector<int2> lay;
   int kw = 0, n_points = 0;
   long long n_active = 0;
+  // A_hat: per sensor, per mirror, the corner taps; the valid subapertures
+  std::vector<int4> sens;
+  std::vector<int2> sens_off, sub_ab;
+  std::vector<int> sx0, sy0;
+  std::vector<double> sfx, sfy;
+  int max_S = 0;
 };
 
 // Left tap and fraction of coordinate g: g = i0 + f, 0 <= f < 1.
@@ -488,6 +617,36 @@ tomo_status build_tables(const tomo::HostPlan &H, const tomo_fit_geometry *g, Fi
     }
     for (auto v : hit) T->n_active += v;
   }
+  // the mirrors on the plan's sensors: corner (a, b) of sensor m sees mirror k at
+  // ((1 - h_k/H_m) r + theta_m h_k), cone factor 1 for a natural star
+  for (int m = 0; m < H.n_wfs; ++m) {
+    const tomo::WfsDev &W = H.wfs[m];
+    const int n = W.n, ncm = W.nc;
+    const double h_gs = H.wfs_height[m];
+    std::vector<int2> subs;
+    for (int b = 0; b < n; ++b)
+      for (int a = 0; a < n; ++a)
+        if (H.sub_idx[W.sub_off + b * n + a] >= 0) subs.push_back({a, b});
+    T->sens.push_back({W.slope_off, static_cast<int>(subs.size()), ncm, W.kind == tomo::kTTOnly ? 1 : 0});
+    T->sens_off.push_back({static_cast<int>(T->sx0.size()), static_cast<int>(T->sub_ab.size())});
+    T->sub_ab.insert(T->sub_ab.end(), subs.begin(), subs.end());
+    T->max_S = std::max(T->max_S, static_cast<int>(subs.size()));
+    for (int k = 0; k < g->n_dm; ++k) {
+      const tomo_dm &dm = g->dms[k];
+      const double cone = std::isfinite(h_gs) ? 1.0 - dm.altitude / h_gs : 1.0;
+      for (int axis = 0; axis < 2; ++axis) {
+        const double th = axis == 0 ? H.wfs_theta[m].x : H.wfs_theta[m].y;
+        for (int a = 0; a < ncm; ++a) {
+          const double r = (a - 0.5 * n) * W.d_sub;
+          int i0;
+          double f;
+          tap((cone * r + th * dm.altitude) / dm.pitch + 0.5 * (dm.n - 1), &i0, &f);
+          (axis == 0 ? T->sx0 : T->sy0).push_back(i0);
+          (axis == 0 ? T->sfx : T->sfy).push_back(f);
+        }
+      }
+    }
+  }
   // layer taps (natural guide star: no cone)
   const int L = H.n_layers;
   T->px0.resize(static_cast<size_t>(L) * nd * nc);
@@ -546,33 +705,59 @@ tomo_status enqueue_fit_any(tomo_fit *f, const void *layers, void *a, int iters,
                            : enqueue_fit<double>(f, layers, a, iters, warm, s, nk);
 }
 
-// kind 0: tomo_fit_solve, 1: tomo_reconstruct.
-tomo_status enqueue_kind(tomo_fit *f, int kind, const void *in, void *x, void *a, int iters, int fit_iters,
-                         int warm, cudaStream_t s, int *nk) {
-  if (kind == 0) return enqueue_fit_any(f, in, a, fit_iters, warm, s, nk);
+// The launches of one call on stream s (added to the launch count).
+tomo_status enqueue_call(tomo_fit *f, const tomo_fit::Call &c, cudaStream_t s, int *nk) {
+  if (c.kind == 0) return enqueue_fit_any(f, c.in, c.a, c.fit_iters, c.warm, s, nk);
+  const void *slopes = c.in;
+  int k0 = 0;
+  if (c.kind == 2) {
+    // Algorithm 4.1, step 1: s_ol = s + A_hat a_{t-2}
+    if (f->precision == 0)
+      FIT_CUDA(tomo::mirror_slopes<float>(f->F, static_cast<const float *>(c.a_tm2), static_cast<const float *>(c.in),
+                                          static_cast<float *>(f->F.s_ol), 1.f, s), "pseudo-open-loop slopes");
+    else
+      FIT_CUDA(tomo::mirror_slopes<double>(f->F, static_cast<const double *>(c.a_tm2),
+                                           static_cast<const double *>(c.in), static_cast<double *>(f->F.s_ol), 1.0,
+                                           s), "pseudo-open-loop slopes");
+    tomo::count_launches(1);
+    slopes = f->F.s_ol;
+    k0 = 1;
+  }
   int k1 = 0, k2 = 0;
-  FIT_TRY(tomo::enqueue_plan_solve(f->plan, in, x, iters, warm, s, &k1));
+  FIT_TRY(tomo::enqueue_plan_solve(f->plan, slopes, c.x, c.iters, c.warm, s, &k1));
   // phi = W^-1 c into the fit's layer buffer
   tomo_plan *p = f->plan;
   tomo::IoArgs io{};
-  io.in0[0] = x;
+  io.in0[0] = c.x;
   io.out0[0] = f->phi;
   const tomo::LaunchSet &L = p->ls;
   FIT_CUDA(tomo::launch_synthesis(L.precision, 0, L.lf, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem, io, s),
            "synthesis of the reconstructed layers");
   tomo::count_launches(1);
-  FIT_TRY(enqueue_fit_any(f, f->phi, a, fit_iters, warm, s, &k2));
-  *nk = k1 + 1 + k2;
+  FIT_TRY(enqueue_fit_any(f, f->phi, c.a, c.fit_iters, c.warm, s, &k2));
+  int k3 = 0;
+  if (c.kind == 2) {
+    // steps 2 and 3: a_t = a_{t-1} + g (R s_ol - a_{t-2})
+    if (f->precision == 0)
+      FIT_CUDA(tomo::polc_update<float>(f->F, static_cast<const float *>(c.a_tm1), static_cast<const float *>(c.a),
+                                        static_cast<const float *>(c.a_tm2), static_cast<float *>(c.a_t),
+                                        static_cast<float>(c.gain), s), "control update");
+    else
+      FIT_CUDA(tomo::polc_update<double>(f->F, static_cast<const double *>(c.a_tm1), static_cast<const double *>(c.a),
+                                         static_cast<const double *>(c.a_tm2), static_cast<double *>(c.a_t), c.gain,
+                                         s), "control update");
+    tomo::count_launches(1);
+    k3 = 1;
+  }
+  *nk = k0 + k1 + 1 + k2 + k3;
   return TOMO_OK;
 }
 
-tomo_status run_graph(tomo_fit *f, int kind, const void *in, void *x, void *a, int iters, int fit_iters,
-                      int warm, cudaStream_t s) {
+// Replays the call from a graph cached per argument set (captured on first use).
+tomo_status run_graph(tomo_fit *f, const tomo_fit::Call &c, cudaStream_t s) {
   tomo_fit::Graph *ge = nullptr;
   for (auto &g : f->graphs)
-    if (g.kind == kind && g.in == in && g.x == x && g.a == a && g.iters == iters && g.fit_iters == fit_iters &&
-        g.warm == warm)
-      ge = &g;
+    if (g.call == c) ge = &g;
   if (!ge) {
     if (f->graphs.size() >= 16) {
       cudaGraphExecDestroy(f->graphs.front().exec);
@@ -582,7 +767,7 @@ tomo_status run_graph(tomo_fit *f, int kind, const void *in, void *x, void *a, i
     FIT_CUDA(cudaStreamBeginCapture(f->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
     int nk = 0;
     const long long before = tomo_launch_count();
-    tomo_status st = enqueue_kind(f, kind, in, x, a, iters, fit_iters, warm, f->cap, &nk);
+    tomo_status st = enqueue_call(f, c, f->cap, &nk);
     tomo::count_launches(before - tomo_launch_count());   // a capture launches nothing
     cudaError_t ce = cudaStreamEndCapture(f->cap, &graph);
     if (st != TOMO_OK) {
@@ -594,12 +779,20 @@ tomo_status run_graph(tomo_fit *f, int kind, const void *in, void *x, void *a, i
     ce = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     if (ce != cudaSuccess) return fit_cuda(ce, "graph instantiate");
-    f->graphs.push_back({kind, in, x, a, iters, fit_iters, warm, exec, nk});
+    f->graphs.push_back({c, exec, nk});
     ge = &f->graphs.back();
   }
   FIT_CUDA(cudaGraphLaunch(ge->exec, s), "graph launch");
   tomo::count_launches(ge->kernels);
   return TOMO_OK;
+}
+
+// Runs a call from its graph, or launch by launch when the plan's launch mode
+// says so.
+tomo_status run_call(tomo_fit *f, const tomo_fit::Call &c, cudaStream_t s) {
+  if (f->plan->use_graphs) return run_graph(f, c, s);
+  int nk = 0;
+  return enqueue_call(f, c, s, &nk);
 }
 
 template <typename T>
@@ -656,6 +849,8 @@ tomo_status tomo_fit_create(tomo_plan *p, const tomo_fit_geometry *g, tomo_fit *
   F.n_act = static_cast<int>(n_act);
   F.kw = T.kw;
   F.n_points = T.n_points;
+  F.n_wfs = H.n_wfs;
+  F.max_S = std::max(1, T.max_S);
   F.nblk_adj = static_cast<int>((4 * n_act + tomo::kFitThreads - 1) / tomo::kFitThreads);
   F.nblk_upd = static_cast<int>((n_act + tomo::kFitThreads - 1) / tomo::kFitThreads);
   F.part_stride = std::max(F.nblk_adj, F.nblk_upd);
@@ -672,7 +867,7 @@ tomo_status tomo_fit_create(tomo_plan *p, const tomo_fit_geometry *g, tomo_fit *
   const size_t es = f->esz;
   struct Item { size_t *off; size_t bytes; };
   size_t o_act, o_lay, o_hx0, o_hy0, o_hfx, o_hfy, o_px0, o_py0, o_pfx, o_pfy, o_wx0, o_wy0, o_wxw, o_wyw,
-      o_u, o_r, o_p, o_q, o_phi, o_part, o_flag;
+      o_sens, o_soff, o_sub, o_sx0, o_sy0, o_sfx, o_sfy, o_u, o_r, o_p, o_q, o_phi, o_sol, o_part, o_flag;
   const Item items[] = {
       {&o_act, T.act.size()},
       {&o_lay, T.lay.size() * sizeof(int2)},
@@ -688,11 +883,19 @@ tomo_status tomo_fit_create(tomo_plan *p, const tomo_fit_geometry *g, tomo_fit *
       {&o_wy0, T.wy0.size() * sizeof(int)},
       {&o_wxw, T.wxw.size() * es},
       {&o_wyw, T.wyw.size() * es},
+      {&o_sens, T.sens.size() * sizeof(int4)},
+      {&o_soff, T.sens_off.size() * sizeof(int2)},
+      {&o_sub, T.sub_ab.size() * sizeof(int2)},
+      {&o_sx0, T.sx0.size() * sizeof(int)},
+      {&o_sy0, T.sy0.size() * sizeof(int)},
+      {&o_sfx, T.sfx.size() * es},
+      {&o_sfy, T.sfy.size() * es},
       {&o_u, static_cast<size_t>(nd) * nc * nc * es},
       {&o_r, n_act * es},
       {&o_p, n_act * es},
       {&o_q, n_act * es},
       {&o_phi, static_cast<size_t>(H.n) * es},
+      {&o_sol, static_cast<size_t>(H.n_slopes) * es},
       {&o_part, static_cast<size_t>(tomo::kRrSlots + 2) * F.part_stride * sizeof(double)},
       {&o_flag, sizeof(double)},
   };
@@ -711,8 +914,14 @@ tomo_status tomo_fit_create(tomo_plan *p, const tomo_fit_geometry *g, tomo_fit *
   std::memcpy(img.data() + o_py0, T.py0.data(), T.py0.size() * sizeof(int));
   std::memcpy(img.data() + o_wx0, T.wx0.data(), T.wx0.size() * sizeof(int));
   std::memcpy(img.data() + o_wy0, T.wy0.data(), T.wy0.size() * sizeof(int));
+  std::memcpy(img.data() + o_sens, T.sens.data(), T.sens.size() * sizeof(int4));
+  std::memcpy(img.data() + o_soff, T.sens_off.data(), T.sens_off.size() * sizeof(int2));
+  std::memcpy(img.data() + o_sub, T.sub_ab.data(), T.sub_ab.size() * sizeof(int2));
+  std::memcpy(img.data() + o_sx0, T.sx0.data(), T.sx0.size() * sizeof(int));
+  std::memcpy(img.data() + o_sy0, T.sy0.data(), T.sy0.size() * sizeof(int));
   const std::pair<size_t, const std::vector<double> *> reals[] = {
-      {o_hfx, &T.hfx}, {o_hfy, &T.hfy}, {o_pfx, &T.pfx}, {o_pfy, &T.pfy}, {o_wxw, &T.wxw}, {o_wyw, &T.wyw}};
+      {o_hfx, &T.hfx}, {o_hfy, &T.hfy}, {o_pfx, &T.pfx}, {o_pfy, &T.pfy}, {o_wxw, &T.wxw}, {o_wyw, &T.wyw},
+      {o_sfx, &T.sfx}, {o_sfy, &T.sfy}};
   for (const auto &rv : reals) {
     if (f->precision) put<double>(img, rv.first, *rv.second);
     else put<float>(img, rv.first, *rv.second);
@@ -746,6 +955,14 @@ tomo_status tomo_fit_create(tomo_plan *p, const tomo_fit_geometry *g, tomo_fit *
   F.wy0 = reinterpret_cast<const int *>(base + o_wy0);
   F.wxw = base + o_wxw;
   F.wyw = base + o_wyw;
+  F.sens = reinterpret_cast<const int4 *>(base + o_sens);
+  F.sens_off = reinterpret_cast<const int2 *>(base + o_soff);
+  F.sub_ab = reinterpret_cast<const int2 *>(base + o_sub);
+  F.sx0 = reinterpret_cast<const int *>(base + o_sx0);
+  F.sy0 = reinterpret_cast<const int *>(base + o_sy0);
+  F.sfx = base + o_sfx;
+  F.sfy = base + o_sfy;
+  F.s_ol = base + o_sol;
   F.u = base + o_u;
   F.r = base + o_r;
   F.p = base + o_p;
@@ -823,11 +1040,8 @@ tomo_status tomo_fit_solve(tomo_fit *f, const void *d_layers, void *d_a, int ite
   if (!f || !d_layers || !d_a) return fit_fail(TOMO_ERR_ARG, "NULL argument");
   if (iters < 0 || iters > 100000) return fit_fail(TOMO_ERR_ARG, "iters out of range");
   tomo::DeviceGuard dg(f->device);
-  const tomo_plan *p = f->plan;
-  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-  if (p->use_graphs) return run_graph(f, 0, d_layers, nullptr, d_a, 0, iters, warm ? 1 : 0, s);
-  int nk = 0;
-  return enqueue_fit_any(f, d_layers, d_a, iters, warm ? 1 : 0, s, &nk);
+  tomo_fit::Call c{0, d_layers, nullptr, d_a, nullptr, nullptr, nullptr, 0.0, 0, iters, warm ? 1 : 0};
+  return run_call(f, c, static_cast<cudaStream_t>(cuda_stream));
 }
 
 tomo_status tomo_reconstruct(tomo_fit *f, const void *d_slopes, void *d_coeffs, void *d_a, int iters,
@@ -836,10 +1050,39 @@ tomo_status tomo_reconstruct(tomo_fit *f, const void *d_slopes, void *d_coeffs, 
   if (iters < 0 || iters > 100000 || fit_iters < 0 || fit_iters > 100000)
     return fit_fail(TOMO_ERR_ARG, "iters out of range");
   tomo::DeviceGuard dg(f->device);
+  tomo_fit::Call c{1, d_slopes, d_coeffs, d_a, nullptr, nullptr, nullptr, 0.0, iters, fit_iters, warm ? 1 : 0};
+  return run_call(f, c, static_cast<cudaStream_t>(cuda_stream));
+}
+
+tomo_status tomo_mirror_slopes(tomo_fit *f, const void *d_a, const void *d_in, void *d_out, double scale,
+                               void *cuda_stream) {
+  if (!f || !d_a || !d_out) return fit_fail(TOMO_ERR_ARG, "NULL argument");
+  if (!std::isfinite(scale)) return fit_fail(TOMO_ERR_ARG, "scale must be finite");
+  tomo::DeviceGuard dg(f->device);
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-  if (f->plan->use_graphs) return run_graph(f, 1, d_slopes, d_coeffs, d_a, iters, fit_iters, warm ? 1 : 0, s);
-  int nk = 0;
-  return enqueue_kind(f, 1, d_slopes, d_coeffs, d_a, iters, fit_iters, warm ? 1 : 0, s, &nk);
+  if (f->precision == 0)
+    FIT_CUDA(tomo::mirror_slopes<float>(f->F, static_cast<const float *>(d_a), static_cast<const float *>(d_in),
+                                        static_cast<float *>(d_out), static_cast<float>(scale), s), "mirror slopes");
+  else
+    FIT_CUDA(tomo::mirror_slopes<double>(f->F, static_cast<const double *>(d_a), static_cast<const double *>(d_in),
+                                         static_cast<double *>(d_out), scale, s), "mirror slopes");
+  tomo::count_launches(1);
+  return TOMO_OK;
+}
+
+tomo_status tomo_polc_step(tomo_fit *f, const void *d_slopes, void *d_coeffs, void *d_a_rec, const void *d_a_tm2,
+                           const void *d_a_tm1, void *d_a_t, double gain, int iters, int fit_iters, int warm,
+                           void *cuda_stream) {
+  if (!f || !d_slopes || !d_coeffs || !d_a_rec || !d_a_tm2 || !d_a_tm1 || !d_a_t)
+    return fit_fail(TOMO_ERR_ARG, "NULL argument");
+  if (iters < 0 || iters > 100000 || fit_iters < 0 || fit_iters > 100000)
+    return fit_fail(TOMO_ERR_ARG, "iters out of range");
+  if (!std::isfinite(gain)) return fit_fail(TOMO_ERR_ARG, "gain must be finite");
+  if (d_a_t == d_a_tm1 || d_a_rec == d_a_tm2 || d_a_rec == d_a_tm1 || d_a_rec == d_a_t)
+    return fit_fail(TOMO_ERR_ARG, "a_t may share storage with a_tm2 only; a_rec with none");
+  tomo::DeviceGuard dg(f->device);
+  tomo_fit::Call c{2, d_slopes, d_coeffs, d_a_rec, d_a_tm2, d_a_tm1, d_a_t, gain, iters, fit_iters, warm ? 1 : 0};
+  return run_call(f, c, static_cast<cudaStream_t>(cuda_stream));
 }
 
 void tomo_fit_destroy(tomo_fit *f) {

@@ -313,6 +313,8 @@ tomo_status build_host_plan(const tomo_geometry *geo, HostPlan *P, std::string *
     d.v_off = v_off;
     v_off += nc * nc;
     P->wfs.push_back(d);
+    P->wfs_theta.push_back({W.theta_x, W.theta_y});
+    P->wfs_height.push_back(lgs ? W.height : INFINITY);
   }
   P->n_slopes = slope_off;
   P->v_total = v_off;

@@ -27,6 +27,8 @@ struct HostPlan {
   std::vector<LayerDev> layers;
   std::vector<double> layer_alt, layer_dx;   // altitude and grid spacing (m) of each layer
   std::vector<WfsDev> wfs;
+  std::vector<double2> wfs_theta;          // guide-star direction (rad) of each sensor
+  std::vector<double> wfs_height;          // laser guide star altitude (m); INFINITY: natural star
   std::vector<int> sub_idx;
   std::vector<unsigned char> active;
   std::vector<int> pos_off, pos_i0;
