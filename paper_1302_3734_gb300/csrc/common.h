@@ -19,7 +19,8 @@ constexpr int kAnalysisThreadsMax = 1024;  // ... when its shared memory leaves 
 constexpr int kSynthThreads = 512;     // threads per CTA of the synthesis kernel (at most)
 constexpr int kGatherThreads = 512;    // threads per CTA of the separate gather kernel
 constexpr int kMaxGatherSensors = 64;  // dense sensors the separate gather kernel stages
-constexpr int kUpdChunk = 1024;    // coefficients per CTA of the vector update
+constexpr int kUpdChunk = 1024;    // coefficients per pass of a vector-update CTA
+constexpr int kUpdMaxBlocks = 608; // update CTAs per instance at most (four per SM of 152 SMs)
 constexpr int kMaxTapsNode = 4;    // corners per axis whose bilinear taps reach one node
 
 enum WfsKind : int { kFull = 0, kRemoveTT = 1, kTTOnly = 2 };
@@ -215,6 +216,6 @@ TOMO_HD inline StageLayout stage_layout(int n_dense, int N, int R0, int rec_stri
 // Work items.
 struct ClusterItem { int inst, layer; };
 struct FwdItem { int inst, wfs, a0, b0, tile, pad0, pad1, pad2; };  // a0 < 0: tip/tilt-only sensor
-struct UpdItem { int inst, start, blk, pad; };
+struct UpdItem { int inst, start, blk, chunks; };   // chunks: passes of kUpdChunk coefficients
 
 }  // namespace tomo

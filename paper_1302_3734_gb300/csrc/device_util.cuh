@@ -127,7 +127,8 @@ static __device__ double2 block_sum2(Acc<float> a, Acc<float> b) {
 }
 
 // The block's double-float sums of (a, b) as (a.hi, a.lo, b.hi, b.lo), valid
-// in thread 0.
+// in thread 0.  No barrier at the end: warp 0 may still read the scratch when
+// the other warps return, so a second call needs a __syncthreads() first.
 static __device__ float4 block_sum2_df(Acc<float> a, Acc<float> b) {
   __shared__ float s_red[4][32];
   warp_merge_down(a);

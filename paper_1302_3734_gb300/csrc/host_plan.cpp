@@ -664,10 +664,15 @@ tomo_status build_host_plan(const tomo_geometry *geo, HostPlan *P, std::string *
   P->cl_part_off = part;
   part += 2 * P->n_layers * P->C;   // (dot, second dot) per CTA
   for (int l = 0; l < P->n_layers; ++l) P->cl_items.push_back({0, l});
-  P->n_upd_blocks = (P->n + kUpdChunk - 1) / kUpdChunk;
+  // update CTAs: consecutive chunks of kUpdChunk coefficients, at most kUpdMaxBlocks CTAs
+  // (the consumers of their partials sum one partial per CTA)
+  const int chunks = (P->n + kUpdChunk - 1) / kUpdChunk;
+  const int per_cta = (chunks + kUpdMaxBlocks - 1) / kUpdMaxBlocks;
+  P->n_upd_blocks = (chunks + per_cta - 1) / per_cta;
   P->upd_part_off = part;
   part += 2 * P->n_upd_blocks;
-  for (int b = 0; b < P->n_upd_blocks; ++b) P->upd_items.push_back({0, b * kUpdChunk, b, 0});
+  for (int b = 0; b < P->n_upd_blocks; ++b)
+    P->upd_items.push_back({0, b * per_cta * kUpdChunk, b, std::min(per_cta, chunks - b * per_cta)});
   P->fwd_part_off = part;
   for (int m = 0; m < P->n_wfs; ++m) {
     WfsDev &d = P->wfs[m];

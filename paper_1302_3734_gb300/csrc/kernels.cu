@@ -313,6 +313,7 @@ __global__ void __launch_bounds__(kThreads) k_forward(const InstDev *__restrict_
   // 4. tip/tilt removal: this tile's sums of z (the consumer forms the means)
   if (four) {
     store_tile_partial(I.part + W.part_off + 4 * it.tile, sx_acc, sy_acc);
+    __syncthreads();   // warp 0 has read the reduction scratch before it is reused
     store_tile_partial(I.part + W.part_off + 4 * it.tile + 2, qx_acc, qy_acc);
   } else {
     store_tile_partial(I.part + W.part_off + 2 * it.tile, sx_acc, sy_acc);
@@ -724,6 +725,8 @@ __device__ void gather_rows_staged(const InstDev &I, const GatherStage<T> &st, i
 // reach (gt_cols), then the pupil-edge list.  Each node receives the sensors'
 // terms in sensor order, as the fused gathers do.  For plans whose tables do
 // not fit the analysis CTAs' shared memory; k_gather runs it.
+constexpr int kGatherRows = 2;   // rows of a column one thread of k_gather gathers at once
+
 template <typename T, int KT>
 __device__ void gather_band_global(const InstDev &I, int l, int N, int R0, int crank, T *A,
                                    const T *s_coef, const int *s_go, const int *s_nc, const int *s_el,
@@ -737,30 +740,46 @@ __device__ void gather_band_global(const InstDev &I, int l, int N, int R0, int c
   for (int md = 0; md < Md; ++md) {
     const int2 cols = s_cols[md];
     if (cols.y == 0) continue;
-    // threads per row: the power of two >= the column count (at most nt)
+    // threads per column group: tpr threads cover the columns (tpr the power of two
+    // >= the column count, at most nt), the nt / tpr groups share the rows
     int tpr = 1;
     while (tpr < cols.y && tpr < nt) tpr <<= 1;
-    const int rows_per_pass = nt / tpr, ci = tid % tpr;
+    const int groups = nt / tpr, ci = tid % tpr, rg = tid / tpr;
     const T *xr = rec + static_cast<size_t>(s_go[md]) * RS;
     const T *yr = rec + static_cast<size_t>(s_go[md] + N + k0) * RS;
-    for (int kl = tid / tpr; kl < R0; kl += rows_per_pass) {
-      TapRec<T, KT> y;
-      y.load(yr + kl * RS);
-      if (y.off < 0) continue;
-      for (int c = ci; c < cols.y; c += tpr) {
-        const int i = (cols.x + c) & (N - 1);
-        TapRec<T, KT> x;
-        x.load(xr + i * RS);
-        if (x.off < 0) continue;
-        T acc = window_sum<T, KT, false>(vv + y.off + x.off, s_nc[md], x, y);
-        if (s_el[md] >= 0) {
-          // spot elongation with tip/tilt removal: the windows of m_x Gx + m_y Gy
-          const T *gx = static_cast<const T *>(I.gel), *gy = gx + I.v_total;
-          const int k = s_el[md];
-          acc += s_coef[2 * kMaxEdgeSlots + 2 * k] * window_sum<T, KT, false>(gx + y.off + x.off, s_nc[md], x, y) +
-                 s_coef[2 * kMaxEdgeSlots + 2 * k + 1] * window_sum<T, KT, false>(gy + y.off + x.off, s_nc[md], x, y);
+    const int nc = s_nc[md], el = s_el[md];
+    for (int c = ci; c < cols.y; c += tpr) {
+      const int i = (cols.x + c) & (N - 1);
+      TapRec<T, KT> x;   // the column's record, once for all rows of the band
+      x.load(xr + i * RS);
+      if (x.off < 0) continue;
+      // kGatherRows rows at a time: their records, then their windows, have no
+      // dependences between them
+      for (int kb = rg; kb < R0; kb += kGatherRows * groups) {
+        TapRec<T, KT> y[kGatherRows];
+#pragma unroll
+        for (int u = 0; u < kGatherRows; ++u) {
+          const int kl = kb + u * groups;
+          if (kl < R0) y[u].load(yr + kl * RS);
+          else y[u].off = -1;
         }
-        A[kl * N + i] += acc;
+        T acc[kGatherRows];
+#pragma unroll
+        for (int u = 0; u < kGatherRows; ++u) {
+          acc[u] = T(0);
+          if (y[u].off < 0) continue;
+          acc[u] = window_sum<T, KT, false>(vv + y[u].off + x.off, nc, x, y[u]);
+          if (el >= 0) {
+            // spot elongation with tip/tilt removal: the windows of m_x Gx + m_y Gy
+            const T *gx = static_cast<const T *>(I.gel), *gy = gx + I.v_total;
+            acc[u] += s_coef[2 * kMaxEdgeSlots + 2 * el] * window_sum<T, KT, false>(gx + y[u].off + x.off, nc, x, y[u]) +
+                      s_coef[2 * kMaxEdgeSlots + 2 * el + 1] *
+                          window_sum<T, KT, false>(gy + y[u].off + x.off, nc, x, y[u]);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kGatherRows; ++u)
+          if (y[u].off >= 0) A[(kb + u * groups) * N + i] += acc[u];
       }
     }
     __syncthreads();
@@ -780,7 +799,7 @@ __device__ void gather_band_global(const InstDev &I, int l, int N, int R0, int c
 // finished (dependency wait) and the next synthesis rewrites it.
 // tt_mode as in edge_coefficients; io.in1: the slopes (tip/tilt-only data).
 template <typename T>
-__global__ void __launch_bounds__(kGatherThreads) k_gather(const InstDev *__restrict__ insts,
+__global__ void __launch_bounds__(kGatherThreads, sizeof(T) == 4 ? 2 : 1) k_gather(const InstDev *__restrict__ insts,
                                                            const ClusterItem *__restrict__ items,
                                                            IoArgs io, int C, int tt_mode) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1397,32 +1416,11 @@ __global__ void __launch_bounds__(kSynthThreads, 1) k_synthesis(const InstDev *_
 // -------------------------------------------------------------- k_update
 // alpha = (r.z)_it / (p.Ap) from the analysis partials; x += alpha p,
 // r -= alpha q, z = J^-1 r; partials r.z and r.r per CTA.  io.out0: x.
-// Four consecutive elements per thread (kUpdChunk = 4 * kThreads).
+// Four consecutive elements per thread and pass (kUpdChunk = 4 * kThreads);
+// a CTA makes it.chunks passes over consecutive chunks.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_update(const InstDev *__restrict__ insts,
-                                                    const UpdItem *__restrict__ items, IoArgs io,
-                                                    int flags) {
-  __shared__ T s_alpha;
-  pdl_trigger();
-  const UpdItem it = items[blockIdx.x];
-  if (io.active && !io.active[it.inst]) return;
-  const InstDev *I = insts + it.inst;
-  T *X = static_cast<T *>(io.out0[it.inst]);
-  T *R = static_cast<T *>(I->r);
-  const T *P = static_cast<const T *>(I->p);
-  const T *Q = static_cast<const T *>(I->q);
-  const T *Jv = static_cast<const T *>(I->jinv);
-  const int precond = I->precond;
-  const int n = I->n;
-  const int iter = flags >> kIterShift;
-  pdl_wait();
-  // the vectors do not depend on alpha: their loads go out first
-  const int i0 = it.start + 4 * threadIdx.x;
-  const bool vec = sizeof(T) == 4 && i0 + 3 < n &&
-                   ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(R) |
-                     reinterpret_cast<uintptr_t>(P) | reinterpret_cast<uintptr_t>(Q) |
-                     reinterpret_cast<uintptr_t>(Jv)) & 15) == 0;
-  T xv[4], rv[4], pv[4], qv[4], jv[4];
+__device__ __forceinline__ void upd_load(const T *X, const T *R, const T *P, const T *Q, const T *Jv, int precond,
+                                         int n, int i0, bool vec, T *xv, T *rv, T *pv, T *qv, T *jv) {
   if (vec) {
     const float4 x4 = reinterpret_cast<const float4 *>(X)[i0 >> 2];
     const float4 r4 = reinterpret_cast<const float4 *>(R)[i0 >> 2];
@@ -1445,6 +1443,49 @@ __global__ void __launch_bounds__(kThreads) k_update(const InstDev *__restrict__
       jv[u] = precond ? Jv[idx] : T(1);
     }
   }
+}
+
+template <typename T>
+__device__ __forceinline__ void upd_store(T *X, T *R, int n, int i0, bool vec, const T *xv, const T *rv) {
+  if (vec) {
+    reinterpret_cast<float4 *>(X)[i0 >> 2] = make_float4(xv[0], xv[1], xv[2], xv[3]);
+    reinterpret_cast<float4 *>(R)[i0 >> 2] = make_float4(rv[0], rv[1], rv[2], rv[3]);
+  } else {
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (i0 + u < n) {
+        X[i0 + u] = xv[u];
+        R[i0 + u] = rv[u];
+      }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_update(const InstDev *__restrict__ insts,
+                                                    const UpdItem *__restrict__ items, IoArgs io,
+                                                    int flags) {
+  __shared__ T s_alpha;
+  pdl_trigger();
+  const UpdItem it = items[blockIdx.x];
+  if (io.active && !io.active[it.inst]) return;
+  const InstDev *I = insts + it.inst;
+  T *X = static_cast<T *>(io.out0[it.inst]);
+  T *R = static_cast<T *>(I->r);
+  const T *P = static_cast<const T *>(I->p);
+  const T *Q = static_cast<const T *>(I->q);
+  const T *Jv = static_cast<const T *>(I->jinv);
+  const int precond = I->precond;
+  const int n = I->n;
+  const int iter = flags >> kIterShift;
+  pdl_wait();
+  const bool aligned = ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(R) |
+                         reinterpret_cast<uintptr_t>(P) | reinterpret_cast<uintptr_t>(Q) |
+                         reinterpret_cast<uintptr_t>(Jv)) & 15) == 0;
+  // the first pass's vectors do not depend on alpha: their loads go out first
+  int i0 = it.start + 4 * threadIdx.x;
+  bool vec = sizeof(T) == 4 && i0 + 3 < n && aligned;
+  T xv[4], rv[4], pv[4], qv[4], jv[4];
+  upd_load(X, R, P, Q, Jv, precond, n, i0, vec, xv, rv, pv, qv, jv);
   {
     const double rz = I->scal[kRz0 + (iter & 1)];
     const double flag = I->scal[kFlag];
@@ -1460,26 +1501,22 @@ __global__ void __launch_bounds__(kThreads) k_update(const InstDev *__restrict__
   }
   const T alpha = s_alpha;
   Acc<T> rz, rr;
+  for (int c = 0;;) {
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    xv[u] += alpha * pv[u];
-    rv[u] -= alpha * qv[u];
-    const T z = precond ? jv[u] * rv[u] : rv[u];
-    if (i0 + u < n) {
-      rz.add_prod(rv[u], z);
-      rr.add_prod(rv[u], rv[u]);
-    }
-  }
-  if (vec) {
-    reinterpret_cast<float4 *>(X)[i0 >> 2] = make_float4(xv[0], xv[1], xv[2], xv[3]);
-    reinterpret_cast<float4 *>(R)[i0 >> 2] = make_float4(rv[0], rv[1], rv[2], rv[3]);
-  } else {
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int u = 0; u < 4; ++u) {
+      xv[u] += alpha * pv[u];
+      rv[u] -= alpha * qv[u];
+      const T z = precond ? jv[u] * rv[u] : rv[u];
       if (i0 + u < n) {
-        X[i0 + u] = xv[u];
-        R[i0 + u] = rv[u];
+        rz.add_prod(rv[u], z);
+        rr.add_prod(rv[u], rv[u]);
       }
+    }
+    upd_store(X, R, n, i0, vec, xv, rv);
+    if (++c >= it.chunks) break;
+    i0 += kUpdChunk;
+    vec = sizeof(T) == 4 && i0 + 3 < n && aligned;
+    upd_load(X, R, P, Q, Jv, precond, n, i0, vec, xv, rv, pv, qv, jv);
   }
   const double2 s = block_sum2(rz, rr);
   if (threadIdx.x == 0) {
