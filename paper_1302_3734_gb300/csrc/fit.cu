@@ -7,14 +7,20 @@
 // H_j a (x) = sum_k a_k(x + h_k theta_j), each mirror a piecewise-bilinear
 // function of its actuator grid; P_j phi (x) = sum_l phi_l(x + h_l theta_j)
 // (eq. ngsproj), bilinear on the periodic layer grids; x runs over the corners
-// of the valid subapertures of the aperture sampling grid.  Three kernels per
-// CG iteration:
+// of the valid subapertures of the aperture sampling grid.  H^T H is constant:
+// it is assembled once on the host (FP64, CSR) and each CG iteration is two
+// kernels:
 //
-//   k_fit_mirror   u_j = H_j p on every (direction, corner), with the CG
-//                  direction p = r + beta p formed on the fly      [corner per thread]
-//   k_fit_adjoint  q = sum_j H_j^T u_j as a gather over per-actuator tap
-//                  windows; writes p; p.q partials                  [4 threads per actuator]
+//   k_fit_spmv     q = H^T H p, with the CG direction p = r + beta p formed on
+//                  the fly and written to the other of two p buffers;
+//                  p.q partials                                     [warp per row]
 //   k_fit_update   alpha, a += alpha p, r -= alpha q, r.r partials  [actuator per thread]
+//
+// The right-hand side and the initial residual stay matrix-free:
+//
+//   k_fit_mirror   u_j = P_j phi - H_j a on every (direction, corner)  [corner per thread]
+//   k_fit_adjoint  r = sum_j H_j^T u_j as a gather over per-actuator tap
+//                  windows; r.r partials                            [4 threads per actuator]
 //
 // The tap tables (corner -> actuator and corner -> layer node, and for H^T
 // each actuator's window of corners with its weights) are built in FP64 on
@@ -24,6 +30,7 @@
 // block, partials summed by every consumer block in a fixed order), so results
 // are bitwise reproducible.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -40,10 +47,12 @@
 
 namespace tomo {
 
-constexpr int kFitThreads = 256;
+constexpr int kFitThreads = 256;   // equals kFwdTile^2: one thread per subaperture of an A_hat tile
+constexpr int kFitRmsThreads = 1024;
 constexpr int kMaxDm = 4;
 constexpr int kMaxFitDirs = 256;
 constexpr int kRrSlots = 4;   // r.r partial slots (ring over iterations), then 2 p.q slots
+constexpr int kFitDirBatch = 4;   // directions whose gather loads one thread issues together
 
 // Everything the fitting kernels read (passed by value).
 struct FitDev {
@@ -59,43 +68,70 @@ struct FitDev {
   const int *wx0, *wy0;       // per (dm, dir, actuator column / row): first corner of its window
   const void *wxw, *wyw;      //   kw weights (T), zero beyond the window
   void *u;                    // [dir][nc*nc]
-  void *r, *p, *q;            // [n_act]
+  void *r, *q;                // [n_act]
+  void *p[2];                 // [n_act]: the CG direction of iteration it is p[it & 1]
+  const int *nrm_ptr;         // H^T H in CSR: row starts (n_act + 1), columns, values (T)
+  const int *nrm_col;
+  const void *nrm_val;
+  int nblk_spmv;
   double *part;               // (kRrSlots + 2) * part_stride
   double *flag;               // nonzero after a breakdown
   // the mirrors seen by the plan's sensors (A_hat)
-  int n_wfs, max_S;
-  const int4 *sens;           // per sensor: slope offset, valid subapertures S, corners per side, tip/tilt only
-  const int2 *sens_off;       // per sensor: first (sensor, mirror) tap entry, first subaperture
+  int n_ms_items;
+  const int4 *ms_items;       // (sensor, first subaperture column, row, tip/tilt only): a 16x16 tile
+                              // of a full sensor, or a whole tip/tilt-only sensor
+  const int4 *sens;           // per sensor: slope offset, valid subapertures S, corners per side
+  const int4 *sens_off;       // per sensor: first (sensor, mirror) tap entry, subaperture index table,
+                              // first pupil-edge corner, pupil-edge corners
   const int *sx0, *sy0;       // per (sensor, mirror): left / lower actuator of each corner column / row
   const void *sfx, *sfy;      //   and its fraction (T)
-  const int2 *sub_ab;         // valid subapertures (a, b) of every sensor, row-major
+  const int *sidx;            // per sensor n x n: slope index of each subaperture, -1 if not valid
+  const int *e_idx;           // pupil-edge corners (b nc + a) of every sensor
+  const void *e_t;            //   and (Gamma^T 1_x, Gamma^T 1_y) there (T pairs)
   void *s_ol;                 // pseudo-open-loop slopes (the plan's slope layout)
 };
 
-// Fixed-order sum of n FP64 partials, returned to every thread of the block.
-__device__ double fit_sum(const double *part, int n) {
-  __shared__ double s_v;
-  if (threadIdx.x < 32) {
-    double a = 0.0;
-    for (int i = threadIdx.x; i < n; i += 32) a += part[i];
-    a = warp_sum(a);
-    if (threadIdx.x == 0) s_v = a;
+// Fixed-order sums of two arrays of FP64 partials (n1 and n2 of them),
+// returned to every thread of the block: each thread adds a strided subset,
+// then the warps' sums are added in warp order.
+__device__ double2 fit_sum2(const double *p1, int n1, const double *p2, int n2) {
+  __shared__ double s_w[2][32];
+  __shared__ double2 s_v;
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < n1; i += blockDim.x) a += p1[i];
+  for (int i = threadIdx.x; i < n2; i += blockDim.x) b += p2[i];
+  a = warp_sum(a);
+  b = warp_sum(b);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    s_w[0][w] = a;
+    s_w[1][w] = b;
   }
   __syncthreads();
-  const double v = s_v;
+  if (w == 0) {
+    const int nw = blockDim.x >> 5;
+    double x = lane < nw ? s_w[0][lane] : 0.0, y = lane < nw ? s_w[1][lane] : 0.0;
+    x = warp_sum(x);
+    y = warp_sum(y);
+    if (lane == 0) s_v = make_double2(x, y);
+  }
   __syncthreads();
-  return v;
+  return s_v;
 }
 
-// r.r of CG iteration `it` (it = 0: the initial residual, from the adjoint
-// kernel; later ones from the updates).
-__device__ __forceinline__ double fit_rr(const FitDev &F, int it) {
-  return fit_sum(F.part + (it % kRrSlots) * F.part_stride, it == 0 ? F.nblk_adj : F.nblk_upd);
+// The r.r partials of CG iteration `it` (it = 0: the initial residual, from
+// the adjoint kernel; later ones from the updates) and their count.
+__device__ __forceinline__ const double *fit_rr_part(const FitDev &F, int it, int *n) {
+  *n = it == 0 ? F.nblk_adj : F.nblk_upd;
+  return F.part + (it % kRrSlots) * F.part_stride;
 }
 
+// beta of iteration it >= 1: r.r of this iteration over r.r of the previous.
 __device__ __forceinline__ double fit_beta(const FitDev &F, int it) {
-  const double num = fit_rr(F, it), den = fit_rr(F, it - 1);
-  return den != 0.0 ? num / den : 0.0;
+  int n1, n0;
+  const double *p1 = fit_rr_part(F, it, &n1), *p0 = fit_rr_part(F, it - 1, &n0);
+  const double2 v = fit_sum2(p1, n1, p0, n0);
+  return v.y != 0.0 ? v.x / v.y : 0.0;
 }
 
 template <typename T>
@@ -112,66 +148,57 @@ __device__ __forceinline__ T fit_dir(const T *r, const T *p, int i, bool first, 
   return first ? r[i] : fit_fma(beta, p[i], r[i]);
 }
 
-// MODE 0: u_j = H_j p, p the CG direction of iteration `it` (from r and the
-//         previous p).
-// MODE 1: u_j = P_j phi - H_j x (x = NULL: P_j phi).
-// MODE 2: u_j = H_j x.
-template <typename T, int MODE>
+// u_j = P_j phi - H_j x on every (direction, corner); phi = NULL: no layers,
+// x = NULL: no mirrors.
+template <typename T>
 __global__ void __launch_bounds__(kFitThreads) k_fit_mirror(FitDev F, const T *__restrict__ x,
-                                                           const T *__restrict__ phi, int it) {
+                                                           const T *__restrict__ phi) {
   pdl_trigger();
   const int j = blockIdx.y, nc = F.nc, nn = nc * nc;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool on = c < nn && F.act[c];
+  if (c >= nn) return;
+  const bool on = F.act[c];
   const int a = c % nc, b = c / nc;
   pdl_wait();
-  T beta = T(0);
-  const bool first = it == 0;
-  if (MODE == 0 && !first) beta = T(fit_beta(F, it));
-  if (c >= nn) return;
   T val = T(0);
-  if (on) {
-    if (MODE == 1 && phi) {
-      const T *fx = static_cast<const T *>(F.pfx), *fy = static_cast<const T *>(F.pfy);
-      for (int l = 0; l < F.n_layers; ++l) {
-        const int2 L = F.lay[l];
-        const int tx = (l * F.n_dir + j) * nc + a, ty = (l * F.n_dir + j) * nc + b;
-        const int x0 = F.px0[tx], y0 = F.py0[ty];
-        const int x1 = (x0 + 1) & (L.x - 1), y1 = (y0 + 1) & (L.x - 1);
-        const T wx = fx[tx], wy = fy[ty];
-        const T *g = phi + L.y;
-        val += (T(1) - wy) * ((T(1) - wx) * g[y0 * L.x + x0] + wx * g[y0 * L.x + x1]) +
-               wy * ((T(1) - wx) * g[y1 * L.x + x0] + wx * g[y1 * L.x + x1]);
-      }
+  if (on && phi) {
+    const T *fx = static_cast<const T *>(F.pfx), *fy = static_cast<const T *>(F.pfy);
+    for (int l = 0; l < F.n_layers; ++l) {
+      const int2 L = F.lay[l];
+      const int tx = (l * F.n_dir + j) * nc + a, ty = (l * F.n_dir + j) * nc + b;
+      const int x0 = F.px0[tx], y0 = F.py0[ty];
+      const int x1 = (x0 + 1) & (L.x - 1), y1 = (y0 + 1) & (L.x - 1);
+      const T wx = fx[tx], wy = fy[ty];
+      const T *g = phi + L.y;
+      val += (T(1) - wy) * ((T(1) - wx) * g[y0 * L.x + x0] + wx * g[y0 * L.x + x1]) +
+             wy * ((T(1) - wx) * g[y1 * L.x + x0] + wx * g[y1 * L.x + x1]);
     }
-    if (MODE != 1 || x) {
-      const T *fx = static_cast<const T *>(F.hfx), *fy = static_cast<const T *>(F.hfy);
-      const T *r = static_cast<const T *>(F.r), *p = static_cast<const T *>(F.p);
-      T h = T(0);
-      for (int k = 0; k < F.n_dm; ++k) {
-        const int n = F.dm_n[k], o = F.dm_off[k];
-        const int tx = (k * F.n_dir + j) * nc + a, ty = (k * F.n_dir + j) * nc + b;
-        const int x0 = F.hx0[tx], y0 = F.hy0[ty];
-        const T wx1 = fx[tx], wy1 = fy[ty];
-        const T wx[2] = {T(1) - wx1, wx1}, wy[2] = {T(1) - wy1, wy1};
+  }
+  if (on && x) {
+    const T *fx = static_cast<const T *>(F.hfx), *fy = static_cast<const T *>(F.hfy);
+    T h = T(0);
 #pragma unroll
-        for (int dy = 0; dy < 2; ++dy) {
-          const int iy = y0 + dy;
-          if (iy < 0 || iy >= n) continue;
-          T row = T(0);
+    for (int k = 0; k < kMaxDm; ++k) {
+      if (k >= F.n_dm) break;
+      const int n = F.dm_n[k], o = F.dm_off[k];
+      const int tx = (k * F.n_dir + j) * nc + a, ty = (k * F.n_dir + j) * nc + b;
+      const int x0 = F.hx0[tx], y0 = F.hy0[ty];
+      const T wx1 = fx[tx], wy1 = fy[ty];
+      const T wx[2] = {T(1) - wx1, wx1}, wy[2] = {T(1) - wy1, wy1};
 #pragma unroll
-          for (int dx = 0; dx < 2; ++dx) {
-            const int ix = x0 + dx;
-            if (ix < 0 || ix >= n) continue;
-            const int i = o + iy * n + ix;
-            const T v = MODE == 0 ? fit_dir(r, p, i, first, beta) : x[i];
-            row += wx[dx] * v;
-          }
-          h += wy[dy] * row;
+      for (int dy = 0; dy < 2; ++dy) {
+        const int iy = y0 + dy;
+        if (iy < 0 || iy >= n) continue;
+        T row = T(0);
+#pragma unroll
+        for (int dx = 0; dx < 2; ++dx) {
+          const int ix = x0 + dx;
+          if (ix >= 0 && ix < n) row += wx[dx] * x[o + iy * n + ix];
         }
+        h += wy[dy] * row;
       }
-      val = MODE == 1 ? val - h : h;
     }
+    val -= h;
   }
   static_cast<T *>(F.u)[j * nn + c] = val;
 }
@@ -185,32 +212,44 @@ __device__ __forceinline__ T fit_gather(const FitDev &F, int k, int i, int jj, i
   const T *u = static_cast<const T *>(F.u);
   const T *wxw = static_cast<const T *>(F.wxw), *wyw = static_cast<const T *>(F.wyw);
   T s = T(0);
-  for (int j = g; j < F.n_dir; j += 4) {
-    const int ex = F.w_off[k] + j * n + i, ey = F.w_off[k] + j * n + jj;
-    const T *ux = u + j * nn + F.wy0[ey] * nc + F.wx0[ex];
-    T wx[KW];
+  // kFitDirBatch of this thread's directions at a time: their window starts,
+  // then their weights and corners, are loaded without dependences between them
+  for (int j0 = g; j0 < F.n_dir; j0 += 4 * kFitDirBatch) {
+    int ex[kFitDirBatch], ey[kFitDirBatch], base[kFitDirBatch];
 #pragma unroll
-    for (int t = 0; t < KW; ++t) wx[t] = wxw[ex * KW + t];
-    T acc = T(0);
-#pragma unroll
-    for (int t2 = 0; t2 < KW; ++t2) {
-      T row = T(0);
-#pragma unroll
-      for (int t1 = 0; t1 < KW; ++t1) row += wx[t1] * ux[t2 * nc + t1];
-      acc += wyw[ey * KW + t2] * row;
+    for (int b = 0; b < kFitDirBatch; ++b) {
+      const int j = min(j0 + 4 * b, F.n_dir - 1);
+      ex[b] = F.w_off[k] + j * n + i;
+      ey[b] = F.w_off[k] + j * n + jj;
+      base[b] = j * nn + F.wy0[ey[b]] * nc + F.wx0[ex[b]];
     }
-    s += acc;
+#pragma unroll
+    for (int b = 0; b < kFitDirBatch; ++b) {
+      if (j0 + 4 * b >= F.n_dir) break;
+      const T *ux = u + base[b];
+      T wx[KW];
+#pragma unroll
+      for (int t = 0; t < KW; ++t) wx[t] = wxw[ex[b] * KW + t];
+      T acc = T(0);
+#pragma unroll
+      for (int t2 = 0; t2 < KW; ++t2) {
+        T row = T(0);
+#pragma unroll
+        for (int t1 = 0; t1 < KW; ++t1) row += wx[t1] * ux[t2 * nc + t1];
+        acc += wyw[ey[b] * KW + t2] * row;
+      }
+      s += acc;
+    }
   }
   s += __shfl_xor_sync(0xffffffffu, s, 1);
   s += __shfl_xor_sync(0xffffffffu, s, 2);
   return s;
 }
 
-// MODE 0 (CG iteration `it`): q = H^T u, p written, p.q partials.
-// MODE 1 (initial residual): r = H^T u, r.r partials.
+// MODE 1 (initial residual): r = H^T u, r.r partials (slot 0).
 // MODE 2: out = H^T u.
 template <typename T, int MODE, int KW>
-__global__ void __launch_bounds__(kFitThreads) k_fit_adjoint(FitDev F, T *__restrict__ out, int it) {
+__global__ void __launch_bounds__(kFitThreads) k_fit_adjoint(FitDev F, T *__restrict__ out) {
   pdl_trigger();
   const int gid = blockIdx.x * blockDim.x + threadIdx.x;
   const int g = gid & 3, act = gid >> 2;
@@ -220,30 +259,65 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_adjoint(FitDev F, T *__rest
   const int loc = act - F.dm_off[k], n = F.dm_n[k];
   const int i = loc % n, jj = loc / n;
   pdl_wait();
-  T beta = T(0);
-  const bool first = it == 0;
-  if (MODE == 0 && !first) beta = T(fit_beta(F, it));
   // idle lanes take part in the shuffles with an empty direction loop
   const T s = on ? fit_gather<T, KW>(F, k, i, jj, g) : fit_gather<T, KW>(F, 0, 0, 0, F.n_dir);
   Acc<T> d, z;
   if (on && g == 0) {
-    T *r = static_cast<T *>(F.r), *p = static_cast<T *>(F.p), *q = static_cast<T *>(F.q);
     if (MODE == 2) {
       out[act] = s;
-    } else if (MODE == 1) {
-      r[act] = s;
-      d.add_prod(s, s);
     } else {
-      const T pn = fit_dir(r, p, act, first, beta);
-      p[act] = pn;
-      q[act] = s;
-      d.add_prod(pn, s);
+      static_cast<T *>(F.r)[act] = s;
+      d.add_prod(s, s);
     }
   }
-  if (MODE != 2) {
+  if (MODE == 1) {
     const double2 v = block_sum2(d, z);
-    const int slot = MODE == 1 ? 0 : kRrSlots + (it & 1);
-    if (threadIdx.x == 0) F.part[slot * F.part_stride + blockIdx.x] = v.x;
+    if (threadIdx.x == 0) F.part[blockIdx.x] = v.x;
+  }
+}
+
+// q = H^T H p for CG iteration `it` (MODE 0): one warp per row of the CSR
+// matrix, the direction p = r + beta p_prev formed on the fly for every column
+// (p = r when it == 0) and written to p[it & 1] by the row's warp; p.q
+// partials (slot kRrSlots + (it & 1)).  MODE 2: out = H^T H x.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kFitThreads) k_fit_spmv(FitDev F, const T *__restrict__ x, T *__restrict__ out,
+                                                         int it) {
+  pdl_trigger();
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const bool on = warp < F.n_act;
+  int beg = 0, end = 0;
+  if (on) {
+    beg = F.nrm_ptr[warp];
+    end = F.nrm_ptr[warp + 1];
+  }
+  pdl_wait();
+  const bool first = it == 0;
+  T beta = T(0);
+  if (MODE == 0 && !first) beta = T(fit_beta(F, it));
+  const T *val = static_cast<const T *>(F.nrm_val);
+  const T *r = static_cast<const T *>(F.r), *pp = static_cast<const T *>(F.p[(it + 1) & 1]);
+  T acc = T(0);
+  for (int e = beg + lane; e < end; e += 32) {
+    const int c = F.nrm_col[e];
+    acc += val[e] * (MODE == 0 ? fit_dir(r, pp, c, first, beta) : x[c]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  Acc<T> d, z;
+  if (on && lane == 0) {
+    if (MODE == 2) {
+      out[warp] = acc;
+    } else {
+      const T pn = fit_dir(r, pp, warp, first, beta);
+      static_cast<T *>(F.p[it & 1])[warp] = pn;
+      static_cast<T *>(F.q)[warp] = acc;
+      d.add_prod(pn, acc);
+    }
+  }
+  if (MODE == 0) {
+    const double2 v = block_sum2(d, z);
+    if (threadIdx.x == 0) F.part[(kRrSlots + (it & 1)) * F.part_stride + blockIdx.x] = v.x;
   }
 }
 
@@ -254,8 +328,10 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_update(FitDev F, T *__restr
   pdl_trigger();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   pdl_wait();
-  const double rr = fit_rr(F, it);
-  const double pq = fit_sum(F.part + (kRrSlots + (it & 1)) * F.part_stride, F.nblk_adj);
+  int n_rr;
+  const double *p_rr = fit_rr_part(F, it, &n_rr);
+  const double2 sums = fit_sum2(p_rr, n_rr, F.part + (kRrSlots + (it & 1)) * F.part_stride, F.nblk_spmv);
+  const double rr = sums.x, pq = sums.y;
   double alpha = 0.0;
   if (pq == 0.0 && rr == 0.0) {
     alpha = 0.0;   // exact iterate: CG stops moving
@@ -267,7 +343,7 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_update(FitDev F, T *__restr
   Acc<T> d, z;
   if (i < F.n_act) {
     const T al = T(alpha);
-    const T *p = static_cast<const T *>(F.p), *q = static_cast<const T *>(F.q);
+    const T *p = static_cast<const T *>(F.p[it & 1]), *q = static_cast<const T *>(F.q);
     T *r = static_cast<T *>(F.r);
     a[i] = (cold && it == 0) ? al * p[i] : fit_fma(al, p[i], a[i]);
     const T rn = fit_fma(-al, q[i], r[i]);
@@ -283,7 +359,7 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_update(FitDev F, T *__restr
 // direction (the quality measure of Sec. 5.1; the Strehl ratio follows on the
 // host).
 template <typename T>
-__global__ void __launch_bounds__(kFitThreads) k_fit_rms(FitDev F, double *__restrict__ rms) {
+__global__ void __launch_bounds__(kFitRmsThreads) k_fit_rms(FitDev F, double *__restrict__ rms) {
   pdl_trigger();
   const int j = blockIdx.x, nn = F.nc * F.nc;
   const T *u = static_cast<const T *>(F.u) + static_cast<size_t>(j) * nn;
@@ -309,7 +385,9 @@ __device__ __forceinline__ T sensor_mirror(const FitDev &F, const T *__restrict_
                                            int b) {
   const T *fx = static_cast<const T *>(F.sfx), *fy = static_cast<const T *>(F.sfy);
   T psi = T(0);
-  for (int k = 0; k < F.n_dm; ++k) {
+#pragma unroll
+  for (int k = 0; k < kMaxDm; ++k) {
+    if (k >= F.n_dm) break;
     const int n = F.dm_n[k], o = tab + k * nc;
     const int x0 = F.sx0[o + a], y0 = F.sy0[o + b];
     const T wx1 = fx[o + a], wy1 = fy[o + b];
@@ -330,34 +408,30 @@ __device__ __forceinline__ T sensor_mirror(const FitDev &F, const T *__restrict_
   return psi;
 }
 
-// Fried slopes of the mirror field on valid subaperture (a, b).
-template <typename T>
-__device__ __forceinline__ T2<T> mirror_slopes_at(const FitDev &F, const T *cmd, int tab, int nc, int a, int b) {
-  const T p00 = sensor_mirror(F, cmd, tab, nc, a, b), p10 = sensor_mirror(F, cmd, tab, nc, a + 1, b);
-  const T p01 = sensor_mirror(F, cmd, tab, nc, a, b + 1), p11 = sensor_mirror(F, cmd, tab, nc, a + 1, b + 1);
-  return {T(0.5) * (p10 + p11 - p00 - p01), T(0.5) * (p01 + p11 - p00 - p10)};
-}
-
-// out = in + scale * A_hat cmd (in = NULL: 0) in the plan's slope layout:
-// Fried slopes of the mirrors on every valid subaperture, or their two means
-// for a tip/tilt-only sensor.  grid.y = sensor.
+// out = in + scale * A_hat cmd (in = NULL: 0) in the plan's slope layout.  A
+// tile item computes the mirrors on the 17 x 17 corners of its 16 x 16
+// subapertures once, then their Fried slopes.  A tip/tilt-only sensor's two
+// mean slopes are sum_c (Gamma^T 1)_c psi_c / S over its pupil-edge corners,
+// the only corners where Gamma^T 1 is nonzero.
 template <typename T>
 __global__ void __launch_bounds__(kFitThreads) k_mirror_slopes(FitDev F, const T *__restrict__ cmd,
                                                               const T *__restrict__ in, T *__restrict__ out,
                                                               T scale) {
+  __shared__ T s_psi[kFwdTile + 1][kFwdTile + 2];
   pdl_trigger();
-  const int m = blockIdx.y;
-  const int4 sd = F.sens[m];
-  const int2 so = F.sens_off[m];
+  const int4 item = F.ms_items[blockIdx.x];
+  const int4 sd = F.sens[item.x], so = F.sens_off[item.x];
+  const int nc = sd.z, n = nc - 1;
   pdl_wait();
-  if (sd.w) {
-    if (blockIdx.x != 0) return;
+  if (item.w) {
+    const T *et = static_cast<const T *>(F.e_t) + 2 * so.z;
+    const int *ei = F.e_idx + so.z;
     Acc<T> ax, ay;
-    for (int j = threadIdx.x; j < sd.y; j += blockDim.x) {
-      const int2 ab = F.sub_ab[so.y + j];
-      const T2<T> g = mirror_slopes_at(F, cmd, so.x, sd.z, ab.x, ab.y);
-      ax.add(g.x);
-      ay.add(g.y);
+    for (int e = threadIdx.x; e < so.w; e += blockDim.x) {
+      const int c = ei[e];
+      const T ps = sensor_mirror(F, cmd, so.x, nc, c % nc, c / nc);
+      ax.add_prod(et[2 * e], ps);
+      ay.add_prod(et[2 * e + 1], ps);
     }
     const double2 v = block_sum2(ax, ay);
     if (threadIdx.x == 0) {
@@ -366,12 +440,22 @@ __global__ void __launch_bounds__(kFitThreads) k_mirror_slopes(FitDev F, const T
     }
     return;
   }
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= sd.y) return;
-  const int2 ab = F.sub_ab[so.y + j];
-  const T2<T> g = mirror_slopes_at(F, cmd, so.x, sd.z, ab.x, ab.y);
-  out[sd.x + j] = (in ? in[sd.x + j] : T(0)) + scale * g.x;
-  out[sd.x + sd.y + j] = (in ? in[sd.x + sd.y + j] : T(0)) + scale * g.y;
+  const int a0 = item.y, b0 = item.z;
+  for (int idx = threadIdx.x; idx < (kFwdTile + 1) * (kFwdTile + 1); idx += blockDim.x) {
+    const int u = idx % (kFwdTile + 1), w = idx / (kFwdTile + 1);
+    const int a = a0 + u, b = b0 + w;
+    s_psi[w][u] = (a < nc && b < nc) ? sensor_mirror(F, cmd, so.x, nc, a, b) : T(0);
+  }
+  __syncthreads();
+  const int u = threadIdx.x % kFwdTile, w = threadIdx.x / kFwdTile;
+  const int a = a0 + u, b = b0 + w;
+  if (a >= n || b >= n) return;
+  const int j = F.sidx[so.y + b * n + a];
+  if (j < 0) return;
+  const T p00 = s_psi[w][u], p10 = s_psi[w][u + 1], p01 = s_psi[w + 1][u], p11 = s_psi[w + 1][u + 1];
+  const T sx = T(0.5) * (p10 + p11 - p00 - p01), sy = T(0.5) * (p01 + p11 - p00 - p10);
+  out[sd.x + j] = (in ? in[sd.x + j] : T(0)) + scale * sx;
+  out[sd.x + sd.y + j] = (in ? in[sd.x + sd.y + j] : T(0)) + scale * sy;
 }
 
 // Algorithm 4.1, step 3 with step 2 folded in: a_t = a_{t-1} + g (R s_ol - a_{t-2}).
@@ -388,37 +472,41 @@ __global__ void __launch_bounds__(kFitThreads) k_polc_update(FitDev F, const T *
 // ------------------------------------------------------------------ launchers
 
 template <typename T>
-cudaError_t fit_mirror(int mode, const FitDev &F, const T *x, const T *phi, int it, cudaStream_t s) {
+cudaError_t fit_mirror(const FitDev &F, const T *x, const T *phi, cudaStream_t s) {
   const dim3 g((F.nc * F.nc + kFitThreads - 1) / kFitThreads, F.n_dir);
-  if (mode == 0) return launch_ex(k_fit_mirror<T, 0>, g, kFitThreads, 0, 0, s, F, x, phi, it);
-  if (mode == 1) return launch_ex(k_fit_mirror<T, 1>, g, kFitThreads, 0, 0, s, F, x, phi, it);
-  return launch_ex(k_fit_mirror<T, 2>, g, kFitThreads, 0, 0, s, F, x, phi, it);
-}
-
-template <typename T, int KW>
-cudaError_t fit_adjoint_kw(int mode, const FitDev &F, T *out, int it, cudaStream_t s) {
-  const dim3 g(F.nblk_adj);
-  if (mode == 0) return launch_ex(k_fit_adjoint<T, 0, KW>, g, kFitThreads, 0, 0, s, F, out, it);
-  if (mode == 1) return launch_ex(k_fit_adjoint<T, 1, KW>, g, kFitThreads, 0, 0, s, F, out, it);
-  return launch_ex(k_fit_adjoint<T, 2, KW>, g, kFitThreads, 0, 0, s, F, out, it);
+  return launch_ex(k_fit_mirror<T>, g, kFitThreads, 0, 0, s, F, x, phi);
 }
 
 template <typename T>
-cudaError_t fit_adjoint(int mode, const FitDev &F, T *out, int it, cudaStream_t s) {
-  if (F.kw <= 2) return fit_adjoint_kw<T, 2>(mode, F, out, it, s);
-  if (F.kw <= 4) return fit_adjoint_kw<T, 4>(mode, F, out, it, s);
-  return fit_adjoint_kw<T, 8>(mode, F, out, it, s);
+cudaError_t fit_spmv(int mode, const FitDev &F, const T *x, T *out, int it, cudaStream_t s) {
+  const dim3 g(F.nblk_spmv);
+  if (mode == 0) return launch_ex(k_fit_spmv<T, 0>, g, kFitThreads, 0, 0, s, F, x, out, it);
+  return launch_ex(k_fit_spmv<T, 2>, g, kFitThreads, 0, 0, s, F, x, out, it);
+}
+
+template <typename T, int KW>
+cudaError_t fit_adjoint_kw(int mode, const FitDev &F, T *out, cudaStream_t s) {
+  const dim3 g(F.nblk_adj);
+  if (mode == 1) return launch_ex(k_fit_adjoint<T, 1, KW>, g, kFitThreads, 0, 0, s, F, out);
+  return launch_ex(k_fit_adjoint<T, 2, KW>, g, kFitThreads, 0, 0, s, F, out);
+}
+
+// mode 1: r = H^T u with the r.r partials; mode 2: out = H^T u.
+template <typename T>
+cudaError_t fit_adjoint(int mode, const FitDev &F, T *out, cudaStream_t s) {
+  if (F.kw <= 2) return fit_adjoint_kw<T, 2>(mode, F, out, s);
+  if (F.kw <= 4) return fit_adjoint_kw<T, 4>(mode, F, out, s);
+  return fit_adjoint_kw<T, 8>(mode, F, out, s);
 }
 
 template <typename T>
 cudaError_t fit_rms(const FitDev &F, double *rms, cudaStream_t s) {
-  return launch_ex(k_fit_rms<T>, dim3(F.n_dir), kFitThreads, 0, 0, s, F, rms);
+  return launch_ex(k_fit_rms<T>, dim3(F.n_dir), kFitRmsThreads, 0, 0, s, F, rms);
 }
 
 template <typename T>
 cudaError_t mirror_slopes(const FitDev &F, const T *cmd, const T *in, T *out, T scale, cudaStream_t s) {
-  const dim3 g((F.max_S + kFitThreads - 1) / kFitThreads, F.n_wfs);
-  return launch_ex(k_mirror_slopes<T>, g, kFitThreads, 0, 0, s, F, cmd, in, out, scale);
+  return launch_ex(k_mirror_slopes<T>, dim3(F.n_ms_items), kFitThreads, 0, 0, s, F, cmd, in, out, scale);
 }
 
 template <typename T>
@@ -500,12 +588,13 @@ struct FitTables {
   std::vector<int2> lay;
   int kw = 0, n_points = 0;
   long long n_active = 0;
-  // A_hat: per sensor, per mirror, the corner taps; the valid subapertures
-  std::vector<int4> sens;
-  std::vector<int2> sens_off, sub_ab;
+  // H^T H in CSR (FP64)
+  std::vector<int> nrm_ptr, nrm_col;
+  std::vector<double> nrm_val;
+  // A_hat: work items, per sensor and mirror the corner taps
+  std::vector<int4> ms_items, sens, sens_off;
   std::vector<int> sx0, sy0;
   std::vector<double> sfx, sfy;
-  int max_S = 0;
 };
 
 // Left tap and fraction of coordinate g: g = i0 + f, 0 <= f < 1.
@@ -617,20 +706,98 @@ tomo_status build_tables(const tomo::HostPlan &H, const tomo_fit_geometry *g, Fi
     }
     for (auto v : hit) T->n_active += v;
   }
+  // H^T H: H as rows (direction, active corner) of (actuator, weight), from the
+  // same taps as the mirror kernel; its columns; then each row of H^T H by
+  // Gustavson's method (a sparse accumulator over the H rows touching it)
+  {
+    std::vector<int> dm_off(g->n_dm + 1, 0);
+    for (int k = 0; k < g->n_dm; ++k) dm_off[k + 1] = dm_off[k] + g->dms[k].n * g->dms[k].n;
+    const int n_act = dm_off[g->n_dm];
+    std::vector<int> h_ptr{0}, h_col;
+    std::vector<double> h_w;
+    for (int j = 0; j < nd; ++j)
+      for (int c = 0; c < nc * nc; ++c) {
+        if (!T->act[c]) continue;
+        const int a = c % nc, b = c / nc;
+        for (int k = 0; k < g->n_dm; ++k) {
+          const int n = g->dms[k].n;
+          const size_t o = (static_cast<size_t>(k) * nd + j) * nc;
+          const double wx[2] = {1.0 - T->hfx[o + a], T->hfx[o + a]};
+          const double wy[2] = {1.0 - T->hfy[o + b], T->hfy[o + b]};
+          for (int dy = 0; dy < 2; ++dy)
+            for (int dx = 0; dx < 2; ++dx) {
+              const int ix = T->hx0[o + a] + dx, iy = T->hy0[o + b] + dy;
+              const double w = wx[dx] * wy[dy];
+              if (ix < 0 || ix >= n || iy < 0 || iy >= n || w == 0.0) continue;
+              h_col.push_back(dm_off[k] + iy * n + ix);
+              h_w.push_back(w);
+            }
+        }
+        h_ptr.push_back(static_cast<int>(h_col.size()));
+      }
+    const int n_rows = static_cast<int>(h_ptr.size()) - 1;
+    std::vector<int> t_ptr(n_act + 1, 0), t_row(h_col.size());
+    std::vector<double> t_w(h_col.size());
+    for (int col : h_col) ++t_ptr[col + 1];
+    for (int i = 0; i < n_act; ++i) t_ptr[i + 1] += t_ptr[i];
+    std::vector<int> fill(t_ptr.begin(), t_ptr.end() - 1);
+    for (int r = 0; r < n_rows; ++r)
+      for (int e = h_ptr[r]; e < h_ptr[r + 1]; ++e) {
+        const int at = fill[h_col[e]]++;
+        t_row[at] = r;
+        t_w[at] = h_w[e];
+      }
+    std::vector<double> acc(n_act, 0.0);
+    std::vector<int> mark(n_act, -1), touched;
+    T->nrm_ptr.assign(1, 0);
+    for (int i = 0; i < n_act; ++i) {
+      touched.clear();
+      for (int e = t_ptr[i]; e < t_ptr[i + 1]; ++e) {
+        const int r = t_row[e];
+        const double wa = t_w[e];
+        for (int f = h_ptr[r]; f < h_ptr[r + 1]; ++f) {
+          const int col = h_col[f];
+          if (mark[col] != i) {
+            mark[col] = i;
+            acc[col] = 0.0;
+            touched.push_back(col);
+          }
+          acc[col] += wa * h_w[f];
+        }
+      }
+      std::sort(touched.begin(), touched.end());
+      for (int col : touched) {
+        T->nrm_col.push_back(col);
+        T->nrm_val.push_back(acc[col]);
+      }
+      if (T->nrm_col.size() > static_cast<size_t>(INT32_MAX)) {
+        *err = "the fitting normal matrix has too many entries";
+        return TOMO_ERR_UNSUPPORTED;
+      }
+      T->nrm_ptr.push_back(static_cast<int>(T->nrm_col.size()));
+    }
+  }
   // the mirrors on the plan's sensors: corner (a, b) of sensor m sees mirror k at
   // ((1 - h_k/H_m) r + theta_m h_k), cone factor 1 for a natural star
   for (int m = 0; m < H.n_wfs; ++m) {
     const tomo::WfsDev &W = H.wfs[m];
     const int n = W.n, ncm = W.nc;
     const double h_gs = H.wfs_height[m];
-    std::vector<int2> subs;
-    for (int b = 0; b < n; ++b)
-      for (int a = 0; a < n; ++a)
-        if (H.sub_idx[W.sub_off + b * n + a] >= 0) subs.push_back({a, b});
-    T->sens.push_back({W.slope_off, static_cast<int>(subs.size()), ncm, W.kind == tomo::kTTOnly ? 1 : 0});
-    T->sens_off.push_back({static_cast<int>(T->sx0.size()), static_cast<int>(T->sub_ab.size())});
-    T->sub_ab.insert(T->sub_ab.end(), subs.begin(), subs.end());
-    T->max_S = std::max(T->max_S, static_cast<int>(subs.size()));
+    const bool tt = W.kind == tomo::kTTOnly;
+    T->sens.push_back({W.slope_off, W.S, ncm, tt ? 1 : 0});
+    T->sens_off.push_back({static_cast<int>(T->sx0.size()), W.sub_off, W.edge_off, W.n_edge});
+    if (tt) {
+      T->ms_items.push_back({m, 0, 0, 1});
+    } else {
+      for (int b0 = 0; b0 < n; b0 += tomo::kFwdTile)
+        for (int a0 = 0; a0 < n; a0 += tomo::kFwdTile) {
+          bool any = false;
+          for (int b = b0; b < std::min(n, b0 + tomo::kFwdTile) && !any; ++b)
+            for (int a = a0; a < std::min(n, a0 + tomo::kFwdTile) && !any; ++a)
+              any = H.sub_idx[W.sub_off + b * n + a] >= 0;
+          if (any) T->ms_items.push_back({m, a0, b0, 0});
+        }
+    }
     for (int k = 0; k < g->n_dm; ++k) {
       const tomo_dm &dm = g->dms[k];
       const double cone = std::isfinite(h_gs) ? 1.0 - dm.altitude / h_gs : 1.0;
@@ -685,14 +852,13 @@ tomo_status enqueue_fit(tomo_fit *f, const void *layers, void *a, int iters, int
   T *av = static_cast<T *>(a);
   int k = 0;
   if (!warm && iters == 0) FIT_CUDA(cudaMemsetAsync(a, 0, F.n_act * sizeof(T), s), "zero start");
-  FIT_CUDA(tomo::fit_mirror<T>(1, F, warm ? av : nullptr, static_cast<const T *>(layers), 0, s), "fit residual");
-  FIT_CUDA(tomo::fit_adjoint<T>(1, F, nullptr, 0, s), "fit residual gather");
+  FIT_CUDA(tomo::fit_mirror<T>(F, warm ? av : nullptr, static_cast<const T *>(layers), s), "fit residual");
+  FIT_CUDA(tomo::fit_adjoint<T>(1, F, nullptr, s), "fit residual gather");
   k += 2;
   for (int it = 0; it < iters; ++it) {
-    FIT_CUDA(tomo::fit_mirror<T>(0, F, nullptr, nullptr, it, s), "fit mirror");
-    FIT_CUDA(tomo::fit_adjoint<T>(0, F, nullptr, it, s), "fit gather");
+    FIT_CUDA(tomo::fit_spmv<T>(0, F, nullptr, nullptr, it, s), "fit normal operator");
     FIT_CUDA(tomo::fit_update<T>(F, av, it, warm ? 0 : 1, s), "fit update");
-    k += 3;
+    k += 2;
   }
   tomo::count_launches(k);
   *nk = k;
@@ -849,11 +1015,11 @@ tomo_status tomo_fit_create(tomo_plan *p, const tomo_fit_geometry *g, tomo_fit *
   F.n_act = static_cast<int>(n_act);
   F.kw = T.kw;
   F.n_points = T.n_points;
-  F.n_wfs = H.n_wfs;
-  F.max_S = std::max(1, T.max_S);
+  F.n_ms_items = static_cast<int>(T.ms_items.size());
   F.nblk_adj = static_cast<int>((4 * n_act + tomo::kFitThreads - 1) / tomo::kFitThreads);
   F.nblk_upd = static_cast<int>((n_act + tomo::kFitThreads - 1) / tomo::kFitThreads);
-  F.part_stride = std::max(F.nblk_adj, F.nblk_upd);
+  F.nblk_spmv = static_cast<int>((32 * n_act + tomo::kFitThreads - 1) / tomo::kFitThreads);
+  F.part_stride = std::max(F.nblk_adj, std::max(F.nblk_upd, F.nblk_spmv));
   int off = 0, woff = 0;
   for (int k = 0; k < g->n_dm; ++k) {
     F.dm_n[k] = g->dms[k].n;
@@ -867,7 +1033,8 @@ tomo_status tomo_fit_create(tomo_plan *p, const tomo_fit_geometry *g, tomo_fit *
   const size_t es = f->esz;
   struct Item { size_t *off; size_t bytes; };
   size_t o_act, o_lay, o_hx0, o_hy0, o_hfx, o_hfy, o_px0, o_py0, o_pfx, o_pfy, o_wx0, o_wy0, o_wxw, o_wyw,
-      o_sens, o_soff, o_sub, o_sx0, o_sy0, o_sfx, o_sfy, o_u, o_r, o_p, o_q, o_phi, o_sol, o_part, o_flag;
+      o_msi, o_sens, o_soff, o_sidx, o_eidx, o_et, o_sx0, o_sy0, o_sfx, o_sfy, o_nptr, o_ncol, o_nval, o_u, o_r,
+      o_p0, o_p1, o_q, o_phi, o_sol, o_part, o_flag;
   const Item items[] = {
       {&o_act, T.act.size()},
       {&o_lay, T.lay.size() * sizeof(int2)},
@@ -883,16 +1050,23 @@ tomo_status tomo_fit_create(tomo_plan *p, const tomo_fit_geometry *g, tomo_fit *
       {&o_wy0, T.wy0.size() * sizeof(int)},
       {&o_wxw, T.wxw.size() * es},
       {&o_wyw, T.wyw.size() * es},
+      {&o_msi, T.ms_items.size() * sizeof(int4)},
       {&o_sens, T.sens.size() * sizeof(int4)},
-      {&o_soff, T.sens_off.size() * sizeof(int2)},
-      {&o_sub, T.sub_ab.size() * sizeof(int2)},
+      {&o_soff, T.sens_off.size() * sizeof(int4)},
+      {&o_sidx, H.sub_idx.size() * sizeof(int)},
+      {&o_eidx, H.edge_idx.size() * sizeof(int)},
+      {&o_et, H.edge_t.size() * es},
       {&o_sx0, T.sx0.size() * sizeof(int)},
       {&o_sy0, T.sy0.size() * sizeof(int)},
       {&o_sfx, T.sfx.size() * es},
       {&o_sfy, T.sfy.size() * es},
+      {&o_nptr, T.nrm_ptr.size() * sizeof(int)},
+      {&o_ncol, T.nrm_col.size() * sizeof(int)},
+      {&o_nval, T.nrm_val.size() * es},
       {&o_u, static_cast<size_t>(nd) * nc * nc * es},
       {&o_r, n_act * es},
-      {&o_p, n_act * es},
+      {&o_p0, n_act * es},
+      {&o_p1, n_act * es},
       {&o_q, n_act * es},
       {&o_phi, static_cast<size_t>(H.n) * es},
       {&o_sol, static_cast<size_t>(H.n_slopes) * es},
@@ -914,14 +1088,18 @@ tomo_status tomo_fit_create(tomo_plan *p, const tomo_fit_geometry *g, tomo_fit *
   std::memcpy(img.data() + o_py0, T.py0.data(), T.py0.size() * sizeof(int));
   std::memcpy(img.data() + o_wx0, T.wx0.data(), T.wx0.size() * sizeof(int));
   std::memcpy(img.data() + o_wy0, T.wy0.data(), T.wy0.size() * sizeof(int));
+  std::memcpy(img.data() + o_nptr, T.nrm_ptr.data(), T.nrm_ptr.size() * sizeof(int));
+  std::memcpy(img.data() + o_ncol, T.nrm_col.data(), T.nrm_col.size() * sizeof(int));
+  std::memcpy(img.data() + o_msi, T.ms_items.data(), T.ms_items.size() * sizeof(int4));
   std::memcpy(img.data() + o_sens, T.sens.data(), T.sens.size() * sizeof(int4));
-  std::memcpy(img.data() + o_soff, T.sens_off.data(), T.sens_off.size() * sizeof(int2));
-  std::memcpy(img.data() + o_sub, T.sub_ab.data(), T.sub_ab.size() * sizeof(int2));
+  std::memcpy(img.data() + o_soff, T.sens_off.data(), T.sens_off.size() * sizeof(int4));
+  std::memcpy(img.data() + o_sidx, H.sub_idx.data(), H.sub_idx.size() * sizeof(int));
+  std::memcpy(img.data() + o_eidx, H.edge_idx.data(), H.edge_idx.size() * sizeof(int));
   std::memcpy(img.data() + o_sx0, T.sx0.data(), T.sx0.size() * sizeof(int));
   std::memcpy(img.data() + o_sy0, T.sy0.data(), T.sy0.size() * sizeof(int));
   const std::pair<size_t, const std::vector<double> *> reals[] = {
       {o_hfx, &T.hfx}, {o_hfy, &T.hfy}, {o_pfx, &T.pfx}, {o_pfy, &T.pfy}, {o_wxw, &T.wxw}, {o_wyw, &T.wyw},
-      {o_sfx, &T.sfx}, {o_sfy, &T.sfy}};
+      {o_sfx, &T.sfx}, {o_sfy, &T.sfy}, {o_et, &H.edge_t}, {o_nval, &T.nrm_val}};
   for (const auto &rv : reals) {
     if (f->precision) put<double>(img, rv.first, *rv.second);
     else put<float>(img, rv.first, *rv.second);
@@ -955,9 +1133,12 @@ tomo_status tomo_fit_create(tomo_plan *p, const tomo_fit_geometry *g, tomo_fit *
   F.wy0 = reinterpret_cast<const int *>(base + o_wy0);
   F.wxw = base + o_wxw;
   F.wyw = base + o_wyw;
+  F.ms_items = reinterpret_cast<const int4 *>(base + o_msi);
   F.sens = reinterpret_cast<const int4 *>(base + o_sens);
-  F.sens_off = reinterpret_cast<const int2 *>(base + o_soff);
-  F.sub_ab = reinterpret_cast<const int2 *>(base + o_sub);
+  F.sens_off = reinterpret_cast<const int4 *>(base + o_soff);
+  F.sidx = reinterpret_cast<const int *>(base + o_sidx);
+  F.e_idx = reinterpret_cast<const int *>(base + o_eidx);
+  F.e_t = base + o_et;
   F.sx0 = reinterpret_cast<const int *>(base + o_sx0);
   F.sy0 = reinterpret_cast<const int *>(base + o_sy0);
   F.sfx = base + o_sfx;
@@ -965,7 +1146,11 @@ tomo_status tomo_fit_create(tomo_plan *p, const tomo_fit_geometry *g, tomo_fit *
   F.s_ol = base + o_sol;
   F.u = base + o_u;
   F.r = base + o_r;
-  F.p = base + o_p;
+  F.p[0] = base + o_p0;
+  F.p[1] = base + o_p1;
+  F.nrm_ptr = reinterpret_cast<const int *>(base + o_nptr);
+  F.nrm_col = reinterpret_cast<const int *>(base + o_ncol);
+  F.nrm_val = base + o_nval;
   F.q = base + o_q;
   f->phi = base + o_phi;
   F.part = reinterpret_cast<double *>(base + o_part);
@@ -981,7 +1166,7 @@ tomo_status tomo_fit_get_info(const tomo_fit *f, tomo_fit_info *out) {
   out->n_points = f->n_points;
   out->n_dir = f->F.n_dir;
   out->n_dm = f->F.n_dm;
-  out->kernels_per_iteration = 3;
+  out->kernels_per_iteration = 2;
   out->kernels_per_solve_base = 2;
   out->device_bytes = static_cast<long long>(f->arena_bytes);
   return TOMO_OK;
@@ -991,14 +1176,13 @@ tomo_status tomo_fit_apply_normal(tomo_fit *f, const void *d_a, void *d_out, voi
   if (!f || !d_a || !d_out) return fit_fail(TOMO_ERR_ARG, "NULL argument");
   tomo::DeviceGuard dg(f->device);
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-  if (f->precision == 0) {
-    FIT_CUDA(tomo::fit_mirror<float>(2, f->F, static_cast<const float *>(d_a), nullptr, 0, s), "fit mirror");
-    FIT_CUDA(tomo::fit_adjoint<float>(2, f->F, static_cast<float *>(d_out), 0, s), "fit gather");
-  } else {
-    FIT_CUDA(tomo::fit_mirror<double>(2, f->F, static_cast<const double *>(d_a), nullptr, 0, s), "fit mirror");
-    FIT_CUDA(tomo::fit_adjoint<double>(2, f->F, static_cast<double *>(d_out), 0, s), "fit gather");
-  }
-  tomo::count_launches(2);
+  if (f->precision == 0)
+    FIT_CUDA(tomo::fit_spmv<float>(2, f->F, static_cast<const float *>(d_a), static_cast<float *>(d_out), 0, s),
+             "fit normal operator");
+  else
+    FIT_CUDA(tomo::fit_spmv<double>(2, f->F, static_cast<const double *>(d_a), static_cast<double *>(d_out), 0, s),
+             "fit normal operator");
+  tomo::count_launches(1);
   return TOMO_OK;
 }
 
@@ -1007,12 +1191,11 @@ tomo_status tomo_fit_rhs(tomo_fit *f, const void *d_layers, void *d_out, void *c
   tomo::DeviceGuard dg(f->device);
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   if (f->precision == 0) {
-    FIT_CUDA(tomo::fit_mirror<float>(1, f->F, nullptr, static_cast<const float *>(d_layers), 0, s), "fit project");
-    FIT_CUDA(tomo::fit_adjoint<float>(2, f->F, static_cast<float *>(d_out), 0, s), "fit gather");
+    FIT_CUDA(tomo::fit_mirror<float>(f->F, nullptr, static_cast<const float *>(d_layers), s), "fit project");
+    FIT_CUDA(tomo::fit_adjoint<float>(2, f->F, static_cast<float *>(d_out), s), "fit gather");
   } else {
-    FIT_CUDA(tomo::fit_mirror<double>(1, f->F, nullptr, static_cast<const double *>(d_layers), 0, s),
-             "fit project");
-    FIT_CUDA(tomo::fit_adjoint<double>(2, f->F, static_cast<double *>(d_out), 0, s), "fit gather");
+    FIT_CUDA(tomo::fit_mirror<double>(f->F, nullptr, static_cast<const double *>(d_layers), s), "fit project");
+    FIT_CUDA(tomo::fit_adjoint<double>(2, f->F, static_cast<double *>(d_out), s), "fit gather");
   }
   tomo::count_launches(2);
   return TOMO_OK;
@@ -1024,12 +1207,12 @@ tomo_status tomo_fit_residual_rms(tomo_fit *f, const void *d_layers, const void 
   tomo::DeviceGuard dg(f->device);
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   if (f->precision == 0) {
-    FIT_CUDA(tomo::fit_mirror<float>(1, f->F, static_cast<const float *>(d_a), static_cast<const float *>(d_layers),
-                                     0, s), "fit residual");
+    FIT_CUDA(tomo::fit_mirror<float>(f->F, static_cast<const float *>(d_a), static_cast<const float *>(d_layers), s),
+             "fit residual");
     FIT_CUDA(tomo::fit_rms<float>(f->F, d_rms, s), "fit residual rms");
   } else {
-    FIT_CUDA(tomo::fit_mirror<double>(1, f->F, static_cast<const double *>(d_a),
-                                      static_cast<const double *>(d_layers), 0, s), "fit residual");
+    FIT_CUDA(tomo::fit_mirror<double>(f->F, static_cast<const double *>(d_a), static_cast<const double *>(d_layers),
+                                      s), "fit residual");
     FIT_CUDA(tomo::fit_rms<double>(f->F, d_rms, s), "fit residual rms");
   }
   tomo::count_launches(2);
