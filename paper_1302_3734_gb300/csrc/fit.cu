@@ -53,6 +53,7 @@ constexpr int kMaxDm = 4;
 constexpr int kMaxFitDirs = 256;
 constexpr int kRrSlots = 4;   // r.r partial slots (ring over iterations), then 2 p.q slots
 constexpr int kFitDirBatch = 4;   // directions whose gather loads one thread issues together
+constexpr int kSpmvBatch = 4;     // matrix entries whose loads one lane of k_fit_spmv issues together
 
 // Everything the fitting kernels read (passed by value).
 struct FitDev {
@@ -297,10 +298,16 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_spmv(FitDev F, const T *__r
   if (MODE == 0 && !first) beta = T(fit_beta(F, it));
   const T *val = static_cast<const T *>(F.nrm_val);
   const T *r = static_cast<const T *>(F.r), *pp = static_cast<const T *>(F.p[(it + 1) & 1]);
+  // kSpmvBatch entries per lane at a time: their columns, then their values and
+  // vector elements, are loaded without dependences between them
   T acc = T(0);
-  for (int e = beg + lane; e < end; e += 32) {
-    const int c = F.nrm_col[e];
-    acc += val[e] * (MODE == 0 ? fit_dir(r, pp, c, first, beta) : x[c]);
+  for (int e0 = beg + lane; e0 < end; e0 += 32 * kSpmvBatch) {
+    int c[kSpmvBatch];
+#pragma unroll
+    for (int b = 0; b < kSpmvBatch; ++b) c[b] = e0 + 32 * b < end ? F.nrm_col[e0 + 32 * b] : -1;
+#pragma unroll
+    for (int b = 0; b < kSpmvBatch; ++b)
+      if (c[b] >= 0) acc += val[e0 + 32 * b] * (MODE == 0 ? fit_dir(r, pp, c[b], first, beta) : x[c[b]]);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
