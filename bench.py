@@ -43,8 +43,8 @@ METRIC = "tomography solves/s and p99 frame latency at 84x84 MCAO vs plain GPU P
 # DRAM bytes (read + write) per launch of each PCG kernel on this workload, from one ncu capture
 # with flushed caches, valid only for the kernel source file they were taken from.
 NCU_TRAFFIC = {
-    "kernels_cu_sha256": "2772239d08ea4d0be8796178826e0bb2c9396ed493531b9f2fba940e200ea6c6",
-    "bytes": {"analysis": 7466240, "synthesis": 659968, "forward": 752256, "update": 2982144},
+    "kernels_cu_sha256": "e041a19d3ba3fee84a0bb4a49117351dc34fbd2dab7b214ae89f33d8b3c1e1ef",
+    "bytes": {"analysis": 7456000, "synthesis": 663040, "forward": 755200, "update": 2983680},
 }
 
 
