@@ -363,9 +363,9 @@ typedef struct {
   long long tag;               /* the caller's tag from tomo_server_submit */
   double t_submit;             /* tomo_server_submit copied the frame in */
   double t_launch;             /* the launch holding the frame was enqueued */
-  double t_done;               /* its coefficients were in host memory */
+  double t_done;               /* its result was in host memory */
   int batch_size;              /* frames in that launch */
-  int result_slot;             /* where tomo_server_result finds the coefficients */
+  int result_slot;             /* where tomo_server_result finds the result */
 } tomo_frame_result;
 
 typedef struct {
@@ -396,6 +396,21 @@ tomo_status tomo_server_admit(tomo_server *s, const tomo_geometry *g, int *teles
 tomo_status tomo_server_admit_ex(tomo_server *s, const tomo_geometry *g, const tomo_plan_options *opt,
                                  int *telescope);
 
+/* Admit a telescope that the server runs in closed loop (Sec. 4.2, Algorithm
+ * 4.1, two-frame delay): each submitted frame holds the residual slopes that
+ * were measured while the commands returned two frames earlier were applied
+ * (zero for the first two frames); the server runs one tomo_polc_step with
+ * `gain` and `fit_iters` fitting iterations (its `iters` for the tomography),
+ * and the frame's result is the commands a_t (the fit's command layout: n_act
+ * elements of the plan's type).  The tomography coefficients and the
+ * reconstructed commands are warm-started from the telescope's previous frame.
+ * fit == NULL admits an open-loop telescope (tomo_server_admit_ex).  Frames of
+ * closed-loop telescopes are not batched with others: each is its own control
+ * step on the launch's stream.  Under the latest-frame policy a superseded
+ * frame is also skipped by the integrator. */
+tomo_status tomo_server_admit_loop(tomo_server *s, const tomo_geometry *g, const tomo_plan_options *opt,
+                                   const tomo_fit_geometry *fit, double gain, int fit_iters, int *telescope);
+
 /* Frame policy: 0 (default) solves every frame of a telescope in order; 1 solves
  * only the newest waiting frame when a launch is formed and reports the older
  * waiting ones as TOMO_ERR_SUPERSEDED (the real-time choice when the stream
@@ -414,8 +429,9 @@ tomo_status tomo_server_submit(tomo_server *s, int telescope, const void *host_s
 /* Up to `max` finished frames (oldest first) into out; returns how many. */
 int tomo_server_poll(tomo_server *s, tomo_frame_result *out, int max);
 
-/* Copy the coefficients (n_coeffs elements) of a finished frame into
- * host_out.  TOMO_ERR_ARG if that slot already holds a later frame. */
+/* Copy the result of a finished frame into host_out: the coefficients
+ * (n_coeffs elements), or for a closed-loop telescope the commands a_t (n_act
+ * elements of its fit).  TOMO_ERR_ARG if that slot already holds a later frame. */
 tomo_status tomo_server_result(tomo_server *s, int telescope, int result_slot, long long tag,
                                void *host_out);
 
@@ -428,6 +444,9 @@ tomo_status tomo_server_get_stats(tomo_server *s, tomo_server_stats *out);
 /* The plan of an admitted telescope (owned by the server; for
  * tomo_plan_get_info and the operator calls, not for solves). */
 tomo_status tomo_server_get_plan(tomo_server *s, int telescope, const tomo_plan **out);
+
+/* The fit of a closed-loop telescope (NULL for an open-loop one), owned by the server. */
+tomo_status tomo_server_get_fit(tomo_server *s, int telescope, const tomo_fit **out);
 
 /* The steady clock of the frame timestamps (seconds). */
 double tomo_server_clock(void);

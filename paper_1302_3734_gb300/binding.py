@@ -134,6 +134,9 @@ SIGNATURES = [
     ("tomo_server_drain", _I, [_VP, ctypes.c_double]),
     ("tomo_server_get_stats", _I, [_VP, ctypes.POINTER(ServerStats)]),
     ("tomo_server_get_plan", _I, [_VP, _I, ctypes.POINTER(_VP)]),
+    ("tomo_server_admit_loop", _I, [_VP, ctypes.POINTER(Geometry), ctypes.POINTER(PlanOptions),
+                                    ctypes.POINTER(FitGeometry), ctypes.c_double, _I, ctypes.POINTER(_I)]),
+    ("tomo_server_get_fit", _I, [_VP, _I, ctypes.POINTER(_VP)]),
     ("tomo_server_clock", ctypes.c_double, []),
     ("tomo_server_destroy", None, [_VP]),
     ("tomo_fit_create", _I, [_VP, ctypes.POINTER(FitGeometry), ctypes.POINTER(_VP)]),
@@ -448,6 +451,7 @@ class Server:
                                       int(queue_depth), int(result_slots), ctypes.byref(h)))
         self._h = h
         self._info = {}
+        self._n_out = {}
         self._buf = (FrameResult * 4096)()
 
     def admit(self, geom, cluster_size=0):
@@ -467,6 +471,30 @@ class Server:
         self._info[tid.value] = inf
         return tid.value
 
+    def admit_loop(self, geom, gain=0.4, fit_iters=4, cluster_size=0):
+        """Admit a telescope run in closed loop (pseudo-open-loop control with the mirrors of
+        geom["fitting"]): its frames are residual slopes, its results mirror commands."""
+        lib = load_library()
+        g, keep = geometry_struct(geom)
+        fg, keep_f = fit_geometry_struct(geom["fitting"])
+        tid = ctypes.c_int(-1)
+        opt = PlanOptions()
+        opt.cluster_size = int(cluster_size)
+        _check(lib.tomo_server_admit_loop(self._h, ctypes.byref(g), ctypes.byref(opt), ctypes.byref(fg),
+                                          float(gain), int(fit_iters), ctypes.byref(tid)))
+        del keep, keep_f
+        plan = ctypes.c_void_p()
+        _check(lib.tomo_server_get_plan(self._h, tid.value, ctypes.byref(plan)))
+        inf = PlanInfo()
+        _check(lib.tomo_plan_get_info(plan, ctypes.byref(inf)))
+        fit = ctypes.c_void_p()
+        _check(lib.tomo_server_get_fit(self._h, tid.value, ctypes.byref(fit)))
+        fi = FitInfo()
+        _check(lib.tomo_fit_get_info(fit, ctypes.byref(fi)))
+        self._info[tid.value] = inf
+        self._n_out[tid.value] = int(fi.n_act)
+        return tid.value
+
     def info(self, telescope):
         return self._info[telescope]
 
@@ -478,6 +506,7 @@ class Server:
     def release(self, telescope):
         _check(load_library().tomo_server_release(self._h, int(telescope)))
         self._info.pop(telescope, None)
+        self._n_out.pop(telescope, None)
 
     def submit(self, telescope, slopes, tag):
         """slopes: C-contiguous host array (float32, or float64 for precision-1 plans) of
@@ -507,9 +536,11 @@ class Server:
                 return out
 
     def result(self, telescope, result_slot, tag):
-        """Coefficients of a finished frame (numpy array), or None if the slot moved on."""
+        """The result of a finished frame (numpy array): coefficients, or the mirror commands of
+        a closed-loop telescope; None if the slot moved on."""
         inf = self._info[telescope]
-        out = np.empty(int(inf.n_coeffs), dtype=np.float64 if inf.precision else np.float32)
+        n = self._n_out.get(telescope, int(inf.n_coeffs))
+        out = np.empty(n, dtype=np.float64 if inf.precision else np.float32)
         st = load_library().tomo_server_result(self._h, int(telescope), int(result_slot), int(tag),
                                                 ctypes.c_void_p(out.ctypes.data))
         return out if st == 0 else None

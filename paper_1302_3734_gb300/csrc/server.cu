@@ -10,6 +10,7 @@
 // worker paused) never changes the batch or a telescope under a launch.
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <list>
@@ -54,6 +55,15 @@ struct Telescope {
   int next_out = 0;
   bool busy = false;                          // a frame of this telescope is in flight
   size_t bytes = 0;                           // device bytes (plan + slot)
+  // closed loop (Algorithm 4.1): the fit, the gain, two alternating command
+  // buffers (a_t overwrites a_{t-2}), the reconstructed commands R s_ol and
+  // the number of frames processed so far
+  tomo_fit *fit = nullptr;
+  double gain = 0.0;
+  int fit_iters = 0;
+  void *d_a[2] = {nullptr, nullptr}, *d_rec = nullptr;
+  long long steps = 0;
+  size_t n_out = 0;                           // elements of a result: coefficients, or commands
 };
 
 struct Launch {
@@ -136,25 +146,42 @@ tomo_status enqueue_launch(tomo_server *S, const Launch &L) {
   cudaStream_t st = S->streams[j];
   cudaError_t e = cudaSuccess;
   std::memset(S->h_mask[j], 0, sizeof(int) * S->mask_len);
+  bool open = false;
   for (const auto &f : L.frames) {
     const Telescope *t = S->tels.at(f.tel);
-    S->h_mask[j][S->mask_index.at(f.tel)] = 1;
+    if (!t->fit) {
+      S->h_mask[j][S->mask_index.at(f.tel)] = 1;
+      open = true;
+    }
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(t->d_slopes, t->h_in + f.in_slot * t->ns * t->esz, t->ns * t->esz,
                           cudaMemcpyHostToDevice, st);
   }
-  if (e == cudaSuccess)
+  if (e == cudaSuccess && open)
     e = cudaMemcpyAsync(S->d_mask[j], S->h_mask[j], sizeof(int) * S->mask_len, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return set_error(TOMO_ERR_CUDA, std::string("server copies: ") + cudaGetErrorString(e));
-  std::vector<const int *> active(S->group_off.size());
-  for (size_t g = 0; g < active.size(); ++g) active[g] = S->d_mask[j] + S->group_off[g];
-  const tomo_status ts = tomo::batch_solve(S->batch, S->pos_slopes.data(), S->pos_x.data(), active.data(),
-                                           S->iters, 1, st);
-  if (ts != TOMO_OK) return ts;
+  if (open) {
+    // the open-loop telescopes with a frame: one masked batched solve
+    std::vector<const int *> active(S->group_off.size());
+    for (size_t g = 0; g < active.size(); ++g) active[g] = S->d_mask[j] + S->group_off[g];
+    const tomo_status ts = tomo::batch_solve(S->batch, S->pos_slopes.data(), S->pos_x.data(), active.data(),
+                                             S->iters, 1, st);
+    if (ts != TOMO_OK) return ts;
+  }
   for (const auto &f : L.frames) {
-    const Telescope *t = S->tels.at(f.tel);
+    Telescope *t = S->tels.at(f.tel);
+    const void *res = t->d_x;
+    if (t->fit) {
+      // closed loop: one control step, a_t into the buffer of a_{t-2}
+      void *a_t = t->d_a[t->steps & 1];
+      const tomo_status ts = tomo_polc_step(t->fit, t->d_slopes, t->d_x, t->d_rec, a_t, t->d_a[(t->steps + 1) & 1],
+                                            a_t, t->gain, S->iters, t->fit_iters, 1, st);
+      if (ts != TOMO_OK) return ts;
+      ++t->steps;
+      res = a_t;
+    }
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(t->h_out + f.out_slot * t->n * t->esz, t->d_x, t->n * t->esz,
+      e = cudaMemcpyAsync(t->h_out + f.out_slot * t->n_out * t->esz, res, t->n_out * t->esz,
                           cudaMemcpyDeviceToHost, st);
   }
   if (e == cudaSuccess) e = cudaEventRecord(S->events[j], st);
@@ -278,13 +305,16 @@ void resume(tomo_server *S) {
 tomo_status rebuild(tomo_server *S, const std::map<int, Telescope *> &tels) {
   tomo::Batch *nb = nullptr;
   std::vector<tomo_plan *> plans;
-  for (const auto &kv : tels) plans.push_back(kv.second->plan);
+  std::map<int, Telescope *> open;   // the batch holds the open-loop telescopes
+  for (const auto &kv : tels)
+    if (!kv.second->fit) open[kv.first] = kv.second;
+  for (const auto &kv : open) plans.push_back(kv.second->plan);
   if (!plans.empty()) {
     const tomo_status st = tomo::build_batch(plans.data(), static_cast<int>(plans.size()), &nb);
     if (st != TOMO_OK) return st;
   }
   std::vector<int> ids;
-  for (const auto &kv : tels) ids.push_back(kv.first);
+  for (const auto &kv : open) ids.push_back(kv.first);
   std::map<int, int> mask_index;
   std::vector<int> group_off;
   int len = 0;
@@ -325,7 +355,7 @@ tomo_status rebuild(tomo_server *S, const std::map<int, Telescope *> &tels) {
   S->mask_len = len;
   S->pos_slopes.clear();
   S->pos_x.clear();
-  for (const auto &kv : tels) {
+  for (const auto &kv : open) {
     S->pos_slopes.push_back(kv.second->d_slopes);
     S->pos_x.push_back(kv.second->d_x);
   }
@@ -334,6 +364,10 @@ tomo_status rebuild(tomo_server *S, const std::map<int, Telescope *> &tels) {
 
 void free_telescope(Telescope *t) {
   if (!t) return;
+  if (t->fit) tomo_fit_destroy(t->fit);
+  cudaFree(t->d_a[0]);
+  cudaFree(t->d_a[1]);
+  cudaFree(t->d_rec);
   cudaFree(t->d_slopes);
   cudaFree(t->d_x);
   cudaFreeHost(t->h_in);
@@ -396,7 +430,14 @@ tomo_status tomo_server_set_policy(tomo_server *S, int latest_only) {
 
 tomo_status tomo_server_admit_ex(tomo_server *S, const tomo_geometry *g, const tomo_plan_options *opt,
                                  int *telescope) {
+  return tomo_server_admit_loop(S, g, opt, nullptr, 0.0, 0, telescope);
+}
+
+tomo_status tomo_server_admit_loop(tomo_server *S, const tomo_geometry *g, const tomo_plan_options *opt,
+                                   const tomo_fit_geometry *fit, double gain, int fit_iters, int *telescope) {
   if (!S || !g || !telescope) return set_error(TOMO_ERR_ARG, "server, geometry and telescope must not be NULL");
+  if (fit && (!std::isfinite(gain) || fit_iters < 0 || fit_iters > 100000))
+    return set_error(TOMO_ERR_ARG, "gain must be finite and fit_iters in 0..100000");
   std::lock_guard<std::mutex> admin(S->admin_mu);
   cudaSetDevice(S->device);
   Telescope *t = new Telescope();
@@ -410,7 +451,22 @@ tomo_status tomo_server_admit_ex(tomo_server *S, const tomo_geometry *g, const t
   t->n = static_cast<size_t>(info.n_coeffs);
   t->ns = static_cast<size_t>(info.n_slopes);
   t->esz = info.precision ? 8 : 4;
+  t->n_out = t->n;
   t->bytes = tomo_plan_device_bytes(t->plan) + (t->n + t->ns) * t->esz;
+  if (fit) {
+    st = tomo_fit_create(t->plan, fit, &t->fit);
+    if (st != TOMO_OK) {
+      tomo_destroy(t->plan);
+      delete t;
+      return st;
+    }
+    tomo_fit_info fi{};
+    tomo_fit_get_info(t->fit, &fi);
+    t->gain = gain;
+    t->fit_iters = fit_iters;
+    t->n_out = static_cast<size_t>(fi.n_act);
+    t->bytes += static_cast<size_t>(fi.device_bytes) + 3 * t->n_out * t->esz;
+  }
   {
     std::lock_guard<std::mutex> lk(S->mu);
     if (S->budget && used_bytes(S) + t->bytes > S->budget) {
@@ -425,8 +481,13 @@ tomo_status tomo_server_admit_ex(tomo_server *S, const tomo_geometry *g, const t
   cudaError_t e = cudaMalloc(&t->d_slopes, t->ns * t->esz);
   if (e == cudaSuccess) e = cudaMalloc(&t->d_x, t->n * t->esz);
   if (e == cudaSuccess) e = cudaMemsetAsync(t->d_x, 0, t->n * t->esz, S->admin_stream);
+  for (void **buf : {&t->d_a[0], &t->d_a[1], &t->d_rec}) {
+    if (!t->fit || e != cudaSuccess) break;
+    e = cudaMalloc(buf, t->n_out * t->esz);
+    if (e == cudaSuccess) e = cudaMemsetAsync(*buf, 0, t->n_out * t->esz, S->admin_stream);
+  }
   if (e == cudaSuccess) e = cudaHostAlloc(&t->h_in, t->ns * t->esz * S->queue_depth, cudaHostAllocDefault);
-  if (e == cudaSuccess) e = cudaHostAlloc(&t->h_out, t->n * t->esz * S->result_slots, cudaHostAllocDefault);
+  if (e == cudaSuccess) e = cudaHostAlloc(&t->h_out, t->n_out * t->esz * S->result_slots, cudaHostAllocDefault);
   if (e == cudaSuccess) e = cudaStreamSynchronize(S->admin_stream);
   if (e != cudaSuccess) {
     free_telescope(t);
@@ -522,7 +583,7 @@ tomo_status tomo_server_result(tomo_server *S, int telescope, int result_slot, l
   if (result_slot < 0 || result_slot >= S->result_slots) return set_error(TOMO_ERR_ARG, "result slot out of range");
   if (t->out_writing[result_slot] || t->out_tag[result_slot] != tag)
     return set_error(TOMO_ERR_ARG, "the result slot no longer holds that frame");
-  std::memcpy(host_out, t->h_out + result_slot * t->n * t->esz, t->n * t->esz);
+  std::memcpy(host_out, t->h_out + result_slot * t->n_out * t->esz, t->n_out * t->esz);
   return TOMO_OK;
 }
 
@@ -546,6 +607,15 @@ tomo_status tomo_server_get_stats(tomo_server *S, tomo_server_stats *out) {
   out->budget_bytes = static_cast<long long>(S->budget);
   out->telescopes = static_cast<int>(S->tels.size());
   out->in_flight = static_cast<int>(S->inflight.size());
+  return TOMO_OK;
+}
+
+tomo_status tomo_server_get_fit(tomo_server *S, int telescope, const tomo_fit **out) {
+  if (!S || !out) return set_error(TOMO_ERR_ARG, "server and out must not be NULL");
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->tels.find(telescope);
+  if (it == S->tels.end()) return set_error(TOMO_ERR_ARG, "no such telescope");
+  *out = it->second->fit;
   return TOMO_OK;
 }
 

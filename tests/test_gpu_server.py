@@ -206,3 +206,69 @@ def test_every_100th_frame_of_a_served_stream_matches_the_oracle(lib):
             x_ref = ora.pcg(ora.rhs(s), x0, ITERS, ora.jacobi_diagonal())
             e = rel(got[(i, k)].astype(np.float64), x_ref, f"served-stream/{g['name']}/frame{k}")
             assert e < 1e-5, (g["name"], k, e)
+
+
+def test_closed_loop_telescopes_are_their_control_steps_and_match_the_oracle_loop(lib):
+    """Two telescopes served in closed loop (Algorithm 4.1, gain 0.4, two-frame delay) next to
+    an open-loop one.  A CPU plant measures each frozen-flow atmosphere behind the commands
+    the server returned two frames earlier.  The served commands are bitwise the control
+    steps run directly through the Fit API on the same residual slopes, and follow the
+    oracle's own closed loop."""
+    from oracle.control import Control
+    torch, pkg = lib
+    loop_geoms = [configs.with_fitting(configs.small_lgs_config(16, 32, 3, 2), altitudes=(0.0, 4000.0, 9000.0),
+                                       field_arcmin=1.2, n_dir=3),
+                  configs.with_fitting(configs.small_lgs_config(24, 64, 2, 3, order=2), altitudes=(0.0, 6000.0),
+                                       field_arcmin=1.2, n_dir=3)]
+    gain, fit_iters, K = 0.4, 4, 6
+    srv = pkg.Server(iters=ITERS, queue_depth=4, result_slots=8)
+    ids = [srv.admit_loop(g, gain=gain, fit_iters=fit_iters) for g in loop_geoms]
+    open_geom = configs.small_lgs_config(16, 32, 3, 2)
+    open_id = srv.admit(open_geom)
+    _, open_frames = _frames(open_geom, K, 5)
+    ctls = [Control(g) for g in loop_geoms]
+    meas = []
+    for i, (g, ctl) in enumerate(zip(loop_geoms, ctls)):
+        ns = int(ctl.tom.meas_offsets[-1])
+        sig = np.concatenate([np.full(2 if w["tt_only"] else 2 * int(w["valid"].sum()), w["sigma"]) for w in g["wfs"]])
+        flow = FrozenFlow(g, 3, instance=30 + i)
+        meas.append([ctl.tom.measure(flow.layers(0.002 * t)) + gaussian_noise(ns, 1.0, 800 + 50 * i + t) * sig
+                     for t in range(K)])
+    served = [[np.zeros(c.fit.n), np.zeros(c.fit.n)] for c in ctls]   # a_0 = a_1 = 0
+    submitted = [[] for _ in ctls]
+    for t in range(K):
+        for i, tid in enumerate(ids):
+            s = (meas[i][t] - ctls[i].mirror_slopes(served[i][t].astype(np.float64))).astype(np.float32)
+            submitted[i].append(s)
+            assert srv.submit(tid, s, tag=t)
+        assert srv.submit(open_id, open_frames[t], tag=t)
+        srv.drain(60.0)
+        for r in srv.poll():
+            assert r["status"] == 0 and r["tag"] == t
+            if r["telescope"] in ids:
+                served[ids.index(r["telescope"])].append(srv.result(r["telescope"], r["result_slot"], t))
+    srv.close()
+    for i, g in enumerate(loop_geoms):
+        # the same control steps through the Fit API
+        plan = pkg.Plan(g)
+        fit = pkg.Fit(plan, g["fitting"])
+        buf = [torch.zeros(fit.n, dtype=torch.float32, device="cuda") for _ in range(2)]
+        x = torch.zeros(plan.n, dtype=torch.float32, device="cuda")
+        rec = torch.zeros(fit.n, dtype=torch.float32, device="cuda")
+        for t in range(K):
+            a_tm2, a_tm1 = buf[t % 2], buf[(t + 1) % 2]
+            fit.polc_step(torch.tensor(submitted[i][t], device="cuda"), x, rec, a_tm2, a_tm1, a_tm2, gain, ITERS,
+                          fit_iters, warm=True)
+            assert np.array_equal(a_tm2.cpu().numpy(), served[i][t + 2]), (g["name"], t)
+        fit.close()
+        plan.close()
+        # the oracle's closed loop on the same measurements
+        ctl = ctls[i]
+        a = [np.zeros(ctl.fit.n), np.zeros(ctl.fit.n)]
+        xo, reco = np.zeros(ctl.tom.n), np.zeros(ctl.fit.n)
+        for t in range(K):
+            a_t, xo, reco = ctl.step(meas[i][t] - ctl.mirror_slopes(a[t]), a[t], a[t + 1], xo, reco, gain,
+                                     ITERS, fit_iters)
+            a.append(a_t)
+            e = rel(served[i][t + 2].astype(np.float64), a_t, f"served-closed-loop/{g['name']}/frame{t}")
+            assert e < 1e-4, (g["name"], t, e)
