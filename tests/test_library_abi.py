@@ -130,3 +130,33 @@ def test_plan_options_validation_without_gpu(lib):
         assert lib.tomo_plan_create_ex(ctypes.byref(g), ctypes.byref(opt), None, ctypes.byref(h)) == 1
         assert "cluster size" in lib.tomo_last_error().decode()
     assert not h.value
+
+
+def test_fit_and_control_argument_validation_without_gpu(lib):
+    """The fitting, closed-loop and server-loop entry points refuse NULL objects and
+    out-of-range arguments before touching a device."""
+    import ctypes
+    from synth import configs
+    from paper_1302_3734_gb300.binding import fit_geometry_struct, geometry_struct, PlanOptions
+    h = ctypes.c_void_p()
+    g = configs.with_fitting(configs.small_lgs_config())
+    fg, keep = fit_geometry_struct(g["fitting"])
+    assert lib.tomo_fit_create(None, ctypes.byref(fg), ctypes.byref(h)) == 1
+    assert not h.value
+    assert lib.tomo_fit_apply_normal(None, None, None, None) == 1
+    assert lib.tomo_fit_rhs(None, None, None, None) == 1
+    assert lib.tomo_fit_residual_rms(None, None, None, None, None) == 1
+    assert lib.tomo_fit_solve(None, None, None, 4, 0, None) == 1
+    assert lib.tomo_reconstruct(None, None, None, None, 10, 4, 1, None) == 1
+    assert lib.tomo_mirror_slopes(None, None, None, None, 1.0, None) == 1
+    assert lib.tomo_polc_step(None, None, None, None, None, None, None, 0.4, 10, 4, 1, None) == 1
+    assert lib.tomo_fit_get_info(None, None) == 1
+    lib.tomo_fit_destroy(None)
+    # the server refuses a closed-loop admission with a non-finite gain before building a plan
+    gs, keep_g = geometry_struct(g)
+    opt = PlanOptions()
+    tid = ctypes.c_int(-1)
+    assert lib.tomo_server_admit_loop(None, ctypes.byref(gs), ctypes.byref(opt), ctypes.byref(fg), 0.4, 4,
+                                      ctypes.byref(tid)) == 1
+    assert lib.tomo_server_get_fit(None, 0, ctypes.byref(h)) == 1
+    assert "NULL" in lib.tomo_last_error().decode()
