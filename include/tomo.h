@@ -61,7 +61,7 @@ typedef enum {
   TOMO_ERR_CUDA = 5,         /* a CUDA runtime call failed (message has the CUDA error) */
   TOMO_ERR_TIMEOUT = 6,      /* reserved for waits with a deadline */
   TOMO_ERR_BREAKDOWN = 7,    /* p.Ap <= 0 or not finite during (P)CG: iterate frozen */
-  TOMO_ERR_UNSUPPORTED = 8,  /* valid request this build does not implement */
+  TOMO_ERR_UNSUPPORTED = 8,  /* valid request the library does not implement (sizes beyond its tables) */
   TOMO_ERR_FULL = 9,         /* a bounded queue is full (served frames of one telescope) */
   TOMO_ERR_SUPERSEDED = 10   /* a served frame skipped because a newer one of its telescope
                                 was waiting (latest-frame policy) */
