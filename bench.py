@@ -15,8 +15,9 @@ flushed (a 256 MiB write) before every timed step, outside the timed window.
 Further legs of the same line: ``batched`` (16 E-ELT systems, and 64 systems of
 uneven size, per launch), ``large`` (the 100 m system), ``closed_loop`` (the
 E-ELT system with its three mirrors: fitting and pseudo-open-loop control per
-frame, with the Strehl ratio of the correction) and ``served`` (16 telescopes
-streaming frames through the server).
+frame, with the Strehl ratio of the correction), ``served`` (16 telescopes
+streaming frames through the server) and ``served_closed_loop`` (4 E-ELT
+telescopes in closed loop through the server, each with a plant on the GPU).
 
 ``--impl reference`` times the FP64 CPU oracle on the same frames instead.
 Under torchrun every rank solves its own independent telescope stream (weak
@@ -484,6 +485,80 @@ def bench_closed_loop(pkg, torch, dev, flush, frames, gain=0.4, fit_iters=4):
     return out
 
 
+def bench_served_loop(pkg, torch, dev, telescopes=4, frames=60, gain=0.4, fit_iters=4):
+    """Closed loop through the server (Algorithm 4.1 per telescope): `telescopes` E-ELT systems
+    with their three mirrors, admitted with tomo_server_admit_loop (cluster size 4).  Each has
+    its own frozen-flow atmosphere and a plant on the GPU (the library's own measurement minus
+    its mirror slopes of the commands returned two frames earlier, plus seeded noise).  A round
+    submits every telescope's residual frame from pinned host memory and waits for the
+    commands; the rounds run as fast as the loop closes, with no pacing.  Reported: control
+    steps per second over all telescopes, the server's submit-to-result latency, and the
+    long-exposure Strehl at 2200 nm over the second half of the frames."""
+    from synth import configs, FrozenFlow, gaussian_noise
+    g = configs.with_fitting(configs.config1())
+    srv = pkg.Server(iters=int(g["iters"]), max_in_flight=4, queue_depth=4, result_slots=8)
+    ids = [srv.admit_loop(g, gain=gain, fit_iters=fit_iters, cluster_size=4) for _ in range(telescopes)]
+    plant = pkg.Plan(g)
+    pfit = pkg.Fit(plant, g["fitting"])
+    n, ns, na, nd = plant.n, plant.n_slopes, pfit.n, int(pfit.info.n_dir)
+    sig = np.concatenate([np.full(2 if w["tt_only"] else 2 * int(w["valid"].sum()), w["sigma"])
+                          for w in g["wfs"]])
+    truth = torch.empty((telescopes, frames, n), dtype=torch.float32, device=dev)
+    meas = torch.empty((telescopes, frames, ns), dtype=torch.float32, device=dev)
+    for i in range(telescopes):
+        flow = FrozenFlow(g, 1, instance=20 + i)
+        for t in range(frames):
+            truth[i, t].copy_(torch.from_numpy(np.concatenate([p.ravel() for p in flow.layers(0.002 * t)])
+                                               .astype(np.float32)))
+            plant.layers_to_slopes(truth[i, t], meas[i, t])
+            meas[i, t] += torch.from_numpy((gaussian_noise(ns, 1.0, 7_000_000 + 1000 * i + t) * sig)
+                                           .astype(np.float32)).to(dev)
+    hist = [[torch.zeros(na, dtype=torch.float32, device=dev) for _ in range(2)] for _ in range(telescopes)]
+    s_dev = torch.empty(ns, dtype=torch.float32, device=dev)
+    s_host = [torch.empty(ns, dtype=torch.float32, pin_memory=True) for _ in range(telescopes)]
+    rms = torch.empty((telescopes, frames, nd), dtype=torch.float64, device=dev)
+    lat, t0 = [], None
+    for t in range(frames):
+        if t == 2:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()   # from the first frame that closes the loop
+        for i, tid in enumerate(ids):
+            a_applied = hist[i][t]     # the commands returned two frames earlier
+            pfit.residual_rms(truth[i, t], a_applied, rms[i, t])
+            pfit.mirror_slopes(a_applied, s_dev, slopes_in=meas[i, t], scale=-1.0)
+            s_host[i].copy_(s_dev)
+            assert srv.submit(tid, s_host[i].numpy(), tag=t)
+        got = 0
+        while got < telescopes:
+            for r in srv.poll():
+                assert r["status"] == 0
+                i = ids.index(r["telescope"])
+                a = srv.result(r["telescope"], r["result_slot"], r["tag"])
+                hist[i].append(torch.from_numpy(a).to(dev))
+                if t >= 2:
+                    lat.append(1000.0 * (r["t_done"] - r["t_submit"]))
+                got += 1
+            if got < telescopes:
+                time.sleep(0.0001)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    stats = srv.stats()
+    srv.close()
+    le = slice(frames // 2, frames)
+    strehl = np.exp(-(rms.cpu().numpy()[:, le] * (500.0 / 2200.0)) ** 2).mean(axis=1)   # [telescope, direction]
+    out = {"telescopes": telescopes, "frames_per_telescope": frames, "gain": gain, "fit_iters": fit_iters,
+           "cluster_size": 4, "max_in_flight": 4,
+           "control_steps_per_s": telescopes * (frames - 2) / wall,
+           "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+           "launches": stats["launches"],
+           "strehl_2200nm_long_exposure_field_average": [float(x) for x in strehl.mean(axis=1)],
+           "note": "rounds of one frame per telescope, each waiting for the commands that close the loop; "
+                   "the plant (measurement, mirror slopes, Strehl) runs on the same GPU between the rounds"}
+    pfit.close()
+    plant.close()
+    return out
+
+
 def served_geometries():
     """16 telescopes cycling the three geometry families: the 8 m system (FP32 operator, Jacobi
     PCG), the E-ELT system, and instances of the uneven 64-instance set."""
@@ -744,6 +819,8 @@ def main():
         line["closed_loop"] = bench_closed_loop(pkg, torch, dev, flush, args.loop_frames)
     if args.serve_seconds > 0 and rank == 0:
         line["served"] = bench_served(pkg, torch, args, dev)
+    if not args.no_loop and args.serve_seconds > 0 and rank == 0:
+        line["served_closed_loop"] = bench_served_loop(pkg, torch, dev)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         from oracle import Tomography
         ora = Tomography(geom)

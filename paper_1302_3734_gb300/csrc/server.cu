@@ -138,6 +138,26 @@ bool ready(const tomo_server *S) {
   return false;
 }
 
+// The telescopes of the next launch: every idle open-loop telescope with a
+// waiting frame (one batched solve), or else one closed-loop telescope (its own
+// control step, so that several run on separate streams at once).
+std::vector<Telescope *> next_launch(tomo_server *S) {
+  std::vector<Telescope *> open;
+  Telescope *loop = nullptr;
+  for (auto &kv : S->tels) {
+    Telescope *t = kv.second;
+    if (t->busy || t->queue.empty()) continue;
+    if (t->fit) {
+      if (!loop) loop = t;
+    } else {
+      open.push_back(t);
+    }
+  }
+  if (!open.empty()) return open;
+  if (loop) return {loop};
+  return {};
+}
+
 // Enqueue one launch on its stream: frame copies in, the mask, the batched
 // solve, coefficient copies out, the completion event.  Runs without the
 // lock; the launch is in flight, so the batch and the telescopes are fixed.
@@ -199,9 +219,7 @@ void worker_main(tomo_server *S) {
     Launch &L = S->inflight.back();
     L.slot = free_slot(S);
     S->slot_busy[L.slot] = true;
-    for (auto &kv : S->tels) {
-      Telescope *t = kv.second;
-      if (t->busy || t->queue.empty()) continue;
+    for (Telescope *t : next_launch(S)) {
       if (S->latest_only) {
         const double tnow = now_s();
         while (t->queue.size() > 1) {
