@@ -768,6 +768,7 @@ tomo_status tomo_solve(tomo_plan *p, const void *d_slopes, void *d_coeffs, int i
   if (!d_slopes || !d_coeffs) return fail(TOMO_ERR_ARG, "slopes and coefficients must be device pointers");
   if (iters < 0 || iters > 100000) return fail(TOMO_ERR_ARG, "iters out of range");
   DeviceGuard dg(p->device);
+  NvtxRange nvtx("tomo_solve");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   warm = warm ? 1 : 0;
   const void *sl[1] = {d_slopes};
@@ -913,6 +914,7 @@ tomo_status tomo_solve_batch(tomo_plan *const *plans, const void *const *d_slope
     for (int j = 0; j < i; ++j)
       if (plans[j] == plans[i]) return fail(TOMO_ERR_ARG, "a plan appears twice in one batch");
   }
+  NvtxRange nvtx("tomo_solve_batch");
   Batch *b = nullptr;
   TOMO_TRY(get_batch(plans, count, &b));
   DeviceGuard dg(b->device);

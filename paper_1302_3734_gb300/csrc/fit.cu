@@ -963,6 +963,8 @@ tomo_status run_graph(tomo_fit *f, const tomo_fit::Call &c, cudaStream_t s) {
 // Runs a call from its graph, or launch by launch when the plan's launch mode
 // says so.
 tomo_status run_call(tomo_fit *f, const tomo_fit::Call &c, cudaStream_t s) {
+  static const char *const kNames[] = {"tomo_fit_solve", "tomo_reconstruct", "tomo_polc_step"};
+  tomo::NvtxRange nvtx(kNames[c.kind]);
   if (f->plan->use_graphs) return run_graph(f, c, s);
   int nk = 0;
   return enqueue_call(f, c, s, &nk);

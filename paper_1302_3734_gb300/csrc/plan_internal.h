@@ -5,6 +5,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/tomo.h"
 #include "common.h"
@@ -61,6 +62,15 @@ tomo_status set_error(tomo_status st, const std::string &msg);
 
 // Add k kernel launches to the count tomo_launch_count() reports.
 void count_launches(long long k);
+
+// An NVTX range over the guard's lifetime (a no-op unless a profiler is attached):
+// the public entry points mark their host-side enqueue work with it.
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Makes `dev` the current device for the guard's lifetime.
 struct DeviceGuard {

@@ -162,6 +162,7 @@ std::vector<Telescope *> next_launch(tomo_server *S) {
 // solve, coefficient copies out, the completion event.  Runs without the
 // lock; the launch is in flight, so the batch and the telescopes are fixed.
 tomo_status enqueue_launch(tomo_server *S, const Launch &L) {
+  tomo::NvtxRange nvtx("tomo_server launch");
   const int j = L.slot;
   cudaStream_t st = S->streams[j];
   cudaError_t e = cudaSuccess;
