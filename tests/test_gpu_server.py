@@ -272,3 +272,22 @@ def test_closed_loop_telescopes_are_their_control_steps_and_match_the_oracle_loo
             a.append(a_t)
             e = rel(served[i][t + 2].astype(np.float64), a_t, f"served-closed-loop/{g['name']}/frame{t}")
             assert e < 1e-4, (g["name"], t, e)
+
+
+def test_drain_deadline_reports_a_timeout_and_the_server_stays_usable(lib):
+    torch, pkg = lib
+    g = configs.small_lgs_config(16, 32, 3, 2)
+    srv = pkg.Server(iters=3000, queue_depth=2, result_slots=2)
+    tid = srv.admit(g)
+    s = np.ones(srv.info(tid).n_slopes, dtype=np.float32)
+    assert srv.submit(tid, s, tag=1)
+    with pytest.raises(pkg.TomoError) as ei:
+        srv.drain(1e-4)                     # a 3000-iteration frame is still on the GPU
+    assert ei.value.status == 6
+    srv.drain(60.0)
+    (r,) = srv.poll()
+    assert r["status"] == 0 and r["tag"] == 1
+    assert srv.submit(tid, s, tag=2)
+    srv.drain(60.0)
+    assert [r["tag"] for r in srv.poll()] == [2]
+    srv.close()
