@@ -31,8 +31,15 @@ def _cut():
     return g
 
 
+def _single():
+    """The degenerate case: one mirror seen from one direction (on axis)."""
+    return configs.with_fitting(configs.small_lgs_config(16, 32, 3, 2), altitudes=(0.0,), pitches=(0.5,),
+                                field_arcmin=0.0, n_dir=1)
+
+
 CASES = {
     "small": _small,
+    "single-mirror-single-direction": _single,
     "small-fp64": lambda: _small(1),
     "cut-mirrors": _cut,
     "eelt": lambda: configs.with_fitting(configs.config1()),
@@ -158,6 +165,13 @@ def test_fitting_rejects_bad_geometry(lib):
     with pytest.raises(pkg.TomoError) as ei:
         pkg.Fit(plan, empty)
     assert ei.value.status == 2
+    # a 2x2 sampling grid (3 corners per side) under 1 m actuators: 3-corner windows, which the
+    # gather rounds up to 4 taps, more than the grid holds
+    tiny = dict(g["fitting"], n_sub=2, valid=np.ones((2, 2), np.uint8),
+                dms=[{"altitude": 0.0, "pitch": 1.0, "n": 5}])
+    with pytest.raises(pkg.TomoError) as ei:
+        pkg.Fit(plan, tiny)
+    assert ei.value.status == 8
     plan.close()
 
 
