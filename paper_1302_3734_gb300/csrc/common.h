@@ -14,6 +14,8 @@ constexpr int kMaxLevels = 12;
 constexpr int kFwdTile = 16;       // corners per side of a forward tile
 constexpr int kMaxBatch = 96;      // instances per launch (kernel-argument arrays)
 constexpr int kThreads = 256;      // threads per CTA of the hot kernels (transforms: below)
+constexpr int kFwdThreads = 512;   // largest forward CTA; small launches use it, big batches kThreads
+constexpr int kFwdSmallLaunch = 608;   // forward CTAs up to which a launch uses kFwdThreads
 constexpr int kAnalysisThreads = 512;  // threads per CTA of the gather + analysis kernel when two fit an SM
 constexpr int kAnalysisThreadsMax = 1024;  // ... when its shared memory leaves room for one
 constexpr int kSynthThreads = 512;     // threads per CTA of the synthesis kernel (at most)

@@ -120,6 +120,10 @@ __device__ __forceinline__ T trace_corner(const InstDev &I, int m, int nc, const
 // io.in0: layer grids (NULL = the plan's phi); io.in1: slopes (MODE 1, 2).
 // EL: some sensor of the launch has elongated spots (Sec. 4.3); without it the
 // elongation code is compiled out.
+// Launched with kThreads or kFwdThreads threads.  The per-corner steps use
+// every thread; the steps that feed the tile's partial sums (the slopes and
+// the tip/tilt-only chunks) keep a fixed kThreads-thread mapping, so the
+// partials, and every result, are bitwise the same at either block size.
 constexpr int kHalo = kFwdTile + 2;
 
 __host__ __device__ constexpr size_t fwd_table_bytes(int L, size_t esz) {
@@ -127,7 +131,7 @@ __host__ __device__ constexpr size_t fwd_table_bytes(int L, size_t esz) {
 }
 
 template <typename T, int MODE, bool EL>
-__global__ void __launch_bounds__(kThreads) k_forward(const InstDev *__restrict__ insts,
+__global__ void __launch_bounds__(kFwdThreads) k_forward(const InstDev *__restrict__ insts,
                                                      const FwdItem *__restrict__ items, IoArgs io) {
   extern __shared__ __align__(16) unsigned char fsm[];
   __shared__ InstDev sI;
@@ -149,8 +153,8 @@ __global__ void __launch_bounds__(kThreads) k_forward(const InstDev *__restrict_
     // subapertures is <Gamma^T 1, psi>, which lives on the pupil-edge corners;
     // one (edge corner, layer) term per thread, one FP64 partial per chunk.
     if (MODE == 2) return;   // data only: the model term is zero
-    const int pair = it.tile * blockDim.x + tid;
-    const bool on = pair < W.n_edge * L;
+    const int pair = it.tile * kThreads + tid;
+    const bool on = tid < kThreads && pair < W.n_edge * L;
     int x0 = 0, y0 = 0, x1 = 0, y1 = 0, N = 1, off = 0;
     T fx = T(0), fy = T(0), tx = T(0), ty = T(0);
     if (on) {
@@ -256,7 +260,7 @@ __global__ void __launch_bounds__(kThreads) k_forward(const InstDev *__restrict_
   const T el_cx = EL ? T(0.5 - 0.5 * n) * el_d - T(W.el_lx) : T(0);
   const T el_cy = EL ? T(0.5 - 0.5 * n) * el_d - T(W.el_ly) : T(0);
   const bool four = EL && tile_partials(W) == 4;
-  for (int idx = tid; idx < (kFwdTile + 1) * (kFwdTile + 1); idx += blockDim.x) {
+  for (int idx = tid; tid < kThreads && idx < (kFwdTile + 1) * (kFwdTile + 1); idx += kThreads) {
     const int u = idx % (kFwdTile + 1), w = idx / (kFwdTile + 1);
     const int a = a0 - 1 + u, b = b0 - 1 + w;
     T ex = T(0), ey = T(0);
@@ -300,7 +304,7 @@ __global__ void __launch_bounds__(kThreads) k_forward(const InstDev *__restrict_
   __syncthreads();
   // 3. Gamma^T: each corner gathers its four neighbouring subapertures
   T *v = static_cast<T *>(I.v) + W.v_off;
-  {
+  if (tid < kFwdTile * kFwdTile) {
     const int u = tid % kFwdTile, w = tid / kFwdTile;
     const int a = a0 + u, b = b0 + w;
     if (a < nc && b < nc) {
@@ -1801,22 +1805,23 @@ cudaError_t launch_analysis(int precision, int src, int epi, int lf, int flags, 
 }
 
 template <typename T, bool EL>
-cudaError_t fwd_t(int mode, dim3 g, size_t sm, cudaStream_t s, const InstDev *insts, const FwdItem *items,
-                  const IoArgs &io) {
-  if (mode == 0) return launch_ex(k_forward<T, 0, EL>, g, kThreads, 0, sm, s, insts, items, io);
-  if (mode == 1) return launch_ex(k_forward<T, 1, EL>, g, kThreads, 0, sm, s, insts, items, io);
-  return launch_ex(k_forward<T, 2, EL>, g, kThreads, 0, sm, s, insts, items, io);
+cudaError_t fwd_t(int mode, dim3 g, int nt, size_t sm, cudaStream_t s, const InstDev *insts,
+                  const FwdItem *items, const IoArgs &io) {
+  if (mode == 0) return launch_ex(k_forward<T, 0, EL>, g, nt, 0, sm, s, insts, items, io);
+  if (mode == 1) return launch_ex(k_forward<T, 1, EL>, g, nt, 0, sm, s, insts, items, io);
+  return launch_ex(k_forward<T, 2, EL>, g, nt, 0, sm, s, insts, items, io);
 }
 
 cudaError_t launch_forward(int precision, int mode, int max_layers, int elong, const InstDev *insts,
                            const FwdItem *items, int n_items, const IoArgs &io, cudaStream_t s) {
   const dim3 g(n_items);
+  const int nt = n_items <= kFwdSmallLaunch ? kFwdThreads : kThreads;
   const size_t sm = forward_smem(max_layers, precision);
   if (precision == 0)
-    return elong ? fwd_t<float, true>(mode, g, sm, s, insts, items, io)
-                 : fwd_t<float, false>(mode, g, sm, s, insts, items, io);
-  return elong ? fwd_t<double, true>(mode, g, sm, s, insts, items, io)
-               : fwd_t<double, false>(mode, g, sm, s, insts, items, io);
+    return elong ? fwd_t<float, true>(mode, g, nt, sm, s, insts, items, io)
+                 : fwd_t<float, false>(mode, g, nt, sm, s, insts, items, io);
+  return elong ? fwd_t<double, true>(mode, g, nt, sm, s, insts, items, io)
+               : fwd_t<double, false>(mode, g, nt, sm, s, insts, items, io);
 }
 
 cudaError_t launch_update(int precision, int flags, const InstDev *insts, const UpdItem *items,
