@@ -44,8 +44,8 @@ METRIC = "tomography solves/s and p99 frame latency at 84x84 MCAO vs plain GPU P
 # DRAM bytes (read + write) per launch of each PCG kernel on this workload, from one ncu capture
 # with flushed caches, valid only for the kernel source file they were taken from.
 NCU_TRAFFIC = {
-    "kernels_cu_sha256": "e041a19d3ba3fee84a0bb4a49117351dc34fbd2dab7b214ae89f33d8b3c1e1ef",
-    "bytes": {"analysis": 7456000, "synthesis": 663040, "forward": 755200, "update": 2983680},
+    "kernels_cu_sha256": "7d56b17733ca93b92628886307e8bcea7ec29c36ba7c2be51cb16910057991bb",
+    "bytes": {"analysis": 7456256, "synthesis": 662784, "forward": 749824, "update": 2983424},
 }
 
 
