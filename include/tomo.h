@@ -275,10 +275,14 @@ typedef struct {
   long long device_bytes;      /* device memory held by the fit */
 } tomo_fit_info;
 
-/* Build a fit for plan p: validates g, builds the tap tables of H, H^T and P
- * (FP64 on the host, stored in the plan's element type) and allocates the
- * workspace.  Synchronises the device.  On success *out owns device memory
- * until tomo_fit_destroy.  TOMO_ERR_ARG: an argument out of the ranges above. */
+/* Build a fit for plan p: validates g, builds the tap tables of H, H^T, P and
+ * of the mirrors as the plan's sensors see them (A_hat, below), assembles
+ * H^T H as a sparse matrix (all in FP64 on the host, stored in the plan's
+ * element type) and allocates the workspace.  Synchronises the device.  On
+ * success *out owns device memory until tomo_fit_destroy.  TOMO_ERR_ARG: an
+ * argument out of the ranges above; TOMO_ERR_GEOMETRY: no valid subaperture;
+ * TOMO_ERR_UNSUPPORTED: an actuator's window of sampling corners longer than 8
+ * or than the sampling grid. */
 tomo_status tomo_fit_create(tomo_plan *p, const tomo_fit_geometry *g, tomo_fit **out);
 
 tomo_status tomo_fit_get_info(const tomo_fit *f, tomo_fit_info *out);
