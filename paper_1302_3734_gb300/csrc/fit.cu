@@ -74,6 +74,7 @@ struct FitDev {
   const int *nrm_ptr;         // H^T H in CSR: row starts (n_act + 1), columns, values (T)
   const int *nrm_col;
   const void *nrm_val;
+  const int *nrm_order;       // rows by decreasing length: warp w of k_fit_spmv takes row nrm_order[w]
   int nblk_spmv;
   double *part;               // (kRrSlots + 2) * part_stride
   double *flag;               // nonzero after a breakdown
@@ -285,12 +286,14 @@ template <typename T, int MODE>
 __global__ void __launch_bounds__(kFitThreads) k_fit_spmv(FitDev F, const T *__restrict__ x, T *__restrict__ out,
                                                          int it) {
   pdl_trigger();
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  const bool on = warp < F.n_act;
+  const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const bool on = wid < F.n_act;
+  // the longest rows first, so that no late wave holds only long rows
+  const int row = on ? F.nrm_order[wid] : 0;
   int beg = 0, end = 0;
   if (on) {
-    beg = F.nrm_ptr[warp];
-    end = F.nrm_ptr[warp + 1];
+    beg = F.nrm_ptr[row];
+    end = F.nrm_ptr[row + 1];
   }
   pdl_wait();
   const bool first = it == 0;
@@ -314,11 +317,11 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_spmv(FitDev F, const T *__r
   Acc<T> d, z;
   if (on && lane == 0) {
     if (MODE == 2) {
-      out[warp] = acc;
+      out[row] = acc;
     } else {
-      const T pn = fit_dir(r, pp, warp, first, beta);
-      static_cast<T *>(F.p[it & 1])[warp] = pn;
-      static_cast<T *>(F.q)[warp] = acc;
+      const T pn = fit_dir(r, pp, row, first, beta);
+      static_cast<T *>(F.p[it & 1])[row] = pn;
+      static_cast<T *>(F.q)[row] = acc;
       d.add_prod(pn, acc);
     }
   }
@@ -595,8 +598,8 @@ struct FitTables {
   std::vector<int2> lay;
   int kw = 0, n_points = 0;
   long long n_active = 0;
-  // H^T H in CSR (FP64)
-  std::vector<int> nrm_ptr, nrm_col;
+  // H^T H in CSR (FP64) and its rows by decreasing length
+  std::vector<int> nrm_ptr, nrm_col, nrm_order;
   std::vector<double> nrm_val;
   // A_hat: work items, per sensor and mirror the corner taps
   std::vector<int4> ms_items, sens, sens_off;
@@ -783,6 +786,11 @@ tomo_status build_tables(const tomo::HostPlan &H, const tomo_fit_geometry *g, Fi
       }
       T->nrm_ptr.push_back(static_cast<int>(T->nrm_col.size()));
     }
+    T->nrm_order.resize(n_act);
+    for (int i = 0; i < n_act; ++i) T->nrm_order[i] = i;
+    std::stable_sort(T->nrm_order.begin(), T->nrm_order.end(), [&](int a, int b) {
+      return T->nrm_ptr[a + 1] - T->nrm_ptr[a] > T->nrm_ptr[b + 1] - T->nrm_ptr[b];
+    });
   }
   // the mirrors on the plan's sensors: corner (a, b) of sensor m sees mirror k at
   // ((1 - h_k/H_m) r + theta_m h_k), cone factor 1 for a natural star
@@ -1042,7 +1050,7 @@ tomo_status tomo_fit_create(tomo_plan *p, const tomo_fit_geometry *g, tomo_fit *
   const size_t es = f->esz;
   struct Item { size_t *off; size_t bytes; };
   size_t o_act, o_lay, o_hx0, o_hy0, o_hfx, o_hfy, o_px0, o_py0, o_pfx, o_pfy, o_wx0, o_wy0, o_wxw, o_wyw,
-      o_msi, o_sens, o_soff, o_sidx, o_eidx, o_et, o_sx0, o_sy0, o_sfx, o_sfy, o_nptr, o_ncol, o_nval, o_u, o_r,
+      o_msi, o_sens, o_soff, o_sidx, o_eidx, o_et, o_sx0, o_sy0, o_sfx, o_sfy, o_nptr, o_ncol, o_nval, o_nord, o_u, o_r,
       o_p0, o_p1, o_q, o_phi, o_sol, o_part, o_flag;
   const Item items[] = {
       {&o_act, T.act.size()},
@@ -1072,6 +1080,7 @@ tomo_status tomo_fit_create(tomo_plan *p, const tomo_fit_geometry *g, tomo_fit *
       {&o_nptr, T.nrm_ptr.size() * sizeof(int)},
       {&o_ncol, T.nrm_col.size() * sizeof(int)},
       {&o_nval, T.nrm_val.size() * es},
+      {&o_nord, T.nrm_order.size() * sizeof(int)},
       {&o_u, static_cast<size_t>(nd) * nc * nc * es},
       {&o_r, n_act * es},
       {&o_p0, n_act * es},
@@ -1099,6 +1108,7 @@ tomo_status tomo_fit_create(tomo_plan *p, const tomo_fit_geometry *g, tomo_fit *
   std::memcpy(img.data() + o_wy0, T.wy0.data(), T.wy0.size() * sizeof(int));
   std::memcpy(img.data() + o_nptr, T.nrm_ptr.data(), T.nrm_ptr.size() * sizeof(int));
   std::memcpy(img.data() + o_ncol, T.nrm_col.data(), T.nrm_col.size() * sizeof(int));
+  std::memcpy(img.data() + o_nord, T.nrm_order.data(), T.nrm_order.size() * sizeof(int));
   std::memcpy(img.data() + o_msi, T.ms_items.data(), T.ms_items.size() * sizeof(int4));
   std::memcpy(img.data() + o_sens, T.sens.data(), T.sens.size() * sizeof(int4));
   std::memcpy(img.data() + o_soff, T.sens_off.data(), T.sens_off.size() * sizeof(int4));
@@ -1160,6 +1170,7 @@ tomo_status tomo_fit_create(tomo_plan *p, const tomo_fit_geometry *g, tomo_fit *
   F.nrm_ptr = reinterpret_cast<const int *>(base + o_nptr);
   F.nrm_col = reinterpret_cast<const int *>(base + o_ncol);
   F.nrm_val = base + o_nval;
+  F.nrm_order = reinterpret_cast<const int *>(base + o_nord);
   F.q = base + o_q;
   f->phi = base + o_phi;
   F.part = reinterpret_cast<double *>(base + o_part);
