@@ -138,24 +138,27 @@ bool ready(const tomo_server *S) {
   return false;
 }
 
-// The telescopes of the next launch: every idle open-loop telescope with a
-// waiting frame (one batched solve), or else one closed-loop telescope (its own
-// control step, so that several run on separate streams at once).
+// The telescopes of the next launch, oldest waiting frame first: every idle
+// open-loop telescope with a waiting frame (one batched solve), or one
+// closed-loop telescope (its own control step, so that several run on separate
+// streams at once), whichever kind holds the oldest frame.
 std::vector<Telescope *> next_launch(tomo_server *S) {
   std::vector<Telescope *> open;
   Telescope *loop = nullptr;
+  double t_open = INFINITY;
   for (auto &kv : S->tels) {
     Telescope *t = kv.second;
     if (t->busy || t->queue.empty()) continue;
+    const double ts = t->queue.front().t_submit;
     if (t->fit) {
-      if (!loop) loop = t;
+      if (!loop || ts < loop->queue.front().t_submit) loop = t;
     } else {
       open.push_back(t);
+      t_open = std::min(t_open, ts);
     }
   }
-  if (!open.empty()) return open;
-  if (loop) return {loop};
-  return {};
+  if (loop && (open.empty() || loop->queue.front().t_submit < t_open)) return {loop};
+  return open;
 }
 
 // Enqueue one launch on its stream: frame copies in, the mask, the batched
