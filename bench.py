@@ -470,11 +470,23 @@ def bench_closed_loop(pkg, torch, dev, flush, frames, gain=0.4, fit_iters=4):
         ft.append((e0, e1))
     torch.cuda.synchronize()
     fit_ms = np.array([a0.elapsed_time(b0) for a0, b0 in ft[10:]])
+    # the fitting CG's iterations against the bytes they must move (H^T H and the vectors; the
+    # right-hand side's two launches are left out of the bytes and counted in the time)
+    fit_gbs = int(fit.info.bytes_per_iteration) * fit_iters / (float(fit_ms.mean()) / 1000.0) / 1e9
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    l2 = l2_probe(torch, dev)
     out = {"frames": frames, "gain": gain, "fit_iters": fit_iters, "tomo_iters": 10,
            "actuators": na, "actuators_reached": int(fit.info.n_active), "directions": nd,
            "control_steps_per_s": 1000.0 / float(ms[5:].mean()),
            "control_step_ms": {"p50": float(np.percentile(ms[5:], 50)), "p99": float(np.percentile(ms[5:], 99))},
            "fitting_ms": {"mean": float(fit_ms.mean()), "p99": float(np.percentile(fit_ms, 99))},
+           "fitting_roofline": {"bytes_per_iteration": int(fit.info.bytes_per_iteration),
+                                "normal_nonzeros": int(fit.info.normal_nonzeros),
+                                "achieved_GBps": fit_gbs, "frac_of_hbm_peak": fit_gbs / hbm,
+                                "frac_of_l2_peak": fit_gbs / l2,
+                                "note": "L2-resident (H^T H is 10.8 MB); latency-bound at 10 launches per solve"},
            "strehl_2200nm_long_exposure": {"field_average": float(strehl.mean()),
                                            "on_axis": float(strehl[nd // 2]),
                                            "uncorrected_field_average": float(strehl_open.mean())},

@@ -93,7 +93,8 @@ class FitInfo(ctypes.Structure):
     _fields_ = [("n_act", ctypes.c_longlong), ("n_active", ctypes.c_longlong),
                 ("n_points", ctypes.c_int), ("n_dir", ctypes.c_int), ("n_dm", ctypes.c_int),
                 ("kernels_per_iteration", ctypes.c_int), ("kernels_per_solve_base", ctypes.c_int),
-                ("device_bytes", ctypes.c_longlong)]
+                ("device_bytes", ctypes.c_longlong), ("normal_nonzeros", ctypes.c_longlong),
+                ("bytes_per_iteration", ctypes.c_longlong)]
 
 
 # (name, restype, argtypes) of every symbol declared in include/tomo.h

@@ -542,7 +542,7 @@ struct tomo_fit {
   void *arena = nullptr;
   size_t arena_bytes = 0;
   void *phi = nullptr;   // layer grids of tomo_reconstruct
-  long long n_active = 0;
+  long long n_active = 0, nnz = 0;
   int n_points = 0;
   cudaStream_t cap = nullptr;
   // The arguments of one graph-launched call.  kind 0: tomo_fit_solve (in =
@@ -1022,6 +1022,7 @@ tomo_status tomo_fit_create(tomo_plan *p, const tomo_fit_geometry *g, tomo_fit *
   f->precision = H.precision;
   f->esz = H.precision ? 8 : 4;
   f->n_active = T.n_active;
+  f->nnz = static_cast<long long>(T.nrm_col.size());
   f->n_points = T.n_points;
   FitDev &F = f->F;
   const int nc = g->n_sub + 1, nd = g->n_dir;
@@ -1189,6 +1190,11 @@ tomo_status tomo_fit_get_info(const tomo_fit *f, tomo_fit_info *out) {
   out->kernels_per_iteration = 2;
   out->kernels_per_solve_base = 2;
   out->device_bytes = static_cast<long long>(f->arena_bytes);
+  out->normal_nonzeros = f->nnz;
+  // SpMV: every entry and its column, the row starts, p and r read, p and q written;
+  // update: a, p, q, r read, a and r written
+  const long long na = f->F.n_act, es = static_cast<long long>(f->esz);
+  out->bytes_per_iteration = f->nnz * (es + 4) + 4 * (na + 1) + 4 * na * es + 6 * na * es;
   return TOMO_OK;
 }
 

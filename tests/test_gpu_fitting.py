@@ -198,3 +198,24 @@ def test_residual_rms_per_direction(lib, name):
         assert e < tol, e
     fit.close()
     plan.close()
+
+
+@pytest.mark.parametrize("name", ["single-mirror-single-direction", "cut-mirrors"])
+def test_normal_matrix_entries_match_the_brute_force_pattern(lib, name):
+    """The stored entries of H^T H are the actuator pairs that share a sampling
+    point with nonzero weights in some direction (all weights are positive, so no
+    sum cancels).  Pairs whose weight product is a rounding residue sit on a hat's
+    edge, where the two sides may decide either way: the count lies between the
+    pattern with those dropped and the full pattern."""
+    torch, pkg = lib
+    g = CASES[name]()
+    plan = pkg.Plan(g)
+    fit = pkg.Fit(plan, g["fitting"])
+    H = Fitting(g).dense_mirror_bruteforce()
+    hi = int(np.count_nonzero((H != 0).T.astype(np.int64) @ (H != 0).astype(np.int64)))
+    big = np.abs(H) > 1e-9
+    lo = int(np.count_nonzero(big.T.astype(np.int64) @ big.astype(np.int64)))
+    assert lo <= fit.info.normal_nonzeros <= hi, (lo, fit.info.normal_nonzeros, hi)
+    assert fit.info.bytes_per_iteration > fit.info.normal_nonzeros * (8 if g["precision"] else 4)
+    fit.close()
+    plan.close()
