@@ -275,7 +275,7 @@ typedef struct {
   long long device_bytes;      /* device memory held by the fit */
   long long normal_nonzeros;   /* stored entries of H^T H */
   long long bytes_per_iteration; /* algorithmic bytes of one CG iteration: H^T H (entries and
-                                    column indices) and the vectors p, r, q, a */
+                                    column indices, row descriptors) and the vectors r, q, p, a */
 } tomo_fit_info;
 
 /* Build a fit for plan p: validates g, builds the tap tables of H, H^T, P and

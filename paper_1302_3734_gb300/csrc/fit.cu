@@ -8,13 +8,17 @@
 // function of its actuator grid; P_j phi (x) = sum_l phi_l(x + h_l theta_j)
 // (eq. ngsproj), bilinear on the periodic layer grids; x runs over the corners
 // of the valid subapertures of the aperture sampling grid.  H^T H is constant:
-// it is assembled once on the host (FP64, CSR) and each CG iteration is two
-// kernels:
+// it is assembled once on the host (FP64, CSR) and each CG iteration is one
+// kernel:
 //
-//   k_fit_spmv     q = H^T H p, with the CG direction p = r + beta p formed on
-//                  the fly and written to the other of two p buffers;
-//                  p.q partials                                     [warp per row]
-//   k_fit_update   alpha, a += alpha p, r -= alpha q, r.r partials  [actuator per thread]
+//   k_fit_iter     iteration it: r = r - alpha q and p = r + beta p of the
+//                  previous iteration's alpha and this one's beta, formed on
+//                  the fly for every column, and q = H^T H p [warp per nonempty
+//                  row; the row's warp stores its r, p, q and a += alpha p];
+//                  p.q, r.q and q.q partials per block; the block that takes
+//                  the last ticket sums them and leaves alpha, r.r of the next
+//                  iteration (rr - 2 alpha r.q + alpha^2 q.q) and beta
+//   k_fit_finish   a += alpha p of the last iteration        [actuator per thread]
 //
 // The right-hand side and the initial residual stay matrix-free:
 //
@@ -27,8 +31,8 @@
 // the host from the same corner -> actuator taps, so the gather is the exact
 // transpose of the mirror kernel.  Inner products are accumulated as in the
 // tomography kernels (double-float per thread for FP32, one FP64 partial per
-// block, partials summed by every consumer block in a fixed order), so results
-// are bitwise reproducible.
+// block, partials summed in a fixed order), so results are bitwise
+// reproducible.
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -48,17 +52,18 @@
 namespace tomo {
 
 constexpr int kFitThreads = 256;   // equals kFwdTile^2: one thread per subaperture of an A_hat tile
+constexpr int kFitIterThreads = 1024;   // k_fit_iter: 32 rows per block; the last block updates with all
 constexpr int kFitRmsThreads = 1024;
 constexpr int kMaxDm = 4;
 constexpr int kMaxFitDirs = 256;
-constexpr int kRrSlots = 4;   // r.r partial slots (ring over iterations), then 2 p.q slots
+constexpr int kPqSlot = 1;    // partial slots: 0 r.r of the initial residual, 1-3 p.q, r.q, q.q of k_fit_iter
 constexpr int kFitDirBatch = 4;   // directions whose gather loads one thread issues together
-constexpr int kSpmvBatch = 4;     // matrix entries whose loads one lane of k_fit_spmv issues together
+constexpr int kSpmvBatch = 4;     // matrix entries whose loads one lane issues together (fit_row)
 
 // Everything the fitting kernels read (passed by value).
 struct FitDev {
   int n_dir, n_dm, nc, n_layers;
-  int n_act, kw, nblk_adj, nblk_upd, part_stride, n_points;
+  int n_act, kw, nblk_adj, nblk_upd, part_stride, n_points, n_rows;
   int dm_n[kMaxDm], dm_off[kMaxDm], w_off[kMaxDm];
   const unsigned char *act;   // nc*nc corner mask
   const int2 *lay;            // per layer (N, offset in the layer vector)
@@ -69,14 +74,18 @@ struct FitDev {
   const int *wx0, *wy0;       // per (dm, dir, actuator column / row): first corner of its window
   const void *wxw, *wyw;      //   kw weights (T), zero beyond the window
   void *u;                    // [dir][nc*nc]
-  void *r, *q;                // [n_act]
-  void *p[2];                 // [n_act]: the CG direction of iteration it is p[it & 1]
+  void *r[2], *q[2], *p[2];   // [n_act]: residual, H^T H p and direction of CG iteration it in
+                              // [it & 1] (the initial residual in r[0])
   const int *nrm_ptr;         // H^T H in CSR: row starts (n_act + 1), columns, values (T)
   const int *nrm_col;
   const void *nrm_val;
-  const int *nrm_order;       // rows by decreasing length: warp w of k_fit_spmv takes row nrm_order[w]
-  int nblk_spmv;
-  double *part;               // (kRrSlots + 2) * part_stride
+  const int4 *nrm_desc;       // (row, first entry, end, 0) by decreasing row length: warp w takes
+                              // desc[w]; the n_rows nonempty rows come first
+  int nblk_spmv, nblk_iter;
+  double *part;               // 4 * part_stride
+  double *cg;                 // CG scalars of iteration it: alpha in cg[it & 1], r.r in cg[2 + (it & 1)],
+                              // beta in cg[4 + (it & 1)]
+  unsigned *ticket;           // blocks of k_fit_iter done; reset by the last one
   double *flag;               // nonzero after a breakdown
   // the mirrors seen by the plan's sensors (A_hat)
   int n_ms_items;
@@ -100,8 +109,8 @@ __device__ double2 fit_sum2(const double *p1, int n1, const double *p2, int n2) 
   __shared__ double s_w[2][32];
   __shared__ double2 s_v;
   double a = 0.0, b = 0.0;
-  for (int i = threadIdx.x; i < n1; i += blockDim.x) a += p1[i];
-  for (int i = threadIdx.x; i < n2; i += blockDim.x) b += p2[i];
+  for (int i = threadIdx.x; i < n1; i += blockDim.x) a += __ldcg(p1 + i);
+  for (int i = threadIdx.x; i < n2; i += blockDim.x) b += __ldcg(p2 + i);
   a = warp_sum(a);
   b = warp_sum(b);
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -119,21 +128,6 @@ __device__ double2 fit_sum2(const double *p1, int n1, const double *p2, int n2) 
   }
   __syncthreads();
   return s_v;
-}
-
-// The r.r partials of CG iteration `it` (it = 0: the initial residual, from
-// the adjoint kernel; later ones from the updates) and their count.
-__device__ __forceinline__ const double *fit_rr_part(const FitDev &F, int it, int *n) {
-  *n = it == 0 ? F.nblk_adj : F.nblk_upd;
-  return F.part + (it % kRrSlots) * F.part_stride;
-}
-
-// beta of iteration it >= 1: r.r of this iteration over r.r of the previous.
-__device__ __forceinline__ double fit_beta(const FitDev &F, int it) {
-  int n1, n0;
-  const double *p1 = fit_rr_part(F, it, &n1), *p0 = fit_rr_part(F, it - 1, &n0);
-  const double2 v = fit_sum2(p1, n1, p0, n0);
-  return v.y != 0.0 ? v.x / v.y : 0.0;
 }
 
 template <typename T>
@@ -268,7 +262,7 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_adjoint(FitDev F, T *__rest
     if (MODE == 2) {
       out[act] = s;
     } else {
-      static_cast<T *>(F.r)[act] = s;
+      static_cast<T *>(F.r[0])[act] = s;
       d.add_prod(s, s);
     }
   }
@@ -278,31 +272,13 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_adjoint(FitDev F, T *__rest
   }
 }
 
-// q = H^T H p for CG iteration `it` (MODE 0): one warp per row of the CSR
-// matrix, the direction p = r + beta p_prev formed on the fly for every column
-// (p = r when it == 0) and written to p[it & 1] by the row's warp; p.q
-// partials (slot kRrSlots + (it & 1)).  MODE 2: out = H^T H x.
-template <typename T, int MODE>
-__global__ void __launch_bounds__(kFitThreads) k_fit_spmv(FitDev F, const T *__restrict__ x, T *__restrict__ out,
-                                                         int it) {
-  pdl_trigger();
-  const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  const bool on = wid < F.n_act;
-  // the longest rows first, so that no late wave holds only long rows
-  const int row = on ? F.nrm_order[wid] : 0;
-  int beg = 0, end = 0;
-  if (on) {
-    beg = F.nrm_ptr[row];
-    end = F.nrm_ptr[row + 1];
-  }
-  pdl_wait();
-  const bool first = it == 0;
-  T beta = T(0);
-  if (MODE == 0 && !first) beta = T(fit_beta(F, it));
+// One row of H^T H against a vector: lane sums over kSpmvBatch entries at a
+// time (their columns, then their values and vector elements, are loaded
+// without dependences between them), then the warp's tree.  `elem(c)` gives the
+// vector element of column c.
+template <typename T, typename E>
+__device__ __forceinline__ T fit_row(const FitDev &F, int beg, int end, int lane, E elem) {
   const T *val = static_cast<const T *>(F.nrm_val);
-  const T *r = static_cast<const T *>(F.r), *pp = static_cast<const T *>(F.p[(it + 1) & 1]);
-  // kSpmvBatch entries per lane at a time: their columns, then their values and
-  // vector elements, are loaded without dependences between them
   T acc = T(0);
   for (int e0 = beg + lane; e0 < end; e0 += 32 * kSpmvBatch) {
     int c[kSpmvBatch];
@@ -310,58 +286,140 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_spmv(FitDev F, const T *__r
     for (int b = 0; b < kSpmvBatch; ++b) c[b] = e0 + 32 * b < end ? F.nrm_col[e0 + 32 * b] : -1;
 #pragma unroll
     for (int b = 0; b < kSpmvBatch; ++b)
-      if (c[b] >= 0) acc += val[e0 + 32 * b] * (MODE == 0 ? fit_dir(r, pp, c[b], first, beta) : x[c[b]]);
+      if (c[b] >= 0) acc += val[e0 + 32 * b] * elem(c[b]);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  Acc<T> d, z;
+  return acc;
+}
+
+// out = H^T H x: one warp per row, the longest rows first.
+template <typename T>
+__global__ void __launch_bounds__(kFitThreads) k_fit_spmv(FitDev F, const T *__restrict__ x, T *__restrict__ out) {
+  pdl_trigger();
+  const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (wid >= F.n_act) return;
+  const int4 d = F.nrm_desc[wid];
+  pdl_wait();
+  const T acc = fit_row<T>(F, d.y, d.z, lane, [&](int c) { return x[c]; });
+  if (lane == 0) out[d.x] = acc;
+}
+
+// CG iteration `it` of the fitting solve, with the update of iteration it - 1
+// folded in: for every column c, r(c) = r_prev(c) - alpha_prev q_prev(c) and
+// p(c) = r(c) + beta p_prev(c) (p = r, the initial residual, when it == 0),
+// formed on the fly, and q = H^T H p over the nonempty rows, one warp per row
+// with the longest rows first.  The row's warp stores r, p and q of its row
+// in the buffers of iteration it and adds alpha_prev p_prev to a.  Actuators
+// no sampling point reaches have empty rows and columns: their r, p and q
+// stay zero and a keeps its value.  Each block leaves its p.q, r.q and q.q
+// partials; the block that takes the last ticket sums them in block order
+// and stores alpha = r.r / p.q, r.r of iteration it + 1 from its recurrence
+// rr - 2 alpha r.q + alpha^2 q.q, and beta = r.r(it + 1) / r.r(it).  cold:
+// a starts from zero (written by the first iteration).
+template <typename T>
+__global__ void __launch_bounds__(kFitIterThreads, sizeof(T) == 4 ? 2 : 1)
+    k_fit_iter(FitDev F, T *__restrict__ a, int it, int cold) {
+  __shared__ double s_v[3][kFitIterThreads / 32];
+  pdl_trigger();
+  const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const bool on = wid < F.n_rows;
+  const int4 d = on ? F.nrm_desc[wid] : make_int4(0, 0, 0, 0);
+  pdl_wait();
+  const bool first = it == 0;
+  if (first && cold)
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < F.n_act; i += gridDim.x * blockDim.x) a[i] = T(0);
+  const int cur = it & 1, prev = (it + 1) & 1;
+  const T al = first ? T(0) : T(__ldcg(F.cg + prev)), beta = first ? T(0) : T(__ldcg(F.cg + 4 + cur));
+  const T *rp = static_cast<const T *>(F.r[first ? 0 : prev]), *qp = static_cast<const T *>(F.q[prev]),
+          *pp = static_cast<const T *>(F.p[prev]);
+  // r and p of iteration it at column c
+  auto rc = [&](int c) { return first ? rp[c] : fit_fma(-al, qp[c], rp[c]); };
+  auto pc = [&](int c) { return first ? rp[c] : fit_fma(beta, pp[c], fit_fma(-al, qp[c], rp[c])); };
+  T r_row = T(0), pp_row = T(0);
   if (on && lane == 0) {
-    if (MODE == 2) {
-      out[row] = acc;
-    } else {
-      const T pn = fit_dir(r, pp, row, first, beta);
-      static_cast<T *>(F.p[it & 1])[row] = pn;
-      static_cast<T *>(F.q)[row] = acc;
-      d.add_prod(pn, acc);
-    }
+    r_row = rc(d.x);
+    if (!first) pp_row = pp[d.x];
   }
-  if (MODE == 0) {
-    const double2 v = block_sum2(d, z);
-    if (threadIdx.x == 0) F.part[(kRrSlots + (it & 1)) * F.part_stride + blockIdx.x] = v.x;
+  const T acc = fit_row<T>(F, d.y, d.z, lane, pc);
+  double v0 = 0.0, v1 = 0.0, v2 = 0.0;
+  if (on && lane == 0) {
+    const T p_row = first ? r_row : fit_fma(beta, pp_row, r_row);
+    static_cast<T *>(F.p[cur])[d.x] = p_row;
+    static_cast<T *>(F.q[cur])[d.x] = acc;
+    if (!first) {
+      static_cast<T *>(F.r[cur])[d.x] = r_row;
+      a[d.x] = fit_fma(al, pp_row, a[d.x]);
+    }
+    v0 = double(p_row) * double(acc);
+    v1 = double(r_row) * double(acc);
+    v2 = double(acc) * double(acc);
+  }
+  const int w = threadIdx.x >> 5;
+  if (lane == 0) {
+    s_v[0][w] = v0;
+    s_v[1][w] = v1;
+    s_v[2][w] = v2;
+  }
+  __syncthreads();   // the block's row stores are ordered before warp 0's release below
+  if (w != 0) return;
+  const int nw = blockDim.x >> 5;
+  double x0 = lane < nw ? s_v[0][lane] : 0.0, x1 = lane < nw ? s_v[1][lane] : 0.0,
+         x2 = lane < nw ? s_v[2][lane] : 0.0;
+  x0 = warp_sum(x0);
+  x1 = warp_sum(x1);
+  x2 = warp_sum(x2);
+  unsigned ticket = 0;
+  if (lane == 0) {
+    double *pt = F.part + kPqSlot * F.part_stride + blockIdx.x;
+    pt[0] = x0;
+    pt[F.part_stride] = x1;
+    pt[2 * F.part_stride] = x2;
+    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;" : "=r"(ticket) : "l"(F.ticket) : "memory");
+  }
+  ticket = __shfl_sync(0xffffffffu, ticket, 0);
+  if (ticket != gridDim.x - 1) return;
+  __syncwarp();
+  // the last block: every block's partials, summed in block order (lane-strided, then the tree)
+  const int nb = gridDim.x;
+  const double *pq = F.part + kPqSlot * F.part_stride;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  for (int b = lane; b < nb; b += 32) {
+    s0 += __ldcg(pq + b);
+    s1 += __ldcg(pq + F.part_stride + b);
+    s2 += __ldcg(pq + 2 * F.part_stride + b);
+  }
+  if (first)
+    for (int b = lane; b < F.nblk_adj; b += 32) s3 += __ldcg(F.part + b);
+  s0 = warp_sum(s0);
+  s1 = warp_sum(s1);
+  s2 = warp_sum(s2);
+  s3 = warp_sum(s3);
+  if (lane == 0) {
+    const double rr = first ? s3 : __ldcg(F.cg + 2 + cur);
+    double alpha = 0.0;
+    if (s0 == 0.0 && rr == 0.0) {
+      alpha = 0.0;   // exact iterate: CG stops moving
+    } else if (!(s0 > 0.0) || !isfinite(rr / s0)) {
+      F.flag[0] = 1.0;
+    } else {
+      alpha = rr / s0;
+    }
+    const double rr_next = fmax(0.0, rr - 2.0 * alpha * s1 + alpha * alpha * s2);
+    F.cg[cur] = alpha;
+    F.cg[2 + prev] = rr_next;
+    F.cg[4 + prev] = rr != 0.0 ? rr_next / rr : 0.0;
+    *F.ticket = 0u;
   }
 }
 
-// alpha = r.r / p.q of iteration `it`; a += alpha p (a = alpha p when the
-// solve started from zero), r -= alpha q, r.r partials of iteration it + 1.
+// a += alpha p of the last CG iteration `it`.
 template <typename T>
-__global__ void __launch_bounds__(kFitThreads) k_fit_update(FitDev F, T *__restrict__ a, int it, int cold) {
+__global__ void __launch_bounds__(kFitThreads) k_fit_finish(FitDev F, T *__restrict__ a, int it) {
   pdl_trigger();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   pdl_wait();
-  int n_rr;
-  const double *p_rr = fit_rr_part(F, it, &n_rr);
-  const double2 sums = fit_sum2(p_rr, n_rr, F.part + (kRrSlots + (it & 1)) * F.part_stride, F.nblk_spmv);
-  const double rr = sums.x, pq = sums.y;
-  double alpha = 0.0;
-  if (pq == 0.0 && rr == 0.0) {
-    alpha = 0.0;   // exact iterate: CG stops moving
-  } else if (!(pq > 0.0) || !isfinite(rr / pq)) {
-    if (i == 0) F.flag[0] = 1.0;
-  } else {
-    alpha = rr / pq;
-  }
-  Acc<T> d, z;
-  if (i < F.n_act) {
-    const T al = T(alpha);
-    const T *p = static_cast<const T *>(F.p[it & 1]), *q = static_cast<const T *>(F.q);
-    T *r = static_cast<T *>(F.r);
-    a[i] = (cold && it == 0) ? al * p[i] : fit_fma(al, p[i], a[i]);
-    const T rn = fit_fma(-al, q[i], r[i]);
-    r[i] = rn;
-    d.add_prod(rn, rn);
-  }
-  const double2 v = block_sum2(d, z);
-  if (threadIdx.x == 0) F.part[((it + 1) % kRrSlots) * F.part_stride + blockIdx.x] = v.x;
+  if (i < F.n_act) a[i] = fit_fma(T(F.cg[it & 1]), static_cast<const T *>(F.p[it & 1])[i], a[i]);
 }
 
 // r(theta_j) of the residual u_j on the sampling points: the root mean square
@@ -488,10 +546,18 @@ cudaError_t fit_mirror(const FitDev &F, const T *x, const T *phi, cudaStream_t s
 }
 
 template <typename T>
-cudaError_t fit_spmv(int mode, const FitDev &F, const T *x, T *out, int it, cudaStream_t s) {
-  const dim3 g(F.nblk_spmv);
-  if (mode == 0) return launch_ex(k_fit_spmv<T, 0>, g, kFitThreads, 0, 0, s, F, x, out, it);
-  return launch_ex(k_fit_spmv<T, 2>, g, kFitThreads, 0, 0, s, F, x, out, it);
+cudaError_t fit_spmv(const FitDev &F, const T *x, T *out, cudaStream_t s) {
+  return launch_ex(k_fit_spmv<T>, dim3(F.nblk_spmv), kFitThreads, 0, 0, s, F, x, out);
+}
+
+template <typename T>
+cudaError_t fit_iter(const FitDev &F, T *a, int it, int cold, cudaStream_t s) {
+  return launch_ex(k_fit_iter<T>, dim3(F.nblk_iter), kFitIterThreads, 0, 0, s, F, a, it, cold);
+}
+
+template <typename T>
+cudaError_t fit_finish(const FitDev &F, T *a, int it, cudaStream_t s) {
+  return launch_ex(k_fit_finish<T>, dim3(F.nblk_upd), kFitThreads, 0, 0, s, F, a, it);
 }
 
 template <typename T, int KW>
@@ -523,11 +589,6 @@ template <typename T>
 cudaError_t polc_update(const FitDev &F, const T *a_tm1, const T *a_rec, const T *a_tm2, T *a_t, T gain,
                         cudaStream_t s) {
   return launch_ex(k_polc_update<T>, dim3(F.nblk_upd), kFitThreads, 0, 0, s, F, a_tm1, a_rec, a_tm2, a_t, gain);
-}
-
-template <typename T>
-cudaError_t fit_update(const FitDev &F, T *a, int it, int cold, cudaStream_t s) {
-  return launch_ex(k_fit_update<T>, dim3(F.nblk_upd), kFitThreads, 0, 0, s, F, a, it, cold);
 }
 
 }  // namespace tomo
@@ -599,7 +660,9 @@ struct FitTables {
   int kw = 0, n_points = 0;
   long long n_active = 0;
   // H^T H in CSR (FP64) and its rows by decreasing length
-  std::vector<int> nrm_ptr, nrm_col, nrm_order;
+  std::vector<int> nrm_ptr, nrm_col;
+  std::vector<int4> nrm_desc;
+  int n_rows = 0;
   std::vector<double> nrm_val;
   // A_hat: work items, per sensor and mirror the corner taps
   std::vector<int4> ms_items, sens, sens_off;
@@ -786,11 +849,20 @@ tomo_status build_tables(const tomo::HostPlan &H, const tomo_fit_geometry *g, Fi
       }
       T->nrm_ptr.push_back(static_cast<int>(T->nrm_col.size()));
     }
-    T->nrm_order.resize(n_act);
-    for (int i = 0; i < n_act; ++i) T->nrm_order[i] = i;
-    std::stable_sort(T->nrm_order.begin(), T->nrm_order.end(), [&](int a, int b) {
+    // rows by decreasing length, so that no late wave holds only long rows;
+    // the empty rows (actuators no sampling point reaches) come last
+    std::vector<int> order(n_act);
+    for (int i = 0; i < n_act; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
       return T->nrm_ptr[a + 1] - T->nrm_ptr[a] > T->nrm_ptr[b + 1] - T->nrm_ptr[b];
     });
+    T->nrm_desc.resize(n_act);
+    T->n_rows = 0;
+    for (int w = 0; w < n_act; ++w) {
+      const int i = order[w];
+      T->nrm_desc[w] = make_int4(i, T->nrm_ptr[i], T->nrm_ptr[i + 1], 0);
+      if (T->nrm_ptr[i + 1] > T->nrm_ptr[i]) ++T->n_rows;
+    }
   }
   // the mirrors on the plan's sensors: corner (a, b) of sensor m sees mirror k at
   // ((1 - h_k/H_m) r + theta_m h_k), cone factor 1 for a natural star
@@ -871,9 +943,12 @@ tomo_status enqueue_fit(tomo_fit *f, const void *layers, void *a, int iters, int
   FIT_CUDA(tomo::fit_adjoint<T>(1, F, nullptr, s), "fit residual gather");
   k += 2;
   for (int it = 0; it < iters; ++it) {
-    FIT_CUDA(tomo::fit_spmv<T>(0, F, nullptr, nullptr, it, s), "fit normal operator");
-    FIT_CUDA(tomo::fit_update<T>(F, av, it, warm ? 0 : 1, s), "fit update");
-    k += 2;
+    FIT_CUDA(tomo::fit_iter<T>(F, av, it, warm ? 0 : 1, s), "fit CG iteration");
+    ++k;
+  }
+  if (iters > 0) {
+    FIT_CUDA(tomo::fit_finish<T>(F, av, iters - 1, s), "fit last update");
+    ++k;
   }
   tomo::count_launches(k);
   *nk = k;
@@ -1037,7 +1112,9 @@ tomo_status tomo_fit_create(tomo_plan *p, const tomo_fit_geometry *g, tomo_fit *
   F.nblk_adj = static_cast<int>((4 * n_act + tomo::kFitThreads - 1) / tomo::kFitThreads);
   F.nblk_upd = static_cast<int>((n_act + tomo::kFitThreads - 1) / tomo::kFitThreads);
   F.nblk_spmv = static_cast<int>((32 * n_act + tomo::kFitThreads - 1) / tomo::kFitThreads);
-  F.part_stride = std::max(F.nblk_adj, std::max(F.nblk_upd, F.nblk_spmv));
+  F.n_rows = T.n_rows;
+  F.nblk_iter = std::max(1, (32 * T.n_rows + tomo::kFitIterThreads - 1) / tomo::kFitIterThreads);
+  F.part_stride = std::max(F.nblk_adj, F.nblk_iter);
   int off = 0, woff = 0;
   for (int k = 0; k < g->n_dm; ++k) {
     F.dm_n[k] = g->dms[k].n;
@@ -1052,7 +1129,7 @@ tomo_status tomo_fit_create(tomo_plan *p, const tomo_fit_geometry *g, tomo_fit *
   struct Item { size_t *off; size_t bytes; };
   size_t o_act, o_lay, o_hx0, o_hy0, o_hfx, o_hfy, o_px0, o_py0, o_pfx, o_pfy, o_wx0, o_wy0, o_wxw, o_wyw,
       o_msi, o_sens, o_soff, o_sidx, o_eidx, o_et, o_sx0, o_sy0, o_sfx, o_sfy, o_nptr, o_ncol, o_nval, o_nord, o_u, o_r,
-      o_p0, o_p1, o_q, o_phi, o_sol, o_part, o_flag;
+      o_r1, o_p0, o_p1, o_q, o_q1, o_phi, o_sol, o_part, o_cg, o_ticket, o_flag;
   const Item items[] = {
       {&o_act, T.act.size()},
       {&o_lay, T.lay.size() * sizeof(int2)},
@@ -1081,15 +1158,19 @@ tomo_status tomo_fit_create(tomo_plan *p, const tomo_fit_geometry *g, tomo_fit *
       {&o_nptr, T.nrm_ptr.size() * sizeof(int)},
       {&o_ncol, T.nrm_col.size() * sizeof(int)},
       {&o_nval, T.nrm_val.size() * es},
-      {&o_nord, T.nrm_order.size() * sizeof(int)},
+      {&o_nord, T.nrm_desc.size() * sizeof(int4)},
       {&o_u, static_cast<size_t>(nd) * nc * nc * es},
       {&o_r, n_act * es},
+      {&o_r1, n_act * es},
       {&o_p0, n_act * es},
       {&o_p1, n_act * es},
       {&o_q, n_act * es},
+      {&o_q1, n_act * es},
       {&o_phi, static_cast<size_t>(H.n) * es},
       {&o_sol, static_cast<size_t>(H.n_slopes) * es},
-      {&o_part, static_cast<size_t>(tomo::kRrSlots + 2) * F.part_stride * sizeof(double)},
+      {&o_part, static_cast<size_t>(4) * F.part_stride * sizeof(double)},
+      {&o_cg, 6 * sizeof(double)},
+      {&o_ticket, sizeof(unsigned)},
       {&o_flag, sizeof(double)},
   };
   size_t total = 0;
@@ -1109,7 +1190,7 @@ tomo_status tomo_fit_create(tomo_plan *p, const tomo_fit_geometry *g, tomo_fit *
   std::memcpy(img.data() + o_wy0, T.wy0.data(), T.wy0.size() * sizeof(int));
   std::memcpy(img.data() + o_nptr, T.nrm_ptr.data(), T.nrm_ptr.size() * sizeof(int));
   std::memcpy(img.data() + o_ncol, T.nrm_col.data(), T.nrm_col.size() * sizeof(int));
-  std::memcpy(img.data() + o_nord, T.nrm_order.data(), T.nrm_order.size() * sizeof(int));
+  std::memcpy(img.data() + o_nord, T.nrm_desc.data(), T.nrm_desc.size() * sizeof(int4));
   std::memcpy(img.data() + o_msi, T.ms_items.data(), T.ms_items.size() * sizeof(int4));
   std::memcpy(img.data() + o_sens, T.sens.data(), T.sens.size() * sizeof(int4));
   std::memcpy(img.data() + o_soff, T.sens_off.data(), T.sens_off.size() * sizeof(int4));
@@ -1165,16 +1246,20 @@ tomo_status tomo_fit_create(tomo_plan *p, const tomo_fit_geometry *g, tomo_fit *
   F.sfy = base + o_sfy;
   F.s_ol = base + o_sol;
   F.u = base + o_u;
-  F.r = base + o_r;
+  F.r[0] = base + o_r;
+  F.r[1] = base + o_r1;
   F.p[0] = base + o_p0;
   F.p[1] = base + o_p1;
   F.nrm_ptr = reinterpret_cast<const int *>(base + o_nptr);
   F.nrm_col = reinterpret_cast<const int *>(base + o_ncol);
   F.nrm_val = base + o_nval;
-  F.nrm_order = reinterpret_cast<const int *>(base + o_nord);
-  F.q = base + o_q;
+  F.nrm_desc = reinterpret_cast<const int4 *>(base + o_nord);
+  F.q[0] = base + o_q;
+  F.q[1] = base + o_q1;
   f->phi = base + o_phi;
   F.part = reinterpret_cast<double *>(base + o_part);
+  F.cg = reinterpret_cast<double *>(base + o_cg);
+  F.ticket = reinterpret_cast<unsigned *>(base + o_ticket);
   F.flag = reinterpret_cast<double *>(base + o_flag);
   *out = f;
   return TOMO_OK;
@@ -1187,14 +1272,14 @@ tomo_status tomo_fit_get_info(const tomo_fit *f, tomo_fit_info *out) {
   out->n_points = f->n_points;
   out->n_dir = f->F.n_dir;
   out->n_dm = f->F.n_dm;
-  out->kernels_per_iteration = 2;
-  out->kernels_per_solve_base = 2;
+  out->kernels_per_iteration = 1;
+  out->kernels_per_solve_base = 3;
   out->device_bytes = static_cast<long long>(f->arena_bytes);
   out->normal_nonzeros = f->nnz;
-  // SpMV: every entry and its column, the row starts, p and r read, p and q written;
-  // update: a, p, q, r read, a and r written
+  // every entry and its column, a row descriptor per nonempty row, r, q, p of the previous
+  // iteration read, r, q, p of this one written, a read and written
   const long long na = f->F.n_act, es = static_cast<long long>(f->esz);
-  out->bytes_per_iteration = f->nnz * (es + 4) + 4 * (na + 1) + 4 * na * es + 6 * na * es;
+  out->bytes_per_iteration = f->nnz * (es + 4) + 16LL * f->F.n_rows + 8 * na * es;
   return TOMO_OK;
 }
 
@@ -1203,10 +1288,10 @@ tomo_status tomo_fit_apply_normal(tomo_fit *f, const void *d_a, void *d_out, voi
   tomo::DeviceGuard dg(f->device);
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   if (f->precision == 0)
-    FIT_CUDA(tomo::fit_spmv<float>(2, f->F, static_cast<const float *>(d_a), static_cast<float *>(d_out), 0, s),
+    FIT_CUDA(tomo::fit_spmv<float>(f->F, static_cast<const float *>(d_a), static_cast<float *>(d_out), s),
              "fit normal operator");
   else
-    FIT_CUDA(tomo::fit_spmv<double>(2, f->F, static_cast<const double *>(d_a), static_cast<double *>(d_out), 0, s),
+    FIT_CUDA(tomo::fit_spmv<double>(f->F, static_cast<const double *>(d_a), static_cast<double *>(d_out), s),
              "fit normal operator");
   tomo::count_launches(1);
   return TOMO_OK;
