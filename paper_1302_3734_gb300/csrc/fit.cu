@@ -8,17 +8,17 @@
 // function of its actuator grid; P_j phi (x) = sum_l phi_l(x + h_l theta_j)
 // (eq. ngsproj), bilinear on the periodic layer grids; x runs over the corners
 // of the valid subapertures of the aperture sampling grid.  H^T H is constant:
-// it is assembled once on the host (FP64, CSR) and each CG iteration is one
-// kernel:
+// it is assembled once on the host (FP64, CSR) and each CG iteration is two
+// kernels:
 //
-//   k_fit_iter     iteration it: r = r - alpha q and p = r + beta p of the
-//                  previous iteration's alpha and this one's beta, formed on
-//                  the fly for every column, and q = H^T H p [warp per nonempty
-//                  row; the row's warp stores its r, p, q and a += alpha p];
-//                  p.q, r.q and q.q partials per block; the block that takes
-//                  the last ticket sums them and leaves alpha, r.r of the next
-//                  iteration (rr - 2 alpha r.q + alpha^2 q.q) and beta
-//   k_fit_finish   a += alpha p of the last iteration        [actuator per thread]
+//   k_fit_form     the update of the previous iteration and the new direction:
+//                  a += alpha p, r -= alpha q, p = r + beta p  [actuator per thread]
+//   k_fit_iter     q = H^T H p [warp per nonempty row] and p.q, r.q, q.q
+//                  partials per block; the block that takes the last ticket
+//                  sums them and leaves alpha, r.r of the next iteration
+//                  (rr - 2 alpha r.q + alpha^2 q.q) and beta
+//
+// and k_fit_finish applies the last iteration's a += alpha p.
 //
 // The right-hand side and the initial residual stay matrix-free:
 //
@@ -56,14 +56,13 @@ constexpr int kFitIterThreads = 1024;   // k_fit_iter: 32 rows per block; the la
 constexpr int kFitRmsThreads = 1024;
 constexpr int kMaxDm = 4;
 constexpr int kMaxFitDirs = 256;
-constexpr int kPqSlot = 1;    // partial slots: 0 r.r of the initial residual, 1-3 p.q, r.q, q.q of k_fit_iter
 constexpr int kFitDirBatch = 4;   // directions whose gather loads one thread issues together
 constexpr int kSpmvBatch = 4;     // matrix entries whose loads one lane issues together (fit_row)
 
 // Everything the fitting kernels read (passed by value).
 struct FitDev {
   int n_dir, n_dm, nc, n_layers;
-  int n_act, kw, nblk_adj, nblk_upd, part_stride, n_points, n_rows;
+  int n_act, kw, nblk_adj, nblk_upd, n_points, n_rows;
   int dm_n[kMaxDm], dm_off[kMaxDm], w_off[kMaxDm];
   const unsigned char *act;   // nc*nc corner mask
   const int2 *lay;            // per layer (N, offset in the layer vector)
@@ -74,15 +73,14 @@ struct FitDev {
   const int *wx0, *wy0;       // per (dm, dir, actuator column / row): first corner of its window
   const void *wxw, *wyw;      //   kw weights (T), zero beyond the window
   void *u;                    // [dir][nc*nc]
-  void *r[2], *q[2], *p[2];   // [n_act]: residual, H^T H p and direction of CG iteration it in
-                              // [it & 1] (the initial residual in r[0])
+  void *r, *q, *p;            // [n_act]: the CG residual, H^T H p and direction
   const int *nrm_ptr;         // H^T H in CSR: row starts (n_act + 1), columns, values (T)
-  const int *nrm_col;
-  const void *nrm_val;
+  const void *nrm_cv;         // entries (column, value): int and float (8 B), or int, 0 and double (16 B)
   const int4 *nrm_desc;       // (row, first entry, end, 0) by decreasing row length: warp w takes
                               // desc[w]; the n_rows nonempty rows come first
   int nblk_spmv, nblk_iter;
-  double *part;               // 4 * part_stride
+  double *part;               // r.r partials of the initial residual
+  double *rec;                // per k_fit_iter block: p.q, r.q, q.q, 0
   double *cg;                 // CG scalars of iteration it: alpha in cg[it & 1], r.r in cg[2 + (it & 1)],
                               // beta in cg[4 + (it & 1)]
   unsigned *ticket;           // blocks of k_fit_iter done; reset by the last one
@@ -142,6 +140,18 @@ __device__ __forceinline__ double fit_fma(double a, double b, double c) { return
 template <typename T>
 __device__ __forceinline__ T fit_dir(const T *r, const T *p, int i, bool first, T beta) {
   return first ? r[i] : fit_fma(beta, p[i], r[i]);
+}
+
+// One (column, value) entry of H^T H.
+__device__ __forceinline__ void fit_entry(const void *cv, int e, int &c, float &w) {
+  const int2 x = static_cast<const int2 *>(cv)[e];
+  c = x.x;
+  w = __int_as_float(x.y);
+}
+__device__ __forceinline__ void fit_entry(const void *cv, int e, int &c, double &w) {
+  const int4 x = static_cast<const int4 *>(cv)[e];
+  c = x.x;
+  w = __hiloint2double(x.w, x.z);
 }
 
 // u_j = P_j phi - H_j x on every (direction, corner); phi = NULL: no layers,
@@ -262,7 +272,7 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_adjoint(FitDev F, T *__rest
     if (MODE == 2) {
       out[act] = s;
     } else {
-      static_cast<T *>(F.r[0])[act] = s;
+      static_cast<T *>(F.r)[act] = s;
       d.add_prod(s, s);
     }
   }
@@ -278,15 +288,19 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_adjoint(FitDev F, T *__rest
 // vector element of column c.
 template <typename T, typename E>
 __device__ __forceinline__ T fit_row(const FitDev &F, int beg, int end, int lane, E elem) {
-  const T *val = static_cast<const T *>(F.nrm_val);
   T acc = T(0);
   for (int e0 = beg + lane; e0 < end; e0 += 32 * kSpmvBatch) {
     int c[kSpmvBatch];
+    T w[kSpmvBatch];
 #pragma unroll
-    for (int b = 0; b < kSpmvBatch; ++b) c[b] = e0 + 32 * b < end ? F.nrm_col[e0 + 32 * b] : -1;
+    for (int b = 0; b < kSpmvBatch; ++b) {
+      c[b] = -1;
+      w[b] = T(0);
+      if (e0 + 32 * b < end) fit_entry(F.nrm_cv, e0 + 32 * b, c[b], w[b]);
+    }
 #pragma unroll
     for (int b = 0; b < kSpmvBatch; ++b)
-      if (c[b] >= 0) acc += val[e0 + 32 * b] * elem(c[b]);
+      if (c[b] >= 0) acc += w[b] * elem(c[b]);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -305,98 +319,116 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_spmv(FitDev F, const T *__r
   if (lane == 0) out[d.x] = acc;
 }
 
-// CG iteration `it` of the fitting solve, with the update of iteration it - 1
-// folded in: for every column c, r(c) = r_prev(c) - alpha_prev q_prev(c) and
-// p(c) = r(c) + beta p_prev(c) (p = r, the initial residual, when it == 0),
-// formed on the fly, and q = H^T H p over the nonempty rows, one warp per row
-// with the longest rows first.  The row's warp stores r, p and q of its row
-// in the buffers of iteration it and adds alpha_prev p_prev to a.  Actuators
-// no sampling point reaches have empty rows and columns: their r, p and q
-// stay zero and a keeps its value.  Each block leaves its p.q, r.q and q.q
-// partials; the block that takes the last ticket sums them in block order
-// and stores alpha = r.r / p.q, r.r of iteration it + 1 from its recurrence
-// rr - 2 alpha r.q + alpha^2 q.q, and beta = r.r(it + 1) / r.r(it).  cold:
-// a starts from zero (written by the first iteration).
+// The update of CG iteration it - 1 and the direction of iteration it, per
+// actuator: a += alpha p, r -= alpha q, p = r + beta p (it == 0: p = r, and
+// a = 0 from a cold start).  alpha of it - 1 and beta of it come from the
+// last k_fit_iter block.
 template <typename T>
-__global__ void __launch_bounds__(kFitIterThreads, sizeof(T) == 4 ? 2 : 1)
-    k_fit_iter(FitDev F, T *__restrict__ a, int it, int cold) {
-  __shared__ double s_v[3][kFitIterThreads / 32];
+__global__ void __launch_bounds__(kFitThreads) k_fit_form(FitDev F, T *__restrict__ a, int it, int cold) {
   pdl_trigger();
-  const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  pdl_wait();
+  if (i >= F.n_act) return;
+  T *r = static_cast<T *>(F.r), *p = static_cast<T *>(F.p);
+  if (it == 0) {
+    p[i] = r[i];
+    if (cold) a[i] = T(0);
+    return;
+  }
+  const T al = T(F.cg[(it + 1) & 1]), beta = T(F.cg[4 + (it & 1)]);
+  const T p_i = p[i], r_i = fit_fma(-al, static_cast<const T *>(F.q)[i], r[i]);
+  a[i] = fit_fma(al, p_i, a[i]);
+  r[i] = r_i;
+  p[i] = fit_fma(beta, p_i, r_i);
+}
+
+// q = H^T H p of CG iteration `it` over the nonempty rows, one warp per row
+// with the longest rows first (actuators no sampling point reaches have empty
+// rows and columns: their r, p and q stay zero).  Each block leaves a
+// (p.q, r.q, q.q) record; the block that takes the last ticket sums them in
+// block order and stores alpha = r.r / p.q, r.r of iteration it + 1 from its
+// recurrence rr - 2 alpha r.q + alpha^2 q.q, and beta = r.r(it + 1) / r.r(it)
+// (r.r of iteration 0 from the initial residual's partials).
+template <typename T>
+__global__ void __launch_bounds__(kFitIterThreads, sizeof(T) == 4 ? 2 : 1) k_fit_iter(FitDev F, int it) {
+  __shared__ double s_v[4][kFitIterThreads / 32];
+  __shared__ int s_last;
+  pdl_trigger();
+  const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const bool on = wid < F.n_rows;
   const int4 d = on ? F.nrm_desc[wid] : make_int4(0, 0, 0, 0);
   pdl_wait();
   const bool first = it == 0;
-  if (first && cold)
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < F.n_act; i += gridDim.x * blockDim.x) a[i] = T(0);
   const int cur = it & 1, prev = (it + 1) & 1;
-  const T al = first ? T(0) : T(__ldcg(F.cg + prev)), beta = first ? T(0) : T(__ldcg(F.cg + 4 + cur));
-  const T *rp = static_cast<const T *>(F.r[first ? 0 : prev]), *qp = static_cast<const T *>(F.q[prev]),
-          *pp = static_cast<const T *>(F.p[prev]);
-  // r and p of iteration it at column c
-  auto rc = [&](int c) { return first ? rp[c] : fit_fma(-al, qp[c], rp[c]); };
-  auto pc = [&](int c) { return first ? rp[c] : fit_fma(beta, pp[c], fit_fma(-al, qp[c], rp[c])); };
-  T r_row = T(0), pp_row = T(0);
+  const T *p = static_cast<const T *>(F.p);
+  T r_row = T(0), p_row = T(0);
   if (on && lane == 0) {
-    r_row = rc(d.x);
-    if (!first) pp_row = pp[d.x];
+    r_row = static_cast<const T *>(F.r)[d.x];
+    p_row = p[d.x];
   }
-  const T acc = fit_row<T>(F, d.y, d.z, lane, pc);
+  const T acc = fit_row<T>(F, d.y, d.z, lane, [&](int c) { return p[c]; });
   double v0 = 0.0, v1 = 0.0, v2 = 0.0;
   if (on && lane == 0) {
-    const T p_row = first ? r_row : fit_fma(beta, pp_row, r_row);
-    static_cast<T *>(F.p[cur])[d.x] = p_row;
-    static_cast<T *>(F.q[cur])[d.x] = acc;
-    if (!first) {
-      static_cast<T *>(F.r[cur])[d.x] = r_row;
-      a[d.x] = fit_fma(al, pp_row, a[d.x]);
-    }
+    static_cast<T *>(F.q)[d.x] = acc;
     v0 = double(p_row) * double(acc);
     v1 = double(r_row) * double(acc);
     v2 = double(acc) * double(acc);
   }
-  const int w = threadIdx.x >> 5;
   if (lane == 0) {
     s_v[0][w] = v0;
     s_v[1][w] = v1;
     s_v[2][w] = v2;
   }
-  __syncthreads();   // the block's row stores are ordered before warp 0's release below
-  if (w != 0) return;
+  __syncthreads();   // the block's row stores are ordered before thread 0's release below
   const int nw = blockDim.x >> 5;
-  double x0 = lane < nw ? s_v[0][lane] : 0.0, x1 = lane < nw ? s_v[1][lane] : 0.0,
-         x2 = lane < nw ? s_v[2][lane] : 0.0;
-  x0 = warp_sum(x0);
-  x1 = warp_sum(x1);
-  x2 = warp_sum(x2);
-  unsigned ticket = 0;
-  if (lane == 0) {
-    double *pt = F.part + kPqSlot * F.part_stride + blockIdx.x;
-    pt[0] = x0;
-    pt[F.part_stride] = x1;
-    pt[2 * F.part_stride] = x2;
-    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;" : "=r"(ticket) : "l"(F.ticket) : "memory");
+  if (w == 0) {
+    double x0 = lane < nw ? s_v[0][lane] : 0.0, x1 = lane < nw ? s_v[1][lane] : 0.0,
+           x2 = lane < nw ? s_v[2][lane] : 0.0;
+    x0 = warp_sum(x0);
+    x1 = warp_sum(x1);
+    x2 = warp_sum(x2);
+    if (lane == 0) {
+      double2 *rec = reinterpret_cast<double2 *>(F.rec) + 2 * blockIdx.x;
+      rec[0] = make_double2(x0, x1);
+      rec[1] = make_double2(x2, 0.0);
+      unsigned ticket;
+      asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;" : "=r"(ticket) : "l"(F.ticket) : "memory");
+      s_last = ticket == gridDim.x - 1;
+    }
   }
-  ticket = __shfl_sync(0xffffffffu, ticket, 0);
-  if (ticket != gridDim.x - 1) return;
-  __syncwarp();
-  // the last block: every block's partials, summed in block order (lane-strided, then the tree)
-  const int nb = gridDim.x;
-  const double *pq = F.part + kPqSlot * F.part_stride;
+  __syncthreads();   // orders the last block's loads below after thread 0's acquire
+  if (!s_last) return;
+  // the last block: the blocks' records (and at it == 0 the initial residual's
+  // r.r partials), each thread a strided subset, then the warps in order
+  const double rr_prev = first ? 0.0 : __ldcg(F.cg + 2 + cur);
   double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-  for (int b = lane; b < nb; b += 32) {
-    s0 += __ldcg(pq + b);
-    s1 += __ldcg(pq + F.part_stride + b);
-    s2 += __ldcg(pq + 2 * F.part_stride + b);
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+    const double2 x = __ldcg(reinterpret_cast<const double2 *>(F.rec) + 2 * b);
+    s0 += x.x;
+    s1 += x.y;
+    s2 += __ldcg(F.rec + 4 * b + 2);
   }
   if (first)
-    for (int b = lane; b < F.nblk_adj; b += 32) s3 += __ldcg(F.part + b);
+    for (int b = threadIdx.x; b < F.nblk_adj; b += blockDim.x) s3 += __ldcg(F.part + b);
   s0 = warp_sum(s0);
   s1 = warp_sum(s1);
   s2 = warp_sum(s2);
   s3 = warp_sum(s3);
+  __syncthreads();   // s_v is reused
   if (lane == 0) {
-    const double rr = first ? s3 : __ldcg(F.cg + 2 + cur);
+    s_v[0][w] = s0;
+    s_v[1][w] = s1;
+    s_v[2][w] = s2;
+    s_v[3][w] = s3;
+  }
+  __syncthreads();
+  if (w != 0) return;
+  s0 = warp_sum(lane < nw ? s_v[0][lane] : 0.0);
+  s1 = warp_sum(lane < nw ? s_v[1][lane] : 0.0);
+  s2 = warp_sum(lane < nw ? s_v[2][lane] : 0.0);
+  s3 = warp_sum(lane < nw ? s_v[3][lane] : 0.0);
+  if (lane == 0) {
+    const double rr = first ? s3 : rr_prev;
     double alpha = 0.0;
     if (s0 == 0.0 && rr == 0.0) {
       alpha = 0.0;   // exact iterate: CG stops moving
@@ -419,7 +451,7 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_finish(FitDev F, T *__restr
   pdl_trigger();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   pdl_wait();
-  if (i < F.n_act) a[i] = fit_fma(T(F.cg[it & 1]), static_cast<const T *>(F.p[it & 1])[i], a[i]);
+  if (i < F.n_act) a[i] = fit_fma(T(F.cg[it & 1]), static_cast<const T *>(F.p)[i], a[i]);
 }
 
 // r(theta_j) of the residual u_j on the sampling points: the root mean square
@@ -551,8 +583,13 @@ cudaError_t fit_spmv(const FitDev &F, const T *x, T *out, cudaStream_t s) {
 }
 
 template <typename T>
-cudaError_t fit_iter(const FitDev &F, T *a, int it, int cold, cudaStream_t s) {
-  return launch_ex(k_fit_iter<T>, dim3(F.nblk_iter), kFitIterThreads, 0, 0, s, F, a, it, cold);
+cudaError_t fit_iter(const FitDev &F, int it, cudaStream_t s) {
+  return launch_ex(k_fit_iter<T>, dim3(F.nblk_iter), kFitIterThreads, 0, 0, s, F, it);
+}
+
+template <typename T>
+cudaError_t fit_form(const FitDev &F, T *a, int it, int cold, cudaStream_t s) {
+  return launch_ex(k_fit_form<T>, dim3(F.nblk_upd), kFitThreads, 0, 0, s, F, a, it, cold);
 }
 
 template <typename T>
@@ -943,11 +980,12 @@ tomo_status enqueue_fit(tomo_fit *f, const void *layers, void *a, int iters, int
   FIT_CUDA(tomo::fit_adjoint<T>(1, F, nullptr, s), "fit residual gather");
   k += 2;
   for (int it = 0; it < iters; ++it) {
-    FIT_CUDA(tomo::fit_iter<T>(F, av, it, warm ? 0 : 1, s), "fit CG iteration");
-    ++k;
+    FIT_CUDA(tomo::fit_form<T>(F, av, it, warm ? 0 : 1, s), "fit CG direction");
+    FIT_CUDA(tomo::fit_iter<T>(F, it, s), "fit normal operator");
+    k += 2;
   }
   if (iters > 0) {
-    FIT_CUDA(tomo::fit_finish<T>(F, av, iters - 1, s), "fit last update");
+    FIT_CUDA(tomo::fit_finish<T>(F, av, iters - 1, s), "fit commands");
     ++k;
   }
   tomo::count_launches(k);
@@ -1114,7 +1152,6 @@ tomo_status tomo_fit_create(tomo_plan *p, const tomo_fit_geometry *g, tomo_fit *
   F.nblk_spmv = static_cast<int>((32 * n_act + tomo::kFitThreads - 1) / tomo::kFitThreads);
   F.n_rows = T.n_rows;
   F.nblk_iter = std::max(1, (32 * T.n_rows + tomo::kFitIterThreads - 1) / tomo::kFitIterThreads);
-  F.part_stride = std::max(F.nblk_adj, F.nblk_iter);
   int off = 0, woff = 0;
   for (int k = 0; k < g->n_dm; ++k) {
     F.dm_n[k] = g->dms[k].n;
@@ -1128,8 +1165,8 @@ tomo_status tomo_fit_create(tomo_plan *p, const tomo_fit_geometry *g, tomo_fit *
   const size_t es = f->esz;
   struct Item { size_t *off; size_t bytes; };
   size_t o_act, o_lay, o_hx0, o_hy0, o_hfx, o_hfy, o_px0, o_py0, o_pfx, o_pfy, o_wx0, o_wy0, o_wxw, o_wyw,
-      o_msi, o_sens, o_soff, o_sidx, o_eidx, o_et, o_sx0, o_sy0, o_sfx, o_sfy, o_nptr, o_ncol, o_nval, o_nord, o_u, o_r,
-      o_r1, o_p0, o_p1, o_q, o_q1, o_phi, o_sol, o_part, o_cg, o_ticket, o_flag;
+      o_msi, o_sens, o_soff, o_sidx, o_eidx, o_et, o_sx0, o_sy0, o_sfx, o_sfy, o_nptr, o_ncv, o_nord, o_u, o_r,
+      o_p, o_q, o_phi, o_sol, o_part, o_rec, o_cg, o_ticket, o_flag;
   const Item items[] = {
       {&o_act, T.act.size()},
       {&o_lay, T.lay.size() * sizeof(int2)},
@@ -1156,19 +1193,16 @@ tomo_status tomo_fit_create(tomo_plan *p, const tomo_fit_geometry *g, tomo_fit *
       {&o_sfx, T.sfx.size() * es},
       {&o_sfy, T.sfy.size() * es},
       {&o_nptr, T.nrm_ptr.size() * sizeof(int)},
-      {&o_ncol, T.nrm_col.size() * sizeof(int)},
-      {&o_nval, T.nrm_val.size() * es},
+      {&o_ncv, T.nrm_col.size() * 2 * es},
       {&o_nord, T.nrm_desc.size() * sizeof(int4)},
       {&o_u, static_cast<size_t>(nd) * nc * nc * es},
       {&o_r, n_act * es},
-      {&o_r1, n_act * es},
-      {&o_p0, n_act * es},
-      {&o_p1, n_act * es},
+      {&o_p, n_act * es},
       {&o_q, n_act * es},
-      {&o_q1, n_act * es},
       {&o_phi, static_cast<size_t>(H.n) * es},
       {&o_sol, static_cast<size_t>(H.n_slopes) * es},
-      {&o_part, static_cast<size_t>(4) * F.part_stride * sizeof(double)},
+      {&o_part, static_cast<size_t>(F.nblk_adj) * sizeof(double)},
+      {&o_rec, static_cast<size_t>(F.nblk_iter) * 4 * sizeof(double)},
       {&o_cg, 6 * sizeof(double)},
       {&o_ticket, sizeof(unsigned)},
       {&o_flag, sizeof(double)},
@@ -1189,7 +1223,18 @@ tomo_status tomo_fit_create(tomo_plan *p, const tomo_fit_geometry *g, tomo_fit *
   std::memcpy(img.data() + o_wx0, T.wx0.data(), T.wx0.size() * sizeof(int));
   std::memcpy(img.data() + o_wy0, T.wy0.data(), T.wy0.size() * sizeof(int));
   std::memcpy(img.data() + o_nptr, T.nrm_ptr.data(), T.nrm_ptr.size() * sizeof(int));
-  std::memcpy(img.data() + o_ncol, T.nrm_col.data(), T.nrm_col.size() * sizeof(int));
+  // (column, value) entries of H^T H
+  for (size_t e = 0; e < T.nrm_col.size(); ++e) {
+    unsigned char *at = img.data() + o_ncv + e * 2 * es;
+    std::memcpy(at, &T.nrm_col[e], sizeof(int));
+    if (f->precision) {
+      const double v = T.nrm_val[e];
+      std::memcpy(at + 8, &v, sizeof(double));
+    } else {
+      const float v = static_cast<float>(T.nrm_val[e]);
+      std::memcpy(at + 4, &v, sizeof(float));
+    }
+  }
   std::memcpy(img.data() + o_nord, T.nrm_desc.data(), T.nrm_desc.size() * sizeof(int4));
   std::memcpy(img.data() + o_msi, T.ms_items.data(), T.ms_items.size() * sizeof(int4));
   std::memcpy(img.data() + o_sens, T.sens.data(), T.sens.size() * sizeof(int4));
@@ -1200,7 +1245,7 @@ tomo_status tomo_fit_create(tomo_plan *p, const tomo_fit_geometry *g, tomo_fit *
   std::memcpy(img.data() + o_sy0, T.sy0.data(), T.sy0.size() * sizeof(int));
   const std::pair<size_t, const std::vector<double> *> reals[] = {
       {o_hfx, &T.hfx}, {o_hfy, &T.hfy}, {o_pfx, &T.pfx}, {o_pfy, &T.pfy}, {o_wxw, &T.wxw}, {o_wyw, &T.wyw},
-      {o_sfx, &T.sfx}, {o_sfy, &T.sfy}, {o_et, &H.edge_t}, {o_nval, &T.nrm_val}};
+      {o_sfx, &T.sfx}, {o_sfy, &T.sfy}, {o_et, &H.edge_t}};
   for (const auto &rv : reals) {
     if (f->precision) put<double>(img, rv.first, *rv.second);
     else put<float>(img, rv.first, *rv.second);
@@ -1246,18 +1291,15 @@ tomo_status tomo_fit_create(tomo_plan *p, const tomo_fit_geometry *g, tomo_fit *
   F.sfy = base + o_sfy;
   F.s_ol = base + o_sol;
   F.u = base + o_u;
-  F.r[0] = base + o_r;
-  F.r[1] = base + o_r1;
-  F.p[0] = base + o_p0;
-  F.p[1] = base + o_p1;
+  F.r = base + o_r;
+  F.p = base + o_p;
+  F.q = base + o_q;
   F.nrm_ptr = reinterpret_cast<const int *>(base + o_nptr);
-  F.nrm_col = reinterpret_cast<const int *>(base + o_ncol);
-  F.nrm_val = base + o_nval;
+  F.nrm_cv = base + o_ncv;
   F.nrm_desc = reinterpret_cast<const int4 *>(base + o_nord);
-  F.q[0] = base + o_q;
-  F.q[1] = base + o_q1;
   f->phi = base + o_phi;
   F.part = reinterpret_cast<double *>(base + o_part);
+  F.rec = reinterpret_cast<double *>(base + o_rec);
   F.cg = reinterpret_cast<double *>(base + o_cg);
   F.ticket = reinterpret_cast<unsigned *>(base + o_ticket);
   F.flag = reinterpret_cast<double *>(base + o_flag);
@@ -1272,14 +1314,14 @@ tomo_status tomo_fit_get_info(const tomo_fit *f, tomo_fit_info *out) {
   out->n_points = f->n_points;
   out->n_dir = f->F.n_dir;
   out->n_dm = f->F.n_dm;
-  out->kernels_per_iteration = 1;
+  out->kernels_per_iteration = 2;
   out->kernels_per_solve_base = 3;
   out->device_bytes = static_cast<long long>(f->arena_bytes);
   out->normal_nonzeros = f->nnz;
-  // every entry and its column, a row descriptor per nonempty row, r, q, p of the previous
-  // iteration read, r, q, p of this one written, a read and written
+  // k_fit_form: a, p, q, r read, a, r, p written; k_fit_iter: every entry and its
+  // column, a row descriptor per nonempty row, p and r read, q written
   const long long na = f->F.n_act, es = static_cast<long long>(f->esz);
-  out->bytes_per_iteration = f->nnz * (es + 4) + 16LL * f->F.n_rows + 8 * na * es;
+  out->bytes_per_iteration = 7 * na * es + f->nnz * (es + 4) + 16LL * f->F.n_rows + 3 * na * es;
   return TOMO_OK;
 }
 
