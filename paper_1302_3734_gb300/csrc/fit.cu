@@ -80,7 +80,7 @@ struct FitDev {
                               // desc[w]; the n_rows nonempty rows come first
   int nblk_spmv, nblk_iter;
   double *part;               // r.r partials of the initial residual
-  double *rec;                // per k_fit_iter block: p.q, r.q, q.q, 0
+  double *rec;                // per k_fit_iter block (32 B): p.q, r.q, q.q as FP32 pairs or FP64
   double *cg;                 // CG scalars of iteration it: alpha in cg[it & 1], r.r in cg[2 + (it & 1)],
                               // beta in cg[4 + (it & 1)]
   unsigned *ticket;           // blocks of k_fit_iter done; reset by the last one
@@ -141,6 +141,31 @@ template <typename T>
 __device__ __forceinline__ T fit_dir(const T *r, const T *p, int i, bool first, T beta) {
   return first ? r[i] : fit_fma(beta, p[i], r[i]);
 }
+
+// Accumulators in shared memory and in the k_fit_iter block records: an FP32
+// pair (hi, lo) for FP32, an FP64 value for FP64; sums over a warp leave the
+// result in lane 0.
+template <typename T>
+struct AccIO;
+template <>
+struct AccIO<float> {
+  using S = float2;
+  static __device__ __forceinline__ S pack(const Acc<float> &a) { return make_float2(a.hi, a.lo); }
+  static __device__ __forceinline__ void add(Acc<float> &a, S v) { a.merge(v.x, v.y); }
+  static __device__ __forceinline__ void add_double(Acc<float> &a, double v) {
+    const float hi = __double2float_rn(v);
+    a.merge(hi, __double2float_rn(v - double(hi)));
+  }
+  static __device__ __forceinline__ void warp(Acc<float> &a) { warp_merge_down(a); }
+};
+template <>
+struct AccIO<double> {
+  using S = double;
+  static __device__ __forceinline__ S pack(const Acc<double> &a) { return a.s; }
+  static __device__ __forceinline__ void add(Acc<double> &a, S v) { a.s += v; }
+  static __device__ __forceinline__ void add_double(Acc<double> &a, double v) { a.s += v; }
+  static __device__ __forceinline__ void warp(Acc<double> &a) { a.s = warp_sum(a.s); }
+};
 
 // One (column, value) entry of H^T H.
 __device__ __forceinline__ void fit_entry(const void *cv, int e, int &c, float &w) {
@@ -351,7 +376,7 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_form(FitDev F, T *__restric
 // (r.r of iteration 0 from the initial residual's partials).
 template <typename T>
 __global__ void __launch_bounds__(kFitIterThreads, sizeof(T) == 4 ? 2 : 1) k_fit_iter(FitDev F, int it) {
-  __shared__ double s_v[4][kFitIterThreads / 32];
+  __shared__ typename AccIO<T>::S s_v[4][kFitIterThreads / 32];
   __shared__ int s_last;
   pdl_trigger();
   const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -367,30 +392,37 @@ __global__ void __launch_bounds__(kFitIterThreads, sizeof(T) == 4 ? 2 : 1) k_fit
     p_row = p[d.x];
   }
   const T acc = fit_row<T>(F, d.y, d.z, lane, [&](int c) { return p[c]; });
-  double v0 = 0.0, v1 = 0.0, v2 = 0.0;
+  // lane 0 of each warp holds its row's terms; sums in FP32 pairs (FP64 arithmetic is slow here)
+  using IO = AccIO<T>;
+  Acc<T> a0, a1, a2;
   if (on && lane == 0) {
     static_cast<T *>(F.q)[d.x] = acc;
-    v0 = double(p_row) * double(acc);
-    v1 = double(r_row) * double(acc);
-    v2 = double(acc) * double(acc);
+    a0.add_prod(p_row, acc);
+    a1.add_prod(r_row, acc);
+    a2.add_prod(acc, acc);
   }
   if (lane == 0) {
-    s_v[0][w] = v0;
-    s_v[1][w] = v1;
-    s_v[2][w] = v2;
+    s_v[0][w] = IO::pack(a0);
+    s_v[1][w] = IO::pack(a1);
+    s_v[2][w] = IO::pack(a2);
   }
   __syncthreads();   // the block's row stores are ordered before thread 0's release below
   const int nw = blockDim.x >> 5;
   if (w == 0) {
-    double x0 = lane < nw ? s_v[0][lane] : 0.0, x1 = lane < nw ? s_v[1][lane] : 0.0,
-           x2 = lane < nw ? s_v[2][lane] : 0.0;
-    x0 = warp_sum(x0);
-    x1 = warp_sum(x1);
-    x2 = warp_sum(x2);
+    Acc<T> x0, x1, x2;
+    if (lane < nw) {
+      IO::add(x0, s_v[0][lane]);
+      IO::add(x1, s_v[1][lane]);
+      IO::add(x2, s_v[2][lane]);
+    }
+    IO::warp(x0);
+    IO::warp(x1);
+    IO::warp(x2);
     if (lane == 0) {
-      double2 *rec = reinterpret_cast<double2 *>(F.rec) + 2 * blockIdx.x;
-      rec[0] = make_double2(x0, x1);
-      rec[1] = make_double2(x2, 0.0);
+      typename IO::S *rec = reinterpret_cast<typename IO::S *>(F.rec) + 4 * blockIdx.x;
+      rec[0] = IO::pack(x0);
+      rec[1] = IO::pack(x1);
+      rec[2] = IO::pack(x2);
       unsigned ticket;
       asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;" : "=r"(ticket) : "l"(F.ticket) : "memory");
       s_last = ticket == gridDim.x - 1;
@@ -399,36 +431,48 @@ __global__ void __launch_bounds__(kFitIterThreads, sizeof(T) == 4 ? 2 : 1) k_fit
   __syncthreads();   // orders the last block's loads below after thread 0's acquire
   if (!s_last) return;
   // the last block: the blocks' records (and at it == 0 the initial residual's
-  // r.r partials), each thread a strided subset, then the warps in order
+  // r.r partials), each thread a strided subset, then the warps in order; only
+  // the warps that hold some take part in the first stage
   const double rr_prev = first ? 0.0 : __ldcg(F.cg + 2 + cur);
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-    const double2 x = __ldcg(reinterpret_cast<const double2 *>(F.rec) + 2 * b);
-    s0 += x.x;
-    s1 += x.y;
-    s2 += __ldcg(F.rec + 4 * b + 2);
+  const int nb = gridDim.x, n_in = max(nb, first ? F.nblk_adj : 0);
+  Acc<T> x0, x1, x2, x3;
+  if (w * 32 < n_in) {
+    const typename IO::S *rec = reinterpret_cast<const typename IO::S *>(F.rec);
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+      IO::add(x0, __ldcg(rec + 4 * b));
+      IO::add(x1, __ldcg(rec + 4 * b + 1));
+      IO::add(x2, __ldcg(rec + 4 * b + 2));
+    }
+    if (first)
+      for (int b = threadIdx.x; b < F.nblk_adj; b += blockDim.x) IO::add_double(x3, __ldcg(F.part + b));
+    IO::warp(x0);
+    IO::warp(x1);
+    IO::warp(x2);
+    IO::warp(x3);
   }
-  if (first)
-    for (int b = threadIdx.x; b < F.nblk_adj; b += blockDim.x) s3 += __ldcg(F.part + b);
-  s0 = warp_sum(s0);
-  s1 = warp_sum(s1);
-  s2 = warp_sum(s2);
-  s3 = warp_sum(s3);
   __syncthreads();   // s_v is reused
   if (lane == 0) {
-    s_v[0][w] = s0;
-    s_v[1][w] = s1;
-    s_v[2][w] = s2;
-    s_v[3][w] = s3;
+    s_v[0][w] = IO::pack(x0);
+    s_v[1][w] = IO::pack(x1);
+    s_v[2][w] = IO::pack(x2);
+    s_v[3][w] = IO::pack(x3);
   }
   __syncthreads();
   if (w != 0) return;
-  s0 = warp_sum(lane < nw ? s_v[0][lane] : 0.0);
-  s1 = warp_sum(lane < nw ? s_v[1][lane] : 0.0);
-  s2 = warp_sum(lane < nw ? s_v[2][lane] : 0.0);
-  s3 = warp_sum(lane < nw ? s_v[3][lane] : 0.0);
+  Acc<T> y0, y1, y2, y3;
+  if (lane < nw) {
+    IO::add(y0, s_v[0][lane]);
+    IO::add(y1, s_v[1][lane]);
+    IO::add(y2, s_v[2][lane]);
+    IO::add(y3, s_v[3][lane]);
+  }
+  IO::warp(y0);
+  IO::warp(y1);
+  IO::warp(y2);
+  IO::warp(y3);
   if (lane == 0) {
-    const double rr = first ? s3 : rr_prev;
+    const double s0 = y0.value(), s1 = y1.value(), s2 = y2.value();
+    const double rr = first ? y3.value() : rr_prev;
     double alpha = 0.0;
     if (s0 == 0.0 && rr == 0.0) {
       alpha = 0.0;   // exact iterate: CG stops moving
