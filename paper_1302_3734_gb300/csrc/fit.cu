@@ -12,7 +12,8 @@
 // kernels:
 //
 //   k_fit_form     the update of the previous iteration and the new direction:
-//                  a += alpha p, r -= alpha q, p = r + beta p  [actuator per thread]
+//                  a += alpha p, r -= alpha q, p = r + beta p  [actuator per thread;
+//                  not in the first iteration, whose direction is r itself]
 //   k_fit_iter     q = H^T H p [warp per nonempty row] and p.q, r.q, q.q
 //                  partials per block; the block that takes the last ticket
 //                  sums them and leaves alpha, r.r of the next iteration
@@ -344,10 +345,11 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_spmv(FitDev F, const T *__r
   if (lane == 0) out[d.x] = acc;
 }
 
-// The update of CG iteration it - 1 and the direction of iteration it, per
-// actuator: a += alpha p, r -= alpha q, p = r + beta p (it == 0: p = r, and
-// a = 0 from a cold start).  alpha of it - 1 and beta of it come from the
-// last k_fit_iter block.
+// The update of CG iteration it - 1 and the direction of iteration it >= 1,
+// per actuator: a += alpha p (a = alpha p from a cold start when it == 1),
+// r -= alpha q, p = r + beta p.  The direction of iteration 0 is the initial
+// residual r itself.  alpha of it - 1 and beta of it come from the last
+// k_fit_iter block.
 template <typename T>
 __global__ void __launch_bounds__(kFitThreads) k_fit_form(FitDev F, T *__restrict__ a, int it, int cold) {
   pdl_trigger();
@@ -355,14 +357,9 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_form(FitDev F, T *__restric
   pdl_wait();
   if (i >= F.n_act) return;
   T *r = static_cast<T *>(F.r), *p = static_cast<T *>(F.p);
-  if (it == 0) {
-    p[i] = r[i];
-    if (cold) a[i] = T(0);
-    return;
-  }
   const T al = T(F.cg[(it + 1) & 1]), beta = T(F.cg[4 + (it & 1)]);
-  const T p_i = p[i], r_i = fit_fma(-al, static_cast<const T *>(F.q)[i], r[i]);
-  a[i] = fit_fma(al, p_i, a[i]);
+  const T p_i = it == 1 ? r[i] : p[i], r_i = fit_fma(-al, static_cast<const T *>(F.q)[i], r[i]);
+  a[i] = (cold && it == 1) ? al * p_i : fit_fma(al, p_i, a[i]);
   r[i] = r_i;
   p[i] = fit_fma(beta, p_i, r_i);
 }
@@ -385,7 +382,7 @@ __global__ void __launch_bounds__(kFitIterThreads, sizeof(T) == 4 ? 2 : 1) k_fit
   pdl_wait();
   const bool first = it == 0;
   const int cur = it & 1, prev = (it + 1) & 1;
-  const T *p = static_cast<const T *>(F.p);
+  const T *p = static_cast<const T *>(first ? F.r : F.p);   // p = r in iteration 0
   T r_row = T(0), p_row = T(0);
   if (on && lane == 0) {
     r_row = static_cast<const T *>(F.r)[d.x];
@@ -489,13 +486,16 @@ __global__ void __launch_bounds__(kFitIterThreads, sizeof(T) == 4 ? 2 : 1) k_fit
   }
 }
 
-// a += alpha p of the last CG iteration `it`.
+// a += alpha p of the last CG iteration `it` (a = alpha p from a cold start
+// when it == 0; the direction of iteration 0 is r).
 template <typename T>
-__global__ void __launch_bounds__(kFitThreads) k_fit_finish(FitDev F, T *__restrict__ a, int it) {
+__global__ void __launch_bounds__(kFitThreads) k_fit_finish(FitDev F, T *__restrict__ a, int it, int cold) {
   pdl_trigger();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   pdl_wait();
-  if (i < F.n_act) a[i] = fit_fma(T(F.cg[it & 1]), static_cast<const T *>(F.p)[i], a[i]);
+  if (i >= F.n_act) return;
+  const T al = T(F.cg[it & 1]), p_i = static_cast<const T *>(it == 0 ? F.r : F.p)[i];
+  a[i] = (cold && it == 0) ? al * p_i : fit_fma(al, p_i, a[i]);
 }
 
 // r(theta_j) of the residual u_j on the sampling points: the root mean square
@@ -637,8 +637,8 @@ cudaError_t fit_form(const FitDev &F, T *a, int it, int cold, cudaStream_t s) {
 }
 
 template <typename T>
-cudaError_t fit_finish(const FitDev &F, T *a, int it, cudaStream_t s) {
-  return launch_ex(k_fit_finish<T>, dim3(F.nblk_upd), kFitThreads, 0, 0, s, F, a, it);
+cudaError_t fit_finish(const FitDev &F, T *a, int it, int cold, cudaStream_t s) {
+  return launch_ex(k_fit_finish<T>, dim3(F.nblk_upd), kFitThreads, 0, 0, s, F, a, it, cold);
 }
 
 template <typename T, int KW>
@@ -1024,12 +1024,15 @@ tomo_status enqueue_fit(tomo_fit *f, const void *layers, void *a, int iters, int
   FIT_CUDA(tomo::fit_adjoint<T>(1, F, nullptr, s), "fit residual gather");
   k += 2;
   for (int it = 0; it < iters; ++it) {
-    FIT_CUDA(tomo::fit_form<T>(F, av, it, warm ? 0 : 1, s), "fit CG direction");
+    if (it > 0) {
+      FIT_CUDA(tomo::fit_form<T>(F, av, it, warm ? 0 : 1, s), "fit CG direction");
+      ++k;
+    }
     FIT_CUDA(tomo::fit_iter<T>(F, it, s), "fit normal operator");
-    k += 2;
+    ++k;
   }
   if (iters > 0) {
-    FIT_CUDA(tomo::fit_finish<T>(F, av, iters - 1, s), "fit commands");
+    FIT_CUDA(tomo::fit_finish<T>(F, av, iters - 1, warm ? 0 : 1, s), "fit commands");
     ++k;
   }
   tomo::count_launches(k);
@@ -1358,8 +1361,10 @@ tomo_status tomo_fit_get_info(const tomo_fit *f, tomo_fit_info *out) {
   out->n_points = f->n_points;
   out->n_dir = f->F.n_dir;
   out->n_dm = f->F.n_dm;
+  // 2 + 2 iters launches: the first iteration has no k_fit_form, the last one is
+  // followed by k_fit_finish
   out->kernels_per_iteration = 2;
-  out->kernels_per_solve_base = 3;
+  out->kernels_per_solve_base = 2;
   out->device_bytes = static_cast<long long>(f->arena_bytes);
   out->normal_nonzeros = f->nnz;
   // k_fit_form: a, p, q, r read, a, r, p written; k_fit_iter: every entry and its
