@@ -14,10 +14,11 @@
 //   k_fit_form     the update of the previous iteration and the new direction:
 //                  a += alpha p, r -= alpha q, p = r + beta p  [actuator per thread;
 //                  not in the first iteration, whose direction is r itself]
-//   k_fit_iter     q = H^T H p [warp per nonempty row] and p.q, r.q, q.q
+//   k_fit_iter     q = H^T H p [warp per nonempty row] and p.q, r.q, q.q, r.r
 //                  partials per block; the block that takes the last ticket
-//                  sums them and leaves alpha, r.r of the next iteration
-//                  (rr - 2 alpha r.q + alpha^2 q.q) and beta
+//                  sums them and leaves alpha = r.r / p.q and beta of the next
+//                  iteration, its r.r taken from the recurrence
+//                  rr - 2 alpha r.q + alpha^2 q.q
 //
 // and k_fit_finish applies the last iteration's a += alpha p.
 //
@@ -25,7 +26,7 @@
 //
 //   k_fit_mirror   u_j = P_j phi - H_j a on every (direction, corner)  [corner per thread]
 //   k_fit_adjoint  r = sum_j H_j^T u_j as a gather over per-actuator tap
-//                  windows; r.r partials                            [4 threads per actuator]
+//                  windows                                          [4 threads per actuator]
 //
 // The tap tables (corner -> actuator and corner -> layer node, and for H^T
 // each actuator's window of corners with its weights) are built in FP64 on
@@ -80,10 +81,8 @@ struct FitDev {
   const int4 *nrm_desc;       // (row, first entry, end, 0) by decreasing row length: warp w takes
                               // desc[w]; the n_rows nonempty rows come first
   int nblk_spmv, nblk_iter;
-  double *part;               // r.r partials of the initial residual
-  double *rec;                // per k_fit_iter block (32 B): p.q, r.q, q.q as FP32 pairs or FP64
-  double *cg;                 // CG scalars of iteration it: alpha in cg[it & 1], r.r in cg[2 + (it & 1)],
-                              // beta in cg[4 + (it & 1)]
+  double *rec;                // per k_fit_iter block (32 B): p.q, r.q, q.q, r.r as FP32 pairs or FP64
+  double *cg;                 // CG scalars of iteration it: alpha in cg[it & 1], beta in cg[2 + (it & 1)]
   unsigned *ticket;           // blocks of k_fit_iter done; reset by the last one
   double *flag;               // nonzero after a breakdown
   // the mirrors seen by the plan's sensors (A_hat)
@@ -101,47 +100,8 @@ struct FitDev {
   void *s_ol;                 // pseudo-open-loop slopes (the plan's slope layout)
 };
 
-// Fixed-order sums of two arrays of FP64 partials (n1 and n2 of them),
-// returned to every thread of the block: each thread adds a strided subset,
-// then the warps' sums are added in warp order.
-__device__ double2 fit_sum2(const double *p1, int n1, const double *p2, int n2) {
-  __shared__ double s_w[2][32];
-  __shared__ double2 s_v;
-  double a = 0.0, b = 0.0;
-  for (int i = threadIdx.x; i < n1; i += blockDim.x) a += __ldcg(p1 + i);
-  for (int i = threadIdx.x; i < n2; i += blockDim.x) b += __ldcg(p2 + i);
-  a = warp_sum(a);
-  b = warp_sum(b);
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) {
-    s_w[0][w] = a;
-    s_w[1][w] = b;
-  }
-  __syncthreads();
-  if (w == 0) {
-    const int nw = blockDim.x >> 5;
-    double x = lane < nw ? s_w[0][lane] : 0.0, y = lane < nw ? s_w[1][lane] : 0.0;
-    x = warp_sum(x);
-    y = warp_sum(y);
-    if (lane == 0) s_v = make_double2(x, y);
-  }
-  __syncthreads();
-  return s_v;
-}
-
-template <typename T>
-struct T2 {
-  T x, y;
-};
-
 __device__ __forceinline__ float fit_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fit_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
-
-// CG direction of actuator i: p = r (first iteration) or r + beta p.
-template <typename T>
-__device__ __forceinline__ T fit_dir(const T *r, const T *p, int i, bool first, T beta) {
-  return first ? r[i] : fit_fma(beta, p[i], r[i]);
-}
 
 // Accumulators in shared memory and in the k_fit_iter block records: an FP32
 // pair (hi, lo) for FP32, an FP64 value for FP64; sums over a warp leave the
@@ -278,8 +238,7 @@ __device__ __forceinline__ T fit_gather(const FitDev &F, int k, int i, int jj, i
   return s;
 }
 
-// MODE 1 (initial residual): r = H^T u, r.r partials (slot 0).
-// MODE 2: out = H^T u.
+// MODE 1 (initial residual): r = H^T u.  MODE 2: out = H^T u.
 template <typename T, int MODE, int KW>
 __global__ void __launch_bounds__(kFitThreads) k_fit_adjoint(FitDev F, T *__restrict__ out) {
   pdl_trigger();
@@ -293,19 +252,7 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_adjoint(FitDev F, T *__rest
   pdl_wait();
   // idle lanes take part in the shuffles with an empty direction loop
   const T s = on ? fit_gather<T, KW>(F, k, i, jj, g) : fit_gather<T, KW>(F, 0, 0, 0, F.n_dir);
-  Acc<T> d, z;
-  if (on && g == 0) {
-    if (MODE == 2) {
-      out[act] = s;
-    } else {
-      static_cast<T *>(F.r)[act] = s;
-      d.add_prod(s, s);
-    }
-  }
-  if (MODE == 1) {
-    const double2 v = block_sum2(d, z);
-    if (threadIdx.x == 0) F.part[blockIdx.x] = v.x;
-  }
+  if (on && g == 0) (MODE == 2 ? out : static_cast<T *>(F.r))[act] = s;
 }
 
 // One row of H^T H against a vector: lane sums over kSpmvBatch entries at a
@@ -357,7 +304,7 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_form(FitDev F, T *__restric
   pdl_wait();
   if (i >= F.n_act) return;
   T *r = static_cast<T *>(F.r), *p = static_cast<T *>(F.p);
-  const T al = T(F.cg[(it + 1) & 1]), beta = T(F.cg[4 + (it & 1)]);
+  const T al = T(F.cg[(it + 1) & 1]), beta = T(F.cg[2 + (it & 1)]);
   const T p_i = it == 1 ? r[i] : p[i], r_i = fit_fma(-al, static_cast<const T *>(F.q)[i], r[i]);
   a[i] = (cold && it == 1) ? al * p_i : fit_fma(al, p_i, a[i]);
   r[i] = r_i;
@@ -367,10 +314,12 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_form(FitDev F, T *__restric
 // q = H^T H p of CG iteration `it` over the nonempty rows, one warp per row
 // with the longest rows first (actuators no sampling point reaches have empty
 // rows and columns: their r, p and q stay zero).  Each block leaves a
-// (p.q, r.q, q.q) record; the block that takes the last ticket sums them in
-// block order and stores alpha = r.r / p.q, r.r of iteration it + 1 from its
-// recurrence rr - 2 alpha r.q + alpha^2 q.q, and beta = r.r(it + 1) / r.r(it)
-// (r.r of iteration 0 from the initial residual's partials).
+// (p.q, r.q, q.q, r.r) record; the block that takes the last ticket sums them
+// in block order and stores alpha = r.r / p.q and beta = r.r(it + 1) /
+// r.r(it).  r.r(it + 1) comes from the recurrence rr - 2 alpha r.q +
+// alpha^2 q.q, since the next direction needs beta before r(it + 1) exists;
+// alpha takes the norm of the stored residual, so an iterate that is already
+// exact (r = 0) stops moving.
 template <typename T>
 __global__ void __launch_bounds__(kFitIterThreads, sizeof(T) == 4 ? 2 : 1) k_fit_iter(FitDev F, int it) {
   __shared__ typename AccIO<T>::S s_v[4][kFitIterThreads / 32];
@@ -391,35 +340,40 @@ __global__ void __launch_bounds__(kFitIterThreads, sizeof(T) == 4 ? 2 : 1) k_fit
   const T acc = fit_row<T>(F, d.y, d.z, lane, [&](int c) { return p[c]; });
   // lane 0 of each warp holds its row's terms; sums in FP32 pairs (FP64 arithmetic is slow here)
   using IO = AccIO<T>;
-  Acc<T> a0, a1, a2;
+  Acc<T> a0, a1, a2, a3;
   if (on && lane == 0) {
     static_cast<T *>(F.q)[d.x] = acc;
     a0.add_prod(p_row, acc);
     a1.add_prod(r_row, acc);
     a2.add_prod(acc, acc);
+    a3.add_prod(r_row, r_row);
   }
   if (lane == 0) {
     s_v[0][w] = IO::pack(a0);
     s_v[1][w] = IO::pack(a1);
     s_v[2][w] = IO::pack(a2);
+    s_v[3][w] = IO::pack(a3);
   }
   __syncthreads();   // the block's row stores are ordered before thread 0's release below
   const int nw = blockDim.x >> 5;
   if (w == 0) {
-    Acc<T> x0, x1, x2;
+    Acc<T> x0, x1, x2, x3;
     if (lane < nw) {
       IO::add(x0, s_v[0][lane]);
       IO::add(x1, s_v[1][lane]);
       IO::add(x2, s_v[2][lane]);
+      IO::add(x3, s_v[3][lane]);
     }
     IO::warp(x0);
     IO::warp(x1);
     IO::warp(x2);
+    IO::warp(x3);
     if (lane == 0) {
       typename IO::S *rec = reinterpret_cast<typename IO::S *>(F.rec) + 4 * blockIdx.x;
       rec[0] = IO::pack(x0);
       rec[1] = IO::pack(x1);
       rec[2] = IO::pack(x2);
+      rec[3] = IO::pack(x3);
       unsigned ticket;
       asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;" : "=r"(ticket) : "l"(F.ticket) : "memory");
       s_last = ticket == gridDim.x - 1;
@@ -427,21 +381,18 @@ __global__ void __launch_bounds__(kFitIterThreads, sizeof(T) == 4 ? 2 : 1) k_fit
   }
   __syncthreads();   // orders the last block's loads below after thread 0's acquire
   if (!s_last) return;
-  // the last block: the blocks' records (and at it == 0 the initial residual's
-  // r.r partials), each thread a strided subset, then the warps in order; only
-  // the warps that hold some take part in the first stage
-  const double rr_prev = first ? 0.0 : __ldcg(F.cg + 2 + cur);
-  const int nb = gridDim.x, n_in = max(nb, first ? F.nblk_adj : 0);
+  // the last block: the blocks' records, each thread a strided subset, then
+  // the warps in order; only the warps that hold some take part in the first stage
+  const int nb = gridDim.x;
   Acc<T> x0, x1, x2, x3;
-  if (w * 32 < n_in) {
+  if (w * 32 < nb) {
     const typename IO::S *rec = reinterpret_cast<const typename IO::S *>(F.rec);
     for (int b = threadIdx.x; b < nb; b += blockDim.x) {
       IO::add(x0, __ldcg(rec + 4 * b));
       IO::add(x1, __ldcg(rec + 4 * b + 1));
       IO::add(x2, __ldcg(rec + 4 * b + 2));
+      IO::add(x3, __ldcg(rec + 4 * b + 3));
     }
-    if (first)
-      for (int b = threadIdx.x; b < F.nblk_adj; b += blockDim.x) IO::add_double(x3, __ldcg(F.part + b));
     IO::warp(x0);
     IO::warp(x1);
     IO::warp(x2);
@@ -469,7 +420,7 @@ __global__ void __launch_bounds__(kFitIterThreads, sizeof(T) == 4 ? 2 : 1) k_fit
   IO::warp(y3);
   if (lane == 0) {
     const double s0 = y0.value(), s1 = y1.value(), s2 = y2.value();
-    const double rr = first ? y3.value() : rr_prev;
+    const double rr = y3.value();
     double alpha = 0.0;
     if (s0 == 0.0 && rr == 0.0) {
       alpha = 0.0;   // exact iterate: CG stops moving
@@ -480,8 +431,7 @@ __global__ void __launch_bounds__(kFitIterThreads, sizeof(T) == 4 ? 2 : 1) k_fit
     }
     const double rr_next = fmax(0.0, rr - 2.0 * alpha * s1 + alpha * alpha * s2);
     F.cg[cur] = alpha;
-    F.cg[2 + prev] = rr_next;
-    F.cg[4 + prev] = rr != 0.0 ? rr_next / rr : 0.0;
+    F.cg[2 + prev] = rr != 0.0 ? rr_next / rr : 0.0;
     *F.ticket = 0u;
   }
 }
@@ -1213,7 +1163,7 @@ tomo_status tomo_fit_create(tomo_plan *p, const tomo_fit_geometry *g, tomo_fit *
   struct Item { size_t *off; size_t bytes; };
   size_t o_act, o_lay, o_hx0, o_hy0, o_hfx, o_hfy, o_px0, o_py0, o_pfx, o_pfy, o_wx0, o_wy0, o_wxw, o_wyw,
       o_msi, o_sens, o_soff, o_sidx, o_eidx, o_et, o_sx0, o_sy0, o_sfx, o_sfy, o_nptr, o_ncv, o_nord, o_u, o_r,
-      o_p, o_q, o_phi, o_sol, o_part, o_rec, o_cg, o_ticket, o_flag;
+      o_p, o_q, o_phi, o_sol, o_rec, o_cg, o_ticket, o_flag;
   const Item items[] = {
       {&o_act, T.act.size()},
       {&o_lay, T.lay.size() * sizeof(int2)},
@@ -1248,9 +1198,8 @@ tomo_status tomo_fit_create(tomo_plan *p, const tomo_fit_geometry *g, tomo_fit *
       {&o_q, n_act * es},
       {&o_phi, static_cast<size_t>(H.n) * es},
       {&o_sol, static_cast<size_t>(H.n_slopes) * es},
-      {&o_part, static_cast<size_t>(F.nblk_adj) * sizeof(double)},
       {&o_rec, static_cast<size_t>(F.nblk_iter) * 4 * sizeof(double)},
-      {&o_cg, 6 * sizeof(double)},
+      {&o_cg, 4 * sizeof(double)},
       {&o_ticket, sizeof(unsigned)},
       {&o_flag, sizeof(double)},
   };
@@ -1345,7 +1294,6 @@ tomo_status tomo_fit_create(tomo_plan *p, const tomo_fit_geometry *g, tomo_fit *
   F.nrm_cv = base + o_ncv;
   F.nrm_desc = reinterpret_cast<const int4 *>(base + o_nord);
   f->phi = base + o_phi;
-  F.part = reinterpret_cast<double *>(base + o_part);
   F.rec = reinterpret_cast<double *>(base + o_rec);
   F.cg = reinterpret_cast<double *>(base + o_cg);
   F.ticket = reinterpret_cast<unsigned *>(base + o_ticket);

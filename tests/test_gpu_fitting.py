@@ -219,3 +219,26 @@ def test_normal_matrix_entries_match_the_brute_force_pattern(lib, name):
     assert fit.info.bytes_per_iteration > fit.info.normal_nonzeros * (8 if g["precision"] else 4)
     fit.close()
     plan.close()
+
+
+def test_solve_that_converges_in_one_iteration_stays_put(lib):
+    """One mirror on the sampling points, seen from one direction: H^T H is the
+    identity on the reached actuators, so CG is exact after one iteration.  The
+    later iterations must leave the commands where they are (r = 0 gives
+    alpha = 0), however many are asked for."""
+    torch, pkg = lib
+    g = _single()
+    plan = pkg.Plan(g)
+    fit = pkg.Fit(plan, g["fitting"])
+    ora = Fitting(g)
+    tom = Tomography(g)
+    phis = tom.synthesis(np.random.default_rng(19).standard_normal(tom.n))
+    layers = torch.tensor(tom.join(phis), dtype=plan.dtype, device="cuda")
+    b_ref = ora.rhs(phis)
+    for iters in (1, 2, 12):
+        x = torch.full((ora.n,), float("nan"), dtype=plan.dtype, device="cuda")
+        fit.solve(layers, x, iters, warm=False)
+        e = rel(x.double().cpu().numpy(), ora.cg(b_ref, np.zeros(ora.n), iters), f"fit-exact-iterate/{iters}")
+        assert e < 1e-5, (iters, e)
+    fit.close()
+    plan.close()
