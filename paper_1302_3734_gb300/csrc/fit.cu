@@ -31,10 +31,10 @@
 // The tap tables (corner -> actuator and corner -> layer node, and for H^T
 // each actuator's window of corners with its weights) are built in FP64 on
 // the host from the same corner -> actuator taps, so the gather is the exact
-// transpose of the mirror kernel.  Inner products are accumulated as in the
-// tomography kernels (double-float per thread for FP32, one FP64 partial per
-// block, partials summed in a fixed order), so results are bitwise
-// reproducible.
+// transpose of the mirror kernel.  Inner products are accumulated in a fixed
+// order, so results are bitwise reproducible: for FP32 in double-float pairs
+// (per thread, per block record and in the sums of the records), since FP64
+// arithmetic is slow on this part.
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -76,9 +76,9 @@ struct FitDev {
   const void *wxw, *wyw;      //   kw weights (T), zero beyond the window
   void *u;                    // [dir][nc*nc]
   void *r, *q, *p;            // [n_act]: the CG residual, H^T H p and direction
-  const int *nrm_ptr;         // H^T H in CSR: row starts (n_act + 1), columns, values (T)
-  const void *nrm_cv;         // entries (column, value): int and float (8 B), or int, 0 and double (16 B)
-  const int4 *nrm_desc;       // (row, first entry, end, 0) by decreasing row length: warp w takes
+  const void *nrm_cv;         // H^T H in CSR, its entries (column, value): int and float (8 B), or int,
+                              // 0 and double (16 B)
+  const int4 *nrm_desc;       // its rows (row, first entry, end, 0) by decreasing length: warp w takes
                               // desc[w]; the n_rows nonempty rows come first
   int nblk_spmv, nblk_iter;
   double *rec;                // per k_fit_iter block (32 B): p.q, r.q, q.q, r.r as FP32 pairs or FP64
@@ -1162,7 +1162,7 @@ tomo_status tomo_fit_create(tomo_plan *p, const tomo_fit_geometry *g, tomo_fit *
   const size_t es = f->esz;
   struct Item { size_t *off; size_t bytes; };
   size_t o_act, o_lay, o_hx0, o_hy0, o_hfx, o_hfy, o_px0, o_py0, o_pfx, o_pfy, o_wx0, o_wy0, o_wxw, o_wyw,
-      o_msi, o_sens, o_soff, o_sidx, o_eidx, o_et, o_sx0, o_sy0, o_sfx, o_sfy, o_nptr, o_ncv, o_nord, o_u, o_r,
+      o_msi, o_sens, o_soff, o_sidx, o_eidx, o_et, o_sx0, o_sy0, o_sfx, o_sfy, o_ncv, o_nord, o_u, o_r,
       o_p, o_q, o_phi, o_sol, o_rec, o_cg, o_ticket, o_flag;
   const Item items[] = {
       {&o_act, T.act.size()},
@@ -1189,7 +1189,6 @@ tomo_status tomo_fit_create(tomo_plan *p, const tomo_fit_geometry *g, tomo_fit *
       {&o_sy0, T.sy0.size() * sizeof(int)},
       {&o_sfx, T.sfx.size() * es},
       {&o_sfy, T.sfy.size() * es},
-      {&o_nptr, T.nrm_ptr.size() * sizeof(int)},
       {&o_ncv, T.nrm_col.size() * 2 * es},
       {&o_nord, T.nrm_desc.size() * sizeof(int4)},
       {&o_u, static_cast<size_t>(nd) * nc * nc * es},
@@ -1218,7 +1217,6 @@ tomo_status tomo_fit_create(tomo_plan *p, const tomo_fit_geometry *g, tomo_fit *
   std::memcpy(img.data() + o_py0, T.py0.data(), T.py0.size() * sizeof(int));
   std::memcpy(img.data() + o_wx0, T.wx0.data(), T.wx0.size() * sizeof(int));
   std::memcpy(img.data() + o_wy0, T.wy0.data(), T.wy0.size() * sizeof(int));
-  std::memcpy(img.data() + o_nptr, T.nrm_ptr.data(), T.nrm_ptr.size() * sizeof(int));
   // (column, value) entries of H^T H
   for (size_t e = 0; e < T.nrm_col.size(); ++e) {
     unsigned char *at = img.data() + o_ncv + e * 2 * es;
@@ -1290,7 +1288,6 @@ tomo_status tomo_fit_create(tomo_plan *p, const tomo_fit_geometry *g, tomo_fit *
   F.r = base + o_r;
   F.p = base + o_p;
   F.q = base + o_q;
-  F.nrm_ptr = reinterpret_cast<const int *>(base + o_nptr);
   F.nrm_cv = base + o_ncv;
   F.nrm_desc = reinterpret_cast<const int4 *>(base + o_nord);
   f->phi = base + o_phi;
