@@ -82,6 +82,7 @@ extern "C" tomo_status tomo_jacobi_diagonal_noalloc(const tomo_plan *p, double a
                             reinterpret_cast<const int *>(sb + b_prof),
                             reinterpret_cast<const double *>(sb + b_prof + b_off), d_out, nullptr,
                             H.precision, p->nc_max, alpha, s);
+  if (e == cudaSuccess) tomo::count_launches(1);
   if (prev >= 0 && prev != p->device) cudaSetDevice(prev);
   if (e != cudaSuccess)
     return set_error(TOMO_ERR_CUDA, std::string("tomo_jacobi_diagonal_noalloc: ") + cudaGetErrorString(e));
