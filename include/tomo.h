@@ -121,8 +121,10 @@ typedef struct {
   long long device_bytes;      /* device memory held by the plan */
   long long bytes_per_iteration; /* algorithmic bytes of one PCG iteration: (15 n + 2 V) elements,
                                     13 n + 2 V without the preconditioner (n coefficients,
-                                    V sensor corners) */
+                                    V corner values of the sensors that are not tip/tilt-only,
+                                    (n_sub + 1)^2 each) */
   int precision;
+  int breakdown_pending;       /* 1: a solve of the plan broke down and no call has reported it yet */
 } tomo_plan_info;
 
 /* Launch shape of a plan (zero-initialise; every field 0 means the default). */
@@ -151,15 +153,25 @@ tomo_status tomo_plan_create_ex(const tomo_geometry *g, const tomo_plan_options 
  * d_slopes: n_slopes elements (read).  d_coeffs: n_coeffs elements; read as x0 when
  * warm != 0 (warm restart: the previous frame's solution), ignored otherwise (x0 = 0);
  * overwritten with x.  out_resnorm: host, may be NULL; when given the call waits for
- * the stream and stores ||r|| (2-norm of the final recurrence residual); a breakdown
- * is reported only then (TOMO_ERR_BREAKDOWN). */
+ * the stream and stores ||r|| (2-norm of the final recurrence residual), and a
+ * breakdown of this solve returns TOMO_ERR_BREAKDOWN.
+ * Breakdown (p.Ap <= 0 or a non-finite value, e.g. NaN slopes): the iterate is
+ * frozen (x keeps its last finite value, x0 for a breakdown in the first
+ * iteration) and the update kernel sets the plan's breakdown word, a mapped host
+ * word that never costs a synchronisation.  Without out_resnorm the breakdown is
+ * reported by the first later tomo_solve or tomo_solve_batch of the plan that is
+ * called after that solve's work has completed on the device: that call returns
+ * TOMO_ERR_BREAKDOWN, clears the word and enqueues nothing (call it again).
+ * tomo_plan_get_info shows the word without clearing it. */
 tomo_status tomo_solve(tomo_plan *p, const void *d_slopes, void *d_coeffs, int iters,
                        int warm, void *cuda_stream, double *out_resnorm);
 
 /* `count` independent frames of `count` distinct plans that share precision and
  * precond, solved together: every phase of the iteration is one launch for all
  * of them.  plans/d_slopes/d_coeffs: host arrays of `count`; same per-plan
- * semantics as tomo_solve. */
+ * semantics as tomo_solve.  When an earlier solve of any of the plans has broken
+ * down (its breakdown word is set), the call clears every set word, returns
+ * TOMO_ERR_BREAKDOWN and enqueues nothing. */
 tomo_status tomo_solve_batch(tomo_plan *const *plans, const void *const *d_slopes,
                              void *const *d_coeffs, int count, int iters, int warm,
                              void *cuda_stream);
@@ -202,7 +214,8 @@ tomo_status tomo_jacobi_diagonal(tomo_plan *p, double *d_out, void *cuda_stream)
  * of it must start at zero), and all calls share it: calls that overlap on the
  * GPU (different streams, or different host threads) race and must be
  * serialised by the caller.  The plan itself is not modified.  Enqueued on
- * `cuda_stream`; the host tables are copied before the call returns. */
+ * `cuda_stream`; the work reads the plan's host-side tables, so keep the plan
+ * alive until that work has completed on the stream. */
 tomo_status tomo_jacobi_diagonal_noalloc(const tomo_plan *p, double alpha, double *d_out,
                                          void *cuda_stream);
 
@@ -366,7 +379,9 @@ typedef struct tomo_server tomo_server;
 
 typedef struct {
   int telescope;               /* id from tomo_server_admit */
-  int status;                  /* TOMO_OK, or the error of the launch that held the frame */
+  int status;                  /* TOMO_OK; TOMO_ERR_BREAKDOWN when the frame's solve broke down (its
+                                  iterate frozen, so the telescope's warm start stays finite);
+                                  TOMO_ERR_SUPERSEDED; or the error of the launch that held it */
   long long tag;               /* the caller's tag from tomo_server_submit */
   double t_submit;             /* tomo_server_submit copied the frame in */
   double t_launch;             /* the launch holding the frame was enqueued */

@@ -76,7 +76,8 @@ class PlanInfo(ctypes.Structure):
                 ("n_layers", ctypes.c_int), ("n_wfs", ctypes.c_int),
                 ("cluster_size", ctypes.c_int), ("kernels_per_iteration", ctypes.c_int),
                 ("kernels_per_solve_base", ctypes.c_int), ("device_bytes", ctypes.c_longlong),
-                ("bytes_per_iteration", ctypes.c_longlong), ("precision", ctypes.c_int)]
+                ("bytes_per_iteration", ctypes.c_longlong), ("precision", ctypes.c_int),
+                ("breakdown_pending", ctypes.c_int)]
 
 
 class Dm(ctypes.Structure):

@@ -183,8 +183,10 @@ tomo_status read_resnorm(tomo_plan *p, int iters, cudaStream_t s, double *out) {
   double rr = 0.0;
   for (int q = 0; q < cnt; ++q) rr += part[off + 2 * q + 1];
   *out = std::sqrt(std::max(0.0, rr));
-  if (sc[kFlag] != 0.0 || !std::isfinite(rr))
+  if (sc[kFlag] != 0.0 || !std::isfinite(rr)) {
+    take_breakdown(p);   // reported here, not again by the next call
     return fail(TOMO_ERR_BREAKDOWN, "PCG breakdown: p.Ap <= 0 or not finite");
+  }
   return TOMO_OK;
 }
 
@@ -502,6 +504,18 @@ tomo_status tomo_plan_create_ex(const tomo_geometry *g, const tomo_plan_options 
     return fail(TOMO_ERR_NOMEM, std::string("cudaMalloc of the plan: ") + cudaGetErrorString(ce));
   }
   char *base = static_cast<char *>(p->arena);
+  // the breakdown word: page-locked, mapped, written by the update kernel
+  ce = cudaHostAlloc(reinterpret_cast<void **>(&p->bd_host), sizeof(int), cudaHostAllocMapped);
+  if (ce == cudaSuccess) {
+    *p->bd_host = 0;
+    ce = cudaHostGetDevicePointer(reinterpret_cast<void **>(&p->h_inst.bd_word), p->bd_host, 0);
+  }
+  if (ce != cudaSuccess) {
+    cudaFree(p->arena);
+    if (p->bd_host) cudaFreeHost(p->bd_host);
+    delete p;
+    return fail(TOMO_ERR_NOMEM, std::string("mapped host word of the plan: ") + cudaGetErrorString(ce));
+  }
 
   InstDev &I = p->h_inst;
   I.n = H.n;
@@ -627,6 +641,7 @@ tomo_status tomo_plan_create_ex(const tomo_geometry *g, const tomo_plan_options 
 
   auto bail = [&](tomo_status code, const std::string &msg) {
     cudaFree(p->arena);
+    cudaFreeHost(p->bd_host);
     delete p;
     return fail(code, msg);
   };
@@ -700,6 +715,7 @@ void tomo_destroy(tomo_plan *p) {
   for (auto e : p->timer.pool) cudaEventDestroy(e);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   cudaFree(p->arena);
+  if (p->bd_host) cudaFreeHost(p->bd_host);
   delete p;
 }
 
@@ -719,9 +735,15 @@ tomo_status tomo_plan_get_info(const tomo_plan *p, tomo_plan_info *out) {
   out->device_bytes = static_cast<long long>(p->arena_bytes);
   // p-update + W^-1 (r, J^-1, p in; p, phi out), ray-trace (phi in, v out),
   // gather + W + prior (v, p in; q out), update (x, p, r, q, J^-1 in; x, r out)
+  // V: corner values of the sensors with a corner field (the forward kernel writes them and
+  // the gather reads them; a tip/tilt-only sensor reaches the layers through its edge list)
   const long long vec = H.precond ? 15 : 13;
-  out->bytes_per_iteration = (vec * H.n + 2LL * H.v_total) * static_cast<long long>(p->esz);
+  long long V = 0;
+  for (const auto &w : H.wfs)
+    if (w.kind != kTTOnly) V += static_cast<long long>(w.nc) * w.nc;
+  out->bytes_per_iteration = (vec * H.n + 2LL * V) * static_cast<long long>(p->esz);
   out->precision = H.precision;
+  out->breakdown_pending = p->bd_host ? *reinterpret_cast<volatile int *>(p->bd_host) : 0;
   return TOMO_OK;
 }
 
@@ -767,6 +789,9 @@ tomo_status tomo_solve(tomo_plan *p, const void *d_slopes, void *d_coeffs, int i
   TOMO_TRY(check_plan(p));
   if (!d_slopes || !d_coeffs) return fail(TOMO_ERR_ARG, "slopes and coefficients must be device pointers");
   if (iters < 0 || iters > 100000) return fail(TOMO_ERR_ARG, "iters out of range");
+  if (take_breakdown(p))
+    return fail(TOMO_ERR_BREAKDOWN, "an earlier solve of this plan broke down (p.Ap <= 0 or not finite) and "
+                                    "froze its iterate; this call enqueued nothing");
   DeviceGuard dg(p->device);
   NvtxRange nvtx("tomo_solve");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
@@ -914,6 +939,13 @@ tomo_status tomo_solve_batch(tomo_plan *const *plans, const void *const *d_slope
     for (int j = 0; j < i; ++j)
       if (plans[j] == plans[i]) return fail(TOMO_ERR_ARG, "a plan appears twice in one batch");
   }
+  int broke = -1;
+  for (int i = 0; i < count; ++i)
+    if (take_breakdown(plans[i]) && broke < 0) broke = i;
+  if (broke >= 0)
+    return fail(TOMO_ERR_BREAKDOWN, "an earlier solve of plan " + std::to_string(broke) +
+                                        " of the batch (and of any other plan whose word was set) broke down "
+                                        "and froze its iterate; this call enqueued nothing");
   NvtxRange nvtx("tomo_solve_batch");
   Batch *b = nullptr;
   TOMO_TRY(get_batch(plans, count, &b));

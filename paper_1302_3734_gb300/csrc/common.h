@@ -137,6 +137,10 @@ struct InstDev {
   const void *edge_t;           // (t_x, t_y) of each edge corner (T, interleaved)
   const int *run_rows;          // per sensor (n+1): start of row b's runs in run_ab
   const int2 *run_ab;           // [a_lo, a_hi) runs of valid subapertures in a row
+  // The plan's breakdown word: page-locked host memory mapped into the device
+  // address space.  The update kernel sets it to 1 when a (P)CG step breaks
+  // down; only the host clears it, after reporting it (NULL: not recorded).
+  int *bd_word;
 };
 
 // Per-launch pointer arguments (indexed by the instance's slot in the launch).

@@ -1498,18 +1498,26 @@ __global__ void __launch_bounds__(kThreads) k_update(const InstDev *__restrict__
       // r = 0 (so p = 0 and p.Ap = 0) means the iterate is already exact: step 0
       const bool exact = (pq.x == 0.0 && rz == 0.0);
       const bool bad = !exact && (!(pq.x > 0.0) || !isfinite(pq.x) || !isfinite(rz) || flag != 0.0);
-      if (bad && it.blk == 0) I->scal[kFlag] = 1.0;
+      if (bad && it.blk == 0) {
+        I->scal[kFlag] = 1.0;
+        if (I->bd_word) *reinterpret_cast<volatile int *>(I->bd_word) = 1;
+      }
       s_alpha = T((bad || exact) ? 0.0 : rz / pq.x);
     }
     __syncthreads();
   }
   const T alpha = s_alpha;
+  // a step of zero (breakdown, or an exact iterate) leaves x and r as they are,
+  // even where p or q is not finite: the iterate is frozen
+  const bool step = alpha != T(0);
   Acc<T> rz, rr;
   for (int c = 0;;) {
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      xv[u] += alpha * pv[u];
-      rv[u] -= alpha * qv[u];
+      if (step) {
+        xv[u] += alpha * pv[u];
+        rv[u] -= alpha * qv[u];
+      }
       const T z = precond ? jv[u] * rv[u] : rv[u];
       if (i0 + u < n) {
         rz.add_prod(rv[u], z);

@@ -105,6 +105,7 @@ struct tomo_plan {
   tomo::Timer timer;
   double kind_ms[tomo::kNumKinds] = {0};
   long long kind_n[tomo::kNumKinds] = {0};
+  int *bd_host = nullptr;     // breakdown word (page-locked, mapped; h_inst.bd_word on the device)
 };
 
 namespace tomo {
@@ -145,6 +146,16 @@ void free_batch(Batch *b);
 // slot (nonzero = solve), or NULL for all.
 tomo_status batch_solve(Batch *b, const void *const *slopes, void *const *x, const int *const *active_g,
                         int iters, int warm, cudaStream_t s);
+
+// Reads and clears plan p's breakdown word: true when a solve of p has broken
+// down since the word was last cleared (only work that has completed on the
+// device is seen).
+inline bool take_breakdown(tomo_plan *p) {
+  volatile int *w = p->bd_host;
+  if (!w || *w == 0) return false;
+  *w = 0;
+  return true;
+}
 
 // Enqueue one solve of plan p on stream s, kernel by kernel (for capture into
 // a caller's graph); *n_kernels receives the number of launches.

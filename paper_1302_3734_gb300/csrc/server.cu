@@ -259,11 +259,13 @@ void finish(tomo_server *S, std::list<Launch>::iterator it, int status) {
   const int n = static_cast<int>(it->frames.size());
   for (const auto &f : it->frames) {
     Telescope *tel = S->tels.at(f.tel);
+    // a frame whose solve broke down (the plan's breakdown word, set on the device)
+    const int st = (status == TOMO_OK && tomo::take_breakdown(tel->plan)) ? TOMO_ERR_BREAKDOWN : status;
     tel->busy = false;
     tel->free_in.push_back(f.in_slot);
     tel->out_writing[f.out_slot] = 0;
-    tel->out_tag[f.out_slot] = status == TOMO_OK ? f.tag : -1;
-    S->results.push_back({f.tel, status, f.tag, f.t_submit, it->t_launch, t, n, f.out_slot});
+    tel->out_tag[f.out_slot] = st == TOMO_OK ? f.tag : -1;
+    S->results.push_back({f.tel, st, f.tag, f.t_submit, it->t_launch, t, n, f.out_slot});
   }
   S->done += n;
   S->slot_busy[it->slot] = false;

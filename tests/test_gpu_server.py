@@ -113,6 +113,37 @@ def test_served_frames_match_the_oracle(lib):
             assert e < 1e-5, (g["name"], k, e)
 
 
+def test_served_breakdown_is_the_frame_status(lib):
+    """A frame of NaN slopes comes back with TOMO_ERR_BREAKDOWN; the telescope's
+    warm start stays that of its previous frame, so its next frame is served as
+    if the broken one had not been there, and the other telescope is unaffected."""
+    torch, pkg = lib
+    geoms = _geoms()[:2]
+    K = 3
+    frames = [_frames(g, K, 30 + i)[1] for i, g in enumerate(geoms)]
+    srv = pkg.Server(iters=ITERS, result_slots=8, queue_depth=8)
+    ids = [srv.admit(g) for g in geoms]
+    nan = np.full_like(frames[0][0], np.nan)
+    order = [(0, frames[0][0], 0), (1, frames[1][0], 0), (0, nan, 1), (1, frames[1][1], 1),
+             (0, frames[0][1], 2), (1, frames[1][2], 2)]
+    for i, s, tag in order:
+        assert srv.submit(ids[i], s, tag=tag)
+        srv.drain(60.0)                        # one frame at a time: a fixed order
+    res = {(ids.index(r["telescope"]), r["tag"]): r for r in srv.poll()}
+    assert res[(0, 1)]["status"] == 7
+    assert all(r["status"] == 0 for key, r in res.items() if key != (0, 1))
+    got0 = srv.result(ids[0], res[(0, 2)]["result_slot"], 2)
+    got1 = srv.result(ids[1], res[(1, 2)]["result_slot"], 2)
+    srv.close()
+    for i, ks, got in ((0, (0, 1), got0), (1, (0, 1, 2), got1)):
+        plan = pkg.Plan(geoms[i])
+        x = torch.zeros(plan.n, dtype=torch.float32, device="cuda")
+        for k in ks:
+            plan.solve(torch.tensor(frames[i][k], device="cuda"), x, ITERS, warm=True)
+        assert np.array_equal(x.cpu().numpy(), got), i
+        plan.close()
+
+
 def test_admission_by_memory_budget(lib):
     torch, pkg = lib
     g = configs.small_lgs_config(16, 32, 3, 2)
@@ -271,7 +302,7 @@ def test_closed_loop_telescopes_are_their_control_steps_and_match_the_oracle_loo
                                      ITERS, fit_iters)
             a.append(a_t)
             e = rel(served[i][t + 2].astype(np.float64), a_t, f"served-closed-loop/{g['name']}/frame{t}")
-            assert e < 1e-4, (g["name"], t, e)
+            assert e < 1e-5, (g["name"], t, e)
 
 
 def test_drain_deadline_reports_a_timeout_and_the_server_stays_usable(lib):
