@@ -121,7 +121,7 @@ def test_closed_loop_against_the_oracle_loop(lib):
         fit.polc_step(s, x, rec, a_tm2, a_tm1, a_tm2, gain, iters, fit_iters, warm=t > 0)
         got = a_tm2.double().cpu().numpy()
         e = rel(got, a_o[t + 2], f"closed-loop/frame{t}")
-        assert e < 1e-4, (t, e)
+        assert e < 1e-5, (t, e)
     fit.close()
     plan.close()
 

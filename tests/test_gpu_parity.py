@@ -61,12 +61,17 @@ CASES = {
     "ragged-multitile": lambda: configs.small_lgs_config(n_sub=40, N=64, n_layers=4, levels=3),
     "wrap": lambda: configs.small_lgs_config(n_sub=12, N=32, n_layers=3, levels=2, wrap=True),
     "db4-J1": lambda: configs.small_lgs_config(n_sub=16, N=32, n_layers=2, levels=1, order=4),
-    # FP32 rounding of each operator application (~1.5e-7 relative) is amplified
-    # by CG roughly with the iteration count and the conditioning; this 16^2
-    # Haar case is the worst conditioned of the set, so it runs the 4 PCG
-    # iterations of the paper's accelerated method (Sec. 5.3).
-    "haar-N16": lambda: dict(configs.small_lgs_config(n_sub=8, N=16, n_layers=2, levels=3, order=1,
-                                                      d_sub=0.5, dx=0.5), iters=4),
+    # The worst-conditioned case of the set (Haar, three levels on 16^2: the
+    # Jacobi-preconditioned normal matrix has condition number 7.5e5), at its
+    # configuration's 8 PCG iterations.  CG amplifies the rounding of every
+    # operator application steeply with the iteration count here: the FP32 path
+    # measured 1.1e-7, 8.2e-7, 3.8e-6 after 1, 4, 8 iterations and 2.3e-5, 4.3e-4
+    # after 9, 10 (the FP64 path 2e-16 ... 4e-13 over the same counts), and an
+    # FP64 emulation that only rounds the operator's and the state's values to
+    # FP32 gives 2e-6 at 8 and 2e-4 at 10: the growth is the problem's, not the
+    # kernels'.
+    "haar-N16": lambda: configs.small_lgs_config(n_sub=8, N=16, n_layers=2, levels=3, order=1,
+                                                 d_sub=0.5, dx=0.5),
     "db2-noprecond": lambda: configs.small_lgs_config(n_sub=16, N=32, n_layers=2, levels=3,
                                                       order=2, precond=0),
     "small-fp64": lambda: configs.small_lgs_config(n_sub=16, N=32, n_layers=3, levels=2,
@@ -205,6 +210,73 @@ def test_nan_data_reports_breakdown(torch_cuda):
     s.zero_()
     assert plan.solve(s, x, 2, warm=False, resnorm=True) == 0.0
     plan.close()
+
+
+def test_breakdown_without_resnorm_is_reported_by_the_next_call(torch_cuda):
+    """NaN slopes in a graph-replayed solve without out_resnorm: the iterate stays
+    x0 (frozen), the plan's breakdown word is set, and the next tomo_solve returns
+    TOMO_ERR_BREAKDOWN without enqueuing anything; the call after it solves."""
+    import paper_1302_3734_gb300 as pkg
+    g = configs.small_lgs_config(n_sub=8, N=32, n_layers=2, levels=2)
+    plan = pkg.Plan(g)
+    rng = np.random.default_rng(17)
+    x0 = torch_cuda.tensor(rng.standard_normal(plan.n), dtype=torch_cuda.float32, device="cuda")
+    good = torch_cuda.tensor(rng.standard_normal(plan.n_slopes), dtype=torch_cuda.float32, device="cuda")
+    bad = torch_cuda.full((plan.n_slopes,), float("nan"), device="cuda")
+    x = x0.clone()
+    plan.solve(good, x, 3, warm=True)          # the graph of this signature exists
+    torch_cuda.cuda.synchronize()
+    assert plan._info().breakdown_pending == 0
+    x.copy_(x0)
+    plan.solve(bad, x, 3, warm=True)           # returns at once: no synchronisation
+    torch_cuda.cuda.synchronize()
+    assert torch_cuda.equal(x, x0), "the iterate was not frozen at x0"
+    assert plan._info().breakdown_pending == 1
+    with pytest.raises(pkg.TomoError) as e:
+        plan.solve(good, x, 3, warm=True)
+    assert e.value.status == 7
+    torch_cuda.cuda.synchronize()
+    assert torch_cuda.equal(x, x0), "the reporting call enqueued work"
+    assert plan._info().breakdown_pending == 0
+    plan.solve(good, x, 3, warm=True)
+    ref = x0.clone()
+    plan.set_launch_mode(0)
+    plan.solve(good, ref, 3, warm=True)
+    plan.set_launch_mode(1)
+    torch_cuda.cuda.synchronize()
+    assert torch_cuda.equal(x, ref) and bool(torch_cuda.isfinite(x).all())
+    plan.close()
+
+
+def test_batch_breakdown_is_reported_by_the_next_batch_call(torch_cuda):
+    """One instance of a batch gets NaN slopes: the other instance's result is its
+    single solve, the broken one stays at x0, and the next tomo_solve_batch reports it."""
+    import paper_1302_3734_gb300 as pkg
+    geoms = [configs.small_lgs_config(n_sub=16, N=32, n_layers=3, levels=2),
+             configs.small_lgs_config(n_sub=12, N=32, n_layers=2, levels=2)]
+    plans = [pkg.Plan(g) for g in geoms]
+    rng = np.random.default_rng(19)
+    s = [torch_cuda.tensor(rng.standard_normal(p.n_slopes), dtype=torch_cuda.float32, device="cuda")
+         for p in plans]
+    x0 = [torch_cuda.tensor(rng.standard_normal(p.n), dtype=torch_cuda.float32, device="cuda")
+          for p in plans]
+    alone = x0[0].clone()
+    plans[0].solve(s[0], alone, 4, warm=True)
+    bad = [s[0], torch_cuda.full_like(s[1], float("nan"))]
+    xb = [xi.clone() for xi in x0]
+    pkg.solve_batch(plans, bad, xb, 4, warm=True)
+    torch_cuda.cuda.synchronize()
+    assert torch_cuda.equal(xb[0], alone) and torch_cuda.equal(xb[1], x0[1])
+    assert [p._info().breakdown_pending for p in plans] == [0, 1]
+    with pytest.raises(pkg.TomoError) as e:
+        pkg.solve_batch(plans, s, xb, 4, warm=True)
+    assert e.value.status == 7
+    assert [p._info().breakdown_pending for p in plans] == [0, 0]
+    pkg.solve_batch(plans, s, xb, 4, warm=True)
+    torch_cuda.cuda.synchronize()
+    assert all(bool(torch_cuda.isfinite(x).all()) for x in xb)
+    for p in plans:
+        p.close()
 
 
 def test_zero_data_cold_start_is_exact(torch_cuda):
