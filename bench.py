@@ -103,7 +103,8 @@ def workload():
     return g, {"workload": "E-ELT MCAO 42m, 6 LGS 84x84 @90km + 3 TT NGS, 9 layers 128^2 @0.5m, "
                            "db3 J=4, Jacobi PCG 10 it, warm start, 500 Hz frozen flow",
                "n_coeffs": sum(l["N"] ** 2 for l in g["layers"]), "iters": g["iters"],
-               "precision": "FP32 operator, FP64 dots/scalars"}
+               "precision": "FP32 operator and vectors; in-block dot products as float-float pairs "
+                            "(about 48 bits); FP64 cross-block partials, alpha, beta and norms"}
 
 
 def frame_screens(geom, k, rank):
