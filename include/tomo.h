@@ -228,8 +228,11 @@ size_t tomo_plan_device_bytes(const tomo_plan *p);
 /* Per-kernel timing: when enabled, every launch of the plan is bracketed by CUDA
  * events; tomo_get_kernel_times returns, per kernel kind, the number of timed
  * launches and their summed milliseconds since the last reset (waits for the
- * stream).  Kinds: 0 transform-synthesis, 1 ray-trace/slopes, 2 adjoint+analysis,
- * 3 vector update, 4 other.  n_kinds = 5. */
+ * stream).  Kinds: 0 transform-synthesis, 1 ray-trace/slopes, 2 adjoint+analysis
+ * (the transform alone for plans whose gather runs separately), 3 vector update,
+ * 4 other, 5 the separate gather kernel.  n_kinds = 6.  While timing is enabled on
+ * the first plan of a tomo_solve_batch call, the batch's kernels are launched
+ * directly (no graph) and timed on that plan. */
 tomo_status tomo_set_kernel_timing(tomo_plan *p, int enable);
 tomo_status tomo_get_kernel_times(tomo_plan *p, int *counts, double *ms, int n_kinds);
 
@@ -475,6 +478,16 @@ double tomo_server_clock(void);
 
 /* Stop the threads, finish the frames in flight, release every plan.  NULL-safe. */
 void tomo_server_destroy(tomo_server *s);
+
+/* Measurement utility (the paper has no counterpart): the L2 read bandwidth in
+ * GB/s of the current device, the denominator of the benchmark's L2 fractions.
+ * d_buf: device buffer of `bytes` (16-byte aligned, small enough to stay in the
+ * L2, e.g. 32 MiB), owned by the caller; its contents are read, not changed.
+ * One untimed pass brings it into the L2, then `reps` launches each read it
+ * `passes` times (CTAs rotate over the slices between passes, loads bypass
+ * L1), timed by CUDA events on `cuda_stream`; waits for the stream. */
+tomo_status tomo_probe_l2_read(void *d_buf, long long bytes, int passes, int reps, void *cuda_stream,
+                               double *out_gbs);
 
 /* Number of kernels this library has launched so far in this process. */
 long long tomo_launch_count(void);

@@ -20,7 +20,7 @@ STATUS = {0: "TOMO_OK", 1: "TOMO_ERR_ARG", 2: "TOMO_ERR_GEOMETRY", 3: "TOMO_ERR_
           7: "TOMO_ERR_BREAKDOWN", 8: "TOMO_ERR_UNSUPPORTED", 9: "TOMO_ERR_FULL",
           10: "TOMO_ERR_SUPERSEDED"}
 
-KERNEL_KINDS = ("synthesis", "forward", "analysis", "update", "other")
+KERNEL_KINDS = ("synthesis", "forward", "analysis", "update", "other", "gather")
 
 
 class TomoError(RuntimeError):
@@ -120,6 +120,7 @@ SIGNATURES = [
     ("tomo_set_kernel_timing", _I, [_VP, _I]),
     ("tomo_get_kernel_times", _I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double), _I]),
     ("tomo_set_launch_mode", _I, [_VP, _I]),
+    ("tomo_probe_l2_read", _I, [_VP, ctypes.c_longlong, _I, _I, _VP, ctypes.POINTER(ctypes.c_double)]),
     ("tomo_launch_count", ctypes.c_longlong, []),
     ("tomo_last_error", ctypes.c_char_p, []),
     ("tomo_destroy", None, [_VP]),
@@ -573,6 +574,16 @@ class Server:
 
 def launch_count():
     return int(load_library().tomo_launch_count())
+
+
+def probe_l2_read(buf, passes=8, reps=20, stream=None):
+    """L2 read bandwidth (GB/s) measured on the CUDA tensor `buf` (it should fit the L2)."""
+    if not buf.is_cuda or not buf.is_contiguous():
+        raise ValueError("buf must be a contiguous CUDA tensor")
+    out = ctypes.c_double(0.0)
+    _check(load_library().tomo_probe_l2_read(ctypes.c_void_p(buf.data_ptr()), buf.numel() * buf.element_size(),
+                                             int(passes), int(reps), _stream(stream), ctypes.byref(out)))
+    return out.value
 
 
 def version():

@@ -131,10 +131,14 @@ tomo_status enqueue_solve(tomo_plan *tp, const LaunchSet &L, const void *const *
       io.out0[i] = x[i];
       io.in1[i] = slopes[i];   // tip/tilt-only sensors' data term
     }
+    if (L.split)
+      TOMO_TRY(timed(tp, kKindGather, s, [&] {
+        return launch_gather(L.precision, warm ? 1 : 2, L.d_inst, L.cl, L.n_cl, L.C, L.smem_g, io, s);
+      }, "gather (residual)"));
     TOMO_TRY(timed(tp, kKindAnalysis, s, [&] {
-      return launch_analysis(L.precision, 1, 2, L.lf, warm ? kFlagWarm : 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem_a,
-                             io, s, L.split, L.smem_g);
-    }, "analysis (residual)", analysis_launches(1, L.split)));
+      return launch_analysis(L.precision, L.split ? 2 : 1, 2, L.lf, warm ? kFlagWarm : 0, L.d_inst, L.cl, L.n_cl,
+                             L.C, L.smem_a, io, s, 0, 0);
+    }, "analysis (residual)"));
     nk += analysis_launches(1, L.split);
   }
   for (int it = 0; it < iters; ++it) {
@@ -147,9 +151,14 @@ tomo_status enqueue_solve(tomo_plan *tp, const LaunchSet &L, const void *const *
     TOMO_TRY(timed(tp, kKindFwd, s, [&] {
       return launch_forward(L.precision, 0, L.max_layers, L.elong, L.d_inst, L.fwd, L.n_fwd, none, s);
     }, "forward"));
+    if (L.split)
+      TOMO_TRY(timed(tp, kKindGather, s, [&] {
+        return launch_gather(L.precision, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem_g, none, s);
+      }, "gather"));
     TOMO_TRY(timed(tp, kKindAnalysis, s, [&] {
-      return launch_analysis(L.precision, 1, 1, L.lf, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem_a, none, s, L.split, L.smem_g);
-    }, "analysis", analysis_launches(1, L.split)));
+      return launch_analysis(L.precision, L.split ? 2 : 1, 1, L.lf, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem_a, none,
+                             s, 0, 0);
+    }, "analysis"));
     IoArgs io{};
     io.active = active;
     for (int i = 0; i < L.count; ++i) io.out0[i] = x[i];
@@ -339,7 +348,7 @@ tomo_status build_batch(tomo_plan *const *plans, int count, Batch **out) {
 // One solve of every instance of the batch (each group in turn); `active`
 // (device, one int per batch position) lets instances sit out.
 tomo_status batch_enqueue(Batch *b, const void *const *slopes, void *const *x, const int *const *active_g,
-                          int iters, int warm, cudaStream_t s, int *n_kernels) {
+                          int iters, int warm, cudaStream_t s, int *n_kernels, tomo_plan *timing = nullptr) {
   int total = 0;
   for (size_t gi = 0; gi < b->groups.size(); ++gi) {
     const BatchGroup &g = b->groups[gi];
@@ -350,7 +359,7 @@ tomo_status batch_enqueue(Batch *b, const void *const *slopes, void *const *x, c
       xs[slot] = x[g.members[slot]];
     }
     int nk = 0;
-    TOMO_TRY(enqueue_solve(nullptr, g.ls, sl.data(), xs.data(), iters, warm, s, &nk,
+    TOMO_TRY(enqueue_solve(timing, g.ls, sl.data(), xs.data(), iters, warm, s, &nk,
                            active_g ? active_g[gi] : nullptr));
     total += nk;
   }
@@ -361,6 +370,10 @@ tomo_status batch_enqueue(Batch *b, const void *const *slopes, void *const *x, c
 tomo_status batch_solve(Batch *b, const void *const *slopes, void *const *x, const int *const *active_g,
                         int iters, int warm, cudaStream_t s) {
   const int count = static_cast<int>(b->plans.size());
+  if (b->plans[0]->timer.on) {
+    // per-kernel timing (on the first plan): every launch direct, between events
+    return batch_enqueue(b, slopes, x, active_g, iters, warm, s, nullptr, b->plans[0]);
+  }
   const int *key_active = active_g ? active_g[0] : nullptr;
   BatchGraph *ge = nullptr;
   for (auto &g : b->graphs)
@@ -472,6 +485,7 @@ tomo_status tomo_plan_create_ex(const tomo_geometry *g, const tomo_plan_options 
   const size_t o_eslot = A.take(sizeof(EdgeSlot) * H.edge_slots.size());
   const size_t o_gel = A.take(esz * std::max<size_t>(2, H.gel.size()));
   const size_t o_gtcols = A.take(sizeof(int2) * std::max<size_t>(1, H.gt_cols.size()));
+  const size_t o_gtbrows = A.take(sizeof(int2) * std::max<size_t>(1, H.gt_brows.size()));
   const size_t o_ttseg = A.take(sizeof(int2) * H.tt_seg.size());
   const size_t o_ttnode = A.take(sizeof(int) * std::max<size_t>(1, H.tt_node.size()));
   const size_t o_ttbeg = A.take(sizeof(int) * H.tt_beg.size());
@@ -559,6 +573,7 @@ tomo_status tomo_plan_create_ex(const tomo_geometry *g, const tomo_plan_options 
   I.edge_slots = reinterpret_cast<const EdgeSlot *>(base + o_eslot);
   I.gel = H.gel.empty() ? nullptr : base + o_gel;
   I.gt_cols = reinterpret_cast<const int2 *>(base + o_gtcols);
+  I.gt_brows = reinterpret_cast<const int2 *>(base + o_gtbrows);
   I.img_stride = H.img_stride;
   I.tt_seg = reinterpret_cast<const int2 *>(base + o_ttseg);
   I.tt_node = reinterpret_cast<const int *>(base + o_ttnode);
@@ -626,6 +641,7 @@ tomo_status tomo_plan_create_ex(const tomo_geometry *g, const tomo_plan_options 
   put(o_eslot, H.edge_slots.data(), sizeof(EdgeSlot) * H.edge_slots.size());
   if (!H.gel.empty()) put_real(o_gel, H.gel);
   put(o_gtcols, H.gt_cols.data(), sizeof(int2) * H.gt_cols.size());
+  put(o_gtbrows, H.gt_brows.data(), sizeof(int2) * H.gt_brows.size());
   put_real(o_ttw, H.tt_w);
   put(o_gtoff, H.gt_off.data(), sizeof(int) * H.gt_off.size());
   put(o_ttseg, H.tt_seg.data(), sizeof(int2) * H.tt_seg.size());

@@ -110,6 +110,8 @@ struct InstDev {
   const int4 *vs_run;           // per (layer, rank, dense sensor): v run {g0, 16-byte words, smem offset}
   int vstage, v_total;          // staged v elements per analysis CTA; corner values of all sensors
   const int2 *gt_cols;          // per (m,l): columns [x, x+y) mod N_l that the sensor's taps reach
+  const int2 *gt_brows;         // per (m,l,rank): {v offset of the first corner row the band's row
+                                // records reach, number of rows}
   const void *stage_img;        // per (layer, rank): the CTA's stage image (img_stride bytes apart)
   long long img_stride;
   // Pupil-edge corrections: a tip/tilt-only sensor's corner field is
@@ -217,6 +219,21 @@ TOMO_HD inline StageLayout stage_layout(int n_dense, int N, int R0, int rec_stri
   L.vs = L.image;
   L.total = L.vs + vstage * esz;
   return L;
+}
+
+// Shared-memory layout of the separate gather kernel (bytes, 16-byte aligned):
+// the band buffer of R0 x N nodes, the band's row records (first corner row,
+// KT weights per node row), then the column-summed corner rows of one sensor
+// (the plan's largest band needs max_band_cells elements there).
+struct GatherSmem {
+  int ry, rw, u;
+};
+TOMO_HD inline GatherSmem gather_smem_layout(int R0, int N, int KT, int esz) {
+  GatherSmem g;
+  g.ry = (R0 * N * esz + 15) / 16 * 16;
+  g.rw = g.ry + (4 * R0 + 15) / 16 * 16;
+  g.u = g.rw + (R0 * KT * esz + 15) / 16 * 16;
+  return g;
 }
 
 // Work items.

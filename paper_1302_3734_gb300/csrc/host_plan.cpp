@@ -471,6 +471,31 @@ tomo_status build_host_plan(const tomo_geometry *geo, HostPlan *P, std::string *
       }
       P->gt_cols[m * P->n_layers + l] = cols;
     }
+  // per (sensor, layer, cluster rank): the corner rows that the row records of the
+  // rank's band of node rows reach, {v offset of the first row, row count}
+  P->gt_brows.assign(static_cast<size_t>(P->n_wfs) * P->n_layers * P->C, make_int2(0, 0));
+  P->max_band_cells = 0;
+  for (int m = 0; m < P->n_wfs; ++m)
+    for (int l = 0; l < P->n_layers; ++l) {
+      const int go = P->gt_off[m * P->n_layers + l];
+      if (go < 0) continue;
+      const WfsDev &d = P->wfs[m];
+      const int N = P->layers[l].N, R0 = N / P->C, KT = P->max_taps;
+      for (int c = 0; c < P->C; ++c) {
+        int lo = d.nc, hi = -1;
+        for (int k = c * R0; k < (c + 1) * R0; ++k) {
+          const int ro = P->gt_ro[go + N + k];
+          if (ro < 0) continue;
+          const int b0 = (ro - d.v_off) / d.nc;
+          lo = std::min(lo, b0);
+          hi = std::max(hi, std::min(d.nc, b0 + KT));
+        }
+        if (hi <= lo) continue;
+        P->gt_brows[(static_cast<size_t>(m) * P->n_layers + l) * P->C + c] = make_int2(d.v_off + lo * d.nc, hi - lo);
+        P->max_band_cells = std::max<long long>(P->max_band_cells,
+                                                static_cast<long long>(hi - lo) * P->gt_cols[m * P->n_layers + l].y);
+      }
+    }
   if (P->n_edge_wfs > 64) {
     *err = "more than 64 sensors with tip/tilt removal or tip/tilt-only measurement";
     return TOMO_ERR_UNSUPPORTED;
@@ -570,10 +595,14 @@ tomo_status build_host_plan(const tomo_geometry *geo, HostPlan *P, std::string *
     }
     P->gather_staged = fits ? 1 : 0;
     P->smem_analysis = fits ? need : P->smem_transform;
+    // the separate gather kernel: the band buffer (N/C rows of N), the band's row
+    // records, then one sensor's column-summed corner rows
     for (const auto &d : P->layers)
-      P->smem_gather = std::max<long long>(P->smem_gather, static_cast<long long>(d.N / P->C) * d.N * esz);
+      P->smem_gather = std::max<long long>(P->smem_gather,
+                                           gather_smem_layout(d.N / P->C, d.N, P->max_taps, esz).u);
+    P->smem_gather += P->max_band_cells * esz;
     if (!fits && P->smem_gather > 220LL * 1024) {
-      *err = "layer grids too large for the separate gather kernel's band buffer";
+      *err = "layer grids too large for the separate gather kernel's band buffers";
       return TOMO_ERR_UNSUPPORTED;
     }
     if (!fits && P->n_dense > kMaxGatherSensors) {

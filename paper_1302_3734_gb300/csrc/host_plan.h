@@ -42,6 +42,8 @@ struct HostPlan {
   std::vector<double> gt_rw;       // 4 per record, 0 beyond the window's taps
   std::vector<int> gt_ys;          // row records: window start in the CTA's staged v rows
   std::vector<int2> gt_cols;       // per (m,l): columns [x, x+y) mod N that the sensor's taps reach
+  std::vector<int2> gt_brows;      // per (m,l,rank): {v offset of the band's first corner row, rows}
+  long long max_band_cells = 0;    // largest (corner rows x columns) of one (sensor, layer, band)
   long long smem_gather = 0;       // dynamic shared memory of the separate gather kernel (bytes)
   std::vector<int4> vs_run;        // per (layer, rank, dense sensor): {g0, nvec, smem offset, 0}
   int vstage = 0;                  // largest staged v (T elements) of one analysis CTA

@@ -29,6 +29,12 @@ cudaError_t launch_synthesis(int precision, int src, int lf, int flags, const In
 cudaError_t launch_analysis(int precision, int src, int epi, int lf, int flags, const InstDev *insts,
                             const ClusterItem *items, int n_clusters, int C, size_t smem,
                             const IoArgs &io, cudaStream_t s, int split, size_t smem_gather);
+// The separate gather kernel alone (g = sum_m P_m^T v_m into the plan's phi),
+// for plans whose gather tables are not staged; launch_analysis with src 2 then
+// transforms its output.  tt_mode: 0 operator, 1 warm residual, 2 data only.
+cudaError_t launch_gather(int precision, int tt_mode, const InstDev *insts, const ClusterItem *items,
+                          int n_clusters, int C, size_t smem_gather, const IoArgs &io, cudaStream_t s);
+
 // Kernels one launch_analysis call launches.
 inline int analysis_launches(int src, int split) { return (src == 1 && split) ? 2 : 1; }
 

@@ -13,7 +13,8 @@
 
 namespace tomo {
 
-enum Kind : int { kKindSynth = 0, kKindFwd = 1, kKindAnalysis = 2, kKindUpd = 3, kKindOther = 4, kNumKinds = 5 };
+enum Kind : int { kKindSynth = 0, kKindFwd = 1, kKindAnalysis = 2, kKindUpd = 3, kKindOther = 4, kKindGather = 5,
+                  kNumKinds = 6 };
 
 // Everything one launch sequence needs (one plan, or a batch of plans).
 struct LaunchSet {
