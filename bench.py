@@ -59,24 +59,12 @@ def ncu_traffic(kind):
     return NCU_TRAFFIC["bytes"].get(kind) if digest == NCU_TRAFFIC["kernels_cu_sha256"] else None
 
 
-def l2_probe(torch, dev):
-    """Copy bandwidth of a 32 MiB -> 32 MiB copy that stays in the 129 MB L2 (read + write bytes
-    over CUDA-event time, best of 20 after warm-up)."""
-    a = torch.empty(8 << 20, dtype=torch.float32, device=dev).fill_(1.0)
-    b = torch.empty_like(a)
-    for _ in range(5):
-        b.copy_(a)
-    best = float("inf")
-    for _ in range(20):
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(10):
-            b.copy_(a)
-        e1.record()
-        torch.cuda.synchronize()
-        best = min(best, e0.elapsed_time(e1) / 10)
-    return 2 * a.numel() * 4 / (best / 1000.0) / 1e9
+def l2_probe(pkg, torch, dev):
+    """L2 read bandwidth: the library's probe reads a 24 MiB buffer (resident in the 129 MB L2)
+    8 times per launch over 20 launches, loads bypassing L1, timed with CUDA events; best of 3."""
+    a = torch.ones(6 << 20, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream().cuda_stream
+    return max(pkg.probe_l2_read(a, passes=8, reps=20, stream=stream) for _ in range(3))
 
 
 def parse():
@@ -300,6 +288,54 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def launch_bytes(plans, geoms):
+    """Algorithmic bytes of one launch of each PCG kernel kind over the given plans (inputs read,
+    outputs written, each once): synthesis reads r, J^-1, p and writes p, phi (5n); the forward
+    kernel reads phi and writes the corner fields (n + V); the fused gather + analysis reads v, p
+    and writes q (2n + V); where the gather runs separately it reads v and writes the gathered
+    grids (n + V) and the analysis reads those and p and writes q (3n); the update reads x, r, p,
+    q, J^-1 and writes x, r (7n).  V: corner values of the sensors that are not tip/tilt-only."""
+    out = {"synthesis": 0, "forward": 0, "analysis": 0, "update": 0, "gather": 0}
+    for p, g in zip(plans, geoms):
+        e = 8 if p.precision else 4
+        n = p.n
+        V = (p.info.bytes_per_iteration // e - (15 if g["precond"] else 13) * n) // 2
+        split = p.info.kernels_per_iteration == 5
+        out["synthesis"] += 5 * n * e
+        out["forward"] += (n + V) * e
+        out["analysis"] += (3 * n if split else 2 * n + V) * e
+        out["gather"] += (n + V) * e if split else 0
+        out["update"] += 7 * n * e
+    return out
+
+
+def kernel_roofline(kt, per_launch, peak, note=None):
+    """The dominant kernel (by event time) of per-kind CUDA-event timings kt {kind: (launches, ms)}:
+    its algorithmic bytes per launch over its mean launch time, against the HBM peak."""
+    kinds = [k for k in per_launch if kt.get(k, (0, 0.0))[0] > 0 and per_launch[k] > 0]
+    dom = max(kinds, key=lambda k: kt[k][1])
+    cnt, ms = kt[dom]
+    achieved = per_launch[dom] * cnt / (ms / 1000.0) / 1e9
+    out = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+           "frac": achieved / peak, "bytes_per_launch": per_launch[dom],
+           "kernel_us_per_launch": {k: 1000.0 * kt[k][1] / kt[k][0] for k in kinds},
+           "share_of_kernel_time": {k: kt[k][1] / sum(kt[j][1] for j in kinds) for k in kinds}}
+    if note:
+        out["note"] = note
+    return out
+
+
+def _timed_kinds(pkg, torch, plans, run, flush, reps):
+    """Per-kind CUDA-event kernel times of `reps` calls of run(), timing on the first plan."""
+    plans[0].set_kernel_timing(True)
+    for k in range(reps):
+        flush.fill_(float(k))
+        run()
+    kt = plans[0].kernel_times()
+    plans[0].set_kernel_timing(False)
+    return kt
+
+
 def _time_batch(pkg, torch, plans, slopes, xs, iters, flush, steps, warmup):
     for _ in range(warmup):
         pkg.solve_batch(plans, slopes, xs, iters, warm=True)
@@ -333,11 +369,15 @@ def bench_batched(pkg, torch, geom, slopes, flush, iters, args, peak, dev):
     t = _time_batch(pkg, torch, plans, sl, xs, iters, flush, steps, 3)
     ms = float(np.mean(t))
     bytes_it = sum(p.info.bytes_per_iteration for p in plans)
+    kt = _timed_kinds(pkg, torch, plans, lambda: pkg.solve_batch(plans, sl, xs, iters, warm=True), flush, 3)
     out["eelt"] = {"instances": B, "solves_per_s": B * 1000.0 / ms, "ms_per_batch": ms,
                    "cluster_size": c_e, "autotune_solves_per_s": tab_e,
                    "p99_ms": float(np.percentile(t, 99)),
                    "achieved_GBps_per_iteration_bytes": bytes_it * iters / (ms / 1000.0) / 1e9,
-                   "frac_of_hbm_peak": bytes_it * iters / (ms / 1000.0) / 1e9 / peak}
+                   "frac_of_hbm_peak": bytes_it * iters / (ms / 1000.0) / 1e9 / peak,
+                   "roofline": kernel_roofline(kt, launch_bytes(plans, [geom] * B), peak,
+                                               "events around every launch of 3 batched solves (direct "
+                                               "launches), L2 flushed before each")}
     for p in plans:
         p.close()
     # the 64-instance uneven workload
@@ -354,7 +394,11 @@ def bench_batched(pkg, torch, geom, slopes, flush, iters, args, peak, dev):
     t = _time_batch(pkg, torch, plans, sl, xs, 10, flush, steps, 3)
     ms = float(np.mean(t))
     bytes_it = sum(p.info.bytes_per_iteration for p in plans)
+    kt = _timed_kinds(pkg, torch, plans, lambda: pkg.solve_batch(plans, sl, xs, 10, warm=True), flush, 3)
     out["uneven64"] = {"instances": len(plans), "solves_per_s": len(plans) * 1000.0 / ms,
+                       "roofline": kernel_roofline(kt, launch_bytes(plans, geoms), peak,
+                                                   "events around every launch of 3 batched solves "
+                                                   "(direct launches), L2 flushed before each"),
                        "cluster_size": c_u, "autotune_solves_per_s": tab_u,
                        "ms_per_batch": ms, "p99_ms": float(np.percentile(t, 99)),
                        "coefficients": int(sum(p.n for p in plans)),
@@ -399,8 +443,12 @@ def bench_large(pkg, torch, dev, flush, peak, steps=5, warmup=2):
         torch.cuda.synchronize()
         ms = float(np.mean([a.elapsed_time(b) for a, b in t]))
         gbs = k * bytes_it * iters / (ms / 1000.0) / 1e9
+        kt = _timed_kinds(pkg, torch, plans, once, flush, 2)
         out[label] = {"solves_per_s": k * 1000.0 / ms, "ms": ms, "achieved_GBps_per_iteration_bytes": gbs,
-                      "frac_of_hbm_peak": gbs / peak}
+                      "frac_of_hbm_peak": gbs / peak,
+                      "roofline": kernel_roofline(kt, launch_bytes(plans[:k], [g] * k), peak,
+                                                  "events around every launch of 2 solves (direct launches), "
+                                                  "L2 flushed before each")}
     for p in plans:
         p.close()
     return out
@@ -783,12 +831,8 @@ def main():
     run(0, min(args.steps, 50), args.warmup, False)
     kt = plan.kernel_times()
     plan.set_kernel_timing(False)
-    nlaunch = {k: v[0] for k, v in kt.items()}
-    dominant = max(kt, key=lambda k: kt[k][1])
-    sT = 4
-    V = (info.bytes_per_iteration // sT - 15 * n) // 2
-    per_launch_bytes = {"synthesis": 5 * n * sT, "forward": (n + V) * sT,
-                        "analysis": (2 * n + V) * sT, "update": 7 * n * sT}
+    per_launch_bytes = launch_bytes([plan], [geom])
+    dominant = max((k for k in per_launch_bytes if kt[k][0] > 0), key=lambda k: kt[k][1])
     cnt, ms = kt[dominant]
     achieved = per_launch_bytes[dominant] * cnt / (ms / 1000.0) / 1e9
     peaks = {}
@@ -797,7 +841,7 @@ def main():
         peak, peak_src = float(peaks["hbm_gbs"]), "measured"
     except (OSError, KeyError, ValueError):
         peak, peak_src = 6800.0, "fallback"
-    l2_gbs = l2_probe(torch, dev)
+    l2_gbs = l2_probe(pkg, torch, dev)
 
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws,
@@ -819,7 +863,8 @@ def main():
                      "unit": "GB/s", "frac": achieved / peak, "traffic": ncu_traffic(dominant),
                      "peak_source": peak_src,
                      "l2_peak_gbs": l2_gbs, "frac_of_l2_peak": achieved / l2_gbs,
-                     "kernel_ms_per_launch": {k: (v[1] / v[0] if v[0] else None) for k, v in kt.items()},
+                     "bytes_per_launch": per_launch_bytes[dominant],
+                     "kernel_ms_per_launch": {k: v[1] / v[0] for k, v in kt.items() if v[0]},
                      "bytes_per_iteration": info.bytes_per_iteration},
         "gpu_launches": launches,
         "clocks": clk.summary(),

@@ -7,7 +7,7 @@ eq. eqn_lse) and the fitting step that turns its layers into mirror commands
 compiles the library in-tree.
 """
 from .binding import (Plan, Fit, Server, TomoError, solve_batch, launch_count, load_library, version,
-                      geometry_struct, fit_geometry_struct, SIGNATURES, LIB_PATH)
+                      probe_l2_read, geometry_struct, fit_geometry_struct, SIGNATURES, LIB_PATH)
 
 __all__ = ["Plan", "Fit", "Server", "TomoError", "solve_batch", "launch_count", "load_library", "version",
-           "geometry_struct", "fit_geometry_struct", "SIGNATURES", "LIB_PATH"]
+           "probe_l2_read", "geometry_struct", "fit_geometry_struct", "SIGNATURES", "LIB_PATH"]
