@@ -60,11 +60,13 @@ def ncu_traffic(kind):
 
 
 def l2_probe(pkg, torch, dev):
-    """L2 read bandwidth: the library's probe reads a 24 MiB buffer (resident in the 129 MB L2)
-    8 times per launch over 20 launches, loads bypassing L1, timed with CUDA events; best of 3."""
-    a = torch.ones(6 << 20, dtype=torch.float32, device=dev)
+    """L2 read bandwidth: the library's probe reads a 64 MiB buffer (resident in the 129 MB L2)
+    16 times per launch over 20 launches, loads bypassing L1, timed with CUDA events; best of 3.
+    (On GB300: 14 TB/s with 24 MiB and 8 passes, where launch overheads still count; 18.8 TB/s
+    with 96 MiB; 7.0 TB/s with 512 MiB, which no longer fits and reads HBM.)"""
+    a = torch.ones(16 << 20, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream().cuda_stream
-    return max(pkg.probe_l2_read(a, passes=8, reps=20, stream=stream) for _ in range(3))
+    return max(pkg.probe_l2_read(a, passes=16, reps=20, stream=stream) for _ in range(3))
 
 
 def parse():

@@ -5,8 +5,9 @@ Its layer grids do not fit the analysis CTAs' staged gather, so this is the
 global-memory gather path, and the transform caches hold only the coarse
 levels.  Each result is compared element by element with the FP64 oracle on
 the full vectors: the Jacobi diagonal, the normal operator, the right-hand
-side and two PCG iterations; a batch of two instances is bitwise the single
-solve.
+side and the configuration's own solve (20 PCG iterations from a cold start
+on a frame of von Karman layers, about 40 s of oracle time); a batch of two
+instances is bitwise the single solve.
 """
 import numpy as np
 import pytest
@@ -56,20 +57,49 @@ def test_large_normal_operator(large):
     assert e < 1e-5, e
 
 
-def test_large_rhs_and_two_pcg_iterations(large):
+class _Iterates(list):
+    """A history for Tomography.pcg that keeps only x after the chosen iterations."""
+
+    def __init__(self, keep):
+        super().__init__()
+        self.keep, self.k, self.x = set(keep), 0, {}
+
+    def append(self, item):
+        self.k += 1
+        if self.k in self.keep:
+            self.x[self.k] = item[0].copy()
+
+
+def test_large_rhs_and_full_pcg_solve(large):
+    """The configuration's own solve: 20 PCG iterations from a cold start on one
+    frame of von Karman layers with noise.  The FP32 iterate follows the FP64
+    oracle's within 1e-5 through the E-ELT configuration's 10 iterations
+    (measured 6.0e-6) and within 1e-3 after 20 (measured 3.0e-4): on this system
+    the FP32 rounding of the operator is amplified by CG steeply past about 14
+    iterations (1.1e-5 at 14, 2.5e-5 at 17, 3.0e-4 at 20; on pure-noise slopes
+    already 1.2e-5 at 8).  The kernels' arithmetic is checked tightly by the
+    operator and right-hand-side tests above (2e-7)."""
+    from synth import FrozenFlow
     torch, pkg, g, plan, ora = large
-    s = gaussian_noise(plan.n_slopes, 0.3, 42)
+    phis = FrozenFlow(g, 4).layers(0.0)
+    sig = np.concatenate([np.full(2 if w["tt_only"] else 2 * int(w["valid"].sum()), w["sigma"])
+                          for w in g["wfs"]])
+    s = ora.measure(phis) + gaussian_noise(len(sig), 1.0, 4_000_042) * sig
     ds = torch.tensor(s, dtype=torch.float32, device="cuda")
     b = torch.empty(plan.n, dtype=torch.float32, device="cuda")
     plan.rhs(ds, b)
     b_ref = ora.rhs(s)
-    e = rel(b.double().cpu().numpy(), b_ref, "rhs/cfg4-full")
+    e = rel(b.double().cpu().numpy(), b_ref, "rhs/cfg4-screens")
     assert e < 1e-5, e
-    x = torch.zeros(plan.n, dtype=torch.float32, device="cuda")
-    plan.solve(ds, x, 2, warm=False)
-    x_ref = ora.pcg(b_ref, np.zeros(ora.n), 2, ora.jacobi_diagonal())
-    e = rel(x.double().cpu().numpy(), x_ref, "solve-2it/cfg4-full")
-    assert e < 1e-5, e
+    iters = int(g["iters"])
+    assert iters == 20
+    hist = _Iterates((10, iters))
+    ora.pcg(b_ref, np.zeros(ora.n), iters, ora.jacobi_diagonal(), history=hist)
+    for k, bound in ((10, 1e-5), (iters, 1e-3)):
+        x = torch.zeros(plan.n, dtype=torch.float32, device="cuda")
+        plan.solve(ds, x, k, warm=False)
+        e = rel(x.double().cpu().numpy(), hist.x[k], f"solve-{k}it/cfg4-screens")
+        assert e < bound, (k, e)
 
 
 def test_large_batch_of_two_is_bitwise_single(large):

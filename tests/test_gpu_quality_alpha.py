@@ -1,13 +1,17 @@
 """The regularisation-weight sweep of the quality metric through the GPU path,
 point by point against the oracle (Sec. 5.2, the role of alpha; Sec. 5.1,
-residual RMS): for every alpha of the sweep, tomo_reconstruct (30 PCG
-iterations, W^-1, 4 fitting CG iterations) and tomo_fit_residual_rms against
-the truth, compared with the oracle's reconstruction, commands and residual
-RMS per direction; the GPU curve has its minimum at the same alpha.
+residual RMS): for every alpha of the sweep, tomo_reconstruct (PCG, W^-1, 4
+fitting CG iterations) and tomo_fit_residual_rms against the truth, compared
+with the oracle's commands and residual RMS per direction.
 
-Tolerances: the commands 1e-5 relative L2 (the FP32 path's target); the
-residual RMS per direction 1e-5 relative (an RMS of FP32 fields of a few rad,
-accumulated in double-float).
+* The FP64 build at the sweep's 20 PCG iterations: commands within 1e-6 and
+  RMS within 1e-7 (measured up to 2e-8 and 3e-9), and the GPU curve has its
+  minimum at the same alpha as the oracle's.  Beyond about 20 iterations this
+  small system is so ill-conditioned that CG amplifies rounding differences of
+  1e-16 between two FP64 implementations to 1e-3 by iteration 30, so a
+  point-by-point comparison stops being meaningful there.
+* The FP32 build at the small configuration's own 8 iterations: commands
+  within 1e-5 and RMS within 1e-6 (measured up to 6e-7 and 1.3e-7).
 """
 import numpy as np
 import pytest
@@ -28,31 +32,37 @@ def lib():
     return torch, pkg
 
 
-def test_alpha_sweep_matches_the_oracle(lib):
+def _gpu_point(torch, pkg, plan, fit, truth, s, iters, dt):
+    x = torch.zeros(plan.n, dtype=dt, device="cuda")
+    a = torch.zeros(fit.n, dtype=dt, device="cuda")
+    fit.reconstruct(torch.tensor(s, dtype=dt, device="cuda"), x, a, iters, qs.FIT_ITERS, warm=False)
+    truth_d = torch.tensor(np.concatenate([t.ravel() for t in truth]), dtype=dt, device="cuda")
+    out = torch.empty(fit.info.n_dir, dtype=torch.float64, device="cuda")
+    fit.residual_rms(truth_d, a, out)
+    torch.cuda.synchronize()
+    return a.double().cpu().numpy(), out.cpu().numpy()
+
+
+@pytest.mark.parametrize("precision,iters,tol_a,tol_r", [(1, qs.ITERS, 1e-6, 1e-7), (0, 8, 1e-5, 1e-6)])
+def test_alpha_sweep_matches_the_oracle(lib, precision, iters, tol_a, tol_r):
     torch, pkg = lib
+    dt = torch.float64 if precision else torch.float32
     frames = [qs.frame(k) for k in range(qs.FRAMES)]
     gpu_curve, ora_curve = {}, {}
     for alpha in qs.ALPHAS:
-        g = qs.geometry(alpha)
+        g = qs.geometry(alpha, precision)
         plan = pkg.Plan(g)
         fit = pkg.Fit(plan, g["fitting"])
         rms_g, rms_o = [], []
         for k, (truth, s) in enumerate(frames):
-            _, a_ref, r_ref = qs.oracle_point(alpha, truth, s)
-            x = torch.zeros(plan.n, dtype=torch.float32, device="cuda")
-            a = torch.zeros(fit.n, dtype=torch.float32, device="cuda")
-            fit.reconstruct(torch.tensor(s, dtype=torch.float32, device="cuda"), x, a, qs.ITERS,
-                            qs.FIT_ITERS, warm=False)
-            truth_d = torch.tensor(np.concatenate([t.ravel() for t in truth]), dtype=torch.float32,
-                                   device="cuda")
-            out = torch.empty(len(r_ref), dtype=torch.float64, device="cuda")
-            fit.residual_rms(truth_d, a, out)
-            torch.cuda.synchronize()
-            e_a = rel(a.double().cpu().numpy(), a_ref, f"alpha-sweep/commands/alpha{alpha}/frame{k}")
-            e_r = rel(out.cpu().numpy(), r_ref, f"alpha-sweep/rms/alpha{alpha}/frame{k}")
-            assert e_a < 1e-5, (alpha, k, e_a)
-            assert e_r < 1e-5, (alpha, k, e_r)
-            rms_g.append(float(out.mean()))
+            _, a_ref, r_ref = qs.oracle_point(alpha, truth, s, iters)
+            a, r = _gpu_point(torch, pkg, plan, fit, truth, s, iters, dt)
+            key = f"alpha-sweep/fp{64 if precision else 32}-{iters}it/alpha{alpha}/frame{k}"
+            e_a = rel(a, a_ref, key + "/commands")
+            e_r = rel(r, r_ref, key + "/rms")
+            assert e_a < tol_a, (alpha, k, e_a)
+            assert e_r < tol_r, (alpha, k, e_r)
+            rms_g.append(float(np.mean(r)))
             rms_o.append(float(np.mean(r_ref)))
         gpu_curve[alpha] = float(np.mean(rms_g))
         ora_curve[alpha] = float(np.mean(rms_o))
