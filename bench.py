@@ -527,7 +527,7 @@ def bench_closed_loop(pkg, torch, dev, flush, frames, gain=0.4, fit_iters=4):
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    l2 = l2_probe(torch, dev)
+    l2 = l2_probe(pkg, torch, dev)
     out = {"frames": frames, "gain": gain, "fit_iters": fit_iters, "tomo_iters": 10,
            "actuators": na, "actuators_reached": int(fit.info.n_active), "directions": nd,
            "control_steps_per_s": 1000.0 / float(ms[5:].mean()),
@@ -685,35 +685,52 @@ def bench_served(pkg, torch, args, dev, frames_per_tel=16, rate_hz=500.0):
         srv.submit(t, frames[i][0], tag=-1)
     srv.drain(120.0)
     srv.poll()
-    period = 1.0 / rate_hz
-    n_frames = int(args.serve_seconds * rate_hz)
-    rng = np.random.default_rng(3)
-    phase = rng.uniform(0.0, period, len(ids))
-    t0 = srv.clock() + 0.05
-    sched = sorted((t0 + phase[i] + k * period, i, k) for i in range(len(ids)) for k in range(n_frames))
-    results, lag, full = [], [], 0
-    j = 0
-    while j < len(sched):
-        now = srv.clock()
-        if sched[j][0] > now:
-            if sched[j][0] - now > 0.0005:
-                results += srv.poll()
-                time.sleep(0.0002)
-            continue
-        while j < len(sched) and sched[j][0] <= now:
-            ts, i, k = sched[j]
-            if not srv.submit(ids[i], frames[i][k % frames_per_tel], tag=k):
-                full += 1
-            lag.append(now - ts)
-            j += 1
-    srv.drain(300.0)
-    results += srv.poll()
-    stats = srv.stats()
+
+    def stream(rate, seconds, seed):
+        """Every telescope submits frames at `rate` Hz (seeded phases) for `seconds`."""
+        period = 1.0 / rate
+        n_frames = int(seconds * rate)
+        phase = np.random.default_rng(seed).uniform(0.0, period, len(ids))
+        launches0 = srv.stats()["launches"]
+        t0 = srv.clock() + 0.05
+        sched = sorted((t0 + phase[i] + k * period, i, k) for i in range(len(ids)) for k in range(n_frames))
+        results, lag, full = [], [], 0
+        j = 0
+        while j < len(sched):
+            now = srv.clock()
+            if sched[j][0] > now:
+                if sched[j][0] - now > 0.0005:
+                    results += srv.poll()
+                    time.sleep(0.0002)
+                continue
+            while j < len(sched) and sched[j][0] <= now:
+                ts, i, k = sched[j]
+                if not srv.submit(ids[i], frames[i][k % frames_per_tel], tag=k):
+                    full += 1
+                lag.append(now - ts)
+                j += 1
+        srv.drain(300.0)
+        results += srv.poll()
+        ok = [r for r in results if r["status"] == 0]
+        lat = np.array([r["t_done"] - r["t_submit"] for r in ok]) * 1000.0
+        span = max(r["t_done"] for r in ok) - t0
+        return sched, ok, results, lat, span, lag, full, srv.stats()["launches"] - launches0
+
+    # capacity curve: shorter streams at lower offered loads
+    curve = []
+    for rate in (250.0, 350.0, 425.0, 475.0):
+        sched, ok, results, lat, span, _, _, nl = stream(rate, 2.0, 7)
+        curve.append({"offered_frames_per_s": len(ids) * rate, "solves_per_s": len(ok) / span,
+                      "superseded_fraction": sum(1 for r in results if r["status"] == 10) / len(sched),
+                      "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                      "mean_frames_per_launch": len(ok) / max(1, nl)})
+    sched, ok, results, lat, span, lag, full, nl = stream(rate_hz, args.serve_seconds, 3)
     srv.close()
-    ok = [r for r in results if r["status"] == 0]
     superseded = sum(1 for r in results if r["status"] == 10)
-    lat = np.array([r["t_done"] - r["t_submit"] for r in ok]) * 1000.0
-    span = max(r["t_done"] for r in ok) - t0
+    curve.append({"offered_frames_per_s": len(ids) * rate_hz, "solves_per_s": len(ok) / span,
+                  "superseded_fraction": superseded / len(sched),
+                  "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                  "mean_frames_per_launch": len(ok) / max(1, nl)})
     kinds = {}
     for r in ok:
         name = geoms[ids.index(r["telescope"])]["name"].split("-")[0]
@@ -727,11 +744,13 @@ def bench_served(pkg, torch, args, dev, frames_per_tel=16, rate_hz=500.0):
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                        "max": float(lat.max())},
         "latency_ms_p99_by_family": {k: float(np.percentile(v, 99)) for k, v in kinds.items()},
-        "launches": stats["launches"], "mean_frames_per_launch": len(ok) / max(1, stats["launches"]),
+        "launches": nl, "mean_frames_per_launch": len(ok) / max(1, nl),
+        "capacity_curve": curve,
         "client_pacing_lag_ms_p99": float(np.percentile(np.array(lag) * 1000.0, 99)),
         "device_bytes_admitted": stats0["bytes_in_use"], "budget_bytes": stats0["budget_bytes"],
         "workload": "16 telescopes cycling the 8 m (FP32 PCG), E-ELT and uneven-instance "
-                    "geometries; 500 Hz frozen-flow frames each; 10 PCG iterations, warm start",
+                    "geometries; 500 Hz frozen-flow frames each; 10 PCG iterations, warm start; "
+                    "capacity curve: 2 s streams at 250-475 Hz per telescope, then the 500 Hz stream",
     }
 
 
