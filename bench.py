@@ -302,7 +302,7 @@ def launch_bytes(plans, geoms):
         e = 8 if p.precision else 4
         n = p.n
         V = (p.info.bytes_per_iteration // e - (15 if g["precond"] else 13) * n) // 2
-        split = p.info.kernels_per_iteration == 5
+        split = bool(p.info.gather_separate)
         out["synthesis"] += 5 * n * e
         out["forward"] += (n + V) * e
         out["analysis"] += (3 * n if split else 2 * n + V) * e

@@ -125,6 +125,8 @@ typedef struct {
                                     (n_sub + 1)^2 each) */
   int precision;
   int breakdown_pending;       /* 1: a solve of the plan broke down and no call has reported it yet */
+  int gather_separate;         /* 1: the transposed ray-trace runs in its own kernel before the analysis */
+  int streamed;                /* 1: streamed transforms (tomo_plan_options.transforms) */
 } tomo_plan_info;
 
 /* Launch shape of a plan (zero-initialise; every field 0 means the default). */
@@ -133,7 +135,11 @@ typedef struct {
                                   per layer): 0 = min(16, N_min/8); else a power of two in
                                   [1, min(16, N_min/2)].  Large clusters give the lowest latency of
                                   one solve, small ones the most solves per second in big batches */
-  int reserved[7];             /* must be 0 */
+  int transforms;              /* 0: chosen by the plan; 1: one thread-block cluster per layer and
+                                  transform; 2: streamed, level by level over row tiles of every
+                                  layer with no cluster (the default when a layer's cluster CTAs
+                                  could not share an SM, e.g. 512^2 layers) */
+  int reserved[6];             /* must be 0 */
 } tomo_plan_options;
 
 /* Build a plan: validates `g`, copies every host input, builds the index

@@ -68,7 +68,7 @@ class ServerStats(ctypes.Structure):
 
 
 class PlanOptions(ctypes.Structure):
-    _fields_ = [("cluster_size", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+    _fields_ = [("cluster_size", ctypes.c_int), ("transforms", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -77,7 +77,7 @@ class PlanInfo(ctypes.Structure):
                 ("cluster_size", ctypes.c_int), ("kernels_per_iteration", ctypes.c_int),
                 ("kernels_per_solve_base", ctypes.c_int), ("device_bytes", ctypes.c_longlong),
                 ("bytes_per_iteration", ctypes.c_longlong), ("precision", ctypes.c_int),
-                ("breakdown_pending", ctypes.c_int)]
+                ("breakdown_pending", ctypes.c_int), ("gather_separate", ctypes.c_int), ("streamed", ctypes.c_int)]
 
 
 class Dm(ctypes.Structure):
@@ -227,12 +227,13 @@ def geometry_struct(geom):
 class Plan:
     """One adaptive-optics system: tables, prior, Jacobi diagonal and workspace on the GPU."""
 
-    def __init__(self, geom, stream=None, cluster_size=0):
+    def __init__(self, geom, stream=None, cluster_size=0, transforms=0):
         lib = load_library()
         g, keep = geometry_struct(geom)
         h = ctypes.c_void_p()
         opt = PlanOptions()
         opt.cluster_size = int(cluster_size)
+        opt.transforms = int(transforms)
         _check(lib.tomo_plan_create_ex(ctypes.byref(g), ctypes.byref(opt), _stream(stream),
                                        ctypes.byref(h)))
         self._h = h

@@ -100,8 +100,33 @@ tomo_status timed(tomo_plan *p, int kind, cudaStream_t s, F fn, const char *what
     if (st_ != TOMO_OK) return st_;   \
   } while (0)
 
+// W of the grids a separate gather left in phi (src 2) or of io.in0's layers
+// (src 0), with epilogue epi, for a launch set without the fused gather.
+cudaError_t anal_ls(const LaunchSet &L, int src, int epi, int flags, const IoArgs &io, cudaStream_t s) {
+  return L.stream ? launch_analysis_streamed(L.precision, src, epi, L.lf, flags, L.d_inst, L.ss, io, s)
+                  : launch_analysis(L.precision, src, epi, L.lf, flags, L.d_inst, L.cl, L.n_cl, L.C, L.smem_a, io, s,
+                                    0, 0);
+}
+int anal_launches(const LaunchSet &L) { return L.stream ? streamed_launches(L.ss) : 1; }
+
+// The gather of the plan's corner fields and W of the result with epilogue epi
+// (0 plain into io.out0, 1 operator with p = io.in1 and q = io.out0): the fused
+// kernel, or the separate gather and then the transform.
+tomo_status adjoint_ls(tomo_plan *p, const LaunchSet &L, int epi, const IoArgs &io, cudaStream_t s) {
+  if (!L.split)
+    return timed(p, kKindAnalysis, s, [&] {
+      return launch_analysis(L.precision, 1, epi, L.lf, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem_a, io, s, 0, 0);
+    }, "analysis");
+  const int tt_mode = epi == 1 ? 0 : 2;   // operator: the model term; otherwise the data alone
+  TOMO_TRY(timed(p, kKindGather, s, [&] {
+    return launch_gather(L.precision, tt_mode, L.d_inst, L.cl, L.n_cl, L.C, L.smem_g, io, s);
+  }, "gather"));
+  return timed(p, kKindAnalysis, s, [&] { return anal_ls(L, 2, epi, 0, io, s); }, "analysis", anal_launches(L));
+}
+
 // The launch sequence of one solve (Sec. 5.1): right-hand side and initial
-// residual, then `iters` (P)CG iterations of four kernels each.
+// residual, then `iters` (P)CG iterations: synthesis, forward, (gather,)
+// analysis, update.
 tomo_status enqueue_solve(tomo_plan *tp, const LaunchSet &L, const void *const *slopes,
                           void *const *x, int iters, int warm, cudaStream_t s, int *n_kernels,
                           const int *active = nullptr) {
@@ -110,10 +135,9 @@ tomo_status enqueue_solve(tomo_plan *tp, const LaunchSet &L, const void *const *
     IoArgs io{};
     io.active = active;
     for (int i = 0; i < L.count; ++i) io.in0[i] = x[i];
-    TOMO_TRY(timed(tp, kKindSynth, s, [&] {
-      return launch_synthesis(L.precision, 0, L.lf, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem, io, s);
-    }, "synthesis (warm start)"));
-    ++nk;
+    TOMO_TRY(timed(tp, kKindSynth, s, [&] { return synthesis_of(L, 0, 0, io, s); }, "synthesis (warm start)",
+                   synthesis_launches(L)));
+    nk += synthesis_launches(L);
   }
   {
     IoArgs io{};
@@ -131,41 +155,48 @@ tomo_status enqueue_solve(tomo_plan *tp, const LaunchSet &L, const void *const *
       io.out0[i] = x[i];
       io.in1[i] = slopes[i];   // tip/tilt-only sensors' data term
     }
-    if (L.split)
+    if (L.split) {
       TOMO_TRY(timed(tp, kKindGather, s, [&] {
         return launch_gather(L.precision, warm ? 1 : 2, L.d_inst, L.cl, L.n_cl, L.C, L.smem_g, io, s);
       }, "gather (residual)"));
-    TOMO_TRY(timed(tp, kKindAnalysis, s, [&] {
-      return launch_analysis(L.precision, L.split ? 2 : 1, 2, L.lf, warm ? kFlagWarm : 0, L.d_inst, L.cl, L.n_cl,
-                             L.C, L.smem_a, io, s, 0, 0);
-    }, "analysis (residual)"));
-    nk += analysis_launches(1, L.split);
+      TOMO_TRY(timed(tp, kKindAnalysis, s, [&] { return anal_ls(L, 2, 2, warm ? kFlagWarm : 0, io, s); },
+                     "analysis (residual)", anal_launches(L)));
+      nk += 1 + anal_launches(L);
+    } else {
+      TOMO_TRY(timed(tp, kKindAnalysis, s, [&] {
+        return launch_analysis(L.precision, 1, 2, L.lf, warm ? kFlagWarm : 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem_a,
+                               io, s, 0, 0);
+      }, "analysis (residual)"));
+      ++nk;
+    }
   }
   for (int it = 0; it < iters; ++it) {
     IoArgs none{};
     none.active = active;
     TOMO_TRY(timed(tp, kKindSynth, s, [&] {
-      return launch_synthesis(L.precision, 1, L.lf, (it == 0 ? kFlagFirst : 0) | (it << kIterShift), L.d_inst,
-                              L.cl, L.n_cl, L.C, L.smem, none, s);
-    }, "synthesis"));
+      return synthesis_of(L, 1, (it == 0 ? kFlagFirst : 0) | (it << kIterShift), none, s);
+    }, "synthesis", synthesis_launches(L)));
     TOMO_TRY(timed(tp, kKindFwd, s, [&] {
       return launch_forward(L.precision, 0, L.max_layers, L.elong, L.d_inst, L.fwd, L.n_fwd, none, s);
     }, "forward"));
-    if (L.split)
+    if (L.split) {
       TOMO_TRY(timed(tp, kKindGather, s, [&] {
         return launch_gather(L.precision, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem_g, none, s);
       }, "gather"));
-    TOMO_TRY(timed(tp, kKindAnalysis, s, [&] {
-      return launch_analysis(L.precision, L.split ? 2 : 1, 1, L.lf, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem_a, none,
-                             s, 0, 0);
-    }, "analysis"));
+      TOMO_TRY(timed(tp, kKindAnalysis, s, [&] { return anal_ls(L, 2, 1, it << kIterShift, none, s); }, "analysis",
+                     anal_launches(L)));
+    } else {
+      TOMO_TRY(timed(tp, kKindAnalysis, s, [&] {
+        return launch_analysis(L.precision, 1, 1, L.lf, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem_a, none, s, 0, 0);
+      }, "analysis"));
+    }
     IoArgs io{};
     io.active = active;
     for (int i = 0; i < L.count; ++i) io.out0[i] = x[i];
     TOMO_TRY(timed(tp, kKindUpd, s, [&] {
       return launch_update(L.precision, it << kIterShift, L.d_inst, L.upd, L.n_upd, io, s);
     }, "update"));
-    nk += 3 + analysis_launches(1, L.split);
+    nk += synthesis_launches(L) + 2 + (L.split ? 1 + anal_launches(L) : 1);
   }
   if (n_kernels) *n_kernels = nk;
   return TOMO_OK;
@@ -188,7 +219,7 @@ tomo_status read_resnorm(tomo_plan *p, int iters, cudaStream_t s, double *out) {
   TOMO_CUDA(cudaMemcpyAsync(sc, p->h_inst.scal, sizeof(sc), cudaMemcpyDeviceToHost, s), "reading scalars");
   TOMO_CUDA(cudaStreamSynchronize(s), "synchronising the solve");
   const int off = iters > 0 ? H.upd_part_off : H.cl_part_off;
-  const int cnt = iters > 0 ? H.n_upd_blocks : H.n_layers * H.C;
+  const int cnt = iters > 0 ? H.n_upd_blocks : H.n_cl_part;
   double rr = 0.0;
   for (int q = 0; q < cnt; ++q) rr += part[off + 2 * q + 1];
   *out = std::sqrt(std::max(0.0, rr));
@@ -268,7 +299,7 @@ tomo_status build_batch(tomo_plan *const *plans, int count, Batch **out) {
     for (auto &cand : b->groups) {
       const HostPlan &H0 = plans[cand.members[0]]->hp;
       if (H0.C == H.C && H0.Lf == H.Lf && H0.precision == H.precision &&
-          H0.gather_staged == H.gather_staged &&
+          H0.gather_staged == H.gather_staged && H0.stream_tf == H.stream_tf &&
           static_cast<int>(cand.members.size()) < kMaxBatch)
         g = &cand;
     }
@@ -284,6 +315,7 @@ tomo_status build_batch(tomo_plan *const *plans, int count, Batch **out) {
     std::vector<ClusterItem> cl;
     std::vector<FwdItem> fwd;
     std::vector<UpdItem> upd;
+    std::vector<PassItem> pass[kMaxLevels + 1], coarse;
     LaunchSet &L = g.ls;
     for (int slot = 0; slot < k; ++slot) {
       const tomo_plan *p = plans[g.members[slot]];
@@ -307,18 +339,44 @@ tomo_status build_batch(tomo_plan *const *plans, int count, Batch **out) {
       L.split = H.gather_staged ? 0 : 1;
       L.smem_g = std::max(L.smem_g, static_cast<size_t>(H.smem_gather));
       for (const auto &w : H.wfs) L.elong |= w.elong;
+      L.stream = H.stream_tf;
+      if (H.stream_tf) {
+        for (int lv = 1; lv <= H.pass_kmax; ++lv)
+          for (int q = 0; q < H.pass_cnt[lv]; ++q) {
+            PassItem it = H.pass_items[H.pass_off[lv] + q];
+            it.inst = slot;
+            pass[lv].push_back(it);
+          }
+        for (PassItem it : H.coarse_items) {
+          it.inst = slot;
+          coarse.push_back(it);
+        }
+        L.ss.kmax = std::max(L.ss.kmax, H.pass_kmax);
+        L.ss.smem_pass = std::max(L.ss.smem_pass, static_cast<size_t>(H.smem_pass));
+        L.ss.smem_coarse = std::max(L.ss.smem_coarse, static_cast<size_t>(H.smem_coarse));
+      }
+    }
+    std::vector<PassItem> passes;
+    for (int lv = 1; lv <= L.ss.kmax; ++lv) {
+      L.ss.off[lv] = static_cast<int>(passes.size());
+      L.ss.cnt[lv] = static_cast<int>(pass[lv].size());
+      passes.insert(passes.end(), pass[lv].begin(), pass[lv].end());
     }
     Arena A;
     const size_t o_i = A.take(sizeof(InstDev) * insts.size());
     const size_t o_c = A.take(sizeof(ClusterItem) * cl.size());
     const size_t o_f = A.take(sizeof(FwdItem) * fwd.size());
     const size_t o_u = A.take(sizeof(UpdItem) * upd.size());
+    const size_t o_ps = A.take(sizeof(PassItem) * std::max<size_t>(1, passes.size()));
+    const size_t o_co = A.take(sizeof(PassItem) * std::max<size_t>(1, coarse.size()));
     const size_t bytes = align_up(A.size, 256);
     std::vector<char> img(bytes, 0);
     std::memcpy(img.data() + o_i, insts.data(), sizeof(InstDev) * insts.size());
     std::memcpy(img.data() + o_c, cl.data(), sizeof(ClusterItem) * cl.size());
     std::memcpy(img.data() + o_f, fwd.data(), sizeof(FwdItem) * fwd.size());
     std::memcpy(img.data() + o_u, upd.data(), sizeof(UpdItem) * upd.size());
+    if (!passes.empty()) std::memcpy(img.data() + o_ps, passes.data(), sizeof(PassItem) * passes.size());
+    if (!coarse.empty()) std::memcpy(img.data() + o_co, coarse.data(), sizeof(PassItem) * coarse.size());
     cudaError_t e = cudaMalloc(&g.arena, bytes);
     g.bytes = bytes;
     if (e == cudaSuccess) e = cudaMemcpy(g.arena, img.data(), bytes, cudaMemcpyHostToDevice);
@@ -335,6 +393,9 @@ tomo_status build_batch(tomo_plan *const *plans, int count, Batch **out) {
     L.n_fwd = static_cast<int>(fwd.size());
     L.upd = reinterpret_cast<const UpdItem *>(base + o_u);
     L.n_upd = static_cast<int>(upd.size());
+    L.ss.items = reinterpret_cast<const PassItem *>(base + o_ps);
+    L.ss.coarse = reinterpret_cast<const PassItem *>(base + o_co);
+    L.ss.n_coarse = static_cast<int>(coarse.size());
   }
   cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
@@ -412,6 +473,18 @@ tomo_status batch_solve(Batch *b, const void *const *slopes, void *const *x, con
 
 }  // namespace tomo
 
+namespace tomo {
+
+// W^-1 of a launch set: the cluster kernel, or the streamed coarse kernel and
+// passes.  src 0: io.in0 coefficients; 1: the PCG direction update fused in.
+cudaError_t synthesis_of(const LaunchSet &L, int src, int flags, const IoArgs &io, cudaStream_t s) {
+  return L.stream ? launch_synthesis_streamed(L.precision, src, L.lf, flags, L.d_inst, L.ss, io, s)
+                  : launch_synthesis(L.precision, src, L.lf, flags, L.d_inst, L.cl, L.n_cl, L.C, L.smem, io, s);
+}
+int synthesis_launches(const LaunchSet &L) { return L.stream ? streamed_launches(L.ss) : 1; }
+
+}  // namespace tomo
+
 extern "C" {
 
 const char *tomo_version(void) { return "tomo-gb300 0.1 (sm_103a)"; }
@@ -428,17 +501,18 @@ tomo_status tomo_plan_create_ex(const tomo_geometry *g, const tomo_plan_options 
                                 tomo_plan **out) {
   if (!out) return fail(TOMO_ERR_ARG, "out is NULL");
   *out = nullptr;
-  int creq = 0;
+  int creq = 0, treq = 0;
   if (opt) {
     for (int r : opt->reserved)
       if (r != 0) return fail(TOMO_ERR_ARG, "tomo_plan_options.reserved must be zero");
     if (opt->cluster_size < 0) return fail(TOMO_ERR_ARG, "cluster size must be >= 0");
     creq = opt->cluster_size;
+    treq = opt->transforms;
   }
   tomo_plan *p = new (std::nothrow) tomo_plan();
   if (!p) return fail(TOMO_ERR_NOMEM, "host allocation failed");
   std::string err;
-  tomo_status st = build_host_plan(g, &p->hp, &err, creq);
+  tomo_status st = build_host_plan(g, &p->hp, &err, creq, treq);
   if (st != TOMO_OK) {
     delete p;
     return fail(st, err);
@@ -498,6 +572,8 @@ tomo_status tomo_plan_create_ex(const tomo_geometry *g, const tomo_plan_options 
   const size_t o_cl = A.take(sizeof(ClusterItem) * H.cl_items.size());
   const size_t o_fwd = A.take(sizeof(FwdItem) * H.fwd_items.size());
   const size_t o_upd = A.take(sizeof(UpdItem) * H.upd_items.size());
+  const size_t o_pass = A.take(sizeof(PassItem) * std::max<size_t>(1, H.pass_items.size()));
+  const size_t o_coarse = A.take(sizeof(PassItem) * std::max<size_t>(1, H.coarse_items.size()));
   const size_t tables_end = align_up(A.size, 256);
   const size_t n = static_cast<size_t>(H.n);
   const size_t o_r = A.take(esz * n);
@@ -511,6 +587,9 @@ tomo_status tomo_plan_create_ex(const tomo_geometry *g, const tomo_plan_options 
   const size_t o_jdiag = A.take(sizeof(double) * n);
   const size_t o_scal = A.take(sizeof(double) * kNumScalars);
   const size_t o_part = A.take(sizeof(double) * std::max(1, H.n_part));
+  // streamed transforms: the second direction buffer and the low-low scratch
+  const size_t o_p2 = H.stream_tf ? A.take(esz * n) : 0;
+  const size_t o_lls = H.stream_tf ? A.take(esz * std::max<long long>(1, H.lls_elems)) : 0;
   p->arena_bytes = align_up(A.size, 256);
   ce = cudaMalloc(&p->arena, p->arena_bytes);
   if (ce != cudaSuccess) {
@@ -556,6 +635,10 @@ tomo_status tomo_plan_create_ex(const tomo_geometry *g, const tomo_plan_options 
   I.jinv = base + o_jinv;
   I.scal = reinterpret_cast<double *>(base + o_scal);
   I.part = reinterpret_cast<double *>(base + o_part);
+  I.stream_tf = H.stream_tf;
+  I.n_cl_part = H.n_cl_part;
+  I.p2 = H.stream_tf ? base + o_p2 : nullptr;
+  I.lls = H.stream_tf ? base + o_lls : nullptr;
   I.layers = reinterpret_cast<const LayerDev *>(base + o_layers);
   I.wfs = reinterpret_cast<const WfsDev *>(base + o_wfs);
   I.sub_idx = reinterpret_cast<const int *>(base + o_sub);
@@ -654,6 +737,8 @@ tomo_status tomo_plan_create_ex(const tomo_geometry *g, const tomo_plan_options 
   put(o_cl, H.cl_items.data(), sizeof(ClusterItem) * H.cl_items.size());
   put(o_fwd, H.fwd_items.data(), sizeof(FwdItem) * H.fwd_items.size());
   put(o_upd, H.upd_items.data(), sizeof(UpdItem) * H.upd_items.size());
+  put(o_pass, H.pass_items.data(), sizeof(PassItem) * H.pass_items.size());
+  put(o_coarse, H.coarse_items.data(), sizeof(PassItem) * H.coarse_items.size());
 
   auto bail = [&](tomo_status code, const std::string &msg) {
     cudaFree(p->arena);
@@ -713,6 +798,20 @@ tomo_status tomo_plan_create_ex(const tomo_geometry *g, const tomo_plan_options 
   L.smem_g = static_cast<size_t>(H.smem_gather);
   L.elong = 0;
   for (const auto &w : H.wfs) L.elong |= w.elong;
+  L.stream = H.stream_tf;
+  if (H.stream_tf) {
+    StreamSet &S = L.ss;
+    S.items = reinterpret_cast<const PassItem *>(base + o_pass);
+    S.kmax = H.pass_kmax;
+    for (int k = 1; k <= H.pass_kmax; ++k) {
+      S.off[k] = H.pass_off[k];
+      S.cnt[k] = H.pass_cnt[k];
+    }
+    S.coarse = reinterpret_cast<const PassItem *>(base + o_coarse);
+    S.n_coarse = static_cast<int>(H.coarse_items.size());
+    S.smem_pass = static_cast<size_t>(H.smem_pass);
+    S.smem_coarse = static_cast<size_t>(H.smem_coarse);
+  }
   *out = p;
   g_err.clear();
   return TOMO_OK;
@@ -746,8 +845,12 @@ tomo_status tomo_plan_get_info(const tomo_plan *p, tomo_plan_info *out) {
   out->n_layers = H.n_layers;
   out->n_wfs = H.n_wfs;
   out->cluster_size = H.C;
-  out->kernels_per_iteration = 3 + analysis_launches(1, p->ls.split);
-  out->kernels_per_solve_base = 2 + analysis_launches(1, p->ls.split);
+  const LaunchSet &L = p->ls;
+  const int adj = L.split ? 1 + anal_launches(L) : 1;
+  out->kernels_per_iteration = synthesis_launches(L) + 2 + adj;
+  out->kernels_per_solve_base = synthesis_launches(L) + 1 + adj;
+  out->gather_separate = L.split;
+  out->streamed = L.stream;
   out->device_bytes = static_cast<long long>(p->arena_bytes);
   // p-update + W^-1 (r, J^-1, p in; p, phi out), ray-trace (phi in, v out),
   // gather + W + prior (v, p in; q out), update (x, p, r, q, J^-1 in; x, r out)
@@ -862,9 +965,7 @@ tomo_status tomo_coeffs_to_layers(tomo_plan *p, const void *d_coeffs, void *d_la
   IoArgs io{};
   io.in0[0] = d_coeffs;
   io.out0[0] = d_layers;
-  return timed(p, kKindSynth, s, [&] {
-    return launch_synthesis(L.precision, 0, L.lf, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem, io, s);
-  }, "synthesis");
+  return timed(p, kKindSynth, s, [&] { return synthesis_of(L, 0, 0, io, s); }, "synthesis", synthesis_launches(L));
 }
 
 tomo_status tomo_layers_to_coeffs(tomo_plan *p, const void *d_layers, void *d_coeffs, void *cuda_stream) {
@@ -876,9 +977,7 @@ tomo_status tomo_layers_to_coeffs(tomo_plan *p, const void *d_layers, void *d_co
   IoArgs io{};
   io.in0[0] = d_layers;
   io.out0[0] = d_coeffs;
-  return timed(p, kKindAnalysis, s, [&] {
-    return launch_analysis(L.precision, 0, 0, L.lf, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem_a, io, s, L.split, L.smem_g);
-  }, "analysis");
+  return timed(p, kKindAnalysis, s, [&] { return anal_ls(L, 0, 0, 0, io, s); }, "analysis", anal_launches(L));
 }
 
 tomo_status tomo_layers_to_slopes(tomo_plan *p, const void *d_layers, void *d_slopes, void *cuda_stream) {
@@ -903,18 +1002,14 @@ tomo_status tomo_apply_normal(tomo_plan *p, const void *d_in, void *d_out, void 
   const LaunchSet &L = p->ls;
   IoArgs a{};
   a.in0[0] = d_in;
-  TOMO_TRY(timed(p, kKindSynth, s, [&] {
-    return launch_synthesis(L.precision, 0, L.lf, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem, a, s);
-  }, "synthesis"));
+  TOMO_TRY(timed(p, kKindSynth, s, [&] { return synthesis_of(L, 0, 0, a, s); }, "synthesis", synthesis_launches(L)));
   IoArgs b{};
   TOMO_TRY(timed(p, kKindFwd, s, [&] { return launch_forward(L.precision, 0, L.max_layers, L.elong, L.d_inst, L.fwd, L.n_fwd, b, s); },
                  "forward"));
   IoArgs c{};
   c.in1[0] = d_in;
   c.out0[0] = d_out;
-  return timed(p, kKindAnalysis, s, [&] {
-    return launch_analysis(L.precision, 1, 1, L.lf, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem_a, c, s, L.split, L.smem_g);
-  }, "analysis", analysis_launches(1, L.split));
+  return adjoint_ls(p, L, 1, c, s);
 }
 
 tomo_status tomo_rhs(tomo_plan *p, const void *d_slopes, void *d_out, void *cuda_stream) {
@@ -930,9 +1025,7 @@ tomo_status tomo_rhs(tomo_plan *p, const void *d_slopes, void *d_out, void *cuda
   IoArgs c{};
   c.out0[0] = d_out;
   c.in1[0] = d_slopes;
-  return timed(p, kKindAnalysis, s, [&] {
-    return launch_analysis(L.precision, 1, 0, L.lf, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem_a, c, s, L.split, L.smem_g);
-  }, "analysis", analysis_launches(1, L.split));
+  return adjoint_ls(p, L, 0, c, s);
 }
 
 tomo_status tomo_jacobi_diagonal(tomo_plan *p, double *d_out, void *cuda_stream) {

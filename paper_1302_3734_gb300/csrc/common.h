@@ -24,6 +24,9 @@ constexpr int kMaxGatherSensors = 64;  // dense sensors the separate gather kern
 constexpr int kUpdChunk = 1024;    // coefficients per pass of a vector-update CTA
 constexpr int kUpdMaxBlocks = 608; // update CTAs per instance at most (four per SM of 152 SMs)
 constexpr int kMaxTapsNode = 4;    // corners per axis whose bilinear taps reach one node
+constexpr int kPassRows = 8;       // half-rows of a level one CTA of a streamed transform pass covers
+constexpr int kPassThreads = 512;  // threads per CTA of the streamed transform kernels
+constexpr int kCoarseMax = 64;     // block side up to which one CTA finishes a layer's transform
 
 enum WfsKind : int { kFull = 0, kRemoveTT = 1, kTTOnly = 2 };
 
@@ -48,6 +51,12 @@ struct LayerDev {
   int cache_kc;                 // transforms cache the coefficients of levels >= cache_kc
   double dalpha[kMaxLevels + 1];  // alpha * D at level k (index k = 1..J)
   double dprior[kMaxLevels + 1];  // D at level k, without alpha
+  // Streamed transforms: levels 1..ks-1 run as row-tile passes over the whole
+  // grid, levels ks..J in one CTA per layer (block side N >> (ks - 1) <= kCoarseMax);
+  // ll_off[k]: offset in the plan's scratch of the low-low block of level k
+  // (side N >> k), k = 1..ks-1.
+  int ks, pad_ks;
+  int ll_off[kMaxLevels + 1];
 };
 
 struct WfsDev {
@@ -139,6 +148,13 @@ struct InstDev {
   const void *edge_t;           // (t_x, t_y) of each edge corner (T, interleaved)
   const int *run_rows;          // per sensor (n+1): start of row b's runs in run_ab
   const int2 *run_ab;           // [a_lo, a_hi) runs of valid subapertures in a row
+  // Streamed transforms (stream_tf != 0): the direction p of PCG iteration it
+  // lives in p (it even) or p2 (it odd), since a pass reads the previous
+  // direction of halo rows that another CTA rewrites; lls holds the low-low
+  // blocks between the passes.  n_cl_part: (dot, dot) partials of the analysis
+  // CTAs at cl_part_off.
+  int stream_tf, n_cl_part;
+  void *p2, *lls;
   // The plan's breakdown word: page-locked host memory mapped into the device
   // address space.  The update kernel sets it to 1 when a (P)CG step breaks
   // down; only the host clears it, after reporting it (NULL: not recorded).
@@ -238,6 +254,30 @@ TOMO_HD inline GatherSmem gather_smem_layout(int R0, int N, int KT, int esz) {
 
 // Work items.
 struct ClusterItem { int inst, layer; };
+// One CTA of a streamed transform: a tile of kPassRows half-rows from row0 (a
+// pass), or a whole layer's coarse levels (row0 unused); slot: its partial pair.
+struct PassItem { int inst, layer, row0, slot; };
+
+// The work of a streamed transform over one launch: pass items per level
+// (items[off[k] .. off[k] + cnt[k]) for level k = 1..kmax), then one coarse
+// item per layer; dynamic shared memory of the passes and of the coarse kernel.
+struct StreamSet {
+  const PassItem *items = nullptr;
+  int off[kMaxLevels + 1] = {0}, cnt[kMaxLevels + 1] = {0};
+  int kmax = 0;
+  const PassItem *coarse = nullptr;
+  int n_coarse = 0;
+  size_t smem_pass = 0, smem_coarse = 0;
+};
+
+// Shared memory of a streamed pass at block side M (elements of T): the analysis
+// stages 2 kPassRows + LF - 2 input rows and their row transforms; the synthesis
+// 2 (kPassRows + LF/2 - 1) coefficient rows and their row syntheses.
+TOMO_HD inline int pass_smem_elems(int M, int LF) {
+  const int a = 2 * (2 * kPassRows + LF - 2) * M;
+  const int s = 4 * (kPassRows + LF / 2 - 1) * M;
+  return a > s ? a : s;
+}
 struct FwdItem { int inst, wfs, a0, b0, tile, pad0, pad1, pad2; };  // a0 < 0: tip/tilt-only sensor
 struct UpdItem { int inst, start, blk, chunks; };   // chunks: passes of kUpdChunk coefficients
 

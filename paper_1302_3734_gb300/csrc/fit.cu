@@ -1022,9 +1022,8 @@ tomo_status enqueue_call(tomo_fit *f, const tomo_fit::Call &c, cudaStream_t s, i
   io.in0[0] = c.x;
   io.out0[0] = f->phi;
   const tomo::LaunchSet &L = p->ls;
-  FIT_CUDA(tomo::launch_synthesis(L.precision, 0, L.lf, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem, io, s),
-           "synthesis of the reconstructed layers");
-  tomo::count_launches(1);
+  FIT_CUDA(tomo::synthesis_of(L, 0, 0, io, s), "synthesis of the reconstructed layers");
+  tomo::count_launches(tomo::synthesis_launches(L));
   FIT_TRY(enqueue_fit_any(f, f->phi, c.a, c.fit_iters, c.warm, s, &k2));
   int k3 = 0;
   if (c.kind == 2) {

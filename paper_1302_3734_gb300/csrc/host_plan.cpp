@@ -118,7 +118,7 @@ bool daubechies_filter(int p, std::vector<double> *h, std::string *err) {
 }
 
 tomo_status build_host_plan(const tomo_geometry *geo, HostPlan *P, std::string *err,
-                            int cluster_request) {
+                            int cluster_request, int transforms) {
   char buf[256];
   if (!geo || !geo->wfs || !geo->layers || geo->n_wfs < 1 || geo->n_layers < 1) {
     *err = "geometry, its sensor and layer arrays must be non-empty";
@@ -198,19 +198,51 @@ tomo_status build_host_plan(const tomo_geometry *geo, HostPlan *P, std::string *
     const long long esz = P->precision ? 8 : 4;
     const long long budget = 220LL * 1024 - 4096;   // opt-in limit minus static shared memory
     long long need = 0;
+    bool cluster_fits = true;
     for (auto &d : P->layers) {
       const long long base = transform_cache_offset(d.N, P->C);
       int kc = 1;
       while (kc <= J && (base + transform_cache_size(d.N, P->C, J, kc)) * esz > budget) ++kc;
       const long long bytes = (base + transform_cache_size(d.N, P->C, J, kc)) * esz;
-      if (bytes > budget) {
-        *err = "layer grids too large for the transform kernels at this precision";
-        return TOMO_ERR_UNSUPPORTED;
-      }
+      cluster_fits = cluster_fits && bytes <= budget;
       d.cache_kc = kc;
       need = std::max(need, bytes);
     }
     P->smem_transform = need;
+    // streamed transforms when asked, or when the cluster CTAs cannot share an SM
+    // (one cluster per GPC at a time) or do not fit at all
+    if (transforms < 0 || transforms > 2) {
+      *err = "transforms must be 0 (choose), 1 (clusters) or 2 (streamed)";
+      return TOMO_ERR_ARG;
+    }
+    P->stream_tf = transforms == 2 || (transforms == 0 && need > static_cast<long long>(108 * 1024));
+    if (!P->stream_tf && !cluster_fits) {
+      *err = "layer grids too large for the cluster transform kernels at this precision";
+      return TOMO_ERR_UNSUPPORTED;
+    }
+    if (P->stream_tf) {
+      int M0 = 1;
+      for (auto &d : P->layers) {
+        P->smem_pass = std::max<long long>(P->smem_pass, pass_smem_elems(d.N, P->Lf) * esz);
+        d.ks = 1;
+        while (d.ks <= J && (d.N >> (d.ks - 1)) > kCoarseMax) ++d.ks;
+        M0 = std::max(M0, d.N >> (d.ks - 1));
+        for (int k = 1; k < d.ks; ++k) {
+          d.ll_off[k] = static_cast<int>(P->lls_elems);
+          P->lls_elems += static_cast<long long>(d.N >> k) * (d.N >> k);
+        }
+        P->pass_kmax = std::max(P->pass_kmax, d.ks - 1);
+      }
+      P->smem_coarse = 3LL * M0 * M0 * esz;
+      if (P->smem_pass > budget || P->smem_coarse > budget) {
+        *err = "layer grids too large for the streamed transform kernels at this precision";
+        return TOMO_ERR_UNSUPPORTED;
+      }
+      if (P->lls_elems > (1LL << 31) - 1) {
+        *err = "layer grids too large for the streamed transforms' scratch";
+        return TOMO_ERR_UNSUPPORTED;
+      }
+    }
   }
 
   // --------------------------------------------------------------- sensors
@@ -593,6 +625,7 @@ tomo_status build_host_plan(const tomo_geometry *geo, HostPlan *P, std::string *
       fits = fits && st <= budget;
       need = std::max(need, st);
     }
+    fits = fits && !P->stream_tf;   // streamed transforms take the gather from its own kernel
     P->gather_staged = fits ? 1 : 0;
     P->smem_analysis = fits ? need : P->smem_transform;
     // the separate gather kernel: the band buffer (N/C rows of N), the band's row
@@ -691,8 +724,27 @@ tomo_status build_host_plan(const tomo_geometry *geo, HostPlan *P, std::string *
   // --------------------------------------------------------- work tables
   int part = 0;
   P->cl_part_off = part;
-  part += 2 * P->n_layers * P->C;   // (dot, second dot) per CTA
   for (int l = 0; l < P->n_layers; ++l) P->cl_items.push_back({0, l});
+  if (!P->stream_tf) {
+    P->n_cl_part = P->n_layers * P->C;   // (dot, second dot) per analysis CTA
+  } else {
+    // streamed: per level the row tiles of the layers that pass through it, then one
+    // coarse CTA per layer; every analysis CTA has its partial slot
+    int slot = 0;
+    for (int k = 1; k <= P->pass_kmax; ++k) {
+      P->pass_off[k] = static_cast<int>(P->pass_items.size());
+      for (int l = 0; l < P->n_layers; ++l) {
+        const LayerDev &d = P->layers[l];
+        if (k >= d.ks) continue;
+        const int H = (d.N >> (k - 1)) >> 1;
+        for (int r0 = 0; r0 < H; r0 += kPassRows) P->pass_items.push_back({0, l, r0, slot++});
+      }
+      P->pass_cnt[k] = static_cast<int>(P->pass_items.size()) - P->pass_off[k];
+    }
+    for (int l = 0; l < P->n_layers; ++l) P->coarse_items.push_back({0, l, 0, slot++});
+    P->n_cl_part = slot;
+  }
+  part += 2 * P->n_cl_part;
   // update CTAs: consecutive chunks of kUpdChunk coefficients, at most kUpdMaxBlocks CTAs
   // (the consumers of their partials sum one partial per CTA)
   const int chunks = (P->n + kUpdChunk - 1) / kUpdChunk;

@@ -67,12 +67,20 @@ struct HostPlan {
   std::vector<FwdItem> fwd_items;
   std::vector<ClusterItem> cl_items;
   std::vector<UpdItem> upd_items;
+  // streamed transforms: pass items grouped by level (pass_off[k], pass_cnt[k],
+  // k = 1..pass_kmax), one coarse item per layer, the analysis partials
+  int stream_tf = 0, n_cl_part = 0, pass_kmax = 0;
+  int pass_off[kMaxLevels + 1] = {0}, pass_cnt[kMaxLevels + 1] = {0};
+  std::vector<PassItem> pass_items, coarse_items;
+  long long smem_pass = 0, smem_coarse = 0, lls_elems = 0;
 };
 
 // Returns TOMO_OK or an error status with *err set.  cluster_request > 0 asks
 // for that many CTAs per layer in the transform kernels (0: the default).
+// transforms: 0 chooses, 1 asks for the cluster transforms, 2 for the streamed
+// ones (level by level over row tiles).
 tomo_status build_host_plan(const tomo_geometry *g, HostPlan *out, std::string *err,
-                            int cluster_request = 0);
+                            int cluster_request = 0, int transforms = 0);
 
 // Orthonormal Daubechies low-pass filter with p vanishing moments (2p taps),
 // by spectral factorisation; exposed for tests through the plan only.

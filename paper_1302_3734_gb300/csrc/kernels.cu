@@ -32,6 +32,7 @@
 #include "common.h"
 #include "device_util.cuh"
 #include "launch.h"
+#include "transform.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -61,34 +62,6 @@ __device__ __forceinline__ void store_tile_partial(double *slot, Acc<float> a, A
   if (threadIdx.x == 0) *reinterpret_cast<float4 *>(slot) = s;
 }
 
-// Copy one instance descriptor into shared memory.
-__device__ __forceinline__ void load_inst(InstDev *dst, const InstDev *src) {
-  const int nw = sizeof(InstDev) / sizeof(int);
-  const int *s = reinterpret_cast<const int *>(src);
-  int *d = reinterpret_cast<int *>(dst);
-  for (int i = threadIdx.x; i < nw; i += blockDim.x) d[i] = s[i];
-  __syncthreads();
-}
-
-// Asynchronous global -> shared copies (cp.async: 16 bytes through L2 only,
-// or one element) and their completion for the calling thread.
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
-  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(__cvta_generic_to_global(gmem))
-               : "memory");
-}
-template <typename T>
-__device__ __forceinline__ void cp_async_elem(T *smem, const T *gmem) {
-  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-  if constexpr (sizeof(T) == 4)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(__cvta_generic_to_global(gmem))
-                 : "memory");
-  else
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(__cvta_generic_to_global(gmem))
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // psi at corner (a, b) of sensor m: sum over layers of the bilinear
 // interpolation of phi_l at the corner's traced position (Sec. 2.1, P_m).
@@ -325,21 +298,6 @@ __global__ void __launch_bounds__(kFwdThreads) k_forward(const InstDev *__restri
 }
 
 // ------------------------------------------------------- transform helpers
-
-template <typename T, int LF>
-struct Filt {
-  T h[LF], g[LF];
-  // taps 2s + parity without a runtime array index
-  __device__ __forceinline__ T hs(int parity, int s) const { return parity ? h[2 * s + 1] : h[2 * s]; }
-  __device__ __forceinline__ T gs(int parity, int s) const { return parity ? g[2 * s + 1] : g[2 * s]; }
-  __device__ __forceinline__ void load(const InstDev &I) {
-#pragma unroll
-    for (int t = 0; t < LF; ++t) {
-      h[t] = T(I.h[t]);
-      g[t] = T(I.g[t]);
-    }
-  }
-};
 
 // Coefficients owned by cluster rank c of one layer, and their place in the
 // CTA's shared-memory cache.  Distributed levels k = 1..kd (block side
@@ -890,61 +848,6 @@ __global__ void __launch_bounds__(kGatherThreads, sizeof(T) == 4 ? 2 : 1) k_gath
   for (int node = threadIdx.x; node < R0 * N; node += blockDim.x) g[node] = A[node];
 }
 
-// Epilogue of the analysis for one output coefficient.
-enum Epi : int { kEpiPlain = 0, kEpiOp = 1, kEpiResid = 2 };
-
-template <typename T, int EPI>
-struct Emit {
-  T *out;          // plain: destination
-  const T *P;      // op: direction p (global), cached copy in `cache`
-  T *Q;            // op: q
-  T *R, *Pn, *X;   // resid: r, p, x
-  const T *jinv;
-  const T *cache;
-  const T *dalpha; // alpha D per level
-  int off, N, precond, warm;
-  Acc<T> acc0, acc1;
-  // What the epilogue of (row, col) reads besides w: p (op) or x (warm
-  // residual), from the cache when slot >= 0, and J^-1 (residual).  Fetched
-  // ahead so that several outputs' loads are in flight together.
-  struct Pre {
-    T a, j;
-  };
-  __device__ __forceinline__ Pre fetch(int row, int col, int slot) const {
-    Pre f{T(0), T(1)};
-    const int idx = off + row * N + col;
-    if (EPI == kEpiOp) {
-      f.a = slot >= 0 ? cache[slot] : P[idx];
-    } else if (EPI == kEpiResid) {
-      if (warm) f.a = slot >= 0 ? cache[slot] : X[idx];
-      if (precond) f.j = jinv[idx];
-    }
-    return f;
-  }
-  __device__ __forceinline__ void put(int row, int col, int level, T w, const Pre &f) {
-    const int idx = off + row * N + col;
-    if (EPI == kEpiPlain) {
-      out[idx] = w;
-    } else if (EPI == kEpiOp) {
-      const T q = w + dalpha[level] * f.a;
-      Q[idx] = q;
-      acc0.add_prod(f.a, q);
-    } else {
-      T r = w;
-      if (warm) r -= dalpha[level] * f.a;
-      else X[idx] = T(0);
-      const T z = precond ? f.j * r : r;
-      R[idx] = r;
-      Pn[idx] = z;
-      acc0.add_prod(r, z);
-      acc1.add_prod(r, r);
-    }
-  }
-  __device__ __forceinline__ void operator()(int row, int col, int level, T w, int slot) {
-    put(row, col, level, w, fetch(row, col, slot));
-  }
-};
-
 // ------------------------------------------------------------ k_analysis
 // SRC 0: layer grids from io.in0.  SRC 1: adjoint gather from the plan's v.
 // SRC 2: the gather k_gather left in the plan's phi.
@@ -1232,7 +1135,7 @@ __global__ void __launch_bounds__(kSynthThreads, 1) k_synthesis(const InstDev *_
     // r.z of this iteration; the first CTA of the instance records it
     const double prev = I.scal[kRz0 + ((iter + 1) & 1)];
     const double flag = I.scal[kFlag];
-    const double2 s = iter == 0 ? sum_partials(I.part + I.cl_part_off, I.n_layers * C)
+    const double2 s = iter == 0 ? sum_partials(I.part + I.cl_part_off, I.n_cl_part)
                                 : sum_partials(I.part + I.upd_part_off, I.n_upd_blocks);
     if (tid == 0) {
       double beta = 0.0;
@@ -1520,12 +1423,12 @@ __global__ void __launch_bounds__(kThreads) k_update(const InstDev *__restrict__
   const InstDev *I = insts + it.inst;
   T *X = static_cast<T *>(io.out0[it.inst]);
   T *R = static_cast<T *>(I->r);
-  const T *P = static_cast<const T *>(I->p);
+  const int iter = flags >> kIterShift;
+  const T *P = dir_buffer<T>(*I, iter);
   const T *Q = static_cast<const T *>(I->q);
   const T *Jv = static_cast<const T *>(I->jinv);
   const int precond = I->precond;
   const int n = I->n;
-  const int iter = flags >> kIterShift;
   pdl_wait();
   const bool aligned = ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(R) |
                          reinterpret_cast<uintptr_t>(P) | reinterpret_cast<uintptr_t>(Q) |
@@ -1538,7 +1441,7 @@ __global__ void __launch_bounds__(kThreads) k_update(const InstDev *__restrict__
   {
     const double rz = I->scal[kRz0 + (iter & 1)];
     const double flag = I->scal[kFlag];
-    const double2 pq = sum_partials(I->part + I->cl_part_off, I->n_layers * I->C);
+    const double2 pq = sum_partials(I->part + I->cl_part_off, I->n_cl_part);
     if (threadIdx.x == 0) {
       // r = 0 (so p = 0 and p.Ap = 0) means the iterate is already exact: step 0
       const bool exact = (pq.x == 0.0 && rz == 0.0);
@@ -1824,6 +1727,7 @@ cudaError_t anal_t(int src, int epi, int lf, int flags, const InstDev *insts, co
 cudaError_t configure_kernels() {
   cudaError_t e = allow_type<float>();
   if (e == cudaSuccess) e = allow_type<double>();
+  if (e == cudaSuccess) e = configure_streamed_kernels();
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
   return e;

@@ -35,6 +35,18 @@ cudaError_t launch_analysis(int precision, int src, int epi, int lf, int flags, 
 cudaError_t launch_gather(int precision, int tt_mode, const InstDev *insts, const ClusterItem *items,
                           int n_clusters, int C, size_t smem_gather, const IoArgs &io, cudaStream_t s);
 
+// Streamed transforms (plans with stream_tf): the synthesis launches the coarse
+// kernel, then the passes from the coarsest streamed level down to level 1; the
+// analysis the passes from level 1 up, then the coarse kernel.  src as in
+// launch_synthesis / launch_analysis (the analysis: 0 = io.in0 layers, 2 = the
+// gathered grids in phi); streamed_launches: kernels one such call launches.
+cudaError_t launch_synthesis_streamed(int precision, int src, int lf, int flags, const InstDev *insts,
+                                      const StreamSet &S, const IoArgs &io, cudaStream_t s);
+cudaError_t launch_analysis_streamed(int precision, int src, int epi, int lf, int flags, const InstDev *insts,
+                                     const StreamSet &S, const IoArgs &io, cudaStream_t s);
+int streamed_launches(const StreamSet &S);
+cudaError_t configure_streamed_kernels();
+
 // Kernels one launch_analysis call launches.
 inline int analysis_launches(int src, int split) { return (src == 1 && split) ? 2 : 1; }
 

@@ -31,6 +31,8 @@ struct LaunchSet {
   int split = 0;                 // gather in its own kernel (tables not staged in shared memory)
   size_t smem_g = 0;             // its dynamic shared memory
   int elong = 0;                 // some sensor has elongated spots (k_forward variant)
+  int stream = 0;                // streamed transforms (level passes over row tiles, no clusters)
+  StreamSet ss;                  // their work items
 };
 
 struct Timer {
@@ -147,6 +149,12 @@ void free_batch(Batch *b);
 // slot (nonzero = solve), or NULL for all.
 tomo_status batch_solve(Batch *b, const void *const *slopes, void *const *x, const int *const *active_g,
                         int iters, int warm, cudaStream_t s);
+
+// W^-1 over a launch set (cluster or streamed kernels); src 0: io.in0
+// coefficients, 1: the PCG direction update fused in.  synthesis_launches: the
+// kernels one call launches.
+cudaError_t synthesis_of(const LaunchSet &L, int src, int flags, const IoArgs &io, cudaStream_t s);
+int synthesis_launches(const LaunchSet &L);
 
 // Reads and clears plan p's breakdown word: true when a solve of p has broken
 // down since the word was last cleared (only work that has completed on the
