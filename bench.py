@@ -82,6 +82,9 @@ def parse():
     ap.add_argument("--no-large", action="store_true", help="skip the 100 m configuration")
     ap.add_argument("--no-loop", action="store_true", help="skip the E-ELT closed loop with fitting")
     ap.add_argument("--loop-frames", type=int, default=120)
+    ap.add_argument("--profile-leg", default=None, choices=["eelt", "batch16", "uneven64", "large"],
+                    help="run only this workload's solves (no JSON line), for kernel profiles")
+    ap.add_argument("--solves", type=int, default=3, help="solves of --profile-leg")
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="length of the served 16-telescope stream (0: skip it)")
     return ap.parse_args()
@@ -360,11 +363,11 @@ def bench_batched(pkg, torch, geom, slopes, flush, iters, args, peak, dev):
     from synth import configs, gaussian_noise
     out = {}
     steps = max(5, min(args.steps, 100))
-    from paper_1302_3734_gb300.autotune import tune_cluster_size, _plans
+    from paper_1302_3734_gb300.autotune import tune, _plans
     # B E-ELT instances, each on its own frame of the stream, at the tuned cluster size
     B = args.batch
-    c_e, tab_e = tune_cluster_size([geom] * B, iters)
-    plans = _plans([geom] * B, c_e)
+    (c_e, tf_e), tab_e = tune([geom] * B, iters)
+    plans = _plans([geom] * B, c_e, tf_e)
     F = slopes.shape[0]
     sl = [slopes[(3 * i) % F].clone() for i in range(B)]
     xs = [torch.zeros(plans[0].n, dtype=torch.float32, device=dev) for _ in range(B)]
@@ -373,7 +376,9 @@ def bench_batched(pkg, torch, geom, slopes, flush, iters, args, peak, dev):
     bytes_it = sum(p.info.bytes_per_iteration for p in plans)
     kt = _timed_kinds(pkg, torch, plans, lambda: pkg.solve_batch(plans, sl, xs, iters, warm=True), flush, 3)
     out["eelt"] = {"instances": B, "solves_per_s": B * 1000.0 / ms, "ms_per_batch": ms,
-                   "cluster_size": c_e, "autotune_solves_per_s": tab_e,
+                   "cluster_size": c_e, "transforms": "streamed" if tf_e == 2 else "cluster",
+                   "autotune_solves_per_s": tab_e,
+                   "autotune_note": "keys: cluster size / transforms (1 cluster kernels, 2 streamed passes)",
                    "p99_ms": float(np.percentile(t, 99)),
                    "achieved_GBps_per_iteration_bytes": bytes_it * iters / (ms / 1000.0) / 1e9,
                    "frac_of_hbm_peak": bytes_it * iters / (ms / 1000.0) / 1e9 / peak,
@@ -384,8 +389,8 @@ def bench_batched(pkg, torch, geom, slopes, flush, iters, args, peak, dev):
         p.close()
     # the 64-instance uneven workload
     geoms = configs.config2()
-    c_u, tab_u = tune_cluster_size(geoms, 10)
-    plans = _plans(geoms, c_u)
+    (c_u, tf_u), tab_u = tune(geoms, 10)
+    plans = _plans(geoms, c_u, tf_u)
     sl = []
     for i, (g, p) in enumerate(zip(geoms, plans)):
         sig = np.concatenate([np.full(2 if w["tt_only"] else 2 * int(w["valid"].sum()), w["sigma"])
@@ -401,7 +406,8 @@ def bench_batched(pkg, torch, geom, slopes, flush, iters, args, peak, dev):
                        "roofline": kernel_roofline(kt, launch_bytes(plans, geoms), peak,
                                                    "events around every launch of 3 batched solves "
                                                    "(direct launches), L2 flushed before each"),
-                       "cluster_size": c_u, "autotune_solves_per_s": tab_u,
+                       "cluster_size": c_u, "transforms": "streamed" if tf_u == 2 else "cluster",
+                       "autotune_solves_per_s": tab_u,
                        "ms_per_batch": ms, "p99_ms": float(np.percentile(t, 99)),
                        "coefficients": int(sum(p.n for p in plans)),
                        "achieved_GBps_per_iteration_bytes": bytes_it * 10 / (ms / 1000.0) / 1e9,
@@ -664,8 +670,8 @@ def bench_served(pkg, torch, args, dev, frames_per_tel=16, rate_hz=500.0):
             fr.append(np.ascontiguousarray(sl.cpu().numpy() + noise.astype(np.float32)))
         frames.append(fr)
         p.close()
-    from paper_1302_3734_gb300.autotune import tune_cluster_size
-    c_s, tab_s = tune_cluster_size(geoms, 10)
+    from paper_1302_3734_gb300.autotune import tune
+    (c_s, tf_s), tab_s = tune(geoms, 10)
     srv = pkg.Server(budget_bytes=16 << 30, iters=10, max_in_flight=3, queue_depth=64, result_slots=2)
     srv.set_policy(latest_only=True)
     ids = []
@@ -673,7 +679,7 @@ def bench_served(pkg, torch, args, dev, frames_per_tel=16, rate_hz=500.0):
         cc = c_s
         while True:
             try:
-                ids.append(srv.admit(g, cluster_size=cc))
+                ids.append(srv.admit(g, cluster_size=cc, transforms=tf_s))
                 break
             except pkg.TomoError as e:
                 if e.status not in (1, 8) or cc >= 16:
@@ -739,7 +745,8 @@ def bench_served(pkg, torch, args, dev, frames_per_tel=16, rate_hz=500.0):
         "telescopes": len(ids), "rate_hz_per_telescope": rate_hz, "seconds": args.serve_seconds,
         "frames_offered": len(sched), "frames_done": len(ok), "frames_refused_queue_full": full,
         "frames_superseded": superseded, "policy": "latest frame (older waiting frames superseded)",
-        "cluster_size": c_s, "autotune_solves_per_s": tab_s,
+        "cluster_size": c_s, "transforms": "streamed" if tf_s == 2 else "cluster",
+        "autotune_solves_per_s": tab_s,
         "solves_per_s": len(ok) / span,
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                        "max": float(lat.max())},
@@ -754,10 +761,55 @@ def bench_served(pkg, torch, args, dev, frames_per_tel=16, rate_hz=500.0):
     }
 
 
+def profile_leg(args):
+    """One workload's solves and nothing else, so a profiler's launch list holds only them:
+    eelt (the E-ELT frame, 10 warm PCG iterations, graph), batch16 (16 E-ELT instances at
+    cluster size 2), uneven64 (the 64 uneven instances at cluster size 4), large (the 100 m
+    system, 20 cold PCG iterations).  Plans are built before the first solve."""
+    import torch
+    import paper_1302_3734_gb300 as pkg
+    from paper_1302_3734_gb300 import build
+    from synth import configs, gaussian_noise
+    build.build()
+    dev = torch.device("cuda", 0)
+    leg = args.profile_leg
+    if leg == "large":
+        geoms, C, iters, warm = [configs.config4()], 0, 20, False
+    elif leg == "uneven64":
+        geoms, C, iters, warm = configs.config2(), 4, 10, True
+    else:
+        geoms, C, iters, warm = [configs.config1()] * (16 if leg == "batch16" else 1), (2 if leg == "batch16" else 0), 10, True
+    plans = []
+    for g in geoms:
+        cc = C
+        while True:
+            try:
+                plans.append(pkg.Plan(g, cluster_size=cc))
+                break
+            except pkg.TomoError as e:
+                if e.status not in (1, 8) or cc == 0 or cc >= 16:
+                    raise
+                cc *= 2
+    sl = [torch.tensor(gaussian_noise(p.n_slopes, 0.3, 100 + i), dtype=torch.float32, device=dev)
+          for i, p in enumerate(plans)]
+    xs = [torch.zeros(p.n, dtype=torch.float32, device=dev) for p in plans]
+    for _ in range(args.solves):
+        if len(plans) == 1:
+            plans[0].solve(sl[0], xs[0], iters, warm=warm)
+        else:
+            pkg.solve_batch(plans, sl, xs, iters, warm=warm)
+    torch.cuda.synchronize()
+    print(f"{leg}: {args.solves} solves of {len(plans)} plan(s), {iters} PCG iterations", flush=True)
+    for p in plans:
+        p.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_leg:
+        return profile_leg(args)
     import torch
     import paper_1302_3734_gb300 as pkg
     from paper_1302_3734_gb300 import build

@@ -1,14 +1,20 @@
 """Launch-shape autotuner for batched solves.
 
-The transform kernels run one thread-block cluster of C CTAs per layer
-(``cluster_size``).  A large C finishes one solve soonest: the layer's rows are
-spread over more SMs.  Many instances solved together fill the GPU anyway, and
-then a small C wins: fewer cluster barriers per level and more clusters
-resident at once.  Which C is best depends on the geometries, the batch and
-the GPU, so it is measured: every candidate builds the batch's plans, times
-``solve_batch`` with CUDA events, and the fastest wins.  Results are cached per
-(batch signature, iterations, device) in memory and, when a path is given, in
-a JSON file.
+Two knobs set how a plan's kernels are shaped:
+
+* the cluster size C (``cluster_size``): the cluster transform kernels run one
+  thread-block cluster of C CTAs per layer, and the gather works on bands of
+  N/C rows.  A large C finishes one solve soonest (a layer's rows spread over
+  more SMs); many instances solved together fill the GPU anyway, and then a
+  small C wins: fewer cluster barriers per level, more clusters resident;
+* the transforms (``transforms``): cluster kernels with the gather staged in
+  the analysis kernel when its tables fit (1), or streamed level passes over
+  row tiles with the gather in its own kernel (2).
+
+Which shape is best depends on the geometries, the batch and the GPU, so it is
+measured: every candidate builds the batch's plans, times ``solve_batch`` with
+CUDA events, and the fastest wins.  Results are cached per (batch signature,
+iterations, device) in memory and, when a path is given, in a JSON file.
 """
 import hashlib
 import json
@@ -19,6 +25,7 @@ import numpy as np
 from .binding import Plan, TomoError, solve_batch
 
 CANDIDATES = (16, 8, 4, 2, 1)
+TRANSFORMS = (1, 2)     # cluster kernels, streamed passes
 _cache = {}
 
 
@@ -36,7 +43,7 @@ def signature(geoms, iters):
     return h.hexdigest()[:24]
 
 
-def _plans(geoms, c):
+def _plans(geoms, c, transforms=0):
     """Plans at cluster size c; a plan that cannot take c gets the next larger size."""
     plans = []
     try:
@@ -44,7 +51,7 @@ def _plans(geoms, c):
             cc, p = c, None
             while p is None:
                 try:
-                    p = Plan(g, cluster_size=cc)
+                    p = Plan(g, cluster_size=cc, transforms=transforms)
                 except TomoError as e:
                     if e.status not in (1, 8) or cc >= 16:
                         raise
@@ -118,3 +125,30 @@ def tune_cluster_size(geoms, iters=10, candidates=CANDIDATES, steps=10, warmup=3
         with open(path, "w") as f:
             json.dump(stored, f, indent=1)
     return best, table
+
+
+def tune(geoms, iters=10, candidates=CANDIDATES, transforms=TRANSFORMS, steps=10, warmup=3):
+    """Best (cluster size, transforms) for solving `geoms` together.  Returns ((C, tf), table)
+    where table maps "C/tf" to the measured solves/s (None: no plan could be built)."""
+    import torch
+    key = f"shape:{signature(geoms, iters)}:{torch.cuda.get_device_name()}"
+    if key in _cache:
+        return _cache[key]
+    table = {}
+    for c in candidates:
+        for tf in transforms:
+            plans = _plans(geoms, c, tf)
+            if plans is None:
+                table[f"{c}/{tf}"] = None
+                continue
+            ms = _time(torch, plans, iters, steps, warmup)
+            table[f"{c}/{tf}"] = len(geoms) * 1000.0 / ms
+            for p in plans:
+                p.close()
+    valid = {k: v for k, v in table.items() if v is not None}
+    if not valid:
+        raise RuntimeError("no candidate launch shape can build these plans")
+    best = max(valid, key=valid.get)
+    c, tf = (int(x) for x in best.split("/"))
+    _cache[key] = ((c, tf), table)
+    return (c, tf), table

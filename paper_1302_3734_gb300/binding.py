@@ -458,7 +458,7 @@ class Server:
         self._n_out = {}
         self._buf = (FrameResult * 4096)()
 
-    def admit(self, geom, cluster_size=0):
+    def admit(self, geom, cluster_size=0, transforms=0):
         """Admit a telescope; returns its id (TomoError with status TOMO_ERR_NOMEM when the
         budget does not allow it)."""
         lib = load_library()
@@ -466,6 +466,7 @@ class Server:
         tid = ctypes.c_int(-1)
         opt = PlanOptions()
         opt.cluster_size = int(cluster_size)
+        opt.transforms = int(transforms)
         _check(lib.tomo_server_admit_ex(self._h, ctypes.byref(g), ctypes.byref(opt), ctypes.byref(tid)))
         del keep
         plan = ctypes.c_void_p()

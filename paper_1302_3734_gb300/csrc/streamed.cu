@@ -321,6 +321,15 @@ struct SynthCoef {
 // Coefficients (and low-low values) staged per thread at once by the synthesis kernels.
 constexpr int kCoefU = 4;
 
+// 16 bytes of T: the unit of the vector loads of the streamed synthesis pass.
+template <typename T>
+struct Vec16 {
+  static constexpr int kN = 16 / static_cast<int>(sizeof(T));
+  T v[kN];
+  __device__ __forceinline__ void load(const T *p) { *reinterpret_cast<uint4 *>(v) = *reinterpret_cast<const uint4 *>(p); }
+  __device__ __forceinline__ void store(T *p) const { *reinterpret_cast<uint4 *>(p) = *reinterpret_cast<const uint4 *>(v); }
+};
+
 template <typename T, int SRC>
 __device__ __forceinline__ SynthCoef<T, SRC> synth_coef(const InstDev &I, const IoArgs &io, int inst, int flags,
                                                         T beta) {
@@ -391,34 +400,38 @@ __global__ void __launch_bounds__(kPassThreads) k_idwt_coarse(const InstDev *__r
   for (int k = J; k >= ks; --k) {
     const int lgM = L.log2N - (k - 1), M = 1 << lgM, H = M >> 1;
     // row synthesis (x) of the low-y rows [LL | HL] into XL and the high-y rows [LH | HH] into XH
-    for (int idx = tid; idx < 2 * H * M; idx += nt) {
-      const int r = idx >> lgM, j = idx & (M - 1);
-      const int q = j & 1;
+    const int lgH = lgM - 1;
+    for (int idx = tid; idx < 2 * H * H; idx += nt) {
+      const int r = idx >> lgH, m = idx & (H - 1);
       const bool high = r >= H;
       const int ii = high ? r - H : r;
-      T acc = T(0);
+      T even = T(0), odd = T(0);
 #pragma unroll
       for (int s = 0; s < LF / 2; ++s) {
-        const int jj = ((j >> 1) - s) & (H - 1);
+        const int jj = (m - s) & (H - 1);
         const T lo = high ? Cf[(H + ii) * M0 + jj] : A[ii * H + jj];
         const T hi = Cf[(high ? H + ii : ii) * M0 + H + jj];
-        acc += f.hs(q, s) * lo + f.gs(q, s) * hi;
+        even += f.h[2 * s] * lo + f.g[2 * s] * hi;
+        odd += f.h[2 * s + 1] * lo + f.g[2 * s + 1] * hi;
       }
-      (high ? XH : XL)[ii * M + j] = acc;
+      T *xr = (high ? XH : XL) + ii * M + 2 * m;
+      xr[0] = even;
+      xr[1] = odd;
     }
     __syncthreads();
     // column synthesis (y): the block of side M, the next level's low-low block
-    for (int idx = tid; idx < M * M; idx += nt) {
-      const int y = idx >> lgM, x = idx & (M - 1);
-      const int p = y & 1;
-      const int b = (y - p) >> 1;
-      T acc = T(0);
+    for (int idx = tid; idx < H * M; idx += nt) {
+      const int b = idx >> lgM, x = idx & (M - 1);
+      T even = T(0), odd = T(0);
 #pragma unroll
       for (int s = 0; s < LF / 2; ++s) {
         const int ii = (b - s) & (H - 1);
-        acc += f.hs(p, s) * XL[ii * M + x] + f.gs(p, s) * XH[ii * M + x];
+        const T xl = XL[ii * M + x], xh = XH[ii * M + x];
+        even += f.h[2 * s] * xl + f.g[2 * s] * xh;
+        odd += f.h[2 * s + 1] * xl + f.g[2 * s + 1] * xh;
       }
-      A[idx] = acc;
+      A[(2 * b) * M + x] = even;
+      A[(2 * b + 1) * M + x] = odd;
     }
     __syncthreads();
   }
@@ -436,7 +449,7 @@ __global__ void __launch_bounds__(kPassThreads) k_idwt_coarse(const InstDev *__r
 // HL = LF/2 - 1 half-rows before the tile are read too.  Output to the scratch
 // (the low-low block of level k - 1) or, k = 1, the output grid.
 template <typename T, int SRC, int LF>
-__global__ void __launch_bounds__(kPassThreads) k_idwt_pass(const InstDev *__restrict__ insts,
+__global__ void __launch_bounds__(kPassThreads, 2) k_idwt_pass(const InstDev *__restrict__ insts,
                                                             const PassItem *__restrict__ items, IoArgs io,
                                                             int k, int flags) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -460,7 +473,59 @@ __global__ void __launch_bounds__(kPassThreads) k_idwt_pass(const InstDev *__res
   pdl_wait();
   const T beta = SRC == 1 ? streamed_beta<T>(I, flags >> kIterShift, false) : T(0);
   const SynthCoef<T, SRC> coef = synth_coef<T, SRC>(I, io, it.inst, flags, beta);
-  // the tile's coefficient rows, kCoefU positions per thread loaded before any is used
+  // the tile's coefficient rows: 16-byte vectors when every source is aligned (the plan's
+  // buffers are; a caller's coefficient vector may not be), else kCoefU positions per
+  // thread loaded before any is used
+  constexpr int VN = Vec16<T>::kN;
+  const bool vec = (((reinterpret_cast<uintptr_t>(SRC == 0 ? coef.src : coef.Pin) |
+                      reinterpret_cast<uintptr_t>(coef.Rv) | reinterpret_cast<uintptr_t>(coef.Jv) |
+                      reinterpret_cast<uintptr_t>(coef.Pout) | reinterpret_cast<uintptr_t>(ll)) & 15) == 0) &&
+                   ((L.off & (VN - 1)) == 0) && H >= VN;
+  if (vec) {
+    const int lgMv = lgM - (__ffs(VN) - 1), mv = M / VN;
+    for (int q = tid; q < NI * mv; q += nt) {
+      const int j = q >> lgMv, x = (q & (mv - 1)) * VN;
+      const int ii = (it.row0 - HL + j) & (H - 1);
+      const bool own = j >= HL;
+      const size_t lo = static_cast<size_t>(L.off) + static_cast<size_t>(ii) * N + x;
+      const size_t hi = static_cast<size_t>(L.off) + static_cast<size_t>(H + ii) * N + x;
+      Vec16<T> a, b, ar, br, aj, bj;
+      // requests first: the low-y row's low-low values or coefficients, the high-y row's coefficients
+      if (x < H) {
+        a.load(ll + ii * H + x);
+      } else if (SRC == 0) {
+        a.load(coef.src + lo);
+      } else {
+        a.load(coef.Pin + lo);
+        if (!coef.first) {
+          ar.load(coef.Rv + lo);
+          if (coef.pre) aj.load(coef.Jv + lo);
+        }
+      }
+      if (SRC == 0) {
+        b.load(coef.src + hi);
+      } else {
+        b.load(coef.Pin + hi);
+        if (!coef.first) {
+          br.load(coef.Rv + hi);
+          if (coef.pre) bj.load(coef.Jv + hi);
+        }
+      }
+      if (SRC == 1 && !coef.first) {
+#pragma unroll
+        for (int e = 0; e < VN; ++e) {
+          if (x >= H) a.v[e] = (coef.pre ? aj.v[e] * ar.v[e] : ar.v[e]) + coef.beta * a.v[e];
+          b.v[e] = (coef.pre ? bj.v[e] * br.v[e] : br.v[e]) + coef.beta * b.v[e];
+        }
+        if (own) {
+          if (x >= H) a.store(coef.Pout + lo);
+          b.store(coef.Pout + hi);
+        }
+      }
+      a.store(VL + j * M + x);
+      b.store(VH + j * M + x);
+    }
+  } else
   for (int idx0 = tid; idx0 < NI * M; idx0 += kCoefU * nt) {
     typename SynthCoef<T, SRC>::Raw ra[kCoefU], rb[kCoefU];
 #pragma unroll
@@ -487,31 +552,40 @@ __global__ void __launch_bounds__(kPassThreads) k_idwt_pass(const InstDev *__res
     }
   }
   __syncthreads();
-  for (int idx = tid; idx < 2 * NI * M; idx += nt) {
-    const int r = idx >> lgM, j = idx & (M - 1);
-    const int q = j & 1;
+  // row synthesis (x): outputs 2m and 2m + 1 of a row from the same taps
+  const int lgH = lgM - 1;
+  for (int idx = tid; idx < 2 * NI * H; idx += nt) {
+    const int r = idx >> lgH, m = idx & (H - 1);
     const T *row = VL + r * M;   // VH follows VL: rows NI.. are the high-y rows
-    T acc = T(0);
+    T even = T(0), odd = T(0);
 #pragma unroll
     for (int s = 0; s < LF / 2; ++s) {
-      const int jj = ((j >> 1) - s) & (H - 1);
-      acc += f.hs(q, s) * row[jj] + f.gs(q, s) * row[H + jj];
+      const int jj = (m - s) & (H - 1);
+      const T lo = row[jj], hi = row[H + jj];
+      even += f.h[2 * s] * lo + f.g[2 * s] * hi;
+      odd += f.h[2 * s + 1] * lo + f.g[2 * s + 1] * hi;
     }
-    XL[idx] = acc;   // XH follows XL
+    XL[r * M + 2 * m] = even;   // XH follows XL
+    XL[r * M + 2 * m + 1] = odd;
   }
   __syncthreads();
   T *out = k > 1 ? static_cast<T *>(I.lls) + L.ll_off[k - 1]
                  : (io.out0[it.inst] ? static_cast<T *>(io.out0[it.inst]) : static_cast<T *>(I.phi)) + L.off;
   const int stride = k > 1 ? M : N;
-  for (int idx = tid; idx < 2 * kPassRows * M; idx += nt) {
-    const int yl = idx >> lgM, x = idx & (M - 1);
-    const int p = yl & 1;
-    const int base = ((yl - p) >> 1) + HL;
-    T acc = T(0);
+  // column synthesis (y): output rows 2b and 2b + 1 from the same half-rows
+  for (int idx = tid; idx < kPassRows * M; idx += nt) {
+    const int b = idx >> lgM, x = idx & (M - 1);
+    const int base = b + HL;
+    T even = T(0), odd = T(0);
 #pragma unroll
-    for (int s = 0; s < LF / 2; ++s)
-      acc += f.hs(p, s) * XL[(base - s) * M + x] + f.gs(p, s) * XH[(base - s) * M + x];
-    out[static_cast<size_t>(2 * it.row0 + yl) * stride + x] = acc;
+    for (int s = 0; s < LF / 2; ++s) {
+      const T xl = XL[(base - s) * M + x], xh = XH[(base - s) * M + x];
+      even += f.h[2 * s] * xl + f.g[2 * s] * xh;
+      odd += f.h[2 * s + 1] * xl + f.g[2 * s + 1] * xh;
+    }
+    T *o = out + (2 * it.row0 + 2 * b) * stride + x;
+    o[0] = even;
+    o[stride] = odd;
   }
 }
 
