@@ -672,7 +672,7 @@ def bench_served(pkg, torch, args, dev, frames_per_tel=16, rate_hz=500.0):
         p.close()
     from paper_1302_3734_gb300.autotune import tune
     (c_s, tf_s), tab_s = tune(geoms, 10)
-    srv = pkg.Server(budget_bytes=16 << 30, iters=10, max_in_flight=3, queue_depth=64, result_slots=2)
+    srv = pkg.Server(budget_bytes=16 << 30, iters=10, max_in_flight=4, queue_depth=64, result_slots=2)
     srv.set_policy(latest_only=True)
     ids = []
     for g in geoms:
