@@ -357,7 +357,6 @@ __global__ void __launch_bounds__(kPassThreads) k_idwt_coarse(const InstDev *__r
                                                               int flags) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ InstDev sI;
-  constexpr int HL = LF / 2 - 1;
   pdl_trigger();
   const PassItem it = items[blockIdx.x];
   if (io.active && !io.active[it.inst]) return;
@@ -435,7 +434,6 @@ __global__ void __launch_bounds__(kPassThreads) k_idwt_coarse(const InstDev *__r
     }
     __syncthreads();
   }
-  (void)HL;
   T *out = ks > 1 ? static_cast<T *>(I.lls) + L.ll_off[ks - 1]
                   : (io.out0[it.inst] ? static_cast<T *>(io.out0[it.inst]) : static_cast<T *>(I.phi)) + L.off;
   const int stride = ks > 1 ? M0 : N;
