@@ -26,7 +26,7 @@ def _cuda_home():
 
 
 def _sources():
-    return [os.path.join(CSRC, f) for f in ("kernels.cu", "streamed.cu", "api.cu", "noalloc.cu", "server.cu", "fit.cu", "probe.cu", "host_plan.cpp")]
+    return [os.path.join(CSRC, f) for f in ("kernels.cu", "gather.cu", "streamed.cu", "api.cu", "noalloc.cu", "server.cu", "fit.cu", "probe.cu", "host_plan.cpp")]
 
 
 def _deps():

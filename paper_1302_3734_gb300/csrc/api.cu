@@ -104,8 +104,7 @@ tomo_status timed(tomo_plan *p, int kind, cudaStream_t s, F fn, const char *what
 // (src 0), with epilogue epi, for a launch set without the fused gather.
 cudaError_t anal_ls(const LaunchSet &L, int src, int epi, int flags, const IoArgs &io, cudaStream_t s) {
   return L.stream ? launch_analysis_streamed(L.precision, src, epi, L.lf, flags, L.d_inst, L.ss, io, s)
-                  : launch_analysis(L.precision, src, epi, L.lf, flags, L.d_inst, L.cl, L.n_cl, L.C, L.smem_a, io, s,
-                                    0, 0);
+                  : launch_analysis(L.precision, src, epi, L.lf, flags, L.d_inst, L.cl, L.n_cl, L.C, L.smem_a, io, s);
 }
 int anal_launches(const LaunchSet &L) { return L.stream ? streamed_launches(L.ss) : 1; }
 
@@ -115,7 +114,7 @@ int anal_launches(const LaunchSet &L) { return L.stream ? streamed_launches(L.ss
 tomo_status adjoint_ls(tomo_plan *p, const LaunchSet &L, int epi, const IoArgs &io, cudaStream_t s) {
   if (!L.split)
     return timed(p, kKindAnalysis, s, [&] {
-      return launch_analysis(L.precision, 1, epi, L.lf, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem_a, io, s, 0, 0);
+      return launch_analysis(L.precision, 1, epi, L.lf, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem_a, io, s);
     }, "analysis");
   const int tt_mode = epi == 1 ? 0 : 2;   // operator: the model term; otherwise the data alone
   TOMO_TRY(timed(p, kKindGather, s, [&] {
@@ -165,7 +164,7 @@ tomo_status enqueue_solve(tomo_plan *tp, const LaunchSet &L, const void *const *
     } else {
       TOMO_TRY(timed(tp, kKindAnalysis, s, [&] {
         return launch_analysis(L.precision, 1, 2, L.lf, warm ? kFlagWarm : 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem_a,
-                               io, s, 0, 0);
+                               io, s);
       }, "analysis (residual)"));
       ++nk;
     }
@@ -187,7 +186,7 @@ tomo_status enqueue_solve(tomo_plan *tp, const LaunchSet &L, const void *const *
                      anal_launches(L)));
     } else {
       TOMO_TRY(timed(tp, kKindAnalysis, s, [&] {
-        return launch_analysis(L.precision, 1, 1, L.lf, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem_a, none, s, 0, 0);
+        return launch_analysis(L.precision, 1, 1, L.lf, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem_a, none, s);
       }, "analysis"));
     }
     IoArgs io{};

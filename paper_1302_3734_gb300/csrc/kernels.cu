@@ -33,6 +33,7 @@
 #include "device_util.cuh"
 #include "launch.h"
 #include "transform.cuh"
+#include "adjoint.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -377,213 +378,6 @@ struct CoefMap {
   }
 };
 
-// Coefficients of the pupil-edge terms, per edge slot, from the forward
-// kernel's tile partials (one warp per slot, lanes in a fixed order):
-// * tip/tilt removal: -sigma^-2 (mean z_x, mean z_y);
-// * tip/tilt-only sensor: sigma^-2 z / S with z its two mean slopes: the
-//   model's (tt_mode 0), data minus model (1), or the data alone (2), the data
-//   read from `slopes`.
-// FP32 plans sum the double-float partials and form the coefficients in
-// double-float arithmetic; FP64 plans use doubles.
-__device__ __forceinline__ void edge_pair(const EdgeSlot &es, int tt_mode, double a, double b,
-                                          const double *slopes, double *out) {
-  if (es.kind == kRemoveTT) {
-    out[0] = -(a * es.tt_scale);
-    out[1] = -(b * es.tt_scale);
-    return;
-  }
-  double zx = a * es.inv_S, zy = b * es.inv_S;
-  if (tt_mode == 1) {
-    zx = slopes[es.slope_off] - zx;
-    zy = slopes[es.slope_off + 1] - zy;
-  } else if (tt_mode == 2) {
-    zx = slopes[es.slope_off];
-    zy = slopes[es.slope_off + 1];
-  }
-  out[0] = zx * es.tt_scale;
-  out[1] = zy * es.tt_scale;
-}
-
-// (hi + lo) * s as a double-float (s rounded to float first)
-__device__ __forceinline__ float2 df_scale(float hi, float lo, float s) {
-  const float p = __fmul_rn(hi, s);
-  return make_float2(p, __fadd_rn(__fmaf_rn(hi, s, -p), __fmul_rn(lo, s)));
-}
-
-__device__ __forceinline__ float edge_one(const EdgeSlot &es, int tt_mode, float hi, float lo, float data) {
-  const float scale = static_cast<float>(es.tt_scale);
-  if (es.kind == kRemoveTT) {
-    const float2 m = df_scale(hi, lo, scale);
-    return -__fadd_rn(m.x, m.y);
-  }
-  if (tt_mode == 2) return __fmul_rn(data, scale);
-  float2 z = df_scale(hi, lo, static_cast<float>(es.inv_S));
-  if (tt_mode == 1) {
-    // data - z by two-sum, then the low part
-    const float t = __fsub_rn(data, z.x);
-    const float bp = __fsub_rn(t, data);
-    const float e = __fadd_rn(__fsub_rn(data, __fsub_rn(t, bp)), __fsub_rn(-z.x, bp));
-    z = make_float2(t, __fsub_rn(e, z.y));
-  }
-  const float2 c = df_scale(z.x, z.y, scale);
-  return __fadd_rn(c.x, c.y);
-}
-
-// Tip/tilt removal under spot elongation: with m and q the means of z and of
-// C_tilde^-1 z over the subapertures, (I - T) C_tilde^-1 (I - T) z =
-// C_tilde^-1 z - C_tilde^-1 m - (q - M m), M = mean C_tilde_j^-1.  The forward
-// kernel applied the first term; -sigma^-2 m - q + M m is constant over the
-// subapertures (its Gamma^T lives on the pupil edge: this coefficient pair);
-// the rest, sigma^-2 c_j g_j (g_j . m), reaches the corner field as
-// m_x Gx + m_y Gy (returned in mo).
-__device__ __forceinline__ void edge_elong(const EdgeSlot &es, double a, double b, double qa, double qb,
-                                           double *out, double *mo) {
-  const double mx = a * es.inv_S, my = b * es.inv_S, qx = qa * es.inv_S, qy = qb * es.inv_S;
-  out[0] = -es.inv_sigma2 * mx - qx + (es.mb_xx * mx + es.mb_xy * my);
-  out[1] = -es.inv_sigma2 * my - qy + (es.mb_xy * mx + es.mb_yy * my);
-  mo[0] = mx;
-  mo[1] = my;
-}
-
-// s_coef: 2 * kMaxEdgeSlots pupil-edge coefficient pairs, then per slot the
-// mean slopes (m_x, m_y) that weight the elongation fields (0 without).
-template <typename T>
-__device__ void edge_coefficients(const InstDev &I, T *s_coef, int tt_mode, const T *slopes) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int k = warp; k < I.n_edge_wfs; k += nw) {
-    const EdgeSlot es = I.edge_slots[k];
-    const bool sum = !(es.kind == kTTOnly && tt_mode == 2);
-    const int stride = es.elong ? 4 : 2;   // doubles per tile
-    if constexpr (sizeof(T) == 4) {
-      Acc<float> a, b, qa, qb;
-      if (sum)
-        for (int t = lane; t < es.n_tiles; t += 32) {
-          const float4 *pt = reinterpret_cast<const float4 *>(I.part + es.part_off + stride * t);
-          const float4 v = pt[0];
-          a.merge(v.x, v.y);
-          b.merge(v.z, v.w);
-          if (es.elong) {
-            const float4 w = pt[1];
-            qa.merge(w.x, w.y);
-            qb.merge(w.z, w.w);
-          }
-        }
-      warp_merge_down(a);
-      warp_merge_down(b);
-      if (es.elong) {
-        warp_merge_down(qa);
-        warp_merge_down(qb);
-      }
-      if (lane == 0) {
-        if (es.elong) {
-          double out[2], mo[2];
-          edge_elong(es, a.value(), b.value(), qa.value(), qb.value(), out, mo);
-          s_coef[2 * k] = T(out[0]);
-          s_coef[2 * k + 1] = T(out[1]);
-          s_coef[2 * kMaxEdgeSlots + 2 * k] = T(mo[0]);
-          s_coef[2 * kMaxEdgeSlots + 2 * k + 1] = T(mo[1]);
-        } else {
-          const bool tt = es.kind == kTTOnly && tt_mode != 0;
-          s_coef[2 * k] = edge_one(es, tt_mode, a.hi, a.lo, tt ? float(slopes[es.slope_off]) : 0.f);
-          s_coef[2 * k + 1] = edge_one(es, tt_mode, b.hi, b.lo, tt ? float(slopes[es.slope_off + 1]) : 0.f);
-          s_coef[2 * kMaxEdgeSlots + 2 * k] = T(0);
-          s_coef[2 * kMaxEdgeSlots + 2 * k + 1] = T(0);
-        }
-      }
-    } else {
-      double a = 0.0, b = 0.0, qa = 0.0, qb = 0.0;
-      if (sum)
-        for (int t = lane; t < es.n_tiles; t += 32) {
-          a += I.part[es.part_off + stride * t];
-          b += I.part[es.part_off + stride * t + 1];
-          if (es.elong) {
-            qa += I.part[es.part_off + stride * t + 2];
-            qb += I.part[es.part_off + stride * t + 3];
-          }
-        }
-      a = warp_sum(a);
-      b = warp_sum(b);
-      if (es.elong) {
-        qa = warp_sum(qa);
-        qb = warp_sum(qb);
-      }
-      if (lane == 0) {
-        double out[2], mo[2] = {0.0, 0.0};
-        if (es.elong) edge_elong(es, a, b, qa, qb, out, mo);
-        else edge_pair(es, tt_mode, a, b, reinterpret_cast<const double *>(slopes), out);
-        s_coef[2 * k] = T(out[0]);
-        s_coef[2 * k + 1] = T(out[1]);
-        s_coef[2 * kMaxEdgeSlots + 2 * k] = T(mo[0]);
-        s_coef[2 * kMaxEdgeSlots + 2 * k + 1] = T(mo[1]);
-      }
-    }
-  }
-  __syncthreads();
-}
-
-// One adjoint tap record: the window's first tap (an int in slot 0) and its
-// KT weights, read with 16-byte vector loads.
-template <typename T, int KT>
-struct TapRec {
-  static constexpr int RS = KT <= 3 ? 4 : 8;   // T words per record
-  int off;
-  T w[KT];
-  __device__ __forceinline__ void load(const T *rec) {
-    if constexpr (sizeof(T) == 4) {
-      const float4 a = reinterpret_cast<const float4 *>(rec)[0];
-      off = __float_as_int(a.x);
-      w[0] = a.y;
-      w[1] = a.z;
-      if constexpr (KT >= 3) w[2] = a.w;
-      if constexpr (KT >= 4) w[3] = reinterpret_cast<const float4 *>(rec)[1].x;
-    } else {
-      const double2 a = reinterpret_cast<const double2 *>(rec)[0];
-      const double2 b = reinterpret_cast<const double2 *>(rec)[1];
-      off = __double2loint(a.x);
-      w[0] = a.y;
-      w[1] = b.x;
-      if constexpr (KT >= 3) w[2] = b.y;
-      if constexpr (KT >= 4) w[3] = reinterpret_cast<const double2 *>(rec)[2].x;
-    }
-  }
-};
-
-// (P^T v)(node) for one sensor: the KT x KT window of its corner field at p
-// (row stride nc) weighted by the column weights x.w and the row weights y.w.
-template <typename T, int KT, bool SHARED>
-__device__ __forceinline__ T window_sum(const T *__restrict__ p, int nc, const TapRec<T, KT> &x,
-                                        const TapRec<T, KT> &y) {
-  T v[KT][KT];
-#pragma unroll
-  for (int ty = 0; ty < KT; ++ty)
-#pragma unroll
-    for (int tx = 0; tx < KT; ++tx) v[ty][tx] = SHARED ? p[ty * nc + tx] : __ldg(p + ty * nc + tx);
-  T acc = T(0);
-#pragma unroll
-  for (int ty = 0; ty < KT; ++ty) {
-    T sx = x.w[0] * v[ty][0];
-#pragma unroll
-    for (int tx = 1; tx < KT; ++tx) sx += x.w[tx] * v[ty][tx];
-    acc += y.w[ty] * sx;
-  }
-  return acc;
-}
-
-// Pupil-edge terms of the CTA's nodes: A[node] += sum over its entries of
-// (e_x t_x + e_y t_y) w (one short list per node, edge slots in s_coef).
-template <typename T>
-__device__ __forceinline__ void gather_edges(int nn, const int *tn, const int *tb, const int *tk,
-                                             const T *tw, T *A, const T *s_coef) {
-  for (int j = threadIdx.x; j < nn; j += blockDim.x) {
-    T acc = T(0);
-    for (int e = tb[j]; e < tb[j + 1]; ++e) {
-      const int k = tk[e];
-      acc += s_coef[2 * k] * tw[2 * e] + s_coef[2 * k + 1] * tw[2 * e + 1];
-    }
-    A[tn[j]] += acc;
-  }
-}
-
 // Shared-memory copy of the gather tables of one analysis CTA (layer l, rows
 // [k0, k0+R0)), laid out by stage_layout: the plan's stage image for the CTA
 // (tap records, pupil-edge segment, run tables), copied with cp.async before
@@ -679,173 +473,6 @@ __device__ void gather_rows_staged(const InstDev &I, const GatherStage<T> &st, i
   if (I.n_edge_wfs == 0) return;
   __syncthreads();
   gather_edges<T>(st.nn(), st.tn, st.tb, st.tk, st.tw, A, s_coef);
-}
-
-// The gather of one CTA band (layer l, node rows [k0, k0+R0)) from the tap
-// records and corner fields in global memory, into the band buffer A (shared
-// memory), sensor by sensor, then the pupil-edge list.  The bilinear weights
-// are separable, so each sensor's term of node (row k, column i) is
-//   sum_ty wy_ty(k) * U(b0(k) + ty, i),   U(b, i) = sum_tx wx_tx(i) * v(a0(i) + tx, b),
-// the same two nested sums, in the same order, as the window sum of the fused
-// gather.  Pass 1 forms U for the corner rows the band's row records reach
-// (gt_brows) and the columns the sensor's taps reach (gt_cols): one column
-// record per thread, then independent loads of v along the corner rows.  Pass 2
-// takes the node rows from U in shared memory.  Each node receives the
-// sensors' terms in sensor order, as the fused gathers do.  For plans whose
-// tables do not fit the analysis CTAs' shared memory; k_gather runs it.
-constexpr int kGatherRowsU = 4;   // corner rows of a column one thread forms at once in pass 1
-
-template <typename T, int KT>
-__device__ void gather_band_global(const InstDev &I, int l, int N, int R0, int crank, T *A, T *U,
-                                   const T *s_coef, const int *s_go, const int *s_nc, const int *s_el,
-                                   const int2 *s_cols, const int2 *s_br, int *s_ry, T *s_rw, int Md) {
-  constexpr int RS = TapRec<T, KT>::RS;
-  const int nt = blockDim.x, tid = threadIdx.x;
-  const T *vv = static_cast<const T *>(I.v);
-  const T *rec = static_cast<const T *>(I.gt_rec);
-  for (int node = tid; node < R0 * N; node += nt) A[node] = T(0);
-  for (int md = 0; md < Md; ++md) {
-    const int2 cols = s_cols[md], br = s_br[md];
-    if (cols.y == 0 || br.y == 0) continue;
-    const int ncol = cols.y, nb = br.y, nc = s_nc[md], el = s_el[md];
-    const T *xr = rec + static_cast<size_t>(s_go[md]) * RS;
-    const T *yr = rec + static_cast<size_t>(s_go[md] + N + crank * R0) * RS;
-    // the band's row records: first corner row relative to the band's (-1: none) and weights
-    for (int kl = tid; kl < R0; kl += nt) {
-      TapRec<T, KT> y;
-      y.load(yr + kl * RS);
-      s_ry[kl] = y.off < 0 ? -1 : (y.off - br.x) / nc;
-#pragma unroll
-      for (int t = 0; t < KT; ++t) s_rw[kl * KT + t] = y.w[t];
-    }
-    // threads per column group: tpr threads cover the columns (tpr the power of two
-    // >= the column count, at most nt), the nt / tpr groups share the rows
-    int tpr = 1;
-    while (tpr < ncol && tpr < nt) tpr <<= 1;
-    const int groups = nt / tpr, ci = tid % tpr, rg = tid / tpr;
-    // pass 1: U(b, c) for the band's corner rows b (from br.x) and columns c
-    for (int c = ci; c < ncol; c += tpr) {
-      const int i = (cols.x + c) & (N - 1);
-      TapRec<T, KT> x;
-      x.load(xr + i * RS);
-      if (x.off < 0) {
-        for (int bb = rg; bb < nb; bb += groups) U[bb * ncol + c] = T(0);
-        continue;
-      }
-      const T *p0 = vv + br.x + x.off;
-      const T *gx = el >= 0 ? static_cast<const T *>(I.gel) + br.x + x.off : nullptr;
-      for (int bb0 = rg; bb0 < nb; bb0 += kGatherRowsU * groups) {
-        T v[kGatherRowsU][KT];
-#pragma unroll
-        for (int u = 0; u < kGatherRowsU; ++u) {
-          const int bb = bb0 + u * groups;
-#pragma unroll
-          for (int t = 0; t < KT; ++t) v[u][t] = bb < nb ? __ldg(p0 + bb * nc + t) : T(0);
-        }
-        if (el >= 0) {
-          // spot elongation with tip/tilt removal: v + m_x Gx + m_y Gy
-          const T mx = s_coef[2 * kMaxEdgeSlots + 2 * el], my = s_coef[2 * kMaxEdgeSlots + 2 * el + 1];
-#pragma unroll
-          for (int u = 0; u < kGatherRowsU; ++u) {
-            const int bb = bb0 + u * groups;
-            if (bb < nb)
-#pragma unroll
-              for (int t = 0; t < KT; ++t)
-                v[u][t] += mx * __ldg(gx + bb * nc + t) + my * __ldg(gx + I.v_total + bb * nc + t);
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < kGatherRowsU; ++u) {
-          const int bb = bb0 + u * groups;
-          if (bb >= nb) break;
-          T sx = x.w[0] * v[u][0];
-#pragma unroll
-          for (int t = 1; t < KT; ++t) sx += x.w[t] * v[u][t];
-          U[bb * ncol + c] = sx;
-        }
-      }
-    }
-    __syncthreads();
-    // pass 2: the band's node rows from U
-    for (int c = ci; c < ncol; c += tpr) {
-      const int i = (cols.x + c) & (N - 1);
-      for (int kl = rg; kl < R0; kl += groups) {
-        const int b0 = s_ry[kl];
-        if (b0 < 0) continue;
-        const T *u = U + b0 * ncol + c;
-        T acc = T(0);
-#pragma unroll
-        for (int t = 0; t < KT; ++t) acc += s_rw[kl * KT + t] * u[t * ncol];
-        A[kl * N + i] += acc;
-      }
-    }
-    __syncthreads();
-  }
-  if (I.n_edge_wfs == 0) return;
-  const int2 seg = I.tt_seg[l * I.C + crank];
-  gather_edges<T>(seg.y - seg.x, I.tt_node + seg.x, I.tt_beg + seg.x, I.tt_k,
-                  static_cast<const T *>(I.tt_w), A, s_coef);
-  __syncthreads();
-}
-
-// ------------------------------------------------------------- k_gather
-// g = sum_m P_m^T v_m (Sec. 5.1, the transposed ray-trace) into the plan's phi
-// buffer, one CTA per (instance, layer, band of N/C rows), for plans whose
-// gather tables are not staged in the analysis kernel; k_analysis with SRC 2
-// then transforms it.  phi is free here: the forward kernel that read it has
-// finished (dependency wait) and the next synthesis rewrites it.
-// tt_mode as in edge_coefficients; io.in1: the slopes (tip/tilt-only data).
-template <typename T>
-__global__ void __launch_bounds__(kGatherThreads, sizeof(T) == 4 ? 2 : 1) k_gather(const InstDev *__restrict__ insts,
-                                                           const ClusterItem *__restrict__ items,
-                                                           IoArgs io, int C, int tt_mode) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ InstDev sI;
-  __shared__ T s_coef[4 * kMaxEdgeSlots];
-  __shared__ int s_go[kMaxGatherSensors], s_nc[kMaxGatherSensors], s_el[kMaxGatherSensors];
-  __shared__ int2 s_cols[kMaxGatherSensors], s_br[kMaxGatherSensors];
-  __shared__ int s_md;
-  pdl_trigger();
-  const ClusterItem it = items[blockIdx.x / C];
-  const int crank = blockIdx.x % C;
-  if (io.active && !io.active[it.inst]) return;
-  load_inst(&sI, insts + it.inst);
-  const InstDev &I = sI;
-  if (threadIdx.x == 0) {
-    int md = 0;
-    for (int m = 0; m < I.n_wfs && md < kMaxGatherSensors; ++m) {
-      const WfsDev &W = I.wfs[m];
-      if (W.kind == kTTOnly) continue;
-      s_go[md] = I.gt_off[m * I.n_layers + it.layer];
-      s_nc[md] = W.nc;
-      s_el[md] = (W.elong && W.kind == kRemoveTT) ? W.tt_idx : -1;
-      s_cols[md] = I.gt_cols[m * I.n_layers + it.layer];
-      s_br[md] = I.gt_brows[(m * I.n_layers + it.layer) * C + crank];
-      ++md;
-    }
-    s_md = md;
-  }
-  const LayerDev &L = I.layers[it.layer];
-  const int N = L.N, R0 = N / C;
-  // shared memory: the band buffer, the band's row records (first row, weights),
-  // then the column-summed corner rows of one sensor (gather_smem_layout)
-  const GatherSmem gs = gather_smem_layout(R0, N, I.max_taps, static_cast<int>(sizeof(T)));
-  T *A = reinterpret_cast<T *>(smem_raw);
-  int *s_ry = reinterpret_cast<int *>(smem_raw + gs.ry);
-  T *s_rw = reinterpret_cast<T *>(smem_raw + gs.rw);
-  T *U = reinterpret_cast<T *>(smem_raw + gs.u);
-  __syncthreads();
-  pdl_wait();
-  if (I.n_edge_wfs > 0)
-    edge_coefficients<T>(I, s_coef, tt_mode, static_cast<const T *>(io.in1[it.inst]));
-#define TOMO_GB(KT) gather_band_global<T, KT>(I, it.layer, N, R0, crank, A, U, s_coef, s_go, s_nc, s_el, s_cols, \
-                                              s_br, s_ry, s_rw, s_md)
-  if (I.max_taps <= 2) TOMO_GB(2);
-  else if (I.max_taps == 3) TOMO_GB(3);
-  else TOMO_GB(4);
-#undef TOMO_GB
-  T *g = static_cast<T *>(I.phi) + L.off + crank * R0 * N;
-  for (int node = threadIdx.x; node < R0 * N; node += blockDim.x) g[node] = A[node];
 }
 
 // ------------------------------------------------------------ k_analysis
@@ -1663,8 +1290,6 @@ cudaError_t allow_type() {
                         reinterpret_cast<const void *>(k_forward<T, 2, true>)};
   for (int i = 0; i < 6 && e == cudaSuccess; ++i)
     e = cudaFuncSetAttribute(fwd[i], cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxForwardSmem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_gather<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxTransformSmem);
   return e;
 }
 
@@ -1728,6 +1353,7 @@ cudaError_t configure_kernels() {
   cudaError_t e = allow_type<float>();
   if (e == cudaSuccess) e = allow_type<double>();
   if (e == cudaSuccess) e = configure_streamed_kernels();
+  if (e == cudaSuccess) e = configure_gather_kernels();
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
   return e;
@@ -1744,24 +1370,9 @@ cudaError_t launch_synthesis(int precision, int src, int lf, int flags, const In
                         : synth_t<double>(src, lf, flags, insts, items, n_clusters, C, smem, io, s);
 }
 
-cudaError_t launch_gather(int precision, int tt_mode, const InstDev *insts, const ClusterItem *items,
-                          int n_clusters, int C, size_t smem_gather, const IoArgs &io, cudaStream_t s) {
-  const dim3 g(n_clusters * C);
-  return precision == 0
-             ? launch_ex(k_gather<float>, g, kGatherThreads, 0, smem_gather, s, insts, items, io, C, tt_mode)
-             : launch_ex(k_gather<double>, g, kGatherThreads, 0, smem_gather, s, insts, items, io, C, tt_mode);
-}
-
 cudaError_t launch_analysis(int precision, int src, int epi, int lf, int flags, const InstDev *insts,
                              const ClusterItem *items, int n_clusters, int C, size_t smem, const IoArgs &io,
-                             cudaStream_t s, int split, size_t smem_gather) {
-  if (src == 1 && split) {
-    // gather in its own kernel, then the transform of its output
-    const int tt_mode = epi == kEpiOp ? 0 : (epi == kEpiResid && (flags & kFlagWarm) ? 1 : 2);
-    cudaError_t e = launch_gather(precision, tt_mode, insts, items, n_clusters, C, smem_gather, io, s);
-    if (e != cudaSuccess) return e;
-    src = 2;
-  }
+                             cudaStream_t s) {
   return precision == 0 ? anal_t<float>(src, epi, lf, flags, insts, items, n_clusters, C, smem, io, s)
                         : anal_t<double>(src, epi, lf, flags, insts, items, n_clusters, C, smem, io, s);
 }

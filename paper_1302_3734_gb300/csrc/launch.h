@@ -28,7 +28,7 @@ cudaError_t launch_synthesis(int precision, int src, int lf, int flags, const In
 // 1 operator (q, p.q -> alpha), 2 residual (r, p, r.z); flags: kFlagWarm.
 cudaError_t launch_analysis(int precision, int src, int epi, int lf, int flags, const InstDev *insts,
                             const ClusterItem *items, int n_clusters, int C, size_t smem,
-                            const IoArgs &io, cudaStream_t s, int split, size_t smem_gather);
+                            const IoArgs &io, cudaStream_t s);
 // The separate gather kernel alone (g = sum_m P_m^T v_m into the plan's phi),
 // for plans whose gather tables are not staged; launch_analysis with src 2 then
 // transforms its output.  tt_mode: 0 operator, 1 warm residual, 2 data only.
@@ -46,9 +46,8 @@ cudaError_t launch_analysis_streamed(int precision, int src, int epi, int lf, in
                                      const StreamSet &S, const IoArgs &io, cudaStream_t s);
 int streamed_launches(const StreamSet &S);
 cudaError_t configure_streamed_kernels();
-
-// Kernels one launch_analysis call launches.
-inline int analysis_launches(int src, int split) { return (src == 1 && split) ? 2 : 1; }
+// Shared-memory attribute of the separate gather kernel.
+cudaError_t configure_gather_kernels();
 
 // Ray-trace, Fried slopes, noise weighting, Gamma^T.  mode 0 operator, 1 residual,
 // 2 data only.  elong: some sensor of the launch has elongated spots.
