@@ -203,15 +203,30 @@ __device__ __forceinline__ T window_sum(const T *__restrict__ p, int nc, const T
 }
 
 // Pupil-edge terms of the CTA's nodes: A[node] += sum over its entries of
-// (e_x t_x + e_y t_y) w (one short list per node, edge slots in s_coef).
+// (e_x t_x + e_y t_y) w (one short list per node, edge slots in s_coef).  The
+// entries of a node are read kEdgeBatch at a time (independent loads, which
+// matters when the lists are in global memory) and summed in list order.
+constexpr int kEdgeBatch = 4;
+
 template <typename T>
 __device__ __forceinline__ void gather_edges(int nn, const int *tn, const int *tb, const int *tk,
                                              const T *tw, T *A, const T *s_coef) {
   for (int j = threadIdx.x; j < nn; j += blockDim.x) {
     T acc = T(0);
-    for (int e = tb[j]; e < tb[j + 1]; ++e) {
-      const int k = tk[e];
-      acc += s_coef[2 * k] * tw[2 * e] + s_coef[2 * k + 1] * tw[2 * e + 1];
+    const int e1 = tb[j + 1];
+    for (int e0 = tb[j]; e0 < e1; e0 += kEdgeBatch) {
+      int k[kEdgeBatch];
+      T wx[kEdgeBatch], wy[kEdgeBatch];
+#pragma unroll
+      for (int u = 0; u < kEdgeBatch; ++u) {
+        const int e = e0 + u < e1 ? e0 + u : e0;
+        k[u] = tk[e];
+        wx[u] = tw[2 * e];
+        wy[u] = tw[2 * e + 1];
+      }
+#pragma unroll
+      for (int u = 0; u < kEdgeBatch; ++u)
+        if (e0 + u < e1) acc += s_coef[2 * k[u]] * wx[u] + s_coef[2 * k[u] + 1] * wy[u];
     }
     A[tn[j]] += acc;
   }

@@ -118,7 +118,7 @@ tomo_status adjoint_ls(tomo_plan *p, const LaunchSet &L, int epi, const IoArgs &
     }, "analysis");
   const int tt_mode = epi == 1 ? 0 : 2;   // operator: the model term; otherwise the data alone
   TOMO_TRY(timed(p, kKindGather, s, [&] {
-    return launch_gather(L.precision, tt_mode, L.d_inst, L.cl, L.n_cl, L.C, L.smem_g, io, s);
+    return launch_gather(L.precision, tt_mode, L.d_inst, L.gi, L.n_gi, L.C, L.smem_g, io, s);
   }, "gather"));
   return timed(p, kKindAnalysis, s, [&] { return anal_ls(L, 2, epi, 0, io, s); }, "analysis", anal_launches(L));
 }
@@ -156,7 +156,7 @@ tomo_status enqueue_solve(tomo_plan *tp, const LaunchSet &L, const void *const *
     }
     if (L.split) {
       TOMO_TRY(timed(tp, kKindGather, s, [&] {
-        return launch_gather(L.precision, warm ? 1 : 2, L.d_inst, L.cl, L.n_cl, L.C, L.smem_g, io, s);
+        return launch_gather(L.precision, warm ? 1 : 2, L.d_inst, L.gi, L.n_gi, L.C, L.smem_g, io, s);
       }, "gather (residual)"));
       TOMO_TRY(timed(tp, kKindAnalysis, s, [&] { return anal_ls(L, 2, 2, warm ? kFlagWarm : 0, io, s); },
                      "analysis (residual)", anal_launches(L)));
@@ -180,7 +180,7 @@ tomo_status enqueue_solve(tomo_plan *tp, const LaunchSet &L, const void *const *
     }, "forward"));
     if (L.split) {
       TOMO_TRY(timed(tp, kKindGather, s, [&] {
-        return launch_gather(L.precision, 0, L.d_inst, L.cl, L.n_cl, L.C, L.smem_g, none, s);
+        return launch_gather(L.precision, 0, L.d_inst, L.gi, L.n_gi, L.C, L.smem_g, none, s);
       }, "gather"));
       TOMO_TRY(timed(tp, kKindAnalysis, s, [&] { return anal_ls(L, 2, 1, it << kIterShift, none, s); }, "analysis",
                      anal_launches(L)));
@@ -314,7 +314,7 @@ tomo_status build_batch(tomo_plan *const *plans, int count, Batch **out) {
     std::vector<ClusterItem> cl;
     std::vector<FwdItem> fwd;
     std::vector<UpdItem> upd;
-    std::vector<PassItem> pass[kMaxLevels + 1], coarse;
+    std::vector<PassItem> pass[kMaxLevels + 1], coarse, gath;
     LaunchSet &L = g.ls;
     for (int slot = 0; slot < k; ++slot) {
       const tomo_plan *p = plans[g.members[slot]];
@@ -324,6 +324,10 @@ tomo_status build_batch(tomo_plan *const *plans, int count, Batch **out) {
       for (auto f : H.fwd_items) {
         f.inst = slot;
         fwd.push_back(f);
+      }
+      for (auto gi : H.gather_items) {
+        gi.inst = slot;
+        gath.push_back(gi);
       }
       for (auto u : H.upd_items) {
         u.inst = slot;
@@ -361,6 +365,8 @@ tomo_status build_batch(tomo_plan *const *plans, int count, Batch **out) {
       L.ss.cnt[lv] = static_cast<int>(pass[lv].size());
       passes.insert(passes.end(), pass[lv].begin(), pass[lv].end());
     }
+    // the gather CTAs of all members, costliest first
+    std::stable_sort(gath.begin(), gath.end(), [](const PassItem &x, const PassItem &y) { return x.slot > y.slot; });
     Arena A;
     const size_t o_i = A.take(sizeof(InstDev) * insts.size());
     const size_t o_c = A.take(sizeof(ClusterItem) * cl.size());
@@ -368,6 +374,7 @@ tomo_status build_batch(tomo_plan *const *plans, int count, Batch **out) {
     const size_t o_u = A.take(sizeof(UpdItem) * upd.size());
     const size_t o_ps = A.take(sizeof(PassItem) * std::max<size_t>(1, passes.size()));
     const size_t o_co = A.take(sizeof(PassItem) * std::max<size_t>(1, coarse.size()));
+    const size_t o_gi = A.take(sizeof(PassItem) * std::max<size_t>(1, gath.size()));
     const size_t bytes = align_up(A.size, 256);
     std::vector<char> img(bytes, 0);
     std::memcpy(img.data() + o_i, insts.data(), sizeof(InstDev) * insts.size());
@@ -376,6 +383,7 @@ tomo_status build_batch(tomo_plan *const *plans, int count, Batch **out) {
     std::memcpy(img.data() + o_u, upd.data(), sizeof(UpdItem) * upd.size());
     if (!passes.empty()) std::memcpy(img.data() + o_ps, passes.data(), sizeof(PassItem) * passes.size());
     if (!coarse.empty()) std::memcpy(img.data() + o_co, coarse.data(), sizeof(PassItem) * coarse.size());
+    if (!gath.empty()) std::memcpy(img.data() + o_gi, gath.data(), sizeof(PassItem) * gath.size());
     cudaError_t e = cudaMalloc(&g.arena, bytes);
     g.bytes = bytes;
     if (e == cudaSuccess) e = cudaMemcpy(g.arena, img.data(), bytes, cudaMemcpyHostToDevice);
@@ -395,6 +403,8 @@ tomo_status build_batch(tomo_plan *const *plans, int count, Batch **out) {
     L.ss.items = reinterpret_cast<const PassItem *>(base + o_ps);
     L.ss.coarse = reinterpret_cast<const PassItem *>(base + o_co);
     L.ss.n_coarse = static_cast<int>(coarse.size());
+    L.gi = reinterpret_cast<const PassItem *>(base + o_gi);
+    L.n_gi = static_cast<int>(gath.size());
   }
   cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
@@ -573,6 +583,7 @@ tomo_status tomo_plan_create_ex(const tomo_geometry *g, const tomo_plan_options 
   const size_t o_upd = A.take(sizeof(UpdItem) * H.upd_items.size());
   const size_t o_pass = A.take(sizeof(PassItem) * std::max<size_t>(1, H.pass_items.size()));
   const size_t o_coarse = A.take(sizeof(PassItem) * std::max<size_t>(1, H.coarse_items.size()));
+  const size_t o_gitem = A.take(sizeof(PassItem) * std::max<size_t>(1, H.gather_items.size()));
   const size_t tables_end = align_up(A.size, 256);
   const size_t n = static_cast<size_t>(H.n);
   const size_t o_r = A.take(esz * n);
@@ -738,6 +749,7 @@ tomo_status tomo_plan_create_ex(const tomo_geometry *g, const tomo_plan_options 
   put(o_upd, H.upd_items.data(), sizeof(UpdItem) * H.upd_items.size());
   put(o_pass, H.pass_items.data(), sizeof(PassItem) * H.pass_items.size());
   put(o_coarse, H.coarse_items.data(), sizeof(PassItem) * H.coarse_items.size());
+  put(o_gitem, H.gather_items.data(), sizeof(PassItem) * H.gather_items.size());
 
   auto bail = [&](tomo_status code, const std::string &msg) {
     cudaFree(p->arena);
@@ -795,6 +807,8 @@ tomo_status tomo_plan_create_ex(const tomo_geometry *g, const tomo_plan_options 
   L.precision = H.precision;
   L.split = H.gather_staged ? 0 : 1;
   L.smem_g = static_cast<size_t>(H.smem_gather);
+  L.gi = reinterpret_cast<const PassItem *>(base + o_gitem);
+  L.n_gi = static_cast<int>(H.gather_items.size());
   L.elong = 0;
   for (const auto &w : H.wfs) L.elong |= w.elong;
   L.stream = H.stream_tf;

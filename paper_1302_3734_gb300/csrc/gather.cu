@@ -121,14 +121,15 @@ __device__ void gather_band_global(const InstDev &I, int l, int N, int R0, int c
 
 // ------------------------------------------------------------- k_gather
 // g = sum_m P_m^T v_m (Sec. 5.1, the transposed ray-trace) into the plan's phi
-// buffer, one CTA per (instance, layer, band of N/C rows), for plans whose
-// gather tables are not staged in the analysis kernel; k_analysis with SRC 2
+// buffer, one CTA per (instance, layer, band of N/C rows), the costliest bands
+// first (the host orders items), for plans whose gather tables are not staged
+// in the analysis kernel; k_analysis with SRC 2
 // then transforms it.  phi is free here: the forward kernel that read it has
 // finished (dependency wait) and the next synthesis rewrites it.
 // tt_mode as in edge_coefficients; io.in1: the slopes (tip/tilt-only data).
 template <typename T>
 __global__ void __launch_bounds__(kGatherThreads, sizeof(T) == 4 ? 2 : 1) k_gather(const InstDev *__restrict__ insts,
-                                                           const ClusterItem *__restrict__ items,
+                                                           const PassItem *__restrict__ items,
                                                            IoArgs io, int C, int tt_mode) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ InstDev sI;
@@ -137,8 +138,8 @@ __global__ void __launch_bounds__(kGatherThreads, sizeof(T) == 4 ? 2 : 1) k_gath
   __shared__ int2 s_cols[kMaxGatherSensors], s_br[kMaxGatherSensors];
   __shared__ int s_md;
   pdl_trigger();
-  const ClusterItem it = items[blockIdx.x / C];
-  const int crank = blockIdx.x % C;
+  const PassItem it = items[blockIdx.x];
+  const int crank = it.row0;
   if (io.active && !io.active[it.inst]) return;
   load_inst(&sI, insts + it.inst);
   const InstDev &I = sI;
@@ -183,9 +184,9 @@ __global__ void __launch_bounds__(kGatherThreads, sizeof(T) == 4 ? 2 : 1) k_gath
   for (int node = threadIdx.x; node < R0 * N; node += blockDim.x) g[node] = A[node];
 }
 
-cudaError_t launch_gather(int precision, int tt_mode, const InstDev *insts, const ClusterItem *items,
-                          int n_clusters, int C, size_t smem_gather, const IoArgs &io, cudaStream_t s) {
-  const dim3 g(n_clusters * C);
+cudaError_t launch_gather(int precision, int tt_mode, const InstDev *insts, const PassItem *items, int n_items,
+                          int C, size_t smem_gather, const IoArgs &io, cudaStream_t s) {
+  const dim3 g(n_items);
   return precision == 0
              ? launch_ex(k_gather<float>, g, kGatherThreads, 0, smem_gather, s, insts, items, io, C, tt_mode)
              : launch_ex(k_gather<double>, g, kGatherThreads, 0, smem_gather, s, insts, items, io, C, tt_mode);

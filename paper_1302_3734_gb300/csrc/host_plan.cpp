@@ -559,6 +559,26 @@ tomo_status build_host_plan(const tomo_geometry *geo, HostPlan *P, std::string *
     }
     P->tt_beg.push_back(static_cast<int>(P->tt_k.size()));
   }
+  // the separate gather kernel's CTAs, one per (layer, band), costliest first so
+  // that the light bands fill the end of the launch; a band's cost counts its
+  // sensors' column sums and node rows, its pupil-edge entries and its grid rows
+  P->gather_items.clear();
+  for (int l = 0; l < P->n_layers; ++l) {
+    const int N = P->layers[l].N, R0 = N / P->C;
+    for (int c = 0; c < P->C; ++c) {
+      long long cost = static_cast<long long>(R0) * N / 4;
+      for (int m = 0; m < P->n_wfs; ++m) {
+        const int2 br = P->gt_brows[(static_cast<size_t>(m) * P->n_layers + l) * P->C + c];
+        const int ncol = P->gt_cols[m * P->n_layers + l].y;
+        if (br.y > 0 && ncol > 0) cost += static_cast<long long>(br.y + R0) * ncol;
+      }
+      const int2 seg = P->tt_seg[l * P->C + c];
+      cost += 4LL * (P->tt_beg[seg.y] - P->tt_beg[seg.x]);
+      P->gather_items.push_back({0, l, c, static_cast<int>(std::min<long long>(cost, INT_MAX))});
+    }
+  }
+  std::stable_sort(P->gather_items.begin(), P->gather_items.end(),
+                   [](const PassItem &a, const PassItem &b) { return a.slot > b.slot; });
   // staging of the gather tables in the analysis kernel, when it fits
   P->n_dense = 0;
   for (const auto &d : P->wfs) P->n_dense += d.kind != kTTOnly ? 1 : 0;

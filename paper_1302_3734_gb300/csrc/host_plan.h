@@ -72,6 +72,9 @@ struct HostPlan {
   int stream_tf = 0, n_cl_part = 0, pass_kmax = 0;
   int pass_off[kMaxLevels + 1] = {0}, pass_cnt[kMaxLevels + 1] = {0};
   std::vector<PassItem> pass_items, coarse_items;
+  // separate gather kernel: one CTA per (layer, band = row0), costliest first
+  // (slot: the band's estimated cost)
+  std::vector<PassItem> gather_items;
   long long smem_pass = 0, smem_coarse = 0, lls_elems = 0;
 };
 
