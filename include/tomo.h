@@ -134,7 +134,10 @@ typedef struct {
   int cluster_size;            /* CTAs per layer in the transform kernels (one thread-block cluster
                                   per layer): 0 = min(16, N_min/8); else a power of two in
                                   [1, min(16, N_min/2)].  Large clusters give the lowest latency of
-                                  one solve, small ones the most solves per second in big batches */
+                                  one solve, small ones the most solves per second in big batches.
+                                  Streamed plans (transforms 2) use it only as the number of row
+                                  bands of the separate gather kernel, a power of two in
+                                  [1, min(64, N_min/2)] */
   int transforms;              /* 0: chosen by the plan; 1: one thread-block cluster per layer and
                                   transform; 2: streamed, level by level over row tiles of every
                                   layer with no cluster (the default when a layer's cluster CTAs

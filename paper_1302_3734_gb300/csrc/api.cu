@@ -118,7 +118,7 @@ tomo_status adjoint_ls(tomo_plan *p, const LaunchSet &L, int epi, const IoArgs &
     }, "analysis");
   const int tt_mode = epi == 1 ? 0 : 2;   // operator: the model term; otherwise the data alone
   TOMO_TRY(timed(p, kKindGather, s, [&] {
-    return launch_gather(L.precision, tt_mode, L.d_inst, L.gi, L.n_gi, L.C, L.smem_g, io, s);
+    return launch_gather(L.precision, tt_mode, L.d_inst, L.gi, L.n_gi, L.C, L.gather_vs, L.smem_g, io, s);
   }, "gather"));
   return timed(p, kKindAnalysis, s, [&] { return anal_ls(L, 2, epi, 0, io, s); }, "analysis", anal_launches(L));
 }
@@ -156,7 +156,7 @@ tomo_status enqueue_solve(tomo_plan *tp, const LaunchSet &L, const void *const *
     }
     if (L.split) {
       TOMO_TRY(timed(tp, kKindGather, s, [&] {
-        return launch_gather(L.precision, warm ? 1 : 2, L.d_inst, L.gi, L.n_gi, L.C, L.smem_g, io, s);
+        return launch_gather(L.precision, warm ? 1 : 2, L.d_inst, L.gi, L.n_gi, L.C, L.gather_vs, L.smem_g, io, s);
       }, "gather (residual)"));
       TOMO_TRY(timed(tp, kKindAnalysis, s, [&] { return anal_ls(L, 2, 2, warm ? kFlagWarm : 0, io, s); },
                      "analysis (residual)", anal_launches(L)));
@@ -180,7 +180,7 @@ tomo_status enqueue_solve(tomo_plan *tp, const LaunchSet &L, const void *const *
     }, "forward"));
     if (L.split) {
       TOMO_TRY(timed(tp, kKindGather, s, [&] {
-        return launch_gather(L.precision, 0, L.d_inst, L.gi, L.n_gi, L.C, L.smem_g, none, s);
+        return launch_gather(L.precision, 0, L.d_inst, L.gi, L.n_gi, L.C, L.gather_vs, L.smem_g, none, s);
       }, "gather"));
       TOMO_TRY(timed(tp, kKindAnalysis, s, [&] { return anal_ls(L, 2, 1, it << kIterShift, none, s); }, "analysis",
                      anal_launches(L)));
@@ -299,6 +299,7 @@ tomo_status build_batch(tomo_plan *const *plans, int count, Batch **out) {
       const HostPlan &H0 = plans[cand.members[0]]->hp;
       if (H0.C == H.C && H0.Lf == H.Lf && H0.precision == H.precision &&
           H0.gather_staged == H.gather_staged && H0.stream_tf == H.stream_tf &&
+          H0.gather_vstage == H.gather_vstage &&
           static_cast<int>(cand.members.size()) < kMaxBatch)
         g = &cand;
     }
@@ -341,6 +342,7 @@ tomo_status build_batch(tomo_plan *const *plans, int count, Batch **out) {
       L.precision = H.precision;
       L.split = H.gather_staged ? 0 : 1;
       L.smem_g = std::max(L.smem_g, static_cast<size_t>(H.smem_gather));
+      L.gather_vs = H.gather_vstage;
       for (const auto &w : H.wfs) L.elong |= w.elong;
       L.stream = H.stream_tf;
       if (H.stream_tf) {
@@ -662,6 +664,8 @@ tomo_status tomo_plan_create_ex(const tomo_geometry *g, const tomo_plan_options 
   I.vs_run = reinterpret_cast<const int4 *>(base + o_vsrun);
   I.vstage = H.vstage;
   I.v_total = H.v_total;
+  I.max_band_cells = static_cast<int>(H.max_band_cells);
+  I.max_band_v = static_cast<int>(H.max_band_v);
   I.stage_img = base + o_stage;
   I.edge_slots = reinterpret_cast<const EdgeSlot *>(base + o_eslot);
   I.gel = H.gel.empty() ? nullptr : base + o_gel;
@@ -807,6 +811,7 @@ tomo_status tomo_plan_create_ex(const tomo_geometry *g, const tomo_plan_options 
   L.precision = H.precision;
   L.split = H.gather_staged ? 0 : 1;
   L.smem_g = static_cast<size_t>(H.smem_gather);
+  L.gather_vs = H.gather_vstage;
   L.gi = reinterpret_cast<const PassItem *>(base + o_gitem);
   L.n_gi = static_cast<int>(H.gather_items.size());
   L.elong = 0;

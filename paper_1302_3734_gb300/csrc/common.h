@@ -118,6 +118,8 @@ struct InstDev {
   const int *gt_ys;             // per row record: its window start in the staged v rows
   const int4 *vs_run;           // per (layer, rank, dense sensor): v run {g0, 16-byte words, smem offset}
   int vstage, v_total;          // staged v elements per analysis CTA; corner values of all sensors
+  int max_band_cells;           // separate gather: largest column sums of one (sensor, layer, band)
+  int max_band_v;               // ... and largest 16-byte-aligned run of its band rows of v (elements)
   const int2 *gt_cols;          // per (m,l): columns [x, x+y) mod N_l that the sensor's taps reach
   const int2 *gt_brows;         // per (m,l,rank): {v offset of the first corner row the band's row
                                 // records reach, number of rows}
@@ -239,18 +241,26 @@ TOMO_HD inline StageLayout stage_layout(int n_dense, int N, int R0, int rec_stri
 
 // Shared-memory layout of the separate gather kernel (bytes, 16-byte aligned):
 // the band buffer of R0 x N nodes, the band's row records (first corner row,
-// KT weights per node row), then the column-summed corner rows of one sensor
-// (the plan's largest band needs max_band_cells elements there).
+// KT weights per node row), the column-summed corner rows of one sensor (the
+// plan's largest band needs `cells` elements there), then, when the kernel
+// stages the corner rows it reads, `vcells` elements for one sensor's band
+// rows of v.
 struct GatherSmem {
-  int ry, rw, u;
+  int ry, rw, u, v, total;
 };
-TOMO_HD inline GatherSmem gather_smem_layout(int R0, int N, int KT, int esz) {
+TOMO_HD inline GatherSmem gather_smem_layout(int R0, int N, int KT, int esz, long long cells, long long vcells,
+                                             bool vstage) {
   GatherSmem g;
   g.ry = (R0 * N * esz + 15) / 16 * 16;
   g.rw = g.ry + (4 * R0 + 15) / 16 * 16;
   g.u = g.rw + (R0 * KT * esz + 15) / 16 * 16;
+  g.v = g.u + static_cast<int>((cells * esz + 15) / 16 * 16);
+  g.total = g.v + (vstage ? static_cast<int>((vcells * esz + 15) / 16 * 16) : 0);
   return g;
 }
+// Shared memory up to which the gather kernel stages the corner rows (two CTAs
+// per SM keep fitting).
+constexpr int kGatherStageSmem = 104 * 1024;
 
 // Work items.
 struct ClusterItem { int inst, layer; };

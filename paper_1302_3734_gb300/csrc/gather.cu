@@ -24,21 +24,45 @@ namespace tomo {
 // takes the node rows from U in shared memory.  Each node receives the
 // sensors' terms in sensor order, as the fused gathers do.  For plans whose
 // tables do not fit the analysis CTAs' shared memory; k_gather runs it.
+// VS: the band rows of v that pass 1 reads are copied to shared memory V first
+// (cp.async; the next sensor's copy runs during pass 2 of the current one);
+// otherwise pass 1 reads them from global memory.
 constexpr int kGatherRowsU = 4;   // corner rows of a column one thread forms at once in pass 1
 
-template <typename T, int KT>
-__device__ void gather_band_global(const InstDev &I, int l, int N, int R0, int crank, T *A, T *U,
+template <typename T, int KT, bool VS>
+__device__ void gather_band_global(const InstDev &I, int l, int N, int R0, int crank, T *A, T *U, T *V,
                                    const T *s_coef, const int *s_go, const int *s_nc, const int *s_el,
                                    const int2 *s_cols, const int2 *s_br, int *s_ry, T *s_rw, int Md) {
   constexpr int RS = TapRec<T, KT>::RS;
+  constexpr int vq = 16 / static_cast<int>(sizeof(T));   // elements per 16-byte copy
   const int nt = blockDim.x, tid = threadIdx.x;
   const T *vv = static_cast<const T *>(I.v);
   const T *rec = static_cast<const T *>(I.gt_rec);
+  // the copy of sensor md's band rows [br.x, br.x + nb nc) of v, and KT more
+  // elements (zero-weight taps when nc < KT), from the 16-byte boundary at or
+  // below br.x (the plan pads v beyond its last sensor)
+  auto stage = [&](int md) {
+    const int2 br = s_br[md];
+    const int g0 = br.x / vq * vq;
+    const int nq = (br.x - g0 + br.y * s_nc[md] + KT + vq - 1) / vq;
+    const uint4 *src = reinterpret_cast<const uint4 *>(vv + g0);
+    uint4 *dst = reinterpret_cast<uint4 *>(V);
+    for (int j = tid; j < nq; j += nt) cp_async16(dst + j, src + j);
+    cp_async_commit();
+  };
   for (int node = tid; node < R0 * N; node += nt) A[node] = T(0);
+  if constexpr (VS) {
+    if (Md > 0) stage(0);
+  }
+  // (every listed sensor reaches the band: nonempty columns and corner rows)
   for (int md = 0; md < Md; ++md) {
+    if constexpr (VS) {
+      cp_async_wait_all();   // this thread's copies of sensor md
+      __syncthreads();       // everyone's; pass 2 of the previous sensor is done with U
+    }
     const int2 cols = s_cols[md], br = s_br[md];
-    if (cols.y == 0 || br.y == 0) continue;
     const int ncol = cols.y, nb = br.y, nc = s_nc[md], el = s_el[md];
+    const T *vsrc = VS ? V + (br.x - br.x / vq * vq) : vv + br.x;
     const T *xr = rec + static_cast<size_t>(s_go[md]) * RS;
     const T *yr = rec + static_cast<size_t>(s_go[md] + N + crank * R0) * RS;
     // the band's row records: first corner row relative to the band's (-1: none) and weights
@@ -63,7 +87,7 @@ __device__ void gather_band_global(const InstDev &I, int l, int N, int R0, int c
         for (int bb = rg; bb < nb; bb += groups) U[bb * ncol + c] = T(0);
         continue;
       }
-      const T *p0 = vv + br.x + x.off;
+      const T *p0 = vsrc + x.off;
       const T *gx = el >= 0 ? static_cast<const T *>(I.gel) + br.x + x.off : nullptr;
       for (int bb0 = rg; bb0 < nb; bb0 += kGatherRowsU * groups) {
         T v[kGatherRowsU][KT];
@@ -71,7 +95,7 @@ __device__ void gather_band_global(const InstDev &I, int l, int N, int R0, int c
         for (int u = 0; u < kGatherRowsU; ++u) {
           const int bb = bb0 + u * groups;
 #pragma unroll
-          for (int t = 0; t < KT; ++t) v[u][t] = bb < nb ? __ldg(p0 + bb * nc + t) : T(0);
+          for (int t = 0; t < KT; ++t) v[u][t] = bb < nb ? (VS ? p0[bb * nc + t] : __ldg(p0 + bb * nc + t)) : T(0);
         }
         if (el >= 0) {
           // spot elongation with tip/tilt removal: v + m_x Gx + m_y Gy
@@ -97,6 +121,9 @@ __device__ void gather_band_global(const InstDev &I, int l, int N, int R0, int c
       }
     }
     __syncthreads();
+    if constexpr (VS) {
+      if (md + 1 < Md) stage(md + 1);   // V is free: pass 1 is done
+    }
     // pass 2: the band's node rows from U
     for (int c = ci; c < ncol; c += tpr) {
       const int i = (cols.x + c) & (N - 1);
@@ -110,8 +137,9 @@ __device__ void gather_band_global(const InstDev &I, int l, int N, int R0, int c
         A[kl * N + i] += acc;
       }
     }
-    __syncthreads();
+    if constexpr (!VS) __syncthreads();
   }
+  if constexpr (VS) __syncthreads();
   if (I.n_edge_wfs == 0) return;
   const int2 seg = I.tt_seg[l * I.C + crank];
   gather_edges<T>(seg.y - seg.x, I.tt_node + seg.x, I.tt_beg + seg.x, I.tt_k,
@@ -127,7 +155,7 @@ __device__ void gather_band_global(const InstDev &I, int l, int N, int R0, int c
 // then transforms it.  phi is free here: the forward kernel that read it has
 // finished (dependency wait) and the next synthesis rewrites it.
 // tt_mode as in edge_coefficients; io.in1: the slopes (tip/tilt-only data).
-template <typename T>
+template <typename T, bool VS>
 __global__ void __launch_bounds__(kGatherThreads, sizeof(T) == 4 ? 2 : 1) k_gather(const InstDev *__restrict__ insts,
                                                            const PassItem *__restrict__ items,
                                                            IoArgs io, int C, int tt_mode) {
@@ -169,14 +197,16 @@ __global__ void __launch_bounds__(kGatherThreads, sizeof(T) == 4 ? 2 : 1) k_gath
   if (I.n_edge_wfs > 0)
     edge_coefficients<T>(I, s_coef, tt_mode, static_cast<const T *>(io.in1[it.inst]));
   // shared memory: the band buffer, the band's row records (first row, weights),
-  // then the column-summed corner rows of one sensor (gather_smem_layout)
-  const GatherSmem gs = gather_smem_layout(R0, N, I.max_taps, static_cast<int>(sizeof(T)));
+  // the column-summed corner rows of one sensor, the staged rows of v (gather_smem_layout)
+  const GatherSmem gs = gather_smem_layout(R0, N, I.max_taps, static_cast<int>(sizeof(T)), I.max_band_cells,
+                                           I.max_band_v, VS);
   T *A = reinterpret_cast<T *>(smem_raw);
   int *s_ry = reinterpret_cast<int *>(smem_raw + gs.ry);
   T *s_rw = reinterpret_cast<T *>(smem_raw + gs.rw);
   T *U = reinterpret_cast<T *>(smem_raw + gs.u);
-#define TOMO_GB(KT) gather_band_global<T, KT>(I, it.layer, N, R0, crank, A, U, s_coef, s_go, s_nc, s_el, s_cols, \
-                                              s_br, s_ry, s_rw, s_md)
+  T *V = reinterpret_cast<T *>(smem_raw + gs.v);
+#define TOMO_GB(KT) gather_band_global<T, KT, VS>(I, it.layer, N, R0, crank, A, U, V, s_coef, s_go, s_nc, s_el, \
+                                                  s_cols, s_br, s_ry, s_rw, s_md)
   if (I.max_taps <= 2) TOMO_GB(2);
   else if (I.max_taps == 3) TOMO_GB(3);
   else TOMO_GB(4);
@@ -184,20 +214,28 @@ __global__ void __launch_bounds__(kGatherThreads, sizeof(T) == 4 ? 2 : 1) k_gath
   for (int node = threadIdx.x; node < R0 * N; node += blockDim.x) g[node] = A[node];
 }
 
+template <typename T>
+cudaError_t gather_t(int vstage, dim3 g, size_t smem, cudaStream_t s, const InstDev *insts, const PassItem *items,
+                     const IoArgs &io, int C, int tt_mode) {
+  return vstage ? launch_ex(k_gather<T, true>, g, kGatherThreads, 0, smem, s, insts, items, io, C, tt_mode)
+                : launch_ex(k_gather<T, false>, g, kGatherThreads, 0, smem, s, insts, items, io, C, tt_mode);
+}
+
 cudaError_t launch_gather(int precision, int tt_mode, const InstDev *insts, const PassItem *items, int n_items,
-                          int C, size_t smem_gather, const IoArgs &io, cudaStream_t s) {
+                          int C, int vstage, size_t smem_gather, const IoArgs &io, cudaStream_t s) {
   const dim3 g(n_items);
-  return precision == 0
-             ? launch_ex(k_gather<float>, g, kGatherThreads, 0, smem_gather, s, insts, items, io, C, tt_mode)
-             : launch_ex(k_gather<double>, g, kGatherThreads, 0, smem_gather, s, insts, items, io, C, tt_mode);
+  return precision == 0 ? gather_t<float>(vstage, g, smem_gather, s, insts, items, io, C, tt_mode)
+                        : gather_t<double>(vstage, g, smem_gather, s, insts, items, io, C, tt_mode);
 }
 
 cudaError_t configure_gather_kernels() {
   cudaError_t e = cudaSuccess;
 #define TOMO_CFG(K) \
   if (e == cudaSuccess) e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxTransformSmem)
-  TOMO_CFG(k_gather<float>);
-  TOMO_CFG(k_gather<double>);
+  TOMO_CFG((k_gather<float, false>));
+  TOMO_CFG((k_gather<float, true>));
+  TOMO_CFG((k_gather<double, false>));
+  TOMO_CFG((k_gather<double, true>));
 #undef TOMO_CFG
   return e;
 }

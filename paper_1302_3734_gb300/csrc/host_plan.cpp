@@ -183,11 +183,15 @@ tomo_status build_host_plan(const tomo_geometry *geo, HostPlan *P, std::string *
     Nmax = std::max(Nmax, L.N);
   }
   // cluster size: every layer keeps >= 8 rows per CTA at level 1, unless the
-  // caller asks for another power of two (1..16, at most N/2)
+  // caller asks for another power of two (1..16, at most N/2; streamed plans,
+  // whose transforms use no cluster, up to 64 bands of the separate gather)
   P->C = std::min(16, Nmin / 8);
   if (cluster_request > 0) {
-    if (cluster_request > 16 || (cluster_request & (cluster_request - 1)) || cluster_request > Nmin / 2) {
-      *err = "cluster size must be a power of two in [1, min(16, N/2)]";
+    const int cmax = transforms == 2 ? 64 : 16;
+    if (cluster_request > cmax || (cluster_request & (cluster_request - 1)) || cluster_request > Nmin / 2) {
+      *err = transforms == 2 ? "cluster size (gather bands) of a streamed plan must be a power of two in "
+                               "[1, min(64, N/2)]"
+                             : "cluster size must be a power of two in [1, min(16, N/2)]";
       return TOMO_ERR_ARG;
     }
     P->C = cluster_request;
@@ -526,16 +530,34 @@ tomo_status build_host_plan(const tomo_geometry *geo, HostPlan *P, std::string *
         P->gt_brows[(static_cast<size_t>(m) * P->n_layers + l) * P->C + c] = make_int2(d.v_off + lo * d.nc, hi - lo);
         P->max_band_cells = std::max<long long>(P->max_band_cells,
                                                 static_cast<long long>(hi - lo) * P->gt_cols[m * P->n_layers + l].y);
+        // (KT more elements: a window's zero-weight taps may read past the rows when nc < KT)
+        const int vq = P->precision ? 2 : 4, start = d.v_off + lo * d.nc;
+        const long long run = start - start / vq * vq + static_cast<long long>(hi - lo) * d.nc + KT;
+        P->max_band_v = std::max<long long>(P->max_band_v, (run + vq - 1) / vq * vq);
       }
     }
   if (P->n_edge_wfs > 64) {
     *err = "more than 64 sensors with tip/tilt removal or tip/tilt-only measurement";
     return TOMO_ERR_UNSUPPORTED;
   }
-  // group the pupil-edge entries by (layer, cluster rank, node)
-  std::sort(tt_entries.begin(), tt_entries.end(), [](const TTEntry &x, const TTEntry &y) {
+  // group the pupil-edge entries by (layer, cluster rank, node), and merge those
+  // of one (node, edge slot): the slot's coefficients multiply the summed weights
+  std::stable_sort(tt_entries.begin(), tt_entries.end(), [](const TTEntry &x, const TTEntry &y) {
     return x.layer != y.layer ? x.layer < y.layer : (x.node != y.node ? x.node < y.node : x.k < y.k);
   });
+  {
+    size_t w = 0;
+    for (size_t e = 0; e < tt_entries.size(); ++e) {
+      if (w > 0 && tt_entries[w - 1].layer == tt_entries[e].layer && tt_entries[w - 1].node == tt_entries[e].node &&
+          tt_entries[w - 1].k == tt_entries[e].k) {
+        tt_entries[w - 1].wx += tt_entries[e].wx;
+        tt_entries[w - 1].wy += tt_entries[e].wy;
+      } else {
+        tt_entries[w++] = tt_entries[e];
+      }
+    }
+    tt_entries.resize(w);
+  }
   P->tt_seg.assign(static_cast<size_t>(P->n_layers) * P->C, make_int2(0, 0));
   {
     size_t e = 0;
@@ -649,11 +671,17 @@ tomo_status build_host_plan(const tomo_geometry *geo, HostPlan *P, std::string *
     P->gather_staged = fits ? 1 : 0;
     P->smem_analysis = fits ? need : P->smem_transform;
     // the separate gather kernel: the band buffer (N/C rows of N), the band's row
-    // records, then one sensor's column-summed corner rows
-    for (const auto &d : P->layers)
-      P->smem_gather = std::max<long long>(P->smem_gather,
-                                           gather_smem_layout(d.N / P->C, d.N, P->max_taps, esz).u);
-    P->smem_gather += P->max_band_cells * esz;
+    // records, one sensor's column-summed corner rows, and the staged corner rows
+    // of two sensors where two CTAs per SM still fit
+    long long plain = 0, staged = 0;
+    for (const auto &d : P->layers) {
+      plain = std::max<long long>(plain, gather_smem_layout(d.N / P->C, d.N, P->max_taps, esz, P->max_band_cells,
+                                                            P->max_band_v, false).total);
+      staged = std::max<long long>(staged, gather_smem_layout(d.N / P->C, d.N, P->max_taps, esz, P->max_band_cells,
+                                                              P->max_band_v, true).total);
+    }
+    P->gather_vstage = staged <= kGatherStageSmem ? 1 : 0;
+    P->smem_gather = P->gather_vstage ? staged : plain;
     if (!fits && P->smem_gather > 220LL * 1024) {
       *err = "layer grids too large for the separate gather kernel's band buffers";
       return TOMO_ERR_UNSUPPORTED;

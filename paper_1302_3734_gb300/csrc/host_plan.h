@@ -44,6 +44,8 @@ struct HostPlan {
   std::vector<int2> gt_cols;       // per (m,l): columns [x, x+y) mod N that the sensor's taps reach
   std::vector<int2> gt_brows;      // per (m,l,rank): {v offset of the band's first corner row, rows}
   long long max_band_cells = 0;    // largest (corner rows x columns) of one (sensor, layer, band)
+  long long max_band_v = 0;        // largest 16-byte-aligned run of one band's corner rows of v
+  int gather_vstage = 0;           // 1: the separate gather kernel stages those rows in shared memory
   long long smem_gather = 0;       // dynamic shared memory of the separate gather kernel (bytes)
   std::vector<int4> vs_run;        // per (layer, rank, dense sensor): {g0, nvec, smem offset, 0}
   int vstage = 0;                  // largest staged v (T elements) of one analysis CTA

@@ -32,9 +32,10 @@ cudaError_t launch_analysis(int precision, int src, int epi, int lf, int flags, 
 // The separate gather kernel alone (g = sum_m P_m^T v_m into the plan's phi),
 // for plans whose gather tables are not staged; launch_analysis with src 2 then
 // transforms its output.  tt_mode: 0 operator, 1 warm residual, 2 data only.
-// items: one per CTA, {instance, layer, band (row0)}; C: bands per layer.
+// items: one per CTA, {instance, layer, band (row0)}; C: bands per layer;
+// vstage: the plans stage the band rows of v in shared memory.
 cudaError_t launch_gather(int precision, int tt_mode, const InstDev *insts, const PassItem *items, int n_items,
-                          int C, size_t smem_gather, const IoArgs &io, cudaStream_t s);
+                          int C, int vstage, size_t smem_gather, const IoArgs &io, cudaStream_t s);
 
 // Streamed transforms (plans with stream_tf): the synthesis launches the coarse
 // kernel, then the passes from the coarsest streamed level down to level 1; the

@@ -30,6 +30,7 @@ struct LaunchSet {
   int precision = 0;
   int split = 0;                 // gather in its own kernel (tables not staged in shared memory)
   size_t smem_g = 0;             // its dynamic shared memory
+  int gather_vs = 0;             // it stages the band rows of v in shared memory
   const PassItem *gi = nullptr;  // its CTAs' (instance, layer, band), costliest first
   int n_gi = 0;
   int elong = 0;                 // some sensor has elongated spots (k_forward variant)

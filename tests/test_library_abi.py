@@ -129,6 +129,12 @@ def test_plan_options_validation_without_gpu(lib):
         opt.cluster_size = bad
         assert lib.tomo_plan_create_ex(ctypes.byref(g), ctypes.byref(opt), None, ctypes.byref(h)) == 1
         assert "cluster size" in lib.tomo_last_error().decode()
+    opt = PlanOptions()
+    opt.transforms = 2                 # streamed: up to 64 gather bands, at most N/2
+    for bad in (48, 128, 64):
+        opt.cluster_size = bad
+        assert lib.tomo_plan_create_ex(ctypes.byref(g), ctypes.byref(opt), None, ctypes.byref(h)) == 1
+        assert "cluster size" in lib.tomo_last_error().decode()
     assert not h.value
 
 
