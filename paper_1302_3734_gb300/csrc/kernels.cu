@@ -451,24 +451,68 @@ struct GatherStage {
   }
 };
 
-// The gather of gather_rows from the staged records and v rows: one node per
-// thread and pass, sensors inner with the sum in a register.
+// The gather of gather_rows from the staged records and v rows, sensors inner
+// with the sums in registers.  A thread takes one column and two adjacent node
+// rows: they share the column's tap record, and their windows' corner rows
+// overlap, so each corner row's weighted column sum sx is formed once for both
+// (rows of the second window d = 0..2 rows below the first's; other offsets
+// take the two windows apart).  Each node's sum has window_sum's order.
+template <typename T, int KT, int D>
+__device__ __forceinline__ void pair_sums(const T *h, const TapRec<T, KT> &y0, const TapRec<T, KT> &y1, T &acc0,
+                                          T &acc1) {
+  T s0 = T(0), s1 = T(0);
+#pragma unroll
+  for (int ty = 0; ty < KT; ++ty) s0 += y0.w[ty] * h[ty];
+#pragma unroll
+  for (int ty = 0; ty < KT; ++ty) s1 += y1.w[ty] * h[D + ty];
+  acc0 += s0;
+  acc1 += s1;
+}
+
 template <typename T, int KT>
 __device__ void gather_rows_staged(const InstDev &I, const GatherStage<T> &st, int N, int R0,
                                    T *A, const T *s_coef) {
   constexpr int RS = TapRec<T, KT>::RS;
   const int nt = blockDim.x, tid = threadIdx.x, Md = I.n_dense, lgN = __ffs(N) - 1;
-  for (int node = tid; node < R0 * N; node += nt) {
-    const T *xr = st.xr + (node & (N - 1)) * RS;
-    const T *yr = st.yr + (node >> lgN) * RS;
-    T acc = T(0);
+  for (int pr = tid; pr < (R0 >> 1) * N; pr += nt) {
+    const int col = pr & (N - 1), k0 = (pr >> lgN) << 1;
+    const T *xr = st.xr + col * RS;
+    const T *yr = st.yr + k0 * RS;
+    T acc0 = T(0), acc1 = T(0);
     for (int md = 0; md < Md; ++md) {
-      TapRec<T, KT> x, y;
+      TapRec<T, KT> x, y0, y1;
       x.load(xr + md * N * RS);
-      y.load(yr + md * R0 * RS);
-      if (x.off >= 0 && y.off >= 0) acc += window_sum<T, KT, true>(st.vs + y.off + x.off, st.mnc[md], x, y);
+      y0.load(yr + md * R0 * RS);
+      y1.load(yr + md * R0 * RS + RS);
+      if (x.off < 0) continue;
+      const int nc = st.mnc[md];
+      const int d = (y0.off >= 0 && y1.off >= 0) ? (y1.off - y0.off) / nc : -1;
+      if (d >= 0 && d <= 2 && y1.off - y0.off == d * nc) {
+        // the corner rows of both windows, each row's column sum once
+        T h[KT + 2];
+        const T *p = st.vs + y0.off + x.off;
+#pragma unroll
+        for (int r = 0; r < KT + 2; ++r) {
+          if (r < KT + d) {
+            T v[KT];
+#pragma unroll
+            for (int tx = 0; tx < KT; ++tx) v[tx] = p[r * nc + tx];
+            T sx = x.w[0] * v[0];
+#pragma unroll
+            for (int tx = 1; tx < KT; ++tx) sx += x.w[tx] * v[tx];
+            h[r] = sx;
+          }
+        }
+        if (d == 0) pair_sums<T, KT, 0>(h, y0, y1, acc0, acc1);
+        else if (d == 1) pair_sums<T, KT, 1>(h, y0, y1, acc0, acc1);
+        else pair_sums<T, KT, 2>(h, y0, y1, acc0, acc1);
+      } else {
+        if (y0.off >= 0) acc0 += window_sum<T, KT, true>(st.vs + y0.off + x.off, nc, x, y0);
+        if (y1.off >= 0) acc1 += window_sum<T, KT, true>(st.vs + y1.off + x.off, nc, x, y1);
+      }
     }
-    A[node] = acc;
+    A[k0 * N + col] = acc0;
+    A[(k0 + 1) * N + col] = acc1;
   }
   if (I.n_edge_wfs == 0) return;
   __syncthreads();
@@ -853,9 +897,27 @@ __global__ void __launch_bounds__(kSynthThreads, 1) k_synthesis(const InstDev *_
         for (int idx = tid; idx < HJ * HJ; idx += nt) cb[idx] = cache[cm.coarse(idx >> lgHJ, idx & (HJ - 1))];
       }
       __syncthreads();
+      // rows first (x), then columns (y), as at the distributed levels and in
+      // the streamed transforms, so every path gives the same bits
       const T *c3 = cache + cm.coarse(0, 0);
       for (int k = J; k > kd; --k) {
         const int M = N >> (k - 1), H = M >> 1, lgMc = __ffs(M) - 1;
+        // row r < H: [LL | HL] of low-y row r; r >= H: [LH | HH] of high-y row r - H
+        for (int idx = tid; idx < M * M; idx += nt) {
+          const int r = idx >> lgMc, j = idx & (M - 1);
+          const int q = j & 1;
+          T acc = T(0);
+#pragma unroll
+          for (int s = 0; s < LF / 2; ++s) {
+            const int t = q + 2 * s;
+            const int jj = ((j - t) & (M - 1)) >> 1;
+            const T lo = r < H ? cb[r * H + jj] : c3[r * C + jj];
+            const T hi = c3[r * C + H + jj];
+            acc += f.hs(q, s) * lo + f.gs(q, s) * hi;
+          }
+          cb2[r * M + j] = acc;
+        }
+        __syncthreads();
         for (int idx = tid; idx < M * M; idx += nt) {
           const int y = idx >> lgMc, x = idx & (M - 1);
           const int p = y & 1;
@@ -864,24 +926,9 @@ __global__ void __launch_bounds__(kSynthThreads, 1) k_synthesis(const InstDev *_
           for (int s = 0; s < LF / 2; ++s) {
             const int t = p + 2 * s;
             const int ii = ((y - t) & (M - 1)) >> 1;
-            const T lo = x < H ? cb[ii * H + x] : c3[ii * C + x];
-            const T hi = c3[(H + ii) * C + x];
-            acc += f.hs(p, s) * lo + f.gs(p, s) * hi;
+            acc += f.hs(p, s) * cb2[ii * M + x] + f.gs(p, s) * cb2[(H + ii) * M + x];
           }
-          cb2[y * M + x] = acc;
-        }
-        __syncthreads();
-        for (int idx = tid; idx < M * M; idx += nt) {
-          const int y = idx >> lgMc, j = idx & (M - 1);
-          const int q = j & 1;
-          T acc = T(0);
-#pragma unroll
-          for (int s = 0; s < LF / 2; ++s) {
-            const int t = q + 2 * s;
-            const int jj = ((j - t) & (M - 1)) >> 1;
-            acc += f.hs(q, s) * cb2[y * M + jj] + f.gs(q, s) * cb2[y * M + H + jj];
-          }
-          cb[y * M + j] = acc;
+          cb[y * M + x] = acc;
         }
         __syncthreads();
       }

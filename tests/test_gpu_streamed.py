@@ -139,3 +139,36 @@ def test_streamed_batch_is_bitwise_single_and_close_to_clusters(lib):
         pc.close()
     for p in plans:
         p.close()
+
+
+@pytest.mark.parametrize("name", ["eelt", "one-pass-128", "elongated-32", "one-pass-128-fp64"])
+def test_cluster_and_streamed_paths_are_bitwise_the_same(lib, name):
+    """Two independent implementations of every operator: thread-block clusters
+    with the gather fused into the analysis (tables staged in shared memory), and
+    streamed row-tile passes with the separate gather kernel.  They take every
+    output's sums in the same order, so W, W^-1, the normal operator and the
+    right-hand side agree bit for bit, FP32 and FP64, with elongated spots."""
+    torch, pkg = lib
+    g = {"eelt": configs.config1,
+         "one-pass-128": CASES["one-pass-128"],
+         "elongated-32": lambda: configs.with_elongation(configs.small_lgs_config(16, 32, 3, 2),
+                                                         spot_fwhm_arcsec=0.5),
+         "one-pass-128-fp64": CASES["one-pass-128-fp64"]}[name]()
+    dt = torch.float64 if g["precision"] else torch.float32
+    outs = []
+    for tf in (1, 2):
+        p = pkg.Plan(g, transforms=tf)
+        assert (p.info.streamed, p.info.gather_separate) == ((0, 0) if tf == 1 else (1, 1))
+        rng = np.random.default_rng(27)
+        c = torch.tensor(rng.standard_normal(p.n), dtype=dt, device="cuda")
+        s = torch.tensor(rng.standard_normal(p.n_slopes), dtype=dt, device="cuda")
+        res = [torch.empty(p.n, dtype=dt, device="cuda") for _ in range(4)]
+        p.coeffs_to_layers(c, res[0])
+        p.layers_to_coeffs(c, res[1])
+        p.apply_normal(c, res[2])
+        p.rhs(s, res[3])
+        torch.cuda.synchronize()
+        outs.append(res)
+        p.close()
+    for what, a, b in zip(("synthesis", "analysis", "normal", "rhs"), outs[0], outs[1]):
+        assert torch.equal(a, b), what
