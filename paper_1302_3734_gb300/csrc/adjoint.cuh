@@ -208,28 +208,31 @@ __device__ __forceinline__ T window_sum(const T *__restrict__ p, int nc, const T
 // matters when the lists are in global memory) and summed in list order.
 constexpr int kEdgeBatch = 4;
 
+// The pupil-edge sum of one node over its entries [e0, e1), in list order.
+template <typename T>
+__device__ __forceinline__ T edge_node_sum(int e0, int e1, const int *tk, const T *tw, const T *s_coef) {
+  T acc = T(0);
+  for (int b = e0; b < e1; b += kEdgeBatch) {
+    int k[kEdgeBatch];
+    T wx[kEdgeBatch], wy[kEdgeBatch];
+#pragma unroll
+    for (int u = 0; u < kEdgeBatch; ++u) {
+      const int e = b + u < e1 ? b + u : b;
+      k[u] = tk[e];
+      wx[u] = tw[2 * e];
+      wy[u] = tw[2 * e + 1];
+    }
+#pragma unroll
+    for (int u = 0; u < kEdgeBatch; ++u)
+      if (b + u < e1) acc += s_coef[2 * k[u]] * wx[u] + s_coef[2 * k[u] + 1] * wy[u];
+  }
+  return acc;
+}
+
 template <typename T>
 __device__ __forceinline__ void gather_edges(int nn, const int *tn, const int *tb, const int *tk,
                                              const T *tw, T *A, const T *s_coef) {
-  for (int j = threadIdx.x; j < nn; j += blockDim.x) {
-    T acc = T(0);
-    const int e1 = tb[j + 1];
-    for (int e0 = tb[j]; e0 < e1; e0 += kEdgeBatch) {
-      int k[kEdgeBatch];
-      T wx[kEdgeBatch], wy[kEdgeBatch];
-#pragma unroll
-      for (int u = 0; u < kEdgeBatch; ++u) {
-        const int e = e0 + u < e1 ? e0 + u : e0;
-        k[u] = tk[e];
-        wx[u] = tw[2 * e];
-        wy[u] = tw[2 * e + 1];
-      }
-#pragma unroll
-      for (int u = 0; u < kEdgeBatch; ++u)
-        if (e0 + u < e1) acc += s_coef[2 * k[u]] * wx[u] + s_coef[2 * k[u] + 1] * wy[u];
-    }
-    A[tn[j]] += acc;
-  }
+  for (int j = threadIdx.x; j < nn; j += blockDim.x) A[tn[j]] += edge_node_sum<T>(tb[j], tb[j + 1], tk, tw, s_coef);
 }
 
 }  // namespace tomo

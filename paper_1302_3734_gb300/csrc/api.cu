@@ -681,7 +681,6 @@ tomo_status tomo_plan_create_ex(const tomo_geometry *g, const tomo_plan_options 
   I.n_edge_wfs = H.n_edge_wfs;
   I.gather_staged = H.gather_staged;
   I.n_dense = H.n_dense;
-  I.max_tt_nodes = H.max_tt_nodes;
   I.max_tt_entries = H.max_tt_entries;
   I.max_taps = H.max_taps;
   I.rec_stride = H.rec_stride;

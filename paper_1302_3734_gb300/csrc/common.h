@@ -145,7 +145,7 @@ struct InstDev {
   // (loaded before the dependency wait); 0 = read them from global memory.
   int gather_staged, n_dense;   // flag; sensors with a dense corner field
   int max_taps, rec_stride;     // taps per window (2..4); T words per tap record (4 or 8)
-  int max_tt_nodes, max_tt_entries;  // largest per-CTA pupil-edge segment
+  int max_tt_entries;           // largest per-CTA pupil-edge segment (entries)
   const int *edge_idx;          // corner index of each edge corner
   const void *edge_t;           // (t_x, t_y) of each edge corner (T, interleaved)
   const int *run_rows;          // per sensor (n+1): start of row b's runs in run_ab
@@ -213,14 +213,14 @@ TOMO_HD inline int transform_cache_size(int N, int C, int J, int kc) {
 // the plan (per dense sensor N column and R0 row tap records, the latter with
 // their window start in the staged v rows; the CTA's pupil-edge weights; the
 // sensors' nc; the v run prefix and sources; each sensor's edge slot when its
-// corner field takes the elongation correction, else -1; the pupil-edge nodes,
-// entry starts and slots; the node count), then the corner rows of v the CTA
-// reads.
+// corner field takes the elongation correction, else -1; the pupil-edge entry
+// slots; per node of the CTA (R0 N of them, then one more) the index of its
+// first pupil-edge entry, 16-bit), then the corner rows of v the CTA reads.
 struct StageLayout {
-  int xr, yr, tw, mnc, vpre, vsrc, mslot, tn, tb, tk, nn, image, vs, total;
+  int xr, yr, tw, mnc, vpre, vsrc, mslot, tk, eb, image, vs, total;
 };
-TOMO_HD inline StageLayout stage_layout(int n_dense, int N, int R0, int rec_stride, int esz,
-                                        int max_nodes, int max_entries, int vstage) {
+TOMO_HD inline StageLayout stage_layout(int n_dense, int N, int R0, int rec_stride, int esz, int max_entries,
+                                        int vstage) {
   StageLayout L;
   L.xr = 0;
   L.yr = L.xr + n_dense * N * rec_stride * esz;
@@ -229,11 +229,9 @@ TOMO_HD inline StageLayout stage_layout(int n_dense, int N, int R0, int rec_stri
   L.vpre = L.mnc + 4 * n_dense;
   L.vsrc = L.vpre + 4 * (n_dense + 1);
   L.mslot = L.vsrc + 4 * n_dense;
-  L.tn = L.mslot + 4 * n_dense;
-  L.tb = L.tn + 4 * max_nodes;
-  L.tk = L.tb + 4 * (max_nodes + 1);
-  L.nn = L.tk + 4 * max_entries;
-  L.image = (L.nn + 4 + 15) / 16 * 16;
+  L.tk = L.mslot + 4 * n_dense;
+  L.eb = L.tk + 4 * max_entries;
+  L.image = (L.eb + 2 * (R0 * N + 1) + 15) / 16 * 16;
   L.vs = L.image;
   L.total = L.vs + vstage * esz;
   return L;

@@ -605,7 +605,6 @@ tomo_status build_host_plan(const tomo_geometry *geo, HostPlan *P, std::string *
   P->n_dense = 0;
   for (const auto &d : P->wfs) P->n_dense += d.kind != kTTOnly ? 1 : 0;
   for (const auto &sg : P->tt_seg) {
-    P->max_tt_nodes = std::max(P->max_tt_nodes, sg.y - sg.x);
     P->max_tt_entries = std::max(P->max_tt_entries, P->tt_beg[sg.y] - P->tt_beg[sg.x]);
   }
   // Corner rows of v that each analysis CTA's gather reads: per (layer, rank,
@@ -661,13 +660,14 @@ tomo_status build_host_plan(const tomo_geometry *geo, HostPlan *P, std::string *
     for (const auto &d : P->layers) {
       const long long tr = (transform_cache_offset(d.N, P->C) +
                             transform_cache_size(d.N, P->C, J, d.cache_kc)) * static_cast<long long>(esz);
-      const StageLayout sl = stage_layout(P->n_dense, d.N, d.N / P->C, P->rec_stride, esz,
-                                          P->max_tt_nodes, P->max_tt_entries, P->vstage);
+      const StageLayout sl = stage_layout(P->n_dense, d.N, d.N / P->C, P->rec_stride, esz, P->max_tt_entries,
+                                          P->vstage);
       const long long st = (tr + 15) / 16 * 16 + sl.total;
       fits = fits && st <= budget;
       need = std::max(need, st);
     }
     fits = fits && !P->stream_tf;   // streamed transforms take the gather from its own kernel
+    fits = fits && P->max_tt_entries <= 65535;   // the image's 16-bit entry indices
     P->gather_staged = fits ? 1 : 0;
     P->smem_analysis = fits ? need : P->smem_transform;
     // the separate gather kernel: the band buffer (N/C rows of N), the band's row
@@ -696,8 +696,8 @@ tomo_status build_host_plan(const tomo_geometry *geo, HostPlan *P, std::string *
     const int esz = P->precision ? 8 : 4, RS = P->rec_stride;
     long long stride = 16;
     for (const auto &d : P->layers)
-      stride = std::max<long long>(stride, stage_layout(P->n_dense, d.N, d.N / P->C, RS, esz,
-                                                        P->max_tt_nodes, P->max_tt_entries, P->vstage).image);
+      stride = std::max<long long>(stride, stage_layout(P->n_dense, d.N, d.N / P->C, RS, esz, P->max_tt_entries,
+                                                        P->vstage).image);
     P->img_stride = stride;
     P->stage_img.assign(static_cast<size_t>(stride) * P->n_layers * P->C, 0);
     auto put_real = [&](unsigned char *dst, double v) {
@@ -711,8 +711,7 @@ tomo_status build_host_plan(const tomo_geometry *geo, HostPlan *P, std::string *
     auto put_int = [&](unsigned char *dst, int v) { std::memcpy(dst, &v, 4); };
     for (int l = 0; l < P->n_layers; ++l) {
       const int N = P->layers[l].N, R0 = N / P->C;
-      const StageLayout sl = stage_layout(P->n_dense, N, R0, RS, esz, P->max_tt_nodes,
-                                          P->max_tt_entries, P->vstage);
+      const StageLayout sl = stage_layout(P->n_dense, N, R0, RS, esz, P->max_tt_entries, P->vstage);
       for (int c = 0; c < P->C; ++c) {
         unsigned char *img = P->stage_img.data() + static_cast<size_t>(stride) * (l * P->C + c);
         int md = 0, vpre = 0;
@@ -742,14 +741,17 @@ tomo_status build_host_plan(const tomo_geometry *geo, HostPlan *P, std::string *
         put_int(img + sl.vpre + 4 * md, vpre);
         const int2 seg = P->tt_seg[l * P->C + c];
         const int nn = seg.y - seg.x, e0 = P->tt_beg[seg.x], ne = P->tt_beg[seg.y] - e0;
-        for (int j = 0; j < nn; ++j) put_int(img + sl.tn + 4 * j, P->tt_node[seg.x + j]);
-        for (int j = 0; j <= nn; ++j) put_int(img + sl.tb + 4 * j, P->tt_beg[seg.x + j] - e0);
         for (int e = 0; e < ne; ++e) {
           put_int(img + sl.tk + 4 * e, P->tt_k[e0 + e]);
           put_real(img + sl.tw + esz * (2 * e), P->tt_w[2 * (e0 + e)]);
           put_real(img + sl.tw + esz * (2 * e + 1), P->tt_w[2 * (e0 + e) + 1]);
         }
-        put_int(img + sl.nn, nn);
+        // per node the index of its first entry (the entries are sorted by node)
+        for (int node = 0, j = 0; node <= R0 * N; ++node) {
+          while (j < nn && P->tt_node[seg.x + j] < node) ++j;
+          const uint16_t first = static_cast<uint16_t>(P->tt_beg[seg.x + j] - e0);
+          std::memcpy(img + sl.eb + 2 * node, &first, 2);
+        }
       }
     }
   }

@@ -21,7 +21,7 @@ struct HostPlan {
   int n_lgs = 0;
   long long smem_transform = 0;   // dynamic shared memory of the synthesis kernel (bytes)
   long long smem_analysis = 0;    // dynamic shared memory of the gather + analysis kernel (bytes)
-  int gather_staged = 0, n_dense = 0, max_tt_nodes = 0, max_tt_entries = 0, max_taps = 0,
+  int gather_staged = 0, n_dense = 0, max_tt_entries = 0, max_taps = 0,
       rec_stride = 0;
   std::vector<double> h, g;
   std::vector<LayerDev> layers;

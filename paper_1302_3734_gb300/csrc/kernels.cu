@@ -387,12 +387,13 @@ template <typename T>
 struct GatherStage {
   unsigned char *base;
   T *xr, *yr, *vs, *tw;
-  int *mnc, *vpre, *vsrc, *mslot, *tn, *tb, *tk, *pnn;
+  int *mnc, *vpre, *vsrc, *mslot, *tk;
+  const uint16_t *eb;
   int image_bytes;
 
   __device__ void carve(unsigned char *b, int Md, int N, int R0, const InstDev &I) {
-    const StageLayout sl = stage_layout(Md, N, R0, I.rec_stride, static_cast<int>(sizeof(T)),
-                                        I.max_tt_nodes, I.max_tt_entries, I.vstage);
+    const StageLayout sl = stage_layout(Md, N, R0, I.rec_stride, static_cast<int>(sizeof(T)), I.max_tt_entries,
+                                        I.vstage);
     base = b;
     xr = reinterpret_cast<T *>(b + sl.xr);
     yr = reinterpret_cast<T *>(b + sl.yr);
@@ -402,10 +403,8 @@ struct GatherStage {
     vpre = reinterpret_cast<int *>(b + sl.vpre);
     vsrc = reinterpret_cast<int *>(b + sl.vsrc);
     mslot = reinterpret_cast<int *>(b + sl.mslot);
-    tn = reinterpret_cast<int *>(b + sl.tn);
-    tb = reinterpret_cast<int *>(b + sl.tb);
     tk = reinterpret_cast<int *>(b + sl.tk);
-    pnn = reinterpret_cast<int *>(b + sl.nn);
+    eb = reinterpret_cast<const uint16_t *>(b + sl.eb);
     image_bytes = sl.image;
   }
 
@@ -418,8 +417,6 @@ struct GatherStage {
     for (int j = threadIdx.x; j < image_bytes / 16; j += blockDim.x) cp_async16(dst + j, src + j);
     cp_async_commit();
   }
-
-  __device__ int nn() const { return *pnn; }
 
   // Spot elongation with tip/tilt removal: v += m_x Gx + m_y Gy over the staged
   // corner rows of those sensors (the mean slopes from edge_coefficients).
@@ -511,12 +508,16 @@ __device__ void gather_rows_staged(const InstDev &I, const GatherStage<T> &st, i
         if (y1.off >= 0) acc1 += window_sum<T, KT, true>(st.vs + y1.off + x.off, nc, x, y1);
       }
     }
+    if (I.n_edge_wfs > 0) {
+      // the nodes' pupil-edge entries (from the dense per-node index), added after the sensors
+      const int n0 = k0 * N + col, n1 = n0 + N;
+      const int e0 = st.eb[n0], e1 = st.eb[n0 + 1], e2 = st.eb[n1], e3 = st.eb[n1 + 1];
+      if (e1 > e0) acc0 += edge_node_sum<T>(e0, e1, st.tk, st.tw, s_coef);
+      if (e3 > e2) acc1 += edge_node_sum<T>(e2, e3, st.tk, st.tw, s_coef);
+    }
     A[k0 * N + col] = acc0;
     A[(k0 + 1) * N + col] = acc1;
   }
-  if (I.n_edge_wfs == 0) return;
-  __syncthreads();
-  gather_edges<T>(st.nn(), st.tn, st.tb, st.tk, st.tw, A, s_coef);
 }
 
 // ------------------------------------------------------------ k_analysis
