@@ -104,8 +104,12 @@ __host__ __device__ constexpr size_t fwd_table_bytes(int L, size_t esz) {
   return ((sizeof(int) * (2 * L + 2 * L * kHalo) + 15) & ~size_t(15)) + 2 * L * kHalo * esz;
 }
 
-template <typename T, int MODE, bool EL>
-__global__ void __launch_bounds__(kFwdThreads) k_forward(const InstDev *__restrict__ insts,
+// NT: the block size the instance is compiled for: kFwdThreads for small
+// launches, kThreads with kFwdBatchBlocks CTAs per SM (fewer registers) for big ones.
+constexpr int kFwdBatchBlocks = 5;
+
+template <typename T, int MODE, bool EL, int NT>
+__global__ void __launch_bounds__(NT, NT == kFwdThreads ? 1 : kFwdBatchBlocks) k_forward(const InstDev *__restrict__ insts,
                                                      const FwdItem *__restrict__ items, IoArgs io) {
   extern __shared__ __align__(16) unsigned char fsm[];
   __shared__ InstDev sI;
@@ -1330,13 +1334,19 @@ cudaError_t allow_type() {
   if (e == cudaSuccess) e = allow_lf<T, 4>();
   if (e == cudaSuccess) e = allow_lf<T, 6>();
   if (e == cudaSuccess) e = allow_lf<T, 8>();
-  const void *fwd[6] = {reinterpret_cast<const void *>(k_forward<T, 0, false>),
-                        reinterpret_cast<const void *>(k_forward<T, 1, false>),
-                        reinterpret_cast<const void *>(k_forward<T, 2, false>),
-                        reinterpret_cast<const void *>(k_forward<T, 0, true>),
-                        reinterpret_cast<const void *>(k_forward<T, 1, true>),
-                        reinterpret_cast<const void *>(k_forward<T, 2, true>)};
-  for (int i = 0; i < 6 && e == cudaSuccess; ++i)
+  const void *fwd[12] = {reinterpret_cast<const void *>(k_forward<T, 0, false, kFwdThreads>),
+                         reinterpret_cast<const void *>(k_forward<T, 1, false, kFwdThreads>),
+                         reinterpret_cast<const void *>(k_forward<T, 2, false, kFwdThreads>),
+                         reinterpret_cast<const void *>(k_forward<T, 0, true, kFwdThreads>),
+                         reinterpret_cast<const void *>(k_forward<T, 1, true, kFwdThreads>),
+                         reinterpret_cast<const void *>(k_forward<T, 2, true, kFwdThreads>),
+                         reinterpret_cast<const void *>(k_forward<T, 0, false, kThreads>),
+                         reinterpret_cast<const void *>(k_forward<T, 1, false, kThreads>),
+                         reinterpret_cast<const void *>(k_forward<T, 2, false, kThreads>),
+                         reinterpret_cast<const void *>(k_forward<T, 0, true, kThreads>),
+                         reinterpret_cast<const void *>(k_forward<T, 1, true, kThreads>),
+                         reinterpret_cast<const void *>(k_forward<T, 2, true, kThreads>)};
+  for (int i = 0; i < 12 && e == cudaSuccess; ++i)
     e = cudaFuncSetAttribute(fwd[i], cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxForwardSmem);
   return e;
 }
@@ -1425,12 +1435,19 @@ cudaError_t launch_analysis(int precision, int src, int epi, int lf, int flags, 
                         : anal_t<double>(src, epi, lf, flags, insts, items, n_clusters, C, smem, io, s);
 }
 
+template <typename T, bool EL, int NT>
+cudaError_t fwd_nt(int mode, dim3 g, size_t sm, cudaStream_t s, const InstDev *insts, const FwdItem *items,
+                   const IoArgs &io) {
+  if (mode == 0) return launch_ex(k_forward<T, 0, EL, NT>, g, NT, 0, sm, s, insts, items, io);
+  if (mode == 1) return launch_ex(k_forward<T, 1, EL, NT>, g, NT, 0, sm, s, insts, items, io);
+  return launch_ex(k_forward<T, 2, EL, NT>, g, NT, 0, sm, s, insts, items, io);
+}
+
 template <typename T, bool EL>
 cudaError_t fwd_t(int mode, dim3 g, int nt, size_t sm, cudaStream_t s, const InstDev *insts,
                   const FwdItem *items, const IoArgs &io) {
-  if (mode == 0) return launch_ex(k_forward<T, 0, EL>, g, nt, 0, sm, s, insts, items, io);
-  if (mode == 1) return launch_ex(k_forward<T, 1, EL>, g, nt, 0, sm, s, insts, items, io);
-  return launch_ex(k_forward<T, 2, EL>, g, nt, 0, sm, s, insts, items, io);
+  return nt == kFwdThreads ? fwd_nt<T, EL, kFwdThreads>(mode, g, sm, s, insts, items, io)
+                           : fwd_nt<T, EL, kThreads>(mode, g, sm, s, insts, items, io);
 }
 
 cudaError_t launch_forward(int precision, int mode, int max_layers, int elong, const InstDev *insts,
