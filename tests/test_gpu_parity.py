@@ -151,6 +151,10 @@ def test_jacobi_diagonal(case):
     out = case.torch.empty(case.ora.n, dtype=case.torch.float64, device="cuda")
     case.plan.jacobi_diagonal(out)
     assert rel(case.host(out), case.ora.jacobi_diagonal(), f"jacobi/{case.geom['name']}") < 1e-12
+    if case.ora.n <= 3072:
+        # and against the diagonal's definition, one unit vector at a time (not the
+        # oracle's separable-profile route, whose idea the kernel shares)
+        assert rel(case.host(out), case.ora.jacobi_diagonal_probe(), f"jacobi-def/{case.geom['name']}") < 1e-12
 
 
 def _frame(case, seed=7):
