@@ -104,13 +104,14 @@ __host__ __device__ constexpr size_t fwd_table_bytes(int L, size_t esz) {
   return ((sizeof(int) * (2 * L + 2 * L * kHalo) + 15) & ~size_t(15)) + 2 * L * kHalo * esz;
 }
 
-// NT: the block size the instance is compiled for: kFwdThreads for small
-// launches, kThreads with kFwdBatchBlocks CTAs per SM (fewer registers) for big ones.
+// NT: the block size the instance is compiled for: kFwdThreads with two CTAs
+// per SM for small launches, kThreads with kFwdBatchBlocks CTAs per SM (fewer
+// registers) for big ones (FP32; FP64 instances keep the registers they need).
 constexpr int kFwdBatchBlocks = 5;
 
 template <typename T, int MODE, bool EL, int NT>
-__global__ void __launch_bounds__(NT, NT == kFwdThreads ? 1 : kFwdBatchBlocks) k_forward(const InstDev *__restrict__ insts,
-                                                     const FwdItem *__restrict__ items, IoArgs io) {
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (NT == kFwdThreads ? 2 : kFwdBatchBlocks) : 1)
+    k_forward(const InstDev *__restrict__ insts, const FwdItem *__restrict__ items, IoArgs io) {
   extern __shared__ __align__(16) unsigned char fsm[];
   __shared__ InstDev sI;
   __shared__ T s_psi[kHalo][kHalo + 1];
