@@ -55,9 +55,10 @@ def lib():
     return torch, pkg
 
 
-def _serve(pkg, geoms, frames, **kw):
+def _serve(pkg, geoms, frames, shape=None, **kw):
     srv = pkg.Server(iters=ITERS, result_slots=len(frames[0]) + 1, queue_depth=len(frames[0]) + 1, **kw)
-    ids = [srv.admit(g) for g in geoms]
+    ids = [srv.admit(g) if shape is None else srv.admit(g, cluster_size=shape[0], transforms=shape[1])
+           for g in geoms]
     # interleaved arrivals, as several telescopes emit frames at the same rate
     for k in range(len(frames[0])):
         for i, tid in enumerate(ids):
@@ -76,17 +77,21 @@ def _serve(pkg, geoms, frames, **kw):
     return got, res, stats
 
 
-def test_served_frames_are_bitwise_the_frames_solved_alone(lib):
+@pytest.mark.parametrize("shape", [None, (4, 2)], ids=["default", "C4-streamed"])
+def test_served_frames_are_bitwise_the_frames_solved_alone(lib, shape):
+    """Every served frame equals the same frame solved alone by a plan of the same
+    launch shape: the default shapes, and the streamed transforms at cluster size 4
+    that the served benchmark's autotuner picks."""
     torch, pkg = lib
     geoms = _geoms()
     K = 5
     data = [_frames(g, K, i) for i, g in enumerate(geoms)]
     frames = [d[1] for d in data]
-    got, res, stats = _serve(pkg, geoms, frames, max_in_flight=2)
+    got, res, stats = _serve(pkg, geoms, frames, shape=shape, max_in_flight=2)
     assert stats["frames_done"] == K * len(geoms)
     assert max(r["batch_size"] for r in res) > 1, "frames of different telescopes never shared a launch"
     for i, g in enumerate(geoms):
-        plan = pkg.Plan(g)
+        plan = pkg.Plan(g) if shape is None else pkg.Plan(g, cluster_size=shape[0], transforms=shape[1])
         x = torch.zeros(plan.n, dtype=torch.float32, device="cuda")
         for k in range(K):
             s = torch.tensor(frames[i][k], device="cuda")
