@@ -25,12 +25,13 @@ namespace tomo {
 // sensors' terms in sensor order, as the fused gathers do.  For plans whose
 // tables do not fit the analysis CTAs' shared memory; k_gather runs it.
 // VS: the band rows of v that pass 1 reads are copied to shared memory V first
-// (cp.async; the next sensor's copy runs during pass 2 of the current one);
-// otherwise pass 1 reads them from global memory.
+// (one bulk copy per sensor on the mbarrier bar, phase md for sensor md; the
+// next sensor's copy runs during pass 2 of the current one); otherwise pass 1
+// reads them from global memory.
 constexpr int kGatherRowsU = 4;   // corner rows of a column one thread forms at once in pass 1
 
 template <typename T, int KT, bool VS>
-__device__ void gather_band_global(const InstDev &I, int l, int N, int R0, int crank, T *A, T *U, T *V,
+__device__ void gather_band_global(const InstDev &I, int l, int N, int R0, int crank, T *A, T *U, T *V, uint64_t *bar,
                                    const T *s_coef, const int *s_go, const int *s_nc, const int *s_el,
                                    const int2 *s_cols, const int2 *s_br, int *s_ry, T *s_rw, int Md) {
   constexpr int RS = TapRec<T, KT>::RS;
@@ -38,27 +39,30 @@ __device__ void gather_band_global(const InstDev &I, int l, int N, int R0, int c
   const int nt = blockDim.x, tid = threadIdx.x;
   const T *vv = static_cast<const T *>(I.v);
   const T *rec = static_cast<const T *>(I.gt_rec);
-  // the copy of sensor md's band rows [br.x, br.x + nb nc) of v, and KT more
-  // elements (zero-weight taps when nc < KT), from the 16-byte boundary at or
-  // below br.x (the plan pads v beyond its last sensor)
+  // one thread: the bulk copy of sensor md's band rows [br.x, br.x + nb nc) of
+  // v, and KT more elements (zero-weight taps when nc < KT), from the 16-byte
+  // boundary at or below br.x (the plan pads v beyond its last sensor)
   auto stage = [&](int md) {
     const int2 br = s_br[md];
     const int g0 = br.x / vq * vq;
     const int nq = (br.x - g0 + br.y * s_nc[md] + KT + vq - 1) / vq;
-    const uint4 *src = reinterpret_cast<const uint4 *>(vv + g0);
-    uint4 *dst = reinterpret_cast<uint4 *>(V);
-    for (int j = tid; j < nq; j += nt) cp_async16(dst + j, src + j);
-    cp_async_commit();
+    mbar_arm(bar, static_cast<uint32_t>(nq) * 16u);
+    bulk_copy_g2s(V, vv + g0, static_cast<uint32_t>(nq) * 16u, bar);
   };
   for (int node = tid; node < R0 * N; node += nt) A[node] = T(0);
   if constexpr (VS) {
-    if (Md > 0) stage(0);
+    if (tid == 0 && Md > 0) {
+      fence_async_global();   // v was written by the previous kernel
+      stage(0);
+    }
   }
   // (every listed sensor reaches the band: nonempty columns and corner rows)
   for (int md = 0; md < Md; ++md) {
     if constexpr (VS) {
-      cp_async_wait_all();   // this thread's copies of sensor md
-      __syncthreads();       // everyone's; pass 2 of the previous sensor is done with U
+      // sensor md's rows; a copy that never completed (it does not happen with
+      // valid tables) makes the solve report a breakdown
+      if (!mbar_wait(bar, md & 1)) I.scal[kFlag] = 1.0;
+      __syncthreads();   // pass 2 of the previous sensor is done with U
     }
     const int2 cols = s_cols[md], br = s_br[md];
     const int ncol = cols.y, nb = br.y, nc = s_nc[md], el = s_el[md];
@@ -122,7 +126,7 @@ __device__ void gather_band_global(const InstDev &I, int l, int N, int R0, int c
     }
     __syncthreads();
     if constexpr (VS) {
-      if (md + 1 < Md) stage(md + 1);   // V is free: pass 1 is done
+      if (tid == 0 && md + 1 < Md) stage(md + 1);   // V is free: pass 1 is done
     }
     // pass 2: the band's node rows from U
     for (int c = ci; c < ncol; c += tpr) {
@@ -165,6 +169,7 @@ __global__ void __launch_bounds__(kGatherThreads, sizeof(T) == 4 ? 2 : 1) k_gath
   __shared__ int s_go[kMaxGatherSensors], s_nc[kMaxGatherSensors], s_el[kMaxGatherSensors];
   __shared__ int2 s_cols[kMaxGatherSensors], s_br[kMaxGatherSensors];
   __shared__ int s_md;
+  __shared__ uint64_t s_bar;   // the staged corner rows (VS)
   pdl_trigger();
   const PassItem it = items[blockIdx.x];
   const int crank = it.row0;
@@ -188,6 +193,7 @@ __global__ void __launch_bounds__(kGatherThreads, sizeof(T) == 4 ? 2 : 1) k_gath
       ++md;
     }
     s_md = md;
+    if (VS) mbar_init(&s_bar);
   }
   const LayerDev &L = I.layers[it.layer];
   const int N = L.N, R0 = N / C;
@@ -205,8 +211,8 @@ __global__ void __launch_bounds__(kGatherThreads, sizeof(T) == 4 ? 2 : 1) k_gath
   T *s_rw = reinterpret_cast<T *>(smem_raw + gs.rw);
   T *U = reinterpret_cast<T *>(smem_raw + gs.u);
   T *V = reinterpret_cast<T *>(smem_raw + gs.v);
-#define TOMO_GB(KT) gather_band_global<T, KT, VS>(I, it.layer, N, R0, crank, A, U, V, s_coef, s_go, s_nc, s_el, \
-                                                  s_cols, s_br, s_ry, s_rw, s_md)
+#define TOMO_GB(KT) gather_band_global<T, KT, VS>(I, it.layer, N, R0, crank, A, U, V, &s_bar, s_coef, s_go, s_nc, \
+                                                  s_el, s_cols, s_br, s_ry, s_rw, s_md)
   if (I.max_taps <= 2) TOMO_GB(2);
   else if (I.max_taps == 3) TOMO_GB(3);
   else TOMO_GB(4);

@@ -413,14 +413,11 @@ struct GatherStage {
     image_bytes = sl.image;
   }
 
-  // Starts the copy of the CTA's stage image; cp_async_wait_all() and a
-  // barrier complete it.
-  __device__ void issue_image(const InstDev &I, int l, int crank) const {
-    const uint4 *src = reinterpret_cast<const uint4 *>(static_cast<const unsigned char *>(I.stage_img) +
-                                                       I.img_stride * (l * I.C + crank));
-    uint4 *dst = reinterpret_cast<uint4 *>(base);
-    for (int j = threadIdx.x; j < image_bytes / 16; j += blockDim.x) cp_async16(dst + j, src + j);
-    cp_async_commit();
+  // One thread: the bulk copy of the CTA's stage image, completing on bar.
+  __device__ void issue_image(const InstDev &I, int l, int crank, uint64_t *bar) const {
+    const unsigned char *src = static_cast<const unsigned char *>(I.stage_img) + I.img_stride * (l * I.C + crank);
+    mbar_arm(bar, static_cast<uint32_t>(image_bytes));
+    if (image_bytes > 0) bulk_copy_g2s(base, src, static_cast<uint32_t>(image_bytes), bar);
   }
 
   // Spot elongation with tip/tilt removal: v += m_x Gx + m_y Gy over the staged
@@ -437,19 +434,19 @@ struct GatherStage {
     }
   }
 
-  // Starts the asynchronous copy of the CTA's corner rows of v (written by
-  // the previous kernel) into shared memory; cp_async_wait_all() and a
-  // barrier complete it.  Needs fill() and a barrier first.
-  __device__ void load_v_async(const InstDev &I) const {
-    const int nt = blockDim.x, Md = I.n_dense, total = vpre[Md];
+  // One thread, after the dependency wait: the bulk copies of the CTA's
+  // corner rows of v (one aligned run per sensor, written by the previous
+  // kernel), completing on bar.  Needs the stage image in shared memory.
+  __device__ void load_v_bulk(const InstDev &I, uint64_t *bar) const {
+    const int Md = I.n_dense;
     const uint4 *src = static_cast<const uint4 *>(I.v);
     uint4 *dst = reinterpret_cast<uint4 *>(vs);
-    int md = 0;
-    for (int j = threadIdx.x; j < total; j += nt) {
-      while (md + 1 < Md && vpre[md + 1] <= j) ++md;
-      cp_async16(dst + j, src + vsrc[md] + j - vpre[md]);
+    fence_async_global();
+    mbar_arm(bar, static_cast<uint32_t>(vpre[Md]) * 16u);
+    for (int md = 0; md < Md; ++md) {
+      const int n = vpre[md + 1] - vpre[md];
+      if (n > 0) bulk_copy_g2s(dst + vpre[md], src + vsrc[md], static_cast<uint32_t>(n) * 16u, bar);
     }
-    cp_async_commit();
   }
 };
 
@@ -541,6 +538,7 @@ __global__ void __launch_bounds__(kAnalysisThreadsMax, 1) k_analysis(const InstD
   __shared__ CoefMap cm;
   __shared__ T s_coef[4 * kMaxEdgeSlots];
   __shared__ T s_dal[kMaxLevels + 1];
+  __shared__ uint64_t s_bar[2];   // stage image, corner rows of v (bulk copies)
   pdl_trigger();
   cg::cluster_group cluster = cg::this_cluster();
   const int C = static_cast<int>(cluster.num_blocks());
@@ -578,12 +576,18 @@ __global__ void __launch_bounds__(kAnalysisThreadsMax, 1) k_analysis(const InstD
   GatherStage<T> st;
   // SRC 1 plans stage their tables (those that cannot run k_gather, SRC 2)
   const bool staged = SRC == 1;
+  bool copies_ok = true;
   if (staged) {
     const int off = transform_cache_offset(N, C) + transform_cache_size(N, C, J, L.cache_kc);
     unsigned char *sb = smem_raw + ((static_cast<size_t>(off) * sizeof(T) + 15) & ~size_t(15));
     st.carve(sb, I.n_dense, N, R0, I);
-    st.issue_image(I, it.layer, crank);
-    cp_async_wait_all();
+    if (tid == 0) {
+      mbar_init(&s_bar[0]);
+      mbar_init(&s_bar[1]);
+      st.issue_image(I, it.layer, crank, &s_bar[0]);
+    }
+    __syncthreads();   // the barriers are initialised
+    copies_ok = mbar_wait(&s_bar[0], 0);
   }
   __syncthreads();
   pdl_wait();
@@ -593,7 +597,7 @@ __global__ void __launch_bounds__(kAnalysisThreadsMax, 1) k_analysis(const InstD
   // asynchronous copies: the gather's corner rows of v, then the epilogue
   // inputs (p, or x for a warm residual) of every owned coefficient into the
   // coefficient cache; both complete before the transform
-  if (staged) st.load_v_async(I);
+  if (staged && tid == 0) st.load_v_bulk(I, &s_bar[1]);
   const bool use_cache = (EPI == kEpiOp) || (EPI == kEpiResid && emit.warm);
   if (use_cache) {
     const T *srcv = EPI == kEpiOp ? emit.P : emit.X;
@@ -617,7 +621,10 @@ __global__ void __launch_bounds__(kAnalysisThreadsMax, 1) k_analysis(const InstD
     if (I.n_edge_wfs > 0)
       edge_coefficients<T>(I, s_coef, tt_mode, static_cast<const T *>(io.in1[it.inst]));
     if (staged) {
-      cp_async_wait_all();
+      copies_ok = mbar_wait(&s_bar[1], 0) && copies_ok;
+      // a copy that never completed (it does not happen with valid tables): the
+      // solve reports a breakdown and its iterate stays as it was
+      if (!copies_ok) I.scal[kFlag] = 1.0;
       __syncthreads();
       if (I.gel) {
         st.add_elongation(I, s_coef);
