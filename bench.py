@@ -44,8 +44,8 @@ METRIC = "tomography solves/s and p99 frame latency at 84x84 MCAO vs plain GPU P
 # DRAM bytes (read + write) per launch of each PCG kernel on this workload, from one ncu capture
 # with flushed caches, valid only for the kernel source file they were taken from.
 NCU_TRAFFIC = {
-    "kernels_cu_sha256": "cf56455d168f70a79e178003b81fb707d0a77afc495fb52ee7e5171359789427",
-    "bytes": {"analysis": 5126400, "synthesis": 1843072, "forward": 748928, "update": 2985216},
+    "kernels_cu_sha256": "e49932dafe182edea5d511924d14b1b5c22b3b7a74bf17cbbacb537110e9494d",
+    "bytes": {"analysis": 5138432, "synthesis": 1843072, "forward": 749312, "update": 2985344},
 }
 
 
