@@ -44,7 +44,7 @@ METRIC = "tomography solves/s and p99 frame latency at 84x84 MCAO vs plain GPU P
 # DRAM bytes (read + write) per launch of each PCG kernel on this workload, from one ncu capture
 # with flushed caches, valid only for the kernel source file they were taken from.
 NCU_TRAFFIC = {
-    "kernels_cu_sha256": "e49932dafe182edea5d511924d14b1b5c22b3b7a74bf17cbbacb537110e9494d",
+    "kernels_cu_sha256": "0bd9e8be5cd953990a77106764941dd3af385ff59b7a37c922c3bb820e0cbabd",
     "bytes": {"analysis": 5138432, "synthesis": 1843072, "forward": 749312, "update": 2985344},
 }
 

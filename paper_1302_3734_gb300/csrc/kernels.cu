@@ -385,9 +385,10 @@ struct CoefMap {
 
 // Shared-memory copy of the gather tables of one analysis CTA (layer l, rows
 // [k0, k0+R0)), laid out by stage_layout: the plan's stage image for the CTA
-// (tap records, pupil-edge segment, run tables), copied with cp.async before
+// (tap records, pupil-edge entries and index, run tables), one bulk copy before
 // the dependency wait since the tables are constant, so the copy overlaps the
-// previous kernel; after the wait, the corner rows of v that the CTA reads.
+// previous kernel; after the wait, the corner rows of v that the CTA reads,
+// one bulk copy per sensor.
 template <typename T>
 struct GatherStage {
   unsigned char *base;
