@@ -601,12 +601,17 @@ __global__ void __launch_bounds__(kAnalysisThreadsMax, 1) k_analysis(const InstD
   if (staged && tid == 0) st.load_v_bulk(I, &s_bar[1]);
   const bool use_cache = (EPI == kEpiOp) || (EPI == kEpiResid && emit.warm);
   if (use_cache) {
-    const T *srcv = EPI == kEpiOp ? emit.P : emit.X;
-    const int total = cm.total();
-    for (int q = tid; q < total; q += nt) {
-      int row, col;
-      cm.pos(q, row, col);
-      cp_async_elem(cache + q, srcv + L.off + row * N + col);
+    // issued by the warps that the pupil-edge coefficients below leave idle
+    // (one warp per edge slot), so the two overlap
+    const int w0 = SRC == 1 ? min(I.n_edge_wfs, nt / 32 - 1) : 0, t0 = tid - 32 * w0;
+    if (t0 >= 0) {
+      const T *srcv = EPI == kEpiOp ? emit.P : emit.X;
+      const int total = cm.total();
+      for (int q = t0; q < total; q += nt - 32 * w0) {
+        int row, col;
+        cm.pos(q, row, col);
+        cp_async_elem(cache + q, srcv + L.off + row * N + col);
+      }
     }
     cp_async_commit();
   }
