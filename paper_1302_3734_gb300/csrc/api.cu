@@ -638,6 +638,8 @@ tomo_status tomo_plan_create_ex(const tomo_geometry *g, const tomo_plan_options 
   for (int t = 0; t < kMaxTaps; ++t) {
     I.h[t] = t < H.Lf ? H.h[t] : 0.0;
     I.g[t] = t < H.Lf ? H.g[t] : 0.0;
+    I.hf[t] = static_cast<float>(I.h[t]);
+    I.gf[t] = static_cast<float>(I.g[t]);
   }
   I.r = base + o_r;
   I.p = base + o_p;

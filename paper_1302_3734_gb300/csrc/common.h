@@ -99,6 +99,10 @@ struct InstDev {
   int Lf, precond, C, n_slopes;
   int cl_part_off, upd_part_off, n_upd_blocks, fwd_part_off;
   double h[kMaxTaps], g[kMaxTaps];
+  // the same taps rounded to FP32 once on the host (round to nearest, as a
+  // device conversion would): FP32 kernels read these, so no thread spends the
+  // FP64 pipe, a small fraction of the FP32 rate on this GPU, converting them
+  float hf[kMaxTaps], gf[kMaxTaps];
   // workspace
   void *r, *p, *q, *phi, *v, *jinv;
   double *scal, *part;

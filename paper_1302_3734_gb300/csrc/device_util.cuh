@@ -156,20 +156,23 @@ static __device__ float4 block_sum2_df(Acc<float> a, Acc<float> b) {
   return make_float4(x.hi, x.lo, y.hi, y.lo);
 }
 
-// Fixed-order sum of `count` FP64 partial pairs (stride 2): warp 0 sums the
-// first of each pair and warp 1 the second (one of them does both in a
-// one-warp block); the result is returned to every thread.
-static __device__ double2 sum_partials(const double *part, int count) {
-  __shared__ double s_sp[2];
+// Fixed-order FP64 sum of component k of `count` partial pairs (stride 2),
+// valid in thread 0 only: warps 0..3 take the partials w*32 + lane, + 128, ...
+// (a block of fewer warps lets each take several of those four shares), each
+// share's lane tree, then thread 0 adds the four in order.  Only the first
+// four warps touch the FP64 pipe, a small fraction of the FP32 rate on this
+// GPU, and no component is summed that the caller does not use.
+static __device__ double sum_partial(const double *part, int count, int k) {
+  __shared__ double s_sp[4];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int k = w; k < 2; k += nw) {
+  for (int v = w; v < 4; v += nw) {
     double a = 0.0;
-    for (int q = lane; q < count; q += 32) a += part[2 * q + k];
+    for (int q = v * 32 + lane; q < count; q += 128) a += part[2 * q + k];
     a = warp_sum(a);
-    if (lane == 0) s_sp[k] = a;
+    if (lane == 0) s_sp[v] = a;
   }
   __syncthreads();
-  return make_double2(s_sp[0], s_sp[1]);
+  return threadIdx.x == 0 ? ((s_sp[0] + s_sp[1]) + s_sp[2]) + s_sp[3] : 0.0;
 }
 
 // Every hot-path launch allows programmatic dependent launch: the kernel's

@@ -825,16 +825,16 @@ __global__ void __launch_bounds__(kSynthThreads, 1) k_synthesis(const InstDev *_
     // r.z of this iteration; the first CTA of the instance records it
     const double prev = I.scal[kRz0 + ((iter + 1) & 1)];
     const double flag = I.scal[kFlag];
-    const double2 s = iter == 0 ? sum_partials(I.part + I.cl_part_off, I.n_cl_part)
-                                : sum_partials(I.part + I.upd_part_off, I.n_upd_blocks);
+    const double rz = iter == 0 ? sum_partial(I.part + I.cl_part_off, I.n_cl_part, 0)
+                                : sum_partial(I.part + I.upd_part_off, I.n_upd_blocks, 0);
     if (tid == 0) {
       double beta = 0.0;
       if (iter > 0) {
-        const bool stop = flag != 0.0 || !isfinite(s.x) || !(prev != 0.0);
-        beta = stop ? 0.0 : s.x / prev;
+        const bool stop = flag != 0.0 || !isfinite(rz) || !(prev != 0.0);
+        beta = stop ? 0.0 : rz / prev;
       }
       s_beta = T(beta);
-      if (it.layer == 0 && crank == 0) I.scal[kRz0 + (iter & 1)] = s.x;
+      if (it.layer == 0 && crank == 0) I.scal[kRz0 + (iter & 1)] = rz;
     }
   }
   __syncthreads();
@@ -1134,16 +1134,16 @@ __global__ void __launch_bounds__(kThreads) k_update(const InstDev *__restrict__
   {
     const double rz = I->scal[kRz0 + (iter & 1)];
     const double flag = I->scal[kFlag];
-    const double2 pq = sum_partials(I->part + I->cl_part_off, I->n_cl_part);
+    const double pq = sum_partial(I->part + I->cl_part_off, I->n_cl_part, 0);
     if (threadIdx.x == 0) {
       // r = 0 (so p = 0 and p.Ap = 0) means the iterate is already exact: step 0
-      const bool exact = (pq.x == 0.0 && rz == 0.0);
-      const bool bad = !exact && (!(pq.x > 0.0) || !isfinite(pq.x) || !isfinite(rz) || flag != 0.0);
+      const bool exact = (pq == 0.0 && rz == 0.0);
+      const bool bad = !exact && (!(pq > 0.0) || !isfinite(pq) || !isfinite(rz) || flag != 0.0);
       if (bad && it.blk == 0) {
         I->scal[kFlag] = 1.0;
         if (I->bd_word) *reinterpret_cast<volatile int *>(I->bd_word) = 1;
       }
-      s_alpha = T((bad || exact) ? 0.0 : rz / pq.x);
+      s_alpha = T((bad || exact) ? 0.0 : rz / pq);
     }
     __syncthreads();
   }

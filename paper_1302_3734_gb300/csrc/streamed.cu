@@ -267,16 +267,16 @@ __device__ __forceinline__ T streamed_beta(const InstDev &I, int iter, bool reco
   __shared__ T s_b;
   const double prev = I.scal[kRz0 + ((iter + 1) & 1)];
   const double flag = I.scal[kFlag];
-  const double2 s = iter == 0 ? sum_partials(I.part + I.cl_part_off, I.n_cl_part)
-                              : sum_partials(I.part + I.upd_part_off, I.n_upd_blocks);
+  const double rz = iter == 0 ? sum_partial(I.part + I.cl_part_off, I.n_cl_part, 0)
+                              : sum_partial(I.part + I.upd_part_off, I.n_upd_blocks, 0);
   if (threadIdx.x == 0) {
     double beta = 0.0;
     if (iter > 0) {
-      const bool stop = flag != 0.0 || !isfinite(s.x) || !(prev != 0.0);
-      beta = stop ? 0.0 : s.x / prev;
+      const bool stop = flag != 0.0 || !isfinite(rz) || !(prev != 0.0);
+      beta = stop ? 0.0 : rz / prev;
     }
     s_b = T(beta);
-    if (record) I.scal[kRz0 + (iter & 1)] = s.x;
+    if (record) I.scal[kRz0 + (iter & 1)] = rz;
   }
   __syncthreads();
   return s_b;

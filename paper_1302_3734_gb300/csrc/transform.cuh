@@ -89,11 +89,17 @@ struct Filt {
   // taps 2s + parity without a runtime array index
   __device__ __forceinline__ T hs(int parity, int s) const { return parity ? h[2 * s + 1] : h[2 * s]; }
   __device__ __forceinline__ T gs(int parity, int s) const { return parity ? g[2 * s + 1] : g[2 * s]; }
+  // FP32: the descriptor's FP32 copies of the taps; FP64: the taps themselves
   __device__ __forceinline__ void load(const InstDev &I) {
 #pragma unroll
     for (int t = 0; t < LF; ++t) {
-      h[t] = T(I.h[t]);
-      g[t] = T(I.g[t]);
+      if constexpr (sizeof(T) == 4) {
+        h[t] = I.hf[t];
+        g[t] = I.gf[t];
+      } else {
+        h[t] = I.h[t];
+        g[t] = I.g[t];
+      }
     }
   }
 };
