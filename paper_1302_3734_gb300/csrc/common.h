@@ -38,6 +38,7 @@ constexpr int kMaxEdgeSlots = 64;   // sensors with a pupil-edge term
 enum Scalar : int {
   kRz0 = 0,
   kRz1 = 1,
+  kBeta = 2,    // beta of the iteration, stored by the streamed coarse synthesis for its passes
   kFlag = 5,    // 1 after a breakdown (p.Ap <= 0 or not finite)
   kNumScalars = 8
 };
@@ -72,6 +73,7 @@ struct WfsDev {
   int act_off;                  // offset into the active-corner table (nc*nc)
   int run_off;                  // offset of the per-row valid runs (n+1 row offsets)
   int tt_idx;                   // slot among the sensors with a pupil-edge correction, -1 otherwise
+  float inv_sigma2_f;           // inv_sigma2 rounded to FP32 on the host (FP32 kernels read it)
   double inv_sigma2;
   double inv_S;                 // 1 / S (means of the slopes)
   double tt_scale;              // sigma^-2 / S

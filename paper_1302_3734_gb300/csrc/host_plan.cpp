@@ -273,6 +273,7 @@ tomo_status build_host_plan(const tomo_geometry *geo, HostPlan *P, std::string *
     d.kind = W.tt_only ? kTTOnly : (W.remove_tt ? kRemoveTT : kFull);
     d.is_lgs = lgs ? 1 : 0;
     d.inv_sigma2 = 1.0 / (W.sigma * W.sigma);
+    d.inv_sigma2_f = static_cast<float>(d.inv_sigma2);
     if (!(W.elong_tau >= 0.0 && W.elong_tau <= 1.0) || !std::isfinite(W.elong_scale) ||
         !std::isfinite(W.llt_x) || !std::isfinite(W.llt_y)) {
       snprintf(buf, sizeof buf, "sensor %d: elong_tau must be in [0, 1] and the elongation finite", m);

@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (NT == kFwdThreads ? 2 : 
   __syncthreads();
   // 2. weighted slopes of the subapertures the tile's corners touch
   Acc<T> sx_acc, sy_acc, qx_acc, qy_acc;
-  const T isg = T(W.inv_sigma2);
+  const T isg = sizeof(T) == 4 ? T(W.inv_sigma2_f) : T(W.inv_sigma2);   // no FP64 conversion in FP32
   // spot elongation: the block sigma^2 (I + tau g g^T) is inverted in closed
   // form, sigma^-2 (I - c g g^T) with c = tau / (1 + tau |g|^2)
   const bool elong = EL && W.elong != 0;
@@ -653,23 +653,11 @@ __global__ void __launch_bounds__(kAnalysisThreadsMax, 1) k_analysis(const InstD
   const int lgN = L.log2N, lgC = __ffs(C) - 1;
   int M = N, k = 1;
   for (; k <= J && M >= 2 * C; ++k, M >>= 1) {
-    const int lgM = lgN - (k - 1), lgH = lgM - 1, lgR = lgM - lgC;
+    const int lgM = lgN - (k - 1), lgR = lgM - lgC;
     const int R = M >> lgC, H = M >> 1, Rh = R >> 1;
     if (k > 1) cluster_wait();
     // row pass (x): local
-    for (int idx = tid; idx < R * H; idx += nt) {
-      const int j = idx >> lgH, i = idx & (H - 1);
-      const T *row = A + j * M;
-      T lo = T(0), hi = T(0);
-#pragma unroll
-      for (int t = 0; t < LF; ++t) {
-        const T x = row[(2 * i + t) & (M - 1)];
-        lo += f.h[t] * x;
-        hi += f.g[t] * x;
-      }
-      B[j * M + i] = lo;
-      B[j * M + H + i] = hi;
-    }
+    row_analysis<T, LF>(f, A, B, R, lgM, tid, nt);
     cluster.sync();
     // halo: the LF-2 rows after ours (mod M) from the next CTAs
     for (int idx = tid; idx < (LF - 2) * M; idx += nt) {
@@ -739,18 +727,7 @@ __global__ void __launch_bounds__(kAnalysisThreadsMax, 1) k_analysis(const InstD
       __syncthreads();
       for (; k <= J; ++k, M >>= 1) {
         const int H = M >> 1, lgMc = __ffs(M) - 1;
-        for (int idx = tid; idx < M * H; idx += nt) {
-          const int j = idx >> (lgMc - 1), i = idx & (H - 1);
-          T lo = T(0), hi = T(0);
-#pragma unroll
-          for (int t = 0; t < LF; ++t) {
-            const T x = cb[j * M + ((2 * i + t) & (M - 1))];
-            lo += f.h[t] * x;
-            hi += f.g[t] * x;
-          }
-          cb2[j * M + i] = lo;
-          cb2[j * M + H + i] = hi;
-        }
+        row_analysis<T, LF>(f, cb, cb2, M, lgMc, tid, nt);
         __syncthreads();
         for (int idx = tid; idx < H * M; idx += nt) {
           const int i = idx >> lgMc, x = idx & (M - 1);

@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(kPassThreads) k_dwt_pass(const InstDev *__rest
   const InstDev &I = sI;
   const LayerDev &L = I.layers[it.layer];
   const int J = I.J, tid = threadIdx.x, nt = blockDim.x;
-  const int lgM = L.log2N - (k - 1), M = 1 << lgM, H = M >> 1, lgH = lgM - 1;
+  const int lgM = L.log2N - (k - 1), M = 1 << lgM, H = M >> 1;
   constexpr int NR = 2 * kPassRows + LF - 2;
   T *X = reinterpret_cast<T *>(smem_raw);
   T *B = X + NR * M;
@@ -110,19 +110,7 @@ __global__ void __launch_bounds__(kPassThreads) k_dwt_pass(const InstDev *__rest
   cp_async_wait_all();
   __syncthreads();
   // row pass (x)
-  for (int idx = tid; idx < NR * H; idx += nt) {
-    const int j = idx >> lgH, i = idx & (H - 1);
-    const T *row = X + j * M;
-    T lo = T(0), hi = T(0);
-#pragma unroll
-    for (int t = 0; t < LF; ++t) {
-      const T x = row[(2 * i + t) & (M - 1)];
-      lo += f.h[t] * x;
-      hi += f.g[t] * x;
-    }
-    B[j * M + i] = lo;
-    B[j * M + H + i] = hi;
-  }
+  row_analysis<T, LF>(f, X, B, NR, lgM, tid, nt);
   __syncthreads();
   // column pass (y) and the epilogue, kEmitU outputs per thread at once
   for (int idx0 = tid; idx0 < kPassRows * M; idx0 += kEmitU * nt) {
@@ -204,19 +192,8 @@ __global__ void __launch_bounds__(kPassThreads) k_dwt_coarse(const InstDev *__re
   cp_async_wait_all();
   __syncthreads();
   for (int k = ks; k <= J; ++k, M >>= 1, --lgM) {
-    const int H = M >> 1, lgH = lgM - 1;
-    for (int idx = tid; idx < M * H; idx += nt) {
-      const int j = idx >> lgH, i = idx & (H - 1);
-      T lo = T(0), hi = T(0);
-#pragma unroll
-      for (int t = 0; t < LF; ++t) {
-        const T x = A[j * M + ((2 * i + t) & (M - 1))];
-        lo += f.h[t] * x;
-        hi += f.g[t] * x;
-      }
-      B[j * M + i] = lo;
-      B[j * M + H + i] = hi;
-    }
+    const int H = M >> 1;
+    row_analysis<T, LF>(f, A, B, M, lgM, tid, nt);
     __syncthreads();
     for (int idx0 = tid; idx0 < H * M; idx0 += kEmitU * nt) {
       T lo[kEmitU], hi[kEmitU];
@@ -261,7 +238,8 @@ __global__ void __launch_bounds__(kPassThreads) k_dwt_coarse(const InstDev *__re
 }
 
 // beta = (r.z)_iter / (r.z)_(iter-1) from the update's partials, as k_synthesis
-// forms it (0 at iteration 0 and after a breakdown); record: store (r.z)_iter.
+// forms it (0 at iteration 0 and after a breakdown); record: store (r.z)_iter
+// and beta itself, which the level passes that follow read (stored_beta).
 template <typename T>
 __device__ __forceinline__ T streamed_beta(const InstDev &I, int iter, bool record) {
   __shared__ T s_b;
@@ -276,8 +254,22 @@ __device__ __forceinline__ T streamed_beta(const InstDev &I, int iter, bool reco
       beta = stop ? 0.0 : rz / prev;
     }
     s_b = T(beta);
-    if (record) I.scal[kRz0 + (iter & 1)] = rz;
+    if (record) {
+      I.scal[kRz0 + (iter & 1)] = rz;
+      I.scal[kBeta] = beta;
+    }
   }
+  __syncthreads();
+  return s_b;
+}
+
+// beta of the iteration in a level pass: the coarse synthesis kernel, launched
+// before the passes of every streamed synthesis, formed and stored it, so the
+// passes' many CTAs do not each sum the update's partials on the FP64 pipe.
+template <typename T>
+__device__ __forceinline__ T stored_beta(const InstDev &I) {
+  __shared__ T s_b;
+  if (threadIdx.x == 0) s_b = T(I.scal[kBeta]);
   __syncthreads();
   return s_b;
 }
@@ -350,7 +342,7 @@ __device__ __forceinline__ SynthCoef<T, SRC> synth_coef(const InstDev &I, const 
 // the pyramid's block of side N >> (ks - 1) (with the direction update, all owned
 // here), the block synthesised level by level (rows, then columns), the result
 // to the scratch (the low-low input of level ks - 1) or, ks = 1, the output grid.
-// With SRC 1 this kernel records (r.z) of the iteration.
+// With SRC 1 this kernel records (r.z) and beta of the iteration.
 template <typename T, int SRC, int LF>
 __global__ void __launch_bounds__(kPassThreads) k_idwt_coarse(const InstDev *__restrict__ insts,
                                                               const PassItem *__restrict__ items, IoArgs io,
@@ -469,7 +461,7 @@ __global__ void __launch_bounds__(kPassThreads, 2) k_idwt_pass(const InstDev *__
   f.load(I);
   const T *ll = static_cast<const T *>(I.lls) + L.ll_off[k];
   pdl_wait();
-  const T beta = SRC == 1 ? streamed_beta<T>(I, flags >> kIterShift, false) : T(0);
+  const T beta = SRC == 1 ? stored_beta<T>(I) : T(0);
   const SynthCoef<T, SRC> coef = synth_coef<T, SRC>(I, io, it.inst, flags, beta);
   // the tile's coefficient rows: 16-byte vectors when every source is aligned (the plan's
   // buffers are; a caller's coefficient vector may not be), else kCoefU positions per

@@ -104,6 +104,65 @@ struct Filt {
   }
 };
 
+// Row analysis (x) of `rows` rows of side M = 2^lgM: the low half
+// B[j][i] = sum_t h[t] X[j][(2i + t) mod M] and the high half B[j][H + i] with
+// g, each sum over t = 0..LF-1 in that order, as in every other form of the
+// transform (so the results are the same bits).  FP32 rows of M >= 8 give a
+// thread two neighbouring output pairs from one window of LF + 2 inputs read
+// as 16-byte vectors (aligned: rows start on 16 bytes and the window on a
+// multiple of four, which also keeps the periodic wrap inside a vector);
+// other rows take one pair per thread.
+template <typename T, int LF>
+__device__ __forceinline__ void row_analysis(const Filt<T, LF> &f, const T *X, T *B, int rows, int lgM, int tid,
+                                             int nt) {
+  const int M = 1 << lgM, H = M >> 1;
+  if constexpr (sizeof(T) == 4) {
+    if (lgM >= 3) {
+      constexpr int NV = (LF + 5) / 4;   // vectors of a window of LF + 2 inputs
+      const int lgQ = lgM - 2;
+      for (int idx = tid; idx < (rows << lgQ); idx += nt) {
+        const int j = idx >> lgQ, q = idx & ((1 << lgQ) - 1);
+        const T *row = X + (j << lgM);
+        T w[4 * NV];
+#pragma unroll
+        for (int c = 0; c < NV; ++c) {
+          const float4 v = *reinterpret_cast<const float4 *>(row + ((4 * q + 4 * c) & (M - 1)));
+          w[4 * c] = v.x;
+          w[4 * c + 1] = v.y;
+          w[4 * c + 2] = v.z;
+          w[4 * c + 3] = v.w;
+        }
+        T lo0 = T(0), hi0 = T(0), lo1 = T(0), hi1 = T(0);
+#pragma unroll
+        for (int t = 0; t < LF; ++t) {
+          lo0 += f.h[t] * w[t];
+          hi0 += f.g[t] * w[t];
+          lo1 += f.h[t] * w[t + 2];
+          hi1 += f.g[t] * w[t + 2];
+        }
+        T *b = B + (j << lgM) + 2 * q;
+        *reinterpret_cast<float2 *>(b) = make_float2(lo0, lo1);
+        *reinterpret_cast<float2 *>(b + H) = make_float2(hi0, hi1);
+      }
+      return;
+    }
+  }
+  const int lgH = lgM - 1;
+  for (int idx = tid; idx < rows * H; idx += nt) {
+    const int j = idx >> lgH, i = idx & (H - 1);
+    const T *row = X + j * M;
+    T lo = T(0), hi = T(0);
+#pragma unroll
+    for (int t = 0; t < LF; ++t) {
+      const T x = row[(2 * i + t) & (M - 1)];
+      lo += f.h[t] * x;
+      hi += f.g[t] * x;
+    }
+    B[j * M + i] = lo;
+    B[j * M + H + i] = hi;
+  }
+}
+
 // Epilogue of the analysis for one output coefficient.
 enum Epi : int { kEpiPlain = 0, kEpiOp = 1, kEpiResid = 2 };
 
