@@ -542,11 +542,49 @@ __global__ void __launch_bounds__(kPassThreads, 2) k_idwt_pass(const InstDev *__
     }
   }
   __syncthreads();
-  // row synthesis (x): outputs 2m and 2m + 1 of a row from the same taps
+  // row synthesis (x): outputs 2m and 2m + 1 of a row from the same taps.  VH
+  // follows VL (rows NI.. are the high-y rows) and XH follows XL.
   const int lgH = lgM - 1;
+  bool rows_done = false;
+  if constexpr (sizeof(T) == 4 && LF <= 10) {
+    if (lgH >= 2) {
+      // FP32: four neighbouring m per thread from the low and high halves'
+      // inputs m - 4 .. m + 3, two 16-byte vectors each (a multiple of four,
+      // so a vector never straddles the periodic wrap), every output's sum in
+      // the order of the scalar form below
+      const int lgQ = lgH - 2;
+      for (int idx = tid; idx < ((2 * NI) << lgQ); idx += nt) {
+        const int r = idx >> lgQ, m0 = (idx & ((1 << lgQ) - 1)) << 2;
+        const T *row = VL + r * M;
+        T lo[8], hi[8];
+        *reinterpret_cast<float4 *>(lo) = *reinterpret_cast<const float4 *>(row + ((m0 - 4) & (H - 1)));
+        *reinterpret_cast<float4 *>(lo + 4) = *reinterpret_cast<const float4 *>(row + m0);
+        *reinterpret_cast<float4 *>(hi) = *reinterpret_cast<const float4 *>(row + H + ((m0 - 4) & (H - 1)));
+        *reinterpret_cast<float4 *>(hi + 4) = *reinterpret_cast<const float4 *>(row + H + m0);
+        T o[8];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          T even = T(0), odd = T(0);
+#pragma unroll
+          for (int s = 0; s < LF / 2; ++s) {
+            const T l = lo[4 + u - s], h = hi[4 + u - s];
+            even += f.h[2 * s] * l + f.g[2 * s] * h;
+            odd += f.h[2 * s + 1] * l + f.g[2 * s + 1] * h;
+          }
+          o[2 * u] = even;
+          o[2 * u + 1] = odd;
+        }
+        T *x = XL + r * M + 2 * m0;
+        *reinterpret_cast<float4 *>(x) = *reinterpret_cast<const float4 *>(o);
+        *reinterpret_cast<float4 *>(x + 4) = *reinterpret_cast<const float4 *>(o + 4);
+      }
+      rows_done = true;
+    }
+  }
+  if (!rows_done)
   for (int idx = tid; idx < 2 * NI * H; idx += nt) {
     const int r = idx >> lgH, m = idx & (H - 1);
-    const T *row = VL + r * M;   // VH follows VL: rows NI.. are the high-y rows
+    const T *row = VL + r * M;
     T even = T(0), odd = T(0);
 #pragma unroll
     for (int s = 0; s < LF / 2; ++s) {
@@ -555,7 +593,7 @@ __global__ void __launch_bounds__(kPassThreads, 2) k_idwt_pass(const InstDev *__
       even += f.h[2 * s] * lo + f.g[2 * s] * hi;
       odd += f.h[2 * s + 1] * lo + f.g[2 * s + 1] * hi;
     }
-    XL[r * M + 2 * m] = even;   // XH follows XL
+    XL[r * M + 2 * m] = even;
     XL[r * M + 2 * m + 1] = odd;
   }
   __syncthreads();
