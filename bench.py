@@ -42,21 +42,30 @@ METRIC = "tomography solves/s and p99 frame latency at 84x84 MCAO vs plain GPU P
 
 
 # DRAM bytes (read + write) per launch of each PCG kernel on this workload, from one ncu capture
-# with flushed caches, valid only for the kernel source file they were taken from.
+# with flushed caches, valid only for the kernel sources they were taken from (a SHA-256 over
+# these files of paper_1302_3734_gb300/csrc, in this order).
 NCU_TRAFFIC = {
-    "kernels_cu_sha256": "daadef8a22e8a637dd96cb8200989375bec6d8592bd61adaa38d15aad24d3ab7",
-    "bytes": {"analysis": 5136256, "synthesis": 1843072, "forward": 749312, "update": 2985344},
+    "sources": ["kernels.cu", "transform.cuh", "device_util.cuh", "adjoint.cuh", "common.h"],
+    "sha256": "e8bcd2fe627f0f1f28c3a5b33cdb90d1ccbe9aea8a6d05076a506424cac1c457",
+    "bytes": {"analysis": 5139456, "synthesis": 1843456, "forward": 749312, "update": 2985728},
 }
 
 
-def ncu_traffic(kind):
+def sources_digest():
     import hashlib
-    path = os.path.join(ROOT, "paper_1302_3734_gb300", "csrc", "kernels.cu")
+    h = hashlib.sha256()
+    for name in NCU_TRAFFIC["sources"]:
+        with open(os.path.join(ROOT, "paper_1302_3734_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def ncu_traffic(kind):
     try:
-        digest = hashlib.sha256(open(path, "rb").read()).hexdigest()
+        digest = sources_digest()
     except OSError:
         return None
-    return NCU_TRAFFIC["bytes"].get(kind) if digest == NCU_TRAFFIC["kernels_cu_sha256"] else None
+    return NCU_TRAFFIC["bytes"].get(kind) if digest == NCU_TRAFFIC["sha256"] else None
 
 
 def l2_probe(pkg, torch, dev):
@@ -764,8 +773,9 @@ def bench_served(pkg, torch, args, dev, frames_per_tel=16, rate_hz=500.0):
 def profile_leg(args):
     """One workload's solves and nothing else, so a profiler's launch list holds only them:
     eelt (the E-ELT frame, 10 warm PCG iterations, graph), batch16 (16 E-ELT instances at
-    cluster size 2), uneven64 (the 64 uneven instances at cluster size 4), large (the 100 m
-    system, 20 cold PCG iterations).  Plans are built before the first solve."""
+    cluster size 2, streamed transforms), uneven64 (the 64 uneven instances at cluster size 4,
+    streamed transforms), large (the 100 m system, 20 cold PCG iterations).  The batches take
+    the autotuner's pick of the batched legs.  Plans are built before the first solve."""
     import torch
     import paper_1302_3734_gb300 as pkg
     from paper_1302_3734_gb300 import build
@@ -773,18 +783,20 @@ def profile_leg(args):
     build.build()
     dev = torch.device("cuda", 0)
     leg = args.profile_leg
+    tf = 0
     if leg == "large":
         geoms, C, iters, warm = [configs.config4()], 0, 20, False
     elif leg == "uneven64":
-        geoms, C, iters, warm = configs.config2(), 4, 10, True
+        geoms, C, iters, warm, tf = configs.config2(), 4, 10, True, 2
     else:
         geoms, C, iters, warm = [configs.config1()] * (16 if leg == "batch16" else 1), (2 if leg == "batch16" else 0), 10, True
+        tf = 2 if leg == "batch16" else 0
     plans = []
     for g in geoms:
         cc = C
         while True:
             try:
-                plans.append(pkg.Plan(g, cluster_size=cc))
+                plans.append(pkg.Plan(g, cluster_size=cc, transforms=tf))
                 break
             except pkg.TomoError as e:
                 if e.status not in (1, 8) or cc == 0 or cc >= 16:
