@@ -3,7 +3,8 @@ level over row tiles of every layer, without thread-block clusters, with the
 PCG epilogue and the fused direction update of the cluster kernels.  Every
 operator and the fixed-iteration solve against the FP64 oracle at the
 tolerances of the cluster path, on grids that use only the coarse kernel
-(32^2), one pass (128^2) and two passes (256^2, db4), in FP32 and FP64; a
+(32^2), one pass (128^2; also Haar and db2) and two passes (256^2, db4), in FP32
+and FP64; a
 streamed batch of uneven plans is bitwise the plans solved alone, and the
 streamed and cluster paths agree to rounding.
 """
@@ -22,6 +23,15 @@ CASES = {
     "one-pass-128": lambda: configs.small_lgs_config(n_sub=40, N=128, n_layers=3, levels=3, order=3),
     "two-pass-256-db4": lambda: configs.small_lgs_config(n_sub=48, N=256, n_layers=2, levels=4, order=4),
     "one-pass-128-fp64": lambda: configs.small_lgs_config(n_sub=40, N=128, n_layers=2, levels=3, precision=1),
+}
+
+
+# the shortest filters (Haar and db2, lengths 2 and 4) through one streamed pass: the vector
+# windows of the row analysis and synthesis at their narrowest (Haar leaves the synthesis
+# window's first vector unused)
+SHORT = {
+    "one-pass-128-haar": lambda: configs.small_lgs_config(n_sub=40, N=128, n_layers=2, levels=3, order=1),
+    "one-pass-128-db2": lambda: configs.small_lgs_config(n_sub=40, N=128, n_layers=2, levels=3, order=2),
 }
 
 
@@ -141,7 +151,43 @@ def test_streamed_batch_is_bitwise_single_and_close_to_clusters(lib):
         p.close()
 
 
-@pytest.mark.parametrize("name", ["eelt", "one-pass-128", "elongated-32", "one-pass-128-fp64"])
+@pytest.mark.parametrize("name", list(SHORT))
+def test_streamed_short_filters(lib, name):
+    """Haar and db2 through the streamed passes: W, W^-1, the normal operator and the
+    right-hand side against the FP64 oracle, and a three-iteration cold solve."""
+    torch, pkg = lib
+    g = SHORT[name]()
+    plan = pkg.Plan(g, transforms=2)
+    assert plan.info.streamed == 1 and plan.info.gather_separate == 1
+    ora = Tomography(g)
+    dt = torch.float32
+    rng = np.random.default_rng(28)
+    c = rng.standard_normal(plan.n)
+    out = torch.full((plan.n,), float("nan"), dtype=dt, device="cuda")
+    plan.coeffs_to_layers(torch.tensor(c, dtype=dt, device="cuda"), out)
+    e = rel(out.double().cpu().numpy(), ora.join(ora.synthesis(c)), f"streamed-synthesis/{name}")
+    assert e < 2e-6, e
+    plan.layers_to_coeffs(torch.tensor(c, dtype=dt, device="cuda"), out)
+    e = rel(out.double().cpu().numpy(), ora.analysis(ora.split(c)), f"streamed-analysis/{name}")
+    assert e < 2e-6, e
+    plan.apply_normal(torch.tensor(c, dtype=dt, device="cuda"), out)
+    e = rel(out.double().cpu().numpy(), ora.apply_normal(c), f"streamed-normal/{name}")
+    assert e < 1e-5, e
+    s = rng.standard_normal(plan.n_slopes)
+    plan.rhs(torch.tensor(s, dtype=dt, device="cuda"), out)
+    e = rel(out.double().cpu().numpy(), ora.rhs(s), f"streamed-rhs/{name}")
+    assert e < 1e-5, e
+    phis = FrozenFlow(g, 5).layers(0.002)
+    sl = ora.measure(phis) + gaussian_noise(plan.n_slopes, 0.1, 1_000_029)
+    x_ref = ora.pcg(ora.rhs(sl), np.zeros(plan.n), 3, ora.jacobi_diagonal())
+    x = torch.zeros(plan.n, dtype=dt, device="cuda")
+    plan.solve(torch.tensor(sl, dtype=dt, device="cuda"), x, 3, warm=False)
+    e = rel(x.double().cpu().numpy(), x_ref, f"streamed-solve-3it/{name}")
+    assert e < 1e-5, e
+    plan.close()
+
+
+@pytest.mark.parametrize("name", ["eelt", "one-pass-128", "elongated-32", "one-pass-128-fp64"] + list(SHORT))
 def test_cluster_and_streamed_paths_are_bitwise_the_same(lib, name):
     """Two independent implementations of every operator: thread-block clusters
     with the gather fused into the analysis (tables staged in shared memory), and
@@ -153,7 +199,7 @@ def test_cluster_and_streamed_paths_are_bitwise_the_same(lib, name):
          "one-pass-128": CASES["one-pass-128"],
          "elongated-32": lambda: configs.with_elongation(configs.small_lgs_config(16, 32, 3, 2),
                                                          spot_fwhm_arcsec=0.5),
-         "one-pass-128-fp64": CASES["one-pass-128-fp64"]}[name]()
+         "one-pass-128-fp64": CASES["one-pass-128-fp64"], **SHORT}[name]()
     dt = torch.float64 if g["precision"] else torch.float32
     outs = []
     for tf in (1, 2):
